@@ -1,0 +1,188 @@
+"""Plain CPU oracle for multifaceted 4D segmentation (Sauer & Ma, arXiv 1903.12294).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()`` and by the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``. The GPU library never imports,
+links or runs anything from here, and nothing here uses the GPU library.
+
+The arithmetic lives in ``msf_oracle.c`` (plain C, fp64), built with gcc into
+``liborc.so`` beside it; this module only marshals numpy arrays through ctypes.
+
+Functions and the passages they follow:
+  ``bin``       - §3.1 preprocessing index (point samples -> field voxels, per-voxel aggregates)
+  ``segment``   - combined field+point membership (§3.2, choice of variables) and 4D connected
+                  components by breadth-first flood fill (connectivity is this library's
+                  definition; the paper's clustering imposes none, §3.3)
+  ``features``  - per-feature averages (§3.2.2 cluster centre), extent and deviations (§3.4)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "msf_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+SRC_FIELD, SRC_COUNT, SRC_MEAN = 0, 1, 2
+OP_GT, OP_GE, OP_LT, OP_LE, OP_BAND = 0, 1, 2, 3, 4
+EDGE_SPATIAL, EDGE_TEMPORAL, EDGE_TRAJ = 1, 2, 4
+EDGE_ALL = EDGE_SPATIAL | EDGE_TEMPORAL | EDGE_TRAJ
+
+
+def build(force: bool = False) -> str:
+    """Compile msf_oracle.c with gcc (portable flags only: the same source builds on x86 and Arm)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(
+            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+            check=True,
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Pred(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_int32), ("attr", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("lo", ctypes.c_float), ("hi", ctypes.c_float)]
+
+
+class _Criteria(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_int32), ("t1", ctypes.c_int32), ("n_pred", ctypes.c_int32),
+                ("pred", _Pred * 4), ("edges", ctypes.c_uint32)]
+
+
+class _FeatOut(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in (
+        "label", "n_vox", "n_pts", "bbox", "sum_field", "mean_field", "std_field", "min_field",
+        "max_field", "centroid", "sumq", "mean_attr", "std_attr")]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            lib.oracle_bin.argtypes = [ctypes.c_int] * 4 + [i64, ctypes.c_int] + [P] * 8
+            lib.oracle_bin.restype = ctypes.c_int
+            lib.oracle_segment.argtypes = [ctypes.c_int] * 4 + [P, P, P, i64, P,
+                                                                ctypes.POINTER(_Criteria), P, P]
+            lib.oracle_segment.restype = ctypes.c_int
+            lib.oracle_features.argtypes = ([ctypes.c_int] * 4 + [P, P, i64, ctypes.c_int, P, P,
+                                            P, ctypes.c_int, ctypes.c_int, P, i64,
+                                            ctypes.POINTER(_FeatOut), P])
+            lib.oracle_features.restype = ctypes.c_int
+            lib.oracle_scale_exponent.argtypes = [ctypes.c_double, i64]
+            lib.oracle_scale_exponent.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else ctypes.c_void_p(0)
+
+
+def scale_exponent(max_abs: float, n_samples: int) -> int:
+    """k = 62 - e - b of the fixed-point attribute sums (see ``msf_oracle.c``)."""
+    return int(_load().oracle_scale_exponent(float(max_abs), int(n_samples)))
+
+
+def bin(field_shape, pos, attr, keep_sumq=True):
+    """§3.1 preprocessing index. ``field_shape`` = (T, NZ, NY, NX); ``pos`` [T][3][P] fp32;
+    ``attr`` [T][A][P] fp32. Returns dict key, count, sumq, mean, kscale, outside."""
+    T, nz, ny, nx = (int(s) for s in field_shape)
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    P = pos.shape[2]
+    attr = np.ascontiguousarray(attr, dtype=np.float32)
+    if attr.ndim != 3 or attr.shape[0] != T or attr.shape[2] != P:
+        raise ValueError("attr must be [T][A][P]")
+    A = attr.shape[1]
+    key = np.empty((T, P), np.int32)
+    count = np.empty((T, nz, ny, nx), np.int32)
+    sumq = np.empty((A, T, nz, ny, nx), np.int64) if keep_sumq else None
+    mean = np.empty((A, T, nz, ny, nx), np.float32)
+    kscale = np.zeros(max(A, 1), np.int32)
+    outside = np.empty(T, np.int64)
+    rc = _load().oracle_bin(nx, ny, nz, T, P, A, _ptr(pos), _ptr(attr), _ptr(key), _ptr(count),
+                            _ptr(sumq), _ptr(mean), _ptr(kscale), _ptr(outside))
+    if rc != 0:
+        raise RuntimeError(f"oracle_bin failed: {rc}")
+    return dict(key=key, count=count, sumq=sumq, mean=mean, kscale=kscale[:A], outside=outside)
+
+
+def make_criteria(t0, t1, preds=(), edges=EDGE_ALL):
+    """preds: sequence of (src, attr, op, lo, hi)."""
+    c = _Criteria()
+    c.t0, c.t1, c.n_pred, c.edges = int(t0), int(t1), len(preds), int(edges)
+    if len(preds) > 4:
+        raise ValueError("at most 4 predicates")
+    for i, (src, a, op, lo, hi) in enumerate(preds):
+        c.pred[i] = _Pred(int(src), int(a), int(op), float(lo), float(hi))
+    return c
+
+
+def segment(field, count, mean, key, t0, t1, preds=(), edges=EDGE_ALL):
+    """Criterion + 4D connected components. Returns (labels [Tw][NZ][NY][NX] int32, n_features)."""
+    field = np.ascontiguousarray(field, dtype=np.float32)
+    T, nz, ny, nx = field.shape
+    count = np.ascontiguousarray(count, dtype=np.int32)
+    mean = np.ascontiguousarray(mean, dtype=np.float32)
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    P = key.shape[1] if key.ndim == 2 else 0
+    crit = make_criteria(t0, t1, preds, edges)
+    labels = np.empty((max(t1 - t0, 0), nz, ny, nx), np.int32)
+    nf = ctypes.c_int64(0)
+    rc = _load().oracle_segment(nx, ny, nz, T, _ptr(field), _ptr(count), _ptr(mean), P,
+                                _ptr(key), ctypes.byref(crit), _ptr(labels), ctypes.byref(nf))
+    if rc != 0:
+        raise RuntimeError(f"oracle_segment failed: {rc}")
+    return labels, int(nf.value)
+
+
+def features(field, count, attr, key, kscale, t0, t1, labels):
+    """Per-feature statistics, ascending label order. Returns a dict of numpy arrays."""
+    field = np.ascontiguousarray(field, dtype=np.float32)
+    T, nz, ny, nx = field.shape
+    count = np.ascontiguousarray(count, dtype=np.int32)
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    P = key.shape[1] if key.ndim == 2 else 0
+    attr = np.ascontiguousarray(attr, dtype=np.float32)
+    A = attr.shape[1] if attr.ndim == 3 else 0
+    kscale = np.ascontiguousarray(np.asarray(kscale, dtype=np.int32).reshape(-1))
+    if kscale.size == 0:
+        kscale = np.zeros(1, np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    nf = int(np.count_nonzero(labels.reshape(-1) == np.arange(labels.size, dtype=np.int64)))
+    Af = max(A, 1)
+    out = dict(
+        label=np.empty(nf, np.int32), n_vox=np.empty(nf, np.int64), n_pts=np.empty(nf, np.int64),
+        bbox=np.empty((nf, 8), np.int32), sum_field=np.empty(nf, np.float64),
+        mean_field=np.empty(nf, np.float64), std_field=np.empty(nf, np.float64),
+        min_field=np.empty(nf, np.float32), max_field=np.empty(nf, np.float32),
+        centroid=np.empty((nf, 4), np.float64), sumq=np.empty((nf, Af), np.int64),
+        mean_attr=np.empty((nf, Af), np.float64), std_attr=np.empty((nf, Af), np.float64))
+    fo = _FeatOut(*[_ptr(out[n]) for n, _ in _FeatOut._fields_])
+    n_out = ctypes.c_int64(0)
+    rc = _load().oracle_features(nx, ny, nz, T, _ptr(field), _ptr(count), P, A, _ptr(attr),
+                                 _ptr(key), _ptr(kscale), int(t0), int(t1), _ptr(labels), nf,
+                                 ctypes.byref(fo), ctypes.byref(n_out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_features failed: {rc}")
+    for n in ("sumq", "mean_attr", "std_attr"):
+        out[n] = out[n][:, :A]
+    return out
+
+
+def run_all(field, pos, attr, t0, t1, preds, edges=EDGE_ALL):
+    """bin -> segment -> features in one call (the whole path, CPU)."""
+    b = bin(field.shape, pos, attr, keep_sumq=False)
+    labels, nf = segment(field, b["count"], b["mean"], b["key"], t0, t1, preds, edges)
+    f = features(field, b["count"], attr, b["key"], b["kscale"], t0, t1, labels)
+    return b, labels, nf, f
