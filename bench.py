@@ -1,0 +1,356 @@
+"""Benchmark: one step = the whole hot path (bin -> criterion + 4D labelling -> per-feature
+statistics) over the mid workload: 128^3 fp32 field x 32 timesteps, 1M particles with two
+attributes, criterion field > 0.5 AND mean speed in [q40, q90], all edge classes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config 2]
+
+Prints one JSON line. ``value`` is voxel-timesteps per second (Gvt/s) with the dataset
+resident in HBM; ``e2e`` is the same metric through the C ABI with host buffers (the
+host->device copy of the field and particles and the device->host copy of the labels and the
+feature table inside every step). Under torchrun each rank runs its own replica (the path has
+no exchange step for independent workloads): weak scaling, value = all ranks' voxel-timesteps
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gvoxel-timesteps/s per segment query (% HBM roofline); batched queries/s, p99"
+UNIT = "Gvoxel-timesteps/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+        return self
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# per-kernel algorithmic bytes (the minimum each kernel must move through HBM per launch)
+def algorithmic_bytes(name, wl, n_pred_arrays, labels_active):
+    T, nz, ny, nx = wl.field.shape
+    V = nx * ny * nz
+    tw = wl.t1 - wl.t0
+    P = wl.pos.shape[2]
+    A = wl.attr.shape[1]
+    return {
+        "k_scatter": P * (12 + 4 * A + 4),                   # per timestep: pos+attr in, key out
+        "k_finalise": V * (4 + 4 * A),                       # per timestep: count + means out
+        "k_tile": V * tw * 4 * n_pred_arrays + V * tw // 32 * 8,
+        "k_final": V * tw * 4,
+        "k_traj": P * tw * 4,
+        "k_rootbits": V * tw * 4,
+        "k_vox": V * tw * 4 + labels_active * 8,
+        "k_pts": P * tw * (4 + 4 * A),
+    }.get(name)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1903_12294_gb300 import build as libbuild
+    from paper_1903_12294_gb300 import msf, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = synth.make(args.config, device=dev)
+    T, nz, ny, nx = wl.field.shape
+    V = nx * ny * nz
+    tw = wl.t1 - wl.t0
+    vt = V * tw
+    stream = torch.cuda.current_stream(dev)
+    ctx = msf.Context(local, stream)
+    crit = msf.make_criteria(wl.t0, wl.t1, wl.preds, wl.edges)
+    labels = torch.empty((tw, nz, ny, nx), dtype=torch.int32, device=dev)
+    fcap = 1 << 22
+    feats = torch.empty((fcap * msf.FEATURE_DTYPE.itemsize,), dtype=torch.uint8, device=dev)
+    lib = msf.load_library()
+    nf_out = msf.ctypes.c_int64(0)
+
+    ctx.load(wl.field, wl.pos, wl.attr)
+
+    def step():
+        msf.msf_bin_particles(ctx.h, 0)
+        n = msf.msf_segment(ctx.h, crit, labels)
+        st = lib.msf_extract_features(ctx.h, msf.ctypes.byref(crit), labels.data_ptr(),
+                                      msf.MSF_DEVICE, feats.data_ptr(), msf.MSF_DEVICE, fcap,
+                                      msf.ctypes.byref(nf_out))
+        if st != 0:
+            raise msf.MsfError(st, "msf_extract_features")
+        return n
+
+    for _ in range(args.warmup):
+        n_features = step()
+    torch.cuda.synchronize()
+    ctx.kernel_times(reset=True)
+    ctx.profiling(True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            n_features = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ktimes = ctx.kernel_times(reset=True)
+    ctx.profiling(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * vt / (ms * 1e-3) / 1e9
+    launches = sum(n for _, n in ktimes.values()) // max(args.steps, 1)
+
+    # dominant kernel and its roofline
+    lab_active = int((labels >= 0).sum().item())
+    npa = len({(s, a if s == 2 else 0) for s, a, *_ in wl.preds})
+    dom = max(ktimes.items(), key=lambda kv: kv[1][0])
+    name, (tot_ms, nl) = dom
+    per_launch_ms = tot_ms / nl
+    ab = algorithmic_bytes(name, wl, npa, lab_active)
+    peak, peak_kind = peaks()
+    roof = None
+    if ab is not None:
+        ach = ab / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": None, "algorithmic_bytes_per_launch": ab,
+                "avg_launch_ms": round(per_launch_ms, 5)}
+    per_kernel = {k: {"ms_per_step": round(v[0] / args.steps, 4),
+                      "launches_per_step": v[1] // max(args.steps, 1)} for k, v in ktimes.items()}
+    seg_ms = sum(v[0] for k, v in ktimes.items()
+                 if k in ("k_tile", "k_hook", "k_traj", "k_flatten", "k_final")) / args.steps
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hf = wl.field.cpu().pin_memory()
+        hp = wl.pos.cpu().pin_memory()
+        ha = wl.attr.cpu().pin_memory()
+        hl = torch.empty((tw, nz, ny, nx), dtype=torch.int32).pin_memory()
+        hfeat = np.zeros(fcap, msf.FEATURE_DTYPE)
+
+        def e2e_step():
+            ctx.load(hf, hp, ha)
+            msf.msf_bin_particles(ctx.h, 0)
+            msf.msf_segment(ctx.h, crit, hl)
+            st = lib.msf_extract_features(ctx.h, msf.ctypes.byref(crit), hl.data_ptr(),
+                                          msf.MSF_HOST, hfeat.ctypes.data, msf.MSF_HOST, fcap,
+                                          msf.ctypes.byref(nf_out))
+            if st != 0:
+                raise msf.MsfError(st, "msf_extract_features")
+            return int(nf_out.value)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            nfe = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / args.steps * 1e3
+        ms_e2e = max(e0.elapsed_time(e1) / args.steps, wall)
+        if world > 1:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        h2d = hf.numel() * 4 + hp.numel() * 4 + ha.numel() * 4
+        d2h = hl.numel() * 4 + nfe * msf.FEATURE_DTYPE.itemsize
+        e2e = {"value": round(world * vt / (ms_e2e * 1e-3) / 1e9, 3), "unit": UNIT,
+               "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    ctx.close()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {nx}x{ny}x{nz} fp32 field x {T} timesteps, "
+                                   f"{wl.pos.shape[2]} particles x {wl.attr.shape[1]} attributes, "
+                                   f"window [{wl.t0},{wl.t1}), preds {wl.preds}",
+                       "step": "bin + criterion/label + features", "vt_per_step": vt,
+                       "n_features": int(n_features),
+                       "l2": "inputs larger than L2 (field alone 4*V*T bytes)",
+                       "parallelism": f"replicas x{world}"},
+            "segment_only": {"ms": round(seg_ms, 4),
+                             "value": round(vt / (seg_ms * 1e-3) / 1e9, 3) if seg_ms else None,
+                             "unit": UNIT},
+            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches),
+            "kernels": per_kernel, "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(wl, t_lo, t_hi):
+    """The oracle on timesteps [t_lo, t_hi) of the workload (bin + segment + features)."""
+    import oracle
+    f = wl.field[t_lo:t_hi].cpu().numpy()
+    p = wl.pos[t_lo:t_hi].cpu().numpy()
+    a = wl.attr[t_lo:t_hi].cpu().numpy()
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.run_all(f, p, a, 0, t_hi - t_lo, wl.preds, wl.edges)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, steps_in_sample=8):
+    T, nz, ny, nx = wl.field.shape
+    n = min(steps_in_sample, wl.t1 - wl.t0)
+    secs = _oracle_sample(wl, wl.t0, wl.t0 + n)
+    vt = nx * ny * nz * n
+    return {"value": round(vt / secs / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"timesteps [{wl.t0},{wl.t0 + n}) of the workload ({vt} voxel-timesteps, "
+                      f"{wl.pos.shape[2]} particles): bin + segment + features, single thread",
+            "seconds": round(secs, 3)}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle, timed on the host cores, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+
+    from paper_1903_12294_gb300 import synth
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    wl = synth.make(args.config, device=dev)
+    T, nz, ny, nx = wl.field.shape
+    n = 2   # timesteps per step sample
+    for _ in range(args.warmup):
+        _oracle_sample(wl, wl.t0, wl.t0 + n)
+    secs = [_oracle_sample(wl, wl.t0, wl.t0 + n) for _ in range(args.steps)]
+    ms = statistics.mean(secs) * 1e3
+    vt = nx * ny * nz * n
+    value = vt / (ms * 1e-3) / 1e9
+    sample = (f"timesteps [{wl.t0},{wl.t0 + n}) of the workload per step ({vt} voxel-timesteps): "
+              "bin + segment + features, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name, "sample": sample},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * msf.h - C ABI of the GB300 library for multifaceted 4D feature segmentation
+ *         (Sauer & Ma, "Multifaceted 4D Feature Segmentation and Extraction in Point and
+ *          Field-based Datasets", arXiv 1903.12294).
+ *
+ * A dataset is a time-varying regular-grid field plus a set of points (particles, vehicles)
+ * that move over the same timesteps (§3.1, "Data Representation"). The library keeps one such
+ * dataset resident on one GPU and answers segmentation queries over it:
+ *
+ *   msf_load_timesteps    copy the field and point samples to the device (§3.1)
+ *   msf_bin_particles     the §3.1 preprocessing index: voxel of every point sample, and per
+ *                         (voxel, timestep) the sample count and attribute aggregates
+ *   msf_segment           combined field + point membership criterion (§3.2: variables chosen
+ *                         from both data types) and 4D connected features -> int32 labels
+ *   msf_extract_features  per-feature statistics: averages of position, point value and field
+ *                         value (the cluster centre of §3.2.2), spatio-temporal extent and
+ *                         standard deviations (§3.4)
+ *   msf_segment_batch     many queries (own thresholds, attributes, windows) in one launch
+ *
+ * Connectivity. The paper's own clustering imposes no spatio-temporal connectivity (§3.3). A
+ * feature here is a connected component of the graph whose vertices are the voxel-timesteps
+ * inside the query window that meet the criterion, with edges
+ *   MSF_EDGE_SPATIAL   26-neighbour adjacency within a timestep (8-neighbour when nz == 1)
+ *   MSF_EDGE_TEMPORAL  the same voxel at t and t+1
+ *   MSF_EDGE_TRAJ      trajectory links: a point in voxel a at t and in voxel b at t+1
+ *                      (points form trajectories through their fixed id, §3.1)
+ * Labels are canonical: each labelled voxel-timestep holds the smallest window-linear index
+ *   li = (((t - t0) * nz + z) * ny + y) * nx + x
+ * of its component, and -1 when it fails the criterion. The result is therefore unique and
+ * does not depend on scheduling, and a query gives the same labels alone and in a batch.
+ *
+ * Conventions.
+ *  - Every entry point returns MSF_OK (0) or a negative MSF_ERR_* code; msf_status_string()
+ *    names it. A failed call leaves the context usable unless it returns MSF_ERR_CUDA.
+ *  - Pointers are plain host or device addresses. Where an argument may be either, a
+ *    *_kind argument says which (MSF_HOST / MSF_DEVICE). Device pointers must belong to the
+ *    context's device.
+ *  - The caller owns every buffer it passes; the library copies inputs it keeps and never
+ *    frees caller memory. The context owns all device memory it allocates (resident dataset,
+ *    per-query scratch), released by msf_destroy.
+ *  - All work is issued on the context's CUDA stream (msf_create / msf_set_stream). Calls
+ *    that return host-visible results synchronise that stream before returning.
+ *  - One context per host thread; a context is not safe for concurrent calls.
+ */
+#ifndef MSF_H
+#define MSF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define MSF_OK 0
+#define MSF_ERR_INVALID_ARG (-1)   /* bad pointer, size, window, predicate or flag          */
+#define MSF_ERR_NOT_LOADED (-2)    /* no dataset loaded                                     */
+#define MSF_ERR_NOT_BINNED (-3)    /* msf_bin_particles has not run on the loaded dataset   */
+#define MSF_ERR_OUT_OF_MEMORY (-4) /* device allocation failed                              */
+#define MSF_ERR_TOO_LARGE (-5)     /* window has >= 2^31 voxel-timesteps, or a size limit   */
+#define MSF_ERR_TIMEOUT (-6)       /* a bounded device wait gave up                         */
+#define MSF_ERR_CUDA (-7)          /* a CUDA runtime call failed                            */
+#define MSF_ERR_CAPACITY (-8)      /* output buffer too small; the needed count is returned */
+#define MSF_ERR_INTERNAL (-9)      /* a device-side consistency check failed                */
+
+/* ---- enums ------------------------------------------------------------------------------- */
+enum { MSF_HOST = 0, MSF_DEVICE = 1 };
+
+/* Predicate source: the field value v_f(t), the number of point samples in the voxel, or the
+ * mean of one point attribute v_p(t) over those samples (§3.1, §3.2). */
+enum { MSF_SRC_FIELD = 0, MSF_SRC_COUNT = 1, MSF_SRC_MEAN = 2 };
+
+/* Comparison. BAND is lo <= x <= hi (inclusive). Any comparison with NaN (an empty voxel's
+ * mean) is false. COUNT predicates compare the integer count with (int32_t)lo / (int32_t)hi
+ * (truncation toward zero); their thresholds must lie in the int32 range. */
+enum { MSF_OP_GT = 0, MSF_OP_GE = 1, MSF_OP_LT = 2, MSF_OP_LE = 3, MSF_OP_BAND = 4 };
+
+enum { MSF_EDGE_SPATIAL = 1, MSF_EDGE_TEMPORAL = 2, MSF_EDGE_TRAJ = 4, MSF_EDGE_ALL = 7 };
+
+/* msf_bin_particles flags */
+enum { MSF_BIN_KEEP_SUMQ = 1 };  /* also keep the int64 per-voxel attribute sums */
+
+#define MSF_MAX_PRED 4
+#define MSF_MAX_ATTR 8
+
+/* ---- types ------------------------------------------------------------------------------- */
+typedef struct msf_ctx msf_ctx;
+
+typedef struct {
+  int32_t src;  /* MSF_SRC_*                                  */
+  int32_t attr; /* attribute index for MSF_SRC_MEAN, else 0   */
+  int32_t op;   /* MSF_OP_*                                   */
+  float lo, hi; /* threshold(s); hi used by MSF_OP_BAND only  */
+} msf_pred;
+
+/* A segmentation query: window [t0, t1) of absolute timesteps, the AND of n_pred predicates
+ * (n_pred = 0 selects every voxel-timestep), and the edge classes to use. */
+typedef struct {
+  int32_t t0, t1;
+  int32_t n_pred;
+  msf_pred pred[MSF_MAX_PRED];
+  uint32_t edges; /* MSF_EDGE_* bits */
+} msf_criteria;
+
+/* Binning summary. Attribute a is summed in fixed point: q = round_half_even(v * 2^kscale[a])
+ * with kscale[a] = 62 - e - b, where max|v| < 2^e over finite samples and 2^b >= P*T + 1, so
+ * every int64 sum is exact and the per-voxel fp32 mean
+ *   mean = (float)((double)sumq / ((double)count * 2^kscale[a]))   (NaN when count == 0)
+ * is the same on every device. Non-finite attribute values count as 0. */
+typedef struct {
+  int64_t in_domain;              /* samples inside the grid, all timesteps                */
+  int64_t out_of_domain;          /* samples with a non-finite or outside position         */
+  int32_t kscale[MSF_MAX_ATTR];   /* fixed-point exponent per attribute                    */
+  float max_abs[MSF_MAX_ATTR];    /* largest finite |attribute| per attribute              */
+} msf_bin_stats;
+
+/* One extracted feature. t is window-relative in bbox and centroid. Means over voxels use
+ * fp64 sums of the fp32 field; point means use the exact fixed-point sums. Standard
+ * deviations are population deviations: over the feature's voxels for the field, over its
+ * point samples for attributes. */
+typedef struct {
+  int32_t label;                  /* smallest window-linear index of the feature            */
+  int32_t bbox_min[4];            /* t, z, y, x                                             */
+  int32_t bbox_max[4];            /* t, z, y, x (inclusive)                                 */
+  int32_t n_attr;
+  int64_t n_vox;                  /* voxel-timesteps in the feature                         */
+  int64_t n_pts;                  /* point samples in those voxel-timesteps                 */
+  double sum_field, mean_field, std_field;
+  float min_field, max_field;
+  double centroid[4];             /* mean voxel index: t, z, y, x                           */
+  int64_t sumq[MSF_MAX_ATTR];     /* fixed-point attribute sums (scale 2^kscale[a])         */
+  double mean_attr[MSF_MAX_ATTR]; /* NaN when n_pts == 0                                    */
+  double std_attr[MSF_MAX_ATTR];
+} msf_feature;
+
+/* ---- context ----------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`. `stream` is a cudaStream_t (may be NULL for the
+ * legacy default stream); the context issues all its work there. Errors: INVALID_ARG,
+ * CUDA (no such device). */
+int msf_create(msf_ctx** out, int device, void* stream);
+
+/* Release every device allocation of the context (after synchronising its stream). */
+void msf_destroy(msf_ctx* ctx);
+
+/* Change the stream later calls use. */
+int msf_set_stream(msf_ctx* ctx, void* stream);
+
+/* ---- §3.1 data ------------------------------------------------------------------------- */
+
+/* Copy one dataset to the device (replacing any previous one; allocations are reused when the
+ * sizes match). Layouts, all row-major fp32:
+ *   field [T][nz][ny][nx]          v_f(t) at voxel (x,y,z)
+ *   pos   [T][3][P]                x_p(t), y_p(t), z_p(t) in grid units; voxel (x,y,z) covers
+ *                                  [x,x+1) x [y,y+1) x [z,z+1); a point keeps its index p over
+ *                                  all timesteps (its trajectory)
+ *   attr  [T][A][P]                v_p(t), A point attributes (A <= MSF_MAX_ATTR)
+ * ptr_kind says whether the three pointers are host or device memory. P may be 0 (pos and
+ * attr may then be NULL); A may be 0. The previous binning is discarded.
+ * Errors: INVALID_ARG (sizes <= 0, A > MSF_MAX_ATTR, NULL pointers), TOO_LARGE (nx*ny*nz >=
+ * 2^31 or P >= 2^31), OUT_OF_MEMORY, CUDA. */
+int msf_load_timesteps(msf_ctx* ctx, int nx, int ny, int nz, int T, const float* field,
+                       int64_t P, int A, const float* pos, const float* attr, int ptr_kind);
+
+/* The §3.1 preprocessing index over all T timesteps: key[t][p] = voxel of sample (p,t)
+ * ((z*ny + y)*nx + x, or -1 when the position is non-finite or outside [0,n) in any axis),
+ * count[t][v], the fixed-point sums and the fp32 means of every attribute (see
+ * msf_bin_stats). With MSF_BIN_KEEP_SUMQ the int64 sums are kept for msf_get_bins. `stats`
+ * may be NULL. Synchronises the stream. Errors: NOT_LOADED, INVALID_ARG (unknown flag),
+ * OUT_OF_MEMORY, CUDA. */
+int msf_bin_particles(msf_ctx* ctx, unsigned flags, msf_bin_stats* stats);
+
+/* Copy the binning results out (each pointer may be NULL): key [T][P] int32,
+ * count [T][nz][ny][nx] int32, mean [A][T][nz][ny][nx] fp32, sumq [A][T][nz][ny][nx] int64
+ * (only when binned with MSF_BIN_KEEP_SUMQ, else INVALID_ARG). ptr_kind applies to all four.
+ * Synchronises the stream. */
+int msf_get_bins(msf_ctx* ctx, int32_t* key, int32_t* count, float* mean, int64_t* sumq,
+                 int ptr_kind);
+
+/* ---- segmentation --------------------------------------------------------------------- */
+
+/* Evaluate the criterion over the window and label its 4D connected features.
+ * labels: [t1-t0][nz][ny][nx] int32, caller-owned, host or device per labels_kind; receives
+ * the canonical labels described at the top of this file. n_features (host, may be NULL)
+ * receives the number of features. Synchronises the stream.
+ * Errors: NOT_LOADED, NOT_BINNED (a COUNT/MEAN predicate or TRAJ edges before binning),
+ * INVALID_ARG (window outside [0,T], t1 < t0, n_pred outside [0,4], bad source/op/attribute,
+ * COUNT threshold outside int32, unknown edge bits), TOO_LARGE ((t1-t0)*nx*ny*nz >= 2^31),
+ * OUT_OF_MEMORY, CUDA. t1 == t0 is valid: nothing is written and n_features is 0. */
+int msf_segment(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int labels_kind,
+                int64_t* n_features);
+
+/* Per-feature statistics of `labels` (a labelling of `crit`'s window, as produced by
+ * msf_segment) in ascending label order. out: host or device per out_kind, capacity `cap`
+ * records; *n_out receives the number of features. When cap < *n_out nothing is written and
+ * the call returns MSF_ERR_CAPACITY (cap = 0 with out = NULL is a valid size query).
+ * labels: host or device per labels_kind. Synchronises the stream.
+ * Errors: NOT_LOADED, NOT_BINNED, INVALID_ARG, TOO_LARGE, CAPACITY, OUT_OF_MEMORY, CUDA. */
+int msf_extract_features(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
+                         int labels_kind, msf_feature* out, int out_kind, int64_t cap,
+                         int64_t* n_out);
+
+/* ---- tuning, profiling ---------------------------------------------------------------- */
+
+/* Tile shape of the labelling kernels: 32 x by x bz x bt voxel-timesteps with by*bz*bt = 256
+ * and each a power of two. (0,0,0) restores the automatic choice. Errors: INVALID_ARG. */
+int msf_set_tile(msf_ctx* ctx, int by, int bz, int bt);
+
+/* Per-kernel timing: when enabled, every kernel the context launches is bracketed by CUDA
+ * events on its stream; msf_kernel_times fills up to `cap` (name, total ms, launches) entries
+ * accumulated since the last reset and returns the number of kernels seen (>= 0) or an error.
+ * name buffers hold 48 bytes each. */
+int msf_set_profiling(msf_ctx* ctx, int enable);
+int msf_kernel_times(msf_ctx* ctx, char (*names)[48], double* total_ms, int64_t* launches,
+                     int cap, int reset);
+
+/* Short text for a status code. */
+const char* msf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSF_H */

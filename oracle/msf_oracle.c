@@ -85,11 +85,27 @@ static int64_t orc_quantise(float a, int k) {
   return llrint(ldexp((double)a, k));
 }
 
+/* Per-voxel mean of one attribute from its exact fixed-point sum, as a fixed sequence of IEEE
+ * fp32 operations, each rounded to nearest-even: the sum converted to fp32, divided by the
+ * count, then scaled by 2^-k in two exact power-of-two factors (each factor a normal fp32
+ * number for every k this exponent rule produces). The paper keeps running averages in float
+ * (§3.5); fp32 here also keeps the per-voxel work off the GPU's fp64 units. */
+static float orc_mean(int64_t sumq, int32_t count, int k) {
+  if (count == 0) return NAN;
+  int k1 = k / 2, k2 = k - k / 2;
+  volatile float f1 = ldexpf(1.0f, -k1), f2 = ldexpf(1.0f, -k2);
+  volatile float m = (float)sumq;
+  m = m / (float)count;
+  m = m * f1;
+  m = m * f2;
+  return m;
+}
+
 /* Binning of all T timesteps.
  *   key[t][p]        voxel of sample (p,t) or -1
  *   count[t][v]      number of samples in voxel v at t
  *   sumq[a][t][v]    sum of the quantised attribute a over those samples (int64, exact)
- *   mean[a][t][v]    fp32 mean: (float)((double)sumq / ((double)count * 2^k_a)), NaN if empty
+ *   mean[a][t][v]    fp32 mean: ((float)sumq / (float)count) * 2^-k_a in IEEE fp32, NaN if empty
  *   kscale[a]        the exponent k_a used
  *   outside[t]       samples with key -1 at t
  * sumq may be NULL. */
@@ -133,16 +149,10 @@ int oracle_bin(int nx, int ny, int nz, int T, int64_t P, int A, const float* pos
     }
     outside[t] = out;
     for (int a = 0; a < A; ++a) {
-      double scale = ldexp(1.0, kscale[a]);
       for (int64_t v = 0; v < V; ++v) {
         int64_t s = acc[(int64_t)a * V + v];
         if (sumq) sumq[((int64_t)a * T + t) * V + v] = s;
-        float m;
-        if (cnt[v] == 0)
-          m = NAN;
-        else
-          m = (float)((double)s / ((double)cnt[v] * scale));
-        mean[((int64_t)a * T + t) * V + v] = m;
+        mean[((int64_t)a * T + t) * V + v] = orc_mean(s, cnt[v], kscale[a]);
       }
     }
   }

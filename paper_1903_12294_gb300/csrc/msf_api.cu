@@ -1,0 +1,418 @@
+// C ABI of the library (include/msf.h): context, resident dataset, argument checking and the
+// host side of each entry point. Kernels live in k_bin.cu, k_segment.cu and k_features.cu.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "msf_internal.cuh"
+
+namespace msf {
+
+static thread_local char g_last_error[256];
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what,
+           file, line);
+}
+
+int DevBuf::ensure(size_t n) {
+  if (n <= bytes && p) return MSF_OK;
+  release();
+  if (n == 0) n = 16;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    bytes = 0;
+    set_last_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+    return MSF_ERR_OUT_OF_MEMORY;
+  }
+  bytes = n;
+  return MSF_OK;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+int KernelTimer::begin(const char* name, cudaStream_t s, cudaEvent_t* a, cudaEvent_t* b,
+                       int* rec) {
+  int r = -1;
+  for (size_t i = 0; i < recs.size(); ++i)
+    if (recs[i].name == name) r = (int)i;
+  if (r < 0) {
+    recs.push_back({name, 0.0, 0});
+    r = (int)recs.size() - 1;
+  }
+  while (pool.size() < next_event + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    pool.push_back(e);
+  }
+  *a = pool[next_event++];
+  *b = pool[next_event++];
+  cudaEventRecord(*a, s);
+  pending.push_back({r, *a, *b});
+  *rec = r;
+  return 0;
+}
+
+void KernelTimer::flush() {
+  for (auto& p : pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      recs[p.rec].ms += ms;
+      recs[p.rec].n += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  pending.clear();
+  next_event = 0;
+}
+
+void KernelTimer::release() {
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+  pending.clear();
+  recs.clear();
+  next_event = 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// query checks and geometry
+// ---------------------------------------------------------------------------------------------
+int validate_criteria(const msf_ctx* ctx, const msf_criteria* c) {
+  const Dataset& d = ctx->ds;
+  if (!c) return MSF_ERR_INVALID_ARG;
+  if (!d.loaded) return MSF_ERR_NOT_LOADED;
+  if (c->t0 < 0 || c->t1 > d.T || c->t1 < c->t0) return MSF_ERR_INVALID_ARG;
+  if (c->n_pred < 0 || c->n_pred > MSF_MAX_PRED) return MSF_ERR_INVALID_ARG;
+  if (c->edges & ~(uint32_t)MSF_EDGE_ALL) return MSF_ERR_INVALID_ARG;
+  bool need_bins = (c->edges & MSF_EDGE_TRAJ) && d.P > 0;
+  for (int i = 0; i < c->n_pred; ++i) {
+    const msf_pred& p = c->pred[i];
+    if (p.op < MSF_OP_GT || p.op > MSF_OP_BAND) return MSF_ERR_INVALID_ARG;
+    if (p.src == MSF_SRC_FIELD) continue;
+    if (p.src == MSF_SRC_COUNT) {
+      need_bins = true;
+      const float lim = 2147483648.0f;
+      if (!(p.lo >= -lim && p.lo < lim)) return MSF_ERR_INVALID_ARG;
+      if (p.op == MSF_OP_BAND && !(p.hi >= -lim && p.hi < lim)) return MSF_ERR_INVALID_ARG;
+      continue;
+    }
+    if (p.src == MSF_SRC_MEAN) {
+      need_bins = true;
+      if (p.attr < 0 || p.attr >= d.A) return MSF_ERR_INVALID_ARG;
+      continue;
+    }
+    return MSF_ERR_INVALID_ARG;
+  }
+  if (need_bins && !d.binned) return MSF_ERR_NOT_BINNED;
+  if ((int64_t)(c->t1 - c->t0) * d.V >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
+  return MSF_OK;
+}
+
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+int make_geometry(const msf_ctx* ctx, const msf_criteria* c, Geometry* g) {
+  MSF_TRY(validate_criteria(ctx, c));
+  const Dataset& d = ctx->ds;
+  g->nx = d.nx;
+  g->ny = d.ny;
+  g->nz = d.nz;
+  g->V = (int)d.V;
+  g->T = d.T;
+  g->t0 = c->t0;
+  g->tw = c->t1 - c->t0;
+  g->nxs = (d.nx + 31) / 32;
+  int by, bz, bt;
+  if (ctx->tile_by) {
+    by = ctx->tile_by;
+    bz = ctx->tile_bz;
+    bt = ctx->tile_bt;
+  } else if (d.nz == 1) {
+    bz = 1;
+    bt = std::min(16, 1 << ilog2(std::max(1, g->tw)));
+    by = kSegPerTile / bt;
+  } else {
+    bt = std::min(4, 1 << ilog2(std::max(1, g->tw)));
+    const int rest = kSegPerTile / bt;  // 64, 128 or 256
+    bz = rest >= 256 ? 16 : 8;
+    by = rest / bz;
+  }
+  g->lby = ilog2(by);
+  g->lbz = ilog2(bz);
+  g->lbt = ilog2(bt);
+  g->tly = (d.ny + by - 1) / by;
+  g->tlz = (d.nz + bz - 1) / bz;
+  g->tlt = (g->tw + bt - 1) / bt;
+  const int64_t nt = (int64_t)g->nxs * g->tly * g->tlz * g->tlt;
+  if (nt >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
+  g->ntiles = (int)nt;
+  // Components per tile: with 26-neighbour edges a 2x2x2 block of one timestep meets at most
+  // one component, so a tile holds at most ceil(32/2)*ceil(by/2)*ceil(bz/2)*bt of them;
+  // without spatial edges every voxel-timestep may be its own.
+  if (c->edges & MSF_EDGE_SPATIAL)
+    g->cmax = 16 * ((by + 1) / 2) * ((bz + 1) / 2) * bt;
+  else
+    g->cmax = 32 * by * bz * bt;
+  if ((int64_t)g->ntiles * std::max(g->cmax, kSegPerTile * 32) >= ((int64_t)1 << 32))
+    return MSF_ERR_TOO_LARGE;
+  g->nseg = (int64_t)g->tw * d.nz * d.ny * g->nxs;
+  return MSF_OK;
+}
+
+void make_preds(const msf_ctx* ctx, const msf_criteria* c, DevPred* out) {
+  const Dataset& d = ctx->ds;
+  for (int i = 0; i < c->n_pred; ++i) {
+    const msf_pred& p = c->pred[i];
+    DevPred& q = out[i];
+    q.op = p.op;
+    q.lo = p.lo;
+    q.hi = p.hi;
+    q.ilo = (int)p.lo;
+    q.ihi = (int)p.hi;
+    if (p.src == MSF_SRC_FIELD) {
+      q.base = d.field.p;
+      q.is_int = 0;
+    } else if (p.src == MSF_SRC_COUNT) {
+      q.base = d.count.p;
+      q.is_int = 1;
+    } else {
+      q.base = d.mean.as<float>() + (int64_t)p.attr * d.T * d.V;
+      q.is_int = 0;
+    }
+  }
+}
+
+static int copy_in(DevBuf& dst, const void* src, size_t bytes, int kind, cudaStream_t s) {
+  MSF_TRY(dst.ensure(bytes));
+  if (bytes == 0) return MSF_OK;
+  MSF_CUDA_TRY(cudaMemcpyAsync(dst.p, src, bytes,
+                               kind == MSF_HOST ? cudaMemcpyHostToDevice
+                                                : cudaMemcpyDeviceToDevice,
+                               s));
+  return MSF_OK;
+}
+
+}  // namespace msf
+
+using namespace msf;
+
+extern "C" {
+
+const char* msf_status_string(int status) {
+  switch (status) {
+    case MSF_OK: return "ok";
+    case MSF_ERR_INVALID_ARG: return "invalid argument";
+    case MSF_ERR_NOT_LOADED: return "no dataset loaded";
+    case MSF_ERR_NOT_BINNED: return "dataset not binned";
+    case MSF_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case MSF_ERR_TOO_LARGE: return "size limit exceeded";
+    case MSF_ERR_TIMEOUT: return "device wait timed out";
+    case MSF_ERR_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case MSF_ERR_CAPACITY: return "output capacity too small";
+    case MSF_ERR_INTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+int msf_create(msf_ctx** out, int device, void* stream) {
+  if (!out) return MSF_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  MSF_CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return MSF_ERR_INVALID_ARG;
+  MSF_CUDA_TRY(cudaSetDevice(device));
+  msf_ctx* c = new msf_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  *out = c;
+  return MSF_OK;
+}
+
+void msf_destroy(msf_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  Dataset& d = c->ds;
+  for (DevBuf* b : {&d.field, &d.pos, &d.attr, &d.key, &d.count, &d.mean, &d.sumq}) b->release();
+  for (DevBuf* b : {&c->seg.segmask, &c->seg.segrun, &c->seg.runcomp, &c->seg.cparent,
+                    &c->seg.cminli, &c->seg.tileinfo, &c->seg.counters})
+    b->release();
+  for (DevBuf* b : {&c->feat.rootbits, &c->feat.wordrank, &c->feat.blocksums, &c->feat.acc,
+                    &c->feat.out})
+    b->release();
+  for (DevBuf* b : {&c->bin.cnt, &c->bin.sum, &c->bin.absmax, &c->bin.outside}) b->release();
+  c->host_staging.release();
+  c->timer.release();
+  delete c;
+}
+
+int msf_set_stream(msf_ctx* c, void* stream) {
+  if (!c) return MSF_ERR_INVALID_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return MSF_OK;
+}
+
+int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* field, int64_t P,
+                       int A, const float* pos, const float* attr, int ptr_kind) {
+  if (!c || nx <= 0 || ny <= 0 || nz <= 0 || T <= 0 || P < 0 || A < 0 || !field)
+    return MSF_ERR_INVALID_ARG;
+  if (ptr_kind != MSF_HOST && ptr_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
+  if (A > MSF_MAX_ATTR) return MSF_ERR_INVALID_ARG;
+  if (P > 0 && (!pos || (A > 0 && !attr))) return MSF_ERR_INVALID_ARG;
+  if (T > 65535) return MSF_ERR_TOO_LARGE;
+  const int64_t V = (int64_t)nx * ny * nz;
+  if (V >= ((int64_t)1 << 31) || P >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  Dataset& d = c->ds;
+  d.loaded = false;
+  d.binned = false;
+  d.has_sumq = false;
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.T = T;
+  d.P = P;
+  d.A = A;
+  d.V = V;
+  MSF_TRY(copy_in(d.field, field, sizeof(float) * V * T, ptr_kind, c->stream));
+  MSF_TRY(copy_in(d.pos, pos, sizeof(float) * 3 * P * T, ptr_kind, c->stream));
+  MSF_TRY(copy_in(d.attr, attr, sizeof(float) * A * P * T, ptr_kind, c->stream));
+  d.loaded = true;
+  return MSF_OK;
+}
+
+int msf_bin_particles(msf_ctx* c, unsigned flags, msf_bin_stats* stats) {
+  if (!c) return MSF_ERR_INVALID_ARG;
+  if (flags & ~(unsigned)MSF_BIN_KEEP_SUMQ) return MSF_ERR_INVALID_ARG;
+  if (!c->ds.loaded) return MSF_ERR_NOT_LOADED;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  MSF_TRY(bin_run(c, flags));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->in_domain = c->ds.in_domain;
+    stats->out_of_domain = c->ds.out_of_domain;
+    for (int a = 0; a < c->ds.A; ++a) {
+      stats->kscale[a] = c->ds.kscale[a];
+      stats->max_abs[a] = c->ds.max_abs[a];
+    }
+  }
+  return MSF_OK;
+}
+
+int msf_get_bins(msf_ctx* c, int32_t* key, int32_t* count, float* mean, int64_t* sumq,
+                 int ptr_kind) {
+  if (!c || (ptr_kind != MSF_HOST && ptr_kind != MSF_DEVICE)) return MSF_ERR_INVALID_ARG;
+  const Dataset& d = c->ds;
+  if (!d.loaded) return MSF_ERR_NOT_LOADED;
+  if (!d.binned) return MSF_ERR_NOT_BINNED;
+  if (sumq && !d.has_sumq) return MSF_ERR_INVALID_ARG;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  const cudaMemcpyKind k = ptr_kind == MSF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  cudaStream_t s = c->stream;
+  if (key && d.P > 0) MSF_CUDA_TRY(cudaMemcpyAsync(key, d.key.p, sizeof(int32_t) * d.T * d.P, k, s));
+  if (count) MSF_CUDA_TRY(cudaMemcpyAsync(count, d.count.p, sizeof(int32_t) * d.T * d.V, k, s));
+  if (mean && d.A > 0)
+    MSF_CUDA_TRY(cudaMemcpyAsync(mean, d.mean.p, sizeof(float) * d.A * d.T * d.V, k, s));
+  if (sumq && d.A > 0)
+    MSF_CUDA_TRY(cudaMemcpyAsync(sumq, d.sumq.p, sizeof(int64_t) * d.A * d.T * d.V, k, s));
+  MSF_CUDA_TRY(cudaStreamSynchronize(s));
+  return MSF_OK;
+}
+
+int msf_segment(msf_ctx* c, const msf_criteria* crit, int32_t* labels, int labels_kind,
+                int64_t* n_features) {
+  if (!c || !crit) return MSF_ERR_INVALID_ARG;
+  if (labels_kind != MSF_HOST && labels_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
+  MSF_TRY(validate_criteria(c, crit));
+  const int64_t N = (int64_t)(crit->t1 - crit->t0) * c->ds.V;
+  if (N > 0 && !labels) return MSF_ERR_INVALID_ARG;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  int32_t* dst = labels;
+  if (labels_kind == MSF_HOST && N > 0) {
+    MSF_TRY(c->host_staging.ensure(sizeof(int32_t) * N));
+    dst = c->host_staging.as<int32_t>();
+  }
+  MSF_TRY(segment_run(c, crit, dst, n_features));
+  if (labels_kind == MSF_HOST && N > 0) {
+    MSF_CUDA_TRY(cudaMemcpyAsync(labels, dst, sizeof(int32_t) * N, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    MSF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  return MSF_OK;
+}
+
+int msf_extract_features(msf_ctx* c, const msf_criteria* crit, const int32_t* labels,
+                         int labels_kind, msf_feature* out, int out_kind, int64_t cap,
+                         int64_t* n_out) {
+  if (!c || !crit || !n_out || cap < 0) return MSF_ERR_INVALID_ARG;
+  if (labels_kind != MSF_HOST && labels_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
+  if (out_kind != MSF_HOST && out_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
+  if (cap > 0 && !out) return MSF_ERR_INVALID_ARG;
+  MSF_TRY(validate_criteria(c, crit));
+  if (!c->ds.binned) return MSF_ERR_NOT_BINNED;
+  const int64_t N = (int64_t)(crit->t1 - crit->t0) * c->ds.V;
+  if (N > 0 && !labels) return MSF_ERR_INVALID_ARG;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  const int32_t* src = labels;
+  if (labels_kind == MSF_HOST && N > 0) {
+    MSF_TRY(c->host_staging.ensure(sizeof(int32_t) * N));
+    MSF_CUDA_TRY(cudaMemcpyAsync(c->host_staging.p, labels, sizeof(int32_t) * N,
+                                 cudaMemcpyHostToDevice, c->stream));
+    src = c->host_staging.as<int32_t>();
+  }
+  return features_run(c, crit, src, out, out_kind, cap, n_out);
+}
+
+int msf_set_tile(msf_ctx* c, int by, int bz, int bt) {
+  if (!c) return MSF_ERR_INVALID_ARG;
+  if (by == 0 && bz == 0 && bt == 0) {
+    c->tile_by = c->tile_bz = c->tile_bt = 0;
+    return MSF_OK;
+  }
+  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+  if (!pow2(by) || !pow2(bz) || !pow2(bt) || by * bz * bt != kSegPerTile)
+    return MSF_ERR_INVALID_ARG;
+  c->tile_by = by;
+  c->tile_bz = bz;
+  c->tile_bt = bt;
+  return MSF_OK;
+}
+
+int msf_set_profiling(msf_ctx* c, int enable) {
+  if (!c) return MSF_ERR_INVALID_ARG;
+  c->timer.enabled = enable != 0;
+  return MSF_OK;
+}
+
+int msf_kernel_times(msf_ctx* c, char (*names)[48], double* total_ms, int64_t* launches, int cap,
+                     int reset) {
+  if (!c || cap < 0) return MSF_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->stream);
+  c->timer.flush();
+  const int n = (int)c->timer.recs.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    if (names) {
+      strncpy(names[i], c->timer.recs[i].name.c_str(), 47);
+      names[i][47] = 0;
+    }
+    if (total_ms) total_ms[i] = c->timer.recs[i].ms;
+    if (launches) launches[i] = c->timer.recs[i].n;
+  }
+  if (reset) c->timer.recs.clear();
+  return n;
+}
+
+}  // extern "C"

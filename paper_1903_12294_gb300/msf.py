@@ -1,0 +1,325 @@
+"""ctypes binding of libmsf.so (the C ABI in include/msf.h), same names as the C entry points.
+
+Argument marshalling only: every step of binning, criterion, labelling and feature reduction
+runs in the library's CUDA kernels. torch tensors are accepted for convenience (device memory
+and streams); their ``data_ptr()`` is passed as a plain pointer. If the library has not been
+built, loading fails with an error instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmsf.so")
+
+MSF_OK = 0
+MSF_ERR_INVALID_ARG, MSF_ERR_NOT_LOADED, MSF_ERR_NOT_BINNED = -1, -2, -3
+MSF_ERR_OUT_OF_MEMORY, MSF_ERR_TOO_LARGE, MSF_ERR_TIMEOUT = -4, -5, -6
+MSF_ERR_CUDA, MSF_ERR_CAPACITY, MSF_ERR_INTERNAL = -7, -8, -9
+MSF_HOST, MSF_DEVICE = 0, 1
+MSF_SRC_FIELD, MSF_SRC_COUNT, MSF_SRC_MEAN = 0, 1, 2
+MSF_OP_GT, MSF_OP_GE, MSF_OP_LT, MSF_OP_LE, MSF_OP_BAND = 0, 1, 2, 3, 4
+MSF_EDGE_SPATIAL, MSF_EDGE_TEMPORAL, MSF_EDGE_TRAJ, MSF_EDGE_ALL = 1, 2, 4, 7
+MSF_BIN_KEEP_SUMQ = 1
+MSF_MAX_PRED, MSF_MAX_ATTR = 4, 8
+
+# every entry point the header declares (checked by the CPU test-suite)
+EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
+           "msf_bin_particles", "msf_get_bins", "msf_segment", "msf_extract_features",
+           "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string")
+
+
+class msf_pred(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_int32), ("attr", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("lo", ctypes.c_float), ("hi", ctypes.c_float)]
+
+
+class msf_criteria(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_int32), ("t1", ctypes.c_int32), ("n_pred", ctypes.c_int32),
+                ("pred", msf_pred * MSF_MAX_PRED), ("edges", ctypes.c_uint32)]
+
+
+class msf_bin_stats(ctypes.Structure):
+    _fields_ = [("in_domain", ctypes.c_int64), ("out_of_domain", ctypes.c_int64),
+                ("kscale", ctypes.c_int32 * MSF_MAX_ATTR),
+                ("max_abs", ctypes.c_float * MSF_MAX_ATTR)]
+
+
+class msf_feature(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_int32), ("bbox_min", ctypes.c_int32 * 4),
+                ("bbox_max", ctypes.c_int32 * 4), ("n_attr", ctypes.c_int32),
+                ("n_vox", ctypes.c_int64), ("n_pts", ctypes.c_int64),
+                ("sum_field", ctypes.c_double), ("mean_field", ctypes.c_double),
+                ("std_field", ctypes.c_double), ("min_field", ctypes.c_float),
+                ("max_field", ctypes.c_float), ("centroid", ctypes.c_double * 4),
+                ("sumq", ctypes.c_int64 * MSF_MAX_ATTR),
+                ("mean_attr", ctypes.c_double * MSF_MAX_ATTR),
+                ("std_attr", ctypes.c_double * MSF_MAX_ATTR)]
+
+
+FEATURE_DTYPE = np.dtype(msf_feature)
+
+
+class MsfError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {msf_status_string(status)} ({status})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmsf.so; raises if it is missing (build it with ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"libmsf.so not built at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint
+        lib.msf_create.argtypes = [ctypes.POINTER(P), i32, P]
+        lib.msf_destroy.argtypes = [P]
+        lib.msf_destroy.restype = None
+        lib.msf_set_stream.argtypes = [P, P]
+        lib.msf_load_timesteps.argtypes = [P, i32, i32, i32, i32, P, i64, i32, P, P, i32]
+        lib.msf_bin_particles.argtypes = [P, u32, ctypes.POINTER(msf_bin_stats)]
+        lib.msf_get_bins.argtypes = [P, P, P, P, P, i32]
+        lib.msf_segment.argtypes = [P, ctypes.POINTER(msf_criteria), P, i32,
+                                    ctypes.POINTER(ctypes.c_int64)]
+        lib.msf_extract_features.argtypes = [P, ctypes.POINTER(msf_criteria), P, i32, P, i32,
+                                             i64, ctypes.POINTER(ctypes.c_int64)]
+        lib.msf_set_tile.argtypes = [P, i32, i32, i32]
+        lib.msf_set_profiling.argtypes = [P, i32]
+        lib.msf_kernel_times.argtypes = [P, P, P, P, i32, i32]
+        lib.msf_status_string.argtypes = [i32]
+        lib.msf_status_string.restype = ctypes.c_char_p
+        for n in EXPORTS:
+            f = getattr(lib, n)
+            if n not in ("msf_destroy", "msf_status_string"):
+                f.restype = i32
+        _lib = lib
+    return _lib
+
+
+def msf_status_string(status: int) -> str:
+    return load_library().msf_status_string(int(status)).decode()
+
+
+def _check(status, where):
+    if status < 0:
+        raise MsfError(status, where)
+    return status
+
+
+# ---------------------------------------------------------------------------------------------
+# pointer helpers
+# ---------------------------------------------------------------------------------------------
+
+def _ptr_kind(x):
+    """(pointer, kind) for a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None, MSF_HOST
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return (x.ctypes.data if x.size else None), MSF_HOST
+    import torch
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        kind = MSF_DEVICE if x.is_cuda else MSF_HOST
+        return (x.data_ptr() if x.numel() else None), kind
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def make_criteria(t0, t1, preds=(), edges=MSF_EDGE_ALL) -> msf_criteria:
+    """preds: sequence of (src, attr, op, lo, hi)."""
+    if len(preds) > MSF_MAX_PRED:
+        raise ValueError("at most 4 predicates")
+    c = msf_criteria()
+    c.t0, c.t1, c.n_pred, c.edges = int(t0), int(t1), len(preds), int(edges)
+    for i, (src, a, op, lo, hi) in enumerate(preds):
+        c.pred[i] = msf_pred(int(src), int(a), int(op), float(lo), float(hi))
+    return c
+
+
+# ---------------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------------------------
+
+def msf_create(device: int = 0, stream=None):
+    h = ctypes.c_void_p()
+    s = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+    _check(load_library().msf_create(ctypes.byref(h), int(device), s), "msf_create")
+    return h
+
+
+def msf_destroy(ctx):
+    load_library().msf_destroy(ctx)
+
+
+def msf_set_stream(ctx, stream):
+    s = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+    _check(load_library().msf_set_stream(ctx, s), "msf_set_stream")
+
+
+def msf_load_timesteps(ctx, field, pos, attr):
+    """field [T][nz][ny][nx] fp32, pos [T][3][P] fp32, attr [T][A][P] fp32 (all host or all
+    device)."""
+    T, nz, ny, nx = field.shape
+    P = pos.shape[2] if pos is not None else 0
+    A = attr.shape[1] if attr is not None else 0
+    fp, k = _ptr_kind(field)
+    pp, kp = _ptr_kind(pos)
+    ap, ka = _ptr_kind(attr)
+    if P and (kp != k or (A and ka != k)):
+        raise ValueError("field, pos and attr must all be host or all device")
+    _check(load_library().msf_load_timesteps(ctx, nx, ny, nz, T, fp, P, A, pp, ap, k),
+           "msf_load_timesteps")
+
+
+def msf_bin_particles(ctx, flags: int = 0) -> msf_bin_stats:
+    st = msf_bin_stats()
+    _check(load_library().msf_bin_particles(ctx, int(flags), ctypes.byref(st)),
+           "msf_bin_particles")
+    return st
+
+
+def msf_get_bins(ctx, key=None, count=None, mean=None, sumq=None):
+    kinds = {_ptr_kind(x)[1] for x in (key, count, mean, sumq) if x is not None}
+    if len(kinds) > 1:
+        raise ValueError("all outputs must be host or all device")
+    kind = kinds.pop() if kinds else MSF_HOST
+    _check(load_library().msf_get_bins(ctx, _ptr_kind(key)[0], _ptr_kind(count)[0],
+                                       _ptr_kind(mean)[0], _ptr_kind(sumq)[0], kind),
+           "msf_get_bins")
+
+
+def msf_segment(ctx, crit: msf_criteria, labels) -> int:
+    lp, lk = _ptr_kind(labels)
+    n = ctypes.c_int64(0)
+    _check(load_library().msf_segment(ctx, ctypes.byref(crit), lp, lk, ctypes.byref(n)),
+           "msf_segment")
+    return int(n.value)
+
+
+def msf_extract_features(ctx, crit: msf_criteria, labels, cap=None):
+    """Returns a numpy structured array (dtype FEATURE_DTYPE) of the features."""
+    lib = load_library()
+    lp, lk = _ptr_kind(labels)
+    n = ctypes.c_int64(0)
+    if cap is None:
+        st = lib.msf_extract_features(ctx, ctypes.byref(crit), lp, lk, None, MSF_HOST, 0,
+                                      ctypes.byref(n))
+        if st not in (MSF_OK, MSF_ERR_CAPACITY):
+            _check(st, "msf_extract_features")
+        cap = int(n.value)
+    out = np.zeros(max(cap, 1), FEATURE_DTYPE)
+    _check(lib.msf_extract_features(ctx, ctypes.byref(crit), lp, lk, out.ctypes.data, MSF_HOST,
+                                    cap, ctypes.byref(n)), "msf_extract_features")
+    return out[:int(n.value)]
+
+
+def msf_set_tile(ctx, by, bz, bt):
+    _check(load_library().msf_set_tile(ctx, by, bz, bt), "msf_set_tile")
+
+
+def msf_set_profiling(ctx, enable: bool):
+    _check(load_library().msf_set_profiling(ctx, int(bool(enable))), "msf_set_profiling")
+
+
+def msf_kernel_times(ctx, reset=False):
+    """{kernel name: (total ms, launches)} accumulated while profiling was enabled."""
+    cap = 64
+    names = (ctypes.c_char * 48 * cap)()
+    ms = (ctypes.c_double * cap)()
+    nl = (ctypes.c_int64 * cap)()
+    n = _check(load_library().msf_kernel_times(ctx, names, ms, nl, cap, int(bool(reset))),
+               "msf_kernel_times")
+    return {bytes(names[i]).split(b"\0")[0].decode(): (ms[i], nl[i]) for i in range(min(n, cap))}
+
+
+# ---------------------------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------------------------
+
+class Context:
+    """Owns one msf_ctx on a device; all calls run on the given (or torch's current) stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device)
+        self.device = device
+        self.h = msf_create(device, stream)
+        self.shape = None
+
+    def close(self):
+        if self.h:
+            msf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        msf_set_stream(self.h, stream)
+
+    def load(self, field, pos, attr):
+        msf_load_timesteps(self.h, field, pos, attr)
+        self.shape = tuple(field.shape)
+        self.P = pos.shape[2] if pos is not None else 0
+        self.A = attr.shape[1] if attr is not None else 0
+
+    def bin(self, keep_sumq=False):
+        return msf_bin_particles(self.h, MSF_BIN_KEEP_SUMQ if keep_sumq else 0)
+
+    def bins(self, device="cpu", sumq=False):
+        import torch
+        T, nz, ny, nx = self.shape
+        key = torch.empty((T, self.P), dtype=torch.int32, device=device)
+        count = torch.empty((T, nz, ny, nx), dtype=torch.int32, device=device)
+        mean = torch.empty((self.A, T, nz, ny, nx), dtype=torch.float32, device=device)
+        sq = torch.empty((self.A, T, nz, ny, nx), dtype=torch.int64, device=device) \
+            if sumq else None
+        msf_get_bins(self.h, key, count, mean if self.A else None, sq if self.A else None)
+        return key, count, mean, sq
+
+    def segment(self, t0, t1, preds=(), edges=MSF_EDGE_ALL, labels=None):
+        import torch
+        if self.shape is None:            # let the library report the missing dataset
+            return None, msf_segment(self.h, make_criteria(t0, t1, preds, edges), labels)
+        T, nz, ny, nx = self.shape
+        if labels is None:
+            labels = torch.empty((t1 - t0, nz, ny, nx), dtype=torch.int32,
+                                 device=f"cuda:{self.device}")
+        n = msf_segment(self.h, make_criteria(t0, t1, preds, edges), labels)
+        return labels, n
+
+    def features(self, t0, t1, labels, preds=(), edges=MSF_EDGE_ALL):
+        return msf_extract_features(self.h, make_criteria(t0, t1, preds, edges), labels)
+
+    def set_tile(self, by, bz, bt):
+        msf_set_tile(self.h, by, bz, bt)
+
+    def profiling(self, on=True):
+        msf_set_profiling(self.h, on)
+
+    def kernel_times(self, reset=False):
+        return msf_kernel_times(self.h, reset)

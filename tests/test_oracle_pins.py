@@ -40,8 +40,8 @@ def test_bin_voxel_boundaries_closed_form(orc):
 
 def test_bin_conservation_and_exact_sums(orc):
     """Counts conserve samples; int64 sums equal exact Python-integer sums of the quantised
-    values; the fp32 mean lies within one fp32 ulp of the exact rational mean of the raw
-    attributes (quantisation error ~2^-k is far below that)."""
+    values; the fp32 mean lies within two fp32 roundings (2 * 2^-24 relative) of the exact
+    rational mean of the raw attributes, plus the quantisation error 2^-(k+1)."""
     rng = np.random.default_rng(1)
     T, nz, ny, nx, P, A = 3, 3, 4, 5, 400, 2
     pos, attr = _bin_inputs(T, nz, ny, nx, P, A, rng)
@@ -69,8 +69,8 @@ def test_bin_conservation_and_exact_sums(orc):
                     assert np.isnan(m)
                 else:
                     ref = exact / members.size
-                    ulp = np.spacing(np.float32(abs(float(ref)) if ref else 1e-38))
-                    assert abs(float(m) - float(ref)) <= 1.01 * float(ulp) + 2.0 ** (-k + 1)
+                    bound = 2.01 * 2.0 ** -24 * abs(float(ref)) + 2.0 ** (-k - 1) + 1e-45
+                    assert abs(float(m) - float(ref)) <= bound
 
 
 def test_bin_scale_closed_form(orc):
@@ -83,12 +83,13 @@ def test_bin_scale_closed_form(orc):
 
 
 def test_bin_constant_attribute_mean_exact(orc):
-    """Every sample carries the same value c: every non-empty voxel's mean is exactly c and
-    its sum is count * c * 2^k."""
+    """Every sample carries the same value c with a short mantissa (at most 12 significant
+    bits): the sum count * c * 2^k and its quotient by the count are exact in fp32, so every
+    non-empty voxel's mean is exactly c and its sum is count * c * 2^k."""
     rng = np.random.default_rng(2)
     T, nz, ny, nx, P = 2, 4, 4, 4, 300
     pos, _ = _bin_inputs(T, nz, ny, nx, P, 1, rng, spread=0.0)
-    for c in (0.3, -1234.5, 3.0e38):
+    for c in (0.375, -1234.5, 1.5 * 2.0 ** 120, 2.0 ** -130):
         attr = np.full((T, 1, P), c, np.float32)
         b = orc.bin((T, nz, ny, nx), pos, attr)
         cnt = b["count"]
@@ -99,6 +100,23 @@ def test_bin_constant_attribute_mean_exact(orc):
         want = [round(Fraction(float(np.float32(c))) * Fraction(2) ** k) * int(n)
                 for n in cnt.reshape(-1)]
         assert b["sumq"][0].reshape(-1).tolist() == want
+
+
+def test_bin_mean_fp32_sequence(orc):
+    """The mean is the fp32 sequence ((float)sum / (float)count) * 2^-(k/2) * 2^-(k-k/2):
+    checked with numpy float32 scalars on a case with long mantissas and three samples."""
+    T, nz, ny, nx = 1, 1, 1, 2
+    pos = np.array([[[0.5, 0.5, 0.5, 1.5], [0.5] * 4, [0.5] * 4]], np.float32)
+    attr = np.array([[[0.1, 0.2, 0.7, -3.3]]], np.float32)
+    b = orc.bin((T, nz, ny, nx), pos, attr)
+    k = int(b["kscale"][0])
+    for v, members in ((0, [0, 1, 2]), (1, [3])):
+        s = sum(round(Fraction(float(attr[0, 0, p])) * Fraction(2) ** k) for p in members)
+        assert int(b["sumq"][0, 0, 0, 0, v]) == s
+        m = np.float32(np.float32(s) / np.float32(len(members)))
+        m = np.float32(m * np.float32(2.0 ** -(k // 2)))
+        m = np.float32(m * np.float32(2.0 ** -(k - k // 2)))
+        assert b["mean"][0, 0, 0, 0, v] == m
 
 
 def test_bin_empty_particles(orc):
