@@ -68,36 +68,70 @@ __device__ __forceinline__ int32_t voxel_of(float px, float py, float pz, int nx
   return ((int)fz * ny + (int)fy) * nx + (int)fx;
 }
 
+constexpr int kScatterPer = 4;
+
 template <int A>
 __global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ BinArgs b) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t p0 = (int64_t)blockIdx.x * (256 * kScatterPer) + threadIdx.x;
+  const float* pt = b.pos + (int64_t)b.t * 3 * b.P;
+  const float* at = b.attr + (int64_t)b.t * A * b.P;
+  float px[kScatterPer], py[kScatterPer], pz[kScatterPer], av[kScatterPer][A > 0 ? A : 1];
+#pragma unroll
+  for (int j = 0; j < kScatterPer; ++j) {
+    const int64_t p = p0 + j * 256;
+    const bool in = p < b.P;
+    px[j] = in ? __ldcs(pt + p) : NAN;
+    py[j] = in ? __ldcs(pt + b.P + p) : NAN;
+    pz[j] = in ? __ldcs(pt + 2 * b.P + p) : NAN;
+#pragma unroll
+    for (int a = 0; a < A; ++a) av[j][a] = in ? __ldcs(at + (int64_t)a * b.P + p) : 0.f;
+  }
   int out = 0;
-  if (p < b.P) {
-    const float* pt = b.pos + (int64_t)b.t * 3 * b.P;
-    const int32_t k = voxel_of(__ldcs(pt + p), __ldcs(pt + b.P + p), __ldcs(pt + 2 * b.P + p),
-                               b.nx, b.ny, b.nz);
+#pragma unroll
+  for (int j = 0; j < kScatterPer; ++j) {
+    const int64_t p = p0 + j * 256;
+    if (p >= b.P) continue;
+    const int32_t k = voxel_of(px[j], py[j], pz[j], b.nx, b.ny, b.nz);
     __stcs(b.key + (int64_t)b.t * b.P + p, k);
     if (k < 0) {
-      out = 1;
-    } else {
-      atomicAdd(b.scnt + k, 1);
-      const float* at = b.attr + (int64_t)b.t * A * b.P;
-#pragma unroll
-      for (int a = 0; a < A; ++a) {
-        const float v = __ldcs(at + (int64_t)a * b.P + p);
-        const long long q = quantise(v, b.kscale[a]);
-        atomicAdd(b.ssum + (int64_t)a * b.V + k, (unsigned long long)q);
-      }
+      ++out;
+      continue;
     }
+    atomicAdd(b.scnt + k, 1);
+#pragma unroll
+    for (int a = 0; a < A; ++a)
+      atomicAdd(b.ssum + (int64_t)a * b.V + k, (unsigned long long)quantise(av[j][a], b.kscale[a]));
   }
-  const unsigned ball = __ballot_sync(0xFFFFFFFFu, out);
-  if ((threadIdx.x & 31) == 0 && ball) atomicAdd(b.outside + b.t, (unsigned long long)__popc(ball));
+  const int tot = __reduce_add_sync(0xFFFFFFFFu, out);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(b.outside + b.t, (unsigned long long)tot);
+}
+
+// int64 -> fp32, round to nearest-even, with integer operations only (the hardware conversion
+// of 64-bit integers issues on the fp64 pipe, which is narrow on this part). |s| < 2^62.
+// The top 24 significant bits convert exactly; rounding adds one unit to the fp32 bit pattern
+// (a carry out of the mantissa moves into the exponent, as it must); the exponent then rises by
+// the number of dropped bits.
+__device__ __forceinline__ float i64_to_f32_rn(long long s) {
+  const unsigned long long u = s < 0 ? (unsigned long long)(-s) : (unsigned long long)s;
+  const int lz = __clzll(u);
+  uint32_t bits;
+  if (lz >= 40) {
+    bits = __float_as_uint(__uint2float_rn((uint32_t)u));  // < 2^24: exact
+  } else {
+    const int sh = 40 - lz;                                // dropped bits, 1..40
+    const uint32_t m = (uint32_t)(u >> sh);                // 24 significant bits
+    const unsigned long long rem = u << (64 - sh);         // dropped bits, left-aligned
+    const uint32_t up = (rem > 0x8000000000000000ull) ||
+                        (rem == 0x8000000000000000ull && (m & 1u));
+    bits = __float_as_uint(__uint2float_rn(m)) + up + ((uint32_t)sh << 23);
+  }
+  return __uint_as_float(bits | (s < 0 ? 0x80000000u : 0u));
 }
 
 // Per-voxel mean from the exact fixed-point sum: ((float)sum / (float)count) * 2^-k, every step
 // an IEEE fp32 operation rounded to nearest-even (the scaling split into two exact factors).
 __device__ __forceinline__ float voxel_mean(long long s, int c, float f1, float f2) {
-  return __fmul_rn(__fmul_rn(__fdiv_rn(__ll2float_rn(s), __int2float_rn(c)), f1), f2);
+  return __fmul_rn(__fmul_rn(__fdiv_rn(i64_to_f32_rn(s), __int2float_rn(c)), f1), f2);
 }
 
 template <int A, bool KEEP>
@@ -152,7 +186,7 @@ static void launch_bin_step(msf_ctx* ctx, const BinArgs& b, bool keep) {
   cudaStream_t s = ctx->stream;
   if (b.P > 0) {
     ScopedKernel k(ctx, "k_scatter");
-    k_scatter<A><<<(unsigned)((b.P + 255) / 256), 256, 0, s>>>(b);
+    k_scatter<A><<<(unsigned)((b.P + 256 * kScatterPer - 1) / (256 * kScatterPer)), 256, 0, s>>>(b);
   }
   {
     ScopedKernel k(ctx, "k_finalise");
@@ -175,6 +209,60 @@ static void launch_bin_step_a(msf_ctx* ctx, const BinArgs& b, bool keep) {
     default: launch_bin_step<8>(ctx, b, keep); break;
   }
 }
+
+// Persisting L2 window over the scratch slab (the larger of the two buffers gets the window;
+// the smaller one is small enough to stay by itself).
+struct L2Window {
+  msf_ctx* ctx;
+  bool active = false;
+  size_t old_limit = 0;
+  L2Window(msf_ctx* c, void* big, size_t big_bytes, void* small, size_t small_bytes) : ctx(c) {
+    (void)small;
+    (void)small_bytes;
+    if (!ctx->stream) return;  // the legacy default stream takes no attributes
+    int max_persist = 0, max_window = 0;
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, ctx->device);
+    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device);
+    if (max_persist <= 0 || max_window <= 0) return;
+    if (cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    const size_t want = std::min<size_t>(big_bytes, (size_t)max_persist);
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaStreamAttrValue v{};
+    v.accessPolicyWindow.base_ptr = big;
+    v.accessPolicyWindow.num_bytes = std::min<size_t>(big_bytes, (size_t)max_window);
+    v.accessPolicyWindow.hitRatio =
+        (float)std::min(1.0, (double)want / (double)v.accessPolicyWindow.num_bytes);
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    if (cudaStreamSetAttribute(ctx->stream, cudaStreamAttributeAccessPolicyWindow, &v) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+      return;
+    }
+    active = true;
+  }
+  void restore() {
+    if (!active) return;
+    cudaStreamAttrValue v{};
+    v.accessPolicyWindow.num_bytes = 0;
+    v.accessPolicyWindow.hitRatio = 0.f;
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+    cudaStreamSetAttribute(ctx->stream, cudaStreamAttributeAccessPolicyWindow, &v);
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+    cudaGetLastError();
+    active = false;
+  }
+  ~L2Window() { restore(); }
+};
 
 // Host side of the fixed-point exponent: k = 62 - e - b.
 static int scale_exponent(float max_abs, int64_t n_samples) {
@@ -241,6 +329,11 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
     b.f1[a] = ldexpf(1.0f, -(k / 2));
     b.f2[a] = ldexpf(1.0f, -(k - k / 2));
   }
+  // Keep the scratch slab resident in L2 while the atomics of one timestep land on it: a
+  // persisting access window on the stream for the duration of binning (context-scoped; the
+  // previous limit and stream attribute are restored below).
+  L2Window win(ctx, S.sum.p, sizeof(unsigned long long) * d.V * (d.A > 0 ? d.A : 1),
+                S.cnt.p, sizeof(int32_t) * d.V);
   for (int t = 0; t < d.T; ++t) {
     b.t = t;
     launch_bin_step_a(ctx, b, keep);
@@ -250,6 +343,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.T,
                                cudaMemcpyDeviceToHost, s));
   MSF_CUDA_TRY(cudaStreamSynchronize(s));
+  win.restore();
   ctx->timer.flush();
   int64_t o = 0;
   for (auto v : out) o += (int64_t)v;

@@ -2,18 +2,21 @@
 // mean point value, mean field value) and the extent and standard deviations of §3.4, for
 // every feature of a labelling, in ascending label order.
 //
-//   k_rootbits   one bit per voxel-timestep: "this voxel is its feature's label" (label == li);
-//                a feature's rank is the number of such bits before its label
-//   k_scan_*     exclusive prefix of the per-word popcounts (three small passes)
-//   k_vox        one warp per 32-voxel row: lanes of the same feature are grouped with
-//                __match_any_sync, reduced inside the warp, and the group's first lane updates
-//                the feature's accumulators with one atomic per quantity
-//   k_pts        one thread per point sample of the window: exact fixed-point attribute sums
-//                and fp64 sums of squares of the feature its voxel-timestep belongs to
-//   k_records    one thread per feature: means, deviations, centroid -> msf_feature
+// Feature ranks: one bit per voxel-timestep set at each feature's label (its smallest index);
+// a feature's rank is the number of set bits before its label (k_scan_* build the prefix).
+//
+// Two sources of the per-voxel and per-sample feature membership:
+//  * retained segmentation (fast path): when `labels` is what the context's last msf_segment
+//    wrote for the same query, the bits come from the component table and the statistics from
+//    its row masks and runs (k_segment.cu) - the labels are not read back;
+//  * any labelling (generic path): k_rootbits reads the labels, k_vox reduces one warp per
+//    32-voxel row, k_pts looks up the label of every point sample of the window.
+// k_records turns the accumulators into msf_feature records; k_labels fills in the labels.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "msf_internal.cuh"
 
@@ -32,50 +35,37 @@ struct FeatArgs {
   uint32_t* blocksums;
   int64_t nwords;
   unsigned long long* counters;  // [0] roots, [1] labels that are not canonical
-  // accumulators, indexed by feature
-  unsigned long long* n_vox;
-  unsigned long long* n_pts;
-  double* sf;
-  double* sf2;
-  unsigned* fmin;   // order-preserving float keys
-  unsigned* fmax;
-  int* bbmin;       // [F][4] t,z,y,x
-  int* bbmax;
-  unsigned long long* sc;   // [F][4] coordinate sums t,z,y,x
-  unsigned long long* sq;   // [F][A] fixed-point sums
-  double* sa2;              // [F][A]
-  int64_t F;
+  FeatAcc acc;
+  RankArrays rk;
   double scale[MSF_MAX_ATTR];
-  int kscale[MSF_MAX_ATTR];
   msf_feature* out;
 };
 
-__device__ __forceinline__ unsigned float_key(float f) {
-  const unsigned b = __float_as_uint(f);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
 __device__ __forceinline__ float key_float(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-// Rank of a label among the feature labels, or -1 when `lbl` is not one (a labelling that is
-// not canonical); the caller then flags the input as invalid.
-__device__ __forceinline__ int64_t feature_rank(const FeatArgs& a, int32_t lbl) {
-  if (lbl < 0 || (int64_t)lbl >= a.N) return -1;
-  const int w = lbl >> 5, b = lbl & 31;
-  const uint32_t bits = __ldg(a.rootbits + w);
-  if (!((bits >> b) & 1u)) return -1;
-  return (int64_t)__ldg(a.wordrank + w) + __popc(bits & ((1u << b) - 1u));
-}
-
+// 4 labels per lane (16-byte loads); the 4-bit groups of 8 lanes form one 32-bit word.
 __global__ void __launch_bounds__(256) k_rootbits(const __grid_constant__ FeatArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool root = false;
-  if (i < a.N) root = (__ldcs(a.labels + i) == (int32_t)i);
-  const unsigned m = __ballot_sync(0xFFFFFFFFu, root);
-  if ((threadIdx.x & 31) == 0 && (i >> 5) < a.nwords) {
-    a.rootbits[i >> 5] = m;
-    if (m) atomicAdd(&a.counters[0], (unsigned long long)__popc(m));
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < a.nwords * 32;
+       i0 += stride) {
+    unsigned nib = 0;
+    if (i0 + 4 <= a.N && (a.N & 3) == 0) {
+      const int4 l = __ldcs(reinterpret_cast<const int4*>(a.labels + i0));
+      nib = (unsigned)(l.x == (int32_t)i0) | ((unsigned)(l.y == (int32_t)(i0 + 1)) << 1) |
+            ((unsigned)(l.z == (int32_t)(i0 + 2)) << 2) |
+            ((unsigned)(l.w == (int32_t)(i0 + 3)) << 3);
+    } else {
+      for (int j = 0; j < 4; ++j)
+        if (i0 + j < a.N && __ldcs(a.labels + i0 + j) == (int32_t)(i0 + j)) nib |= 1u << j;
+    }
+    const unsigned word = __reduce_or_sync(0xFFu << (lane & 24), nib << ((lane & 7) * 4));
+    if ((lane & 7) == 0) {
+      a.rootbits[i0 >> 5] = word;
+      if (word) atomicAdd(&a.counters[0], (unsigned long long)__popc(word));
+    }
   }
 }
 
@@ -140,7 +130,7 @@ __global__ void __launch_bounds__(256) k_scan_down(const __grid_constant__ FeatA
   __shared__ unsigned s_warp[8];
   const int64_t base = (int64_t)blockIdx.x * kScanBlock;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned carry = a.blocksums[blockIdx.x];
+  const unsigned carry = a.blocksums[blockIdx.x];
   constexpr int PER = kScanBlock / 256;  // 8 consecutive words per thread
   unsigned c[PER];
   unsigned tot = 0;
@@ -170,27 +160,31 @@ __global__ void __launch_bounds__(256) k_scan_down(const __grid_constant__ FeatA
 }
 
 __global__ void __launch_bounds__(256) k_feat_init(const __grid_constant__ FeatArgs a) {
-  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= a.F) return;
-  a.n_vox[f] = 0;
-  a.n_pts[f] = 0;
-  a.sf[f] = 0.0;
-  a.sf2[f] = 0.0;
-  a.fmin[f] = 0xFFFFFFFFu;
-  a.fmax[f] = 0u;
+  const FeatAcc& c = a.acc;
+  const int64_t n = c.F * c.K;
+  const unsigned kmin0 = float_key(INFINITY), kmax0 = float_key(-INFINITY);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    c.n_vox[i] = 0;
+    c.n_pts[i] = 0;
+    c.sf[i] = 0.0;
+    c.sf2[i] = 0.0;
+    c.fmin[i] = kmin0;
+    c.fmax[i] = kmax0;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    a.bbmin[f * 4 + j] = 0x7FFFFFFF;
-    a.bbmax[f * 4 + j] = -1;
-    a.sc[f * 4 + j] = 0;
-  }
-  for (int k = 0; k < a.A; ++k) {
-    a.sq[f * a.A + k] = 0;
-    a.sa2[f * a.A + k] = 0.0;
+    for (int j = 0; j < 4; ++j) {
+      c.bbmin[i * 4 + j] = 0x7FFFFFFF;
+      c.bbmax[i * 4 + j] = -1;
+      c.sc[i * 4 + j] = 0;
+    }
+    for (int k = 0; k < c.A; ++k) {
+      c.sq[i * c.A + k] = 0;
+      c.sa2[i * c.A + k] = 0.0;
+    }
   }
 }
 
-// One warp per 32-voxel row (t, z, y, xs); lane = x offset.
+// Generic path: one warp per 32-voxel row (t, z, y, xs); lane = x offset.
 __global__ void __launch_bounds__(256) k_vox(const __grid_constant__ FeatArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -208,121 +202,101 @@ __global__ void __launch_bounds__(256) k_vox(const __grid_constant__ FeatArgs a)
   if (x < a.nx) lbl = __ldcs(a.labels + (int64_t)tw * a.V + vox);
   int64_t fid = -1;
   if (lbl >= 0) {
-    fid = feature_rank(a, lbl);
+    fid = feature_rank(a.rk, lbl);
     if (fid < 0) atomicOr(&a.counters[1], 1ull);
   }
   const unsigned act = __ballot_sync(0xFFFFFFFFu, fid >= 0);
   if (fid < 0) return;
-  const unsigned grp = __match_any_sync(act, fid);
   const int64_t off = (int64_t)(a.t0 + tw) * a.V + vox;
-  const float f = __ldg(a.field + off);
-  const int c = __ldg(a.count + off);
-  const int n = __popc(grp);
-  const int sum_c = __reduce_add_sync(grp, c);
-  const int sum_x = __reduce_add_sync(grp, x);
-  const unsigned kmin = __reduce_min_sync(grp, float_key(f));
-  const unsigned kmax = __reduce_max_sync(grp, float_key(f));
-  double s1 = 0.0, s2 = 0.0;
-  const double fd = (double)f;
-  for (unsigned m = grp; m; m &= m - 1) {
-    const int src = __ffs(m) - 1;
-    const double v = __shfl_sync(grp, fd, src);
-    s1 += v;
-    s2 += v * v;
-  }
-  const int leader = __ffs(grp) - 1;
-  if (lane != leader) return;
-  const int xmin = xs * 32 + leader, xmax = xs * 32 + (31 - __clz(grp));
-  atomicAdd(a.n_vox + fid, (unsigned long long)n);
-  atomicAdd(a.n_pts + fid, (unsigned long long)sum_c);
-  atomicAdd(a.sf + fid, s1);
-  atomicAdd(a.sf2 + fid, s2);
-  atomicMin(a.fmin + fid, kmin);
-  atomicMax(a.fmax + fid, kmax);
-  int* bmn = a.bbmin + fid * 4;
-  int* bmx = a.bbmax + fid * 4;
-  atomicMin(bmn + 0, tw);
-  atomicMax(bmx + 0, tw);
-  atomicMin(bmn + 1, z);
-  atomicMax(bmx + 1, z);
-  atomicMin(bmn + 2, y);
-  atomicMax(bmx + 2, y);
-  atomicMin(bmn + 3, xmin);
-  atomicMax(bmx + 3, xmax);
-  unsigned long long* scp = a.sc + fid * 4;
-  atomicAdd(scp + 0, (unsigned long long)n * (unsigned long long)tw);
-  atomicAdd(scp + 1, (unsigned long long)n * (unsigned long long)z);
-  atomicAdd(scp + 2, (unsigned long long)n * (unsigned long long)y);
-  atomicAdd(scp + 3, (unsigned long long)sum_x);
+  accumulate_row(a.acc, act, fid, lane, xs * 32, tw, z, y, __ldg(a.field + off),
+                 __ldg(a.count + off));
 }
 
-template <int A>
+// Generic path: every point sample of the window.
 __global__ void __launch_bounds__(256) k_pts(const __grid_constant__ FeatArgs a) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.P) return;
   const int tw = blockIdx.y;
   const int t = a.t0 + tw;
-  const int32_t k = __ldcs(a.key + (int64_t)t * a.P + p);
-  if (k < 0) return;
-  const int32_t lbl = __ldg(a.labels + (int64_t)tw * a.V + k);
-  if (lbl < 0) return;
-  const int64_t fid = feature_rank(a, lbl);
-  if (fid < 0) {
-    atomicOr(&a.counters[1], 1ull);
-    return;
+  int64_t fid = -1;
+  if (p < a.P) {
+    const int32_t k = __ldcs(a.key + (int64_t)t * a.P + p);
+    if (k >= 0) {
+      const int32_t lbl = __ldg(a.labels + (int64_t)tw * a.V + k);
+      if (lbl >= 0) {
+        fid = feature_rank(a.rk, lbl);
+        if (fid < 0) atomicOr(&a.counters[1], 1ull);
+      }
+    }
   }
-  const float* at = a.attr + (int64_t)t * A * a.P + p;
-#pragma unroll
-  for (int j = 0; j < A; ++j) {
-    const float v = __ldcs(at + (int64_t)j * a.P);
-    const bool fin = isfinite(v);
-    const long long q = quantise(v, a.kscale[j]);
-    const double d = fin ? (double)v : 0.0;
-    atomicAdd(a.sq + fid * A + j, (unsigned long long)q);
-    atomicAdd(a.sa2 + fid * A + j, d * d);
-  }
+  accumulate_samples(a.acc, fid >= 0, fid, a.attr + (int64_t)t * a.A * a.P + p, a.P);
 }
 
 __global__ void __launch_bounds__(256) k_records(const __grid_constant__ FeatArgs a) {
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= a.F) return;
+  const FeatAcc& c = a.acc;
+  if (f >= c.F) return;
+  // sum the K copies
+  unsigned long long nv = 0, np = 0, sc[4] = {0, 0, 0, 0};
+  double sf = 0.0, sf2 = 0.0;
+  unsigned kmin = 0xFFFFFFFFu, kmax = 0u;
+  int bmin[4] = {0x7FFFFFFF, 0x7FFFFFFF, 0x7FFFFFFF, 0x7FFFFFFF}, bmax[4] = {-1, -1, -1, -1};
+  unsigned long long sq[MSF_MAX_ATTR] = {};
+  double sa2[MSF_MAX_ATTR] = {};
+  for (int k = 0; k < c.K; ++k) {
+    const int64_t i = (int64_t)k * c.F + f;
+    nv += c.n_vox[i];
+    np += c.n_pts[i];
+    sf += c.sf[i];
+    sf2 += c.sf2[i];
+    kmin = min(kmin, c.fmin[i]);
+    kmax = max(kmax, c.fmax[i]);
+    for (int j = 0; j < 4; ++j) {
+      bmin[j] = min(bmin[j], c.bbmin[i * 4 + j]);
+      bmax[j] = max(bmax[j], c.bbmax[i * 4 + j]);
+      sc[j] += c.sc[i * 4 + j];
+    }
+    for (int j = 0; j < a.A; ++j) {
+      sq[j] += c.sq[i * a.A + j];
+      sa2[j] += c.sa2[i * a.A + j];
+    }
+  }
   msf_feature o;
   memset(&o, 0, sizeof(o));
-  const double n = (double)a.n_vox[f];
+  const double n = (double)nv;
   for (int j = 0; j < 4; ++j) {
-    o.bbox_min[j] = a.bbmin[f * 4 + j];
-    o.bbox_max[j] = a.bbmax[f * 4 + j];
-    o.centroid[j] = (double)a.sc[f * 4 + j] / n;
+    o.bbox_min[j] = bmin[j];
+    o.bbox_max[j] = bmax[j];
+    o.centroid[j] = (double)sc[j] / n;
   }
   o.label = -1;  // set by k_labels
   o.n_attr = a.A;
-  o.n_vox = (int64_t)a.n_vox[f];
-  o.n_pts = (int64_t)a.n_pts[f];
-  o.sum_field = a.sf[f];
-  o.mean_field = a.sf[f] / n;
-  const double var = a.sf2[f] / n - o.mean_field * o.mean_field;
+  o.n_vox = (int64_t)nv;
+  o.n_pts = (int64_t)np;
+  o.sum_field = sf;
+  o.mean_field = sf / n;
+  const double var = sf2 / n - o.mean_field * o.mean_field;
   o.std_field = sqrt(var > 0.0 ? var : 0.0);
-  o.min_field = key_float(a.fmin[f]);
-  o.max_field = key_float(a.fmax[f]);
+  o.min_field = key_float(kmin);
+  o.max_field = key_float(kmax);
   const double qnan = __longlong_as_double(0x7ff8000000000000ll);
   for (int j = 0; j < a.A; ++j) {
-    const long long s = (long long)a.sq[f * a.A + j];
+    const long long s = (long long)sq[j];
     o.sumq[j] = s;
     if (o.n_pts == 0) {
       o.mean_attr[j] = qnan;
       o.std_attr[j] = qnan;
     } else {
-      const double np = (double)o.n_pts;
-      const double m = (double)s / (np * a.scale[j]);
+      const double npd = (double)o.n_pts;
+      const double m = (double)s / (npd * a.scale[j]);
       o.mean_attr[j] = m;
-      const double v = a.sa2[f * a.A + j] / np - m * m;
+      const double v = sa2[j] / npd - m * m;
       o.std_attr[j] = sqrt(v > 0.0 ? v : 0.0);
     }
   }
   a.out[f] = o;
 }
 
-// label of feature f = position of the f-th set root bit; resolved by one thread per word
+// label of feature f = position of the f-th set bit
 __global__ void __launch_bounds__(256) k_labels(const __grid_constant__ FeatArgs a) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= a.nwords) return;
@@ -335,17 +309,13 @@ __global__ void __launch_bounds__(256) k_labels(const __grid_constant__ FeatArgs
   }
 }
 
-template <int A>
-static void launch_pts(const FeatArgs& a, cudaStream_t s) {
-  dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)a.tw);
-  k_pts<A><<<grid, 256, 0, s>>>(a);
-}
-
 int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
-                 msf_feature* out, int out_kind, int64_t cap, int64_t* n_out) {
+                 const void* labels_user, msf_feature* out, int out_kind, int64_t cap,
+                 int64_t* n_out) {
   Geometry g;
   MSF_TRY(make_geometry(ctx, crit, &g));
   Dataset& d = ctx->ds;
+  const bool fast = seg_state_matches(ctx, crit, labels_user);
   FeatArgs a{};
   a.nx = d.nx;
   a.ny = d.ny;
@@ -365,8 +335,9 @@ int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
   a.key = d.key.as<int32_t>();
   for (int j = 0; j < d.A; ++j) {
     a.scale[j] = ldexp(1.0, d.kscale[j]);
-    a.kscale[j] = d.kscale[j];
+    a.acc.kscale[j] = d.kscale[j];
   }
+  a.acc.A = d.A;
   if (a.N == 0) {
     *n_out = 0;
     return MSF_OK;
@@ -374,60 +345,73 @@ int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
   FeatScratch& S = ctx->feat;
   a.nwords = (a.N + 31) / 32;
   const int64_t nblk = (a.nwords + kScanBlock - 1) / kScanBlock;
-  MSF_TRY(S.rootbits.ensure(sizeof(uint32_t) * a.nwords));
+  MSF_TRY(S.rootbits.ensure(sizeof(uint32_t) * (a.nwords + 4)));
   MSF_TRY(S.wordrank.ensure(sizeof(uint32_t) * a.nwords));
   MSF_TRY(S.blocksums.ensure(sizeof(uint32_t) * nblk + 16));
-  MSF_TRY(ctx->seg.counters.ensure(sizeof(unsigned long long) * 4));
+  MSF_TRY(ctx->seg.counters.ensure(sizeof(unsigned long long) * 8));
   a.rootbits = S.rootbits.as<uint32_t>();
   a.wordrank = S.wordrank.as<uint32_t>();
   a.blocksums = S.blocksums.as<uint32_t>();
-  a.counters = ctx->seg.counters.as<unsigned long long>() + 2;
+  a.counters = ctx->seg.counters.as<unsigned long long>() + 4;  // [0..3] belong to msf_segment
+  a.rk = RankArrays{a.rootbits, a.wordrank, a.N};
   cudaStream_t s = ctx->stream;
   MSF_CUDA_TRY(cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), s));
-  {
-    ScopedKernel k(ctx, "k_rootbits");
-    k_rootbits<<<(unsigned)((a.nwords * 32 + 255) / 256), 256, 0, s>>>(a);
-  }
   unsigned long long F = 0;
-  MSF_CUDA_TRY(cudaGetLastError());
-  MSF_CUDA_TRY(cudaMemcpyAsync(&F, a.counters, sizeof(F), cudaMemcpyDeviceToHost, s));
-  MSF_CUDA_TRY(cudaStreamSynchronize(s));
+  if (fast) {
+    MSF_CUDA_TRY(cudaMemsetAsync(a.rootbits, 0, sizeof(uint32_t) * a.nwords, s));
+    MSF_TRY(seg_mark_roots(ctx, a.rootbits, a.counters));
+    F = (unsigned long long)ctx->last.n_features;
+  } else {
+    if (!labels) return MSF_ERR_INVALID_ARG;
+    {
+      ScopedKernel k(ctx, "k_rootbits");
+      const int64_t work = (a.nwords * 32 + 1023) / 1024;
+      const int grid = (int)std::min<int64_t>(work, (int64_t)ctx->sm_count * 16);
+      k_rootbits<<<grid, 256, 0, s>>>(a);
+    }
+    MSF_CUDA_TRY(cudaGetLastError());
+    MSF_CUDA_TRY(cudaMemcpyAsync(&F, a.counters, sizeof(F), cudaMemcpyDeviceToHost, s));
+    MSF_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   *n_out = (int64_t)F;
-  if ((int64_t)F > cap) {
+  if ((int64_t)F > cap || F == 0) {
+    MSF_CUDA_TRY(cudaStreamSynchronize(s));
     ctx->timer.flush();
-    return MSF_ERR_CAPACITY;
+    return (int64_t)F > cap ? MSF_ERR_CAPACITY : MSF_OK;
   }
-  if (F == 0) {
-    ctx->timer.flush();
-    return MSF_OK;
-  }
-  a.F = (int64_t)F;
-  // accumulators: one buffer carved into SoA arrays (8-byte members first)
+  a.acc.F = (int64_t)F;
+  // K copies of the accumulators spread the atomics of large features (K * F <= 2^20)
+  int K = 16;
+  while (K > 1 && (int64_t)K * (int64_t)F > (1 << 20)) K >>= 1;
+  a.acc.K = K;
+  const int64_t FK = (int64_t)F * K;
+  // accumulators: one buffer carved into SoA arrays
   const int Af = d.A > 0 ? d.A : 1;
-  const size_t f8 = sizeof(unsigned long long) * F;
+  const size_t f8 = sizeof(unsigned long long) * FK;
   auto r256 = [](size_t n) { return (n + 255) & ~size_t(255); };
   const size_t bytes = 4 * r256(f8) + r256(f8 * 4) + 2 * r256(f8 * Af) +
-                       2 * r256(sizeof(unsigned) * F) + 2 * r256(sizeof(int) * F * 4) +
+                       2 * r256(sizeof(unsigned) * FK) + 2 * r256(sizeof(int) * FK * 4) +
                        r256(sizeof(msf_feature) * F);
   MSF_TRY(S.acc.ensure(bytes));
   char* p = S.acc.as<char>();
   auto carve = [&](size_t n) {
     char* q = p;
-    p += (n + 255) & ~size_t(255);
+    p += r256(n);
     return q;
   };
-  a.n_vox = reinterpret_cast<unsigned long long*>(carve(f8));
-  a.n_pts = reinterpret_cast<unsigned long long*>(carve(f8));
-  a.sf = reinterpret_cast<double*>(carve(f8));
-  a.sf2 = reinterpret_cast<double*>(carve(f8));
-  a.sc = reinterpret_cast<unsigned long long*>(carve(f8 * 4));
-  a.sq = reinterpret_cast<unsigned long long*>(carve(f8 * Af));
-  a.sa2 = reinterpret_cast<double*>(carve(f8 * Af));
-  a.fmin = reinterpret_cast<unsigned*>(carve(sizeof(unsigned) * F));
-  a.fmax = reinterpret_cast<unsigned*>(carve(sizeof(unsigned) * F));
-  a.bbmin = reinterpret_cast<int*>(carve(sizeof(int) * F * 4));
-  a.bbmax = reinterpret_cast<int*>(carve(sizeof(int) * F * 4));
-  a.out = out_kind == MSF_DEVICE ? out : reinterpret_cast<msf_feature*>(carve(sizeof(msf_feature) * F));
+  a.acc.n_vox = reinterpret_cast<unsigned long long*>(carve(f8));
+  a.acc.n_pts = reinterpret_cast<unsigned long long*>(carve(f8));
+  a.acc.sf = reinterpret_cast<double*>(carve(f8));
+  a.acc.sf2 = reinterpret_cast<double*>(carve(f8));
+  a.acc.sc = reinterpret_cast<unsigned long long*>(carve(f8 * 4));
+  a.acc.sq = reinterpret_cast<unsigned long long*>(carve(f8 * Af));
+  a.acc.sa2 = reinterpret_cast<double*>(carve(f8 * Af));
+  a.acc.fmin = reinterpret_cast<unsigned*>(carve(sizeof(unsigned) * FK));
+  a.acc.fmax = reinterpret_cast<unsigned*>(carve(sizeof(unsigned) * FK));
+  a.acc.bbmin = reinterpret_cast<int*>(carve(sizeof(int) * FK * 4));
+  a.acc.bbmax = reinterpret_cast<int*>(carve(sizeof(int) * FK * 4));
+  a.out = out_kind == MSF_DEVICE ? out
+                                 : reinterpret_cast<msf_feature*>(carve(sizeof(msf_feature) * F));
   const unsigned fb = (unsigned)((F + 255) / 256);
   {
     ScopedKernel k(ctx, "k_scan_reduce");
@@ -443,24 +427,21 @@ int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
   }
   {
     ScopedKernel k(ctx, "k_feat_init");
-    k_feat_init<<<fb, 256, 0, s>>>(a);
+    const int64_t nb = (FK + 255) / 256;
+    k_feat_init<<<(unsigned)std::min<int64_t>(nb, (int64_t)ctx->sm_count * 16), 256, 0, s>>>(a);
   }
-  {
-    ScopedKernel k(ctx, "k_vox");
-    const int64_t rows = (int64_t)g.tw * d.nz * d.ny * g.nxs;
-    k_vox<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(a);
-  }
-  if (d.P > 0 && d.A > 0) {
-    ScopedKernel k(ctx, "k_pts");
-    switch (d.A) {
-      case 1: launch_pts<1>(a, s); break;
-      case 2: launch_pts<2>(a, s); break;
-      case 3: launch_pts<3>(a, s); break;
-      case 4: launch_pts<4>(a, s); break;
-      case 5: launch_pts<5>(a, s); break;
-      case 6: launch_pts<6>(a, s); break;
-      case 7: launch_pts<7>(a, s); break;
-      default: launch_pts<8>(a, s); break;
+  if (fast) {
+    MSF_TRY(seg_feature_stats(ctx, a.rk, a.acc));
+  } else {
+    {
+      ScopedKernel k(ctx, "k_vox");
+      const int64_t rows = (int64_t)g.tw * d.nz * d.ny * g.nxs;
+      k_vox<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(a);
+    }
+    if (d.P > 0 && d.A > 0) {
+      ScopedKernel k(ctx, "k_pts");
+      dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)a.tw);
+      k_pts<<<grid, 256, 0, s>>>(a);
     }
   }
   {

@@ -15,7 +15,8 @@
 //              per component its smallest index. Nothing per voxel is written.
 //   k_hook     one thread per segment: joins components across tile faces (x, y, z and the
 //              t-chunk boundary) with a global union-find on the component table.
-//   k_traj     one thread per (point, t): joins the components of key[t][p] and key[t+1][p].
+//   k_links    one thread per (point, t): joins the components of key[t][p] and key[t+1][p],
+//              and records the point samples that fall in member voxel-timesteps.
 //   k_flatten  one CTA per tile: path-compresses every component to its root and reduces the
 //              smallest index onto the root; counts roots (= features).
 //   k_final    one CTA per tile: resolves each run's label in shared memory and streams the
@@ -44,7 +45,9 @@ struct SegArgs {
   int32_t* cminli;
   int2* tileinfo;  // (runs, components) per tile
   int32_t* labels;
-  unsigned long long* counters;  // [0] features, [1] error flags
+  unsigned long long* counters;  // [0] features, [1] error flags, [3] samples collected
+  int64_t* sample_sid;           // point samples of the window inside a feature: tw * P + p
+  uint32_t* sample_comp;         // ... and their component
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -62,41 +65,30 @@ __device__ __forceinline__ int run_index(uint32_t starts, int x) {
 }
 
 __device__ __forceinline__ bool cmp_pred(const DevPred& p, uint32_t raw) {
-  if (p.is_int) {
-    int c = (int)raw;
-    switch (p.op) {
-      case MSF_OP_GT: return c > p.ilo;
-      case MSF_OP_GE: return c >= p.ilo;
-      case MSF_OP_LT: return c < p.ilo;
-      case MSF_OP_LE: return c <= p.ilo;
-      default: return p.ilo <= c && c <= p.ihi;
-    }
-  }
-  float x = __uint_as_float(raw);
-  switch (p.op) {
-    case MSF_OP_GT: return x > p.lo;
-    case MSF_OP_GE: return x >= p.lo;
-    case MSF_OP_LT: return x < p.lo;
-    case MSF_OP_LE: return x <= p.lo;
-    default: return p.lo <= x && x <= p.hi;
-  }
+  if (p.is_int) return ((int)raw >= p.ilo) & ((int)raw <= p.ihi);
+  const float x = __uint_as_float(raw);
+  return (x >= p.lo) & (x <= p.hi);
 }
 
-// Shared-memory union-find over run slots (values only decrease).
-__device__ __forceinline__ uint32_t sfind(volatile uint32_t* par, uint32_t a) {
-  uint32_t p = par[a];
-  while (p != a) {
-    a = p;
-    p = par[a];
+// Shared-memory union-find over run slots (values only decrease). Path halving: each visited
+// slot is pointed at its grandparent with atomicMin, which only lowers a parent to another
+// ancestor in the same set, so it composes with concurrent linking.
+__device__ __forceinline__ uint32_t sfind(uint32_t* par, uint32_t a) {
+  volatile uint32_t* vp = par;
+  while (true) {
+    const uint32_t p = vp[a];
+    if (p == a) return a;
+    const uint32_t gp = vp[p];
+    if (gp == p) return p;
+    atomicMin(par + a, gp);
+    a = gp;
   }
-  return a;
 }
 
 __device__ __forceinline__ void sunion(uint32_t* par, uint32_t a, uint32_t b) {
-  volatile uint32_t* vp = par;
   while (true) {
-    a = sfind(vp, a);
-    b = sfind(vp, b);
+    a = sfind(par, a);
+    b = sfind(par, b);
     if (a == b) return;
     if (a > b) {
       uint32_t t = a;
@@ -218,7 +210,7 @@ __device__ __forceinline__ TileCoord tile_coord(const Geometry& g, int tile) {
 // ---------------------------------------------------------------------------------------------
 // k_tile: criterion + tile-local labelling
 // ---------------------------------------------------------------------------------------------
-template <int NP, bool SPATIAL>
+template <int NP, bool SPATIAL, bool VEC>
 __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a) {
   constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
   __shared__ uint32_t s_mask[kSegPerTile];
@@ -233,33 +225,70 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a)
   const int tile = blockIdx.x;
   const TileCoord tc = tile_coord(g, tile);
   const int BY = 1 << g.lby, BZ = 1 << g.lbz;
-  const int x = tc.xs * 32 + lane;
 
-  // ---- phase 1: criterion, one ballot per row --------------------------------------------
-  constexpr int U = 8;
+  // ---- phase 1: criterion, one 32-bit activity mask per row -------------------------------
+  if (VEC) {
+    // 16-byte loads: lane = (row r of 4, x-quad q of 8); 4 rows per warp instruction.
+    const int q = lane & 7, rsub = lane >> 3;
+    const int x4 = tc.xs * 32 + 4 * q;
+    constexpr int U = NP <= 2 ? 4 : 2;
 #pragma unroll 1
-  for (int i = 0; i < 32; i += U) {
-    uint32_t raw[U][NP > 0 ? NP : 1];
-    bool valid[U];
+    for (int it = 0; it < 8; it += U) {
+      uint4 raw[U][NP > 0 ? NP : 1];
+      bool valid[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int s = warp * 32 + i + u;
-      const int ly = s & (BY - 1), lz = (s >> g.lby) & (BZ - 1), lt = s >> (g.lby + g.lbz);
-      const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
-      valid[u] = x < g.nx && y < g.ny && z < g.nz && tw < g.tw;
-      const int64_t off =
-          (int64_t)(g.t0 + tw) * g.V + ((int64_t)z * g.ny + y) * g.nx + x;
+      for (int u = 0; u < U; ++u) {
+        const int sg = warp * 32 + 4 * (it + u) + rsub;
+        const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
+        const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
+        valid[u] = x4 < g.nx && y < g.ny && z < g.nz && tw < g.tw;
+        const int64_t off = (int64_t)(g.t0 + tw) * g.V + (int64_t)(z * g.ny + y) * g.nx + x4;
 #pragma unroll
-      for (int j = 0; j < NP; ++j)
-        raw[u][j] = valid[u] ? __ldcs(static_cast<const unsigned int*>(a.pred[j].base) + off) : 0u;
+        for (int j = 0; j < NP; ++j)
+          raw[u][j] = valid[u] ? __ldcs(reinterpret_cast<const uint4*>(
+                                     static_cast<const unsigned int*>(a.pred[j].base) + off))
+                               : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        unsigned nib = valid[u] ? 0xFu : 0u;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          const DevPred& pr = a.pred[j];
+          nib &= (unsigned)cmp_pred(pr, raw[u][j].x) | ((unsigned)cmp_pred(pr, raw[u][j].y) << 1) |
+                 ((unsigned)cmp_pred(pr, raw[u][j].z) << 2) |
+                 ((unsigned)cmp_pred(pr, raw[u][j].w) << 3);
+        }
+        const unsigned m = __reduce_or_sync(0xFFu << (lane & 24), nib << (4 * q));
+        if (q == 0) s_mask[warp * 32 + 4 * (it + u) + rsub] = m;
+      }
     }
+  } else {
+    const int x = tc.xs * 32 + lane;
+    constexpr int U = 8;
+#pragma unroll 1
+    for (int i = 0; i < 32; i += U) {
+      uint32_t raw[U][NP > 0 ? NP : 1];
+      bool valid[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      bool act = valid[u];
+      for (int u = 0; u < U; ++u) {
+        const int sg = warp * 32 + i + u;
+        const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
+        const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
+        valid[u] = x < g.nx && y < g.ny && z < g.nz && tw < g.tw;
+        const int64_t off = (int64_t)(g.t0 + tw) * g.V + (int64_t)(z * g.ny + y) * g.nx + x;
 #pragma unroll
-      for (int j = 0; j < NP; ++j) act = act && cmp_pred(a.pred[j], raw[u][j]);
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, act);
-      if (lane == 0) s_mask[warp * 32 + i + u] = m;
+        for (int j = 0; j < NP; ++j)
+          raw[u][j] = valid[u] ? __ldcs(static_cast<const unsigned int*>(a.pred[j].base) + off) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        bool act = valid[u];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) act = act && cmp_pred(a.pred[j], raw[u][j]);
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, act);
+        if (lane == 0) s_mask[warp * 32 + i + u] = m;
+      }
     }
   }
   __syncthreads();
@@ -366,12 +395,10 @@ __global__ void __launch_bounds__(256) k_hook(const __grid_constant__ SegArgs a)
   if (gs >= g.nseg) return;
   const uint32_t m = __ldg(a.segmask + gs);
   if (!m) return;
-  const int xs = (int)(gs % g.nxs);
-  int64_t r = gs / g.nxs;
-  const int y = (int)(r % g.ny);
-  r /= g.ny;
-  const int z = (int)(r % g.nz);
-  const int tw = (int)(r / g.nz);
+  uint32_t r, xs, y, z, tw;
+  g.fnxs.divmod((uint32_t)gs, r, xs);
+  g.fny.divmod(r, r, y);
+  g.fnz.divmod(r, tw, z);
   const uint32_t st = run_starts(m, SPATIAL);
   const uint32_t rb = __ldg(a.segrun + gs);
 
@@ -393,10 +420,10 @@ __global__ void __launch_bounds__(256) k_hook(const __grid_constant__ SegArgs a)
     if ((m & 1u) && xs > 0) {
       const uint32_t c0 = __ldg(a.runcomp + rb);
       for (int dz = -1; dz <= 1; ++dz) {
-        const int z2 = z + dz;
+        const int z2 = (int)z + dz;
         if (z2 < 0 || z2 >= g.nz) continue;
         for (int dy = -1; dy <= 1; ++dy) {
-          const int y2 = y + dy;
+          const int y2 = (int)y + dy;
           if (y2 < 0 || y2 >= g.ny) continue;
           const int64_t gs2 = seg_index(g, tw, z2, y2, xs - 1);
           const uint32_t m2 = __ldg(a.segmask + gs2);
@@ -411,9 +438,9 @@ __global__ void __launch_bounds__(256) k_hook(const __grid_constant__ SegArgs a)
     const int dys[4] = {-1, -1, 0, 1}, dzs[4] = {0, -1, -1, -1};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int y2 = y + dys[k], z2 = z + dzs[k];
+      const int y2 = (int)y + dys[k], z2 = (int)z + dzs[k];
       if (y2 < 0 || y2 >= g.ny || z2 < 0) continue;
-      if ((y2 >> g.lby) == (y >> g.lby) && (z2 >> g.lbz) == (z >> g.lbz)) continue;
+      if ((y2 >> g.lby) == ((int)y >> g.lby) && (z2 >> g.lbz) == ((int)z >> g.lbz)) continue;
       join_rows(seg_index(g, tw, z2, y2, xs), true);
     }
   }
@@ -422,15 +449,15 @@ __global__ void __launch_bounds__(256) k_hook(const __grid_constant__ SegArgs a)
 }
 
 // ---------------------------------------------------------------------------------------------
-// k_traj: trajectory links
+// k_links: trajectory links and the point samples of the features
 // ---------------------------------------------------------------------------------------------
 template <bool SPATIAL>
 __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) {
   const Geometry& g = a.g;
-  const int x = v % g.nx;
-  const int yz = v / g.nx;
-  const int y = yz % g.ny, z = yz / g.ny;
-  const int64_t gs = seg_index(g, tw, z, y, x >> 5);
+  uint32_t yz, x, z, y;
+  g.fnx.divmod((uint32_t)v, yz, x);
+  g.fny.divmod(yz, z, y);
+  const int64_t gs = seg_index(g, tw, (int)z, (int)y, (int)(x >> 5));
   const uint32_t m = __ldg(a.segmask + gs);
   const int b = x & 31;
   if (!((m >> b) & 1u)) return -1;
@@ -438,19 +465,81 @@ __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) 
   return __ldg(a.runcomp + __ldg(a.segrun + gs) + run_index(st, b));
 }
 
-template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_traj(const __grid_constant__ SegArgs a) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.P) return;
+// One thread per 4 (point, step) pairs of one row tw (points p = base + j * 256 + threadIdx.x):
+// with TRAJ joins the components of key[t][p] and key[t+1][p] (both members); with COLLECT
+// records every sample that lies in a member voxel-timestep (the point part of the features),
+// compacted per block with one atomic. Rows tw = 0 .. rows-1; with TRAJ the last row's t+1
+// samples are recorded by that row too.
+constexpr int kLinkPer = 4;
+
+template <bool SPATIAL, bool TRAJ, bool COLLECT>
+__global__ void __launch_bounds__(256) k_links(const __grid_constant__ SegArgs a) {
+  __shared__ int s_cnt[8];
+  __shared__ unsigned long long s_base;
   const int tw = blockIdx.y;
-  const int32_t ka = __ldcs(a.key + (int64_t)(a.g.t0 + tw) * a.P + p);
-  const int32_t kb = __ldcs(a.key + (int64_t)(a.g.t0 + tw + 1) * a.P + p);
-  if (ka < 0 || kb < 0) return;
-  const int64_t ca = comp_of<SPATIAL>(a, tw, ka);
-  if (ca < 0) return;
-  const int64_t cb = comp_of<SPATIAL>(a, tw + 1, kb);
-  if (cb < 0 || ca == cb) return;
-  gunion(a.cparent, (uint32_t)ca, (uint32_t)cb);
+  const int64_t p0 = (int64_t)blockIdx.x * (256 * kLinkPer) + threadIdx.x;
+  int32_t ka[kLinkPer], kb[kLinkPer];
+#pragma unroll
+  for (int j = 0; j < kLinkPer; ++j) {
+    const int64_t p = p0 + j * 256;
+    ka[j] = kb[j] = -1;
+    if (p < a.P) {
+      ka[j] = __ldcs(a.key + (int64_t)(a.g.t0 + tw) * a.P + p);
+      if (TRAJ) kb[j] = __ldcs(a.key + (int64_t)(a.g.t0 + tw + 1) * a.P + p);
+    }
+  }
+  int64_t ca[kLinkPer], cb[kLinkPer];
+#pragma unroll
+  for (int j = 0; j < kLinkPer; ++j) {
+    ca[j] = ka[j] >= 0 ? comp_of<SPATIAL>(a, tw, ka[j]) : -1;
+    cb[j] = (TRAJ && kb[j] >= 0) ? comp_of<SPATIAL>(a, tw + 1, kb[j]) : -1;
+  }
+  if (TRAJ) {
+#pragma unroll
+    for (int j = 0; j < kLinkPer; ++j)
+      if (ca[j] >= 0 && cb[j] >= 0 && ca[j] != cb[j]) gunion(a.cparent, (uint32_t)ca[j], (uint32_t)cb[j]);
+  }
+  if (COLLECT) {
+    const bool last = TRAJ && tw + 2 == a.g.tw;  // block-uniform
+    int mine = 0;
+#pragma unroll
+    for (int j = 0; j < kLinkPer; ++j) mine += (ca[j] >= 0) + (last && cb[j] >= 0);
+    // block exclusive scan of the per-thread counts
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_cnt[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int k = 0; k < 8; ++k) {
+        const int c = s_cnt[k];
+        s_cnt[k] = tot;
+        tot += c;
+      }
+      s_base = tot ? atomicAdd(&a.counters[3], (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long slot = s_base + s_cnt[w] + x - mine;
+#pragma unroll
+    for (int j = 0; j < kLinkPer; ++j) {
+      const int64_t p = p0 + j * 256;
+      if (ca[j] >= 0) {
+        a.sample_sid[slot] = (int64_t)tw * a.P + p;
+        a.sample_comp[slot] = (uint32_t)ca[j];
+        ++slot;
+      }
+      if (last && cb[j] >= 0) {
+        a.sample_sid[slot] = (int64_t)(tw + 1) * a.P + p;
+        a.sample_comp[slot] = (uint32_t)cb[j];
+        ++slot;
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -482,7 +571,7 @@ __global__ void __launch_bounds__(256) k_flatten(const __grid_constant__ SegArgs
 // ---------------------------------------------------------------------------------------------
 // k_final: stream out the int32 labels
 // ---------------------------------------------------------------------------------------------
-template <bool SPATIAL>
+template <bool SPATIAL, bool VEC>
 __global__ void __launch_bounds__(256) k_final(const __grid_constant__ SegArgs a) {
   constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
   __shared__ int32_t s_lbl[MAXR];
@@ -513,18 +602,48 @@ __global__ void __launch_bounds__(256) k_final(const __grid_constant__ SegArgs a
     s_rb[s] = rr;
   }
   __syncthreads();
+  if (VEC) {
+    // 16-byte stores: lane = (row r of 4, x-quad q of 8)
+    const int q = lane & 7, rsub = lane >> 3;
+    const int x4 = tc.xs * 32 + 4 * q;
+    if (x4 >= g.nx) return;
+#pragma unroll 2
+    for (int it = 0; it < 8; ++it) {
+      const int sg = warp * 32 + 4 * it + rsub;
+      const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
+      const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
+      if (y >= g.ny || z >= g.nz || tw >= g.tw) continue;
+      const uint32_t m = s_mask[sg];
+      int4 o = make_int4(-1, -1, -1, -1);
+      if ((m >> (4 * q)) & 0xFu) {
+        const uint32_t st = run_starts(m, SPATIAL);
+        const uint32_t rb = s_rb[sg];
+        int v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int b = 4 * q + e;
+          v[e] = ((m >> b) & 1u) ? s_lbl[rb + run_index(st, b)] : -1;
+        }
+        o = make_int4(v[0], v[1], v[2], v[3]);
+      }
+      __stcs(reinterpret_cast<int4*>(a.labels + (int64_t)tw * g.V +
+                                     (int64_t)(z * g.ny + y) * g.nx + x4),
+             o);
+    }
+    return;
+  }
   const int x = tc.xs * 32 + lane;
   if (x >= g.nx) return;
 #pragma unroll 4
   for (int i = 0; i < 32; ++i) {
-    const int s = warp * 32 + i;
-    const int ly = s & (BY - 1), lz = (s >> g.lby) & (BZ - 1), lt = s >> (g.lby + g.lbz);
+    const int sg = warp * 32 + i;
+    const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
     const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
     if (y >= g.ny || z >= g.nz || tw >= g.tw) continue;
-    const uint32_t m = s_mask[s];
+    const uint32_t m = s_mask[sg];
     int32_t lbl = -1;
-    if ((m >> lane) & 1u) lbl = s_lbl[s_rb[s] + run_index(run_starts(m, SPATIAL), lane)];
-    __stcs(a.labels + (((int64_t)tw * g.nz + z) * g.ny + y) * g.nx + x, lbl);
+    if ((m >> lane) & 1u) lbl = s_lbl[s_rb[sg] + run_index(run_starts(m, SPATIAL), lane)];
+    __stcs(a.labels + (int64_t)tw * g.V + (int64_t)(z * g.ny + y) * g.nx + x, lbl);
   }
 }
 
@@ -536,66 +655,92 @@ constexpr size_t tile_dyn_smem() {
   return (size_t)kSegPerTile * (SP ? 16 : 32) * (sizeof(uint32_t) + sizeof(uint16_t));
 }
 
-template <int NP, bool SP>
+template <int NP, bool SP, bool VEC>
 static void launch_tile(const SegArgs& a, int grid, cudaStream_t s) {
   static bool attr_set = false;  // per process; the attribute is per function
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tile<NP, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tile<NP, SP, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tile_dyn_smem<SP>());
     attr_set = true;
   }
-  k_tile<NP, SP><<<grid, 256, tile_dyn_smem<SP>(), s>>>(a);
+  k_tile<NP, SP, VEC><<<grid, 256, tile_dyn_smem<SP>(), s>>>(a);
 }
 
-template <bool SP>
+template <bool SP, bool VEC>
 static void launch_tile_np(const SegArgs& a, int grid, cudaStream_t s) {
   switch (a.npred) {
-    case 0: launch_tile<0, SP>(a, grid, s); break;
-    case 1: launch_tile<1, SP>(a, grid, s); break;
-    case 2: launch_tile<2, SP>(a, grid, s); break;
-    case 3: launch_tile<3, SP>(a, grid, s); break;
-    default: launch_tile<4, SP>(a, grid, s); break;
+    case 0: launch_tile<0, SP, VEC>(a, grid, s); break;
+    case 1: launch_tile<1, SP, VEC>(a, grid, s); break;
+    case 2: launch_tile<2, SP, VEC>(a, grid, s); break;
+    case 3: launch_tile<3, SP, VEC>(a, grid, s); break;
+    default: launch_tile<4, SP, VEC>(a, grid, s); break;
   }
 }
 
-int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t* nfeat) {
+static void launch_tile_any(const SegArgs& a, bool spatial, int grid, cudaStream_t s) {
+  const bool vec = (a.g.nx & 3) == 0;  // rows start on 16-byte boundaries
+  if (spatial) {
+    if (vec) launch_tile_np<true, true>(a, grid, s);
+    else launch_tile_np<true, false>(a, grid, s);
+  } else {
+    if (vec) launch_tile_np<false, true>(a, grid, s);
+    else launch_tile_np<false, false>(a, grid, s);
+  }
+}
+
+// Compact-state arguments shared by msf_segment and the retained-segmentation feature path.
+static int seg_args(msf_ctx* ctx, const Geometry& g, bool spatial, SegArgs* a) {
+  *a = SegArgs{};
+  a->g = g;
+  a->key = ctx->ds.key.as<int32_t>();
+  a->P = ctx->ds.P;
+  a->maxr = kSegPerTile * (spatial ? 16 : 32);
+  SegScratch& S = ctx->seg;
+  MSF_TRY(S.segmask.ensure(sizeof(uint32_t) * g.nseg));
+  MSF_TRY(S.segrun.ensure(sizeof(uint32_t) * g.nseg));
+  MSF_TRY(S.runcomp.ensure(sizeof(uint32_t) * (size_t)g.ntiles * a->maxr));
+  MSF_TRY(S.cparent.ensure(sizeof(uint32_t) * (size_t)g.ntiles * g.cmax));
+  MSF_TRY(S.cminli.ensure(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
+  MSF_TRY(S.tileinfo.ensure(sizeof(int2) * (size_t)g.ntiles));
+  MSF_TRY(S.counters.ensure(sizeof(unsigned long long) * 8));
+  a->segmask = S.segmask.as<uint32_t>();
+  a->segrun = S.segrun.as<uint32_t>();
+  a->runcomp = S.runcomp.as<uint32_t>();
+  a->cparent = S.cparent.as<uint32_t>();
+  a->cminli = S.cminli.as<int32_t>();
+  a->tileinfo = S.tileinfo.as<int2>();
+  a->counters = S.counters.as<unsigned long long>();
+  if (a->P > 0) {
+    const size_t ns = (size_t)a->P * (size_t)g.tw;
+    MSF_TRY(ctx->last.sample_sid.ensure(sizeof(int64_t) * ns));
+    MSF_TRY(ctx->last.sample_comp.ensure(sizeof(uint32_t) * ns));
+    a->sample_sid = ctx->last.sample_sid.as<int64_t>();
+    a->sample_comp = ctx->last.sample_comp.as<uint32_t>();
+  }
+  return MSF_OK;
+}
+
+int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t* nfeat,
+                const void* labels_user) {
   Geometry g;
   MSF_TRY(make_geometry(ctx, crit, &g));
+  ctx->last.valid = false;
   if (g.tw == 0) {
     if (nfeat) *nfeat = 0;
     return MSF_OK;
   }
   const bool spatial = crit->edges & MSF_EDGE_SPATIAL;
-  SegArgs a{};
-  a.g = g;
+  SegArgs a;
+  MSF_TRY(seg_args(ctx, g, spatial, &a));
   make_preds(ctx, crit, a.pred);
   a.npred = crit->n_pred;
   a.edges = crit->edges;
-  a.key = ctx->ds.key.as<int32_t>();
-  a.P = ctx->ds.P;
-  a.maxr = kSegPerTile * (spatial ? 16 : 32);
-  SegScratch& S = ctx->seg;
-  MSF_TRY(S.segmask.ensure(sizeof(uint32_t) * g.nseg));
-  MSF_TRY(S.segrun.ensure(sizeof(uint32_t) * g.nseg));
-  MSF_TRY(S.runcomp.ensure(sizeof(uint32_t) * (size_t)g.ntiles * a.maxr));
-  MSF_TRY(S.cparent.ensure(sizeof(uint32_t) * (size_t)g.ntiles * g.cmax));
-  MSF_TRY(S.cminli.ensure(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
-  MSF_TRY(S.tileinfo.ensure(sizeof(int2) * (size_t)g.ntiles));
-  MSF_TRY(S.counters.ensure(sizeof(unsigned long long) * 4));
-  a.segmask = S.segmask.as<uint32_t>();
-  a.segrun = S.segrun.as<uint32_t>();
-  a.runcomp = S.runcomp.as<uint32_t>();
-  a.cparent = S.cparent.as<uint32_t>();
-  a.cminli = S.cminli.as<int32_t>();
-  a.tileinfo = S.tileinfo.as<int2>();
-  a.counters = S.counters.as<unsigned long long>();
   a.labels = labels;
   cudaStream_t s = ctx->stream;
   MSF_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * 4, s));
   {
     ScopedKernel k(ctx, "k_tile");
-    if (spatial) launch_tile_np<true>(a, g.ntiles, s);
-    else launch_tile_np<false>(a, g.ntiles, s);
+    launch_tile_any(a, spatial, g.ntiles, s);
   }
   MSF_CUDA_TRY(cudaGetLastError());
   const unsigned nb = (unsigned)((g.nseg + 255) / 256);
@@ -604,11 +749,13 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
     if (spatial) k_hook<true><<<nb, 256, 0, s>>>(a);
     else k_hook<false><<<nb, 256, 0, s>>>(a);
   }
-  if ((crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1) {
-    ScopedKernel k(ctx, "k_traj");
-    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)(g.tw - 1));
-    if (spatial) k_traj<true><<<grid, 256, 0, s>>>(a);
-    else k_traj<false><<<grid, 256, 0, s>>>(a);
+  // trajectory joins; the same pass records the window's point samples that lie in a feature
+  const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1;
+  if (traj) {
+    ScopedKernel k(ctx, "k_links");
+    dim3 grid((unsigned)((a.P + 256 * kLinkPer - 1) / (256 * kLinkPer)), (unsigned)(g.tw - 1));
+    if (spatial) k_links<true, true, true><<<grid, 256, 0, s>>>(a);
+    else k_links<false, true, true><<<grid, 256, 0, s>>>(a);
   }
   {
     ScopedKernel k(ctx, "k_flatten");
@@ -616,8 +763,15 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   }
   {
     ScopedKernel k(ctx, "k_final");
-    if (spatial) k_final<true><<<g.ntiles, 256, 0, s>>>(a);
-    else k_final<false><<<g.ntiles, 256, 0, s>>>(a);
+    // 16-byte stores need 16-byte aligned rows and a 16-byte aligned labels buffer
+    const bool vec = (g.nx & 3) == 0 && ((uintptr_t)labels & 15) == 0;
+    if (spatial) {
+      if (vec) k_final<true, true><<<g.ntiles, 256, 0, s>>>(a);
+      else k_final<true, false><<<g.ntiles, 256, 0, s>>>(a);
+    } else {
+      if (vec) k_final<false, true><<<g.ntiles, 256, 0, s>>>(a);
+      else k_final<false, false><<<g.ntiles, 256, 0, s>>>(a);
+    }
   }
   MSF_CUDA_TRY(cudaGetLastError());
   unsigned long long h[2];
@@ -626,6 +780,180 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   ctx->timer.flush();
   if (h[1]) return MSF_ERR_INTERNAL;
   if (nfeat) *nfeat = (int64_t)h[0];
+  SegState& L = ctx->last;
+  L.valid = labels_user != nullptr;
+  L.crit = *crit;
+  L.labels_user = labels_user;
+  L.epoch = ctx->epoch;
+  L.g = g;
+  L.maxr = a.maxr;
+  L.n_features = (int64_t)h[0];
+  L.samples = traj;
+  return MSF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// retained-segmentation feature path
+// ---------------------------------------------------------------------------------------------
+static bool same_query(const msf_criteria& a, const msf_criteria& b) {
+  if (a.t0 != b.t0 || a.t1 != b.t1 || a.n_pred != b.n_pred || a.edges != b.edges) return false;
+  for (int i = 0; i < a.n_pred; ++i) {
+    const msf_pred &p = a.pred[i], &q = b.pred[i];
+    if (p.src != q.src || p.op != q.op || p.lo != q.lo) return false;
+    if (p.src == MSF_SRC_MEAN && p.attr != q.attr) return false;
+    if (p.op == MSF_OP_BAND && p.hi != q.hi) return false;
+  }
+  return true;
+}
+
+bool seg_state_matches(const msf_ctx* ctx, const msf_criteria* crit, const void* labels) {
+  const SegState& L = ctx->last;
+  return L.valid && labels && L.labels_user == labels && L.epoch == ctx->epoch &&
+         same_query(L.crit, *crit);
+}
+
+// Sets the bit of every feature's label (the root component's smallest index).
+__global__ void __launch_bounds__(256) k_mark_roots(const __grid_constant__ SegArgs a,
+                                                    uint32_t* rootbits) {
+  const int tile = blockIdx.x;
+  const int nc = min(a.tileinfo[tile].y, a.g.cmax);
+  const uint32_t cbase = (uint32_t)tile * (uint32_t)a.g.cmax;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const uint32_t c = cbase + k;
+    if (__ldg(a.cparent + c) == c) {
+      const int32_t lbl = __ldg(a.cminli + c);
+      atomicOr(rootbits + (lbl >> 5), 1u << (lbl & 31));
+    }
+  }
+}
+
+// Feature rank of every component (through its root's label).
+__global__ void __launch_bounds__(256) k_comp_fid(const __grid_constant__ SegArgs a,
+                                                  RankArrays rk, int32_t* cfid) {
+  const int tile = blockIdx.x;
+  const int nc = min(a.tileinfo[tile].y, a.g.cmax);
+  const uint32_t cbase = (uint32_t)tile * (uint32_t)a.g.cmax;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const uint32_t c = cbase + k;
+    cfid[c] = (int32_t)feature_rank(rk, __ldg(a.cminli + __ldg(a.cparent + c)));
+  }
+}
+
+// Voxel statistics, one CTA per tile: each run's feature comes from the component table, and
+// only member voxels read their field value and count.
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256) k_feat_vox(const __grid_constant__ SegArgs a, FeatAcc acc,
+                                                  const int32_t* __restrict__ cfid,
+                                                  const float* __restrict__ field,
+                                                  const int32_t* __restrict__ count) {
+  constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
+  __shared__ int32_t s_fid[MAXR];
+  __shared__ uint32_t s_mask[kSegPerTile];
+  __shared__ uint32_t s_rb[kSegPerTile];
+  const Geometry& g = a.g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tile = blockIdx.x;
+  const int nrun = min(a.tileinfo[tile].x, MAXR);
+  if (nrun == 0) return;
+  const TileCoord tc = tile_coord(g, tile);
+  const int BY = 1 << g.lby, BZ = 1 << g.lbz;
+  const uint32_t rbase = (uint32_t)tile * (uint32_t)a.maxr;
+  for (int r = tid; r < nrun; r += 256) s_fid[r] = __ldg(cfid + __ldg(a.runcomp + rbase + r));
+  {
+    const int sg = tid;
+    const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
+    const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
+    uint32_t mm = 0, rr = 0;
+    if (y < g.ny && z < g.nz && tw < g.tw) {
+      const int64_t gs = seg_index(g, tw, z, y, tc.xs);
+      mm = __ldg(a.segmask + gs);
+      rr = __ldg(a.segrun + gs) - rbase;
+    }
+    s_mask[sg] = mm;
+    s_rb[sg] = rr;
+  }
+  __syncthreads();
+  for (int i = 0; i < 32; ++i) {
+    const int sg = warp * 32 + i;
+    const uint32_t m = s_mask[sg];
+    if ((m >> lane) & 1u) {
+      const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
+      const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
+      const int x = tc.xs * 32 + lane;
+      const int64_t fid = s_fid[s_rb[sg] + run_index(run_starts(m, SPATIAL), lane)];
+      const int64_t off = (int64_t)(g.t0 + tw) * g.V + ((int64_t)z * g.ny + y) * g.nx + x;
+      accumulate_row(acc, m, fid, lane, tc.xs * 32, tw, z, y, __ldg(field + off),
+                     __ldg(count + off));
+    }
+    __syncwarp();  // one row's warp-synchronous reduction at a time
+  }
+}
+
+// Point statistics from the sample list (grid-stride up to the device-side sample count; the
+// loop bound is warp-uniform so that every lane takes part in the warp-level reduction).
+__global__ void __launch_bounds__(256) k_feat_samples(const __grid_constant__ SegArgs a,
+                                                      FeatAcc acc,
+                                                      const int32_t* __restrict__ cfid,
+                                                      const float* __restrict__ attr) {
+  const int64_t n = (int64_t)*(volatile unsigned long long*)&a.counters[3];
+  const int lane = threadIdx.x & 31;
+  const int64_t wbase = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31));
+  for (int64_t b = wbase; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = b + lane;
+    int64_t fid = -1, tw = 0, p = 0;
+    if (i < n) {
+      const int64_t sid = a.sample_sid[i];
+      fid = __ldg(cfid + a.sample_comp[i]);
+      tw = sid / a.P;
+      p = sid - tw * a.P;
+    }
+    accumulate_samples(acc, fid >= 0, fid, attr + ((int64_t)(a.g.t0 + tw) * acc.A) * a.P + p, a.P);
+  }
+}
+
+int seg_mark_roots(msf_ctx* ctx, uint32_t* rootbits, unsigned long long* counter) {
+  (void)counter;
+  const SegState& L = ctx->last;
+  SegArgs a;
+  MSF_TRY(seg_args(ctx, L.g, L.crit.edges & MSF_EDGE_SPATIAL, &a));
+  ScopedKernel k(ctx, "k_mark_roots");
+  k_mark_roots<<<L.g.ntiles, 256, 0, ctx->stream>>>(a, rootbits);
+  MSF_CUDA_TRY(cudaGetLastError());
+  return MSF_OK;
+}
+
+int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
+  SegState& L = ctx->last;
+  const Geometry& g = L.g;
+  const bool spatial = L.crit.edges & MSF_EDGE_SPATIAL;
+  SegArgs a;
+  MSF_TRY(seg_args(ctx, g, spatial, &a));
+  MSF_TRY(L.cfid.ensure(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
+  int32_t* cfid = L.cfid.as<int32_t>();
+  cudaStream_t s = ctx->stream;
+  const Dataset& d = ctx->ds;
+  {
+    ScopedKernel k(ctx, "k_comp_fid");
+    k_comp_fid<<<g.ntiles, 256, 0, s>>>(a, rk, cfid);
+  }
+  {
+    ScopedKernel k(ctx, "k_feat_vox");
+    if (spatial) k_feat_vox<true><<<g.ntiles, 256, 0, s>>>(a, acc, cfid, d.field.as<float>(), d.count.as<int32_t>());
+    else k_feat_vox<false><<<g.ntiles, 256, 0, s>>>(a, acc, cfid, d.field.as<float>(), d.count.as<int32_t>());
+  }
+  if (a.P > 0 && d.A > 0) {
+    if (!L.samples) {  // no trajectory pass ran: collect the samples now
+      MSF_CUDA_TRY(cudaMemsetAsync(a.counters + 3, 0, sizeof(unsigned long long), s));
+      ScopedKernel k(ctx, "k_links");
+      dim3 grid((unsigned)((a.P + 256 * kLinkPer - 1) / (256 * kLinkPer)), (unsigned)g.tw);
+      if (spatial) k_links<true, false, true><<<grid, 256, 0, s>>>(a);
+      else k_links<false, false, true><<<grid, 256, 0, s>>>(a);
+      L.samples = true;
+    }
+    ScopedKernel k(ctx, "k_feat_samples");
+    k_feat_samples<<<ctx->sm_count * 8, 256, 0, s>>>(a, acc, cfid, d.attr.as<float>());
+  }
+  MSF_CUDA_TRY(cudaGetLastError());
   return MSF_OK;
 }
 

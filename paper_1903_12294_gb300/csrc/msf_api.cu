@@ -1,6 +1,7 @@
 // C ABI of the library (include/msf.h): context, resident dataset, argument checking and the
 // host side of each entry point. Kernels live in k_bin.cu, k_segment.cu and k_features.cu.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -168,6 +169,10 @@ int make_geometry(const msf_ctx* ctx, const msf_criteria* c, Geometry* g) {
   if ((int64_t)g->ntiles * std::max(g->cmax, kSegPerTile * 32) >= ((int64_t)1 << 32))
     return MSF_ERR_TOO_LARGE;
   g->nseg = (int64_t)g->tw * d.nz * d.ny * g->nxs;
+  g->fnx = FastDiv((uint32_t)d.nx);
+  g->fny = FastDiv((uint32_t)d.ny);
+  g->fnz = FastDiv((uint32_t)d.nz);
+  g->fnxs = FastDiv((uint32_t)g->nxs);
   return MSF_OK;
 }
 
@@ -176,11 +181,23 @@ void make_preds(const msf_ctx* ctx, const msf_criteria* c, DevPred* out) {
   for (int i = 0; i < c->n_pred; ++i) {
     const msf_pred& p = c->pred[i];
     DevPred& q = out[i];
-    q.op = p.op;
-    q.lo = p.lo;
-    q.hi = p.hi;
-    q.ilo = (int)p.lo;
-    q.ihi = (int)p.hi;
+    const float inf = INFINITY, nan = NAN;
+    switch (p.op) {  // fp32 interval
+      case MSF_OP_GT: q.lo = p.lo == inf ? nan : nextafterf(p.lo, inf); q.hi = inf; break;
+      case MSF_OP_GE: q.lo = p.lo; q.hi = inf; break;
+      case MSF_OP_LT: q.lo = -inf; q.hi = p.lo == -inf ? nan : nextafterf(p.lo, -inf); break;
+      case MSF_OP_LE: q.lo = -inf; q.hi = p.lo; break;
+      default: q.lo = p.lo; q.hi = p.hi; break;
+    }
+    const int l = p.src == MSF_SRC_COUNT ? (int)p.lo : 0;  // range checked by validate_criteria
+    const int h = p.src == MSF_SRC_COUNT && p.op == MSF_OP_BAND ? (int)p.hi : 0;
+    switch (p.op) {  // int32 interval (an empty one as [1, 0])
+      case MSF_OP_GT: q.ilo = l == INT32_MAX ? 1 : l + 1; q.ihi = l == INT32_MAX ? 0 : INT32_MAX; break;
+      case MSF_OP_GE: q.ilo = l; q.ihi = INT32_MAX; break;
+      case MSF_OP_LT: q.ilo = l == INT32_MIN ? 1 : INT32_MIN; q.ihi = l == INT32_MIN ? 0 : l - 1; break;
+      case MSF_OP_LE: q.ilo = INT32_MIN; q.ihi = l; break;
+      default: q.ilo = l; q.ihi = h; break;
+    }
     if (p.src == MSF_SRC_FIELD) {
       q.base = d.field.p;
       q.is_int = 0;
@@ -254,6 +271,7 @@ void msf_destroy(msf_ctx* c) {
                     &c->feat.out})
     b->release();
   for (DevBuf* b : {&c->bin.cnt, &c->bin.sum, &c->bin.absmax, &c->bin.outside}) b->release();
+  for (DevBuf* b : {&c->last.sample_sid, &c->last.sample_comp, &c->last.cfid}) b->release();
   c->host_staging.release();
   c->timer.release();
   delete c;
@@ -280,6 +298,8 @@ int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* f
   d.loaded = false;
   d.binned = false;
   d.has_sumq = false;
+  c->epoch++;
+  c->last.valid = false;
   d.nx = nx;
   d.ny = ny;
   d.nz = nz;
@@ -299,6 +319,8 @@ int msf_bin_particles(msf_ctx* c, unsigned flags, msf_bin_stats* stats) {
   if (flags & ~(unsigned)MSF_BIN_KEEP_SUMQ) return MSF_ERR_INVALID_ARG;
   if (!c->ds.loaded) return MSF_ERR_NOT_LOADED;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
+  c->epoch++;
+  c->last.valid = false;
   MSF_TRY(bin_run(c, flags));
   if (stats) {
     memset(stats, 0, sizeof(*stats));
@@ -345,7 +367,7 @@ int msf_segment(msf_ctx* c, const msf_criteria* crit, int32_t* labels, int label
     MSF_TRY(c->host_staging.ensure(sizeof(int32_t) * N));
     dst = c->host_staging.as<int32_t>();
   }
-  MSF_TRY(segment_run(c, crit, dst, n_features));
+  MSF_TRY(segment_run(c, crit, dst, n_features, labels));
   if (labels_kind == MSF_HOST && N > 0) {
     MSF_CUDA_TRY(cudaMemcpyAsync(labels, dst, sizeof(int32_t) * N, cudaMemcpyDeviceToHost,
                                  c->stream));
@@ -367,13 +389,15 @@ int msf_extract_features(msf_ctx* c, const msf_criteria* crit, const int32_t* la
   if (N > 0 && !labels) return MSF_ERR_INVALID_ARG;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
   const int32_t* src = labels;
-  if (labels_kind == MSF_HOST && N > 0) {
+  // Labels this context's last msf_segment wrote for the same query are not read back: the
+  // statistics come from the retained segmentation (so host labels need no upload either).
+  if (labels_kind == MSF_HOST && N > 0 && !seg_state_matches(c, crit, labels)) {
     MSF_TRY(c->host_staging.ensure(sizeof(int32_t) * N));
     MSF_CUDA_TRY(cudaMemcpyAsync(c->host_staging.p, labels, sizeof(int32_t) * N,
                                  cudaMemcpyHostToDevice, c->stream));
     src = c->host_staging.as<int32_t>();
   }
-  return features_run(c, crit, src, out, out_kind, cap, n_out);
+  return features_run(c, crit, src, labels, out, out_kind, cap, n_out);
 }
 
 int msf_set_tile(msf_ctx* c, int by, int bz, int bt) {

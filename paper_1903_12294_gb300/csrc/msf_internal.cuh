@@ -64,8 +64,32 @@ struct Dataset {
 constexpr int kSegPerTile = 256;                 // BY * BZ * BT
 constexpr int kMaxRunsPerTile = kSegPerTile * 16; // at most 16 runs in a 32-bit row mask
 
+// Unsigned 32-bit division by a runtime constant: q = (t + ((n - t) >> s1)) >> s2 with
+// t = umulhi(m, n) (the round-up method of Granlund and Montgomery), exact for all n < 2^32.
+struct FastDiv {
+  uint32_t d = 1, m = 1;
+  int s1 = 0, s2 = 0;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t dd) : d(dd) {
+    int l = 0;
+    while (((uint64_t)1 << l) < dd) ++l;
+    m = (uint32_t)((((uint64_t)1 << 32) * (((uint64_t)1 << l) - dd)) / dd + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l > 1 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+  __device__ __forceinline__ void divmod(uint32_t n, uint32_t& q, uint32_t& r) const {
+    q = div(n);
+    r = n - q * d;
+  }
+};
+
 struct Geometry {
   int nx, ny, nz, V, tw, t0, T;
+  FastDiv fnx, fny, fnz, fnxs;  // division by nx, ny, nz and the segments per x-row
   int nxs;                 // segments along x = ceil(nx / 32)
   int lby, lbz, lbt;       // log2 of the tile extent along y, z, t
   int tly, tlz, tlt;       // tiles along y, z, t
@@ -74,10 +98,11 @@ struct Geometry {
   int64_t nseg;            // segments in the window
 };
 
+// A predicate as a closed interval: lo <= x <= hi (fp32) or ilo <= c <= ihi (int32). Strict
+// comparisons move the bound to the next representable value; NaN bounds make it empty.
 struct DevPred {
   const void* base;  // array at absolute timestep 0: [T][V] (field/count) or mean + a*T*V
   int is_int;
-  int op;
   float lo, hi;
   int ilo, ihi;
 };
@@ -88,6 +113,21 @@ struct SegScratch {
 
 struct FeatScratch {
   DevBuf rootbits, wordrank, blocksums, acc, out;
+};
+
+// What msf_segment leaves behind for msf_extract_features: the compact segmentation of one
+// query (row masks, runs, component table in SegScratch), the buffers its labels went to, and
+// the point samples of the window that fell in a feature (sample id tw*P + p, component).
+struct SegState {
+  bool valid = false;
+  msf_criteria crit{};
+  const void* labels_user = nullptr;  // the caller's labels pointer of that call
+  uint64_t epoch = 0;                 // dataset epoch it was computed on
+  Geometry g{};
+  int maxr = 0;
+  int64_t n_features = 0;
+  bool samples = false;               // sample list complete for this query
+  DevBuf sample_sid, sample_comp, cfid;
 };
 
 struct BinScratch {
@@ -126,6 +166,8 @@ struct msf_ctx {
   msf::FeatScratch feat;
   msf::BinScratch bin;
   msf::DevBuf host_staging;  // device-side staging for host label buffers
+  msf::SegState last;        // retained segmentation of the last msf_segment call
+  uint64_t epoch = 1;        // bumped whenever the dataset or its binning changes
   int tile_by = 0, tile_bz = 0, tile_bt = 0;
   msf::KernelTimer timer;
 };
@@ -175,11 +217,206 @@ __device__ __forceinline__ long long quantise(float v, int k) {
   return (b >> 31) ? -q : q;
 }
 
+// ---------------------------------------------------------------------------------------------
+// feature accumulators and the two shared reduction steps
+//
+// Accumulators are SoA arrays of K copies x F features (index copy * F + feature); a block adds
+// into copy blockIdx.x % K, so that the atomics of a large feature spread over K addresses;
+// k_records sums the copies. Sums of field values and squares are formed per warp group in
+// double-float (fp32 pairs with exact TwoSum/TwoProd steps) and committed as two fp64 atomics;
+// no fp64 arithmetic runs on the SM (the part's fp64 pipe is narrow).
+// ---------------------------------------------------------------------------------------------
+struct FeatAcc {
+  unsigned long long* n_vox;
+  unsigned long long* n_pts;
+  double* sf;
+  double* sf2;
+  unsigned* fmin;  // order-preserving float keys
+  unsigned* fmax;
+  int* bbmin;      // [K*F][4] t, z, y, x
+  int* bbmax;
+  unsigned long long* sc;  // [K*F][4] coordinate sums t, z, y, x
+  unsigned long long* sq;  // [K*F][A] fixed-point attribute sums
+  double* sa2;             // [K*F][A] sums of squares
+  int A;
+  int K;                   // copies (power of two)
+  int64_t F;
+  int kscale[MSF_MAX_ATTR];
+};
+
+// Rank arrays of the feature labels: one bit per voxel-timestep (set at each feature's label)
+// and the exclusive prefix of the per-word popcounts.
+struct RankArrays {
+  const uint32_t* rootbits;
+  const uint32_t* wordrank;
+  int64_t N;
+};
+
+// Rank of a label among the feature labels, or -1 when it is not one.
+__device__ __forceinline__ int64_t feature_rank(const RankArrays& r, int32_t lbl) {
+  if (lbl < 0 || (int64_t)lbl >= r.N) return -1;
+  const int w = lbl >> 5, b = lbl & 31;
+  const uint32_t bits = __ldg(r.rootbits + w);
+  if (!((bits >> b) & 1u)) return -1;
+  return (int64_t)__ldg(r.wordrank + w) + __popc(bits & ((1u << b) - 1u));
+}
+
+__device__ __forceinline__ unsigned float_key(float f) {
+  const unsigned b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// float -> double by bit manipulation (exact); zero, subnormal, inf and NaN take the slow path.
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if ((b & 0x7FFFFFFFu) == 0u) return 0.0;
+  if (e == 0u || e == 0xFFu) return (double)f;
+  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)((b & 0x7u) << 29));
+}
+
+// s + e == a + b exactly (Knuth's TwoSum, IEEE fp32, no reassociation).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Double-float accumulator (hi + lo).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+// Both terms of a double-float are exact in fp32; their fp64 sum is formed in L2 atomics.
+__device__ __forceinline__ bool df_safe(float x) {
+  const float a = fabsf(x);
+  return a == 0.f || (a >= 1.0e-18f && a <= 1.0e18f);  // squares neither overflow nor go subnormal
+}
+
+// Voxels of one 32-voxel row (fixed tw, z, y; lane = x - x0): the lanes in `act` with the same
+// feature reduce in the warp and the group's first lane commits one atomic per quantity. All
+// lanes of `act`, and only those, must call this.
+__device__ __forceinline__ void accumulate_row(const FeatAcc& acc, unsigned act, int64_t fid,
+                                               int lane, int x0, int tw, int z, int y, float f,
+                                               int c) {
+  const unsigned grp = __match_any_sync(act, fid);
+  const int x = x0 + lane;
+  const int n = __popc(grp);
+  const int sum_c = __reduce_add_sync(grp, c);
+  const int sum_x = __reduce_add_sync(grp, x);
+  const bool isnan_f = f != f;
+  const unsigned kmin = __reduce_min_sync(grp, isnan_f ? float_key(INFINITY) : float_key(f));
+  const unsigned kmax = __reduce_max_sync(grp, isnan_f ? float_key(-INFINITY) : float_key(f));
+  const int leader = __ffs(grp) - 1;
+  const bool fast = __all_sync(grp, df_safe(f));
+  double s1, s2;
+  if (fast) {
+    const float p = __fmul_rn(f, f), pe = __fmaf_rn(f, f, -p);  // f*f == p + pe exactly
+    float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    for (unsigned m = grp; m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      df_add(h1, l1, __shfl_sync(grp, f, src));
+      df_add(h2, l2, __shfl_sync(grp, p, src));
+      df_add(h2, l2, __shfl_sync(grp, pe, src));
+    }
+    s1 = f2d(h1);
+    s2 = f2d(h2);
+    if (lane == leader) {
+      const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + fid;
+      atomicAdd(acc.sf + i, f2d(l1));
+      atomicAdd(acc.sf2 + i, f2d(l2));
+    }
+  } else {  // non-finite or extreme values: plain fp64 (rare)
+    s1 = 0.0;
+    s2 = 0.0;
+    for (unsigned m = grp; m; m &= m - 1) {
+      const double v = (double)__shfl_sync(grp, f, __ffs(m) - 1);
+      s1 += v;
+      s2 += v * v;
+    }
+  }
+  if (lane != leader) return;
+  const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + fid;
+  atomicAdd(acc.n_vox + i, (unsigned long long)n);
+  atomicAdd(acc.n_pts + i, (unsigned long long)sum_c);
+  atomicAdd(acc.sf + i, s1);
+  atomicAdd(acc.sf2 + i, s2);
+  atomicMin(acc.fmin + i, kmin);
+  atomicMax(acc.fmax + i, kmax);
+  int* bmn = acc.bbmin + i * 4;
+  int* bmx = acc.bbmax + i * 4;
+  atomicMin(bmn + 0, tw);
+  atomicMax(bmx + 0, tw);
+  atomicMin(bmn + 1, z);
+  atomicMax(bmx + 1, z);
+  atomicMin(bmn + 2, y);
+  atomicMax(bmx + 2, y);
+  atomicMin(bmn + 3, x0 + leader);
+  atomicMax(bmx + 3, x0 + (31 - __clz(grp)));
+  unsigned long long* scp = acc.sc + i * 4;
+  atomicAdd(scp + 0, (unsigned long long)n * (unsigned long long)tw);
+  atomicAdd(scp + 1, (unsigned long long)n * (unsigned long long)z);
+  atomicAdd(scp + 2, (unsigned long long)n * (unsigned long long)y);
+  atomicAdd(scp + 3, (unsigned long long)sum_x);
+}
+
+// Point samples (one per lane in `ok`): lanes of the same feature reduce their exact
+// fixed-point attribute values and double-float squares; the group's first lane commits.
+// Every lane of the warp must call this.
+__device__ __forceinline__ void accumulate_samples(const FeatAcc& acc, bool ok, int64_t fid,
+                                                   const float* attr_p, int64_t P) {
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, ok);
+  if (!ok) return;
+  const unsigned grp = __match_any_sync(act, fid);
+  const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+  const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + fid;
+  for (int j = 0; j < acc.A; ++j) {
+    const float v = __ldg(attr_p + (int64_t)j * P);
+    const long long q = quantise(v, acc.kscale[j]);
+    const float d = isfinite(v) ? v : 0.f;
+    long long qs = 0;
+    for (unsigned m = grp; m; m &= m - 1) qs += __shfl_sync(grp, q, __ffs(m) - 1);
+    double s2;
+    if (__all_sync(grp, df_safe(d))) {
+      const float p = __fmul_rn(d, d), pe = __fmaf_rn(d, d, -p);
+      float h = 0.f, l = 0.f;
+      for (unsigned m = grp; m; m &= m - 1) {
+        const int src = __ffs(m) - 1;
+        df_add(h, l, __shfl_sync(grp, p, src));
+        df_add(h, l, __shfl_sync(grp, pe, src));
+      }
+      s2 = f2d(h);
+      if (lane == leader) atomicAdd(acc.sa2 + i * acc.A + j, f2d(l));
+    } else {
+      s2 = 0.0;
+      for (unsigned m = grp; m; m &= m - 1) {
+        const double w = (double)__shfl_sync(grp, d, __ffs(m) - 1);
+        s2 += w * w;
+      }
+    }
+    if (lane == leader) {
+      atomicAdd(acc.sq + i * acc.A + j, (unsigned long long)qs);
+      atomicAdd(acc.sa2 + i * acc.A + j, s2);
+    }
+  }
+}
+
 // entry points of the translation units
 int bin_run(msf_ctx* ctx, unsigned flags);
-int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels_dev, int64_t* nfeat);
+int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels_dev, int64_t* nfeat,
+                const void* labels_user);
 int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels_dev,
-                 msf_feature* out, int out_kind, int64_t cap, int64_t* n_out);
+                 const void* labels_user, msf_feature* out, int out_kind, int64_t cap,
+                 int64_t* n_out);
+// fast feature path (k_segment.cu): marks the feature labels of the retained segmentation in
+// rootbits and counts them; then, after the ranks exist, reduces voxel and point statistics.
+int seg_mark_roots(msf_ctx* ctx, uint32_t* rootbits, unsigned long long* counter);
+int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc);
+bool seg_state_matches(const msf_ctx* ctx, const msf_criteria* crit, const void* labels);
 int validate_criteria(const msf_ctx* ctx, const msf_criteria* c);
 int make_geometry(const msf_ctx* ctx, const msf_criteria* c, Geometry* g);
 void make_preds(const msf_ctx* ctx, const msf_criteria* c, DevPred* out);

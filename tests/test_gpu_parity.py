@@ -31,10 +31,16 @@ def gpu_run(msf, field, pos, attr, t0, t1, preds, edges=7, tile=None, features=T
         if tile:
             ctx.set_tile(*tile)
         labels, n = ctx.segment(t0, t1, preds, edges)
-        feats = ctx.features(t0, t1, labels, preds, edges) if features else None
+        feats = feats_generic = None
+        if features:
+            # the labels msf_segment just wrote: statistics from the retained segmentation
+            feats = ctx.features(t0, t1, labels, preds, edges)
+            # the same labels in another buffer: statistics from the labels themselves
+            feats_generic = ctx.features(t0, t1, labels.clone(), preds, edges)
         torch.cuda.synchronize()
         return dict(stats=st, key=key.numpy(), count=count.numpy(), mean=mean.numpy(),
-                    sumq=sumq.numpy(), labels=labels.cpu().numpy(), n=n, feats=feats)
+                    sumq=sumq.numpy(), labels=labels.cpu().numpy(), n=n, feats=feats,
+                    feats_generic=feats_generic)
     finally:
         ctx.close()
 
@@ -53,8 +59,9 @@ def check_bins(g, o):
 def _close(a, b, rtol=RTOL, atol=0.0):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
-    both_nan = np.isnan(a) & np.isnan(b)
-    ok = both_nan | (np.abs(a - b) <= rtol * np.abs(b) + atol)
+    same = (a == b) | (np.isnan(a) & np.isnan(b))          # equal values, infinities, NaN
+    with np.errstate(invalid="ignore"):
+        ok = same | (np.abs(a - b) <= rtol * np.abs(b) + atol)
     assert ok.all(), (a[~ok][:5], b[~ok][:5])
 
 
@@ -87,6 +94,7 @@ def full_check(gpu, orc, field, pos, attr, t0, t1, preds, edges=7, tile=None):
     assert np.array_equal(g["labels"], lab)
     of = orc.features(field, o["count"], attr, o["key"], o["kscale"], t0, t1, lab)
     check_features(g["feats"], of, attr.shape[1])
+    check_features(g["feats_generic"], of, attr.shape[1])
     return g, o, lab
 
 
@@ -279,4 +287,86 @@ def test_quantisation_rounding_edges(gpu, orc, big):
                 [(C, 0, GE, 1, 0)], features=False)
     o = orc.bin((T, nz, ny, nx), pos, v)
     assert int(o["kscale"][0]) == (-77 if big else 50)
+    check_bins(g, o)
+
+
+def test_retained_segmentation_is_per_query(gpu, orc):
+    """Features of an older query's labels (another buffer, another criterion) are computed
+    from those labels, not from the most recent segmentation; host label buffers take the same
+    paths."""
+    wl = synth.mid(n=40, T=6, P=30000, n_blobs=10)
+    f, p, a = wl.numpy()
+    q1 = wl.preds
+    q2 = [(F, 0, GT, 0.35, 0)]
+    o = orc.bin(f.shape, p, a)
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(f, p, a)
+        ctx.bin()
+        l1, n1 = ctx.segment(0, 6, q1)
+        l2, n2 = ctx.segment(1, 5, q2)
+        fe1 = ctx.features(0, 6, l1, q1)           # not the last query: read from l1
+        fe2 = ctx.features(1, 5, l2, q2)           # the last query: retained segmentation
+        hl = np.empty((4,) + f.shape[1:], np.int32)
+        n3 = gpu.msf_segment(ctx.h, gpu.make_criteria(1, 5, q1), hl)
+        fe3 = gpu.msf_extract_features(ctx.h, gpu.make_criteria(1, 5, q1), hl)
+    finally:
+        ctx.close()
+    for (t0, t1, q, lab_g, fe) in ((0, 6, q1, l1.cpu().numpy(), fe1), (1, 5, q2, l2.cpu().numpy(), fe2),
+                                   (1, 5, q1, hl, fe3)):
+        lab, nf = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, q)
+        assert np.array_equal(lab_g, lab)
+        of = orc.features(f, o["count"], a, o["key"], o["kscale"], t0, t1, lab)
+        check_features(fe, of, a.shape[1])
+    assert n3 == len(fe3)
+
+
+def test_interval_predicate_edges(gpu, orc):
+    """Strict and inclusive comparisons at exact threshold values, +-0, infinities and NaN field
+    values: the library's interval form of each predicate selects what the comparison says."""
+    T, nz, ny, nx = 2, 3, 4, 36
+    vals = np.array([0.0, -0.0, 0.5, np.nextafter(np.float32(0.5), np.float32(1)),
+                     np.nextafter(np.float32(0.5), np.float32(0)), np.inf, -np.inf, np.nan, 1.0,
+                     -1.0, 1e-45, -1e-45], np.float32)
+    f = np.resize(vals, (T, nz, ny, nx)).astype(np.float32)
+    p = np.zeros((T, 3, 0), np.float32)
+    a = np.zeros((T, 0, 0), np.float32)
+    cases = [[(F, 0, GT, 0.5, 0)], [(F, 0, GE, 0.5, 0)], [(F, 0, LT, 0.5, 0)], [(F, 0, LE, 0.5, 0)],
+             [(F, 0, GT, 0.0, 0)], [(F, 0, LT, -0.0, 0)], [(F, 0, GT, np.inf, 0)],
+             [(F, 0, LT, -np.inf, 0)], [(F, 0, GE, -np.inf, 0)], [(F, 0, BAND, -0.0, 0.5)],
+             [(F, 0, GT, np.nan, 0)], [(F, 0, LE, np.inf, 0)]]
+    for preds in cases:
+        full_check(gpu, orc, f, p, a, 0, T, preds, edges=3)
+
+
+def test_mean_conversion_ties(gpu, orc):
+    """Per-voxel fixed-point sums that sit exactly half-way between two fp32 values (2^24 + 1,
+    2^24 + 3, 2^30 + 2^6, ...) must convert to fp32 with round-half-even before the division by
+    the count. With max|v| = 1 and 512 samples (2^10 >= 513, so k = 62 - 1 - 10 = 51) a value v
+    contributes v * 2^51 exactly, so two samples per voxel give any chosen sum."""
+    T, nz, ny, nx = 1, 1, 1, 16
+    k = 51
+    sums = [2 ** 24 + 1, 2 ** 24 + 3, 2 ** 30 + 2 ** 6, 2 ** 30 + 3 * 2 ** 6, 2 ** 40 + 2 ** 16,
+            2 ** 25 + 2, 2 ** 25 + 6, 2 ** 24 - 1, 2 ** 45 + 2 ** 21 + 1, 7]
+    P = 512
+    pos = np.full((T, 3, P), 0.5, np.float32)
+    vals = np.zeros((T, 1, P), np.float32)
+    vals[0, 0, -1] = 1.0                      # sets max|v| = 1 (in voxel 15)
+    pos[0, 0, -1] = 15.5
+    for i, s in enumerate(sums):
+        sh = max(s.bit_length() - 24, 0)      # hi keeps the top 24 significant bits, lo the rest:
+        hi = (s >> sh) << sh                  # both are exactly representable in fp32
+        lo = s - hi
+        for j, part in enumerate((hi, lo)):
+            p = 2 * i + j
+            pos[0, 0, p] = i + 0.5
+            vals[0, 0, p] = np.float32(part * 2.0 ** -k)
+            assert float(vals[0, 0, p]) * 2.0 ** k == part
+    for p in range(2 * len(sums), P - 1):      # the rest sit in voxel 14 with value 0
+        pos[0, 0, p] = 14.5
+    g = gpu_run(gpu, np.ones((T, nz, ny, nx), np.float32), np.ascontiguousarray(pos), vals, 0, T,
+                [(C, 0, GE, 1, 0)], features=False)
+    o = orc.bin((T, nz, ny, nx), pos, vals)
+    assert int(o["kscale"][0]) == k
+    assert [int(x) for x in o["sumq"][0, 0, 0, 0, :len(sums)]] == sums
     check_bins(g, o)
