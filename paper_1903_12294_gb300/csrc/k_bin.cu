@@ -2,16 +2,22 @@
 // (voxel, timestep) the sample count and the attribute aggregates.
 //
 // Determinism: attributes are summed as int64 fixed point, q = round_half_even(v * 2^k) with
-// k = 62 - e - b (max|v| < 2^e, 2^b >= P*T + 1), so the scattered atomic sums are exact and
-// independent of order; the fp32 mean is a fixed sequence of IEEE fp32 operations on that sum.
-// The paper's own GPU scheme keeps float running averages with atomics (§3.5), whose result
-// depends on the order of arrival. No per-sample or per-voxel work touches the fp64 units.
+// k = 62 - e - b (max|v| < 2^e, 2^b >= P*T + 1), so sums are exact and independent of order;
+// the fp32 mean is a fixed sequence of IEEE fp32 operations on that sum. The paper's own GPU
+// scheme keeps float running averages with atomics (§3.5), whose result depends on the order
+// of arrival. No per-sample or per-voxel work touches the fp64 units.
 //
-// Schedule: timestep by timestep, so that the scratch count/sum slab of one step (V * (4 + 8A)
-// bytes) stays in L2 while its atomics land:
-//   k_absmax    largest finite |v| per attribute (once per binning)
-//   k_scatter   one thread per point: key, then atomics into the step's scratch slab
-//   k_finalise  one thread per 4 voxels: count and mean out, scratch back to zero
+// Schedule: a counting sort of the samples by voxel range ("bucket" of R consecutive voxels),
+// so that the per-voxel sums are formed in shared memory rather than with global atomics
+// (scattered L2 atomics run at a fixed rate that would bound the whole pass):
+//   k_bin_keys     one thread per 4 samples of one timestep: key[t][p], and per block a shared-
+//                  memory histogram of buckets merged into hist[t][bucket]
+//   scan           offsets[t][bucket] = exclusive prefix of hist
+//   k_bin_place    one thread per 4 samples: each block reserves its slots per bucket with one
+//                  atomic, then writes (voxel-in-bucket, attributes) records; also the largest
+//                  finite |v| per attribute
+//   k_bin_reduce   one CTA per (bucket, timestep): counts and fixed-point sums of its records
+//                  in shared memory, then count and mean (and the sums) for all R voxels
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -23,40 +29,33 @@
 
 namespace msf {
 
-// Largest finite |v| per attribute. One grid row per (t, a) pair, so the attribute index is
-// uniform in a block.
-__global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ attr, int64_t P, int A,
-                                                unsigned* __restrict__ out) {
-  const int row = blockIdx.x;          // t * A + a
-  const int a = row % A;
-  const float* src = attr + (int64_t)row * P;
-  unsigned m = 0u;
-  for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < P;
-       i += (int64_t)gridDim.y * blockDim.x) {
-    const float v = __ldcs(src + i);
-    if (isfinite(v)) m = max(m, __float_as_uint(fabsf(v)));  // non-negative floats order as uints
-  }
-  m = __reduce_max_sync(0xFFFFFFFFu, m);
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(&out[a], m);
-}
+int scan_exclusive_u32(msf_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, DevBuf& tmp,
+                       uint32_t* total);
+
+constexpr int kBinPer = 4;             // samples per thread in the per-sample passes
+constexpr int kBinBlock = 256 * kBinPer;
+constexpr int kHistSmem = 8192;        // buckets counted in shared memory (else global atomics)
 
 struct BinArgs {
-  int nx, ny, nz, A;
+  int nx, ny, nz, A, T;
   int64_t V, P;
-  int t;
-  const float* pos;    // [T][3][P]
-  const float* attr;   // [T][A][P]
-  int32_t* key;        // [T][P]
-  int32_t* scnt;       // [V] scratch
-  unsigned long long* ssum;  // [A][V] scratch
-  int32_t* count;      // [T][V]
-  float* mean;         // [A][T][V]
-  long long* sumq;     // [A][T][V] or null
-  int T;
-  int kscale[MSF_MAX_ATTR];    // fixed-point exponent per attribute
-  float f1[MSF_MAX_ATTR];      // 2^-(k/2) and 2^-(k - k/2): exact fp32 powers of two
-  float f2[MSF_MAX_ATTR];
-  unsigned long long* outside; // [T]
+  int logR, nb;                 // bucket = voxel >> logR; nb buckets
+  int nblk;                     // sample blocks per timestep
+  int64_t chunk;                // samples per block
+  uint32_t nrec;                // records in all (samples inside the grid)
+  const float* pos;             // [T][3][P]
+  const float* attr;            // [T][A][P]
+  int32_t* key;                 // [T][P]
+  uint32_t* hist;               // [T][nb][nblk] samples per (bucket, block)
+  uint32_t* offs;               // exclusive prefix of hist (slot ranges)
+  uint32_t* cursor;             // running fill positions (global-histogram fallback)
+  uint32_t* rec_v;              // [P*T] voxel within bucket
+  float* rec_a;                 // [A][P*T] attribute values
+  unsigned* absmax;             // [A] float bits of max finite |v|
+  unsigned long long* outside;  // [T]
+  int32_t* count;               // [T][V]
+  float* mean;                  // [A][T][V]
+  long long* sumq;              // [A][T][V] or null
 };
 
 // Voxel of one sample: cells are [i, i+1); non-finite or outside positions give -1.
@@ -68,43 +67,27 @@ __device__ __forceinline__ int32_t voxel_of(float px, float py, float pz, int nx
   return ((int)fz * ny + (int)fy) * nx + (int)fx;
 }
 
-constexpr int kScatterPer = 4;
-
-template <int A>
-__global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ BinArgs b) {
-  const int64_t p0 = (int64_t)blockIdx.x * (256 * kScatterPer) + threadIdx.x;
-  const float* pt = b.pos + (int64_t)b.t * 3 * b.P;
-  const float* at = b.attr + (int64_t)b.t * A * b.P;
-  float px[kScatterPer], py[kScatterPer], pz[kScatterPer], av[kScatterPer][A > 0 ? A : 1];
-#pragma unroll
-  for (int j = 0; j < kScatterPer; ++j) {
-    const int64_t p = p0 + j * 256;
-    const bool in = p < b.P;
-    px[j] = in ? __ldcs(pt + p) : NAN;
-    py[j] = in ? __ldcs(pt + b.P + p) : NAN;
-    pz[j] = in ? __ldcs(pt + 2 * b.P + p) : NAN;
-#pragma unroll
-    for (int a = 0; a < A; ++a) av[j][a] = in ? __ldcs(at + (int64_t)a * b.P + p) : 0.f;
-  }
-  int out = 0;
-#pragma unroll
-  for (int j = 0; j < kScatterPer; ++j) {
-    const int64_t p = p0 + j * 256;
-    if (p >= b.P) continue;
-    const int32_t k = voxel_of(px[j], py[j], pz[j], b.nx, b.ny, b.nz);
-    __stcs(b.key + (int64_t)b.t * b.P + p, k);
-    if (k < 0) {
-      ++out;
-      continue;
+// k = 62 - e - b from the fp32 bits of max|v| (e: frexp exponent, 0 for zero) and the sample
+// count (b: smallest with 2^b >= n + 1).
+__host__ __device__ __forceinline__ int scale_exponent_bits(unsigned mbits, long long n) {
+  int e = 0;
+  if (mbits != 0u && mbits < 0x7F800000u) {
+    const int E = (int)(mbits >> 23);
+    if (E) {
+      e = E - 126;
+    } else {
+      int L = 0;
+      for (unsigned m = mbits; m; m >>= 1) ++L;
+      e = L - 149;
     }
-    atomicAdd(b.scnt + k, 1);
-#pragma unroll
-    for (int a = 0; a < A; ++a)
-      atomicAdd(b.ssum + (int64_t)a * b.V + k, (unsigned long long)quantise(av[j][a], b.kscale[a]));
   }
-  const int tot = __reduce_add_sync(0xFFFFFFFFu, out);
-  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(b.outside + b.t, (unsigned long long)tot);
+  int b = 0;
+  while (((long long)1 << b) < n + 1) ++b;
+  return 62 - e - b;
 }
+
+// 2^x as fp32 for -126 <= x <= 127, built from the bits.
+__device__ __forceinline__ float pow2f(int x) { return __uint_as_float((uint32_t)(x + 127) << 23); }
 
 // int64 -> fp32, round to nearest-even, with integer operations only (the hardware conversion
 // of 64-bit integers issues on the fp64 pipe, which is narrow on this part). |s| < 2^62.
@@ -134,143 +117,385 @@ __device__ __forceinline__ float voxel_mean(long long s, int c, float f1, float 
   return __fmul_rn(__fmul_rn(__fdiv_rn(i64_to_f32_rn(s), __int2float_rn(c)), f1), f2);
 }
 
-template <int A, bool KEEP>
-__global__ void __launch_bounds__(256) k_finalise(const __grid_constant__ BinArgs b) {
-  const int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  if (v0 >= b.V) return;
-  const int64_t tv = (int64_t)b.t * b.V;
-  const float qnan = __int_as_float(0x7fc00000);
-  if (v0 + 4 <= b.V && (b.V & 3) == 0) {
-    const int4 c = __ldcg(reinterpret_cast<const int4*>(b.scnt + v0));
-    __stcs(reinterpret_cast<int4*>(b.count + tv + v0), c);
-    __stcg(reinterpret_cast<int4*>(b.scnt + v0), make_int4(0, 0, 0, 0));
-    const int cc[4] = {c.x, c.y, c.z, c.w};
+// Exact fp32 quotient x / c (IEEE round to nearest): a power-of-two count is an exact scaling,
+// anything else takes the IEEE division. Both give the correctly rounded quotient.
+__device__ __forceinline__ float div_count(float x, int c) {
+  if ((c & (c - 1)) == 0) return __fmul_rn(x, pow2f(-(__ffs(c) - 1)));
+  return __fdiv_rn(x, __int2float_rn(c));
+}
+
+// ---------------------------------------------------------------------------------------------
+// pass 1: keys and the per-block bucket histograms
+// ---------------------------------------------------------------------------------------------
+// Block blk of timestep t owns samples [blk * chunk, (blk + 1) * chunk). Its histogram goes to
+// hist[(t * nb + bucket) * nblk + blk], so one exclusive scan yields every block's slot range.
+template <bool SMEM>
+__global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArgs b) {
+  __shared__ uint32_t s_hist[SMEM ? kHistSmem : 1];
+  const int t = blockIdx.y, blk = blockIdx.x;
+  if (SMEM) {
+    for (int i = threadIdx.x; i < b.nb; i += 256) s_hist[i] = 0u;
+    __syncthreads();
+  }
+  const int64_t pbeg = (int64_t)blk * b.chunk;
+  const int64_t pend = min(pbeg + b.chunk, b.P);
+  const float* pt = b.pos + (int64_t)t * 3 * b.P;
+  int out = 0;
+  for (int64_t q0 = pbeg + threadIdx.x; q0 < pend; q0 += 256 * kBinPer) {
+    float px[kBinPer], py[kBinPer], pz[kBinPer];
 #pragma unroll
-    for (int a = 0; a < A; ++a) {
-      unsigned long long* sp = b.ssum + (int64_t)a * b.V + v0;
-      const ulonglong2 s01 = __ldcg(reinterpret_cast<const ulonglong2*>(sp));
-      const ulonglong2 s23 = __ldcg(reinterpret_cast<const ulonglong2*>(sp + 2));
-      __stcg(reinterpret_cast<ulonglong2*>(sp), make_ulonglong2(0ull, 0ull));
-      __stcg(reinterpret_cast<ulonglong2*>(sp + 2), make_ulonglong2(0ull, 0ull));
-      const long long ss[4] = {(long long)s01.x, (long long)s01.y, (long long)s23.x,
-                               (long long)s23.y};
-      float mm[4];
+    for (int j = 0; j < kBinPer; ++j) {
+      const int64_t p = q0 + j * 256;
+      const bool in = p < pend;
+      px[j] = in ? __ldcs(pt + p) : NAN;
+      py[j] = in ? __ldcs(pt + b.P + p) : NAN;
+      pz[j] = in ? __ldcs(pt + 2 * b.P + p) : NAN;
+    }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) mm[j] = cc[j] ? voxel_mean(ss[j], cc[j], b.f1[a], b.f2[a]) : qnan;
-      const int64_t o = ((int64_t)a * b.T) * b.V + tv + v0;
-      __stcs(reinterpret_cast<float4*>(b.mean + o), make_float4(mm[0], mm[1], mm[2], mm[3]));
-      if (KEEP) {
-        __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2(ss[0], ss[1]));
-        __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2), make_longlong2(ss[2], ss[3]));
+    for (int j = 0; j < kBinPer; ++j) {
+      const int64_t p = q0 + j * 256;
+      if (p >= pend) continue;
+      const int32_t k = voxel_of(px[j], py[j], pz[j], b.nx, b.ny, b.nz);
+      __stcs(b.key + (int64_t)t * b.P + p, k);
+      if (k < 0) {
+        ++out;
+      } else if (SMEM) {
+        atomicAdd(s_hist + (k >> b.logR), 1u);
+      } else {
+        atomicAdd(b.hist + ((int64_t)t * b.nb + (k >> b.logR)) * b.nblk + blk, 1u);
       }
     }
-    return;
   }
-  for (int64_t v = v0; v < v0 + 4 && v < b.V; ++v) {
-    const int c = b.scnt[v];
-    b.count[tv + v] = c;
-    b.scnt[v] = 0;
+  const int tot = __reduce_add_sync(0xFFFFFFFFu, out);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(b.outside + t, (unsigned long long)tot);
+  if (SMEM) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < b.nb; i += 256)
+      b.hist[((int64_t)t * b.nb + i) * b.nblk + blk] = s_hist[i];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// pass 2: records in bucket order (and the attribute maxima)
+// ---------------------------------------------------------------------------------------------
+// The block sorts its samples by bucket in shared memory first (a counting sort against the
+// block's own histogram), then writes each bucket's run to its slot range, so that a warp's
+// stores land in a few contiguous runs rather than 32 scattered sectors.
+constexpr int kPlaceChunk = 4096;      // samples per block in the shared-memory sort path
+constexpr int kPlaceSmemMax = 200 * 1024;
+
+template <int A>
+__global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
+  extern __shared__ uint32_t s_place[];
+  uint32_t* s_gbase = s_place;                    // [nb] global slot of the block's run
+  uint32_t* s_lpos = s_place + b.nb;              // [nb] local start, then fill cursor
+  uint32_t* s_rv = s_place + 2 * b.nb;            // [chunk] voxel-in-bucket
+  uint32_t* s_rb = s_rv + kPlaceChunk;            // [chunk] bucket
+  float* s_ra = reinterpret_cast<float*>(s_rb + kPlaceChunk);  // [A][chunk]
+  __shared__ unsigned s_max[A > 0 ? A : 1];
+  __shared__ int s_warp[8];
+  __shared__ int s_n;
+  const int t = blockIdx.y, blk = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < b.nb; i += 256) {
+    s_gbase[i] = b.offs[((int64_t)t * b.nb + i) * b.nblk + blk];
+    s_lpos[i] = b.hist[((int64_t)t * b.nb + i) * b.nblk + blk];  // counts, scanned below
+  }
+  if (threadIdx.x < A) s_max[threadIdx.x] = 0u;
+  __syncthreads();
+  // exclusive scan of the block's bucket counts (one thread per chunk of buckets)
+  {
+    const int per = (b.nb + 255) / 256;
+    const int lo = threadIdx.x * per, hi = min(lo + per, b.nb);
+    int tot = 0;
+    for (int i = lo; i < hi; ++i) tot += (int)s_lpos[i];
+    int x = tot;
 #pragma unroll
-    for (int a = 0; a < A; ++a) {
-      const long long s = (long long)b.ssum[(int64_t)a * b.V + v];
-      b.ssum[(int64_t)a * b.V + v] = 0ull;
-      const int64_t o = ((int64_t)a * b.T) * b.V + tv + v;
-      b.mean[o] = c ? voxel_mean(s, c, b.f1[a], b.f2[a]) : qnan;
-      if (KEEP) b.sumq[o] = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    int run = x - tot;
+    for (int k = 0; k < w; ++k) run += s_warp[k];
+    if (threadIdx.x == 255) s_n = run + tot;
+    for (int i = lo; i < hi; ++i) {
+      const int c = (int)s_lpos[i];
+      s_lpos[i] = (uint32_t)run;
+      run += c;
     }
   }
+  __syncthreads();
+  const int64_t pbeg = (int64_t)blk * b.chunk;
+  const int64_t pend = min(pbeg + b.chunk, b.P);
+  unsigned lmax[A > 0 ? A : 1];
+#pragma unroll
+  for (int a = 0; a < A; ++a) lmax[a] = 0u;
+  for (int64_t q0 = pbeg + threadIdx.x; q0 < pend; q0 += 256 * kBinPer) {
+    int32_t kk[kBinPer];
+    float av[kBinPer][A > 0 ? A : 1];
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j) {
+      const int64_t p = q0 + j * 256;
+      const bool in = p < pend;
+      kk[j] = in ? __ldcs(b.key + (int64_t)t * b.P + p) : -1;
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        av[j][a] = in ? __ldcs(b.attr + ((int64_t)t * A + a) * b.P + p) : 0.f;
+        if (isfinite(av[j][a])) lmax[a] = max(lmax[a], __float_as_uint(fabsf(av[j][a])));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j) {
+      if (kk[j] < 0) continue;
+      const int bk = kk[j] >> b.logR;
+      const uint32_t pos = atomicAdd(s_lpos + bk, 1u);
+      s_rv[pos] = (uint32_t)kk[j] & ((1u << b.logR) - 1u);
+      s_rb[pos] = (uint32_t)bk;
+#pragma unroll
+      for (int a = 0; a < A; ++a) s_ra[a * kPlaceChunk + pos] = av[j][a];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const unsigned m = __reduce_max_sync(0xFFFFFFFFu, lmax[a]);
+    if (lane == 0 && m) atomicMax(s_max + a, m);
+  }
+  __syncthreads();
+  // s_lpos[bk] is now the end of bucket bk's local run; its start is end - count
+  const int64_t NR = (int64_t)b.P * b.T;
+  const int n = s_n;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const uint32_t bk = s_rb[i];
+    const uint32_t cnt = b.hist[((int64_t)t * b.nb + bk) * b.nblk + blk];
+    const uint32_t slot = s_gbase[bk] + (uint32_t)i - (s_lpos[bk] - cnt);
+    b.rec_v[slot] = s_rv[i];
+#pragma unroll
+    for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * NR + slot] = s_ra[a * kPlaceChunk + i];
+  }
+  if (threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
+}
+
+// Fallback for many buckets (global histogram): one slot atomic per sample.
+template <int A>
+__global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant__ BinArgs b) {
+  __shared__ unsigned s_max[A > 0 ? A : 1];
+  const int t = blockIdx.y, blk = blockIdx.x;
+  if (threadIdx.x < A) s_max[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t pbeg = (int64_t)blk * b.chunk;
+  const int64_t pend = min(pbeg + b.chunk, b.P);
+  const int64_t NR = (int64_t)b.P * b.T;
+  unsigned lmax[A > 0 ? A : 1];
+#pragma unroll
+  for (int a = 0; a < A; ++a) lmax[a] = 0u;
+  for (int64_t p = pbeg + threadIdx.x; p < pend; p += 256) {
+    const int32_t k = __ldcs(b.key + (int64_t)t * b.P + p);
+    float av[A > 0 ? A : 1];
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      av[a] = __ldcs(b.attr + ((int64_t)t * A + a) * b.P + p);
+      if (isfinite(av[a])) lmax[a] = max(lmax[a], __float_as_uint(fabsf(av[a])));
+    }
+    if (k < 0) continue;
+    const int bk = k >> b.logR;
+    const uint32_t slot = atomicAdd(b.cursor + ((int64_t)t * b.nb + bk) * b.nblk + blk, 1u);
+    b.rec_v[slot] = (uint32_t)k & ((1u << b.logR) - 1u);
+#pragma unroll
+    for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * NR + slot] = av[a];
+  }
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const unsigned m = __reduce_max_sync(0xFFFFFFFFu, lmax[a]);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(s_max + a, m);
+  }
+  __syncthreads();
+  if (threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// pass 3: per (bucket, timestep) counts, sums, means
+// ---------------------------------------------------------------------------------------------
+template <int A, bool KEEP>
+__global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinArgs b) {
+  extern __shared__ unsigned long long s_dyn64[];
+  const int R = 1 << b.logR;
+  unsigned long long* s_sum = s_dyn64;                                    // [A][R]
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_dyn64 + (size_t)A * R);  // [R]
+  uint32_t* s_list = s_cnt + R;                                           // [R]
+  __shared__ int s_k[A > 0 ? A : 1];
+  __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
+  __shared__ int s_nlist;
+  const int bucket = blockIdx.x, t = blockIdx.y;
+  {
+    uint4* z = reinterpret_cast<uint4*>(s_dyn64);
+    const int n16 = (int)(((size_t)A * R * 8 + (size_t)R * 4) / 16);
+    for (int i = threadIdx.x; i < n16; i += 256) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  if (threadIdx.x < A) {
+    const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.P * b.T);
+    s_k[threadIdx.x] = k;
+    s_f1[threadIdx.x] = pow2f(-(k / 2));
+    s_f2[threadIdx.x] = pow2f(-(k - k / 2));
+  }
+  if (threadIdx.x == 0) s_nlist = 0;
+  __syncthreads();
+  const int64_t row = (int64_t)t * b.nb + bucket;
+  uint32_t r0 = 0, r1 = 0;  // no records at all: the offsets were never formed
+  if (b.nrec) {
+    r0 = b.offs[row * b.nblk];
+    r1 = (row + 1 < (int64_t)b.T * b.nb) ? b.offs[(row + 1) * b.nblk] : b.nrec;
+  }
+  const int64_t NR = (int64_t)b.P * b.T;
+  for (uint32_t r = r0 + threadIdx.x; r < r1; r += 256) {
+    const uint32_t v = __ldcs(b.rec_v + r);
+    atomicAdd(s_cnt + v, 1u);
+#pragma unroll
+    for (int a = 0; a < A; ++a)
+      atomicAdd(s_sum + (size_t)a * R + v,
+                (unsigned long long)quantise(__ldcs(b.rec_a + (int64_t)a * NR + r), s_k[a]));
+  }
+  __syncthreads();
+  // counts for all voxels (4 per thread); empty voxels get NaN means; the others are listed
+  const int64_t vbase = (int64_t)bucket << b.logR;
+  const int nv = (int)min((int64_t)R, b.V - vbase);
+  const float qnan = __int_as_float(0x7fc00000);
+  const bool vec = (b.V & 3) == 0;
+  const int lane = threadIdx.x & 31;
+  for (int i0 = 0; i0 < nv; i0 += 1024) {
+    const int i = i0 + 4 * threadIdx.x;
+    const bool in = i < nv;
+    uint4 c4 = make_uint4(0, 0, 0, 0);
+    if (in) c4 = *reinterpret_cast<const uint4*>(s_cnt + i);
+    const uint32_t c[4] = {c4.x, c4.y, c4.z, c4.w};
+    unsigned nz = 0;
+    if (in) {
+      const int64_t v = vbase + i;
+      if (vec) {
+        __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v), c4);
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
+          float4 m = make_float4(qnan, qnan, qnan, qnan);  // non-empty lanes are overwritten
+          __stcs(reinterpret_cast<float4*>(b.mean + o), m);
+          if (KEEP) {
+            __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2(0, 0));
+            __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2), make_longlong2(0, 0));
+          }
+        }
+      } else {
+        for (int e = 0; e < 4 && i + e < nv; ++e) {
+          __stcs(b.count + (int64_t)t * b.V + v + e, (int)c[e]);
+          for (int a = 0; a < A; ++a) {
+            const int64_t o = ((int64_t)a * b.T + t) * b.V + v + e;
+            __stcs(b.mean + o, qnan);
+            if (KEEP) __stcs(b.sumq + o, 0ll);
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) nz += (c[e] != 0u && i + e < nv);
+    }
+    // list the non-empty voxels (warp-aggregated)
+    int x = (int)nz;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    int base = 0;
+    if (lane == 31 && x) base = atomicAdd(&s_nlist, x);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31) + x - (int)nz;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (in && c[e] != 0u && i + e < nv) s_list[base++] = (uint32_t)(i + e);
+  }
+  __syncthreads();  // the NaN stores above precede the mean stores below in program order
+  const int nl = s_nlist;
+  for (int j = threadIdx.x; j < nl; j += 256) {
+    const int i = (int)s_list[j];
+    const int c = (int)s_cnt[i];
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const long long sq = (long long)s_sum[(size_t)a * R + i];
+      const int64_t o = ((int64_t)a * b.T + t) * b.V + vbase + i;
+      __stcs(b.mean + o, __fmul_rn(__fmul_rn(div_count(i64_to_f32_rn(sq), c), s_f1[a]), s_f2[a]));
+      if (KEEP) __stcs(b.sumq + o, sq);
+    }
+  }
+}
+
+// Bucket width per attribute count: R counts, A*R sums and an R-entry list within 48 KB of
+// dynamic shared memory (four CTAs per SM), at most 4096 voxels.
+static int bucket_log2(int A) {
+  int l = 12;
+  while (l > 6 && ((size_t)1 << l) * (8 + 8 * (size_t)A) > 48 * 1024) --l;
+  return l;
+}
+
+static size_t reduce_smem(int A, int logR) { return ((size_t)1 << logR) * (8 + 8 * (size_t)A); }
+
+static size_t place_smem(int A, int nb) {
+  return sizeof(uint32_t) * (2 * (size_t)nb + 2 * (size_t)kPlaceChunk) +
+         sizeof(float) * (size_t)A * kPlaceChunk;
 }
 
 template <int A>
-static void launch_bin_step(msf_ctx* ctx, const BinArgs& b, bool keep) {
+static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, bool smem) {
   cudaStream_t s = ctx->stream;
-  if (b.P > 0) {
-    ScopedKernel k(ctx, "k_scatter");
-    k_scatter<A><<<(unsigned)((b.P + 256 * kScatterPer - 1) / (256 * kScatterPer)), 256, 0, s>>>(b);
-  }
-  {
-    ScopedKernel k(ctx, "k_finalise");
-    const unsigned nb = (unsigned)((b.V + 1023) / 1024);
-    if (keep) k_finalise<A, true><<<nb, 256, 0, s>>>(b);
-    else k_finalise<A, false><<<nb, 256, 0, s>>>(b);
+  const dim3 gs((unsigned)b.nblk, (unsigned)b.T);
+  if (phase == 0) {
+    ScopedKernel k(ctx, "k_bin_keys");
+    if (smem) k_bin_keys<true><<<gs, 256, 0, s>>>(b);
+    else k_bin_keys<false><<<gs, 256, 0, s>>>(b);
+  } else if (phase == 1) {
+    ScopedKernel k(ctx, "k_bin_place");
+    if (smem) {  // caller guarantees place_smem(A, nb) <= kPlaceSmemMax
+      static bool set = false;
+      if (!set) {
+        cudaFuncSetAttribute(k_bin_place_sorted<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kPlaceSmemMax);
+        set = true;
+      }
+      k_bin_place_sorted<A><<<gs, 256, place_smem(A, b.nb), s>>>(b);
+    } else {
+      k_bin_place_atomic<A><<<gs, 256, 0, s>>>(b);
+    }
+  } else {
+    ScopedKernel k(ctx, "k_bin_reduce");
+    const size_t sm = reduce_smem(A, b.logR);
+    const dim3 gr((unsigned)b.nb, (unsigned)b.T);
+    if (keep) {
+      static bool set = false;
+      if (!set) {
+        cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 92 * 1024);
+        set = true;
+      }
+      k_bin_reduce<A, true><<<gr, 256, sm, s>>>(b);
+    } else {
+      static bool set = false;
+      if (!set) {
+        cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 92 * 1024);
+        set = true;
+      }
+      k_bin_reduce<A, false><<<gr, 256, sm, s>>>(b);
+    }
   }
 }
 
-static void launch_bin_step_a(msf_ctx* ctx, const BinArgs& b, bool keep) {
+static void launch_bin_a(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, bool smem) {
   switch (b.A) {
-    case 0: launch_bin_step<0>(ctx, b, keep); break;
-    case 1: launch_bin_step<1>(ctx, b, keep); break;
-    case 2: launch_bin_step<2>(ctx, b, keep); break;
-    case 3: launch_bin_step<3>(ctx, b, keep); break;
-    case 4: launch_bin_step<4>(ctx, b, keep); break;
-    case 5: launch_bin_step<5>(ctx, b, keep); break;
-    case 6: launch_bin_step<6>(ctx, b, keep); break;
-    case 7: launch_bin_step<7>(ctx, b, keep); break;
-    default: launch_bin_step<8>(ctx, b, keep); break;
+    case 0: launch_bin<0>(ctx, b, keep, phase, smem); break;
+    case 1: launch_bin<1>(ctx, b, keep, phase, smem); break;
+    case 2: launch_bin<2>(ctx, b, keep, phase, smem); break;
+    case 3: launch_bin<3>(ctx, b, keep, phase, smem); break;
+    case 4: launch_bin<4>(ctx, b, keep, phase, smem); break;
+    case 5: launch_bin<5>(ctx, b, keep, phase, smem); break;
+    case 6: launch_bin<6>(ctx, b, keep, phase, smem); break;
+    case 7: launch_bin<7>(ctx, b, keep, phase, smem); break;
+    default: launch_bin<8>(ctx, b, keep, phase, smem); break;
   }
-}
-
-// Persisting L2 window over the scratch slab (the larger of the two buffers gets the window;
-// the smaller one is small enough to stay by itself).
-struct L2Window {
-  msf_ctx* ctx;
-  bool active = false;
-  size_t old_limit = 0;
-  L2Window(msf_ctx* c, void* big, size_t big_bytes, void* small, size_t small_bytes) : ctx(c) {
-    (void)small;
-    (void)small_bytes;
-    if (!ctx->stream) return;  // the legacy default stream takes no attributes
-    int max_persist = 0, max_window = 0;
-    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, ctx->device);
-    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device);
-    if (max_persist <= 0 || max_window <= 0) return;
-    if (cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
-      cudaGetLastError();
-      return;
-    }
-    const size_t want = std::min<size_t>(big_bytes, (size_t)max_persist);
-    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
-      cudaGetLastError();
-      return;
-    }
-    cudaStreamAttrValue v{};
-    v.accessPolicyWindow.base_ptr = big;
-    v.accessPolicyWindow.num_bytes = std::min<size_t>(big_bytes, (size_t)max_window);
-    v.accessPolicyWindow.hitRatio =
-        (float)std::min(1.0, (double)want / (double)v.accessPolicyWindow.num_bytes);
-    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-    if (cudaStreamSetAttribute(ctx->stream, cudaStreamAttributeAccessPolicyWindow, &v) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
-      return;
-    }
-    active = true;
-  }
-  void restore() {
-    if (!active) return;
-    cudaStreamAttrValue v{};
-    v.accessPolicyWindow.num_bytes = 0;
-    v.accessPolicyWindow.hitRatio = 0.f;
-    v.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
-    v.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
-    cudaStreamSetAttribute(ctx->stream, cudaStreamAttributeAccessPolicyWindow, &v);
-    cudaCtxResetPersistingL2Cache();
-    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
-    cudaGetLastError();
-    active = false;
-  }
-  ~L2Window() { restore(); }
-};
-
-// Host side of the fixed-point exponent: k = 62 - e - b.
-static int scale_exponent(float max_abs, int64_t n_samples) {
-  int e = 0;
-  if (max_abs > 0.f && isfinite(max_abs)) frexp((double)max_abs, &e);
-  int bbits = 0;
-  while (((int64_t)1 << bbits) < n_samples + 1) ++bbits;
-  return 62 - e - bbits;
 }
 
 int bin_run(msf_ctx* ctx, unsigned flags) {
@@ -278,73 +503,85 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   const bool keep = flags & MSF_BIN_KEEP_SUMQ;
   cudaStream_t s = ctx->stream;
   BinScratch& S = ctx->bin;
-  MSF_TRY(S.absmax.ensure(sizeof(unsigned) * MSF_MAX_ATTR));
-  MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.T));
-  MSF_TRY(S.cnt.ensure(sizeof(int32_t) * d.V));
-  MSF_TRY(S.sum.ensure(sizeof(unsigned long long) * d.V * (d.A > 0 ? d.A : 1)));
-  MSF_TRY(d.key.ensure(sizeof(int32_t) * d.T * (d.P > 0 ? d.P : 1)));
-  MSF_TRY(d.count.ensure(sizeof(int32_t) * d.T * d.V));
-  MSF_TRY(d.mean.ensure(sizeof(float) * d.T * d.V * (d.A > 0 ? d.A : 1)));
-  if (keep) MSF_TRY(d.sumq.ensure(sizeof(int64_t) * d.T * d.V * (d.A > 0 ? d.A : 1)));
-  MSF_CUDA_TRY(cudaMemsetAsync(S.absmax.p, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
-  MSF_CUDA_TRY(cudaMemsetAsync(S.outside.p, 0, sizeof(unsigned long long) * d.T, s));
-  MSF_CUDA_TRY(cudaMemsetAsync(S.cnt.p, 0, sizeof(int32_t) * d.V, s));
-  MSF_CUDA_TRY(cudaMemsetAsync(S.sum.p, 0, sizeof(unsigned long long) * d.V * (d.A > 0 ? d.A : 1), s));
-  unsigned hmax[MSF_MAX_ATTR] = {};
-  if (d.A > 0 && d.P > 0) {
-    {
-      ScopedKernel k(ctx, "k_absmax");
-      const int gy = (int)std::min<int64_t>((d.P + 1023) / 1024, 64);
-      dim3 grid((unsigned)(d.T * d.A), gy);
-      k_absmax<<<grid, 256, 0, s>>>(d.attr.as<float>(), d.P, d.A, S.absmax.as<unsigned>());
-    }
-    MSF_CUDA_TRY(cudaGetLastError());
-    MSF_CUDA_TRY(cudaMemcpyAsync(hmax, S.absmax.p, sizeof(hmax), cudaMemcpyDeviceToHost, s));
-    MSF_CUDA_TRY(cudaStreamSynchronize(s));
-  }
   BinArgs b{};
   b.nx = d.nx;
   b.ny = d.ny;
   b.nz = d.nz;
   b.A = d.A;
+  b.T = d.T;
   b.V = d.V;
   b.P = d.P;
-  b.T = d.T;
+  b.logR = bucket_log2(d.A);
+  b.nb = (int)((d.V + ((int64_t)1 << b.logR) - 1) >> b.logR);
+  // samples per block: the shared-memory sort handles kPlaceChunk; with too many buckets for
+  // shared memory the blocks grow so that the per-block histograms stay small
+  const bool smem = b.nb <= kHistSmem && place_smem(d.A, b.nb) <= (size_t)kPlaceSmemMax;
+  b.chunk = kPlaceChunk;
+  if (!smem)
+    while ((int64_t)b.nb * ((d.P + b.chunk - 1) / b.chunk) > (1 << 22) && b.chunk < ((int64_t)1 << 30))
+      b.chunk <<= 1;
+  b.nblk = (int)std::max<int64_t>(1, (d.P + b.chunk - 1) / b.chunk);
+  const int64_t TB = (int64_t)d.T * b.nb * b.nblk;
+  const int64_t NR = d.P * (int64_t)d.T;
+  const int Af = d.A > 0 ? d.A : 1;
+  if (NR >= ((int64_t)1 << 32) || TB >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
+  MSF_TRY(S.hist.ensure(sizeof(uint32_t) * TB));
+  MSF_TRY(S.offs.ensure(sizeof(uint32_t) * TB));
+  MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * TB));
+  MSF_TRY(S.rec_v.ensure(sizeof(uint32_t) * (NR > 0 ? NR : 1)));
+  MSF_TRY(S.rec_a.ensure(sizeof(float) * (NR > 0 ? NR : 1) * Af));
+  MSF_TRY(S.absmax.ensure(sizeof(unsigned) * MSF_MAX_ATTR));
+  MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.T));
+  MSF_TRY(S.total.ensure(sizeof(uint32_t) * 2));
+  MSF_TRY(d.key.ensure(sizeof(int32_t) * d.T * (d.P > 0 ? d.P : 1)));
+  MSF_TRY(d.count.ensure(sizeof(int32_t) * d.T * d.V));
+  MSF_TRY(d.mean.ensure(sizeof(float) * d.T * d.V * Af));
+  if (keep) MSF_TRY(d.sumq.ensure(sizeof(int64_t) * d.T * d.V * Af));
   b.pos = d.pos.as<float>();
   b.attr = d.attr.as<float>();
   b.key = d.key.as<int32_t>();
-  b.scnt = S.cnt.as<int32_t>();
-  b.ssum = S.sum.as<unsigned long long>();
+  b.hist = S.hist.as<uint32_t>();
+  b.offs = S.offs.as<uint32_t>();
+  b.cursor = S.cursor.as<uint32_t>();
+  b.rec_v = S.rec_v.as<uint32_t>();
+  b.rec_a = S.rec_a.as<float>();
+  b.absmax = S.absmax.as<unsigned>();
+  b.outside = S.outside.as<unsigned long long>();
   b.count = d.count.as<int32_t>();
   b.mean = d.mean.as<float>();
   b.sumq = keep ? d.sumq.as<long long>() : nullptr;
-  b.outside = S.outside.as<unsigned long long>();
+  MSF_CUDA_TRY(cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * TB, s));
+  MSF_CUDA_TRY(cudaMemsetAsync(b.absmax, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
+  MSF_CUDA_TRY(cudaMemsetAsync(b.outside, 0, sizeof(unsigned long long) * d.T, s));
+  b.nrec = 0;
+  if (d.P > 0) {
+    launch_bin_a(ctx, b, keep, 0, smem);
+    MSF_CUDA_TRY(cudaGetLastError());
+    MSF_TRY(scan_exclusive_u32(ctx, b.hist, b.offs, TB, S.scan_tmp, S.total.as<uint32_t>()));
+    if (!smem)
+      MSF_CUDA_TRY(cudaMemcpyAsync(b.cursor, b.offs, sizeof(uint32_t) * TB,
+                                   cudaMemcpyDeviceToDevice, s));
+    launch_bin_a(ctx, b, keep, 1, smem);
+    MSF_CUDA_TRY(cudaGetLastError());
+    // the last bucket's end: the total number of records (read back once, small)
+    MSF_CUDA_TRY(cudaMemcpyAsync(&b.nrec, S.total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    MSF_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  launch_bin_a(ctx, b, keep, 2, smem);
+  MSF_CUDA_TRY(cudaGetLastError());
+  std::vector<unsigned long long> out(d.T);
+  unsigned hmax[MSF_MAX_ATTR] = {};
+  MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.T,
+                               cudaMemcpyDeviceToHost, s));
+  MSF_CUDA_TRY(cudaMemcpyAsync(hmax, S.absmax.p, sizeof(hmax), cudaMemcpyDeviceToHost, s));
+  MSF_CUDA_TRY(cudaStreamSynchronize(s));
+  ctx->timer.flush();
   for (int a = 0; a < d.A; ++a) {
     float m;
     memcpy(&m, &hmax[a], sizeof(float));
     d.max_abs[a] = m;
-    d.kscale[a] = scale_exponent(m, d.P * (int64_t)d.T);
-    const int k = d.kscale[a];
-    b.kscale[a] = k;
-    b.f1[a] = ldexpf(1.0f, -(k / 2));
-    b.f2[a] = ldexpf(1.0f, -(k - k / 2));
+    d.kscale[a] = scale_exponent_bits(hmax[a], d.P * (int64_t)d.T);
   }
-  // Keep the scratch slab resident in L2 while the atomics of one timestep land on it: a
-  // persisting access window on the stream for the duration of binning (context-scoped; the
-  // previous limit and stream attribute are restored below).
-  L2Window win(ctx, S.sum.p, sizeof(unsigned long long) * d.V * (d.A > 0 ? d.A : 1),
-                S.cnt.p, sizeof(int32_t) * d.V);
-  for (int t = 0; t < d.T; ++t) {
-    b.t = t;
-    launch_bin_step_a(ctx, b, keep);
-  }
-  MSF_CUDA_TRY(cudaGetLastError());
-  std::vector<unsigned long long> out(d.T);
-  MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.T,
-                               cudaMemcpyDeviceToHost, s));
-  MSF_CUDA_TRY(cudaStreamSynchronize(s));
-  win.restore();
-  ctx->timer.flush();
   int64_t o = 0;
   for (auto v : out) o += (int64_t)v;
   d.out_of_domain = o;

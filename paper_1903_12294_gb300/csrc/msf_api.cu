@@ -270,7 +270,9 @@ void msf_destroy(msf_ctx* c) {
   for (DevBuf* b : {&c->feat.rootbits, &c->feat.wordrank, &c->feat.blocksums, &c->feat.acc,
                     &c->feat.out})
     b->release();
-  for (DevBuf* b : {&c->bin.cnt, &c->bin.sum, &c->bin.absmax, &c->bin.outside}) b->release();
+  for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.rec_v, &c->bin.rec_a,
+                    &c->bin.absmax, &c->bin.outside, &c->bin.scan_tmp, &c->bin.total})
+    b->release();
   for (DevBuf* b : {&c->last.sample_sid, &c->last.sample_comp, &c->last.cfid}) b->release();
   c->host_staging.release();
   c->timer.release();

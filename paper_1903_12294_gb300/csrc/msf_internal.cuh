@@ -131,7 +131,7 @@ struct SegState {
 };
 
 struct BinScratch {
-  DevBuf cnt, sum, absmax, outside;
+  DevBuf hist, offs, cursor, rec_v, rec_a, absmax, outside, scan_tmp, total;
 };
 
 // Named kernel timing (optional; on the context stream).
