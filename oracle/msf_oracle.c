@@ -89,7 +89,7 @@ static int64_t orc_quantise(float a, int k) {
  * fp32 operations, each rounded to nearest-even: the sum converted to fp32, divided by the
  * count, then scaled by 2^-k in two exact power-of-two factors (each factor a normal fp32
  * number for every k this exponent rule produces). The paper keeps running averages in float
- * (§3.5); fp32 here also keeps the per-voxel work off the GPU's fp64 units. */
+ * (§3.4); fp32 here also keeps the per-voxel work off the GPU's fp64 units. */
 static float orc_mean(int64_t sumq, int32_t count, int k) {
   if (count == 0) return NAN;
   int k1 = k / 2, k2 = k - k / 2;

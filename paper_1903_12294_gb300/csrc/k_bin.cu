@@ -4,7 +4,7 @@
 // Determinism: attributes are summed as int64 fixed point, q = round_half_even(v * 2^k) with
 // k = 62 - e - b (max|v| < 2^e, 2^b >= P*T + 1), so sums are exact and independent of order;
 // the fp32 mean is a fixed sequence of IEEE fp32 operations on that sum. The paper's own GPU
-// scheme keeps float running averages with atomics (§3.5), whose result depends on the order
+// scheme keeps float running averages with atomics (§3.4), whose result depends on the order
 // of arrival. No per-sample or per-voxel work touches the fp64 units.
 //
 // Schedule: a counting sort of the samples by voxel range ("bucket" of R consecutive voxels),
