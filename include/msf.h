@@ -200,6 +200,32 @@ int msf_extract_features(msf_ctx* ctx, const msf_criteria* crit, const int32_t* 
                          int labels_kind, msf_feature* out, int out_kind, int64_t cap,
                          int64_t* n_out);
 
+/* ---- allocation-free labelling ----------------------------------------------------------- */
+
+/* Field-only labelling that allocates nothing, for callers that cannot allocate device memory
+ * when they need a segmentation: code running while its stream is captured into a CUDA graph,
+ * where allocation calls are not allowed, and services that reserve all device memory up front
+ * in their own pool and forbid cudaMalloc/cudaFree (which can synchronise the device or fail
+ * under memory pressure). The paper has no counterpart; this is a service of this library.
+ *
+ * Computes what msf_segment computes for a dataset without points: labels of the window given
+ * by `field` ([tw][nz][ny][nx] fp32, device) under one optional field predicate (`pred`, host,
+ * NULL = every voxel-timestep is a member; src must be MSF_SRC_FIELD) with MSF_EDGE_SPATIAL and/or
+ * MSF_EDGE_TEMPORAL edges. `labels` ([tw][nz][ny][nx] int32, device) receives the canonical
+ * labels; `n_features` (host, may be NULL) the number of features. `stream` is a cudaStream_t
+ * (NULL = legacy default stream); the call synchronises it before returning.
+ * No context is needed. Scratch is one 16 MiB array in the library's device image (present on
+ * every device that loads the library until the process exits): windows that need more are
+ * rejected with MSF_ERR_TOO_LARGE (about 4 million voxel-timesteps when nx is a multiple of 32).
+ * The first call on each device looks up the array's device address; make that first call
+ * before any stream capture. Every call shares the array, so calls that run concurrently on the
+ * GPU (for example on different streams) race and must be serialised by the caller.
+ * Errors: INVALID_ARG (sizes, NULL buffers, predicate not on the field, TRAJ or unknown edge
+ * bits), TOO_LARGE, CUDA. tw == 0 is valid and writes nothing. */
+int msf_segment_field_noalloc(int nx, int ny, int nz, int tw, const float* field,
+                              const msf_pred* pred, uint32_t edges, int32_t* labels,
+                              int64_t* n_features, void* stream);
+
 /* ---- tuning, profiling ---------------------------------------------------------------- */
 
 /* Tile shape of the labelling kernels: 32 x by x bz x bt voxel-timesteps with by*bz*bt = 256

@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "msf_internal.cuh"
 
 namespace msf {
@@ -954,6 +956,129 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
     k_feat_samples<<<ctx->sm_count * 8, 256, 0, s>>>(a, acc, cfid, d.attr.as<float>());
   }
   MSF_CUDA_TRY(cudaGetLastError());
+  return MSF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// field-only labelling over fixed scratch (the allocation-free entry point)
+// ---------------------------------------------------------------------------------------------
+static int ilog2_i(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+int geometry_for_dims(int nx, int ny, int nz, int tw, uint32_t edges, Geometry* g) {
+  *g = Geometry{};
+  g->nx = nx;
+  g->ny = ny;
+  g->nz = nz;
+  g->V = nx * ny * nz;
+  g->T = tw;
+  g->t0 = 0;
+  g->tw = tw;
+  g->nxs = (nx + 31) / 32;
+  int by, bz, bt;  // the automatic tile shape of msf_segment
+  if (nz == 1) {
+    bz = 1;
+    bt = std::min(16, 1 << ilog2_i(std::max(1, tw)));
+    by = kSegPerTile / bt;
+  } else {
+    bt = std::min(4, 1 << ilog2_i(std::max(1, tw)));
+    const int rest = kSegPerTile / bt;
+    bz = rest >= 256 ? 16 : 8;
+    by = rest / bz;
+  }
+  g->lby = ilog2_i(by);
+  g->lbz = ilog2_i(bz);
+  g->lbt = ilog2_i(bt);
+  g->tly = (ny + by - 1) / by;
+  g->tlz = (nz + bz - 1) / bz;
+  g->tlt = (tw + bt - 1) / bt;
+  const int64_t nt = (int64_t)g->nxs * g->tly * g->tlz * g->tlt;
+  if (nt >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
+  g->ntiles = (int)nt;
+  g->cmax = (edges & MSF_EDGE_SPATIAL) ? 16 * ((by + 1) / 2) * ((bz + 1) / 2) * bt : 32 * by * bz * bt;
+  g->nseg = (int64_t)tw * nz * ny * g->nxs;
+  g->fnx = FastDiv((uint32_t)nx);
+  g->fny = FastDiv((uint32_t)ny);
+  g->fnz = FastDiv((uint32_t)nz);
+  g->fnxs = FastDiv((uint32_t)g->nxs);
+  return MSF_OK;
+}
+
+static size_t up256(size_t n) { return (n + 255) & ~size_t(255); }
+
+size_t fixed_scratch_bytes(const Geometry& g, bool spatial) {
+  const size_t maxr = (size_t)kSegPerTile * (spatial ? 16 : 32);
+  return 2 * up256(sizeof(uint32_t) * (size_t)g.nseg) +
+         up256(sizeof(uint32_t) * (size_t)g.ntiles * maxr) +
+         2 * up256(sizeof(uint32_t) * (size_t)g.ntiles * (size_t)g.cmax) +
+         up256(sizeof(int2) * (size_t)g.ntiles) + up256(sizeof(unsigned long long) * 8);
+}
+
+void fixed_scratch_carve(void* base, const Geometry& g, bool spatial, FixedScratch* o) {
+  const size_t maxr = (size_t)kSegPerTile * (spatial ? 16 : 32);
+  char* p = static_cast<char*>(base);
+  auto take = [&](size_t n) {
+    char* q = p;
+    p += up256(n);
+    return q;
+  };
+  o->segmask = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)g.nseg));
+  o->segrun = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)g.nseg));
+  o->runcomp = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)g.ntiles * maxr));
+  o->cparent = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)g.ntiles * g.cmax));
+  o->cminli = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
+  o->tileinfo = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)g.ntiles));
+  o->counters = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * 8));
+}
+
+int segment_field_fixed(const Geometry& g, int npred, const DevPred& pred, uint32_t edges,
+                        const FixedScratch& S, int32_t* labels, cudaStream_t s,
+                        int64_t* n_features) {
+  const bool spatial = edges & MSF_EDGE_SPATIAL;
+  SegArgs a{};
+  a.g = g;
+  a.pred[0] = pred;
+  a.npred = npred;
+  a.edges = edges;
+  a.key = nullptr;
+  a.P = 0;
+  a.maxr = kSegPerTile * (spatial ? 16 : 32);
+  a.segmask = S.segmask;
+  a.segrun = S.segrun;
+  a.runcomp = S.runcomp;
+  a.cparent = S.cparent;
+  a.cminli = S.cminli;
+  a.tileinfo = S.tileinfo;
+  a.counters = S.counters;
+  a.labels = labels;
+  // The scratch keeps the previous call's contents: only the counters must start at zero
+  // (every other entry the kernels read is written earlier in this same call).
+  MSF_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * 8, s));
+  launch_tile_any(a, spatial, g.ntiles, s);
+  MSF_CUDA_TRY(cudaGetLastError());
+  const unsigned nb = (unsigned)((g.nseg + 255) / 256);
+  if (edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) {
+    if (spatial) k_hook<true><<<nb, 256, 0, s>>>(a);
+    else k_hook<false><<<nb, 256, 0, s>>>(a);
+  }
+  k_flatten<<<g.ntiles, 256, 0, s>>>(a);
+  const bool vec = (g.nx & 3) == 0 && ((uintptr_t)labels & 15) == 0;
+  if (spatial) {
+    if (vec) k_final<true, true><<<g.ntiles, 256, 0, s>>>(a);
+    else k_final<true, false><<<g.ntiles, 256, 0, s>>>(a);
+  } else {
+    if (vec) k_final<false, true><<<g.ntiles, 256, 0, s>>>(a);
+    else k_final<false, false><<<g.ntiles, 256, 0, s>>>(a);
+  }
+  MSF_CUDA_TRY(cudaGetLastError());
+  unsigned long long h[2];
+  MSF_CUDA_TRY(cudaMemcpyAsync(h, a.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MSF_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h[1]) return MSF_ERR_INTERNAL;
+  if (n_features) *n_features = (int64_t)h[0];
   return MSF_OK;
 }
 

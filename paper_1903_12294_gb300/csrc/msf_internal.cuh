@@ -412,6 +412,25 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels_dev, int
 int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels_dev,
                  const void* labels_user, msf_feature* out, int out_kind, int64_t cap,
                  int64_t* n_out);
+// Field-only labelling over caller-provided scratch (k_segment.cu), for the allocation-free
+// entry point: the window is the caller's field of tw steps, one optional field predicate,
+// spatial/temporal edges only. No allocation, no timing.
+struct FixedScratch {
+  uint32_t* segmask;
+  uint32_t* segrun;
+  uint32_t* runcomp;
+  uint32_t* cparent;
+  int32_t* cminli;
+  int2* tileinfo;
+  unsigned long long* counters;  // [8]
+};
+int geometry_for_dims(int nx, int ny, int nz, int tw, uint32_t edges, Geometry* g);
+size_t fixed_scratch_bytes(const Geometry& g, bool spatial);
+void fixed_scratch_carve(void* base, const Geometry& g, bool spatial, FixedScratch* out);
+int segment_field_fixed(const Geometry& g, int npred, const DevPred& pred, uint32_t edges,
+                        const FixedScratch& S, int32_t* labels, cudaStream_t s,
+                        int64_t* n_features);
+
 // fast feature path (k_segment.cu): marks the feature labels of the retained segmentation in
 // rootbits and counts them; then, after the ranks exist, reduces voxel and point statistics.
 int seg_mark_roots(msf_ctx* ctx, uint32_t* rootbits, unsigned long long* counter);

@@ -30,7 +30,8 @@ MSF_MAX_PRED, MSF_MAX_ATTR = 4, 8
 # every entry point the header declares (checked by the CPU test-suite)
 EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_bin_particles", "msf_get_bins", "msf_segment", "msf_extract_features",
-           "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string")
+           "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
+           "msf_segment_field_noalloc")
 
 
 class msf_pred(ctypes.Structure):
@@ -98,6 +99,8 @@ def load_library(path: str = LIB_PATH):
         lib.msf_set_tile.argtypes = [P, i32, i32, i32]
         lib.msf_set_profiling.argtypes = [P, i32]
         lib.msf_kernel_times.argtypes = [P, P, P, P, i32, i32]
+        lib.msf_segment_field_noalloc.argtypes = [i32, i32, i32, i32, P, ctypes.POINTER(msf_pred),
+                                                  u32, P, ctypes.POINTER(ctypes.c_int64), P]
         lib.msf_status_string.argtypes = [i32]
         lib.msf_status_string.restype = ctypes.c_char_p
         for n in EXPORTS:
@@ -225,6 +228,27 @@ def msf_extract_features(ctx, crit: msf_criteria, labels, cap=None):
     _check(lib.msf_extract_features(ctx, ctypes.byref(crit), lp, lk, out.ctypes.data, MSF_HOST,
                                     cap, ctypes.byref(n)), "msf_extract_features")
     return out[:int(n.value)]
+
+
+def msf_segment_field_noalloc(field, labels, pred=None, edges=MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL,
+                              stream=None) -> int:
+    """Field-only labelling without any allocation (see include/msf.h). field and labels are
+    device tensors [tw][nz][ny][nx]; pred is (src, attr, op, lo, hi) on the field or None."""
+    tw, nz, ny, nx = field.shape
+    fp, fk = _ptr_kind(field)
+    lp, lk = _ptr_kind(labels)
+    if (fp and fk != MSF_DEVICE) or (lp and lk != MSF_DEVICE):
+        raise ValueError("field and labels must be device memory")
+    pp = None
+    if pred is not None:
+        src, a, op, lo, hi = pred
+        pp = ctypes.byref(msf_pred(int(src), int(a), int(op), float(lo), float(hi)))
+    s = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+    n = ctypes.c_int64(0)
+    _check(load_library().msf_segment_field_noalloc(nx, ny, nz, tw, fp, pp, int(edges), lp,
+                                                    ctypes.byref(n), s),
+           "msf_segment_field_noalloc")
+    return int(n.value)
 
 
 def msf_set_tile(ctx, by, bz, bt):
