@@ -256,6 +256,9 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(dev)
 
     ctx.close()
     if rank == 0:
@@ -275,11 +278,71 @@ def run_gpu(args):
                              "value": round(vt / (seg_ms * 1e-3) / 1e9, 3) if seg_ms else None,
                              "unit": UNIT},
             "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches),
-            "kernels": per_kernel, "cpu_baseline": cpu,
+            "kernels": per_kernel, "cpu_baseline": cpu, "batched": batched,
         }
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batched(dev, reps=3):
+    """Batched form: 64 queries with their own thresholds, attributes and windows (T_w uniform in
+    2..32) on a 192^3 x 32 field with 4M 3-attribute points, as one msf_segment_batch call,
+    against a loop of msf_segment calls on the same context. Both produce identical labels."""
+    import torch
+
+    from paper_1903_12294_gb300 import msf, synth
+    wl = synth.batched(device=dev)
+    T, nz, ny, nx = wl.field.shape
+    V = nx * ny * nz
+    stream = torch.cuda.current_stream(dev)
+    ctx = msf.Context(dev.index, stream)
+    ctx.load(wl.field, wl.pos, wl.attr)
+    ctx.bin()
+    crits = [msf.make_criteria(t0, t1, pr, e) for (t0, t1, pr, e) in wl.queries]
+    labels = [torch.empty((t1 - t0, nz, ny, nx), dtype=torch.int32, device=dev)
+              for (t0, t1, _, _) in wl.queries]
+    vt = sum((t1 - t0) * V for (t0, t1, _, _) in wl.queries)
+
+    def plain():
+        return [msf.msf_segment(ctx.h, c, l) for c, l in zip(crits, labels)]
+
+    def batch():
+        return msf.msf_segment_batch(ctx.h, crits, labels)
+
+    out = {}
+    ctx.kernel_times(reset=True)
+    for name, fn in (("plain", plain), ("batched", batch)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(reps):
+            nf = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3) / reps
+        out[name] = {"ms_per_batch": round(ms, 3), "queries_per_s": round(len(crits) / (ms * 1e-3), 1),
+                     "gvt_per_s": round(vt / (ms * 1e-3) / 1e9, 2), "n_features_total": int(sum(nf))}
+        ctx.profiling(True)                       # one more pass for the per-kernel split
+        fn()
+        ctx.profiling(False)
+        out[name]["kernels_ms"] = {k: round(v[0], 3) for k, v in ctx.kernel_times(reset=True).items()}
+    # same labels both ways
+    ref = [l.clone() for l in labels]
+    batch()
+    same = all(torch.equal(a, b) for a, b in zip(ref, labels))
+    ctx.close()
+    del labels, ref
+    torch.cuda.empty_cache()
+    return {"workload": f"{nx}x{ny}x{nz} x {T}, {wl.pos.shape[2]} points x {wl.attr.shape[1]} "
+                        f"attrs, {len(crits)} queries, T_w in 2..32, {vt} query-voxel-timesteps",
+            "plain": out["plain"], "batched": out["batched"],
+            "speedup": round(out["plain"]["ms_per_batch"] / out["batched"]["ms_per_batch"], 2),
+            "labels_identical": bool(same)}
 
 
 def _oracle_sample(wl, t_lo, t_hi):
@@ -345,6 +408,7 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

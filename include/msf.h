@@ -15,7 +15,7 @@
  *   msf_extract_features  per-feature statistics: averages of position, point value and field
  *                         value (the cluster centre of §3.2.2), spatio-temporal extent and
  *                         standard deviations (§3.4)
- *   msf_segment_batch     many queries (own thresholds, attributes, windows) in one launch
+ *   msf_segment_batch     many queries (own thresholds, attributes, windows) labelled together
  *
  * Connectivity. The paper's own clustering imposes no spatio-temporal connectivity (§3.3). A
  * feature here is a connected component of the graph whose vertices are the voxel-timesteps
@@ -104,9 +104,10 @@ typedef struct {
 
 /* Binning summary. Attribute a is summed in fixed point: q = round_half_even(v * 2^kscale[a])
  * with kscale[a] = 62 - e - b, where max|v| < 2^e over finite samples and 2^b >= P*T + 1, so
- * every int64 sum is exact and the per-voxel fp32 mean
- *   mean = (float)((double)sumq / ((double)count * 2^kscale[a]))   (NaN when count == 0)
- * is the same on every device. Non-finite attribute values count as 0. */
+ * every int64 sum is exact, and the per-voxel fp32 mean (NaN when count == 0)
+ *   mean = (((float)sumq / (float)count) * 2^-(k/2)) * 2^-(k - k/2),   k = kscale[a]
+ * (each operation IEEE fp32 with round-to-nearest-even, k/2 truncating toward zero) is the
+ * same on every device. Non-finite attribute values count as 0. */
 typedef struct {
   int64_t in_domain;              /* samples inside the grid, all timesteps                */
   int64_t out_of_domain;          /* samples with a non-finite or outside position         */
@@ -199,6 +200,17 @@ int msf_segment(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int lab
 int msf_extract_features(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
                          int labels_kind, msf_feature* out, int out_kind, int64_t cap,
                          int64_t* n_out);
+
+/* Many queries in one go: the labels of crits[i] go to labels[i] (device, [t1-t0][nz][ny][nx]
+ * int32, caller-owned; may be NULL for an empty window) and, if n_features is not NULL, their
+ * feature counts to n_features[i] (host). Results are identical to nq separate msf_segment calls.
+ * The queries share one launch per labelling phase: queries that cover the same timesteps read
+ * the same input rows back to back (shared through L2), and there is one stream
+ * synchronisation for the whole batch. The context's scratch arena grows to hold every query's
+ * labelling state at once (about 3.3 bytes per voxel-timestep of each window). Synchronises
+ * the stream. Errors: as msf_segment for any query; nothing is written on an argument error. */
+int msf_segment_batch(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
+                      int64_t* n_features);
 
 /* ---- allocation-free labelling ----------------------------------------------------------- */
 

@@ -27,6 +27,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <string.h>
+#include <vector>
 
 #include "msf_internal.cuh"
 
@@ -212,19 +214,25 @@ __device__ __forceinline__ TileCoord tile_coord(const Geometry& g, int tile) {
 // ---------------------------------------------------------------------------------------------
 // k_tile: criterion + tile-local labelling
 // ---------------------------------------------------------------------------------------------
+// Shared memory of one tile's labelling (row masks, run slots, scan scratch, union-find).
+struct TileSmem {
+  uint32_t* mask;  // [kSegPerTile]
+  uint32_t* rb;    // [kSegPerTile]
+  int* warp;       // [8]
+  uint32_t* par;   // [MAXR]
+  uint16_t* cid;   // [MAXR]
+};
+
 template <int NP, bool SPATIAL, bool VEC>
-__global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a) {
-  constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
-  __shared__ uint32_t s_mask[kSegPerTile];
-  __shared__ uint32_t s_rb[kSegPerTile];
-  __shared__ int s_warp[8];
-  extern __shared__ uint32_t s_dyn[];
-  uint32_t* s_par = s_dyn;                                        // [MAXR]
-  uint16_t* s_cid = reinterpret_cast<uint16_t*>(s_dyn + MAXR);     // [MAXR]
+__device__ __forceinline__ void tile_body(const SegArgs& a, const int tile, const TileSmem& sm) {
+  uint32_t* s_mask = sm.mask;
+  uint32_t* s_rb = sm.rb;
+  int* s_warp = sm.warp;
+  uint32_t* s_par = sm.par;
+  uint16_t* s_cid = sm.cid;
 
   const Geometry& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tile = blockIdx.x;
   const TileCoord tc = tile_coord(g, tile);
   const int BY = 1 << g.lby, BZ = 1 << g.lbz;
 
@@ -242,8 +250,8 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a)
       for (int u = 0; u < U; ++u) {
         const int sg = warp * 32 + 4 * (it + u) + rsub;
         const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
-        const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
-        valid[u] = x4 < g.nx && y < g.ny && z < g.nz && tw < g.tw;
+        const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
+        valid[u] = x4 < g.nx && y < g.ny && z < g.nz && tw >= 0 && tw < g.tw;
         const int64_t off = (int64_t)(g.t0 + tw) * g.V + (int64_t)(z * g.ny + y) * g.nx + x4;
 #pragma unroll
         for (int j = 0; j < NP; ++j)
@@ -276,8 +284,8 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a)
       for (int u = 0; u < U; ++u) {
         const int sg = warp * 32 + i + u;
         const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
-        const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
-        valid[u] = x < g.nx && y < g.ny && z < g.nz && tw < g.tw;
+        const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
+        valid[u] = x < g.nx && y < g.ny && z < g.nz && tw >= 0 && tw < g.tw;
         const int64_t off = (int64_t)(g.t0 + tw) * g.V + (int64_t)(z * g.ny + y) * g.nx + x;
 #pragma unroll
         for (int j = 0; j < NP; ++j)
@@ -361,8 +369,8 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a)
   }
   const uint32_t rbase = (uint32_t)tile * (uint32_t)a.maxr;
   const uint32_t cbase = (uint32_t)tile * (uint32_t)g.cmax;
-  const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
-  if (y < g.ny && z < g.nz && tw < g.tw) {
+  const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
+  if (y < g.ny && z < g.nz && tw >= 0 && tw < g.tw) {
     const int64_t gs = (((int64_t)tw * g.nz + z) * g.ny + y) * g.nxs + tc.xs;
     a.segmask[gs] = m;
     a.segrun[gs] = rbase + rb;
@@ -383,6 +391,17 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a)
   if (tid == 0) a.tileinfo[tile] = make_int2(nrun_tile, ncomp_tile);
 }
 
+template <int NP, bool SPATIAL, bool VEC>
+__global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a) {
+  constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
+  __shared__ uint32_t s_mask[kSegPerTile];
+  __shared__ uint32_t s_rb[kSegPerTile];
+  __shared__ int s_warp[8];
+  extern __shared__ uint32_t s_dyn[];
+  const TileSmem sm{s_mask, s_rb, s_warp, s_dyn, reinterpret_cast<uint16_t*>(s_dyn + MAXR)};
+  tile_body<NP, SPATIAL, VEC>(a, blockIdx.x, sm);
+}
+
 // ---------------------------------------------------------------------------------------------
 // k_hook: joins across tile boundaries
 // ---------------------------------------------------------------------------------------------
@@ -391,9 +410,8 @@ __device__ __forceinline__ int64_t seg_index(const Geometry& g, int tw, int z, i
 }
 
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_hook(const __grid_constant__ SegArgs a) {
+__device__ __forceinline__ void hook_body(const SegArgs& a, const int64_t gs) {
   const Geometry& g = a.g;
-  const int64_t gs = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gs >= g.nseg) return;
   const uint32_t m = __ldg(a.segmask + gs);
   if (!m) return;
@@ -446,8 +464,13 @@ __global__ void __launch_bounds__(256) k_hook(const __grid_constant__ SegArgs a)
       join_rows(seg_index(g, tw, z2, y2, xs), true);
     }
   }
-  if ((a.edges & MSF_EDGE_TEMPORAL) && tw > 0 && (tw & ((1 << g.lbt) - 1)) == 0)
+  if ((a.edges & MSF_EDGE_TEMPORAL) && tw > 0 && ((tw + g.toff) & ((1 << g.lbt) - 1)) == 0)
     join_rows(seg_index(g, tw - 1, z, y, xs), false);
+}
+
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256) k_hook(const __grid_constant__ SegArgs a) {
+  hook_body<SPATIAL>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -547,11 +570,10 @@ __global__ void __launch_bounds__(256) k_links(const __grid_constant__ SegArgs a
 // ---------------------------------------------------------------------------------------------
 // k_flatten: compress to roots, smallest index onto the root, count features
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_flatten(const __grid_constant__ SegArgs a) {
-  __shared__ int s_n;
+__device__ __forceinline__ void flatten_body(const SegArgs& a, const int tile, int* s_n_ptr) {
+  int& s_n = *s_n_ptr;
   if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
-  const int tile = blockIdx.x;
   const int nc = min(a.tileinfo[tile].y, a.g.cmax);
   const uint32_t cbase = (uint32_t)tile * (uint32_t)a.g.cmax;
   int roots = 0;
@@ -570,18 +592,20 @@ __global__ void __launch_bounds__(256) k_flatten(const __grid_constant__ SegArgs
   if (threadIdx.x == 0 && s_n) atomicAdd(&a.counters[0], (unsigned long long)s_n);
 }
 
+__global__ void __launch_bounds__(256) k_flatten(const __grid_constant__ SegArgs a) {
+  __shared__ int s_n;
+  flatten_body(a, blockIdx.x, &s_n);
+}
+
 // ---------------------------------------------------------------------------------------------
 // k_final: stream out the int32 labels
 // ---------------------------------------------------------------------------------------------
 template <bool SPATIAL, bool VEC>
-__global__ void __launch_bounds__(256) k_final(const __grid_constant__ SegArgs a) {
+__device__ __forceinline__ void final_body(const SegArgs& a, const int tile, int32_t* s_lbl,
+                                           uint32_t* s_mask, uint32_t* s_rb) {
   constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
-  __shared__ int32_t s_lbl[MAXR];
-  __shared__ uint32_t s_mask[kSegPerTile];
-  __shared__ uint32_t s_rb[kSegPerTile];
   const Geometry& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tile = blockIdx.x;
   const TileCoord tc = tile_coord(g, tile);
   const int BY = 1 << g.lby, BZ = 1 << g.lbz;
   const int nrun = min(a.tileinfo[tile].x, MAXR);
@@ -593,9 +617,9 @@ __global__ void __launch_bounds__(256) k_final(const __grid_constant__ SegArgs a
   {
     const int s = tid;
     const int ly = s & (BY - 1), lz = (s >> g.lby) & (BZ - 1), lt = s >> (g.lby + g.lbz);
-    const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
+    const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
     uint32_t mm = 0, rr = 0;
-    if (nrun && y < g.ny && z < g.nz && tw < g.tw) {
+    if (nrun && y < g.ny && z < g.nz && tw >= 0 && tw < g.tw) {
       const int64_t gs = seg_index(g, tw, z, y, tc.xs);
       mm = __ldcg(a.segmask + gs);
       rr = __ldcg(a.segrun + gs) - rbase;
@@ -613,8 +637,8 @@ __global__ void __launch_bounds__(256) k_final(const __grid_constant__ SegArgs a
     for (int it = 0; it < 8; ++it) {
       const int sg = warp * 32 + 4 * it + rsub;
       const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
-      const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
-      if (y >= g.ny || z >= g.nz || tw >= g.tw) continue;
+      const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
+      if (y >= g.ny || z >= g.nz || tw < 0 || tw >= g.tw) continue;
       const uint32_t m = s_mask[sg];
       int4 o = make_int4(-1, -1, -1, -1);
       if ((m >> (4 * q)) & 0xFu) {
@@ -640,13 +664,22 @@ __global__ void __launch_bounds__(256) k_final(const __grid_constant__ SegArgs a
   for (int i = 0; i < 32; ++i) {
     const int sg = warp * 32 + i;
     const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
-    const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
-    if (y >= g.ny || z >= g.nz || tw >= g.tw) continue;
+    const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
+    if (y >= g.ny || z >= g.nz || tw < 0 || tw >= g.tw) continue;
     const uint32_t m = s_mask[sg];
     int32_t lbl = -1;
     if ((m >> lane) & 1u) lbl = s_lbl[s_rb[sg] + run_index(run_starts(m, SPATIAL), lane)];
     __stcs(a.labels + (int64_t)tw * g.V + (int64_t)(z * g.ny + y) * g.nx + x, lbl);
   }
+}
+
+template <bool SPATIAL, bool VEC>
+__global__ void __launch_bounds__(256) k_final(const __grid_constant__ SegArgs a) {
+  constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
+  __shared__ int32_t s_lbl[MAXR];
+  __shared__ uint32_t s_mask[kSegPerTile];
+  __shared__ uint32_t s_rb[kSegPerTile];
+  final_body<SPATIAL, VEC>(a, blockIdx.x, s_lbl, s_mask, s_rb);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -864,9 +897,9 @@ __global__ void __launch_bounds__(256) k_feat_vox(const __grid_constant__ SegArg
   {
     const int sg = tid;
     const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
-    const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
+    const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
     uint32_t mm = 0, rr = 0;
-    if (y < g.ny && z < g.nz && tw < g.tw) {
+    if (y < g.ny && z < g.nz && tw >= 0 && tw < g.tw) {
       const int64_t gs = seg_index(g, tw, z, y, tc.xs);
       mm = __ldg(a.segmask + gs);
       rr = __ldg(a.segrun + gs) - rbase;
@@ -880,7 +913,7 @@ __global__ void __launch_bounds__(256) k_feat_vox(const __grid_constant__ SegArg
     const uint32_t m = s_mask[sg];
     if ((m >> lane) & 1u) {
       const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
-      const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt;
+      const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
       const int x = tc.xs * 32 + lane;
       const int64_t fid = s_fid[s_rb[sg] + run_index(run_starts(m, SPATIAL), lane)];
       const int64_t off = (int64_t)(g.t0 + tw) * g.V + ((int64_t)z * g.ny + y) * g.nx + x;
@@ -1079,6 +1112,412 @@ int segment_field_fixed(const Geometry& g, int npred, const DevPred& pred, uint3
   MSF_CUDA_TRY(cudaStreamSynchronize(s));
   if (h[1]) return MSF_ERR_INTERNAL;
   if (n_features) *n_features = (int64_t)h[0];
+  return MSF_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// batched segmentation: many queries, one launch per phase
+// ---------------------------------------------------------------------------------------------
+// All queries of a batch use one tile shape with time chunks aligned to absolute timesteps
+// (each query's window starts toff rows into its first chunk), so every query covering a
+// chunk tiles it the same way. The tile phase walks its work chunk-major, then spatial tile,
+// then query: the CTAs that label one spatial tile for the different queries covering it run
+// back to back and read the same input rows, which they share through L2. The other phases
+// walk query-major. Every kernel is a fixed-size grid striding over its items.
+struct BatchPlan {
+  const SegArgs* qargs;        // [nq]
+  int nq;
+  int nchunk;                  // absolute time chunks touched by any query of the group
+  const int64_t* chunk_begin;  // [nchunk + 1] first tile item of each chunk
+  const int* chunk_nq;         // [nchunk] queries covering the chunk
+  const int* chunk_qoff;       // [nchunk] start of the chunk's query list in qlist
+  const int* qlist;            // query ids, chunk by chunk
+  const int* k0;               // [nq] first absolute chunk of each query (minus chunk 0 of the plan)
+  int nspat;                   // spatial tiles per chunk
+  const int64_t* seg_begin;    // [nq + 1] prefix of segments
+  const int64_t* tile_begin;   // [nq + 1] prefix of tiles
+  const int64_t* row_begin;    // [nq + 1] prefix of trajectory rows (tw - 1 per query)
+  const int* row_q;            // [rows] query of each trajectory row, rows in timestep order
+  const int* row_tw;           // [rows] window-relative step of each trajectory row
+  int64_t row0;                // first trajectory row of this launch (gridDim.y rows each)
+};
+
+// Largest i < n with begin[i] <= idx (begin ascending, begin[0] == 0).
+__device__ __forceinline__ int find_range(const int64_t* begin, int n, int64_t idx) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(begin + mid) <= idx) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Copy one query's arguments into shared memory (all threads; caller synchronises).
+__device__ __forceinline__ void load_args(SegArgs* dst, const SegArgs* src) {
+  static_assert(sizeof(SegArgs) % 4 == 0, "word copy");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(SegArgs) / 4); i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+template <int NP, bool SPATIAL, bool VEC>
+__global__ void __launch_bounds__(256) k_tile_batch(const __grid_constant__ BatchPlan b) {
+  constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
+  __shared__ uint32_t s_mask[kSegPerTile];
+  __shared__ uint32_t s_rb[kSegPerTile];
+  __shared__ int s_warp[8];
+  __shared__ __align__(16) SegArgs s_args;
+  extern __shared__ uint32_t s_dyn[];
+  const TileSmem sm{s_mask, s_rb, s_warp, s_dyn, reinterpret_cast<uint16_t*>(s_dyn + MAXR)};
+  const int64_t total = b.chunk_begin[b.nchunk];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_range(b.chunk_begin, b.nchunk, item);
+    const int64_t local = item - b.chunk_begin[c];
+    const int nqc = b.chunk_nq[c];
+    const int sidx = (int)(local / nqc), j = (int)(local - (int64_t)sidx * nqc);
+    const int q = b.qlist[b.chunk_qoff[c] + j];
+    load_args(&s_args, b.qargs + q);
+    __syncthreads();
+    tile_body<NP, SPATIAL, VEC>(s_args, (c - b.k0[q]) * b.nspat + sidx, sm);
+    __syncthreads();
+  }
+}
+
+// query = blockIdx.y; x strides over that query's segments
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256) k_hook_batch(const __grid_constant__ BatchPlan b) {
+  const int q = blockIdx.y;
+  const SegArgs& a = b.qargs[q];
+  const int64_t n = a.g.nseg;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    hook_body<SPATIAL>(a, i);
+}
+
+// 4 points per thread (independent chains in flight), like the single-query pass
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256) k_links_batch(const __grid_constant__ BatchPlan b) {
+  // rows in absolute-timestep order: the queries that cover step t read key[t] and key[t+1]
+  // back to back, so those rows come from L2 after the first query
+  const int64_t row = b.row0 + blockIdx.y;
+  const int q = b.row_q[row];
+  const SegArgs& a = b.qargs[q];
+  const int tw = b.row_tw[row];
+  const int64_t p0 = (int64_t)blockIdx.x * (256 * kLinkPer) + threadIdx.x;
+  int32_t ka[kLinkPer], kb[kLinkPer];
+#pragma unroll
+  for (int j = 0; j < kLinkPer; ++j) {
+    const int64_t p = p0 + j * 256;
+    ka[j] = kb[j] = -1;
+    if (p < a.P) {
+      ka[j] = __ldcs(a.key + (int64_t)(a.g.t0 + tw) * a.P + p);
+      kb[j] = __ldcs(a.key + (int64_t)(a.g.t0 + tw + 1) * a.P + p);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kLinkPer; ++j) {
+    if (ka[j] < 0 || kb[j] < 0) continue;
+    const int64_t ca = comp_of<SPATIAL>(a, tw, ka[j]);
+    if (ca < 0) continue;
+    const int64_t cb = comp_of<SPATIAL>(a, tw + 1, kb[j]);
+    if (cb >= 0 && ca != cb) gunion(a.cparent, (uint32_t)ca, (uint32_t)cb);
+  }
+}
+
+// query = blockIdx.y; x strides over that query's tiles
+__global__ void __launch_bounds__(256) k_flatten_batch(const __grid_constant__ BatchPlan b) {
+  __shared__ int s_n;
+  const int q = blockIdx.y;
+  const SegArgs& a = b.qargs[q];
+  for (int tile = blockIdx.x; tile < a.g.ntiles; tile += gridDim.x) {
+    flatten_body(a, tile, &s_n);
+    __syncthreads();
+  }
+}
+
+template <bool SPATIAL, bool VEC>
+__global__ void __launch_bounds__(256) k_final_batch(const __grid_constant__ BatchPlan b) {
+  constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
+  __shared__ int32_t s_lbl[MAXR];
+  __shared__ uint32_t s_mask[kSegPerTile];
+  __shared__ uint32_t s_rb[kSegPerTile];
+  __shared__ __align__(16) SegArgs s_args;
+  load_args(&s_args, b.qargs + blockIdx.y);
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < s_args.g.ntiles; tile += gridDim.x) {
+    final_body<SPATIAL, VEC>(s_args, tile, s_lbl, s_mask, s_rb);
+    __syncthreads();
+  }
+}
+
+template <int NP, bool SP, bool VEC>
+static void launch_tile_batch(const BatchPlan& b, int grid, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_tile_batch<NP, SP, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tile_dyn_smem<SP>());
+    attr_set = true;
+  }
+  k_tile_batch<NP, SP, VEC><<<grid, 256, tile_dyn_smem<SP>(), s>>>(b);
+}
+
+template <bool SP, bool VEC>
+static void launch_tile_batch_np(const BatchPlan& b, int np, int grid, cudaStream_t s) {
+  switch (np) {
+    case 0: launch_tile_batch<0, SP, VEC>(b, grid, s); break;
+    case 1: launch_tile_batch<1, SP, VEC>(b, grid, s); break;
+    case 2: launch_tile_batch<2, SP, VEC>(b, grid, s); break;
+    case 3: launch_tile_batch<3, SP, VEC>(b, grid, s); break;
+    default: launch_tile_batch<4, SP, VEC>(b, grid, s); break;
+  }
+}
+
+// One group of queries with the same predicate count and spatial edge flag.
+static int batch_group(msf_ctx* ctx, const std::vector<int>& qs, const msf_criteria* crits,
+                       int32_t* const* labels, int by, int bz, int bt, bool spatial, int np,
+                       std::vector<int64_t>& nfeat_out) {
+  const Dataset& d = ctx->ds;
+  const int nq = (int)qs.size();
+  cudaStream_t s = ctx->stream;
+  const int lby = ilog2_i(by), lbz = ilog2_i(bz), lbt = ilog2_i(bt);
+  // per-query geometry and scratch sizes
+  std::vector<SegArgs> args(nq);
+  std::vector<size_t> need(nq);
+  int cmin = 1 << 30, cmax_chunk = 0;
+  const int maxr = kSegPerTile * (spatial ? 16 : 32);
+  for (int i = 0; i < nq; ++i) {
+    const msf_criteria& c = crits[qs[i]];
+    Geometry g;
+    MSF_TRY(make_geometry(ctx, &c, &g));
+    g.lby = lby;
+    g.lbz = lbz;
+    g.lbt = lbt;
+    g.toff = c.t0 & (bt - 1);
+    g.tly = (d.ny + by - 1) / by;
+    g.tlz = (d.nz + bz - 1) / bz;
+    g.tlt = (g.tw + g.toff + bt - 1) / bt;
+    g.ntiles = g.nxs * g.tly * g.tlz * g.tlt;
+    g.cmax = spatial ? 16 * ((by + 1) / 2) * ((bz + 1) / 2) * bt : 32 * by * bz * bt;
+    if ((int64_t)g.ntiles * std::max(g.cmax, maxr) >= ((int64_t)1 << 32)) return MSF_ERR_TOO_LARGE;
+    SegArgs& a = args[i];
+    a = SegArgs{};
+    a.g = g;
+    make_preds(ctx, &c, a.pred);
+    a.npred = c.n_pred;
+    a.edges = c.edges;
+    a.key = d.key.as<int32_t>();
+    a.P = d.P;
+    a.maxr = maxr;
+    a.labels = labels[qs[i]];
+    need[i] = fixed_scratch_bytes(g, spatial);
+    const int k0 = c.t0 >> lbt, k1 = (c.t1 - 1) >> lbt;
+    cmin = std::min(cmin, k0);
+    cmax_chunk = std::max(cmax_chunk, k1);
+  }
+  const int nchunk = cmax_chunk - cmin + 1;
+  // plan arrays
+  std::vector<int64_t> chunk_begin(nchunk + 1, 0), seg_begin(nq + 1, 0), tile_begin(nq + 1, 0),
+      row_begin(nq + 1, 0);
+  std::vector<int> chunk_nq(nchunk, 0), chunk_qoff(nchunk, 0), qlist, k0(nq);
+  const int nspat = args[0].g.nxs * args[0].g.tly * args[0].g.tlz;
+  for (int k = 0; k < nchunk; ++k) {
+    chunk_qoff[k] = (int)qlist.size();
+    for (int i = 0; i < nq; ++i) {
+      const msf_criteria& c = crits[qs[i]];
+      const int ka = (c.t0 >> lbt) - cmin, kb = ((c.t1 - 1) >> lbt) - cmin;
+      if (k >= ka && k <= kb) qlist.push_back(i);
+    }
+    chunk_nq[k] = (int)qlist.size() - chunk_qoff[k];
+    chunk_begin[k + 1] = chunk_begin[k] + (int64_t)chunk_nq[k] * nspat;
+  }
+  for (int i = 0; i < nq; ++i) {
+    k0[i] = (crits[qs[i]].t0 >> lbt) - cmin;
+    seg_begin[i + 1] = seg_begin[i] + args[i].g.nseg;
+    tile_begin[i + 1] = tile_begin[i] + args[i].g.ntiles;
+    const bool traj = (args[i].edges & MSF_EDGE_TRAJ) && d.P > 0 && args[i].g.tw > 1;
+    row_begin[i + 1] = row_begin[i] + (traj ? args[i].g.tw - 1 : 0);
+  }
+  if (qlist.empty()) qlist.push_back(0);
+  std::vector<int> row_q, row_tw;  // trajectory rows sorted by absolute timestep
+  {
+    std::vector<std::pair<int, int>> rows;  // (absolute t, query)
+    for (int i = 0; i < nq; ++i)
+      for (int64_t r = 0; r < row_begin[i + 1] - row_begin[i]; ++r)
+        rows.push_back({crits[qs[i]].t0 + (int)r, i});
+    std::stable_sort(rows.begin(), rows.end(),
+                     [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+                       return x.first < y.first;
+                     });
+    for (auto& r : rows) {
+      row_q.push_back(r.second);
+      row_tw.push_back(r.first - crits[qs[r.second]].t0);
+    }
+    if (row_q.empty()) {
+      row_q.push_back(0);
+      row_tw.push_back(0);
+    }
+  }
+  // one arena: per-query scratch, then the plan arrays and the argument table
+  auto up = [](size_t n) { return (n + 255) & ~size_t(255); };
+  size_t total = 0;
+  std::vector<size_t> qoff(nq);
+  for (int i = 0; i < nq; ++i) {
+    qoff[i] = total;
+    total += up(need[i]);
+  }
+  const size_t off_args = total;
+  total += up(sizeof(SegArgs) * nq);
+  const size_t off_i64 = total;
+  const size_t n_i64 = (size_t)(nchunk + 1) + 3 * (size_t)(nq + 1);
+  total += up(sizeof(int64_t) * n_i64);
+  const size_t off_i32 = total;
+  const size_t n_i32 = (size_t)nchunk * 2 + qlist.size() + nq + 2 * row_q.size();
+  total += up(sizeof(int) * n_i32);
+  MSF_TRY(ctx->batch.arena.ensure(total));
+  char* base = ctx->batch.arena.as<char>();
+  for (int i = 0; i < nq; ++i) {
+    FixedScratch S;
+    fixed_scratch_carve(base + qoff[i], args[i].g, spatial, &S);
+    SegArgs& a = args[i];
+    a.segmask = S.segmask;
+    a.segrun = S.segrun;
+    a.runcomp = S.runcomp;
+    a.cparent = S.cparent;
+    a.cminli = S.cminli;
+    a.tileinfo = S.tileinfo;
+    a.counters = S.counters;
+    MSF_CUDA_TRY(cudaMemsetAsync(S.counters, 0, sizeof(unsigned long long) * 8, s));
+  }
+  // host image of the plan, copied in one transfer through pinned staging
+  const size_t hbytes = total - off_args;
+  MSF_TRY(ctx->batch.ensure_host(hbytes));
+  char* h = static_cast<char*>(ctx->batch.host);
+  memcpy(h, args.data(), sizeof(SegArgs) * nq);
+  int64_t* h64 = reinterpret_cast<int64_t*>(h + (off_i64 - off_args));
+  size_t o = 0;
+  for (auto v : chunk_begin) h64[o++] = v;
+  for (auto v : seg_begin) h64[o++] = v;
+  for (auto v : tile_begin) h64[o++] = v;
+  for (auto v : row_begin) h64[o++] = v;
+  int* h32 = reinterpret_cast<int*>(h + (off_i32 - off_args));
+  o = 0;
+  for (auto v : chunk_nq) h32[o++] = v;
+  for (auto v : chunk_qoff) h32[o++] = v;
+  for (auto v : qlist) h32[o++] = v;
+  for (auto v : k0) h32[o++] = v;
+  for (auto v : row_q) h32[o++] = v;
+  for (auto v : row_tw) h32[o++] = v;
+  MSF_CUDA_TRY(cudaMemcpyAsync(base + off_args, h, hbytes, cudaMemcpyHostToDevice, s));
+  BatchPlan b{};
+  b.qargs = reinterpret_cast<const SegArgs*>(base + off_args);
+  b.nq = nq;
+  b.nchunk = nchunk;
+  const int64_t* d64 = reinterpret_cast<const int64_t*>(base + off_i64);
+  b.chunk_begin = d64;
+  b.seg_begin = d64 + (nchunk + 1);
+  b.tile_begin = b.seg_begin + (nq + 1);
+  b.row_begin = b.tile_begin + (nq + 1);
+  const int* d32 = reinterpret_cast<const int*>(base + off_i32);
+  b.chunk_nq = d32;
+  b.chunk_qoff = d32 + nchunk;
+  b.qlist = b.chunk_qoff + nchunk;
+  b.k0 = b.qlist + qlist.size();
+  b.row_q = b.k0 + nq;
+  b.row_tw = b.row_q + row_q.size();
+  b.nspat = nspat;
+  const bool vec = (d.nx & 3) == 0;
+  const int per_sm = 5;  // resident CTAs of the tile kernel per SM
+  {
+    ScopedKernel k(ctx, "k_tile_batch");
+    const int grid = (int)std::min<int64_t>(chunk_begin[nchunk], (int64_t)ctx->sm_count * per_sm);
+    if (spatial) {
+      if (vec) launch_tile_batch_np<true, true>(b, np, std::max(grid, 1), s);
+      else launch_tile_batch_np<true, false>(b, np, std::max(grid, 1), s);
+    } else {
+      if (vec) launch_tile_batch_np<false, true>(b, np, std::max(grid, 1), s);
+      else launch_tile_batch_np<false, false>(b, np, std::max(grid, 1), s);
+    }
+  }
+  bool any_link = false;
+  for (int i = 0; i < nq; ++i) any_link |= (args[i].edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0;
+  int64_t max_seg = 1, max_tiles = 1;
+  for (int i = 0; i < nq; ++i) {
+    max_seg = std::max<int64_t>(max_seg, args[i].g.nseg);
+    max_tiles = std::max<int64_t>(max_tiles, args[i].g.ntiles);
+  }
+  // 2D grids: y = query (<= 65535 per launch, checked by the caller), x over its items
+  if (any_link) {
+    ScopedKernel k(ctx, "k_hook_batch");
+    const int64_t gx = (max_seg + 255) / 256;  // one segment per thread
+    if (spatial) k_hook_batch<true><<<dim3((unsigned)gx, nq), 256, 0, s>>>(b);
+    else k_hook_batch<false><<<dim3((unsigned)gx, nq), 256, 0, s>>>(b);
+  }
+  for (int64_t r0 = 0; r0 < row_begin[nq]; r0 += 65535) {  // gridDim.y limit per launch
+    ScopedKernel k(ctx, "k_links_batch");
+    const int64_t gx = (d.P + 256 * kLinkPer - 1) / (256 * kLinkPer);
+    dim3 grid((unsigned)std::max<int64_t>(gx, 1), (unsigned)std::min<int64_t>(65535, row_begin[nq] - r0));
+    BatchPlan br = b;
+    br.row0 = r0;
+    if (spatial) k_links_batch<true><<<grid, 256, 0, s>>>(br);
+    else k_links_batch<false><<<grid, 256, 0, s>>>(br);
+  }
+  {
+    ScopedKernel k(ctx, "k_flatten_batch");
+    k_flatten_batch<<<dim3((unsigned)max_tiles, nq), 256, 0, s>>>(b);
+  }
+  {
+    ScopedKernel k(ctx, "k_final_batch");
+    const dim3 grid((unsigned)max_tiles, nq);
+    bool vq = vec;
+    for (int i = 0; i < nq; ++i) vq &= ((uintptr_t)args[i].labels & 15) == 0;
+    if (spatial) {
+      if (vq) k_final_batch<true, true><<<grid, 256, 0, s>>>(b);
+      else k_final_batch<true, false><<<grid, 256, 0, s>>>(b);
+    } else {
+      if (vq) k_final_batch<false, true><<<grid, 256, 0, s>>>(b);
+      else k_final_batch<false, false><<<grid, 256, 0, s>>>(b);
+    }
+  }
+  MSF_CUDA_TRY(cudaGetLastError());
+  // feature counts and error flags of every query
+  std::vector<unsigned long long> cnt((size_t)nq * 2);
+  for (int i = 0; i < nq; ++i)
+    MSF_CUDA_TRY(cudaMemcpyAsync(&cnt[(size_t)i * 2], args[i].counters, 2 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+  MSF_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < nq; ++i) {
+    if (cnt[(size_t)i * 2 + 1]) return MSF_ERR_INTERNAL;
+    nfeat_out[qs[i]] = (int64_t)cnt[(size_t)i * 2];
+  }
+  return MSF_OK;
+}
+
+int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
+                      int64_t* n_features) {
+  const Dataset& d = ctx->ds;
+  ctx->last.valid = false;
+  std::vector<int64_t> nf(nq, 0);
+  // one tile shape for the whole batch: time chunks of 4 (16 for 2D+time) absolute steps
+  const int bt = d.nz == 1 ? 16 : 4;
+  const int by = d.nz == 1 ? 16 : 8, bz = d.nz == 1 ? 1 : 8;
+  // groups by (predicate count, spatial edges); empty windows need no work
+  for (int np = 0; np <= MSF_MAX_PRED; ++np)
+    for (int sp = 0; sp < 2; ++sp) {
+      std::vector<int> qs;
+      for (int i = 0; i < nq; ++i)
+        if (crits[i].n_pred == np && ((crits[i].edges & MSF_EDGE_SPATIAL) != 0) == (sp != 0) &&
+            crits[i].t1 > crits[i].t0)
+          qs.push_back(i);
+      for (size_t i0 = 0; i0 < qs.size(); i0 += 65535) {  // grid y holds the query index
+        std::vector<int> part(qs.begin() + i0, qs.begin() + std::min(qs.size(), i0 + 65535));
+        MSF_TRY(batch_group(ctx, part, crits, labels, by, bz, bt, sp != 0, np, nf));
+      }
+    }
+  ctx->timer.flush();
+  if (n_features)
+    for (int i = 0; i < nq; ++i) n_features[i] = nf[i];
   return MSF_OK;
 }
 

@@ -40,6 +40,29 @@ void DevBuf::release() {
   bytes = 0;
 }
 
+int BatchScratch::ensure_host(size_t n) {
+  if (n <= host_bytes && host) return MSF_OK;
+  if (host) cudaFreeHost(host);
+  host = nullptr;
+  host_bytes = 0;
+  cudaError_t e = cudaMallocHost(&host, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    host = nullptr;
+    set_last_cuda_error(e, "cudaMallocHost", __FILE__, __LINE__);
+    return MSF_ERR_OUT_OF_MEMORY;
+  }
+  host_bytes = n;
+  return MSF_OK;
+}
+
+void BatchScratch::release() {
+  arena.release();
+  if (host) cudaFreeHost(host);
+  host = nullptr;
+  host_bytes = 0;
+}
+
 int KernelTimer::begin(const char* name, cudaStream_t s, cudaEvent_t* a, cudaEvent_t* b,
                        int* rec) {
   int r = -1;
@@ -153,6 +176,7 @@ int make_geometry(const msf_ctx* ctx, const msf_criteria* c, Geometry* g) {
   g->lby = ilog2(by);
   g->lbz = ilog2(bz);
   g->lbt = ilog2(bt);
+  g->toff = 0;
   g->tly = (d.ny + by - 1) / by;
   g->tlz = (d.nz + bz - 1) / bz;
   g->tlt = (g->tw + bt - 1) / bt;
@@ -275,6 +299,7 @@ void msf_destroy(msf_ctx* c) {
     b->release();
   for (DevBuf* b : {&c->last.sample_sid, &c->last.sample_comp, &c->last.cfid}) b->release();
   c->host_staging.release();
+  c->batch.release();
   c->timer.release();
   delete c;
 }
@@ -400,6 +425,18 @@ int msf_extract_features(msf_ctx* c, const msf_criteria* crit, const int32_t* la
     src = c->host_staging.as<int32_t>();
   }
   return features_run(c, crit, src, labels, out, out_kind, cap, n_out);
+}
+
+int msf_segment_batch(msf_ctx* c, int nq, const msf_criteria* crits, int32_t* const* labels,
+                      int64_t* n_features) {
+  if (!c || nq < 0 || (nq > 0 && (!crits || !labels))) return MSF_ERR_INVALID_ARG;
+  for (int i = 0; i < nq; ++i) {
+    MSF_TRY(validate_criteria(c, &crits[i]));
+    if (crits[i].t1 > crits[i].t0 && !labels[i]) return MSF_ERR_INVALID_ARG;
+  }
+  if (nq == 0) return MSF_OK;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  return segment_batch_run(c, nq, crits, labels, n_features);
 }
 
 int msf_set_tile(msf_ctx* c, int by, int bz, int bt) {

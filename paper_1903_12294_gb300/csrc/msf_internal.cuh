@@ -92,6 +92,7 @@ struct Geometry {
   FastDiv fnx, fny, fnz, fnxs;  // division by nx, ny, nz and the segments per x-row
   int nxs;                 // segments along x = ceil(nx / 32)
   int lby, lbz, lbt;       // log2 of the tile extent along y, z, t
+  int toff;                // window start within its first time chunk (0: chunks start at t0)
   int tly, tlz, tlt;       // tiles along y, z, t
   int ntiles;
   int cmax;                // component slots per tile
@@ -130,6 +131,15 @@ struct SegState {
   DevBuf sample_sid, sample_comp, cfid;
 };
 
+// Device arena and pinned host staging of msf_segment_batch (grow-only).
+struct BatchScratch {
+  DevBuf arena;
+  void* host = nullptr;
+  size_t host_bytes = 0;
+  int ensure_host(size_t n);
+  void release();
+};
+
 struct BinScratch {
   DevBuf hist, offs, cursor, rec_v, rec_a, absmax, outside, scan_tmp, total;
 };
@@ -165,6 +175,7 @@ struct msf_ctx {
   msf::SegScratch seg;
   msf::FeatScratch feat;
   msf::BinScratch bin;
+  msf::BatchScratch batch;
   msf::DevBuf host_staging;  // device-side staging for host label buffers
   msf::SegState last;        // retained segmentation of the last msf_segment call
   uint64_t epoch = 1;        // bumped whenever the dataset or its binning changes
@@ -409,6 +420,8 @@ __device__ __forceinline__ void accumulate_samples(const FeatAcc& acc, bool ok, 
 int bin_run(msf_ctx* ctx, unsigned flags);
 int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels_dev, int64_t* nfeat,
                 const void* labels_user);
+int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
+                      int64_t* n_features);
 int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels_dev,
                  const void* labels_user, msf_feature* out, int out_kind, int64_t cap,
                  int64_t* n_out);

@@ -31,7 +31,7 @@ MSF_MAX_PRED, MSF_MAX_ATTR = 4, 8
 EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_bin_particles", "msf_get_bins", "msf_segment", "msf_extract_features",
            "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
-           "msf_segment_field_noalloc")
+           "msf_segment_field_noalloc", "msf_segment_batch")
 
 
 class msf_pred(ctypes.Structure):
@@ -101,6 +101,9 @@ def load_library(path: str = LIB_PATH):
         lib.msf_kernel_times.argtypes = [P, P, P, P, i32, i32]
         lib.msf_segment_field_noalloc.argtypes = [i32, i32, i32, i32, P, ctypes.POINTER(msf_pred),
                                                   u32, P, ctypes.POINTER(ctypes.c_int64), P]
+        lib.msf_segment_batch.argtypes = [P, i32, ctypes.POINTER(msf_criteria),
+                                          ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.POINTER(ctypes.c_int64)]
         lib.msf_status_string.argtypes = [i32]
         lib.msf_status_string.restype = ctypes.c_char_p
         for n in EXPORTS:
@@ -247,8 +250,20 @@ def msf_segment_field_noalloc(field, labels, pred=None, edges=MSF_EDGE_SPATIAL |
     n = ctypes.c_int64(0)
     _check(load_library().msf_segment_field_noalloc(nx, ny, nz, tw, fp, pp, int(edges), lp,
                                                     ctypes.byref(n), s),
-           "msf_segment_field_noalloc")
+           "msf_segment_field_noalloc", "msf_segment_batch")
     return int(n.value)
+
+
+def msf_segment_batch(ctx, crits, labels):
+    """crits: list of msf_criteria; labels: list of device int32 tensors (or None for empty
+    windows). Returns the list of feature counts."""
+    nq = len(crits)
+    carr = (msf_criteria * max(nq, 1))(*crits)
+    larr = (ctypes.c_void_p * max(nq, 1))(*[_ptr_kind(l)[0] if l is not None else None
+                                            for l in labels])
+    nf = (ctypes.c_int64 * max(nq, 1))()
+    _check(load_library().msf_segment_batch(ctx, nq, carr, larr, nf), "msf_segment_batch")
+    return [int(nf[i]) for i in range(nq)]
 
 
 def msf_set_tile(ctx, by, bz, bt):
@@ -338,6 +353,16 @@ class Context:
 
     def features(self, t0, t1, labels, preds=(), edges=MSF_EDGE_ALL):
         return msf_extract_features(self.h, make_criteria(t0, t1, preds, edges), labels)
+
+    def segment_batch(self, queries, labels=None):
+        """queries: list of (t0, t1, preds, edges). Allocates device label tensors unless given."""
+        import torch
+        T, nz, ny, nx = self.shape
+        crits = [make_criteria(t0, t1, p, e) for (t0, t1, p, e) in queries]
+        if labels is None:
+            labels = [torch.empty((t1 - t0, nz, ny, nx), dtype=torch.int32,
+                                  device=f"cuda:{self.device}") for (t0, t1, _, _) in queries]
+        return labels, msf_segment_batch(self.h, crits, labels)
 
     def set_tile(self, by, bz, bt):
         msf_set_tile(self.h, by, bz, bt)

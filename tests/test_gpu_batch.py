@@ -1,0 +1,56 @@
+"""Batched queries (msf_segment_batch): every query's labels and feature count equal a separate
+msf_segment call on the same data, and equal the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1903_12294_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+F, C, M = 0, 1, 2
+GT, GE, LT, LE, BAND = 0, 1, 2, 3, 4
+
+
+def _check_batch(gpu, orc, f, p, a, queries):
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(*(torch.as_tensor(x).cuda().contiguous() for x in (f, p, a)))
+        ctx.bin()
+        labels, nfs = ctx.segment_batch(queries)
+        singles = [ctx.segment(t0, t1, pr, e) for (t0, t1, pr, e) in queries]
+        torch.cuda.synchronize()
+    finally:
+        ctx.close()
+    o = orc.bin(f.shape, p, a)
+    for (t0, t1, pr, e), lb, nf, (ls, ns) in zip(queries, labels, nfs, singles):
+        assert nf == ns
+        assert torch.equal(lb, ls)
+        lab, n_o = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
+        assert nf == n_o and np.array_equal(lb.cpu().numpy(), lab)
+
+
+def test_batch_mixed_windows_and_criteria(gpu, orc):
+    """Windows starting inside a time chunk, single steps, different predicates and edge
+    classes in one batch (3D)."""
+    wl = synth.mid(n=48, T=11, P=30000, n_blobs=12)
+    f, p, a = wl.numpy()
+    q = wl.preds
+    queries = [(0, 11, q, 7), (1, 4, q, 7), (3, 4, q, 7), (5, 11, [(F, 0, GT, 0.45, 0)], 7),
+               (2, 9, [(F, 0, GT, 0.5, 0), (C, 0, GE, 1, 0)], 3), (6, 8, q, 1), (7, 10, q, 6),
+               (0, 2, [], 7), (4, 4, q, 7), (9, 11, [(M, 1, BAND, 0.4, 0.9), (F, 0, GE, 0.3, 0),
+                                                    (C, 0, LE, 3, 0)], 7)]
+    _check_batch(gpu, orc, f, p, a, queries)
+
+
+def test_batch_2d_time(gpu, orc):
+    rng = np.random.default_rng(4)
+    T, nz, ny, nx = 20, 1, 70, 96
+    f = rng.random((T, nz, ny, nx)).astype(np.float32)
+    P = 3000
+    pos = (rng.random((T, 3, P)) * np.array([nx, ny, nz])[None, :, None]).astype(np.float32)
+    a = rng.normal(size=(T, 2, P)).astype(np.float32)
+    queries = [(t0, t0 + tw, [(F, 0, GT, th, 0)], 7)
+               for t0, tw, th in ((0, 20, 0.6), (3, 5, 0.5), (15, 5, 0.55), (7, 1, 0.4),
+                                  (2, 17, 0.7))]
+    _check_batch(gpu, orc, f, pos, a, queries)
