@@ -38,6 +38,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
+# from an ncu capture of the same kernel on the same workload: {(config, kernel): bytes}
+TRAFFIC = {}
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -94,23 +99,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# per-kernel algorithmic bytes (the minimum each kernel must move through HBM per launch)
-def algorithmic_bytes(name, wl, n_pred_arrays, labels_active):
+# per-kernel algorithmic bytes: the bytes each kernel must move through HBM per launch by the
+# definition of its step (inputs it alone reads, outputs it alone writes); traffic of
+# intermediate state (sorted records, segment masks, union-find tables) is not counted
+def algorithmic_bytes(wl, n_pred_arrays, keep_sumq=False):
     T, nz, ny, nx = wl.field.shape
     V = nx * ny * nz
     tw = wl.t1 - wl.t0
     P = wl.pos.shape[2]
     A = wl.attr.shape[1]
     return {
-        "k_scatter": P * (12 + 4 * A + 4),                   # per timestep: pos+attr in, key out
-        "k_finalise": V * (4 + 4 * A),                       # per timestep: count + means out
-        "k_tile": V * tw * 4 * n_pred_arrays + V * tw // 32 * 8,
-        "k_final": V * tw * 4,
-        "k_traj": P * tw * 4,
-        "k_rootbits": V * tw * 4,
-        "k_vox": V * tw * 4 + labels_active * 8,
-        "k_pts": P * tw * (4 + 4 * A),
-    }.get(name)
+        "k_bin_keys": P * T * (12 + 4),                      # positions in, voxel keys out
+        "k_bin_place": P * T * 4 * A,                        # attributes in
+        "k_bin_reduce": V * T * (4 + 4 * A + (8 * A if keep_sumq else 0)),  # count + means out
+        "k_tile": V * tw * 4 * n_pred_arrays,                # field + predicate arrays in
+        "k_links": P * tw * 4,                               # keys of the window in
+        "k_final": V * tw * 4,                               # labels out
+        "k_feat_vox": V * tw * 8,                            # labels + field in
+    }
 
 
 def run_gpu(args):
@@ -189,25 +195,34 @@ def run_gpu(args):
     value = world * vt / (ms * 1e-3) / 1e9
     launches = sum(n for _, n in ktimes.values()) // max(args.steps, 1)
 
-    # dominant kernel and its roofline
-    lab_active = int((labels >= 0).sum().item())
+    # dominant kernel and its roofline (CUDA events around every launch on the context stream)
     npa = len({(s, a if s == 2 else 0) for s, a, *_ in wl.preds})
-    dom = max(ktimes.items(), key=lambda kv: kv[1][0])
-    name, (tot_ms, nl) = dom
-    per_launch_ms = tot_ms / nl
-    ab = algorithmic_bytes(name, wl, npa, lab_active)
+    abytes = algorithmic_bytes(wl, npa)
     peak, peak_kind = peaks()
+    per_kernel = {}
+    for k, (tot, nl) in ktimes.items():
+        e = {"ms_per_step": round(tot / args.steps, 4), "launches_per_step": nl // max(args.steps, 1)}
+        if abytes.get(k) and nl:
+            gbs = abytes[k] / (tot / nl * 1e-3) / 1e9
+            e.update({"algorithmic_bytes": abytes[k], "gb_per_s": round(gbs, 1),
+                      "frac": round(gbs / peak, 4)})
+        per_kernel[k] = e
+    name, (tot_ms, nl) = max(ktimes.items(), key=lambda kv: kv[1][0])
+    per_launch_ms = tot_ms / nl
+    ab = abytes.get(name)
     roof = None
-    if ab is not None:
+    if ab:
         ach = ab / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(ach / peak, 4),
-                "traffic": None, "algorithmic_bytes_per_launch": ab,
+                "traffic": TRAFFIC.get((args.config, name)), "algorithmic_bytes_per_launch": ab,
                 "avg_launch_ms": round(per_launch_ms, 5)}
-    per_kernel = {k: {"ms_per_step": round(v[0] / args.steps, 4),
-                      "launches_per_step": v[1] // max(args.steps, 1)} for k, v in ktimes.items()}
+    step_bytes = sum(abytes.values())
+    step_roof = {"algorithmic_bytes": step_bytes,
+                 "achieved_gb_per_s": round(step_bytes / (ms * 1e-3) / 1e9, 1),
+                 "frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4)}
     seg_ms = sum(v[0] for k, v in ktimes.items()
-                 if k in ("k_tile", "k_hook", "k_traj", "k_flatten", "k_final")) / args.steps
+                 if k in ("k_tile", "k_hook", "k_links", "k_flatten", "k_final")) / args.steps
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -259,6 +274,9 @@ def run_gpu(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(dev)
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(dev, seconds=args.serve_seconds)
 
     ctx.close()
     if rank == 0:
@@ -277,8 +295,9 @@ def run_gpu(args):
             "segment_only": {"ms": round(seg_ms, 4),
                              "value": round(vt / (seg_ms * 1e-3) / 1e9, 3) if seg_ms else None,
                              "unit": UNIT},
-            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches),
-            "kernels": per_kernel, "cpu_baseline": cpu, "batched": batched,
+            "roofline": roof, "step_roofline": step_roof, "clocks": clk.summary(), "e2e": e2e,
+            "gpu_launches": int(launches), "kernels": per_kernel, "cpu_baseline": cpu,
+            "batched": batched, "serving": serving,
         }
         print(json.dumps(out))
     if world > 1:
@@ -345,6 +364,116 @@ def run_batched(dev, reps=3):
             "labels_identical": bool(same)}
 
 
+def run_serving(dev, seconds=10.0, rate=200.0, saturate=256):
+    """Serving form: the 2D+time traffic-shaped dataset (1024^2 x 96 density field, 208,334
+    walkers x 96 steps) resident on the device; queries with windows of 4..64 steps and random
+    criteria arrive as a Poisson process at `rate`/s and go through the query server
+    (continuous batching, memory admission). Reports latency from submission to the batch's
+    completion on the device (p50/p99), queries/s at that offered load, and the server's
+    capacity on a burst of `saturate` queries against a loop of plain msf_segment calls."""
+    import torch
+
+    from paper_1903_12294_gb300 import msf, synth
+    wl = synth.serving(device=dev)
+    T, nz, ny, nx = wl.field.shape
+    V = nx * ny * nz
+    stream = torch.cuda.current_stream(dev)
+    ctx = msf.Context(dev.index, stream)
+    ctx.load(wl.field, wl.pos, wl.attr)
+    ctx.bin()
+    arrivals = synth.poisson_arrivals(rate, seconds, synth.SEED_BASE + 500)
+    nq = max(len(arrivals), saturate)
+    queries = synth.random_queries(wl, nq, synth.SEED_BASE + 501, (4, 64), field_q=(0.90, 0.99))
+    pool = 8 << 30
+
+    def serve(times, check=()):
+        """Submit queries[i] at times[i] (seconds from start); returns per-query records."""
+        srv = msf.Server(ctx, pool_bytes=pool, max_batch=64, slots=2)
+        n = len(times)
+        rec, kept = {}, {}
+
+        stop = threading.Event()
+        deadline = time.perf_counter() + max(times, default=0.0) + 120.0
+
+        def consume():
+            while len(rec) < n and not stop.is_set() and time.perf_counter() < deadline:
+                for r in srv.poll(cap=128, timeout_ms=100):
+                    rec[r.tag] = (r.status, r.n_features, r.batch_size, r.t_submit_ns,
+                                  r.t_admit_ns, r.t_done_ns)
+                    if r.tag in check:
+                        kept[r.tag] = srv.take_labels(r)
+                    elif r.labels:
+                        srv.release(r.tag)
+        th = threading.Thread(target=consume)
+        th.start()
+        try:
+            t_start = time.perf_counter()
+            for i, t in enumerate(times):
+                d = t_start + t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                t0, t1, pr, e = queries[i]
+                srv.submit(i, t0, t1, pr, e)
+        except BaseException:
+            stop.set()
+            raise
+        finally:
+            th.join()
+            st = srv.stats()
+            srv.close()
+        if len(rec) < n:
+            raise RuntimeError(f"serving: {len(rec)} of {n} results before the deadline")
+        return rec, kept, st
+
+    def summary(rec, st):
+        lat = sorted((v[5] - v[3]) * 1e-6 for v in rec.values())
+        span = (max(v[5] for v in rec.values()) - min(v[3] for v in rec.values())) * 1e-9
+
+        def q(p):
+            return lat[min(len(lat) - 1, int(p * len(lat)))]
+        return {"queries": len(rec), "failed": sum(v[0] != 0 for v in rec.values()),
+                "queries_per_s": round(len(rec) / span, 1),
+                "latency_ms": {"p50": round(q(0.50), 3), "p99": round(q(0.99), 3),
+                               "mean": round(sum(lat) / len(lat), 3), "max": round(lat[-1], 3)},
+                "batches": st.batches, "mean_batch": round(len(rec) / max(st.batches, 1), 2),
+                "max_batch": st.max_batch_seen, "max_slots_busy": st.max_slots_busy,
+                "pool_peak_gb": round(st.pool_peak / 1e9, 3)}
+
+    serve([0.0] * 8)                                         # warm-up
+    rec, _, st = serve(arrivals)
+    offered = summary(rec, st)
+    check = set(range(0, saturate, max(1, saturate // 16)))
+    rec_b, kept, st_b = serve([0.0] * saturate, check)
+    burst = summary(rec_b, st_b)
+    # plain per-query loop on the same burst, and the identity of the server's results
+    crits = [msf.make_criteria(t0, t1, pr, e) for (t0, t1, pr, e) in queries[:saturate]]
+    lab = torch.empty((64, nz, ny, nx), dtype=torch.int32, device=dev)
+    for c in crits[:4]:
+        msf.msf_segment(ctx.h, c, lab)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in crits:
+        msf.msf_segment(ctx.h, c, lab)
+    torch.cuda.synchronize()
+    plain_qps = saturate / (time.perf_counter() - t0)
+    same = True
+    for i in sorted(check):
+        a, b, pr, e = queries[i]
+        n = msf.msf_segment(ctx.h, crits[i], lab[:b - a])
+        same &= (n == rec_b[i][1]) and torch.equal(lab[:b - a], kept[i])
+    ctx.close()
+    del lab
+    torch.cuda.empty_cache()
+    vt_mean = sum((t1 - t0) * V for (t0, t1, _, _) in queries[:saturate]) / saturate
+    return {"workload": f"{nx}x{ny}x{nz} x {T}, {wl.pos.shape[2]} walkers x {T} steps, "
+                        f"T_w in 4..64 (mean {vt_mean / V:.1f} steps), random criteria",
+            "offered": {"rate_per_s": rate, "seconds": seconds, **offered},
+            "burst": {"queries": saturate, **burst, "plain_loop_queries_per_s": round(plain_qps, 1),
+                      "speedup_vs_plain": round(burst["queries_per_s"] / plain_qps, 2)},
+            "labels_identical_alone_and_in_mix": bool(same), "checked": len(check),
+            "pool_gb": pool / 2**30}
+
+
 def _oracle_sample(wl, t_lo, t_hi):
     """The oracle on timesteps [t_lo, t_hi) of the workload (bin + segment + features)."""
     import oracle
@@ -409,6 +538,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -16,6 +16,8 @@
  *                         value (the cluster centre of §3.2.2), spatio-temporal extent and
  *                         standard deviations (§3.4)
  *   msf_segment_batch     many queries (own thresholds, attributes, windows) labelled together
+ *   msf_server_*          a query server over the resident dataset: continuous batching of
+ *                         queries submitted from any thread, admitted by device memory
  *
  * Connectivity. The paper's own clustering imposes no spatio-temporal connectivity (§3.3). A
  * feature here is a connected component of the graph whose vertices are the voxel-timesteps
@@ -62,6 +64,7 @@ extern "C" {
 #define MSF_ERR_CUDA (-7)          /* a CUDA runtime call failed                            */
 #define MSF_ERR_CAPACITY (-8)      /* output buffer too small; the needed count is returned */
 #define MSF_ERR_INTERNAL (-9)      /* a device-side consistency check failed                */
+#define MSF_ERR_BUSY (-10)         /* the dataset is frozen while a query server is attached */
 
 /* ---- enums ------------------------------------------------------------------------------- */
 enum { MSF_HOST = 0, MSF_DEVICE = 1 };
@@ -211,6 +214,82 @@ int msf_extract_features(msf_ctx* ctx, const msf_criteria* crit, const int32_t* 
  * the stream. Errors: as msf_segment for any query; nothing is written on an argument error. */
 int msf_segment_batch(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
                       int64_t* n_features);
+
+/* ---- query server --------------------------------------------------------------------- */
+
+/* An interactive query loop over the resident dataset (the paper's use: a user explores
+ * features by trying criteria, §1 and §3.2). Clients submit queries from any thread; a worker
+ * thread of the server admits them, in arrival order, into launch slots and runs each slot's
+ * queries as one batch (as msf_segment_batch) on the slot's own stream. Slots run concurrently,
+ * so work submitted while other batches are on the GPU is admitted as soon as a slot and pool
+ * memory are free and overlaps with them (continuous batching). A query is admitted only when
+ * its labels (4 bytes per voxel-timestep of its window) and its labelling scratch (about 3.3
+ * bytes per voxel-timestep) fit into the server's device pool, allocated once by
+ * msf_server_create; nothing is allocated while serving. A query whose labels plus scratch
+ * exceed the whole pool is refused at submission (MSF_ERR_TOO_LARGE). Labels are canonical, so
+ * each result is the same as msf_segment of that query alone, whatever it was batched with.
+ *
+ * While a server is attached to a context, msf_load_timesteps and msf_bin_particles on that
+ * context return MSF_ERR_BUSY and msf_destroy does nothing; destroy the server first. The
+ * server uses the context's dataset and device only (not its stream or scratch). */
+typedef struct msf_server msf_server;
+
+typedef struct msf_server_config {
+  uint64_t pool_bytes; /* device pool for labels + scratch of admitted queries (0 = 4 GiB)  */
+  int32_t max_batch;   /* most queries in one batch (0 = 64; 1..4096)                        */
+  int32_t slots;       /* batches in flight at once, one stream each (0 = 2; 1..16)           */
+} msf_server_config;
+
+typedef struct msf_server_result {
+  uint64_t tag;         /* the caller's tag from msf_server_submit                             */
+  int32_t status;       /* MSF_OK or the error that ended this query                           */
+  int32_t batch_size;   /* queries in the batch that carried it (0: none, e.g. empty window)   */
+  int64_t n_features;   /* number of features                                                  */
+  int32_t* labels;      /* device, [t1-t0][nz][ny][nx] int32 canonical labels, owned by the    */
+                        /* server until msf_server_release(tag); NULL if empty or failed        */
+  int64_t n_labels;     /* voxel-timesteps in labels                                           */
+  int64_t t_submit_ns;  /* steady-clock times: submission, admission into a slot, completion */
+  int64_t t_admit_ns;   /* on the device (stamped by a host function behind the batch)       */
+  int64_t t_done_ns;
+} msf_server_result;
+
+typedef struct msf_server_stats {
+  int64_t submitted, completed, batches;
+  int64_t max_batch_seen;   /* largest batch launched                                          */
+  int64_t max_slots_busy;   /* most batches in flight at once                                  */
+  int64_t pending;          /* queued, not yet admitted                                        */
+  int64_t in_flight;        /* admitted, not yet completed                                     */
+  uint64_t pool_bytes, pool_used, pool_peak;
+} msf_server_stats;
+
+/* Start a server over ctx's loaded (and, for COUNT/MEAN predicates or TRAJ edges, binned)
+ * dataset; cfg may be NULL for the defaults. Allocates the pool, one stream, plan area and
+ * pinned staging per slot, and starts the worker thread. The environment variable
+ * MSF_FAULT=admit, read here, makes every admission fail with MSF_ERR_OUT_OF_MEMORY (host-side
+ * fault injection for tests). Errors: INVALID_ARG, NOT_LOADED, OUT_OF_MEMORY, CUDA. */
+int msf_server_create(msf_ctx* ctx, const msf_server_config* cfg, msf_server** out);
+
+/* Queue one query (copied). tag identifies its result and must not be in use by a query that
+ * is still queued, running, unpolled or unreleased. Thread-safe; does not block on the GPU.
+ * An empty window (t1 == t0) completes at once. Errors: as msf_segment's argument checks,
+ * TOO_LARGE (labels + scratch exceed the pool), INVALID_ARG (tag in use, server stopping). */
+int msf_server_submit(msf_server* srv, const msf_criteria* crit, uint64_t tag);
+
+/* Take up to cap finished results (any order across batches). Waits up to timeout_ms for the
+ * first one (0 = do not wait, < 0 = wait indefinitely); *n_out receives the number taken.
+ * Thread-safe. Errors: INVALID_ARG. */
+int msf_server_poll(msf_server* srv, msf_server_result* out, int cap, int* n_out,
+                    int timeout_ms);
+
+/* Return a result's labels to the pool; its labels pointer becomes invalid and the tag is free
+ * again. Thread-safe. Errors: INVALID_ARG (no labels held under tag). */
+int msf_server_release(msf_server* srv, uint64_t tag);
+
+int msf_server_get_stats(msf_server* srv, msf_server_stats* out);
+
+/* Stop admitting, wait for the batches in flight, drop queued queries, free everything
+ * (including labels not yet released). Errors: INVALID_ARG. */
+int msf_server_destroy(msf_server* srv);
 
 /* ---- allocation-free labelling ----------------------------------------------------------- */
 

@@ -27,6 +27,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
+#include <memory>
 #include <string.h>
 #include <vector>
 
@@ -690,14 +692,24 @@ constexpr size_t tile_dyn_smem() {
   return (size_t)kSegPerTile * (SP ? 16 : 32) * (sizeof(uint32_t) + sizeof(uint16_t));
 }
 
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per device (the attribute
+// belongs to the function on the current device). Safe from several host threads: a repeated
+// set is harmless.
+template <class K>
+static void ensure_smem_attr(K kernel, size_t bytes, std::atomic<uint64_t>& mask) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(mask.load(std::memory_order_acquire) & bit)) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    mask.fetch_or(bit, std::memory_order_release);
+  }
+}
+
 template <int NP, bool SP, bool VEC>
 static void launch_tile(const SegArgs& a, int grid, cudaStream_t s) {
-  static bool attr_set = false;  // per process; the attribute is per function
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tile<NP, SP, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tile_dyn_smem<SP>());
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};
+  ensure_smem_attr(k_tile<NP, SP, VEC>, tile_dyn_smem<SP>(), attr_set);
   k_tile<NP, SP, VEC><<<grid, 256, tile_dyn_smem<SP>(), s>>>(a);
 }
 
@@ -1254,12 +1266,8 @@ __global__ void __launch_bounds__(256) k_final_batch(const __grid_constant__ Bat
 
 template <int NP, bool SP, bool VEC>
 static void launch_tile_batch(const BatchPlan& b, int grid, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_batch<NP, SP, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tile_dyn_smem<SP>());
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};
+  ensure_smem_attr(k_tile_batch<NP, SP, VEC>, tile_dyn_smem<SP>(), attr_set);
   k_tile_batch<NP, SP, VEC><<<grid, 256, tile_dyn_smem<SP>(), s>>>(b);
 }
 
@@ -1274,34 +1282,92 @@ static void launch_tile_batch_np(const BatchPlan& b, int np, int grid, cudaStrea
   }
 }
 
-// One group of queries with the same predicate count and spatial edge flag.
-static int batch_group(msf_ctx* ctx, const std::vector<int>& qs, const msf_criteria* crits,
-                       int32_t* const* labels, int by, int bz, int bt, bool spatial, int np,
-                       std::vector<int64_t>& nfeat_out) {
+// zero each query's counters (one block per query; the argument table is on the device)
+__global__ void k_batch_prep(const SegArgs* __restrict__ qargs) {
+  if (threadIdx.x < 8) qargs[blockIdx.x].counters[threadIdx.x] = 0ull;
+}
+
+// gather each query's feature count and error flag into one array for a single copy back
+__global__ void k_batch_counts(const SegArgs* __restrict__ qargs, int nq,
+                               unsigned long long* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nq) {
+    out[2 * q] = __ldcg(qargs[q].counters);
+    out[2 * q + 1] = __ldcg(qargs[q].counters + 1);
+  }
+}
+
+// One launch group: queries with the same predicate count and spatial edge flag (one kernel
+// instantiation), at most 65535 of them (grid y holds the query index).
+struct BatchGroup {
+  int np = 0;
+  bool spatial = false;
+  std::vector<int> qs;          // query indices in the job
+  std::vector<SegArgs> args;    // per query; scratch and label pointers are set at launch
+  int nchunk = 0, nspat = 0;
+  std::vector<int64_t> chunk_begin, seg_begin, tile_begin, row_begin;
+  std::vector<int> chunk_nq, chunk_qoff, qlist, k0, row_q, row_tw;
+  size_t off_args = 0, off_i64 = 0, off_i32 = 0, off_cnt = 0;  // in the job's plan area
+};
+
+struct BatchJob {
+  int nq = 0;
+  int by = 0, bz = 0, bt = 0;
+  std::vector<size_t> scratch;  // device scratch bytes per query (0 for an empty window)
+  std::vector<BatchGroup> groups;
+  size_t plan_bytes = 0;        // device plan area = its host image (tables + counts)
+};
+
+// Tile shape of every batched query: time chunks of 4 (16 for 2D+time) absolute steps.
+static void batch_tile(const Dataset& d, int* by, int* bz, int* bt) {
+  *bt = d.nz == 1 ? 16 : 4;
+  *by = d.nz == 1 ? 16 : 8;
+  *bz = d.nz == 1 ? 1 : 8;
+}
+
+// Geometry of one query inside a batch: the batch tile shape, chunks aligned to absolute time.
+static int batch_geometry(msf_ctx* ctx, const msf_criteria* c, Geometry* out) {
   const Dataset& d = ctx->ds;
-  const int nq = (int)qs.size();
-  cudaStream_t s = ctx->stream;
-  const int lby = ilog2_i(by), lbz = ilog2_i(bz), lbt = ilog2_i(bt);
-  // per-query geometry and scratch sizes
-  std::vector<SegArgs> args(nq);
-  std::vector<size_t> need(nq);
+  int by, bz, bt;
+  batch_tile(d, &by, &bz, &bt);
+  const bool spatial = (c->edges & MSF_EDGE_SPATIAL) != 0;
+  const int maxr = kSegPerTile * (spatial ? 16 : 32);
+  Geometry g;
+  MSF_TRY(make_geometry(ctx, c, &g));
+  g.lby = ilog2_i(by);
+  g.lbz = ilog2_i(bz);
+  g.lbt = ilog2_i(bt);
+  g.toff = c->t0 & (bt - 1);
+  g.tly = (d.ny + by - 1) / by;
+  g.tlz = (d.nz + bz - 1) / bz;
+  g.tlt = (g.tw + g.toff + bt - 1) / bt;
+  g.ntiles = g.nxs * g.tly * g.tlz * g.tlt;
+  g.cmax = spatial ? 16 * ((by + 1) / 2) * ((bz + 1) / 2) * bt : 32 * by * bz * bt;
+  if ((int64_t)g.ntiles * std::max(g.cmax, maxr) >= ((int64_t)1 << 32)) return MSF_ERR_TOO_LARGE;
+  *out = g;
+  return MSF_OK;
+}
+
+int batch_query_scratch(msf_ctx* ctx, const msf_criteria* c, size_t* bytes) {
+  Geometry g;
+  MSF_TRY(batch_geometry(ctx, c, &g));
+  *bytes = fixed_scratch_bytes(g, (c->edges & MSF_EDGE_SPATIAL) != 0);
+  return MSF_OK;
+}
+
+static int plan_group(msf_ctx* ctx, const msf_criteria* crits, BatchJob* job, BatchGroup& gr) {
+  const Dataset& d = ctx->ds;
+  const int lbt = ilog2_i(job->bt);
+  const bool spatial = gr.spatial;
+  const int nq = (int)gr.qs.size();
+  gr.args.resize(nq);
   int cmin = 1 << 30, cmax_chunk = 0;
   const int maxr = kSegPerTile * (spatial ? 16 : 32);
   for (int i = 0; i < nq; ++i) {
-    const msf_criteria& c = crits[qs[i]];
+    const msf_criteria& c = crits[gr.qs[i]];
     Geometry g;
-    MSF_TRY(make_geometry(ctx, &c, &g));
-    g.lby = lby;
-    g.lbz = lbz;
-    g.lbt = lbt;
-    g.toff = c.t0 & (bt - 1);
-    g.tly = (d.ny + by - 1) / by;
-    g.tlz = (d.nz + bz - 1) / bz;
-    g.tlt = (g.tw + g.toff + bt - 1) / bt;
-    g.ntiles = g.nxs * g.tly * g.tlz * g.tlt;
-    g.cmax = spatial ? 16 * ((by + 1) / 2) * ((bz + 1) / 2) * bt : 32 * by * bz * bt;
-    if ((int64_t)g.ntiles * std::max(g.cmax, maxr) >= ((int64_t)1 << 32)) return MSF_ERR_TOO_LARGE;
-    SegArgs& a = args[i];
+    MSF_TRY(batch_geometry(ctx, &c, &g));
+    SegArgs& a = gr.args[i];
     a = SegArgs{};
     a.g = g;
     make_preds(ctx, &c, a.pred);
@@ -1310,128 +1376,117 @@ static int batch_group(msf_ctx* ctx, const std::vector<int>& qs, const msf_crite
     a.key = d.key.as<int32_t>();
     a.P = d.P;
     a.maxr = maxr;
-    a.labels = labels[qs[i]];
-    need[i] = fixed_scratch_bytes(g, spatial);
+    job->scratch[gr.qs[i]] = fixed_scratch_bytes(g, spatial);
     const int k0 = c.t0 >> lbt, k1 = (c.t1 - 1) >> lbt;
     cmin = std::min(cmin, k0);
     cmax_chunk = std::max(cmax_chunk, k1);
   }
   const int nchunk = cmax_chunk - cmin + 1;
-  // plan arrays
-  std::vector<int64_t> chunk_begin(nchunk + 1, 0), seg_begin(nq + 1, 0), tile_begin(nq + 1, 0),
-      row_begin(nq + 1, 0);
-  std::vector<int> chunk_nq(nchunk, 0), chunk_qoff(nchunk, 0), qlist, k0(nq);
-  const int nspat = args[0].g.nxs * args[0].g.tly * args[0].g.tlz;
+  gr.nchunk = nchunk;
+  gr.nspat = gr.args[0].g.nxs * gr.args[0].g.tly * gr.args[0].g.tlz;
+  gr.chunk_begin.assign(nchunk + 1, 0);
+  gr.seg_begin.assign(nq + 1, 0);
+  gr.tile_begin.assign(nq + 1, 0);
+  gr.row_begin.assign(nq + 1, 0);
+  gr.chunk_nq.assign(nchunk, 0);
+  gr.chunk_qoff.assign(nchunk, 0);
+  gr.k0.assign(nq, 0);
   for (int k = 0; k < nchunk; ++k) {
-    chunk_qoff[k] = (int)qlist.size();
+    gr.chunk_qoff[k] = (int)gr.qlist.size();
     for (int i = 0; i < nq; ++i) {
-      const msf_criteria& c = crits[qs[i]];
+      const msf_criteria& c = crits[gr.qs[i]];
       const int ka = (c.t0 >> lbt) - cmin, kb = ((c.t1 - 1) >> lbt) - cmin;
-      if (k >= ka && k <= kb) qlist.push_back(i);
+      if (k >= ka && k <= kb) gr.qlist.push_back(i);
     }
-    chunk_nq[k] = (int)qlist.size() - chunk_qoff[k];
-    chunk_begin[k + 1] = chunk_begin[k] + (int64_t)chunk_nq[k] * nspat;
+    gr.chunk_nq[k] = (int)gr.qlist.size() - gr.chunk_qoff[k];
+    gr.chunk_begin[k + 1] = gr.chunk_begin[k] + (int64_t)gr.chunk_nq[k] * gr.nspat;
   }
   for (int i = 0; i < nq; ++i) {
-    k0[i] = (crits[qs[i]].t0 >> lbt) - cmin;
-    seg_begin[i + 1] = seg_begin[i] + args[i].g.nseg;
-    tile_begin[i + 1] = tile_begin[i] + args[i].g.ntiles;
-    const bool traj = (args[i].edges & MSF_EDGE_TRAJ) && d.P > 0 && args[i].g.tw > 1;
-    row_begin[i + 1] = row_begin[i] + (traj ? args[i].g.tw - 1 : 0);
+    gr.k0[i] = (crits[gr.qs[i]].t0 >> lbt) - cmin;
+    gr.seg_begin[i + 1] = gr.seg_begin[i] + gr.args[i].g.nseg;
+    gr.tile_begin[i + 1] = gr.tile_begin[i] + gr.args[i].g.ntiles;
+    const bool traj = (gr.args[i].edges & MSF_EDGE_TRAJ) && d.P > 0 && gr.args[i].g.tw > 1;
+    gr.row_begin[i + 1] = gr.row_begin[i] + (traj ? gr.args[i].g.tw - 1 : 0);
   }
-  if (qlist.empty()) qlist.push_back(0);
-  std::vector<int> row_q, row_tw;  // trajectory rows sorted by absolute timestep
-  {
-    std::vector<std::pair<int, int>> rows;  // (absolute t, query)
-    for (int i = 0; i < nq; ++i)
-      for (int64_t r = 0; r < row_begin[i + 1] - row_begin[i]; ++r)
-        rows.push_back({crits[qs[i]].t0 + (int)r, i});
-    std::stable_sort(rows.begin(), rows.end(),
-                     [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
-                       return x.first < y.first;
-                     });
-    for (auto& r : rows) {
-      row_q.push_back(r.second);
-      row_tw.push_back(r.first - crits[qs[r.second]].t0);
+  if (gr.qlist.empty()) gr.qlist.push_back(0);
+  // trajectory rows sorted by absolute timestep
+  std::vector<std::pair<int, int>> rows;  // (absolute t, query)
+  for (int i = 0; i < nq; ++i)
+    for (int64_t r = 0; r < gr.row_begin[i + 1] - gr.row_begin[i]; ++r)
+      rows.push_back({crits[gr.qs[i]].t0 + (int)r, i});
+  std::stable_sort(rows.begin(), rows.end(),
+                   [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+                     return x.first < y.first;
+                   });
+  for (auto& r : rows) {
+    gr.row_q.push_back(r.second);
+    gr.row_tw.push_back(r.first - crits[gr.qs[r.second]].t0);
+  }
+  if (gr.row_q.empty()) {
+    gr.row_q.push_back(0);
+    gr.row_tw.push_back(0);
+  }
+  // layout in the job's plan area: argument table, int64 tables, int32 tables, counts
+  gr.off_args = job->plan_bytes;
+  size_t o = gr.off_args + up256(sizeof(SegArgs) * nq);
+  gr.off_i64 = o;
+  o += up256(sizeof(int64_t) * ((size_t)(nchunk + 1) + 3 * (size_t)(nq + 1)));
+  gr.off_i32 = o;
+  o += up256(sizeof(int) * ((size_t)nchunk * 2 + gr.qlist.size() + nq + 2 * gr.row_q.size()));
+  gr.off_cnt = o;
+  o += up256(sizeof(unsigned long long) * 2 * nq);
+  job->plan_bytes = o;
+  return MSF_OK;
+}
+
+int batch_job_plan(msf_ctx* ctx, int nq, const msf_criteria* crits, BatchJob** out) {
+  *out = nullptr;
+  const Dataset& d = ctx->ds;
+  BatchJob* job = new BatchJob();
+  job->nq = nq;
+  job->scratch.assign(nq, 0);
+  batch_tile(d, &job->by, &job->bz, &job->bt);
+  // groups by (predicate count, spatial edges); empty windows need no work
+  for (int np = 0; np <= MSF_MAX_PRED; ++np)
+    for (int sp = 0; sp < 2; ++sp) {
+      std::vector<int> qs;
+      for (int i = 0; i < nq; ++i)
+        if (crits[i].n_pred == np && ((crits[i].edges & MSF_EDGE_SPATIAL) != 0) == (sp != 0) &&
+            crits[i].t1 > crits[i].t0)
+          qs.push_back(i);
+      for (size_t i0 = 0; i0 < qs.size(); i0 += 65535) {
+        job->groups.emplace_back();
+        BatchGroup& gr = job->groups.back();
+        gr.np = np;
+        gr.spatial = sp != 0;
+        gr.qs.assign(qs.begin() + i0, qs.begin() + std::min(qs.size(), i0 + 65535));
+        const int st = plan_group(ctx, crits, job, gr);
+        if (st != MSF_OK) {
+          delete job;
+          return st;
+        }
+      }
     }
-    if (row_q.empty()) {
-      row_q.push_back(0);
-      row_tw.push_back(0);
-    }
-  }
-  // one arena: per-query scratch, then the plan arrays and the argument table
-  auto up = [](size_t n) { return (n + 255) & ~size_t(255); };
-  size_t total = 0;
-  std::vector<size_t> qoff(nq);
-  for (int i = 0; i < nq; ++i) {
-    qoff[i] = total;
-    total += up(need[i]);
-  }
-  const size_t off_args = total;
-  total += up(sizeof(SegArgs) * nq);
-  const size_t off_i64 = total;
-  const size_t n_i64 = (size_t)(nchunk + 1) + 3 * (size_t)(nq + 1);
-  total += up(sizeof(int64_t) * n_i64);
-  const size_t off_i32 = total;
-  const size_t n_i32 = (size_t)nchunk * 2 + qlist.size() + nq + 2 * row_q.size();
-  total += up(sizeof(int) * n_i32);
-  MSF_TRY(ctx->batch.arena.ensure(total));
-  char* base = ctx->batch.arena.as<char>();
-  for (int i = 0; i < nq; ++i) {
-    FixedScratch S;
-    fixed_scratch_carve(base + qoff[i], args[i].g, spatial, &S);
-    SegArgs& a = args[i];
-    a.segmask = S.segmask;
-    a.segrun = S.segrun;
-    a.runcomp = S.runcomp;
-    a.cparent = S.cparent;
-    a.cminli = S.cminli;
-    a.tileinfo = S.tileinfo;
-    a.counters = S.counters;
-    MSF_CUDA_TRY(cudaMemsetAsync(S.counters, 0, sizeof(unsigned long long) * 8, s));
-  }
-  // host image of the plan, copied in one transfer through pinned staging
-  const size_t hbytes = total - off_args;
-  MSF_TRY(ctx->batch.ensure_host(hbytes));
-  char* h = static_cast<char*>(ctx->batch.host);
-  memcpy(h, args.data(), sizeof(SegArgs) * nq);
-  int64_t* h64 = reinterpret_cast<int64_t*>(h + (off_i64 - off_args));
-  size_t o = 0;
-  for (auto v : chunk_begin) h64[o++] = v;
-  for (auto v : seg_begin) h64[o++] = v;
-  for (auto v : tile_begin) h64[o++] = v;
-  for (auto v : row_begin) h64[o++] = v;
-  int* h32 = reinterpret_cast<int*>(h + (off_i32 - off_args));
-  o = 0;
-  for (auto v : chunk_nq) h32[o++] = v;
-  for (auto v : chunk_qoff) h32[o++] = v;
-  for (auto v : qlist) h32[o++] = v;
-  for (auto v : k0) h32[o++] = v;
-  for (auto v : row_q) h32[o++] = v;
-  for (auto v : row_tw) h32[o++] = v;
-  MSF_CUDA_TRY(cudaMemcpyAsync(base + off_args, h, hbytes, cudaMemcpyHostToDevice, s));
-  BatchPlan b{};
-  b.qargs = reinterpret_cast<const SegArgs*>(base + off_args);
-  b.nq = nq;
-  b.nchunk = nchunk;
-  const int64_t* d64 = reinterpret_cast<const int64_t*>(base + off_i64);
-  b.chunk_begin = d64;
-  b.seg_begin = d64 + (nchunk + 1);
-  b.tile_begin = b.seg_begin + (nq + 1);
-  b.row_begin = b.tile_begin + (nq + 1);
-  const int* d32 = reinterpret_cast<const int*>(base + off_i32);
-  b.chunk_nq = d32;
-  b.chunk_qoff = d32 + nchunk;
-  b.qlist = b.chunk_qoff + nchunk;
-  b.k0 = b.qlist + qlist.size();
-  b.row_q = b.k0 + nq;
-  b.row_tw = b.row_q + row_q.size();
-  b.nspat = nspat;
+  *out = job;
+  return MSF_OK;
+}
+
+size_t batch_job_scratch_bytes(const BatchJob* job, int q) { return job->scratch[q]; }
+size_t batch_job_plan_bytes(const BatchJob* job) { return job->plan_bytes; }
+void batch_job_free(BatchJob* job) { delete job; }
+
+static void launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b, cudaStream_t s,
+                         bool timed) {
+  const Dataset& d = ctx->ds;
+  const int nq = (int)gr.qs.size();
+  const bool spatial = gr.spatial;
+  const int np = gr.np;
   const bool vec = (d.nx & 3) == 0;
+  k_batch_prep<<<nq, 32, 0, s>>>(b.qargs);
   const int per_sm = 5;  // resident CTAs of the tile kernel per SM
   {
-    ScopedKernel k(ctx, "k_tile_batch");
-    const int grid = (int)std::min<int64_t>(chunk_begin[nchunk], (int64_t)ctx->sm_count * per_sm);
+    ScopedKernel k(ctx, "k_tile_batch", timed);
+    const int grid = (int)std::min<int64_t>(gr.chunk_begin[gr.nchunk], (int64_t)ctx->sm_count * per_sm);
     if (spatial) {
       if (vec) launch_tile_batch_np<true, true>(b, np, std::max(grid, 1), s);
       else launch_tile_batch_np<true, false>(b, np, std::max(grid, 1), s);
@@ -1441,37 +1496,39 @@ static int batch_group(msf_ctx* ctx, const std::vector<int>& qs, const msf_crite
     }
   }
   bool any_link = false;
-  for (int i = 0; i < nq; ++i) any_link |= (args[i].edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0;
   int64_t max_seg = 1, max_tiles = 1;
+  bool vq = vec;
   for (int i = 0; i < nq; ++i) {
-    max_seg = std::max<int64_t>(max_seg, args[i].g.nseg);
-    max_tiles = std::max<int64_t>(max_tiles, args[i].g.ntiles);
+    const SegArgs& a = gr.args[i];
+    any_link |= (a.edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0;
+    max_seg = std::max<int64_t>(max_seg, a.g.nseg);
+    max_tiles = std::max<int64_t>(max_tiles, a.g.ntiles);
+    vq &= ((uintptr_t)a.labels & 15) == 0;
   }
-  // 2D grids: y = query (<= 65535 per launch, checked by the caller), x over its items
+  // 2D grids: y = query (<= 65535 per group), x over its items
   if (any_link) {
-    ScopedKernel k(ctx, "k_hook_batch");
+    ScopedKernel k(ctx, "k_hook_batch", timed);
     const int64_t gx = (max_seg + 255) / 256;  // one segment per thread
     if (spatial) k_hook_batch<true><<<dim3((unsigned)gx, nq), 256, 0, s>>>(b);
     else k_hook_batch<false><<<dim3((unsigned)gx, nq), 256, 0, s>>>(b);
   }
-  for (int64_t r0 = 0; r0 < row_begin[nq]; r0 += 65535) {  // gridDim.y limit per launch
-    ScopedKernel k(ctx, "k_links_batch");
+  const int64_t nrows = gr.row_begin[nq];
+  for (int64_t r0 = 0; r0 < nrows; r0 += 65535) {  // gridDim.y limit per launch
+    ScopedKernel k(ctx, "k_links_batch", timed);
     const int64_t gx = (d.P + 256 * kLinkPer - 1) / (256 * kLinkPer);
-    dim3 grid((unsigned)std::max<int64_t>(gx, 1), (unsigned)std::min<int64_t>(65535, row_begin[nq] - r0));
+    dim3 grid((unsigned)std::max<int64_t>(gx, 1), (unsigned)std::min<int64_t>(65535, nrows - r0));
     BatchPlan br = b;
     br.row0 = r0;
     if (spatial) k_links_batch<true><<<grid, 256, 0, s>>>(br);
     else k_links_batch<false><<<grid, 256, 0, s>>>(br);
   }
   {
-    ScopedKernel k(ctx, "k_flatten_batch");
+    ScopedKernel k(ctx, "k_flatten_batch", timed);
     k_flatten_batch<<<dim3((unsigned)max_tiles, nq), 256, 0, s>>>(b);
   }
   {
-    ScopedKernel k(ctx, "k_final_batch");
+    ScopedKernel k(ctx, "k_final_batch", timed);
     const dim3 grid((unsigned)max_tiles, nq);
-    bool vq = vec;
-    for (int i = 0; i < nq; ++i) vq &= ((uintptr_t)args[i].labels & 15) == 0;
     if (spatial) {
       if (vq) k_final_batch<true, true><<<grid, 256, 0, s>>>(b);
       else k_final_batch<true, false><<<grid, 256, 0, s>>>(b);
@@ -1480,42 +1537,134 @@ static int batch_group(msf_ctx* ctx, const std::vector<int>& qs, const msf_crite
       else k_final_batch<false, false><<<grid, 256, 0, s>>>(b);
     }
   }
-  MSF_CUDA_TRY(cudaGetLastError());
-  // feature counts and error flags of every query
-  std::vector<unsigned long long> cnt((size_t)nq * 2);
-  for (int i = 0; i < nq; ++i)
-    MSF_CUDA_TRY(cudaMemcpyAsync(&cnt[(size_t)i * 2], args[i].counters, 2 * sizeof(unsigned long long),
-                                 cudaMemcpyDeviceToHost, s));
-  MSF_CUDA_TRY(cudaStreamSynchronize(s));
-  for (int i = 0; i < nq; ++i) {
-    if (cnt[(size_t)i * 2 + 1]) return MSF_ERR_INTERNAL;
-    nfeat_out[qs[i]] = (int64_t)cnt[(size_t)i * 2];
+}
+
+int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* const* scratch,
+                     char* plan_dev, char* plan_host, cudaStream_t s, bool timed) {
+  // host image of every group's tables (the counts area is written by the device)
+  for (BatchGroup& gr : job->groups) {
+    const int nq = (int)gr.qs.size();
+    for (int i = 0; i < nq; ++i) {
+      const int q = gr.qs[i];
+      FixedScratch S;
+      fixed_scratch_carve(scratch[q], gr.args[i].g, gr.spatial, &S);
+      SegArgs& a = gr.args[i];
+      a.segmask = S.segmask;
+      a.segrun = S.segrun;
+      a.runcomp = S.runcomp;
+      a.cparent = S.cparent;
+      a.cminli = S.cminli;
+      a.tileinfo = S.tileinfo;
+      a.counters = S.counters;
+      a.labels = labels[q];
+    }
+    memcpy(plan_host + gr.off_args, gr.args.data(), sizeof(SegArgs) * nq);
+    int64_t* h64 = reinterpret_cast<int64_t*>(plan_host + gr.off_i64);
+    size_t o = 0;
+    for (auto v : gr.chunk_begin) h64[o++] = v;
+    for (auto v : gr.seg_begin) h64[o++] = v;
+    for (auto v : gr.tile_begin) h64[o++] = v;
+    for (auto v : gr.row_begin) h64[o++] = v;
+    int* h32 = reinterpret_cast<int*>(plan_host + gr.off_i32);
+    o = 0;
+    for (auto v : gr.chunk_nq) h32[o++] = v;
+    for (auto v : gr.chunk_qoff) h32[o++] = v;
+    for (auto v : gr.qlist) h32[o++] = v;
+    for (auto v : gr.k0) h32[o++] = v;
+    for (auto v : gr.row_q) h32[o++] = v;
+    for (auto v : gr.row_tw) h32[o++] = v;
   }
+  if (job->groups.empty()) return MSF_OK;
+  // one copy of the tables up (the counts at the end of each group come back)
+  MSF_CUDA_TRY(cudaMemcpyAsync(plan_dev, plan_host, job->plan_bytes, cudaMemcpyHostToDevice, s));
+  for (const BatchGroup& gr : job->groups) {
+    const int nq = (int)gr.qs.size();
+    BatchPlan b{};
+    b.qargs = reinterpret_cast<const SegArgs*>(plan_dev + gr.off_args);
+    b.nq = nq;
+    b.nchunk = gr.nchunk;
+    const int64_t* d64 = reinterpret_cast<const int64_t*>(plan_dev + gr.off_i64);
+    b.chunk_begin = d64;
+    b.seg_begin = d64 + (gr.nchunk + 1);
+    b.tile_begin = b.seg_begin + (nq + 1);
+    b.row_begin = b.tile_begin + (nq + 1);
+    const int* d32 = reinterpret_cast<const int*>(plan_dev + gr.off_i32);
+    b.chunk_nq = d32;
+    b.chunk_qoff = d32 + gr.nchunk;
+    b.qlist = b.chunk_qoff + gr.nchunk;
+    b.k0 = b.qlist + gr.qlist.size();
+    b.row_q = b.k0 + nq;
+    b.row_tw = b.row_q + gr.row_q.size();
+    b.nspat = gr.nspat;
+    launch_group(ctx, gr, b, s, timed);
+    auto* cnt = reinterpret_cast<unsigned long long*>(plan_dev + gr.off_cnt);
+    k_batch_counts<<<(nq + 255) / 256, 256, 0, s>>>(b.qargs, nq, cnt);
+  }
+  MSF_CUDA_TRY(cudaGetLastError());
+  // counts back: the span from the first group's counts to the end of the plan area
+  const size_t c0 = job->groups.front().off_cnt;
+  MSF_CUDA_TRY(cudaMemcpyAsync(plan_host + c0, plan_dev + c0, job->plan_bytes - c0,
+                               cudaMemcpyDeviceToHost, s));
   return MSF_OK;
+}
+
+int batch_job_finish(const BatchJob* job, const char* plan_host, int64_t* n_features,
+                     int* status) {
+  int st_all = MSF_OK;
+  if (n_features)
+    for (int i = 0; i < job->nq; ++i) n_features[i] = 0;
+  for (const BatchGroup& gr : job->groups) {
+    const auto* cnt = reinterpret_cast<const unsigned long long*>(plan_host + gr.off_cnt);
+    for (size_t i = 0; i < gr.qs.size(); ++i) {
+      const int st = cnt[2 * i + 1] ? MSF_ERR_INTERNAL : MSF_OK;
+      if (status) status[gr.qs[i]] = st;
+      if (st != MSF_OK) st_all = st;
+      if (n_features) n_features[gr.qs[i]] = (int64_t)cnt[2 * i];
+    }
+  }
+  return st_all;
+}
+
+size_t batch_plan_bound(int nq, int T, int nz) {
+  // every query of a batch in one group is the largest table set; a group boundary adds at
+  // most four 256-byte roundings, and there are at most 2 * (MSF_MAX_PRED + 1) groups (more
+  // only past 65535 queries)
+  const int bt = nz == 1 ? 16 : 4;
+  const size_t nchunk = (size_t)(T + bt - 1) / bt + 1;
+  const int ngroups = 2 * (MSF_MAX_PRED + 1) + nq / 65535 + 1;
+  size_t b = sizeof(SegArgs) * (size_t)nq + sizeof(int64_t) * (ngroups * (nchunk + 4) + 3 * (size_t)nq) +
+             sizeof(int) * (ngroups * (2 * nchunk + 1) + nchunk * nq + nq + 2 * (size_t)nq * T) +
+             sizeof(unsigned long long) * 2 * (size_t)nq;
+  return b + (size_t)ngroups * 4 * 256;
 }
 
 int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
                       int64_t* n_features) {
-  const Dataset& d = ctx->ds;
   ctx->last.valid = false;
-  std::vector<int64_t> nf(nq, 0);
-  // one tile shape for the whole batch: time chunks of 4 (16 for 2D+time) absolute steps
-  const int bt = d.nz == 1 ? 16 : 4;
-  const int by = d.nz == 1 ? 16 : 8, bz = d.nz == 1 ? 1 : 8;
-  // groups by (predicate count, spatial edges); empty windows need no work
-  for (int np = 0; np <= MSF_MAX_PRED; ++np)
-    for (int sp = 0; sp < 2; ++sp) {
-      std::vector<int> qs;
-      for (int i = 0; i < nq; ++i)
-        if (crits[i].n_pred == np && ((crits[i].edges & MSF_EDGE_SPATIAL) != 0) == (sp != 0) &&
-            crits[i].t1 > crits[i].t0)
-          qs.push_back(i);
-      for (size_t i0 = 0; i0 < qs.size(); i0 += 65535) {  // grid y holds the query index
-        std::vector<int> part(qs.begin() + i0, qs.begin() + std::min(qs.size(), i0 + 65535));
-        MSF_TRY(batch_group(ctx, part, crits, labels, by, bz, bt, sp != 0, np, nf));
-      }
-    }
+  BatchJob* job = nullptr;
+  MSF_TRY(batch_job_plan(ctx, nq, crits, &job));
+  std::unique_ptr<BatchJob> hold(job);
+  // one arena: per-query scratch, then the plan area
+  std::vector<size_t> off(nq, 0);
+  size_t total = 0;
+  for (int i = 0; i < nq; ++i) {
+    off[i] = total;
+    total += up256(job->scratch[i]);
+  }
+  const size_t off_plan = total;
+  total += up256(job->plan_bytes);
+  MSF_TRY(ctx->batch.arena.ensure(std::max<size_t>(total, 256)));
+  MSF_TRY(ctx->batch.ensure_host(std::max<size_t>(job->plan_bytes, 256)));
+  char* base = ctx->batch.arena.as<char>();
+  std::vector<char*> scratch(nq);
+  for (int i = 0; i < nq; ++i) scratch[i] = base + off[i];
+  char* host = static_cast<char*>(ctx->batch.host);
+  MSF_TRY(batch_job_launch(ctx, job, labels, scratch.data(), base + off_plan, host, ctx->stream,
+                           true));
+  MSF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->timer.flush();
+  std::vector<int64_t> nf(nq, 0);
+  MSF_TRY(batch_job_finish(job, host, nf.data(), nullptr));
   if (n_features)
     for (int i = 0; i < nq; ++i) n_features[i] = nf[i];
   return MSF_OK;

@@ -263,6 +263,7 @@ const char* msf_status_string(int status) {
     case MSF_ERR_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
     case MSF_ERR_CAPACITY: return "output capacity too small";
     case MSF_ERR_INTERNAL: return "internal consistency check failed";
+    case MSF_ERR_BUSY: return "dataset in use by a query server";
   }
   return "unknown status";
 }
@@ -284,6 +285,7 @@ int msf_create(msf_ctx** out, int device, void* stream) {
 
 void msf_destroy(msf_ctx* c) {
   if (!c) return;
+  if (c->servers.load() > 0) return;  // a server still reads the dataset: keep everything
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   Dataset& d = c->ds;
@@ -314,6 +316,7 @@ int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* f
                        int A, const float* pos, const float* attr, int ptr_kind) {
   if (!c || nx <= 0 || ny <= 0 || nz <= 0 || T <= 0 || P < 0 || A < 0 || !field)
     return MSF_ERR_INVALID_ARG;
+  if (c->servers.load() > 0) return MSF_ERR_BUSY;
   if (ptr_kind != MSF_HOST && ptr_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
   if (A > MSF_MAX_ATTR) return MSF_ERR_INVALID_ARG;
   if (P > 0 && (!pos || (A > 0 && !attr))) return MSF_ERR_INVALID_ARG;
@@ -343,6 +346,7 @@ int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* f
 
 int msf_bin_particles(msf_ctx* c, unsigned flags, msf_bin_stats* stats) {
   if (!c) return MSF_ERR_INVALID_ARG;
+  if (c->servers.load() > 0) return MSF_ERR_BUSY;
   if (flags & ~(unsigned)MSF_BIN_KEEP_SUMQ) return MSF_ERR_INVALID_ARG;
   if (!c->ds.loaded) return MSF_ERR_NOT_LOADED;
   MSF_CUDA_TRY(cudaSetDevice(c->device));

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <atomic>
 #include <vector>
 
 #include "msf.h"
@@ -181,6 +182,7 @@ struct msf_ctx {
   uint64_t epoch = 1;        // bumped whenever the dataset or its binning changes
   int tile_by = 0, tile_bz = 0, tile_bt = 0;
   msf::KernelTimer timer;
+  std::atomic<int> servers{0};  // query servers attached (the dataset is frozen meanwhile)
 };
 
 namespace msf {
@@ -190,8 +192,10 @@ struct ScopedKernel {
   msf_ctx* ctx;
   cudaEvent_t a = nullptr, b = nullptr;
   int rec = -1;
-  ScopedKernel(msf_ctx* c, const char* name) : ctx(c) {
-    if (ctx->timer.enabled) ctx->timer.begin(name, ctx->stream, &a, &b, &rec);
+  // timed = false for launches on a stream other than the context's (the timer's events are
+  // recorded on the context stream)
+  ScopedKernel(msf_ctx* c, const char* name, bool timed = true) : ctx(c) {
+    if (timed && ctx->timer.enabled) ctx->timer.begin(name, ctx->stream, &a, &b, &rec);
   }
   ~ScopedKernel() {
     if (b) cudaEventRecord(b, ctx->stream);
@@ -422,6 +426,25 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels_dev, int
                 const void* labels_user);
 int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
                       int64_t* n_features);
+// A batch of queries planned on the host (k_segment.cu): per-query geometry, scratch sizes and
+// the tables the batched kernels read. Device memory comes from the caller: each query's
+// scratch (batch_job_scratch_bytes, 256-byte aligned) and one plan area of
+// batch_job_plan_bytes on the device with a pinned host image of the same size.
+// batch_job_launch enqueues the whole batch on stream s, including the copy of the feature
+// counts back into the host image; once the stream has passed it, batch_job_finish reads them.
+struct BatchJob;
+int batch_job_plan(msf_ctx* ctx, int nq, const msf_criteria* crits, BatchJob** out);
+size_t batch_job_scratch_bytes(const BatchJob* job, int q);
+size_t batch_job_plan_bytes(const BatchJob* job);
+int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* const* scratch,
+                     char* plan_dev, char* plan_host, cudaStream_t s, bool timed);
+int batch_job_finish(const BatchJob* job, const char* plan_host, int64_t* n_features,
+                     int* status);
+void batch_job_free(BatchJob* job);
+// Device scratch of one query labelled in a batch (its geometry uses the batch tile shape).
+int batch_query_scratch(msf_ctx* ctx, const msf_criteria* c, size_t* bytes);
+// Upper bound of batch_job_plan_bytes for nq queries on a dataset of T steps and nz planes.
+size_t batch_plan_bound(int nq, int T, int nz);
 int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels_dev,
                  const void* labels_user, msf_feature* out, int out_kind, int64_t cap,
                  int64_t* n_out);

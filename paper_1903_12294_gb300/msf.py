@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmsf.so")
 MSF_OK = 0
 MSF_ERR_INVALID_ARG, MSF_ERR_NOT_LOADED, MSF_ERR_NOT_BINNED = -1, -2, -3
 MSF_ERR_OUT_OF_MEMORY, MSF_ERR_TOO_LARGE, MSF_ERR_TIMEOUT = -4, -5, -6
-MSF_ERR_CUDA, MSF_ERR_CAPACITY, MSF_ERR_INTERNAL = -7, -8, -9
+MSF_ERR_CUDA, MSF_ERR_CAPACITY, MSF_ERR_INTERNAL, MSF_ERR_BUSY = -7, -8, -9, -10
 MSF_HOST, MSF_DEVICE = 0, 1
 MSF_SRC_FIELD, MSF_SRC_COUNT, MSF_SRC_MEAN = 0, 1, 2
 MSF_OP_GT, MSF_OP_GE, MSF_OP_LT, MSF_OP_LE, MSF_OP_BAND = 0, 1, 2, 3, 4
@@ -31,7 +31,9 @@ MSF_MAX_PRED, MSF_MAX_ATTR = 4, 8
 EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_bin_particles", "msf_get_bins", "msf_segment", "msf_extract_features",
            "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
-           "msf_segment_field_noalloc", "msf_segment_batch")
+           "msf_segment_field_noalloc", "msf_segment_batch", "msf_server_create",
+           "msf_server_submit", "msf_server_poll", "msf_server_release", "msf_server_get_stats",
+           "msf_server_destroy")
 
 
 class msf_pred(ctypes.Structure):
@@ -63,6 +65,27 @@ class msf_feature(ctypes.Structure):
 
 
 FEATURE_DTYPE = np.dtype(msf_feature)
+
+
+class msf_server_config(ctypes.Structure):
+    _fields_ = [("pool_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int32),
+                ("slots", ctypes.c_int32)]
+
+
+class msf_server_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("n_features", ctypes.c_int64),
+                ("labels", ctypes.c_void_p), ("n_labels", ctypes.c_int64),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class msf_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("max_batch_seen", ctypes.c_int64),
+                ("max_slots_busy", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("pool_bytes", ctypes.c_uint64),
+                ("pool_used", ctypes.c_uint64), ("pool_peak", ctypes.c_uint64)]
 
 
 class MsfError(RuntimeError):
@@ -104,6 +127,13 @@ def load_library(path: str = LIB_PATH):
         lib.msf_segment_batch.argtypes = [P, i32, ctypes.POINTER(msf_criteria),
                                           ctypes.POINTER(ctypes.c_void_p),
                                           ctypes.POINTER(ctypes.c_int64)]
+        lib.msf_server_create.argtypes = [P, ctypes.POINTER(msf_server_config), ctypes.POINTER(P)]
+        lib.msf_server_submit.argtypes = [P, ctypes.POINTER(msf_criteria), ctypes.c_uint64]
+        lib.msf_server_poll.argtypes = [P, ctypes.POINTER(msf_server_result), i32,
+                                        ctypes.POINTER(ctypes.c_int), i32]
+        lib.msf_server_release.argtypes = [P, ctypes.c_uint64]
+        lib.msf_server_get_stats.argtypes = [P, ctypes.POINTER(msf_server_stats)]
+        lib.msf_server_destroy.argtypes = [P]
         lib.msf_status_string.argtypes = [i32]
         lib.msf_status_string.restype = ctypes.c_char_p
         for n in EXPORTS:
@@ -250,7 +280,7 @@ def msf_segment_field_noalloc(field, labels, pred=None, edges=MSF_EDGE_SPATIAL |
     n = ctypes.c_int64(0)
     _check(load_library().msf_segment_field_noalloc(nx, ny, nz, tw, fp, pp, int(edges), lp,
                                                     ctypes.byref(n), s),
-           "msf_segment_field_noalloc", "msf_segment_batch")
+           "msf_segment_field_noalloc")
     return int(n.value)
 
 
@@ -285,8 +315,53 @@ def msf_kernel_times(ctx, reset=False):
     return {bytes(names[i]).split(b"\0")[0].decode(): (ms[i], nl[i]) for i in range(min(n, cap))}
 
 
+def msf_server_create(ctx, pool_bytes=0, max_batch=0, slots=0):
+    h = ctypes.c_void_p()
+    cfg = msf_server_config(int(pool_bytes), int(max_batch), int(slots))
+    _check(load_library().msf_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)),
+           "msf_server_create")
+    return h
+
+
+def msf_server_submit(srv, crit: msf_criteria, tag: int):
+    _check(load_library().msf_server_submit(srv, ctypes.byref(crit), int(tag)),
+           "msf_server_submit")
+
+
+def msf_server_poll(srv, cap=256, timeout_ms=0):
+    """List of msf_server_result (up to cap), waiting up to timeout_ms for the first."""
+    out = (msf_server_result * max(cap, 1))()
+    n = ctypes.c_int(0)
+    _check(load_library().msf_server_poll(srv, out, int(cap), ctypes.byref(n), int(timeout_ms)),
+           "msf_server_poll")
+    return [out[i] for i in range(n.value)]
+
+
+def msf_server_release(srv, tag: int):
+    _check(load_library().msf_server_release(srv, int(tag)), "msf_server_release")
+
+
+def msf_server_get_stats(srv) -> msf_server_stats:
+    st = msf_server_stats()
+    _check(load_library().msf_server_get_stats(srv, ctypes.byref(st)), "msf_server_get_stats")
+    return st
+
+
+def msf_server_destroy(srv):
+    _check(load_library().msf_server_destroy(srv), "msf_server_destroy")
+
+
+class _DeviceInt32:
+    """Zero-copy view of server-owned device labels (CUDA array interface)."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<i4",
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
 # ---------------------------------------------------------------------------------------------
-# convenience wrapper
+# convenience wrappers
 # ---------------------------------------------------------------------------------------------
 
 class Context:
@@ -372,3 +447,62 @@ class Context:
 
     def kernel_times(self, reset=False):
         return msf_kernel_times(self.h, reset)
+
+
+class Server:
+    """A query server over a Context's resident dataset (see include/msf.h, msf_server_*)."""
+
+    def __init__(self, ctx: Context, pool_bytes=0, max_batch=0, slots=0):
+        self.ctx = ctx
+        self.h = msf_server_create(ctx.h, pool_bytes, max_batch, slots)
+
+    def close(self):
+        if self.h:
+            msf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, tag, t0, t1, preds=(), edges=MSF_EDGE_ALL):
+        msf_server_submit(self.h, make_criteria(t0, t1, preds, edges), tag)
+
+    def poll(self, cap=256, timeout_ms=0):
+        return msf_server_poll(self.h, cap, timeout_ms)
+
+    def labels(self, res):
+        """torch view (no copy) of a result's labels; valid until release(res.tag). Work that
+        reads it on a stream must finish before the release (the pool memory is reused)."""
+        import torch
+        if not res.labels:
+            return None
+        T, nz, ny, nx = self.ctx.shape
+        tw = res.n_labels // (nz * ny * nx)
+        return torch.as_tensor(_DeviceInt32(res.labels, (tw, nz, ny, nx)),
+                               device=f"cuda:{self.ctx.device}")
+
+    def release(self, tag):
+        msf_server_release(self.h, tag)
+
+    def take_labels(self, res):
+        """Copy of a result's labels (None if it has none), then release them to the pool."""
+        import torch
+        v = self.labels(res)
+        if v is None:
+            return None
+        out = v.clone()
+        torch.cuda.current_stream(self.ctx.device).synchronize()
+        self.release(res.tag)
+        return out
+
+    def stats(self):
+        return msf_server_get_stats(self.h)

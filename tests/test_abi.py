@@ -45,3 +45,33 @@ def test_product_path_has_no_oracle_import():
     pkg = os.path.join(ROOT, "paper_1903_12294_gb300")
     for p in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
         assert "oracle" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", open(p).read(), re.M), p
+
+
+def test_struct_layouts_match_c_compiler(msflib, tmp_path):
+    """Every ABI struct's size and field offsets as a C compiler lays them out from the header,
+    against the ctypes binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    structs = ["msf_pred", "msf_criteria", "msf_bin_stats", "msf_feature", "msf_server_config",
+               "msf_server_result", "msf_server_stats"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "msf.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'printf("{s} size %zu\\n", sizeof({s}));')
+        for f, _ in getattr(msflib, s)._fields_:
+            lines.append(f'printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        s, f, v = line.split()
+        cls = getattr(msflib, s)
+        want = ctypes.sizeof(cls) if f == "size" else getattr(cls, f).offset
+        assert int(v) == want, (s, f, int(v), want)
