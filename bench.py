@@ -152,7 +152,7 @@ def run_gpu(args):
     ctx = msf.Context(local, stream)
     crit = msf.make_criteria(wl.t0, wl.t1, wl.preds, wl.edges)
     labels = torch.empty((tw, nz, ny, nx), dtype=torch.int32, device=dev)
-    fcap = 1 << 22
+    fcap = 1 << 20
     feats = torch.empty((fcap * msf.FEATURE_DTYPE.itemsize,), dtype=torch.uint8, device=dev)
     lib = msf.load_library()
     nf_out = msf.ctypes.c_int64(0)

@@ -13,11 +13,15 @@
 //   k_bin_keys     one thread per 4 samples of one timestep: key[t][p], and per block a shared-
 //                  memory histogram of buckets merged into hist[t][bucket]
 //   scan           offsets[t][bucket] = exclusive prefix of hist
-//   k_bin_place    one thread per 4 samples: each block reserves its slots per bucket with one
-//                  atomic, then writes (voxel-in-bucket, attributes) records; also the largest
-//                  finite |v| per attribute
-//   k_bin_reduce   one CTA per (bucket, timestep): counts and fixed-point sums of its records
-//                  in shared memory, then count and mean (and the sums) for all R voxels
+//   k_bin_place    one CTA per 4096 samples of one timestep: the block's keys and attributes
+//                  arrive in shared memory by bulk asynchronous copy while the block reads its
+//                  slot ranges; the block sorts its samples by bucket in shared memory and writes
+//                  (voxel-in-bucket, attributes) records run by run; also the largest finite |v|
+//                  per attribute
+//   k_bin_reduce   one CTA per (bucket, timestep): its records arrive by bulk copy while the
+//                  accumulators are cleared; counts and fixed-point sums in shared memory, means
+//                  of the non-empty voxels into shared memory, then one vector store pass of
+//                  count and mean (and the sums) for all R voxels
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -43,14 +47,16 @@ struct BinArgs {
   int nblk;                     // sample blocks per timestep
   int64_t chunk;                // samples per block
   uint32_t nrec;                // records in all (samples inside the grid)
+  int64_t NRp;                  // stride of rec_a between attributes (P*T rounded up to 4)
   const float* pos;             // [T][3][P]
   const float* attr;            // [T][A][P]
   int32_t* key;                 // [T][P]
   uint32_t* hist;               // [T][nb][nblk] samples per (bucket, block)
   uint32_t* offs;               // exclusive prefix of hist (slot ranges)
   uint32_t* cursor;             // running fill positions (global-histogram fallback)
-  uint32_t* rec_v;              // [P*T] voxel within bucket
-  float* rec_a;                 // [A][P*T] attribute values
+  uint32_t* rec_v;              // [P*T] voxel within bucket (+4 slack for rounded bulk copies)
+  float* rec_a;                 // [A][NRp] attribute values (+4 slack)
+  unsigned* err;                // bounded waits that gave up
   unsigned* absmax;             // [A] float bits of max finite |v|
   unsigned long long* outside;  // [T]
   int32_t* count;               // [T][V]
@@ -178,32 +184,62 @@ __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArg
 // ---------------------------------------------------------------------------------------------
 // pass 2: records in bucket order (and the attribute maxima)
 // ---------------------------------------------------------------------------------------------
-// The block sorts its samples by bucket in shared memory first (a counting sort against the
-// block's own histogram), then writes each bucket's run to its slot range, so that a warp's
-// stores land in a few contiguous runs rather than 32 scattered sectors.
-constexpr int kPlaceChunk = 4096;      // samples per block in the shared-memory sort path
+// The block's keys and attributes (each an aligned-down, rounded-up span of its row) come into
+// shared memory by bulk asynchronous copy, while the threads read the block's slot ranges. The
+// block then sorts its samples by bucket in shared memory (a counting sort against its own
+// histogram, through an index permutation) and writes each bucket's run to its slot range, so
+// that a warp's stores land in a few contiguous runs rather than 32 scattered sectors.
+constexpr int kPlaceChunk = 4096;              // samples per block in the shared-memory path
+constexpr int kPlaceStage = kPlaceChunk + 8;   // staged elements per array (alignment slack)
 constexpr int kPlaceSmemMax = 200 * 1024;
 
 template <int A>
 __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
-  extern __shared__ uint32_t s_place[];
-  uint32_t* s_gbase = s_place;                    // [nb] global slot of the block's run
-  uint32_t* s_lpos = s_place + b.nb;              // [nb] local start, then fill cursor
-  uint32_t* s_rv = s_place + 2 * b.nb;            // [chunk] voxel-in-bucket
-  uint32_t* s_rb = s_rv + kPlaceChunk;            // [chunk] bucket
-  float* s_ra = reinterpret_cast<float*>(s_rb + kPlaceChunk);  // [A][chunk]
+  extern __shared__ __align__(16) uint32_t s_place[];
+  int32_t* s_key = reinterpret_cast<int32_t*>(s_place);                   // [kPlaceStage]
+  float* s_att = reinterpret_cast<float*>(s_place + kPlaceStage);          // [A][kPlaceStage]
+  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + (1 + A) * kPlaceStage);  // [chunk]
+  uint32_t* s_delta = s_place + (1 + A) * kPlaceStage + kPlaceChunk / 2;   // [nb] slot - local
+  uint32_t* s_lpos = s_delta + b.nb;                                       // [nb] fill cursor
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned s_max[A > 0 ? A : 1];
   __shared__ int s_warp[8];
   __shared__ int s_n;
   const int t = blockIdx.y, blk = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t pbeg = (int64_t)blk * b.chunk;
+  const int n = (int)min((int64_t)b.chunk, b.P - pbeg);
+  // element offsets of the block's rows and their misalignment (elements before the row start
+  // that the aligned-down copy brings in)
+  const int64_t ek = (int64_t)t * b.P + pbeg;
+  const int hk = (int)(ek & 3);
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    uint32_t tx = (uint32_t)(((hk + n + 3) & ~3) * 4);
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int64_t ea = ((int64_t)t * A + a) * b.P + pbeg;
+      tx += (uint32_t)((((int)(ea & 3) + n + 3) & ~3) * 4);
+    }
+    mbar_expect_tx(&s_bar, tx);
+    bulk_g2s(s_key, b.key + (ek - hk), (uint32_t)(((hk + n + 3) & ~3) * 4), &s_bar);
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int64_t ea = ((int64_t)t * A + a) * b.P + pbeg;
+      const int ha = (int)(ea & 3);
+      bulk_g2s(s_att + a * kPlaceStage, b.attr + (ea - ha), (uint32_t)(((ha + n + 3) & ~3) * 4),
+               &s_bar);
+    }
+  }
+  // the block's slot ranges and bucket counts (overlapping the copies)
   for (int i = threadIdx.x; i < b.nb; i += 256) {
-    s_gbase[i] = b.offs[((int64_t)t * b.nb + i) * b.nblk + blk];
+    s_delta[i] = b.offs[((int64_t)t * b.nb + i) * b.nblk + blk];
     s_lpos[i] = b.hist[((int64_t)t * b.nb + i) * b.nblk + blk];  // counts, scanned below
   }
   if (threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
-  // exclusive scan of the block's bucket counts (one thread per chunk of buckets)
+  // exclusive scan of the block's bucket counts (one thread per chunk of buckets); s_delta
+  // becomes global slot minus local position
   {
     const int per = (b.nb + 255) / 256;
     const int lo = threadIdx.x * per, hi = min(lo + per, b.nb);
@@ -223,56 +259,53 @@ __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant_
     for (int i = lo; i < hi; ++i) {
       const int c = (int)s_lpos[i];
       s_lpos[i] = (uint32_t)run;
+      s_delta[i] -= (uint32_t)run;
       run += c;
     }
   }
-  __syncthreads();
-  const int64_t pbeg = (int64_t)blk * b.chunk;
-  const int64_t pend = min(pbeg + b.chunk, b.P);
+  const bool ok = mbar_wait(&s_bar, 0);
+  if (__syncthreads_or(!ok)) {  // the copies did not arrive in time
+    if (threadIdx.x == 0) {
+      atomicAdd(b.err, 1u);
+      mbar_wait(&s_bar, 0);      // let copies still in flight land before the block exits
+    }
+    return;
+  }
+  // counting sort: s_inv[local position] = sample
   unsigned lmax[A > 0 ? A : 1];
 #pragma unroll
   for (int a = 0; a < A; ++a) lmax[a] = 0u;
-  for (int64_t q0 = pbeg + threadIdx.x; q0 < pend; q0 += 256 * kBinPer) {
-    int32_t kk[kBinPer];
-    float av[kBinPer][A > 0 ? A : 1];
-#pragma unroll
-    for (int j = 0; j < kBinPer; ++j) {
-      const int64_t p = q0 + j * 256;
-      const bool in = p < pend;
-      kk[j] = in ? __ldcs(b.key + (int64_t)t * b.P + p) : -1;
-#pragma unroll
-      for (int a = 0; a < A; ++a) {
-        av[j][a] = in ? __ldcs(b.attr + ((int64_t)t * A + a) * b.P + p) : 0.f;
-        if (isfinite(av[j][a])) lmax[a] = max(lmax[a], __float_as_uint(fabsf(av[j][a])));
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kBinPer; ++j) {
-      if (kk[j] < 0) continue;
-      const int bk = kk[j] >> b.logR;
-      const uint32_t pos = atomicAdd(s_lpos + bk, 1u);
-      s_rv[pos] = (uint32_t)kk[j] & ((1u << b.logR) - 1u);
-      s_rb[pos] = (uint32_t)bk;
-#pragma unroll
-      for (int a = 0; a < A; ++a) s_ra[a * kPlaceChunk + pos] = av[j][a];
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const int32_t k = s_key[hk + i];
+    if (k >= 0) {
+      const uint32_t pos = atomicAdd(s_lpos + (k >> b.logR), 1u);
+      s_inv[pos] = (uint16_t)i;
     }
   }
 #pragma unroll
   for (int a = 0; a < A; ++a) {
+    const int ha = (int)((((int64_t)t * A + a) * b.P + pbeg) & 3);
+    for (int i = threadIdx.x; i < n; i += 256) {
+      const float v = s_att[a * kPlaceStage + ha + i];
+      if (isfinite(v)) lmax[a] = max(lmax[a], __float_as_uint(fabsf(v)));
+    }
     const unsigned m = __reduce_max_sync(0xFFFFFFFFu, lmax[a]);
     if (lane == 0 && m) atomicMax(s_max + a, m);
   }
   __syncthreads();
-  // s_lpos[bk] is now the end of bucket bk's local run; its start is end - count
-  const int64_t NR = (int64_t)b.P * b.T;
-  const int n = s_n;
-  for (int i = threadIdx.x; i < n; i += 256) {
-    const uint32_t bk = s_rb[i];
-    const uint32_t cnt = b.hist[((int64_t)t * b.nb + bk) * b.nblk + blk];
-    const uint32_t slot = s_gbase[bk] + (uint32_t)i - (s_lpos[bk] - cnt);
-    b.rec_v[slot] = s_rv[i];
+  // runs out: local position j of bucket bk goes to slot s_delta[bk] + j
+  const int nr = s_n;
+  const uint32_t vmask = (1u << b.logR) - 1u;
+  for (int j = threadIdx.x; j < nr; j += 256) {
+    const int i = s_inv[j];
+    const int32_t k = s_key[hk + i];
+    const uint32_t slot = s_delta[k >> b.logR] + (uint32_t)j;
+    b.rec_v[slot] = (uint32_t)k & vmask;
 #pragma unroll
-    for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * NR + slot] = s_ra[a * kPlaceChunk + i];
+    for (int a = 0; a < A; ++a) {
+      const int ha = (int)((((int64_t)t * A + a) * b.P + pbeg) & 3);
+      b.rec_a[(int64_t)a * b.NRp + slot] = s_att[a * kPlaceStage + ha + i];
+    }
   }
   if (threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
 }
@@ -286,7 +319,6 @@ __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant_
   __syncthreads();
   const int64_t pbeg = (int64_t)blk * b.chunk;
   const int64_t pend = min(pbeg + b.chunk, b.P);
-  const int64_t NR = (int64_t)b.P * b.T;
   unsigned lmax[A > 0 ? A : 1];
 #pragma unroll
   for (int a = 0; a < A; ++a) lmax[a] = 0u;
@@ -303,7 +335,7 @@ __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant_
     const uint32_t slot = atomicAdd(b.cursor + ((int64_t)t * b.nb + bk) * b.nblk + blk, 1u);
     b.rec_v[slot] = (uint32_t)k & ((1u << b.logR) - 1u);
 #pragma unroll
-    for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * NR + slot] = av[a];
+    for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * b.NRp + slot] = av[a];
   }
 #pragma unroll
   for (int a = 0; a < A; ++a) {
@@ -317,17 +349,49 @@ __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant_
 // ---------------------------------------------------------------------------------------------
 // pass 3: per (bucket, timestep) counts, sums, means
 // ---------------------------------------------------------------------------------------------
+// Shared memory: sums [A][R] u64, counts [R] u32, then a staging area of R * (1 + A) words that
+// first holds the bucket's records (rec_v, rec_a per attribute; R words each, in pieces when the
+// bucket has more) and afterwards the means [A][R] f32 and the non-empty voxel list [R].
+// Bulk copies of records [a0, a0 + n) (n a multiple of 4) into the staging area.
+template <int A>
+__device__ __forceinline__ void reduce_issue(const BinArgs& b, uint32_t a0, uint32_t n,
+                                             uint32_t* s_stv, float* s_sta, int R, uint64_t* bar) {
+  const uint32_t bytes = 4u * n;
+  mbar_expect_tx(bar, bytes * (1 + A));
+  bulk_g2s(s_stv, b.rec_v + a0, bytes, bar);
+#pragma unroll
+  for (int a = 0; a < A; ++a) bulk_g2s(s_sta + (size_t)a * R, b.rec_a + a * b.NRp + a0, bytes, bar);
+}
+
 template <int A, bool KEEP>
 __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinArgs b) {
-  extern __shared__ unsigned long long s_dyn64[];
+  extern __shared__ __align__(16) unsigned long long s_dyn64[];
   const int R = 1 << b.logR;
   unsigned long long* s_sum = s_dyn64;                                    // [A][R]
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_dyn64 + (size_t)A * R);  // [R]
-  uint32_t* s_list = s_cnt + R;                                           // [R]
+  uint32_t* s_stv = s_cnt + R;                                            // [R] staged rec_v
+  float* s_sta = reinterpret_cast<float*>(s_stv + R);                     // [A][R] staged rec_a
+  float* s_mean = reinterpret_cast<float*>(s_cnt + R);                    // [A][R] (after records)
+  uint32_t* s_list = s_cnt + R + (size_t)A * R;                           // [R]
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_k[A > 0 ? A : 1];
   __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
   __shared__ int s_nlist;
   const int bucket = blockIdx.x, t = blockIdx.y;
+  const int64_t row = (int64_t)t * b.nb + bucket;
+  uint32_t r0 = 0, r1 = 0;  // no records at all: the offsets were never formed
+  if (b.nrec) {
+    r0 = b.offs[row * b.nblk];
+    r1 = (row + 1 < (int64_t)b.T * b.nb) ? b.offs[(row + 1) * b.nblk] : b.nrec;
+  }
+  // records in pieces of R words from the aligned-down start (16-byte bulk copies)
+  const uint32_t s0 = r0 & ~3u, e1 = (r1 + 3u) & ~3u;
+  const int npiece = r1 > r0 ? (int)((e1 - s0 + (uint32_t)R - 1) / (uint32_t)R) : 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    if (npiece) reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, R, &s_bar);
+  }
+  // clear the accumulators while the first piece is in flight
   {
     uint4* z = reinterpret_cast<uint4*>(s_dyn64);
     const int n16 = (int)(((size_t)A * R * 8 + (size_t)R * 4) / 16);
@@ -341,63 +405,52 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinA
   }
   if (threadIdx.x == 0) s_nlist = 0;
   __syncthreads();
-  const int64_t row = (int64_t)t * b.nb + bucket;
-  uint32_t r0 = 0, r1 = 0;  // no records at all: the offsets were never formed
-  if (b.nrec) {
-    r0 = b.offs[row * b.nblk];
-    r1 = (row + 1 < (int64_t)b.T * b.nb) ? b.offs[(row + 1) * b.nblk] : b.nrec;
-  }
-  const int64_t NR = (int64_t)b.P * b.T;
-  for (uint32_t r = r0 + threadIdx.x; r < r1; r += 256) {
-    const uint32_t v = __ldcs(b.rec_v + r);
-    atomicAdd(s_cnt + v, 1u);
+  for (int piece = 0; piece < npiece; ++piece) {
+    const bool ok = mbar_wait(&s_bar, (uint32_t)piece & 1u);
+    if (__syncthreads_or(!ok)) {  // the copy did not arrive in time
+      if (threadIdx.x == 0) {
+        atomicAdd(b.err, 1u);
+        mbar_wait(&s_bar, (uint32_t)piece & 1u);
+      }
+      return;
+    }
+    const uint32_t a0 = s0 + (uint32_t)piece * (uint32_t)R;
+    const int m = (int)min((uint32_t)R, e1 - a0);
+    for (int i = threadIdx.x; i < m; i += 256) {
+      const uint32_t r = a0 + (uint32_t)i;
+      if (r < r0 || r >= r1) continue;  // alignment slack of the neighbouring buckets
+      const uint32_t v = s_stv[i];
+      atomicAdd(s_cnt + v, 1u);
 #pragma unroll
-    for (int a = 0; a < A; ++a)
-      atomicAdd(s_sum + (size_t)a * R + v,
-                (unsigned long long)quantise(__ldcs(b.rec_a + (int64_t)a * NR + r), s_k[a]));
+      for (int a = 0; a < A; ++a)
+        atomicAdd(s_sum + (size_t)a * R + v,
+                  (unsigned long long)quantise(s_sta[(size_t)a * R + i], s_k[a]));
+    }
+    __syncthreads();
+    if (piece + 1 < npiece && threadIdx.x == 0) {
+      fence_proxy_async_smem();  // the reads above before the next copy overwrites the staging
+      const uint32_t a1 = a0 + (uint32_t)R;
+      reduce_issue<A>(b, a1, min((uint32_t)R, e1 - a1), s_stv, s_sta, R, &s_bar);
+    }
   }
-  __syncthreads();
-  // counts for all voxels (4 per thread); empty voxels get NaN means; the others are listed
+  // means: NaN everywhere, then the non-empty voxels (listed, warp-aggregated) get theirs
   const int64_t vbase = (int64_t)bucket << b.logR;
   const int nv = (int)min((int64_t)R, b.V - vbase);
   const float qnan = __int_as_float(0x7fc00000);
-  const bool vec = (b.V & 3) == 0;
   const int lane = threadIdx.x & 31;
-  for (int i0 = 0; i0 < nv; i0 += 1024) {
+  for (int i0 = 0; i0 < R; i0 += 1024) {
     const int i = i0 + 4 * threadIdx.x;
-    const bool in = i < nv;
-    uint4 c4 = make_uint4(0, 0, 0, 0);
-    if (in) c4 = *reinterpret_cast<const uint4*>(s_cnt + i);
-    const uint32_t c[4] = {c4.x, c4.y, c4.z, c4.w};
     unsigned nz = 0;
-    if (in) {
-      const int64_t v = vbase + i;
-      if (vec) {
-        __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v), c4);
+    uint32_t c[4] = {0u, 0u, 0u, 0u};
+    if (i < R) {
+      const uint4 c4 = *reinterpret_cast<const uint4*>(s_cnt + i);
+      c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
 #pragma unroll
-        for (int a = 0; a < A; ++a) {
-          const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
-          float4 m = make_float4(qnan, qnan, qnan, qnan);  // non-empty lanes are overwritten
-          __stcs(reinterpret_cast<float4*>(b.mean + o), m);
-          if (KEEP) {
-            __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2(0, 0));
-            __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2), make_longlong2(0, 0));
-          }
-        }
-      } else {
-        for (int e = 0; e < 4 && i + e < nv; ++e) {
-          __stcs(b.count + (int64_t)t * b.V + v + e, (int)c[e]);
-          for (int a = 0; a < A; ++a) {
-            const int64_t o = ((int64_t)a * b.T + t) * b.V + v + e;
-            __stcs(b.mean + o, qnan);
-            if (KEEP) __stcs(b.sumq + o, 0ll);
-          }
-        }
-      }
+      for (int a = 0; a < A; ++a)
+        *reinterpret_cast<float4*>(s_mean + (size_t)a * R + i) = make_float4(qnan, qnan, qnan, qnan);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) nz += (c[e] != 0u && i + e < nv);
+      for (int e = 0; e < 4; ++e) nz += (c[e] != 0u);
     }
-    // list the non-empty voxels (warp-aggregated)
     int x = (int)nz;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -409,36 +462,64 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinA
     base = __shfl_sync(0xFFFFFFFFu, base, 31) + x - (int)nz;
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      if (in && c[e] != 0u && i + e < nv) s_list[base++] = (uint32_t)(i + e);
+      if (c[e] != 0u) s_list[base++] = (uint32_t)(i + e);
   }
-  __syncthreads();  // the NaN stores above precede the mean stores below in program order
+  __syncthreads();
   const int nl = s_nlist;
   for (int j = threadIdx.x; j < nl; j += 256) {
     const int i = (int)s_list[j];
     const int c = (int)s_cnt[i];
 #pragma unroll
-    for (int a = 0; a < A; ++a) {
-      const long long sq = (long long)s_sum[(size_t)a * R + i];
-      const int64_t o = ((int64_t)a * b.T + t) * b.V + vbase + i;
-      __stcs(b.mean + o, __fmul_rn(__fmul_rn(div_count(i64_to_f32_rn(sq), c), s_f1[a]), s_f2[a]));
-      if (KEEP) __stcs(b.sumq + o, sq);
+    for (int a = 0; a < A; ++a)
+      s_mean[(size_t)a * R + i] = __fmul_rn(
+          __fmul_rn(div_count(i64_to_f32_rn((long long)s_sum[(size_t)a * R + i]), c), s_f1[a]),
+          s_f2[a]);
+  }
+  __syncthreads();
+  // one store of every output word: count, means (and sums), four voxels per thread
+  if ((b.V & 3) == 0) {
+    for (int i = 4 * threadIdx.x; i < nv; i += 1024) {
+      const int64_t v = vbase + i;
+      __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v),
+             *reinterpret_cast<const uint4*>(s_cnt + i));
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
+        __stcs(reinterpret_cast<float4*>(b.mean + o),
+               *reinterpret_cast<const float4*>(s_mean + (size_t)a * R + i));
+        if (KEEP) {
+          const unsigned long long* sq = s_sum + (size_t)a * R + i;
+          __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2((long long)sq[0], (long long)sq[1]));
+          __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2), make_longlong2((long long)sq[2], (long long)sq[3]));
+        }
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < nv; i += 256) {
+      const int64_t v = vbase + i;
+      __stcs(b.count + (int64_t)t * b.V + v, (int)s_cnt[i]);
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
+        __stcs(b.mean + o, s_mean[(size_t)a * R + i]);
+        if (KEEP) __stcs(b.sumq + o, (long long)s_sum[(size_t)a * R + i]);
+      }
     }
   }
 }
 
-// Bucket width per attribute count: R counts, A*R sums and an R-entry list within 48 KB of
-// dynamic shared memory (four CTAs per SM), at most 4096 voxels.
+// Bucket width per attribute count: sums, counts and the record staging area, R * (8 + 12 A)
+// bytes, within 64 KB of dynamic shared memory (three CTAs per SM); at most 2048 voxels.
 static int bucket_log2(int A) {
-  int l = 12;
-  while (l > 6 && ((size_t)1 << l) * (8 + 8 * (size_t)A) > 48 * 1024) --l;
+  int l = 11;
+  while (l > 6 && ((size_t)1 << l) * (8 + 12 * (size_t)A) > 64 * 1024) --l;
   return l;
 }
 
-static size_t reduce_smem(int A, int logR) { return ((size_t)1 << logR) * (8 + 8 * (size_t)A); }
+static size_t reduce_smem(int A, int logR) { return ((size_t)1 << logR) * (8 + 12 * (size_t)A); }
 
 static size_t place_smem(int A, int nb) {
-  return sizeof(uint32_t) * (2 * (size_t)nb + 2 * (size_t)kPlaceChunk) +
-         sizeof(float) * (size_t)A * kPlaceChunk;
+  return sizeof(uint32_t) * ((1 + (size_t)A) * kPlaceStage + kPlaceChunk / 2 + 2 * (size_t)nb);
 }
 
 template <int A>
@@ -469,14 +550,14 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
     if (keep) {
       static bool set = false;
       if (!set) {
-        cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 92 * 1024);
+        cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         set = true;
       }
       k_bin_reduce<A, true><<<gr, 256, sm, s>>>(b);
     } else {
       static bool set = false;
       if (!set) {
-        cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 92 * 1024);
+        cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         set = true;
       }
       k_bin_reduce<A, false><<<gr, 256, sm, s>>>(b);
@@ -528,12 +609,13 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_TRY(S.hist.ensure(sizeof(uint32_t) * TB));
   MSF_TRY(S.offs.ensure(sizeof(uint32_t) * TB));
   MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * TB));
-  MSF_TRY(S.rec_v.ensure(sizeof(uint32_t) * (NR > 0 ? NR : 1)));
-  MSF_TRY(S.rec_a.ensure(sizeof(float) * (NR > 0 ? NR : 1) * Af));
+  const int64_t NRp = (NR + 3) & ~(int64_t)3;
+  MSF_TRY(S.rec_v.ensure(sizeof(uint32_t) * (NRp + 4)));
+  MSF_TRY(S.rec_a.ensure(sizeof(float) * (NRp * Af + 4)));
   MSF_TRY(S.absmax.ensure(sizeof(unsigned) * MSF_MAX_ATTR));
   MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.T));
-  MSF_TRY(S.total.ensure(sizeof(uint32_t) * 2));
-  MSF_TRY(d.key.ensure(sizeof(int32_t) * d.T * (d.P > 0 ? d.P : 1)));
+  MSF_TRY(S.total.ensure(sizeof(uint32_t) * 4));  // [0] records, [2] error word
+  MSF_TRY(d.key.ensure(sizeof(int32_t) * (d.T * d.P + 4)));  // slack for rounded bulk copies
   MSF_TRY(d.count.ensure(sizeof(int32_t) * d.T * d.V));
   MSF_TRY(d.mean.ensure(sizeof(float) * d.T * d.V * Af));
   if (keep) MSF_TRY(d.sumq.ensure(sizeof(int64_t) * d.T * d.V * Af));
@@ -545,6 +627,8 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.cursor = S.cursor.as<uint32_t>();
   b.rec_v = S.rec_v.as<uint32_t>();
   b.rec_a = S.rec_a.as<float>();
+  b.NRp = NRp;
+  b.err = S.total.as<uint32_t>() + 2;
   b.absmax = S.absmax.as<unsigned>();
   b.outside = S.outside.as<unsigned long long>();
   b.count = d.count.as<int32_t>();
@@ -553,6 +637,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_CUDA_TRY(cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * TB, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.absmax, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.outside, 0, sizeof(unsigned long long) * d.T, s));
+  MSF_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), s));
   b.nrec = 0;
   if (d.P > 0) {
     launch_bin_a(ctx, b, keep, 0, smem);
@@ -574,8 +659,14 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.T,
                                cudaMemcpyDeviceToHost, s));
   MSF_CUDA_TRY(cudaMemcpyAsync(hmax, S.absmax.p, sizeof(hmax), cudaMemcpyDeviceToHost, s));
+  uint32_t herr = 0;
+  MSF_CUDA_TRY(cudaMemcpyAsync(&herr, b.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   MSF_CUDA_TRY(cudaStreamSynchronize(s));
   ctx->timer.flush();
+  if (herr) {
+    d.binned = false;
+    return MSF_ERR_TIMEOUT;
+  }
   for (int a = 0; a < d.A; ++a) {
     float m;
     memcpy(&m, &hmax[a], sizeof(float));

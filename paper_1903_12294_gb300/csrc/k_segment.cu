@@ -13,10 +13,12 @@
 //              a union-find in shared memory over the tile's in-tile neighbour rows. Writes the
 //              compact result: per segment its mask and first run slot, per run its component,
 //              per component its smallest index. Nothing per voxel is written.
-//   k_hook     one thread per segment: joins components across tile faces (x, y, z and the
-//              t-chunk boundary) with a global union-find on the component table.
-//   k_links    one thread per (point, t): joins the components of key[t][p] and key[t+1][p],
-//              and records the point samples that fall in member voxel-timesteps.
+//   k_hook     one CTA per tile, one thread per segment: joins components across the tile's
+//              lower faces (x, y, z and the t-chunk boundary) with a global union-find on the
+//              component table, each distinct component pair once per tile.
+//   k_compress one CTA per tile: points every component at its root before the trajectory pass.
+//   k_links    one thread per (point, chunk of 8 steps): joins the components of key[t][p] and
+//              key[t+1][p], and records the point samples that fall in member voxel-timesteps.
 //   k_flatten  one CTA per tile: path-compresses every component to its root and reduces the
 //              smallest index onto the root; counts roots (= features).
 //   k_final    one CTA per tile: resolves each run's label in shared memory and streams the
@@ -110,6 +112,8 @@ __device__ __forceinline__ void sunion(uint32_t* par, uint32_t a, uint32_t b) {
 // Global union-find over component ids; reads bypass L1 so they see other SMs' links. Path
 // halving: each visited node is pointed at its grandparent with atomicMin, which can only lower
 // a parent to another ancestor in the same set, so it composes with concurrent linking.
+constexpr uint32_t kNoComp = 0xFFFFFFFFu;  // never a component id (ntiles * cmax < 2^32)
+
 __device__ __forceinline__ uint32_t gfind(uint32_t* par, uint32_t a) {
   uint32_t p = __ldcg(par + a);
   while (p != a) {
@@ -411,16 +415,14 @@ __device__ __forceinline__ int64_t seg_index(const Geometry& g, int tw, int z, i
   return (((int64_t)tw * g.nz + z) * g.ny + y) * g.nxs + xs;
 }
 
-template <bool SPATIAL>
-__device__ __forceinline__ void hook_body(const SegArgs& a, const int64_t gs) {
+// Cross-tile joins of one segment (tw, z, y, xs) with mask m != 0: its first run against the
+// last runs of the nine rows to the left (another tile), the backward rows in y/z that lie in
+// another tile, and the row one step earlier when the segment opens a time chunk. Every join of
+// two components goes through join(c0, c1).
+template <bool SPATIAL, class J>
+__device__ __forceinline__ void hook_seg(const SegArgs& a, int64_t gs, int tw, int z, int y,
+                                         int xs, uint32_t m, J&& join) {
   const Geometry& g = a.g;
-  if (gs >= g.nseg) return;
-  const uint32_t m = __ldg(a.segmask + gs);
-  if (!m) return;
-  uint32_t r, xs, y, z, tw;
-  g.fnxs.divmod((uint32_t)gs, r, xs);
-  g.fny.divmod(r, r, y);
-  g.fnz.divmod(r, tw, z);
   const uint32_t st = run_starts(m, SPATIAL);
   const uint32_t rb = __ldg(a.segrun + gs);
 
@@ -432,37 +434,35 @@ __device__ __forceinline__ void hook_body(const SegArgs& a, const int64_t gs) {
     row_contacts(m, m2, spatial_rows, SPATIAL, [&](int x1, int x2) {
       const uint32_t c1 = __ldg(a.runcomp + rb + run_index(st, x1));
       const uint32_t c2 = __ldg(a.runcomp + rb2 + run_index(st2, x2));
-      if (c1 != c2) gunion(a.cparent, c1, c2);
+      if (c1 != c2) join(c1, c2);
     });
   };
 
   if (SPATIAL) {
     // x-neighbour segments (always another tile): bit 0 here against bit 31 of the segment
-    // to the left, for all 9 (dy, dz).
+    // to the left, for all 9 (dy, dz)
     if ((m & 1u) && xs > 0) {
       const uint32_t c0 = __ldg(a.runcomp + rb);
-      for (int dz = -1; dz <= 1; ++dz) {
-        const int z2 = (int)z + dz;
-        if (z2 < 0 || z2 >= g.nz) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int y2 = (int)y + dy;
-          if (y2 < 0 || y2 >= g.ny) continue;
-          const int64_t gs2 = seg_index(g, tw, z2, y2, xs - 1);
-          const uint32_t m2 = __ldg(a.segmask + gs2);
-          if (!(m2 >> 31)) continue;
-          const uint32_t st2 = run_starts(m2, SPATIAL);
-          const uint32_t c2 = __ldg(a.runcomp + __ldg(a.segrun + gs2) + __popc(st2) - 1);
-          if (c0 != c2) gunion(a.cparent, c0, c2);
-        }
+      uint32_t last = kNoComp;
+      for (int k = 0; k < 9; ++k) {
+        const int z2 = z + k / 3 - 1, y2 = y + k % 3 - 1;
+        if (z2 < 0 || z2 >= g.nz || y2 < 0 || y2 >= g.ny) continue;
+        const int64_t gs2 = seg_index(g, tw, z2, y2, xs - 1);
+        const uint32_t m2 = __ldg(a.segmask + gs2);
+        if (!(m2 >> 31)) continue;
+        const uint32_t st2 = run_starts(m2, SPATIAL);
+        const uint32_t c2 = __ldg(a.runcomp + __ldg(a.segrun + gs2) + __popc(st2) - 1);
+        if (c2 != c0 && c2 != last) join(c0, c2);
+        last = c2;
       }
     }
     // backward rows in y/z that lie in another tile
     const int dys[4] = {-1, -1, 0, 1}, dzs[4] = {0, -1, -1, -1};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int y2 = (int)y + dys[k], z2 = (int)z + dzs[k];
+      const int y2 = y + dys[k], z2 = z + dzs[k];
       if (y2 < 0 || y2 >= g.ny || z2 < 0) continue;
-      if ((y2 >> g.lby) == ((int)y >> g.lby) && (z2 >> g.lbz) == ((int)z >> g.lbz)) continue;
+      if ((y2 >> g.lby) == (y >> g.lby) && (z2 >> g.lbz) == (z >> g.lbz)) continue;
       join_rows(seg_index(g, tw, z2, y2, xs), true);
     }
   }
@@ -470,9 +470,73 @@ __device__ __forceinline__ void hook_body(const SegArgs& a, const int64_t gs) {
     join_rows(seg_index(g, tw - 1, z, y, xs), false);
 }
 
+// one thread per segment (batched pass)
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_hook(const __grid_constant__ SegArgs a) {
-  hook_body<SPATIAL>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+__device__ __forceinline__ void hook_body(const SegArgs& a, const int64_t gs) {
+  const Geometry& g = a.g;
+  if (gs >= g.nseg) return;
+  const uint32_t m = __ldg(a.segmask + gs);
+  if (!m) return;
+  uint32_t r, xs, y, z, tw;
+  g.fnxs.divmod((uint32_t)gs, r, xs);
+  g.fny.divmod(r, r, y);
+  g.fnz.divmod(r, tw, z);
+  hook_seg<SPATIAL>(a, gs, (int)tw, (int)z, (int)y, (int)xs, m,
+                    [&](uint32_t c0, uint32_t c1) { gunion(a.cparent, c0, c1); });
+}
+
+// The component pairs one tile joins across its faces repeat heavily (a feature crossing a face
+// touches it in many rows). Each tile keeps the pairs it has joined in a shared-memory set and
+// joins a pair only the first time it meets it.
+constexpr int kHookSet = 2048;
+
+__device__ __forceinline__ bool pair_first_seen(unsigned long long* set, uint32_t c0, uint32_t c1) {
+  const uint32_t lo = min(c0, c1), hi = max(c0, c1);
+  const unsigned long long key = ((unsigned long long)lo << 32) | hi;
+  uint32_t h = lo * 0x9E3779B1u + hi * 0x85EBCA77u;
+  h = (h ^ (h >> 16)) & (kHookSet - 1);
+#pragma unroll 1
+  for (int i = 0; i < 16; ++i) {
+    const unsigned long long old = atomicCAS(set + h, ~0ull, key);
+    if (old == ~0ull) return true;
+    if (old == key) return false;
+    h = (h + 1) & (kHookSet - 1);
+  }
+  return true;  // crowded: join without remembering
+}
+
+// one CTA per tile, one thread per segment of the tile
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256, 4) k_hook(const __grid_constant__ SegArgs a) {
+  __shared__ unsigned long long s_set[kHookSet];
+  for (int i = threadIdx.x; i < kHookSet; i += 256) s_set[i] = ~0ull;
+  __syncthreads();
+  const Geometry& g = a.g;
+  const TileCoord tc = tile_coord(g, blockIdx.x);
+  const int sg = threadIdx.x;
+  const int ly = sg & ((1 << g.lby) - 1), lz = (sg >> g.lby) & ((1 << g.lbz) - 1);
+  const int lt = sg >> (g.lby + g.lbz);
+  const int y = (tc.ty << g.lby) + ly, z = (tc.tz << g.lbz) + lz;
+  const int tw = (tc.tt << g.lbt) + lt - g.toff;
+  if (y >= g.ny || z >= g.nz || tw < 0 || tw >= g.tw) return;
+  const int64_t gs = seg_index(g, tw, z, y, tc.xs);
+  const uint32_t m = __ldg(a.segmask + gs);
+  if (!m) return;
+  hook_seg<SPATIAL>(a, gs, tw, z, y, tc.xs, m, [&](uint32_t c0, uint32_t c1) {
+    if (pair_first_seen(s_set, c0, c1)) gunion(a.cparent, c0, c1);
+  });
+}
+
+// Point every component of a tile straight at its root (no joins run concurrently), so that
+// the finds of the trajectory pass start one step from a root.
+__global__ void __launch_bounds__(256) k_compress(const __grid_constant__ SegArgs a) {
+  const int nc = min(a.tileinfo[blockIdx.x].y, a.g.cmax);
+  const uint32_t cbase = (uint32_t)blockIdx.x * (uint32_t)a.g.cmax;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const uint32_t c = cbase + k;
+    const uint32_t r = gfind(a.cparent, c);
+    if (r != c) a.cparent[c] = r;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -492,46 +556,54 @@ __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) 
   return __ldg(a.runcomp + __ldg(a.segrun + gs) + run_index(st, b));
 }
 
-// One thread per 4 (point, step) pairs of one row tw (points p = base + j * 256 + threadIdx.x):
-// with TRAJ joins the components of key[t][p] and key[t+1][p] (both members); with COLLECT
-// records every sample that lies in a member voxel-timestep (the point part of the features),
-// compacted per block with one atomic. Rows tw = 0 .. rows-1; with TRAJ the last row's t+1
-// samples are recorded by that row too.
-constexpr int kLinkPer = 4;
+// One thread per point and chunk of kLinkSteps window steps: the point's voxel keys at those
+// steps (and at the first step of the next chunk) are loaded once and turned into components
+// once, so each key serves both the link ending and the link starting at its step. Links join
+// the components of key[t][p] and key[t+1][p] when both are members; a point that stays in one
+// voxel needs no join when temporal edges are on (the temporal edge already joins the two
+// voxel-timesteps). Every sample that lies in a member voxel-timestep is recorded for the point
+// part of the features, compacted per block with one atomic.
+constexpr int kLinkPer = 4;     // points per thread in the batched pass
+constexpr int kLinkSteps = 8;   // window steps per thread in the single-query pass
 
-template <bool SPATIAL, bool TRAJ, bool COLLECT>
-__global__ void __launch_bounds__(256) k_links(const __grid_constant__ SegArgs a) {
+template <bool SPATIAL, bool TRAJ>
+__global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArgs a) {
   __shared__ int s_cnt[8];
   __shared__ unsigned long long s_base;
-  const int tw = blockIdx.y;
-  const int64_t p0 = (int64_t)blockIdx.x * (256 * kLinkPer) + threadIdx.x;
-  int32_t ka[kLinkPer], kb[kLinkPer];
+  constexpr int L = kLinkSteps;
+  const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int tw = a.g.tw;
+  const bool temporal = (a.edges & MSF_EDGE_TEMPORAL) != 0;
+  const int nchunk = (tw + L - 1) / L;
+  for (int c = blockIdx.y; c < nchunk; c += gridDim.y) {
+    const int s0 = c * L;
+    const int ns = min(L, tw - s0);          // samples of steps s0 .. s0 + ns - 1
+    const int nk = TRAJ ? min(L + 1, tw - s0) : ns;  // keys of steps s0 .. s0 + nk - 1
+    int32_t key[L + 1];
+    uint32_t comp[L + 1];
 #pragma unroll
-  for (int j = 0; j < kLinkPer; ++j) {
-    const int64_t p = p0 + j * 256;
-    ka[j] = kb[j] = -1;
-    if (p < a.P) {
-      ka[j] = __ldcs(a.key + (int64_t)(a.g.t0 + tw) * a.P + p);
-      if (TRAJ) kb[j] = __ldcs(a.key + (int64_t)(a.g.t0 + tw + 1) * a.P + p);
+    for (int j = 0; j <= L; ++j)
+      key[j] = (p < a.P && j < nk) ? __ldcs(a.key + (int64_t)(a.g.t0 + s0 + j) * a.P + p) : -1;
+#pragma unroll
+    for (int j = 0; j <= L; ++j) {
+      comp[j] = kNoComp;
+      if (key[j] >= 0) {
+        const int64_t cj = comp_of<SPATIAL>(a, s0 + j, key[j]);
+        if (cj >= 0) comp[j] = (uint32_t)cj;
+      }
     }
-  }
-  int64_t ca[kLinkPer], cb[kLinkPer];
+    if (TRAJ) {
 #pragma unroll
-  for (int j = 0; j < kLinkPer; ++j) {
-    ca[j] = ka[j] >= 0 ? comp_of<SPATIAL>(a, tw, ka[j]) : -1;
-    cb[j] = (TRAJ && kb[j] >= 0) ? comp_of<SPATIAL>(a, tw + 1, kb[j]) : -1;
-  }
-  if (TRAJ) {
-#pragma unroll
-    for (int j = 0; j < kLinkPer; ++j)
-      if (ca[j] >= 0 && cb[j] >= 0 && ca[j] != cb[j]) gunion(a.cparent, (uint32_t)ca[j], (uint32_t)cb[j]);
-  }
-  if (COLLECT) {
-    const bool last = TRAJ && tw + 2 == a.g.tw;  // block-uniform
+      for (int j = 0; j < L; ++j) {
+        const bool same_voxel = temporal && key[j] == key[j + 1];
+        if (comp[j] != kNoComp && comp[j + 1] != kNoComp && comp[j] != comp[j + 1] && !same_voxel)
+          gunion(a.cparent, comp[j], comp[j + 1]);
+      }
+    }
+    // samples in member voxel-timesteps: block exclusive scan of the per-thread counts
     int mine = 0;
 #pragma unroll
-    for (int j = 0; j < kLinkPer; ++j) mine += (ca[j] >= 0) + (last && cb[j] >= 0);
-    // block exclusive scan of the per-thread counts
+    for (int j = 0; j < L; ++j) mine += (j < ns && comp[j] != kNoComp);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int x = mine;
 #pragma unroll
@@ -544,28 +616,23 @@ __global__ void __launch_bounds__(256) k_links(const __grid_constant__ SegArgs a
     if (threadIdx.x == 0) {
       int tot = 0;
       for (int k = 0; k < 8; ++k) {
-        const int c = s_cnt[k];
+        const int v = s_cnt[k];
         s_cnt[k] = tot;
-        tot += c;
+        tot += v;
       }
       s_base = tot ? atomicAdd(&a.counters[3], (unsigned long long)tot) : 0ull;
     }
     __syncthreads();
     unsigned long long slot = s_base + s_cnt[w] + x - mine;
 #pragma unroll
-    for (int j = 0; j < kLinkPer; ++j) {
-      const int64_t p = p0 + j * 256;
-      if (ca[j] >= 0) {
-        a.sample_sid[slot] = (int64_t)tw * a.P + p;
-        a.sample_comp[slot] = (uint32_t)ca[j];
-        ++slot;
-      }
-      if (last && cb[j] >= 0) {
-        a.sample_sid[slot] = (int64_t)(tw + 1) * a.P + p;
-        a.sample_comp[slot] = (uint32_t)cb[j];
+    for (int j = 0; j < L; ++j) {
+      if (j < ns && comp[j] != kNoComp) {
+        a.sample_sid[slot] = (int64_t)(s0 + j) * a.P + p;
+        a.sample_comp[slot] = comp[j];
         ++slot;
       }
     }
+    __syncthreads();  // s_cnt / s_base are reused by the next chunk
   }
 }
 
@@ -790,19 +857,23 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
     launch_tile_any(a, spatial, g.ntiles, s);
   }
   MSF_CUDA_TRY(cudaGetLastError());
-  const unsigned nb = (unsigned)((g.nseg + 255) / 256);
   if ((crit->edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0) {
     ScopedKernel k(ctx, "k_hook");
-    if (spatial) k_hook<true><<<nb, 256, 0, s>>>(a);
-    else k_hook<false><<<nb, 256, 0, s>>>(a);
+    if (spatial) k_hook<true><<<g.ntiles, 256, 0, s>>>(a);
+    else k_hook<false><<<g.ntiles, 256, 0, s>>>(a);
   }
   // trajectory joins; the same pass records the window's point samples that lie in a feature
   const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1;
   if (traj) {
+    {
+      ScopedKernel k(ctx, "k_compress");
+      k_compress<<<g.ntiles, 256, 0, s>>>(a);
+    }
     ScopedKernel k(ctx, "k_links");
-    dim3 grid((unsigned)((a.P + 256 * kLinkPer - 1) / (256 * kLinkPer)), (unsigned)(g.tw - 1));
-    if (spatial) k_links<true, true, true><<<grid, 256, 0, s>>>(a);
-    else k_links<false, true, true><<<grid, 256, 0, s>>>(a);
+    const int64_t nchunk = (g.tw + kLinkSteps - 1) / kLinkSteps;
+    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
+    if (spatial) k_links<true, true><<<grid, 256, 0, s>>>(a);
+    else k_links<false, true><<<grid, 256, 0, s>>>(a);
   }
   {
     ScopedKernel k(ctx, "k_flatten");
@@ -992,9 +1063,10 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
     if (!L.samples) {  // no trajectory pass ran: collect the samples now
       MSF_CUDA_TRY(cudaMemsetAsync(a.counters + 3, 0, sizeof(unsigned long long), s));
       ScopedKernel k(ctx, "k_links");
-      dim3 grid((unsigned)((a.P + 256 * kLinkPer - 1) / (256 * kLinkPer)), (unsigned)g.tw);
-      if (spatial) k_links<true, false, true><<<grid, 256, 0, s>>>(a);
-      else k_links<false, false, true><<<grid, 256, 0, s>>>(a);
+      const int64_t nchunk = (g.tw + kLinkSteps - 1) / kLinkSteps;
+      dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
+      if (spatial) k_links<true, false><<<grid, 256, 0, s>>>(a);
+      else k_links<false, false><<<grid, 256, 0, s>>>(a);
       L.samples = true;
     }
     ScopedKernel k(ctx, "k_feat_samples");
@@ -1104,10 +1176,9 @@ int segment_field_fixed(const Geometry& g, int npred, const DevPred& pred, uint3
   MSF_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * 8, s));
   launch_tile_any(a, spatial, g.ntiles, s);
   MSF_CUDA_TRY(cudaGetLastError());
-  const unsigned nb = (unsigned)((g.nseg + 255) / 256);
   if (edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) {
-    if (spatial) k_hook<true><<<nb, 256, 0, s>>>(a);
-    else k_hook<false><<<nb, 256, 0, s>>>(a);
+    if (spatial) k_hook<true><<<g.ntiles, 256, 0, s>>>(a);
+    else k_hook<false><<<g.ntiles, 256, 0, s>>>(a);
   }
   k_flatten<<<g.ntiles, 256, 0, s>>>(a);
   const bool vec = (g.nx & 3) == 0 && ((uintptr_t)labels & 15) == 0;

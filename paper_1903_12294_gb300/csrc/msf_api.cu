@@ -236,7 +236,8 @@ void make_preds(const msf_ctx* ctx, const msf_criteria* c, DevPred* out) {
 }
 
 static int copy_in(DevBuf& dst, const void* src, size_t bytes, int kind, cudaStream_t s) {
-  MSF_TRY(dst.ensure(bytes));
+  // 16 bytes of slack: bulk copies of the last row may round their end up to 16 bytes
+  MSF_TRY(dst.ensure(bytes + 16));
   if (bytes == 0) return MSF_OK;
   MSF_CUDA_TRY(cudaMemcpyAsync(dst.p, src, bytes,
                                kind == MSF_HOST ? cudaMemcpyHostToDevice

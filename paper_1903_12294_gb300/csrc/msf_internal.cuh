@@ -202,6 +202,56 @@ struct ScopedKernel {
   }
 };
 
+// ---------------------------------------------------------------------------------------------
+// bulk asynchronous copies global -> shared (cp.async.bulk, completion on an mbarrier)
+// ---------------------------------------------------------------------------------------------
+// Source and destination 16-byte aligned, size a multiple of 16. Waits are bounded in time: a
+// wait that gives up returns false and the kernel reports MSF_ERR_TIMEOUT through its error
+// word instead of spinning on.
+constexpr long long kWaitCycles = 2000000000ll;  // about one second at the SM clock
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// order earlier generic-proxy accesses of shared memory before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
 // q = round_half_even(v * 2^k) with integer operations only: v = +-man * 2^(exp - 150), so
 // v * 2^k = +-man * 2^sh. Equal to llrint(ldexp((double)v, k)) for every finite fp32 v whose
 // result fits the exponent rule (|q| < 2^62); non-finite v gives 0.
