@@ -46,16 +46,13 @@ struct SegArgs {
   const int32_t* key;
   int64_t P;
   int maxr;  // run slots per tile
-  uint32_t* segmask;
-  uint32_t* segrun;
+  uint2* seg;                    // per segment: (row mask, first run slot)
   uint32_t* runcomp;
   uint32_t* cparent;
   int32_t* cminli;
   int2* tileinfo;  // (runs, components) per tile
   int32_t* labels;
-  unsigned long long* counters;  // [0] features, [1] error flags, [3] samples collected
-  int64_t* sample_sid;           // point samples of the window inside a feature: tw * P + p
-  uint32_t* sample_comp;         // ... and their component
+  unsigned long long* counters;  // [0] features, [1] error flags
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -378,8 +375,7 @@ __device__ __forceinline__ void tile_body(const SegArgs& a, const int tile, cons
   const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
   if (y < g.ny && z < g.nz && tw >= 0 && tw < g.tw) {
     const int64_t gs = (((int64_t)tw * g.nz + z) * g.ny + y) * g.nxs + tc.xs;
-    a.segmask[gs] = m;
-    a.segrun[gs] = rbase + rb;
+    a.seg[gs] = make_uint2(m, rbase + rb);
     uint32_t bits = st;
     for (int j = 0; j < nr; ++j) {
       const int x0 = __ffs(bits) - 1;
@@ -420,17 +416,17 @@ __device__ __forceinline__ int64_t seg_index(const Geometry& g, int tw, int z, i
 // another tile, and the row one step earlier when the segment opens a time chunk. Every join of
 // two components goes through join(c0, c1).
 template <bool SPATIAL, class J>
-__device__ __forceinline__ void hook_seg(const SegArgs& a, int64_t gs, int tw, int z, int y,
-                                         int xs, uint32_t m, J&& join) {
+__device__ __forceinline__ void hook_seg(const SegArgs& a, int tw, int z, int y, int xs,
+                                         uint32_t m, uint32_t rb, J&& join) {
   const Geometry& g = a.g;
   const uint32_t st = run_starts(m, SPATIAL);
-  const uint32_t rb = __ldg(a.segrun + gs);
 
   auto join_rows = [&](int64_t gs2, bool spatial_rows) {
-    const uint32_t m2 = __ldg(a.segmask + gs2);
+    const uint2 e2 = __ldg(a.seg + gs2);
+    const uint32_t m2 = e2.x;
     if (!m2) return;
     const uint32_t st2 = run_starts(m2, SPATIAL);
-    const uint32_t rb2 = __ldg(a.segrun + gs2);
+    const uint32_t rb2 = e2.y;
     row_contacts(m, m2, spatial_rows, SPATIAL, [&](int x1, int x2) {
       const uint32_t c1 = __ldg(a.runcomp + rb + run_index(st, x1));
       const uint32_t c2 = __ldg(a.runcomp + rb2 + run_index(st2, x2));
@@ -447,11 +443,9 @@ __device__ __forceinline__ void hook_seg(const SegArgs& a, int64_t gs, int tw, i
       for (int k = 0; k < 9; ++k) {
         const int z2 = z + k / 3 - 1, y2 = y + k % 3 - 1;
         if (z2 < 0 || z2 >= g.nz || y2 < 0 || y2 >= g.ny) continue;
-        const int64_t gs2 = seg_index(g, tw, z2, y2, xs - 1);
-        const uint32_t m2 = __ldg(a.segmask + gs2);
-        if (!(m2 >> 31)) continue;
-        const uint32_t st2 = run_starts(m2, SPATIAL);
-        const uint32_t c2 = __ldg(a.runcomp + __ldg(a.segrun + gs2) + __popc(st2) - 1);
+        const uint2 e2 = __ldg(a.seg + seg_index(g, tw, z2, y2, xs - 1));
+        if (!(e2.x >> 31)) continue;
+        const uint32_t c2 = __ldg(a.runcomp + e2.y + __popc(run_starts(e2.x, SPATIAL)) - 1);
         if (c2 != c0 && c2 != last) join(c0, c2);
         last = c2;
       }
@@ -475,13 +469,13 @@ template <bool SPATIAL>
 __device__ __forceinline__ void hook_body(const SegArgs& a, const int64_t gs) {
   const Geometry& g = a.g;
   if (gs >= g.nseg) return;
-  const uint32_t m = __ldg(a.segmask + gs);
-  if (!m) return;
+  const uint2 e = __ldg(a.seg + gs);
+  if (!e.x) return;
   uint32_t r, xs, y, z, tw;
   g.fnxs.divmod((uint32_t)gs, r, xs);
   g.fny.divmod(r, r, y);
   g.fnz.divmod(r, tw, z);
-  hook_seg<SPATIAL>(a, gs, (int)tw, (int)z, (int)y, (int)xs, m,
+  hook_seg<SPATIAL>(a, (int)tw, (int)z, (int)y, (int)xs, e.x, e.y,
                     [&](uint32_t c0, uint32_t c1) { gunion(a.cparent, c0, c1); });
 }
 
@@ -519,10 +513,9 @@ __global__ void __launch_bounds__(256, 4) k_hook(const __grid_constant__ SegArgs
   const int y = (tc.ty << g.lby) + ly, z = (tc.tz << g.lbz) + lz;
   const int tw = (tc.tt << g.lbt) + lt - g.toff;
   if (y >= g.ny || z >= g.nz || tw < 0 || tw >= g.tw) return;
-  const int64_t gs = seg_index(g, tw, z, y, tc.xs);
-  const uint32_t m = __ldg(a.segmask + gs);
-  if (!m) return;
-  hook_seg<SPATIAL>(a, gs, tw, z, y, tc.xs, m, [&](uint32_t c0, uint32_t c1) {
+  const uint2 e = __ldg(a.seg + seg_index(g, tw, z, y, tc.xs));
+  if (!e.x) return;
+  hook_seg<SPATIAL>(a, tw, z, y, tc.xs, e.x, e.y, [&](uint32_t c0, uint32_t c1) {
     if (pair_first_seen(s_set, c0, c1)) gunion(a.cparent, c0, c1);
   });
 }
@@ -548,12 +541,10 @@ __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) 
   uint32_t yz, x, z, y;
   g.fnx.divmod((uint32_t)v, yz, x);
   g.fny.divmod(yz, z, y);
-  const int64_t gs = seg_index(g, tw, (int)z, (int)y, (int)(x >> 5));
-  const uint32_t m = __ldg(a.segmask + gs);
+  const uint2 e = __ldg(a.seg + seg_index(g, tw, (int)z, (int)y, (int)(x >> 5)));
   const int b = x & 31;
-  if (!((m >> b) & 1u)) return -1;
-  const uint32_t st = run_starts(m, SPATIAL);
-  return __ldg(a.runcomp + __ldg(a.segrun + gs) + run_index(st, b));
+  if (!((e.x >> b) & 1u)) return -1;
+  return __ldg(a.runcomp + e.y + run_index(run_starts(e.x, SPATIAL), b));
 }
 
 // One thread per point and chunk of kLinkSteps window steps: the point's voxel keys at those
@@ -561,29 +552,26 @@ __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) 
 // once, so each key serves both the link ending and the link starting at its step. Links join
 // the components of key[t][p] and key[t+1][p] when both are members; a point that stays in one
 // voxel needs no join when temporal edges are on (the temporal edge already joins the two
-// voxel-timesteps). Every sample that lies in a member voxel-timestep is recorded for the point
-// part of the features, compacted per block with one atomic.
+// voxel-timesteps).
 constexpr int kLinkPer = 4;     // points per thread in the batched pass
 constexpr int kLinkSteps = 8;   // window steps per thread in the single-query pass
 
-template <bool SPATIAL, bool TRAJ>
+template <bool SPATIAL>
 __global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArgs a) {
-  __shared__ int s_cnt[8];
-  __shared__ unsigned long long s_base;
   constexpr int L = kLinkSteps;
   const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (p >= a.P) return;
   const int tw = a.g.tw;
   const bool temporal = (a.edges & MSF_EDGE_TEMPORAL) != 0;
-  const int nchunk = (tw + L - 1) / L;
+  const int nchunk = (tw - 1 + L - 1) / L;  // chunks of links (t, t+1), t < tw - 1
   for (int c = blockIdx.y; c < nchunk; c += gridDim.y) {
     const int s0 = c * L;
-    const int ns = min(L, tw - s0);          // samples of steps s0 .. s0 + ns - 1
-    const int nk = TRAJ ? min(L + 1, tw - s0) : ns;  // keys of steps s0 .. s0 + nk - 1
+    const int nk = min(L + 1, tw - s0);      // keys of steps s0 .. s0 + nk - 1
     int32_t key[L + 1];
     uint32_t comp[L + 1];
 #pragma unroll
     for (int j = 0; j <= L; ++j)
-      key[j] = (p < a.P && j < nk) ? __ldcs(a.key + (int64_t)(a.g.t0 + s0 + j) * a.P + p) : -1;
+      key[j] = j < nk ? __ldcs(a.key + (int64_t)(a.g.t0 + s0 + j) * a.P + p) : -1;
 #pragma unroll
     for (int j = 0; j <= L; ++j) {
       comp[j] = kNoComp;
@@ -592,47 +580,12 @@ __global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArg
         if (cj >= 0) comp[j] = (uint32_t)cj;
       }
     }
-    if (TRAJ) {
-#pragma unroll
-      for (int j = 0; j < L; ++j) {
-        const bool same_voxel = temporal && key[j] == key[j + 1];
-        if (comp[j] != kNoComp && comp[j + 1] != kNoComp && comp[j] != comp[j + 1] && !same_voxel)
-          gunion(a.cparent, comp[j], comp[j + 1]);
-      }
-    }
-    // samples in member voxel-timesteps: block exclusive scan of the per-thread counts
-    int mine = 0;
-#pragma unroll
-    for (int j = 0; j < L; ++j) mine += (j < ns && comp[j] != kNoComp);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_cnt[w] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int k = 0; k < 8; ++k) {
-        const int v = s_cnt[k];
-        s_cnt[k] = tot;
-        tot += v;
-      }
-      s_base = tot ? atomicAdd(&a.counters[3], (unsigned long long)tot) : 0ull;
-    }
-    __syncthreads();
-    unsigned long long slot = s_base + s_cnt[w] + x - mine;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-      if (j < ns && comp[j] != kNoComp) {
-        a.sample_sid[slot] = (int64_t)(s0 + j) * a.P + p;
-        a.sample_comp[slot] = comp[j];
-        ++slot;
-      }
+      const bool same_voxel = temporal && key[j] == key[j + 1];
+      if (comp[j] != kNoComp && comp[j + 1] != kNoComp && comp[j] != comp[j + 1] && !same_voxel)
+        gunion(a.cparent, comp[j], comp[j + 1]);
     }
-    __syncthreads();  // s_cnt / s_base are reused by the next chunk
   }
 }
 
@@ -690,8 +643,9 @@ __device__ __forceinline__ void final_body(const SegArgs& a, const int tile, int
     uint32_t mm = 0, rr = 0;
     if (nrun && y < g.ny && z < g.nz && tw >= 0 && tw < g.tw) {
       const int64_t gs = seg_index(g, tw, z, y, tc.xs);
-      mm = __ldcg(a.segmask + gs);
-      rr = __ldcg(a.segrun + gs) - rbase;
+      const uint2 e = __ldcg(a.seg + gs);
+      mm = e.x;
+      rr = e.y - rbase;
     }
     s_mask[s] = mm;
     s_rb[s] = rr;
@@ -810,27 +764,18 @@ static int seg_args(msf_ctx* ctx, const Geometry& g, bool spatial, SegArgs* a) {
   a->P = ctx->ds.P;
   a->maxr = kSegPerTile * (spatial ? 16 : 32);
   SegScratch& S = ctx->seg;
-  MSF_TRY(S.segmask.ensure(sizeof(uint32_t) * g.nseg));
-  MSF_TRY(S.segrun.ensure(sizeof(uint32_t) * g.nseg));
+  MSF_TRY(S.seg.ensure(sizeof(uint2) * g.nseg));
   MSF_TRY(S.runcomp.ensure(sizeof(uint32_t) * (size_t)g.ntiles * a->maxr));
   MSF_TRY(S.cparent.ensure(sizeof(uint32_t) * (size_t)g.ntiles * g.cmax));
   MSF_TRY(S.cminli.ensure(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
   MSF_TRY(S.tileinfo.ensure(sizeof(int2) * (size_t)g.ntiles));
   MSF_TRY(S.counters.ensure(sizeof(unsigned long long) * 8));
-  a->segmask = S.segmask.as<uint32_t>();
-  a->segrun = S.segrun.as<uint32_t>();
+  a->seg = S.seg.as<uint2>();
   a->runcomp = S.runcomp.as<uint32_t>();
   a->cparent = S.cparent.as<uint32_t>();
   a->cminli = S.cminli.as<int32_t>();
   a->tileinfo = S.tileinfo.as<int2>();
   a->counters = S.counters.as<unsigned long long>();
-  if (a->P > 0) {
-    const size_t ns = (size_t)a->P * (size_t)g.tw;
-    MSF_TRY(ctx->last.sample_sid.ensure(sizeof(int64_t) * ns));
-    MSF_TRY(ctx->last.sample_comp.ensure(sizeof(uint32_t) * ns));
-    a->sample_sid = ctx->last.sample_sid.as<int64_t>();
-    a->sample_comp = ctx->last.sample_comp.as<uint32_t>();
-  }
   return MSF_OK;
 }
 
@@ -862,7 +807,7 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
     if (spatial) k_hook<true><<<g.ntiles, 256, 0, s>>>(a);
     else k_hook<false><<<g.ntiles, 256, 0, s>>>(a);
   }
-  // trajectory joins; the same pass records the window's point samples that lie in a feature
+  // trajectory joins
   const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1;
   if (traj) {
     {
@@ -870,10 +815,10 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
       k_compress<<<g.ntiles, 256, 0, s>>>(a);
     }
     ScopedKernel k(ctx, "k_links");
-    const int64_t nchunk = (g.tw + kLinkSteps - 1) / kLinkSteps;
+    const int64_t nchunk = (g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
     dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
-    if (spatial) k_links<true, true><<<grid, 256, 0, s>>>(a);
-    else k_links<false, true><<<grid, 256, 0, s>>>(a);
+    if (spatial) k_links<true><<<grid, 256, 0, s>>>(a);
+    else k_links<false><<<grid, 256, 0, s>>>(a);
   }
   {
     ScopedKernel k(ctx, "k_flatten");
@@ -906,7 +851,6 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   L.g = g;
   L.maxr = a.maxr;
   L.n_features = (int64_t)h[0];
-  L.samples = traj;
   return MSF_OK;
 }
 
@@ -984,8 +928,9 @@ __global__ void __launch_bounds__(256) k_feat_vox(const __grid_constant__ SegArg
     uint32_t mm = 0, rr = 0;
     if (y < g.ny && z < g.nz && tw >= 0 && tw < g.tw) {
       const int64_t gs = seg_index(g, tw, z, y, tc.xs);
-      mm = __ldg(a.segmask + gs);
-      rr = __ldg(a.segrun + gs) - rbase;
+      const uint2 e = __ldg(a.seg + gs);
+      mm = e.x;
+      rr = e.y - rbase;
     }
     s_mask[sg] = mm;
     s_rb[sg] = rr;
@@ -1007,25 +952,63 @@ __global__ void __launch_bounds__(256) k_feat_vox(const __grid_constant__ SegArg
   }
 }
 
-// Point statistics from the sample list (grid-stride up to the device-side sample count; the
-// loop bound is warp-uniform so that every lane takes part in the warp-level reduction).
-__global__ void __launch_bounds__(256) k_feat_samples(const __grid_constant__ SegArgs a,
-                                                      FeatAcc acc,
-                                                      const int32_t* __restrict__ cfid,
-                                                      const float* __restrict__ attr) {
-  const int64_t n = (int64_t)*(volatile unsigned long long*)&a.counters[3];
-  const int lane = threadIdx.x & 31;
-  const int64_t wbase = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31));
-  for (int64_t b = wbase; b < n; b += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = b + lane;
-    int64_t fid = -1, tw = 0, p = 0;
-    if (i < n) {
-      const int64_t sid = a.sample_sid[i];
-      fid = __ldg(cfid + a.sample_comp[i]);
-      tw = sid / a.P;
-      p = sid - tw * a.P;
+// Point statistics: one thread per point and chunk of kLinkSteps window steps, (step, point)
+// in order so that keys are read coalesced; a sample counts for the feature of the component
+// of its voxel-timestep, if that is a member. Each warp packs its member samples into shared
+// memory and reduces them 32 at a time (the warp-level reduction wants full warps).
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256, 4) k_feat_points(const __grid_constant__ SegArgs a,
+                                                        FeatAcc acc,
+                                                        const int32_t* __restrict__ cfid,
+                                                        const float* __restrict__ attr) {
+  constexpr int L = kLinkSteps;
+  __shared__ int2 s_buf[8][32 * L];  // per warp: (feature, step * 32 + lane)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t pbase = (int64_t)blockIdx.x * 256 + w * 32;
+  const int64_t p = pbase + lane;
+  const bool in = p < a.P;
+  const int tw = a.g.tw;
+  const int nchunk = (tw + L - 1) / L;
+  for (int c = blockIdx.y; c < nchunk; c += gridDim.y) {
+    const int s0 = c * L;
+    int32_t key[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      key[j] = (in && s0 + j < tw) ? __ldcs(a.key + (int64_t)(a.g.t0 + s0 + j) * a.P + p) : -1;
+    int32_t fid[L];
+    int n = 0;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      fid[j] = -1;
+      if (key[j] >= 0) {
+        const int64_t cj = comp_of<SPATIAL>(a, s0 + j, key[j]);
+        if (cj >= 0) fid[j] = __ldg(cfid + cj);
+      }
+      n += fid[j] >= 0;
     }
-    accumulate_samples(acc, fid >= 0, fid, attr + ((int64_t)(a.g.t0 + tw) * acc.A) * a.P + p, a.P);
+    // warp exclusive scan of the member counts -> packed positions
+    int x = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    int pos = x - n;
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      if (fid[j] >= 0) s_buf[w][pos++] = make_int2(fid[j], (j << 5) | lane);
+    __syncwarp();
+    for (int b = 0; b < total; b += 32) {
+      const int i = b + lane;
+      const bool ok = i < total;
+      const int2 e = ok ? s_buf[w][i] : make_int2(-1, 0);
+      const int j = e.y >> 5;
+      accumulate_samples(acc, ok, e.x,
+                         attr + ((int64_t)(a.g.t0 + s0 + j) * acc.A) * a.P + pbase + (e.y & 31),
+                         a.P);
+    }
+    __syncwarp();
   }
 }
 
@@ -1060,17 +1043,11 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
     else k_feat_vox<false><<<g.ntiles, 256, 0, s>>>(a, acc, cfid, d.field.as<float>(), d.count.as<int32_t>());
   }
   if (a.P > 0 && d.A > 0) {
-    if (!L.samples) {  // no trajectory pass ran: collect the samples now
-      MSF_CUDA_TRY(cudaMemsetAsync(a.counters + 3, 0, sizeof(unsigned long long), s));
-      ScopedKernel k(ctx, "k_links");
-      const int64_t nchunk = (g.tw + kLinkSteps - 1) / kLinkSteps;
-      dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
-      if (spatial) k_links<true, false><<<grid, 256, 0, s>>>(a);
-      else k_links<false, false><<<grid, 256, 0, s>>>(a);
-      L.samples = true;
-    }
-    ScopedKernel k(ctx, "k_feat_samples");
-    k_feat_samples<<<ctx->sm_count * 8, 256, 0, s>>>(a, acc, cfid, d.attr.as<float>());
+    ScopedKernel k(ctx, "k_feat_points");
+    const int64_t nchunk = (g.tw + kLinkSteps - 1) / kLinkSteps;
+    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
+    if (spatial) k_feat_points<true><<<grid, 256, 0, s>>>(a, acc, cfid, d.attr.as<float>());
+    else k_feat_points<false><<<grid, 256, 0, s>>>(a, acc, cfid, d.attr.as<float>());
   }
   MSF_CUDA_TRY(cudaGetLastError());
   return MSF_OK;
@@ -1128,7 +1105,7 @@ static size_t up256(size_t n) { return (n + 255) & ~size_t(255); }
 
 size_t fixed_scratch_bytes(const Geometry& g, bool spatial) {
   const size_t maxr = (size_t)kSegPerTile * (spatial ? 16 : 32);
-  return 2 * up256(sizeof(uint32_t) * (size_t)g.nseg) +
+  return up256(sizeof(uint2) * (size_t)g.nseg) +
          up256(sizeof(uint32_t) * (size_t)g.ntiles * maxr) +
          2 * up256(sizeof(uint32_t) * (size_t)g.ntiles * (size_t)g.cmax) +
          up256(sizeof(int2) * (size_t)g.ntiles) + up256(sizeof(unsigned long long) * 8);
@@ -1142,8 +1119,7 @@ void fixed_scratch_carve(void* base, const Geometry& g, bool spatial, FixedScrat
     p += up256(n);
     return q;
   };
-  o->segmask = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)g.nseg));
-  o->segrun = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)g.nseg));
+  o->seg = reinterpret_cast<uint2*>(take(sizeof(uint2) * (size_t)g.nseg));
   o->runcomp = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)g.ntiles * maxr));
   o->cparent = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)g.ntiles * g.cmax));
   o->cminli = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
@@ -1163,8 +1139,7 @@ int segment_field_fixed(const Geometry& g, int npred, const DevPred& pred, uint3
   a.key = nullptr;
   a.P = 0;
   a.maxr = kSegPerTile * (spatial ? 16 : 32);
-  a.segmask = S.segmask;
-  a.segrun = S.segrun;
+  a.seg = S.seg;
   a.runcomp = S.runcomp;
   a.cparent = S.cparent;
   a.cminli = S.cminli;
@@ -1620,8 +1595,7 @@ int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* 
       FixedScratch S;
       fixed_scratch_carve(scratch[q], gr.args[i].g, gr.spatial, &S);
       SegArgs& a = gr.args[i];
-      a.segmask = S.segmask;
-      a.segrun = S.segrun;
+      a.seg = S.seg;
       a.runcomp = S.runcomp;
       a.cparent = S.cparent;
       a.cminli = S.cminli;

@@ -291,7 +291,7 @@ void msf_destroy(msf_ctx* c) {
   cudaStreamSynchronize(c->stream);
   Dataset& d = c->ds;
   for (DevBuf* b : {&d.field, &d.pos, &d.attr, &d.key, &d.count, &d.mean, &d.sumq}) b->release();
-  for (DevBuf* b : {&c->seg.segmask, &c->seg.segrun, &c->seg.runcomp, &c->seg.cparent,
+  for (DevBuf* b : {&c->seg.seg, &c->seg.runcomp, &c->seg.cparent,
                     &c->seg.cminli, &c->seg.tileinfo, &c->seg.counters})
     b->release();
   for (DevBuf* b : {&c->feat.rootbits, &c->feat.wordrank, &c->feat.blocksums, &c->feat.acc,
@@ -300,7 +300,7 @@ void msf_destroy(msf_ctx* c) {
   for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.rec_v, &c->bin.rec_a,
                     &c->bin.absmax, &c->bin.outside, &c->bin.scan_tmp, &c->bin.total})
     b->release();
-  for (DevBuf* b : {&c->last.sample_sid, &c->last.sample_comp, &c->last.cfid}) b->release();
+  c->last.cfid.release();
   c->host_staging.release();
   c->batch.release();
   c->timer.release();

@@ -110,7 +110,7 @@ struct DevPred {
 };
 
 struct SegScratch {
-  DevBuf segmask, segrun, runcomp, cparent, cminli, tileinfo, counters;
+  DevBuf seg, runcomp, cparent, cminli, tileinfo, counters;
 };
 
 struct FeatScratch {
@@ -118,8 +118,7 @@ struct FeatScratch {
 };
 
 // What msf_segment leaves behind for msf_extract_features: the compact segmentation of one
-// query (row masks, runs, component table in SegScratch), the buffers its labels went to, and
-// the point samples of the window that fell in a feature (sample id tw*P + p, component).
+// query (row masks, runs, component table in SegScratch) and the buffers its labels went to.
 struct SegState {
   bool valid = false;
   msf_criteria crit{};
@@ -128,8 +127,7 @@ struct SegState {
   Geometry g{};
   int maxr = 0;
   int64_t n_features = 0;
-  bool samples = false;               // sample list complete for this query
-  DevBuf sample_sid, sample_comp, cfid;
+  DevBuf cfid;                        // feature index of every component
 };
 
 // Device arena and pinned host staging of msf_segment_batch (grow-only).
@@ -502,8 +500,7 @@ int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels_d
 // entry point: the window is the caller's field of tw steps, one optional field predicate,
 // spatial/temporal edges only. No allocation, no timing.
 struct FixedScratch {
-  uint32_t* segmask;
-  uint32_t* segrun;
+  uint2* seg;                    // [nseg] (row mask, first run slot)
   uint32_t* runcomp;
   uint32_t* cparent;
   int32_t* cminli;
