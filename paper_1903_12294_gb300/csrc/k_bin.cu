@@ -37,6 +37,7 @@ int scan_exclusive_u32(msf_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t 
                        uint32_t* total);
 
 constexpr int kBinPer = 4;             // samples per thread in the per-sample passes
+constexpr int kBinNT = 512;            // threads per CTA of the sort and reduce passes
 constexpr int kBinBlock = 256 * kBinPer;
 constexpr int kHistSmem = 8192;        // buckets counted in shared memory (else global atomics)
 
@@ -194,7 +195,7 @@ constexpr int kPlaceStage = kPlaceChunk + 8;   // staged elements per array (ali
 constexpr int kPlaceSmemMax = 200 * 1024;
 
 template <int A>
-__global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
+__global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
   extern __shared__ __align__(16) uint32_t s_place[];
   int32_t* s_key = reinterpret_cast<int32_t*>(s_place);                   // [kPlaceStage]
   float* s_att = reinterpret_cast<float*>(s_place + kPlaceStage);          // [A][kPlaceStage]
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant_
   uint32_t* s_lpos = s_delta + b.nb;                                       // [nb] fill cursor
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned s_max[A > 0 ? A : 1];
-  __shared__ int s_warp[8];
+  __shared__ int s_warp[kBinNT / 32];
   __shared__ int s_n;
   const int t = blockIdx.y, blk = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant_
     }
   }
   // the block's slot ranges and bucket counts (overlapping the copies)
-  for (int i = threadIdx.x; i < b.nb; i += 256) {
+  for (int i = threadIdx.x; i < b.nb; i += kBinNT) {
     s_delta[i] = b.offs[((int64_t)t * b.nb + i) * b.nblk + blk];
     s_lpos[i] = b.hist[((int64_t)t * b.nb + i) * b.nblk + blk];  // counts, scanned below
   }
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant_
   // exclusive scan of the block's bucket counts (one thread per chunk of buckets); s_delta
   // becomes global slot minus local position
   {
-    const int per = (b.nb + 255) / 256;
+    const int per = (b.nb + kBinNT - 1) / kBinNT;
     const int lo = threadIdx.x * per, hi = min(lo + per, b.nb);
     int tot = 0;
     for (int i = lo; i < hi; ++i) tot += (int)s_lpos[i];
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant_
     __syncthreads();
     int run = x - tot;
     for (int k = 0; k < w; ++k) run += s_warp[k];
-    if (threadIdx.x == 255) s_n = run + tot;
+    if (threadIdx.x == kBinNT - 1) s_n = run + tot;
     for (int i = lo; i < hi; ++i) {
       const int c = (int)s_lpos[i];
       s_lpos[i] = (uint32_t)run;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant_
   unsigned lmax[A > 0 ? A : 1];
 #pragma unroll
   for (int a = 0; a < A; ++a) lmax[a] = 0u;
-  for (int i = threadIdx.x; i < n; i += 256) {
+  for (int i = threadIdx.x; i < n; i += kBinNT) {
     const int32_t k = s_key[hk + i];
     if (k >= 0) {
       const uint32_t pos = atomicAdd(s_lpos + (k >> b.logR), 1u);
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant_
 #pragma unroll
   for (int a = 0; a < A; ++a) {
     const int ha = (int)((((int64_t)t * A + a) * b.P + pbeg) & 3);
-    for (int i = threadIdx.x; i < n; i += 256) {
+    for (int i = threadIdx.x; i < n; i += kBinNT) {
       const float v = s_att[a * kPlaceStage + ha + i];
       if (isfinite(v)) lmax[a] = max(lmax[a], __float_as_uint(fabsf(v)));
     }
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(256) k_bin_place_sorted(const __grid_constant_
   // runs out: local position j of bucket bk goes to slot s_delta[bk] + j
   const int nr = s_n;
   const uint32_t vmask = (1u << b.logR) - 1u;
-  for (int j = threadIdx.x; j < nr; j += 256) {
+  for (int j = threadIdx.x; j < nr; j += kBinNT) {
     const int i = s_inv[j];
     const int32_t k = s_key[hk + i];
     const uint32_t slot = s_delta[k >> b.logR] + (uint32_t)j;
@@ -364,7 +365,7 @@ __device__ __forceinline__ void reduce_issue(const BinArgs& b, uint32_t a0, uint
 }
 
 template <int A, bool KEEP>
-__global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinArgs b) {
+__global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant__ BinArgs b) {
   extern __shared__ __align__(16) unsigned long long s_dyn64[];
   const int R = 1 << b.logR;
   unsigned long long* s_sum = s_dyn64;                                    // [A][R]
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinA
   {
     uint4* z = reinterpret_cast<uint4*>(s_dyn64);
     const int n16 = (int)(((size_t)A * R * 8 + (size_t)R * 4) / 16);
-    for (int i = threadIdx.x; i < n16; i += 256) z[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < n16; i += kBinNT) z[i] = make_uint4(0, 0, 0, 0);
   }
   if (threadIdx.x < A) {
     const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.P * b.T);
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinA
     }
     const uint32_t a0 = s0 + (uint32_t)piece * (uint32_t)R;
     const int m = (int)min((uint32_t)R, e1 - a0);
-    for (int i = threadIdx.x; i < m; i += 256) {
+    for (int i = threadIdx.x; i < m; i += kBinNT) {
       const uint32_t r = a0 + (uint32_t)i;
       if (r < r0 || r >= r1) continue;  // alignment slack of the neighbouring buckets
       const uint32_t v = s_stv[i];
@@ -433,21 +434,18 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinA
       reduce_issue<A>(b, a1, min((uint32_t)R, e1 - a1), s_stv, s_sta, R, &s_bar);
     }
   }
-  // means: NaN everywhere, then the non-empty voxels (listed, warp-aggregated) get theirs
+  // means of the non-empty voxels (listed, warp-aggregated); empty voxels get NaN at the store
   const int64_t vbase = (int64_t)bucket << b.logR;
   const int nv = (int)min((int64_t)R, b.V - vbase);
   const float qnan = __int_as_float(0x7fc00000);
   const int lane = threadIdx.x & 31;
-  for (int i0 = 0; i0 < R; i0 += 1024) {
+  for (int i0 = 0; i0 < R; i0 += 4 * kBinNT) {
     const int i = i0 + 4 * threadIdx.x;
     unsigned nz = 0;
     uint32_t c[4] = {0u, 0u, 0u, 0u};
     if (i < R) {
       const uint4 c4 = *reinterpret_cast<const uint4*>(s_cnt + i);
       c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
-#pragma unroll
-      for (int a = 0; a < A; ++a)
-        *reinterpret_cast<float4*>(s_mean + (size_t)a * R + i) = make_float4(qnan, qnan, qnan, qnan);
 #pragma unroll
       for (int e = 0; e < 4; ++e) nz += (c[e] != 0u);
     }
@@ -466,7 +464,7 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinA
   }
   __syncthreads();
   const int nl = s_nlist;
-  for (int j = threadIdx.x; j < nl; j += 256) {
+  for (int j = threadIdx.x; j < nl; j += kBinNT) {
     const int i = (int)s_list[j];
     const int c = (int)s_cnt[i];
 #pragma unroll
@@ -478,15 +476,17 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinA
   __syncthreads();
   // one store of every output word: count, means (and sums), four voxels per thread
   if ((b.V & 3) == 0) {
-    for (int i = 4 * threadIdx.x; i < nv; i += 1024) {
+    for (int i = 4 * threadIdx.x; i < nv; i += 4 * kBinNT) {
       const int64_t v = vbase + i;
-      __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v),
-             *reinterpret_cast<const uint4*>(s_cnt + i));
+      const uint4 c4 = *reinterpret_cast<const uint4*>(s_cnt + i);
+      __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v), c4);
 #pragma unroll
       for (int a = 0; a < A; ++a) {
         const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
+        const float4 m4 = *reinterpret_cast<const float4*>(s_mean + (size_t)a * R + i);
         __stcs(reinterpret_cast<float4*>(b.mean + o),
-               *reinterpret_cast<const float4*>(s_mean + (size_t)a * R + i));
+               make_float4(c4.x ? m4.x : qnan, c4.y ? m4.y : qnan, c4.z ? m4.z : qnan,
+                           c4.w ? m4.w : qnan));
         if (KEEP) {
           const unsigned long long* sq = s_sum + (size_t)a * R + i;
           __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2((long long)sq[0], (long long)sq[1]));
@@ -495,13 +495,14 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const __grid_constant__ BinA
       }
     }
   } else {
-    for (int i = threadIdx.x; i < nv; i += 256) {
+    for (int i = threadIdx.x; i < nv; i += kBinNT) {
       const int64_t v = vbase + i;
-      __stcs(b.count + (int64_t)t * b.V + v, (int)s_cnt[i]);
+      const uint32_t c = s_cnt[i];
+      __stcs(b.count + (int64_t)t * b.V + v, (int)c);
 #pragma unroll
       for (int a = 0; a < A; ++a) {
         const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
-        __stcs(b.mean + o, s_mean[(size_t)a * R + i]);
+        __stcs(b.mean + o, c ? s_mean[(size_t)a * R + i] : qnan);
         if (KEEP) __stcs(b.sumq + o, (long long)s_sum[(size_t)a * R + i]);
       }
     }
@@ -539,7 +540,7 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
                              kPlaceSmemMax);
         set = true;
       }
-      k_bin_place_sorted<A><<<gs, 256, place_smem(A, b.nb), s>>>(b);
+      k_bin_place_sorted<A><<<gs, kBinNT, place_smem(A, b.nb), s>>>(b);
     } else {
       k_bin_place_atomic<A><<<gs, 256, 0, s>>>(b);
     }
@@ -553,14 +554,14 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
         cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         set = true;
       }
-      k_bin_reduce<A, true><<<gr, 256, sm, s>>>(b);
+      k_bin_reduce<A, true><<<gr, kBinNT, sm, s>>>(b);
     } else {
       static bool set = false;
       if (!set) {
         cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         set = true;
       }
-      k_bin_reduce<A, false><<<gr, 256, sm, s>>>(b);
+      k_bin_reduce<A, false><<<gr, kBinNT, sm, s>>>(b);
     }
   }
 }

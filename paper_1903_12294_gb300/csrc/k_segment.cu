@@ -16,7 +16,6 @@
 //   k_hook     one CTA per tile, one thread per segment: joins components across the tile's
 //              lower faces (x, y, z and the t-chunk boundary) with a global union-find on the
 //              component table, each distinct component pair once per tile.
-//   k_compress one CTA per tile: points every component at its root before the trajectory pass.
 //   k_links    one thread per (point, chunk of 8 steps): joins the components of key[t][p] and
 //              key[t+1][p], and records the point samples that fall in member voxel-timesteps.
 //   k_flatten  one CTA per tile: path-compresses every component to its root and reduces the
@@ -520,18 +519,6 @@ __global__ void __launch_bounds__(256, 4) k_hook(const __grid_constant__ SegArgs
   });
 }
 
-// Point every component of a tile straight at its root (no joins run concurrently), so that
-// the finds of the trajectory pass start one step from a root.
-__global__ void __launch_bounds__(256) k_compress(const __grid_constant__ SegArgs a) {
-  const int nc = min(a.tileinfo[blockIdx.x].y, a.g.cmax);
-  const uint32_t cbase = (uint32_t)blockIdx.x * (uint32_t)a.g.cmax;
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-    const uint32_t c = cbase + k;
-    const uint32_t r = gfind(a.cparent, c);
-    if (r != c) a.cparent[c] = r;
-  }
-}
-
 // ---------------------------------------------------------------------------------------------
 // k_links: trajectory links and the point samples of the features
 // ---------------------------------------------------------------------------------------------
@@ -802,24 +789,23 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
     launch_tile_any(a, spatial, g.ntiles, s);
   }
   MSF_CUDA_TRY(cudaGetLastError());
+  // cross-tile joins and trajectory joins touch only the union-find and commute: they run
+  // side by side, the trajectory pass on the auxiliary stream
+  const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1;
+  if (traj) {
+    MSF_TRY(ctx_fork(ctx));
+    ScopedKernel k(ctx, "k_links", ctx->aux);
+    const int64_t nchunk = (g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
+    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
+    if (spatial) k_links<true><<<grid, 256, 0, ctx->aux>>>(a);
+    else k_links<false><<<grid, 256, 0, ctx->aux>>>(a);
+  }
   if ((crit->edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0) {
     ScopedKernel k(ctx, "k_hook");
     if (spatial) k_hook<true><<<g.ntiles, 256, 0, s>>>(a);
     else k_hook<false><<<g.ntiles, 256, 0, s>>>(a);
   }
-  // trajectory joins
-  const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1;
-  if (traj) {
-    {
-      ScopedKernel k(ctx, "k_compress");
-      k_compress<<<g.ntiles, 256, 0, s>>>(a);
-    }
-    ScopedKernel k(ctx, "k_links");
-    const int64_t nchunk = (g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
-    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
-    if (spatial) k_links<true><<<grid, 256, 0, s>>>(a);
-    else k_links<false><<<grid, 256, 0, s>>>(a);
-  }
+  if (traj) MSF_TRY(ctx_join(ctx));
   {
     ScopedKernel k(ctx, "k_flatten");
     k_flatten<<<g.ntiles, 256, 0, s>>>(a);
@@ -1037,18 +1023,23 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
     ScopedKernel k(ctx, "k_comp_fid");
     k_comp_fid<<<g.ntiles, 256, 0, s>>>(a, rk, cfid);
   }
+  // voxel and point statistics only add into the accumulators: the point pass runs beside the
+  // voxel pass on the auxiliary stream
+  const bool points = a.P > 0 && d.A > 0;
+  if (points) {
+    MSF_TRY(ctx_fork(ctx));
+    ScopedKernel k(ctx, "k_feat_points", ctx->aux);
+    const int64_t nchunk = (g.tw + kLinkSteps - 1) / kLinkSteps;
+    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
+    if (spatial) k_feat_points<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
+    else k_feat_points<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
+  }
   {
     ScopedKernel k(ctx, "k_feat_vox");
     if (spatial) k_feat_vox<true><<<g.ntiles, 256, 0, s>>>(a, acc, cfid, d.field.as<float>(), d.count.as<int32_t>());
     else k_feat_vox<false><<<g.ntiles, 256, 0, s>>>(a, acc, cfid, d.field.as<float>(), d.count.as<int32_t>());
   }
-  if (a.P > 0 && d.A > 0) {
-    ScopedKernel k(ctx, "k_feat_points");
-    const int64_t nchunk = (g.tw + kLinkSteps - 1) / kLinkSteps;
-    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
-    if (spatial) k_feat_points<true><<<grid, 256, 0, s>>>(a, acc, cfid, d.attr.as<float>());
-    else k_feat_points<false><<<grid, 256, 0, s>>>(a, acc, cfid, d.attr.as<float>());
-  }
+  if (points) MSF_TRY(ctx_join(ctx));
   MSF_CUDA_TRY(cudaGetLastError());
   return MSF_OK;
 }

@@ -107,6 +107,23 @@ void KernelTimer::release() {
   next_event = 0;
 }
 
+int ctx_fork(msf_ctx* ctx) {
+  if (!ctx->aux) {
+    MSF_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    MSF_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    MSF_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  }
+  MSF_CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  MSF_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+  return MSF_OK;
+}
+
+int ctx_join(msf_ctx* ctx) {
+  MSF_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
+  MSF_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  return MSF_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // query checks and geometry
 // ---------------------------------------------------------------------------------------------
@@ -304,6 +321,12 @@ void msf_destroy(msf_ctx* c) {
   c->host_staging.release();
   c->batch.release();
   c->timer.release();
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    cudaStreamDestroy(c->aux);
+    cudaEventDestroy(c->ev_fork);
+    cudaEventDestroy(c->ev_join);
+  }
   delete c;
 }
 

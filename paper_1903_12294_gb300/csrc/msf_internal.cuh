@@ -181,6 +181,10 @@ struct msf_ctx {
   int tile_by = 0, tile_bz = 0, tile_bt = 0;
   msf::KernelTimer timer;
   std::atomic<int> servers{0};  // query servers attached (the dataset is frozen meanwhile)
+  // a second stream for passes that are independent of each other (forked from and joined
+  // back into the context stream with events; created on first use)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace msf {
@@ -190,15 +194,22 @@ struct ScopedKernel {
   msf_ctx* ctx;
   cudaEvent_t a = nullptr, b = nullptr;
   int rec = -1;
-  // timed = false for launches on a stream other than the context's (the timer's events are
-  // recorded on the context stream)
-  ScopedKernel(msf_ctx* c, const char* name, bool timed = true) : ctx(c) {
-    if (timed && ctx->timer.enabled) ctx->timer.begin(name, ctx->stream, &a, &b, &rec);
+  cudaStream_t st;
+  // timed = false for launches that must not be timed (a stream the context does not order)
+  ScopedKernel(msf_ctx* c, const char* name, bool timed = true) : ScopedKernel(c, name, c->stream, timed) {}
+  // a launch on stream s (the context stream or its auxiliary stream): events go on s
+  ScopedKernel(msf_ctx* c, const char* name, cudaStream_t s, bool timed = true) : ctx(c), st(s) {
+    if (timed && ctx->timer.enabled) ctx->timer.begin(name, st, &a, &b, &rec);
   }
   ~ScopedKernel() {
-    if (b) cudaEventRecord(b, ctx->stream);
+    if (b) cudaEventRecord(b, st);
   }
 };
+
+// Fork: work enqueued on ctx->aux after this runs after everything already on ctx->stream.
+// Join: work enqueued on ctx->stream after this runs after everything enqueued on ctx->aux.
+int ctx_fork(msf_ctx* ctx);
+int ctx_join(msf_ctx* ctx);
 
 // ---------------------------------------------------------------------------------------------
 // bulk asynchronous copies global -> shared (cp.async.bulk, completion on an mbarrier)
