@@ -125,23 +125,17 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_1903_12294_gb300 import build as libbuild
-    from paper_1903_12294_gb300 import msf, synth
+    from paper_1903_12294_gb300 import msf, replicas, synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replicas.layout()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if rank == 0:
         libbuild.build()
-    if world > 1:
-        dist.barrier()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = replicas.barrier
+    barrier()
 
     wl = synth.make(args.config, device=dev)
     T, nz, ny, nx = wl.field.shape
@@ -188,11 +182,8 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     ktimes = ctx.kernel_times(reset=True)
     ctx.profiling(False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * vt / (ms * 1e-3) / 1e9
+    ms = replicas.max_over_ranks(ms, dev)
+    value = replicas.weak_throughput(vt, ms, world) / 1e9
     launches = sum(n for _, n in ktimes.values()) // max(args.steps, 1)
 
     # dominant kernel and its roofline (CUDA events around every launch on the context stream)
@@ -270,24 +261,22 @@ def run_gpu(args):
         torch.cuda.synchronize()
         wall = (time.perf_counter() - t0) / args.steps * 1e3
         ms_e2e = max(e0.elapsed_time(e1) / args.steps, wall)
-        if world > 1:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = replicas.max_over_ranks(ms_e2e, dev)
         h2d = hf.numel() * 4 + hp.numel() * 4 + ha.numel() * 4
         d2h = hl.numel() * 4 + nfe * msf.FEATURE_DTYPE.itemsize
-        e2e = {"value": round(world * vt / (ms_e2e * 1e-3) / 1e9, 3), "unit": UNIT,
+        e2e = {"value": round(replicas.weak_throughput(vt, ms_e2e, world) / 1e9, 3), "unit": UNIT,
                "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
+    # the batched and served forms are reported from rank 0 (each replica would measure the same)
     batched = None
-    if not args.no_batched:
+    if rank == 0 and not args.no_batched:
         batched = run_batched(dev)
     serving = None
-    if not args.no_serving:
+    if rank == 0 and not args.no_serving:
         serving = run_serving(dev, seconds=args.serve_seconds)
 
     ctx.close()
