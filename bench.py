@@ -38,9 +38,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
-# from an ncu capture of the same kernel on the same workload: {(config, kernel): bytes}
-TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
+# the same kernel code on the same workload (profiles/kernels_mid_step.md): {(config, kernel):
+# bytes}. An entry is removed whenever its kernel changes.
+TRAFFIC = {
+    (2, "k_bin_reduce"): 406_917_120 + 745_671_168,
+    (2, "k_tile"): 539_574_272 + 10_779_648,
+}
 
 
 class Clocks:
