@@ -331,6 +331,14 @@ int msf_set_profiling(msf_ctx* ctx, int enable);
 int msf_kernel_times(msf_ctx* ctx, char (*names)[48], double* total_ms, int64_t* launches,
                      int cap, int reset);
 
+/* Limit, in SM clock cycles, of the bounded waits inside the kernels (the asynchronous copies
+ * of the binning passes wait on an mbarrier). A wait that runs out makes the kernel record it
+ * and exit; the call then returns MSF_ERR_TIMEOUT and the context stays usable (a failed
+ * msf_bin_particles leaves the dataset unbinned). cycles < 0 restores the default (about one
+ * second); 0 makes every such wait give up at once, which exercises the timeout path without
+ * any device fault. Errors: INVALID_ARG. */
+int msf_set_wait_limit(msf_ctx* ctx, long long cycles);
+
 /* Short text for a status code. */
 const char* msf_status_string(int status);
 

@@ -58,6 +58,7 @@ struct BinArgs {
   uint32_t* rec_v;              // [P*T] voxel within bucket (+4 slack for rounded bulk copies)
   float* rec_a;                 // [A][NRp] attribute values (+4 slack)
   unsigned* err;                // bounded waits that gave up
+  long long wait_cycles;        // limit of those waits (SM cycles)
   unsigned* absmax;             // [A] float bits of max finite |v|
   unsigned long long* outside;  // [T]
   int32_t* count;               // [T][V]
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
       run += c;
     }
   }
-  const bool ok = mbar_wait(&s_bar, 0);
+  const bool ok = mbar_wait(&s_bar, 0, b.wait_cycles);
   if (__syncthreads_or(!ok)) {  // the copies did not arrive in time
     if (threadIdx.x == 0) {
       atomicAdd(b.err, 1u);
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
   if (threadIdx.x == 0) s_nlist = 0;
   __syncthreads();
   for (int piece = 0; piece < npiece; ++piece) {
-    const bool ok = mbar_wait(&s_bar, (uint32_t)piece & 1u);
+    const bool ok = mbar_wait(&s_bar, (uint32_t)piece & 1u, b.wait_cycles);
     if (__syncthreads_or(!ok)) {  // the copy did not arrive in time
       if (threadIdx.x == 0) {
         atomicAdd(b.err, 1u);
@@ -629,6 +630,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.rec_v = S.rec_v.as<uint32_t>();
   b.rec_a = S.rec_a.as<float>();
   b.NRp = NRp;
+  b.wait_cycles = ctx->wait_cycles;
   b.err = S.total.as<uint32_t>() + 2;
   b.absmax = S.absmax.as<unsigned>();
   b.outside = S.outside.as<unsigned long long>();

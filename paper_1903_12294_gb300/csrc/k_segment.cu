@@ -463,21 +463,6 @@ __device__ __forceinline__ void hook_seg(const SegArgs& a, int tw, int z, int y,
     join_rows(seg_index(g, tw - 1, z, y, xs), false);
 }
 
-// one thread per segment (batched pass)
-template <bool SPATIAL>
-__device__ __forceinline__ void hook_body(const SegArgs& a, const int64_t gs) {
-  const Geometry& g = a.g;
-  if (gs >= g.nseg) return;
-  const uint2 e = __ldg(a.seg + gs);
-  if (!e.x) return;
-  uint32_t r, xs, y, z, tw;
-  g.fnxs.divmod((uint32_t)gs, r, xs);
-  g.fny.divmod(r, r, y);
-  g.fnz.divmod(r, tw, z);
-  hook_seg<SPATIAL>(a, (int)tw, (int)z, (int)y, (int)xs, e.x, e.y,
-                    [&](uint32_t c0, uint32_t c1) { gunion(a.cparent, c0, c1); });
-}
-
 // The component pairs one tile joins across its faces repeat heavily (a feature crossing a face
 // touches it in many rows). Each tile keeps the pairs it has joined in a shared-memory set and
 // joins a pair only the first time it meets it.
@@ -498,14 +483,11 @@ __device__ __forceinline__ bool pair_first_seen(unsigned long long* set, uint32_
   return true;  // crowded: join without remembering
 }
 
-// one CTA per tile, one thread per segment of the tile
+// One tile's cross-face joins, one thread per segment (s_set cleared by the caller).
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256, 4) k_hook(const __grid_constant__ SegArgs a) {
-  __shared__ unsigned long long s_set[kHookSet];
-  for (int i = threadIdx.x; i < kHookSet; i += 256) s_set[i] = ~0ull;
-  __syncthreads();
+__device__ __forceinline__ void hook_tile(const SegArgs& a, int tile, unsigned long long* s_set) {
   const Geometry& g = a.g;
-  const TileCoord tc = tile_coord(g, blockIdx.x);
+  const TileCoord tc = tile_coord(g, tile);
   const int sg = threadIdx.x;
   const int ly = sg & ((1 << g.lby) - 1), lz = (sg >> g.lby) & ((1 << g.lbz) - 1);
   const int lt = sg >> (g.lby + g.lbz);
@@ -517,6 +499,15 @@ __global__ void __launch_bounds__(256, 4) k_hook(const __grid_constant__ SegArgs
   hook_seg<SPATIAL>(a, tw, z, y, tc.xs, e.x, e.y, [&](uint32_t c0, uint32_t c1) {
     if (pair_first_seen(s_set, c0, c1)) gunion(a.cparent, c0, c1);
   });
+}
+
+// one CTA per tile
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256, 4) k_hook(const __grid_constant__ SegArgs a) {
+  __shared__ unsigned long long s_set[kHookSet];
+  for (int i = threadIdx.x; i < kHookSet; i += 256) s_set[i] = ~0ull;
+  __syncthreads();
+  hook_tile<SPATIAL>(a, blockIdx.x, s_set);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -540,19 +531,15 @@ __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) 
 // the components of key[t][p] and key[t+1][p] when both are members; a point that stays in one
 // voxel needs no join when temporal edges are on (the temporal edge already joins the two
 // voxel-timesteps).
-constexpr int kLinkPer = 4;     // points per thread in the batched pass
 constexpr int kLinkSteps = 8;   // window steps per thread in the single-query pass
 
+// The links of point p over window steps s0 .. s0 + kLinkSteps (one chunk).
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArgs a) {
+__device__ __forceinline__ void links_chunk(const SegArgs& a, int64_t p, int s0) {
   constexpr int L = kLinkSteps;
-  const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (p >= a.P) return;
   const int tw = a.g.tw;
   const bool temporal = (a.edges & MSF_EDGE_TEMPORAL) != 0;
-  const int nchunk = (tw - 1 + L - 1) / L;  // chunks of links (t, t+1), t < tw - 1
-  for (int c = blockIdx.y; c < nchunk; c += gridDim.y) {
-    const int s0 = c * L;
+  {
     const int nk = min(L + 1, tw - s0);      // keys of steps s0 .. s0 + nk - 1
     int32_t key[L + 1];
     uint32_t comp[L + 1];
@@ -574,6 +561,15 @@ __global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArg
         gunion(a.cparent, comp[j], comp[j + 1]);
     }
   }
+}
+
+// chunks of links (t, t+1), t < tw - 1, in grid y
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArgs a) {
+  const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (p >= a.P) return;
+  const int nchunk = (a.g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
+  for (int c = blockIdx.y; c < nchunk; c += gridDim.y) links_chunk<SPATIAL>(a, p, c * kLinkSteps);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1186,9 +1182,9 @@ struct BatchPlan {
   int nspat;                   // spatial tiles per chunk
   const int64_t* seg_begin;    // [nq + 1] prefix of segments
   const int64_t* tile_begin;   // [nq + 1] prefix of tiles
-  const int64_t* row_begin;    // [nq + 1] prefix of trajectory rows (tw - 1 per query)
-  const int* row_q;            // [rows] query of each trajectory row, rows in timestep order
-  const int* row_tw;           // [rows] window-relative step of each trajectory row
+  const int64_t* row_begin;    // [nq + 1] prefix of trajectory chunk items per query
+  const int* row_q;            // [items] query of each chunk item, items in timestep order
+  const int* row_tw;           // [items] window-relative first step of each chunk item
   int64_t row0;                // first trajectory row of this launch (gridDim.y rows each)
 };
 
@@ -1234,45 +1230,28 @@ __global__ void __launch_bounds__(256) k_tile_batch(const __grid_constant__ Batc
   }
 }
 
-// query = blockIdx.y; x strides over that query's segments
+// (tile, query) = (blockIdx.x, blockIdx.y): the tile's cross-face joins with its pair set
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_hook_batch(const __grid_constant__ BatchPlan b) {
-  const int q = blockIdx.y;
-  const SegArgs& a = b.qargs[q];
-  const int64_t n = a.g.nseg;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    hook_body<SPATIAL>(a, i);
+__global__ void __launch_bounds__(256, 4) k_hook_batch(const __grid_constant__ BatchPlan b) {
+  __shared__ unsigned long long s_set[kHookSet];
+  __shared__ __align__(16) SegArgs s_args;
+  load_args(&s_args, b.qargs + blockIdx.y);
+  for (int i = threadIdx.x; i < kHookSet; i += 256) s_set[i] = ~0ull;
+  __syncthreads();
+  if ((int)blockIdx.x >= s_args.g.ntiles) return;  // block-uniform
+  hook_tile<SPATIAL>(s_args, blockIdx.x, s_set);
 }
 
-// 4 points per thread (independent chains in flight), like the single-query pass
+// (point block, chunk item) = (blockIdx.x, row0 + blockIdx.y); chunk items in absolute-timestep
+// order, so the queries that cover a step read its key rows back to back (shared through L2)
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_links_batch(const __grid_constant__ BatchPlan b) {
-  // rows in absolute-timestep order: the queries that cover step t read key[t] and key[t+1]
-  // back to back, so those rows come from L2 after the first query
-  const int64_t row = b.row0 + blockIdx.y;
-  const int q = b.row_q[row];
-  const SegArgs& a = b.qargs[q];
-  const int tw = b.row_tw[row];
-  const int64_t p0 = (int64_t)blockIdx.x * (256 * kLinkPer) + threadIdx.x;
-  int32_t ka[kLinkPer], kb[kLinkPer];
-#pragma unroll
-  for (int j = 0; j < kLinkPer; ++j) {
-    const int64_t p = p0 + j * 256;
-    ka[j] = kb[j] = -1;
-    if (p < a.P) {
-      ka[j] = __ldcs(a.key + (int64_t)(a.g.t0 + tw) * a.P + p);
-      kb[j] = __ldcs(a.key + (int64_t)(a.g.t0 + tw + 1) * a.P + p);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kLinkPer; ++j) {
-    if (ka[j] < 0 || kb[j] < 0) continue;
-    const int64_t ca = comp_of<SPATIAL>(a, tw, ka[j]);
-    if (ca < 0) continue;
-    const int64_t cb = comp_of<SPATIAL>(a, tw + 1, kb[j]);
-    if (cb >= 0 && ca != cb) gunion(a.cparent, (uint32_t)ca, (uint32_t)cb);
-  }
+__global__ void __launch_bounds__(256, 4) k_links_batch(const __grid_constant__ BatchPlan b) {
+  __shared__ __align__(16) SegArgs s_args;
+  const int64_t item = b.row0 + blockIdx.y;
+  load_args(&s_args, b.qargs + b.row_q[item]);
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (p < s_args.P) links_chunk<SPATIAL>(s_args, p, b.row_tw[item]);
 }
 
 // query = blockIdx.y; x strides over that query's tiles
@@ -1443,14 +1422,15 @@ static int plan_group(msf_ctx* ctx, const msf_criteria* crits, BatchJob* job, Ba
     gr.seg_begin[i + 1] = gr.seg_begin[i] + gr.args[i].g.nseg;
     gr.tile_begin[i + 1] = gr.tile_begin[i] + gr.args[i].g.ntiles;
     const bool traj = (gr.args[i].edges & MSF_EDGE_TRAJ) && d.P > 0 && gr.args[i].g.tw > 1;
-    gr.row_begin[i + 1] = gr.row_begin[i] + (traj ? gr.args[i].g.tw - 1 : 0);
+    const int nlinkc = traj ? (gr.args[i].g.tw - 1 + kLinkSteps - 1) / kLinkSteps : 0;
+    gr.row_begin[i + 1] = gr.row_begin[i] + nlinkc;
   }
   if (gr.qlist.empty()) gr.qlist.push_back(0);
-  // trajectory rows sorted by absolute timestep
+  // trajectory chunk items (kLinkSteps links each) sorted by absolute first timestep
   std::vector<std::pair<int, int>> rows;  // (absolute t, query)
   for (int i = 0; i < nq; ++i)
     for (int64_t r = 0; r < gr.row_begin[i + 1] - gr.row_begin[i]; ++r)
-      rows.push_back({crits[gr.qs[i]].t0 + (int)r, i});
+      rows.push_back({crits[gr.qs[i]].t0 + (int)r * kLinkSteps, i});
   std::stable_sort(rows.begin(), rows.end(),
                    [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
                      return x.first < y.first;
@@ -1512,8 +1492,8 @@ size_t batch_job_scratch_bytes(const BatchJob* job, int q) { return job->scratch
 size_t batch_job_plan_bytes(const BatchJob* job) { return job->plan_bytes; }
 void batch_job_free(BatchJob* job) { delete job; }
 
-static void launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b, cudaStream_t s,
-                         bool timed) {
+static int launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b, cudaStream_t s,
+                        const StreamPair& sp, bool timed) {
   const Dataset& d = ctx->ds;
   const int nq = (int)gr.qs.size();
   const bool spatial = gr.spatial;
@@ -1542,23 +1522,29 @@ static void launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b,
     max_tiles = std::max<int64_t>(max_tiles, a.g.ntiles);
     vq &= ((uintptr_t)a.labels & 15) == 0;
   }
-  // 2D grids: y = query (<= 65535 per group), x over its items
-  if (any_link) {
-    ScopedKernel k(ctx, "k_hook_batch", timed);
-    const int64_t gx = (max_seg + 255) / 256;  // one segment per thread
-    if (spatial) k_hook_batch<true><<<dim3((unsigned)gx, nq), 256, 0, s>>>(b);
-    else k_hook_batch<false><<<dim3((unsigned)gx, nq), 256, 0, s>>>(b);
-  }
+  (void)max_seg;
+  // trajectory joins on the second stream (when there is one) beside the cross-face joins:
+  // both only join in the union-find, and joins commute
   const int64_t nrows = gr.row_begin[nq];
+  const bool side = nrows > 0 && sp.aux;
+  if (side) MSF_TRY(sp.fork(s));
+  const cudaStream_t ls = side ? sp.aux : s;
   for (int64_t r0 = 0; r0 < nrows; r0 += 65535) {  // gridDim.y limit per launch
-    ScopedKernel k(ctx, "k_links_batch", timed);
-    const int64_t gx = (d.P + 256 * kLinkPer - 1) / (256 * kLinkPer);
+    ScopedKernel k(ctx, "k_links_batch", ls, timed);
+    const int64_t gx = (d.P + 255) / 256;
     dim3 grid((unsigned)std::max<int64_t>(gx, 1), (unsigned)std::min<int64_t>(65535, nrows - r0));
     BatchPlan br = b;
     br.row0 = r0;
-    if (spatial) k_links_batch<true><<<grid, 256, 0, s>>>(br);
-    else k_links_batch<false><<<grid, 256, 0, s>>>(br);
+    if (spatial) k_links_batch<true><<<grid, 256, 0, ls>>>(br);
+    else k_links_batch<false><<<grid, 256, 0, ls>>>(br);
   }
+  // 2D grids: y = query (<= 65535 per group), x = tile
+  if (any_link) {
+    ScopedKernel k(ctx, "k_hook_batch", timed);
+    if (spatial) k_hook_batch<true><<<dim3((unsigned)max_tiles, nq), 256, 0, s>>>(b);
+    else k_hook_batch<false><<<dim3((unsigned)max_tiles, nq), 256, 0, s>>>(b);
+  }
+  if (side) MSF_TRY(sp.join(s));
   {
     ScopedKernel k(ctx, "k_flatten_batch", timed);
     k_flatten_batch<<<dim3((unsigned)max_tiles, nq), 256, 0, s>>>(b);
@@ -1574,10 +1560,12 @@ static void launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b,
       else k_final_batch<false, false><<<grid, 256, 0, s>>>(b);
     }
   }
+  return MSF_OK;
 }
 
 int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* const* scratch,
-                     char* plan_dev, char* plan_host, cudaStream_t s, bool timed) {
+                     char* plan_dev, char* plan_host, cudaStream_t s, const StreamPair& sp,
+                     bool timed) {
   // host image of every group's tables (the counts area is written by the device)
   for (BatchGroup& gr : job->groups) {
     const int nq = (int)gr.qs.size();
@@ -1632,7 +1620,7 @@ int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* 
     b.row_q = b.k0 + nq;
     b.row_tw = b.row_q + gr.row_q.size();
     b.nspat = gr.nspat;
-    launch_group(ctx, gr, b, s, timed);
+    MSF_TRY(launch_group(ctx, gr, b, s, sp, timed));
     auto* cnt = reinterpret_cast<unsigned long long*>(plan_dev + gr.off_cnt);
     k_batch_counts<<<(nq + 255) / 256, 256, 0, s>>>(b.qargs, nq, cnt);
   }
@@ -1695,8 +1683,9 @@ int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* 
   std::vector<char*> scratch(nq);
   for (int i = 0; i < nq; ++i) scratch[i] = base + off[i];
   char* host = static_cast<char*>(ctx->batch.host);
+  MSF_TRY(ctx_aux(ctx));
   MSF_TRY(batch_job_launch(ctx, job, labels, scratch.data(), base + off_plan, host, ctx->stream,
-                           true));
+                           StreamPair{ctx->aux, ctx->ev_fork, ctx->ev_join}, true));
   MSF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->timer.flush();
   std::vector<int64_t> nf(nq, 0);

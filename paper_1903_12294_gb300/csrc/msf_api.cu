@@ -107,12 +107,17 @@ void KernelTimer::release() {
   next_event = 0;
 }
 
-int ctx_fork(msf_ctx* ctx) {
+int ctx_aux(msf_ctx* ctx) {
   if (!ctx->aux) {
     MSF_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
     MSF_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     MSF_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
   }
+  return MSF_OK;
+}
+
+int ctx_fork(msf_ctx* ctx) {
+  MSF_TRY(ctx_aux(ctx));
   MSF_CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->stream));
   MSF_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
   return MSF_OK;
@@ -479,6 +484,12 @@ int msf_set_tile(msf_ctx* c, int by, int bz, int bt) {
   c->tile_by = by;
   c->tile_bz = bz;
   c->tile_bt = bt;
+  return MSF_OK;
+}
+
+int msf_set_wait_limit(msf_ctx* c, long long cycles) {
+  if (!c) return MSF_ERR_INVALID_ARG;
+  c->wait_cycles = cycles < 0 ? kWaitCycles : cycles;
   return MSF_OK;
 }
 

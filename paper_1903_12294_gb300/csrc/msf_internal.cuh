@@ -63,6 +63,7 @@ struct Dataset {
 // segmentation geometry: 32-voxel x-row segments grouped into tiles of 32 x BY x BZ x BT
 // ---------------------------------------------------------------------------------------------
 constexpr int kSegPerTile = 256;                 // BY * BZ * BT
+constexpr long long kWaitCycles = 2000000000ll;  // bounded device waits: about one second
 constexpr int kMaxRunsPerTile = kSegPerTile * 16; // at most 16 runs in a 32-bit row mask
 
 // Unsigned 32-bit division by a runtime constant: q = (t + ((n - t) >> s1)) >> s2 with
@@ -181,6 +182,7 @@ struct msf_ctx {
   int tile_by = 0, tile_bz = 0, tile_bt = 0;
   msf::KernelTimer timer;
   std::atomic<int> servers{0};  // query servers attached (the dataset is frozen meanwhile)
+  long long wait_cycles = msf::kWaitCycles;  // limit of the kernels' bounded waits
   // a second stream for passes that are independent of each other (forked from and joined
   // back into the context stream with events; created on first use)
   cudaStream_t aux = nullptr;
@@ -208,8 +210,25 @@ struct ScopedKernel {
 
 // Fork: work enqueued on ctx->aux after this runs after everything already on ctx->stream.
 // Join: work enqueued on ctx->stream after this runs after everything enqueued on ctx->aux.
+int ctx_aux(msf_ctx* ctx);  // creates the auxiliary stream and its events on first use
 int ctx_fork(msf_ctx* ctx);
 int ctx_join(msf_ctx* ctx);
+
+// An auxiliary stream with its fork and join events, for a main stream given at each use.
+struct StreamPair {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int fork(cudaStream_t main) const {
+    MSF_CUDA_TRY(cudaEventRecord(ev_fork, main));
+    MSF_CUDA_TRY(cudaStreamWaitEvent(aux, ev_fork, 0));
+    return MSF_OK;
+  }
+  int join(cudaStream_t main) const {
+    MSF_CUDA_TRY(cudaEventRecord(ev_join, aux));
+    MSF_CUDA_TRY(cudaStreamWaitEvent(main, ev_join, 0));
+    return MSF_OK;
+  }
+};
 
 // ---------------------------------------------------------------------------------------------
 // bulk asynchronous copies global -> shared (cp.async.bulk, completion on an mbarrier)
@@ -217,7 +236,6 @@ int ctx_join(msf_ctx* ctx);
 // Source and destination 16-byte aligned, size a multiple of 16. Waits are bounded in time: a
 // wait that gives up returns false and the kernel reports MSF_ERR_TIMEOUT through its error
 // word instead of spinning on.
-constexpr long long kWaitCycles = 2000000000ll;  // about one second at the SM clock
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -254,10 +272,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity; false once `limit` SM cycles have passed without it
+// (a limit of 0 gives up at once without looking, which is how the timeout path is tested).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitCycles) {
+  if (limit <= 0) return false;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -496,7 +518,8 @@ int batch_job_plan(msf_ctx* ctx, int nq, const msf_criteria* crits, BatchJob** o
 size_t batch_job_scratch_bytes(const BatchJob* job, int q);
 size_t batch_job_plan_bytes(const BatchJob* job);
 int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* const* scratch,
-                     char* plan_dev, char* plan_host, cudaStream_t s, bool timed);
+                     char* plan_dev, char* plan_host, cudaStream_t s, const StreamPair& sp,
+                     bool timed);
 int batch_job_finish(const BatchJob* job, const char* plan_host, int64_t* n_features,
                      int* status);
 void batch_job_free(BatchJob* job);

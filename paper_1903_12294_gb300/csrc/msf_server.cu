@@ -100,6 +100,7 @@ struct Request {
 struct Slot {
   msf_server* srv = nullptr;
   cudaStream_t stream = nullptr;
+  StreamPair side;            // second stream of the slot (trajectory joins)
   char* plan_dev = nullptr;   // device plan area (tables and counts)
   char* plan_host = nullptr;  // its pinned host image
   size_t plan_cap = 0;
@@ -256,7 +257,7 @@ static int launch_slot(msf_server* srv, Slot* s) {
   for (int i = 0; i < n; ++i)
     if (batch_job_scratch_bytes(job, i) > s->reqs[i].scr_bytes) return MSF_ERR_INTERNAL;
   MSF_TRY(batch_job_launch(srv->ctx, job, labels.data(), scratch.data(), s->plan_dev,
-                           s->plan_host, s->stream, false));
+                           s->plan_host, s->stream, s->side, false));
   MSF_CUDA_TRY(cudaLaunchHostFunc(s->stream, on_batch_done, s));
   return MSF_OK;
 }
@@ -320,6 +321,12 @@ static void server_free(msf_server* srv) {
     }
     if (s.plan_dev) cudaFree(s.plan_dev);
     if (s.plan_host) cudaFreeHost(s.plan_host);
+    if (s.side.aux) {
+      cudaStreamSynchronize(s.side.aux);
+      cudaStreamDestroy(s.side.aux);
+    }
+    if (s.side.ev_fork) cudaEventDestroy(s.side.ev_fork);
+    if (s.side.ev_join) cudaEventDestroy(s.side.ev_join);
     if (s.job) batch_job_free(s.job);
   }
   if (srv->pool) cudaFree(srv->pool);
@@ -357,6 +364,9 @@ extern "C" int msf_server_create(msf_ctx* ctx, const msf_server_config* cfg, msf
     s.srv = srv;
     s.plan_cap = plan_cap;
     if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s.side.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.side.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.side.ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&s.plan_dev, plan_cap) != cudaSuccess ||
         cudaMallocHost(&s.plan_host, plan_cap) != cudaSuccess)
       st = MSF_ERR_OUT_OF_MEMORY;

@@ -33,7 +33,7 @@ EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
            "msf_segment_field_noalloc", "msf_segment_batch", "msf_server_create",
            "msf_server_submit", "msf_server_poll", "msf_server_release", "msf_server_get_stats",
-           "msf_server_destroy")
+           "msf_server_destroy", "msf_set_wait_limit")
 
 
 class msf_pred(ctypes.Structure):
@@ -134,6 +134,7 @@ def load_library(path: str = LIB_PATH):
         lib.msf_server_release.argtypes = [P, ctypes.c_uint64]
         lib.msf_server_get_stats.argtypes = [P, ctypes.POINTER(msf_server_stats)]
         lib.msf_server_destroy.argtypes = [P]
+        lib.msf_set_wait_limit.argtypes = [P, ctypes.c_longlong]
         lib.msf_status_string.argtypes = [i32]
         lib.msf_status_string.restype = ctypes.c_char_p
         for n in EXPORTS:
@@ -300,6 +301,10 @@ def msf_set_tile(ctx, by, bz, bt):
     _check(load_library().msf_set_tile(ctx, by, bz, bt), "msf_set_tile")
 
 
+def msf_set_wait_limit(ctx, cycles: int):
+    _check(load_library().msf_set_wait_limit(ctx, int(cycles)), "msf_set_wait_limit")
+
+
 def msf_set_profiling(ctx, enable: bool):
     _check(load_library().msf_set_profiling(ctx, int(bool(enable))), "msf_set_profiling")
 
@@ -441,6 +446,9 @@ class Context:
 
     def set_tile(self, by, bz, bt):
         msf_set_tile(self.h, by, bz, bt)
+
+    def set_wait_limit(self, cycles):
+        msf_set_wait_limit(self.h, cycles)
 
     def profiling(self, on=True):
         msf_set_profiling(self.h, on)
