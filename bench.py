@@ -43,7 +43,6 @@ def peaks():
 # bytes}. An entry is removed whenever its kernel changes.
 TRAFFIC = {
     (2, "k_bin_reduce"): 406_917_120 + 745_671_168,
-    (2, "k_tile"): 539_574_272 + 10_779_648,
 }
 
 
@@ -62,7 +61,7 @@ class Clocks:
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -536,8 +535,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")

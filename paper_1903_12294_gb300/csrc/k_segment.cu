@@ -223,7 +223,21 @@ struct TileSmem {
   int* warp;       // [8]
   uint32_t* par;   // [MAXR]
   uint16_t* cid;   // [MAXR]
+  int ncid;        // MAXR
 };
+
+// Tiles with at least this many runs join their contacts through a block-wide list.
+constexpr int kListRuns = 256;
+
+// Number of contacts row_contacts reports for two rows.
+__device__ __forceinline__ int contact_count(uint32_t m1, uint32_t m2, bool spatial_rows,
+                                             bool units_are_runs) {
+  const uint32_t both = m1 & m2;
+  int n = __popc(units_are_runs ? (both & ~(both << 1)) : both);
+  if (spatial_rows)
+    n += __popc(m1 & ~m2 & (m2 << 1) & ~(m1 << 1)) + __popc(m1 & ~m2 & (m2 >> 1) & ~(m1 >> 1));
+  return n;
+}
 
 template <int NP, bool SPATIAL, bool VEC>
 __device__ __forceinline__ void tile_body(const SegArgs& a, const int tile, const TileSmem& sm) {
@@ -317,47 +331,85 @@ __device__ __forceinline__ void tile_body(const SegArgs& a, const int tile, cons
   __syncthreads();
 
   // ---- phase 3: unions between in-tile neighbour rows ------------------------------------
+  // Each row meets its "backward" neighbours: four rows of the 8 around (y, z) in the same
+  // step, and the same row one step earlier. Direction d of row s is neighbour_row(d).
   const int ly = s & (BY - 1), lz = (s >> g.lby) & (BZ - 1), lt = s >> (g.lby + g.lbz);
-  if (m) {
-    auto join_rows = [&](int s2, bool spatial_rows) {
-      const uint32_t m2 = s_mask[s2];
-      if (!m2) return;
-      const uint32_t st2 = run_starts(m2, SPATIAL);
-      const uint32_t rb2 = s_rb[s2];
-      row_contacts(m, m2, spatial_rows, SPATIAL, [&](int x1, int x2) {
-        sunion(s_par, rb + run_index(st, x1), rb2 + run_index(st2, x2));
-      });
-    };
-    if (SPATIAL) {
-      // the four "backward" neighbour rows of the 8 around (y, z), same t
-      if (ly > 0) join_rows(s - 1, true);
-      if (lz > 0) {
-        const int sb = s - BY;
-        if (ly > 0) join_rows(sb - 1, true);
-        join_rows(sb, true);
-        if (ly + 1 < BY) join_rows(sb + 1, true);
+  const bool temporal = (a.edges & MSF_EDGE_TEMPORAL) != 0;
+  auto neighbour_row = [&](int d) -> int {
+    if (d == 4) return (temporal && lt > 0) ? s - BY * BZ : -1;
+    if (!SPATIAL) return -1;
+    if (d == 0) return ly > 0 ? s - 1 : -1;
+    if (lz == 0) return -1;
+    if (d == 1) return ly > 0 ? s - BY - 1 : -1;
+    if (d == 2) return s - BY;
+    return ly + 1 < BY ? s - BY + 1 : -1;
+  };
+  if (nrun_tile < kListRuns) {
+    // light tile: every thread joins its own row's contacts
+    if (m) {
+#pragma unroll 1
+      for (int d = 0; d < 5; ++d) {
+        const int s2 = neighbour_row(d);
+        if (s2 < 0) continue;
+        const uint32_t m2 = s_mask[s2];
+        if (!m2) continue;
+        const uint32_t st2 = run_starts(m2, SPATIAL);
+        const uint32_t rb2 = s_rb[s2];
+        row_contacts(m, m2, d < 4, SPATIAL, [&](int x1, int x2) {
+          sunion(s_par, rb + run_index(st, x1), rb2 + run_index(st2, x2));
+        });
       }
     }
-    if ((a.edges & MSF_EDGE_TEMPORAL) && lt > 0) join_rows(s - BY * BZ, false);
+  } else {
+    // heavy tile (many short runs): per direction, the contacts of all rows are listed as slot
+    // pairs and joined by all threads, so that rows with many contacts do not hold up the rest
+    // (the list lives where the component ids go later)
+    uint32_t* s_pairs = reinterpret_cast<uint32_t*>(s_cid);
+    const int cap = sm.ncid / 2;
+#pragma unroll 1
+    for (int d = 0; d < 5; ++d) {
+      const int s2 = m ? neighbour_row(d) : -1;
+      const uint32_t m2 = s2 >= 0 ? s_mask[s2] : 0u;
+      const int nc = m2 ? contact_count(m, m2, d < 4, SPATIAL) : 0;
+      int total;
+      const int off = block_exscan(nc, s_warp, &total);
+      if (nc) {
+        const uint32_t st2 = run_starts(m2, SPATIAL);
+        const uint32_t rb2 = s_rb[s2];
+        int pos = off;
+        row_contacts(m, m2, d < 4, SPATIAL, [&](int x1, int x2) {
+          const uint32_t r1 = rb + run_index(st, x1), r2 = rb2 + run_index(st2, x2);
+          if (pos < cap) s_pairs[pos] = (r1 << 16) | r2;
+          else sunion(s_par, r1, r2);  // beyond the list: joined here
+          ++pos;
+        });
+      }
+      __syncthreads();
+      const int nl = min(total, cap);
+      for (int i = tid; i < nl; i += 256) {
+        const uint32_t pr = s_pairs[i];
+        sunion(s_par, pr >> 16, pr & 0xFFFFu);
+      }
+      __syncthreads();
+    }
   }
   __syncthreads();
 
   // ---- phase 4: roots -> dense component ids (ascending smallest index) --------------------
+  // every run slot to its root (slots spread evenly over the threads; no joins run now)
+  for (int r = tid; r < nrun_tile; r += 256) s_par[r] = sfind(s_par, r);
+  __syncthreads();
+  // roots in ascending slot order: each thread takes a contiguous range of slots
+  const int per = (nrun_tile + 255) >> 8;
+  const int q0 = min(tid * per, nrun_tile), q1 = min(q0 + per, nrun_tile);
   int nroot = 0;
-  for (int j = 0; j < nr; ++j) {
-    const uint32_t r = rb + j;
-    const uint32_t root = sfind(s_par, r);
-    s_par[r] = root;
-    nroot += (root == r);
-  }
+  for (int r = q0; r < q1; ++r) nroot += (s_par[r] == (uint32_t)r);
   int ncomp_tile;
   const int cb = block_exscan(nroot, s_warp, &ncomp_tile);
   {
     int k = cb;
-    for (int j = 0; j < nr; ++j) {
-      const uint32_t r = rb + j;
-      if (s_par[r] == r) s_cid[r] = (uint16_t)(k++);
-    }
+    for (int r = q0; r < q1; ++r)
+      if (s_par[r] == (uint32_t)r) s_cid[r] = (uint16_t)(k++);
   }
   __syncthreads();
 
@@ -393,13 +445,13 @@ __device__ __forceinline__ void tile_body(const SegArgs& a, const int tile, cons
 }
 
 template <int NP, bool SPATIAL, bool VEC>
-__global__ void __launch_bounds__(256) k_tile(const __grid_constant__ SegArgs a) {
+__global__ void __launch_bounds__(256, 6) k_tile(const __grid_constant__ SegArgs a) {
   constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
   __shared__ uint32_t s_mask[kSegPerTile];
   __shared__ uint32_t s_rb[kSegPerTile];
   __shared__ int s_warp[8];
   extern __shared__ uint32_t s_dyn[];
-  const TileSmem sm{s_mask, s_rb, s_warp, s_dyn, reinterpret_cast<uint16_t*>(s_dyn + MAXR)};
+  const TileSmem sm{s_mask, s_rb, s_warp, s_dyn, reinterpret_cast<uint16_t*>(s_dyn + MAXR), MAXR};
   tile_body<NP, SPATIAL, VEC>(a, blockIdx.x, sm);
 }
 
@@ -1208,14 +1260,14 @@ __device__ __forceinline__ void load_args(SegArgs* dst, const SegArgs* src) {
 }
 
 template <int NP, bool SPATIAL, bool VEC>
-__global__ void __launch_bounds__(256) k_tile_batch(const __grid_constant__ BatchPlan b) {
+__global__ void __launch_bounds__(256, 5) k_tile_batch(const __grid_constant__ BatchPlan b) {
   constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
   __shared__ uint32_t s_mask[kSegPerTile];
   __shared__ uint32_t s_rb[kSegPerTile];
   __shared__ int s_warp[8];
   __shared__ __align__(16) SegArgs s_args;
   extern __shared__ uint32_t s_dyn[];
-  const TileSmem sm{s_mask, s_rb, s_warp, s_dyn, reinterpret_cast<uint16_t*>(s_dyn + MAXR)};
+  const TileSmem sm{s_mask, s_rb, s_warp, s_dyn, reinterpret_cast<uint16_t*>(s_dyn + MAXR), MAXR};
   const int64_t total = b.chunk_begin[b.nchunk];
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
     const int c = find_range(b.chunk_begin, b.nchunk, item);
