@@ -115,7 +115,7 @@ def algorithmic_bytes(wl, n_pred_arrays, keep_sumq=False):
         "k_bin_keys": P * T * (12 + 4),                      # positions in, voxel keys out
         "k_bin_place": P * T * 4 * A,                        # attributes in
         "k_bin_reduce": V * T * (4 + 4 * A + (8 * A if keep_sumq else 0)),  # count + means out
-        "k_tile": V * tw * 4 * n_pred_arrays,                # field + predicate arrays in
+        "k_mask": V * tw * 4 * n_pred_arrays,                # field + predicate arrays in
         "k_links": P * tw * 4,                               # keys of the window in
         "k_final": V * tw * 4,                               # labels out
         "k_feat_vox": V * tw * 8,                            # labels + field in

@@ -198,6 +198,10 @@ __device__ __forceinline__ int block_exscan(int v, int* s_warp, int* total) {
   return base + x - v;
 }
 
+__device__ __forceinline__ int64_t seg_index(const Geometry& g, int tw, int z, int y, int xs) {
+  return (((int64_t)tw * g.nz + z) * g.ny + y) * g.nxs + xs;
+}
+
 struct TileCoord {
   int xs, ty, tz, tt;
 };
@@ -217,6 +221,46 @@ __device__ __forceinline__ TileCoord tile_coord(const Geometry& g, int tile) {
 // k_tile: criterion + tile-local labelling
 // ---------------------------------------------------------------------------------------------
 // Shared memory of one tile's labelling (row masks, run slots, scan scratch, union-find).
+// The four voxels of a 16-byte unit against one predicate (the type test is uniform).
+__device__ __forceinline__ void pred4(const DevPred& pr, const uint4& r, bool& b0, bool& b1,
+                                      bool& b2, bool& b3) {
+  if (!pr.is_int) {
+    const float lo = pr.lo, hi = pr.hi;
+    const float x0 = __uint_as_float(r.x), x1 = __uint_as_float(r.y);
+    const float x2 = __uint_as_float(r.z), x3 = __uint_as_float(r.w);
+    b0 &= (x0 >= lo) & (x0 <= hi);
+    b1 &= (x1 >= lo) & (x1 <= hi);
+    b2 &= (x2 >= lo) & (x2 <= hi);
+    b3 &= (x3 >= lo) & (x3 <= hi);
+  } else {
+    const int lo = pr.ilo, hi = pr.ihi;
+    b0 &= ((int)r.x >= lo) & ((int)r.x <= hi);
+    b1 &= ((int)r.y >= lo) & ((int)r.y <= hi);
+    b2 &= ((int)r.z >= lo) & ((int)r.z <= hi);
+    b3 &= ((int)r.w >= lo) & ((int)r.w <= hi);
+  }
+}
+
+// Bits 0..7 of b to bits 0, 4, 8, .., 28.
+__device__ __forceinline__ uint32_t spread4(uint32_t b) {
+  b &= 0xFFu;
+  b = (b | (b << 12)) & 0x000F000Fu;
+  b = (b | (b << 6)) & 0x03030303u;
+  b = (b | (b << 3)) & 0x11111111u;
+  return b;
+}
+
+// Eight lanes hold one 32-voxel row, four voxels each (lane 8r + q: voxels 4q .. 4q+3 of row
+// r, bits b0..b3). Four warp ballots put the row masks together; the value is meaningful in
+// lane 8r. All lanes must call it.
+__device__ __forceinline__ uint32_t row_mask4(int lane, bool b0, bool b1, bool b2, bool b3) {
+  const uint32_t B0 = __ballot_sync(0xFFFFFFFFu, b0), B1 = __ballot_sync(0xFFFFFFFFu, b1);
+  const uint32_t B2 = __ballot_sync(0xFFFFFFFFu, b2), B3 = __ballot_sync(0xFFFFFFFFu, b3);
+  const int sh = lane & 24;
+  return spread4(B0 >> sh) | (spread4(B1 >> sh) << 1) | (spread4(B2 >> sh) << 2) |
+         (spread4(B3 >> sh) << 3);
+}
+
 struct TileSmem {
   uint32_t* mask;  // [kSegPerTile]
   uint32_t* rb;    // [kSegPerTile]
@@ -253,7 +297,16 @@ __device__ __forceinline__ void tile_body(const SegArgs& a, const int tile, cons
   const int BY = 1 << g.lby, BZ = 1 << g.lbz;
 
   // ---- phase 1: criterion, one 32-bit activity mask per row -------------------------------
-  if (VEC) {
+  if constexpr (NP < 0) {
+    // masks already formed by k_mask (kept in the row table's mask word)
+    const int sg = tid;
+    const int ly = sg & (BY - 1), lz = (sg >> g.lby) & (BZ - 1), lt = sg >> (g.lby + g.lbz);
+    const int y = tc.ty * BY + ly, z = tc.tz * BZ + lz, tw = (tc.tt << g.lbt) + lt - g.toff;
+    uint32_t mm = 0u;
+    if (y < g.ny && z < g.nz && tw >= 0 && tw < g.tw)
+      mm = __ldcg(reinterpret_cast<const uint32_t*>(a.seg) + 2 * seg_index(g, tw, z, y, tc.xs));
+    s_mask[sg] = mm;
+  } else if (VEC) {
     // 16-byte loads: lane = (row r of 4, x-quad q of 8); 4 rows per warp instruction.
     const int q = lane & 7, rsub = lane >> 3;
     const int x4 = tc.xs * 32 + 4 * q;
@@ -277,15 +330,10 @@ __device__ __forceinline__ void tile_body(const SegArgs& a, const int tile, cons
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        unsigned nib = valid[u] ? 0xFu : 0u;
+        bool b0 = valid[u], b1 = b0, b2 = b0, b3 = b0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          const DevPred& pr = a.pred[j];
-          nib &= (unsigned)cmp_pred(pr, raw[u][j].x) | ((unsigned)cmp_pred(pr, raw[u][j].y) << 1) |
-                 ((unsigned)cmp_pred(pr, raw[u][j].z) << 2) |
-                 ((unsigned)cmp_pred(pr, raw[u][j].w) << 3);
-        }
-        const unsigned m = __reduce_or_sync(0xFFu << (lane & 24), nib << (4 * q));
+        for (int j = 0; j < NP; ++j) pred4(a.pred[j], raw[u][j], b0, b1, b2, b3);
+        const unsigned m = row_mask4(lane, b0, b1, b2, b3);
         if (q == 0) s_mask[warp * 32 + 4 * (it + u) + rsub] = m;
       }
     }
@@ -458,9 +506,6 @@ __global__ void __launch_bounds__(256, 6) k_tile(const __grid_constant__ SegArgs
 // ---------------------------------------------------------------------------------------------
 // k_hook: joins across tile boundaries
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ int64_t seg_index(const Geometry& g, int tw, int z, int y, int xs) {
-  return (((int64_t)tw * g.nz + z) * g.ny + y) * g.nxs + xs;
-}
 
 // Cross-tile joins of one segment (tw, z, y, xs) with mask m != 0: its first run against the
 // last runs of the nine rows to the left (another tile), the backward rows in y/z that lie in
@@ -762,6 +807,159 @@ static void ensure_smem_attr(K kernel, size_t bytes, std::atomic<uint64_t>& mask
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// k_mask: the criterion alone, as a streaming pass; one 32-bit activity mask per row, written
+// into the row table's mask word (k_tile then starts from the masks, which stay in L2)
+// ---------------------------------------------------------------------------------------------
+// One warp per 32 consecutive rows (segment order); with 16-byte loads a lane covers 4 voxels
+// of one of 4 rows per instruction.
+template <int NP, bool VEC>
+__global__ void __launch_bounds__(256) k_mask(const __grid_constant__ SegArgs a) {
+  const Geometry& g = a.g;
+  const int lane = threadIdx.x & 31;
+  const int64_t wbase = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 32;
+  uint32_t* mk = reinterpret_cast<uint32_t*>(a.seg);
+  if (VEC) {
+    const int q = lane & 7, rsub = lane >> 3;
+    constexpr int U = NP <= 2 ? 4 : 2;
+#pragma unroll 1
+    for (int it = 0; it < 8; it += U) {
+      uint4 raw[U][NP > 0 ? NP : 1];
+      bool valid[U];
+      int64_t gsu[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t gs = wbase + 4 * (it + u) + rsub;
+        gsu[u] = gs;
+        uint32_t r, xs, y, z, tw;
+        g.fnxs.divmod((uint32_t)min(gs, g.nseg - 1), r, xs);
+        g.fny.divmod(r, r, y);
+        g.fnz.divmod(r, tw, z);
+        const int x4 = (int)xs * 32 + 4 * q;
+        valid[u] = gs < g.nseg && x4 < g.nx;
+        const int64_t off = (int64_t)(g.t0 + (int)tw) * g.V + ((int64_t)z * g.ny + y) * g.nx + x4;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+          raw[u][j] = valid[u] ? __ldcs(reinterpret_cast<const uint4*>(
+                                     static_cast<const unsigned int*>(a.pred[j].base) + off))
+                               : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        bool b0 = valid[u], b1 = b0, b2 = b0, b3 = b0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) pred4(a.pred[j], raw[u][j], b0, b1, b2, b3);
+        const unsigned m = row_mask4(lane, b0, b1, b2, b3);
+        if (q == 0 && gsu[u] < g.nseg) mk[2 * gsu[u]] = m;
+      }
+    }
+  } else {
+    constexpr int U = 8;
+#pragma unroll 1
+    for (int i = 0; i < 32; i += U) {
+      uint32_t raw[U][NP > 0 ? NP : 1];
+      bool valid[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t gs = wbase + i + u;
+        uint32_t r, xs, y, z, tw;
+        g.fnxs.divmod((uint32_t)min(gs, g.nseg - 1), r, xs);
+        g.fny.divmod(r, r, y);
+        g.fnz.divmod(r, tw, z);
+        const int x = (int)xs * 32 + lane;
+        valid[u] = gs < g.nseg && x < g.nx;
+        const int64_t off = (int64_t)(g.t0 + (int)tw) * g.V + ((int64_t)z * g.ny + y) * g.nx + x;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+          raw[u][j] = valid[u] ? __ldcs(static_cast<const unsigned int*>(a.pred[j].base) + off) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        bool act = valid[u];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) act = act && cmp_pred(a.pred[j], raw[u][j]);
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, act);
+        if (lane == 0 && wbase + i + u < g.nseg) mk[2 * (wbase + i + u)] = m;
+      }
+    }
+  }
+}
+
+// Rows of 32 voxels are contiguous when nx is a multiple of 32: the window is one linear run
+// of the predicate arrays, row gs starting at voxel 32 * gs. Each thread takes U 16-byte units
+// 256 apart; eight lanes cover one row. The row mask is put together from four warp ballots
+// (bit k of every lane's four voxels) rather than a lane reduction. FLOAT: no COUNT predicate.
+template <int NP, bool FLOAT>
+__global__ void __launch_bounds__(256) k_mask_lin(const __grid_constant__ SegArgs a) {
+  constexpr int U = NP <= 2 ? 4 : 2;
+  const int lane = threadIdx.x & 31, q = lane & 7;
+  const uint32_t n4 = (uint32_t)(a.g.nseg * 8);  // 16-byte units of the window (< 2^29)
+  const int64_t w0 = (int64_t)a.g.t0 * a.g.V / 4;
+  uint32_t* mk = reinterpret_cast<uint32_t*>(a.seg);
+  const uint32_t i0 = blockIdx.x * (256u * U) + threadIdx.x;
+  uint4 raw[U][NP > 0 ? NP : 1];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const uint32_t i = i0 + u * 256u;
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      raw[u][j] = i < n4 ? __ldcs(reinterpret_cast<const uint4*>(a.pred[j].base) + w0 + i)
+                         : make_uint4(0, 0, 0, 0);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const uint32_t i = i0 + u * 256u;
+    bool b0 = i < n4, b1 = b0, b2 = b0, b3 = b0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      if (FLOAT) {
+        DevPred pr = a.pred[j];
+        pr.is_int = 0;
+        pred4(pr, raw[u][j], b0, b1, b2, b3);
+      } else {
+        pred4(a.pred[j], raw[u][j], b0, b1, b2, b3);
+      }
+    }
+    const uint32_t m = row_mask4(lane, b0, b1, b2, b3);
+    if (q == 0 && i < n4) mk[2 * (i >> 3)] = m;
+  }
+}
+
+template <bool VEC>
+static void launch_mask_np(const SegArgs& a, cudaStream_t s) {
+  if ((a.g.nx & 31) == 0) {
+    const int U = a.npred <= 2 ? 4 : 2;
+    const unsigned grid = (unsigned)((a.g.nseg * 8 + 256 * U - 1) / (256 * U));
+    bool fl = true;
+    for (int j = 0; j < a.npred; ++j) fl &= !a.pred[j].is_int;
+    if (fl) {
+      switch (a.npred) {
+        case 0: k_mask_lin<0, true><<<grid, 256, 0, s>>>(a); break;
+        case 1: k_mask_lin<1, true><<<grid, 256, 0, s>>>(a); break;
+        case 2: k_mask_lin<2, true><<<grid, 256, 0, s>>>(a); break;
+        case 3: k_mask_lin<3, true><<<grid, 256, 0, s>>>(a); break;
+        default: k_mask_lin<4, true><<<grid, 256, 0, s>>>(a); break;
+      }
+    } else {
+      switch (a.npred) {
+        case 1: k_mask_lin<1, false><<<grid, 256, 0, s>>>(a); break;
+        case 2: k_mask_lin<2, false><<<grid, 256, 0, s>>>(a); break;
+        case 3: k_mask_lin<3, false><<<grid, 256, 0, s>>>(a); break;
+        default: k_mask_lin<4, false><<<grid, 256, 0, s>>>(a); break;
+      }
+    }
+    return;
+  }
+  const unsigned grid = (unsigned)((a.g.nseg + 255) / 256);
+  switch (a.npred) {
+    case 0: k_mask<0, VEC><<<grid, 256, 0, s>>>(a); break;
+    case 1: k_mask<1, VEC><<<grid, 256, 0, s>>>(a); break;
+    case 2: k_mask<2, VEC><<<grid, 256, 0, s>>>(a); break;
+    case 3: k_mask<3, VEC><<<grid, 256, 0, s>>>(a); break;
+    default: k_mask<4, VEC><<<grid, 256, 0, s>>>(a); break;
+  }
+}
+
 template <int NP, bool SP, bool VEC>
 static void launch_tile(const SegArgs& a, int grid, cudaStream_t s) {
   static std::atomic<uint64_t> attr_set{0};
@@ -833,8 +1031,14 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   cudaStream_t s = ctx->stream;
   MSF_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * 4, s));
   {
+    ScopedKernel k(ctx, "k_mask");
+    if ((a.g.nx & 3) == 0) launch_mask_np<true>(a, s);
+    else launch_mask_np<false>(a, s);
+  }
+  {
     ScopedKernel k(ctx, "k_tile");
-    launch_tile_any(a, spatial, g.ntiles, s);
+    if (spatial) launch_tile<-1, true, false>(a, g.ntiles, s);
+    else launch_tile<-1, false, false>(a, g.ntiles, s);
   }
   MSF_CUDA_TRY(cudaGetLastError());
   // cross-tile joins and trajectory joins touch only the union-find and commute: they run
