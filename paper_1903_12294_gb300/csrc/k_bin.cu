@@ -47,7 +47,7 @@ struct BinArgs {
   int logR, nb;                 // bucket = voxel >> logR; nb buckets
   int nblk;                     // sample blocks per timestep
   int64_t chunk;                // samples per block
-  uint32_t nrec;                // records in all (samples inside the grid)
+  const uint32_t* nrec;         // device: records in all (samples inside the grid); null = none
   int64_t NRp;                  // stride of rec_a between attributes (P*T rounded up to 4)
   const float* pos;             // [T][3][P]
   const float* attr;            // [T][A][P]
@@ -382,9 +382,10 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
   const int bucket = blockIdx.x, t = blockIdx.y;
   const int64_t row = (int64_t)t * b.nb + bucket;
   uint32_t r0 = 0, r1 = 0;  // no records at all: the offsets were never formed
-  if (b.nrec) {
+  const uint32_t nrec = b.nrec ? *b.nrec : 0u;
+  if (nrec) {
     r0 = b.offs[row * b.nblk];
-    r1 = (row + 1 < (int64_t)b.T * b.nb) ? b.offs[(row + 1) * b.nblk] : b.nrec;
+    r1 = (row + 1 < (int64_t)b.T * b.nb) ? b.offs[(row + 1) * b.nblk] : nrec;
   }
   // records in pieces of R words from the aligned-down start (16-byte bulk copies)
   const uint32_t s0 = r0 & ~3u, e1 = (r1 + 3u) & ~3u;
@@ -641,7 +642,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_CUDA_TRY(cudaMemsetAsync(b.absmax, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.outside, 0, sizeof(unsigned long long) * d.T, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), s));
-  b.nrec = 0;
+  b.nrec = nullptr;
   if (d.P > 0) {
     launch_bin_a(ctx, b, keep, 0, smem);
     MSF_CUDA_TRY(cudaGetLastError());
@@ -651,9 +652,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
                                    cudaMemcpyDeviceToDevice, s));
     launch_bin_a(ctx, b, keep, 1, smem);
     MSF_CUDA_TRY(cudaGetLastError());
-    // the last bucket's end: the total number of records (read back once, small)
-    MSF_CUDA_TRY(cudaMemcpyAsync(&b.nrec, S.total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    MSF_CUDA_TRY(cudaStreamSynchronize(s));
+    b.nrec = S.total.as<uint32_t>();  // the scan's total: the last bucket's end
   }
   launch_bin_a(ctx, b, keep, 2, smem);
   MSF_CUDA_TRY(cudaGetLastError());

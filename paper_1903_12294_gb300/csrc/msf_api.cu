@@ -123,6 +123,14 @@ int ctx_fork(msf_ctx* ctx) {
   return MSF_OK;
 }
 
+int ctx_field_ready(msf_ctx* ctx) {
+  if (ctx->field_pending) {
+    MSF_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_field, 0));
+    ctx->field_pending = false;
+  }
+  return MSF_OK;
+}
+
 int ctx_join(msf_ctx* ctx) {
   MSF_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
   MSF_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
@@ -332,6 +340,7 @@ void msf_destroy(msf_ctx* c) {
     cudaEventDestroy(c->ev_fork);
     cudaEventDestroy(c->ev_join);
   }
+  if (c->ev_field) cudaEventDestroy(c->ev_field);
   delete c;
 }
 
@@ -366,9 +375,20 @@ int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* f
   d.P = P;
   d.A = A;
   d.V = V;
-  MSF_TRY(copy_in(d.field, field, sizeof(float) * V * T, ptr_kind, c->stream));
+  // points first on the context stream; then the field on the auxiliary stream, so that
+  // binning (which reads only the points) overlaps the field's copy; readers of the field
+  // wait for it (ctx_field_ready)
   MSF_TRY(copy_in(d.pos, pos, sizeof(float) * 3 * P * T, ptr_kind, c->stream));
   MSF_TRY(copy_in(d.attr, attr, sizeof(float) * A * P * T, ptr_kind, c->stream));
+  if (P > 0) {
+    MSF_TRY(ctx_fork(c));
+    if (!c->ev_field) MSF_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_field, cudaEventDisableTiming));
+    MSF_TRY(copy_in(d.field, field, sizeof(float) * V * T, ptr_kind, c->aux));
+    MSF_CUDA_TRY(cudaEventRecord(c->ev_field, c->aux));
+    c->field_pending = true;
+  } else {
+    MSF_TRY(copy_in(d.field, field, sizeof(float) * V * T, ptr_kind, c->stream));
+  }
   d.loaded = true;
   return MSF_OK;
 }
@@ -422,6 +442,7 @@ int msf_segment(msf_ctx* c, const msf_criteria* crit, int32_t* labels, int label
   const int64_t N = (int64_t)(crit->t1 - crit->t0) * c->ds.V;
   if (N > 0 && !labels) return MSF_ERR_INVALID_ARG;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
+  MSF_TRY(ctx_field_ready(c));
   int32_t* dst = labels;
   if (labels_kind == MSF_HOST && N > 0) {
     MSF_TRY(c->host_staging.ensure(sizeof(int32_t) * N));
@@ -448,6 +469,7 @@ int msf_extract_features(msf_ctx* c, const msf_criteria* crit, const int32_t* la
   const int64_t N = (int64_t)(crit->t1 - crit->t0) * c->ds.V;
   if (N > 0 && !labels) return MSF_ERR_INVALID_ARG;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
+  MSF_TRY(ctx_field_ready(c));
   const int32_t* src = labels;
   // Labels this context's last msf_segment wrote for the same query are not read back: the
   // statistics come from the retained segmentation (so host labels need no upload either).
@@ -469,6 +491,7 @@ int msf_segment_batch(msf_ctx* c, int nq, const msf_criteria* crits, int32_t* co
   }
   if (nq == 0) return MSF_OK;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
+  MSF_TRY(ctx_field_ready(c));
   return segment_batch_run(c, nq, crits, labels, n_features);
 }
 

@@ -187,6 +187,10 @@ struct msf_ctx {
   // back into the context stream with events; created on first use)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the field's copy in can run on the auxiliary stream beside binning; readers of the field
+  // wait for this event first
+  cudaEvent_t ev_field = nullptr;
+  bool field_pending = false;
 };
 
 namespace msf {
@@ -213,6 +217,7 @@ struct ScopedKernel {
 int ctx_aux(msf_ctx* ctx);  // creates the auxiliary stream and its events on first use
 int ctx_fork(msf_ctx* ctx);
 int ctx_join(msf_ctx* ctx);
+int ctx_field_ready(msf_ctx* ctx);  // the context stream waits for a field copy in flight
 
 // An auxiliary stream with its fork and join events, for a main stream given at each use.
 struct StreamPair {

@@ -348,6 +348,10 @@ extern "C" int msf_server_create(msf_ctx* ctx, const msf_server_config* cfg, msf
       c.pool_bytes < 4096)
     return MSF_ERR_INVALID_ARG;
   MSF_CUDA_TRY(cudaSetDevice(ctx->device));
+  // the slots' streams read the dataset: everything queued on the context (the field's copy
+  // in, binning) completes first
+  MSF_TRY(ctx_field_ready(ctx));
+  MSF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   msf_server* srv = new msf_server();
   srv->ctx = ctx;
   srv->max_batch = c.max_batch;
