@@ -468,20 +468,64 @@ __device__ __forceinline__ void accumulate_row(const FeatAcc& acc, unsigned act,
 // Point samples (one per lane in `ok`): lanes of the same feature reduce their exact
 // fixed-point attribute values and double-float squares; the group's first lane commits.
 // Every lane of the warp must call this.
-__device__ __forceinline__ void accumulate_samples(const FeatAcc& acc, bool ok, int64_t fid,
-                                                   const float* attr_p, int64_t P) {
+// Point samples of one warp (lane: ok, feature fid, attributes at attr_p + j * P): the lanes
+// with the same feature reduce in the warp (exact 64-bit fixed-point sums; double-float sums of
+// squares), and one lane per feature hands the sums to sink(f, j, qs, s2a, s2b) with
+// s2 = s2a + s2b. All 32 lanes must call this.
+template <class Sink>
+__device__ __forceinline__ void reduce_samples(const FeatAcc& acc, bool ok, int64_t fid,
+                                               const float* attr_p, int64_t P, Sink&& sink) {
   const unsigned act = __ballot_sync(0xFFFFFFFFu, ok);
+  if (!act) return;
+  const int lane = threadIdx.x & 31;
+  // Common case when the samples come in voxel order: every member lane has the same feature.
+  // The whole warp then reduces by butterfly (lanes without a sample add zeros).
+  const int first = __ffs(act) - 1;
+  const int64_t f0 = __shfl_sync(0xFFFFFFFFu, fid, first);
+  if (__all_sync(0xFFFFFFFFu, !ok || fid == f0)) {
+    for (int j = 0; j < acc.A; ++j) {
+      const float v = ok ? __ldg(attr_p + (int64_t)j * P) : 0.f;
+      const unsigned long long u = ok ? (unsigned long long)quantise(v, acc.kscale[j]) : 0ull;
+      // exact 64-bit sum (mod 2^64) from three lane reductions of 21/21/22-bit parts
+      const uint32_t s0 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(u & 0x1FFFFFull));
+      const uint32_t s1 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)((u >> 21) & 0x1FFFFFull));
+      const uint32_t s2 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(u >> 42));
+      const unsigned long long qs = (unsigned long long)s0 + ((unsigned long long)s1 << 21) +
+                                    ((unsigned long long)s2 << 42);
+      const float d = (ok && isfinite(v)) ? v : 0.f;
+      double a2 = 0.0, b2 = 0.0;
+      if (__all_sync(0xFFFFFFFFu, df_safe(d))) {
+        float h = __fmul_rn(d, d), l = __fmaf_rn(d, d, -h);  // d*d == h + l exactly
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xFFFFFFFFu, h, o), l2 = __shfl_xor_sync(0xFFFFFFFFu, l, o);
+          float sh, se;
+          two_sum(h, h2, sh, se);
+          h = sh;
+          l = __fadd_rn(__fadd_rn(l, l2), se);
+        }
+        a2 = f2d(h);
+        b2 = f2d(l);
+      } else {  // non-finite or extreme values: plain fp64 (rare)
+        double w = (double)d * (double)d;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, o);
+        a2 = w;
+      }
+      if (lane == first) sink(f0, j, qs, a2, b2);
+    }
+    return;
+  }
   if (!ok) return;
   const unsigned grp = __match_any_sync(act, fid);
-  const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
-  const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + fid;
+  const int leader = __ffs(grp) - 1;
   for (int j = 0; j < acc.A; ++j) {
     const float v = __ldg(attr_p + (int64_t)j * P);
     const long long q = quantise(v, acc.kscale[j]);
     const float d = isfinite(v) ? v : 0.f;
     long long qs = 0;
     for (unsigned m = grp; m; m &= m - 1) qs += __shfl_sync(grp, q, __ffs(m) - 1);
-    double s2;
+    double a2 = 0.0, b2 = 0.0;
     if (__all_sync(grp, df_safe(d))) {
       const float p = __fmul_rn(d, d), pe = __fmaf_rn(d, d, -p);
       float h = 0.f, l = 0.f;
@@ -490,20 +534,28 @@ __device__ __forceinline__ void accumulate_samples(const FeatAcc& acc, bool ok, 
         df_add(h, l, __shfl_sync(grp, p, src));
         df_add(h, l, __shfl_sync(grp, pe, src));
       }
-      s2 = f2d(h);
-      if (lane == leader) atomicAdd(acc.sa2 + i * acc.A + j, f2d(l));
+      a2 = f2d(h);
+      b2 = f2d(l);
     } else {
-      s2 = 0.0;
       for (unsigned m = grp; m; m &= m - 1) {
         const double w = (double)__shfl_sync(grp, d, __ffs(m) - 1);
-        s2 += w * w;
+        a2 += w * w;
       }
     }
-    if (lane == leader) {
-      atomicAdd(acc.sq + i * acc.A + j, (unsigned long long)qs);
-      atomicAdd(acc.sa2 + i * acc.A + j, s2);
-    }
+    if (lane == leader) sink(fid, j, (unsigned long long)qs, a2, b2);
   }
+}
+
+// reduce_samples committing straight to the accumulators (copy blockIdx.x % K)
+__device__ __forceinline__ void accumulate_samples(const FeatAcc& acc, bool ok, int64_t fid,
+                                                   const float* attr_p, int64_t P) {
+  reduce_samples(acc, ok, fid, attr_p, P,
+                 [&](int64_t f, int j, unsigned long long qs, double a2, double b2) {
+                   const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + f;
+                   atomicAdd(acc.sq + i * acc.A + j, qs);
+                   atomicAdd(acc.sa2 + i * acc.A + j, a2);
+                   if (b2 != 0.0) atomicAdd(acc.sa2 + i * acc.A + j, b2);
+                 });
 }
 
 // entry points of the translation units
