@@ -1,0 +1,114 @@
+"""Full-size parity on the combustion-shaped, batched and serving workloads (the sizes the
+benchmark and its batched/served forms run), against the CPU oracle. The combustion window is
+compared whole (binning bit-exact, labels bit-exact, feature count); for the batched and served
+workloads the oracle labels the queries with the shortest windows, at the full dataset size."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1903_12294_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _host_gib_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2**20
+    except OSError:
+        pass
+    return 0.0
+
+
+def test_combustion_full_size(gpu, orc):
+    """256^3 x 24, 8M particles with four attributes, a conjunction of three predicates (the
+    comparison holds about 30 GiB of host arrays at its peak)."""
+    if _host_gib_available() < 64:
+        pytest.skip("needs 64 GiB of free host memory for the oracle's arrays")
+    wl = synth.combustion(device="cuda")
+    t0, t1, preds, edges = wl.t0, wl.t1, wl.preds, wl.edges
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(wl.field, wl.pos, wl.attr)
+        ctx.bin()
+        labels, n = ctx.segment(t0, t1, preds, edges)
+        torch.cuda.synchronize()
+        key, count, mean, _ = ctx.bins("cpu")
+        lab = labels.cpu().numpy()
+        del labels
+    finally:
+        ctx.close()
+    f, p, a = wl.numpy()
+    del wl
+    torch.cuda.empty_cache()
+    o = orc.bin(f.shape, p, a, keep_sumq=False)
+    del p, a
+    assert np.array_equal(key.numpy(), o["key"])
+    assert np.array_equal(count.numpy(), o["count"])
+    assert np.array_equal(mean.numpy().view(np.uint32), o["mean"].view(np.uint32))
+    del key, count, mean
+    ref, n_ref = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, preds, edges)
+    assert n == n_ref
+    assert np.array_equal(lab, ref)
+
+
+def _shortest(queries, k):
+    return sorted(range(len(queries)), key=lambda i: queries[i][1] - queries[i][0])[:k]
+
+
+def test_batched_workload_full_size_sampled(gpu, orc):
+    """192^3 x 32, 4M points, 64 queries in one msf_segment_batch call; the three shortest
+    windows against the oracle."""
+    wl = synth.batched(device="cuda")
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(wl.field, wl.pos, wl.attr)
+        ctx.bin()
+        labels, nfs = ctx.segment_batch(wl.queries)
+        torch.cuda.synchronize()
+        picks = _shortest(wl.queries, 3)
+        got = {i: (labels[i].cpu().numpy(), nfs[i]) for i in picks}
+    finally:
+        ctx.close()
+    f, p, a = wl.numpy()
+    o = orc.bin(f.shape, p, a, keep_sumq=False)
+    for i in picks:
+        t0, t1, pr, e = wl.queries[i]
+        ref, n_ref = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
+        assert got[i][1] == n_ref and np.array_equal(got[i][0], ref), i
+
+
+def test_serving_workload_full_size_sampled(gpu, orc):
+    """1024^2 x 96 with 208,334 walkers; 24 queries through the server at once; the three
+    shortest windows against the oracle."""
+    wl = synth.serving(device="cuda", nq=24)
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(wl.field, wl.pos, wl.attr)
+        ctx.bin()
+        srv = gpu.Server(ctx, pool_bytes=4 << 30, max_batch=16, slots=2)
+        try:
+            for i, (t0, t1, pr, e) in enumerate(wl.queries):
+                srv.submit(i, t0, t1, pr, e)
+            picks = set(_shortest(wl.queries, 3))
+            got, seen = {}, 0
+            while seen < len(wl.queries):
+                for r in srv.poll(cap=64, timeout_ms=1000):
+                    seen += 1
+                    assert r.status == gpu.MSF_OK
+                    if r.tag in picks:
+                        got[r.tag] = (srv.take_labels(r).cpu().numpy(), r.n_features)
+                    elif r.labels:
+                        srv.release(r.tag)
+        finally:
+            srv.close()
+    finally:
+        ctx.close()
+    f, p, a = wl.numpy()
+    o = orc.bin(f.shape, p, a, keep_sumq=False)
+    for i in picks:
+        t0, t1, pr, e = wl.queries[i]
+        ref, n_ref = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
+        assert got[i][1] == n_ref and np.array_equal(got[i][0], ref), i
