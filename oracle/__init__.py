@@ -25,6 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "msf_oracle.c")
+_SRC_SLIC = os.path.join(_HERE, "msf_slic.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
@@ -36,11 +37,15 @@ EDGE_ALL = EDGE_SPATIAL | EDGE_TEMPORAL | EDGE_TRAJ
 
 
 def build(force: bool = False) -> str:
-    """Compile msf_oracle.c with gcc (portable flags only: the same source builds on x86 and Arm)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle sources with gcc (portable flags only: the same source builds on x86
+    and Arm; no floating-point contraction, so fp32 expressions round step by step)."""
+    srcs = [_SRC, _SRC_SLIC]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.run(
-            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+            ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, *srcs,
+             "-lm"],
             check=True,
         )
         os.replace(tmp, _LIB)
@@ -55,6 +60,13 @@ class _Pred(ctypes.Structure):
 class _Criteria(ctypes.Structure):
     _fields_ = [("t0", ctypes.c_int32), ("t1", ctypes.c_int32), ("n_pred", ctypes.c_int32),
                 ("pred", _Pred * 4), ("edges", ctypes.c_uint32)]
+
+
+class _SlicParams(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_int), ("t1", ctypes.c_int), ("attr", ctypes.c_int),
+                ("k", ctypes.c_int * 4), ("w_p", ctypes.c_float), ("w_f", ctypes.c_float),
+                ("w_d", ctypes.c_float), ("c_f", ctypes.c_float), ("eps_c", ctypes.c_float),
+                ("max_iter", ctypes.c_int)]
 
 
 class _FeatOut(ctypes.Structure):
@@ -79,6 +91,10 @@ def _load():
                                             P, ctypes.c_int, ctypes.c_int, P, i64,
                                             ctypes.POINTER(_FeatOut), P])
             lib.oracle_features.restype = ctypes.c_int
+            lib.oracle_slic.argtypes = ([ctypes.c_int] * 4 + [P, i64, ctypes.c_int, P, P, P,
+                                        ctypes.POINTER(_SlicParams), P, P, P, P,
+                                        ctypes.POINTER(ctypes.c_int)])
+            lib.oracle_slic.restype = ctypes.c_int
             lib.oracle_scale_exponent.argtypes = [ctypes.c_double, i64]
             lib.oracle_scale_exponent.restype = ctypes.c_int
             _lib = lib
@@ -186,3 +202,32 @@ def run_all(field, pos, attr, t0, t1, preds, edges=EDGE_ALL):
     labels, nf = segment(field, b["count"], b["mean"], b["key"], t0, t1, preds, edges)
     f = features(field, b["count"], attr, b["key"], b["kscale"], t0, t1, labels)
     return b, labels, nf, f
+
+
+def slic(field, pos, attr, key, t0, t1, attr_index, k, w_p=1.0, w_f=1.0, w_d=1.0, c_f=1.0,
+         eps_c=1e-3, max_iter=10):
+    """§3.2 multifaceted 4D clustering (msf_slic.c). k = (kx, ky, kz, kt) seeds per dimension.
+    Returns (field_label [Tw][NZ][NY][NX] int32, point_label [Tw][P] int32, centers [K][6] fp32
+    (x, y, z, t, p_c, f_c), counts [K][2] int64 (field, point samples), updates made)."""
+    field = np.ascontiguousarray(field, dtype=np.float32)
+    T, nz, ny, nx = field.shape
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    attr = np.ascontiguousarray(attr, dtype=np.float32)
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    P = pos.shape[2] if pos.ndim == 3 else 0
+    A = attr.shape[1] if attr.ndim == 3 else 0
+    prm = _SlicParams(int(t0), int(t1), int(attr_index), (ctypes.c_int * 4)(*[int(x) for x in k]),
+                      float(w_p), float(w_f), float(w_d), float(c_f), float(eps_c), int(max_iter))
+    K = int(np.prod(k))
+    tw = t1 - t0
+    fl = np.empty((tw, nz, ny, nx), np.int32)
+    pl = np.empty((tw, P), np.int32)
+    centers = np.empty((K, 6), np.float32)
+    counts = np.empty((K, 2), np.int64)
+    it = ctypes.c_int(0)
+    rc = _load().oracle_slic(nx, ny, nz, T, _ptr(field), P, A, _ptr(pos), _ptr(attr), _ptr(key),
+                             ctypes.byref(prm), _ptr(fl), _ptr(pl), _ptr(centers), _ptr(counts),
+                             ctypes.byref(it))
+    if rc != 0:
+        raise RuntimeError(f"oracle_slic failed: {rc}")
+    return fl, pl, centers, counts, int(it.value)
