@@ -16,6 +16,7 @@
  *                         value (the cluster centre of §3.2.2), spatio-temporal extent and
  *                         standard deviations (§3.4)
  *   msf_segment_batch     many queries (own thresholds, attributes, windows) labelled together
+ *   msf_cluster           the paper's multifaceted 4D clustering of field and point samples
  *   msf_server_*          a query server over the resident dataset: continuous batching of
  *                         queries submitted from any thread, admitted by device memory
  *
@@ -214,6 +215,50 @@ int msf_extract_features(msf_ctx* ctx, const msf_criteria* crit, const int32_t* 
  * the stream. Errors: as msf_segment for any query; nothing is written on an argument error. */
 int msf_segment_batch(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
                       int64_t* n_features);
+
+/* ---- multifaceted 4D clustering ------------------------------------------------------- */
+
+/* The paper's own segmentation (§3.2): a SLIC-style clustering of the field samples and the
+ * point samples of a window together. k[i] centres are seeded per dimension on a 4D rectilinear
+ * grid (§3.2.1: spacing C_i = E_i / k_i over nx, ny, nz and the window's steps, each centre at
+ * its grid cell's centre) and every sample first joins the nearest centre by the space-time
+ * separation S_st = sqrt(dx^2 + dy^2 + dz^2 + (c_f dt)^2). Then, up to max_iter times (§3.2.2):
+ * each centre moves to the mean location of its samples and takes the mean point value p_c of
+ * its point samples and the mean field value f_c of its field samples; the iteration stops
+ * when no centre value changed by more than eps_c relative to its previous value (tested from
+ * the second update on); otherwise every sample joins the centre minimising D_f = w_f |f_s - f_c|
+ * + w_d S_st (field samples) or D_p = w_p |p_s - p_c| + w_d S_st (point samples, p_s = attribute
+ * `attr`) among the centres whose 2C_1 x 2C_2 x 2C_3 x 2C_4 search region holds the sample
+ * (§3.2.3), keeping its centre when none does.
+ * Readings: a field sample sits at its voxel's centre (x + 0.5, y + 0.5, z + 0.5) and every
+ * sample's time is t + 0.5; points take part when binning placed them inside the grid; samples
+ * whose value is not finite take no part (label -1); distances and the change test are IEEE fp32
+ * operations in the order written, ties go to the lower centre index; centre sums are exact
+ * int64 fixed point (scale as in binning), means are (double)sum / n * 2^-k rounded to fp32; a
+ * centre without samples keeps its values (without point or field samples: keeps p_c or f_c);
+ * seeds start with p_c = f_c = 0. The result is deterministic. */
+typedef struct msf_cluster_params {
+  int32_t t0, t1;       /* window [t0, t1) */
+  int32_t attr;         /* point variable: attribute index (required when the dataset has points) */
+  int32_t k[4];         /* centres along x, y, z, t (each >= 1, product <= 2^20) */
+  float w_p, w_f, w_d;  /* weights of the point value, field value and space-time terms */
+  float c_f;            /* time-to-space conversion factor */
+  float eps_c;          /* convergence threshold (relative change) */
+  int32_t max_iter;     /* most centre updates (>= 1) */
+} msf_cluster_params;
+
+/* Cluster the window. field_labels [t1-t0][nz][ny][nx] and point_labels [t1-t0][P] (int32, host
+ * or device per labels_kind, caller-owned, either may be NULL) receive each sample's centre
+ * index (-1 for samples that take no part): the assignment the last centres were computed
+ * from. centers (host, may be NULL) receives [K][6] fp32 (x, y, z, t, p_c, f_c) and counts (host,
+ * may be NULL) [K][2] int64 (field samples, point samples) of the last update, K = k0*k1*k2*k3;
+ * *iterations (may be NULL) the number of centre updates. Synchronises the stream.
+ * Errors: NOT_LOADED, NOT_BINNED (dataset with points), INVALID_ARG (window, k, weights,
+ * eps_c < 0, max_iter < 1, attr), TOO_LARGE (K > 2^20, or a window of >= 2^31 samples of a kind),
+ * OUT_OF_MEMORY, CUDA. */
+int msf_cluster(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* field_labels,
+                int32_t* point_labels, int labels_kind, float* centers, int64_t* counts,
+                int* iterations);
 
 /* ---- query server --------------------------------------------------------------------- */
 

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "msf_internal.cuh"
 
@@ -331,6 +332,10 @@ void msf_destroy(msf_ctx* c) {
                     &c->bin.absmax, &c->bin.outside, &c->bin.scan_tmp, &c->bin.total})
     b->release();
   c->last.cfid.release();
+  for (DevBuf* b : {&c->clu.centers, &c->clu.prev, &c->clu.sums, &c->clu.counts,
+                    &c->clu.cell_start, &c->clu.cell_cursor, &c->clu.cell_items, &c->clu.flags,
+                    &c->clu.scan_tmp, &c->clu.flab, &c->clu.plab})
+    b->release();
   c->host_staging.release();
   c->batch.release();
   c->timer.release();
@@ -493,6 +498,55 @@ int msf_segment_batch(msf_ctx* c, int nq, const msf_criteria* crits, int32_t* co
   MSF_CUDA_TRY(cudaSetDevice(c->device));
   MSF_TRY(ctx_field_ready(c));
   return segment_batch_run(c, nq, crits, labels, n_features);
+}
+
+int msf_cluster(msf_ctx* c, const msf_cluster_params* prm, int32_t* field_labels,
+                int32_t* point_labels, int labels_kind, float* centers, int64_t* counts,
+                int* iterations) {
+  if (!c || !prm) return MSF_ERR_INVALID_ARG;
+  if (labels_kind != MSF_HOST && labels_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
+  const Dataset& d = c->ds;
+  if (!d.loaded) return MSF_ERR_NOT_LOADED;
+  if (prm->t0 < 0 || prm->t1 > d.T || prm->t1 <= prm->t0) return MSF_ERR_INVALID_ARG;
+  int64_t K = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (prm->k[i] < 1) return MSF_ERR_INVALID_ARG;
+    K *= prm->k[i];
+  }
+  if (K > (1 << 20)) return MSF_ERR_TOO_LARGE;
+  if (!std::isfinite(prm->w_p) || !std::isfinite(prm->w_f) || !std::isfinite(prm->w_d) ||
+      !std::isfinite(prm->c_f) || !(prm->eps_c >= 0.f) || prm->max_iter < 1)
+    return MSF_ERR_INVALID_ARG;
+  if (d.P > 0) {
+    if (prm->attr < 0 || prm->attr >= d.A) return MSF_ERR_INVALID_ARG;
+    if (!d.binned) return MSF_ERR_NOT_BINNED;
+  }
+  const int64_t tw = prm->t1 - prm->t0;
+  const int64_t nf = tw * d.V, np = tw * d.P;
+  if (nf >= ((int64_t)1 << 31) || np >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  MSF_TRY(ctx_field_ready(c));
+  int32_t* fl = field_labels;
+  int32_t* pl = point_labels;
+  if (labels_kind == MSF_HOST || !fl) {
+    MSF_TRY(c->clu.flab.ensure(sizeof(int32_t) * (size_t)nf));
+    fl = c->clu.flab.as<int32_t>();
+  }
+  if (labels_kind == MSF_HOST || !pl) {
+    MSF_TRY(c->clu.plab.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(np, 1)));
+    pl = c->clu.plab.as<int32_t>();
+  }
+  MSF_TRY(cluster_run(c, prm, fl, pl, centers, counts, iterations));
+  if (labels_kind == MSF_HOST) {
+    if (field_labels)
+      MSF_CUDA_TRY(cudaMemcpyAsync(field_labels, fl, sizeof(int32_t) * nf, cudaMemcpyDeviceToHost,
+                                   c->stream));
+    if (point_labels && np)
+      MSF_CUDA_TRY(cudaMemcpyAsync(point_labels, pl, sizeof(int32_t) * np,
+                                   cudaMemcpyDeviceToHost, c->stream));
+    MSF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  return MSF_OK;
 }
 
 int msf_set_tile(msf_ctx* c, int by, int bz, int bt) {

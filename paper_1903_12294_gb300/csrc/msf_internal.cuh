@@ -144,6 +144,13 @@ struct BinScratch {
   DevBuf hist, offs, cursor, rec_v, rec_a, absmax, outside, scan_tmp, total;
 };
 
+// Scratch of the clustering (k_cluster.cu): centres, their sums and cells, label buffers for
+// callers that pass host labels or none.
+struct ClusterScratch {
+  DevBuf centers, prev, sums, counts, cell_start, cell_cursor, cell_items, flags, scan_tmp, flab,
+      plab;
+};
+
 // Named kernel timing (optional; on the context stream).
 struct KernelTimer {
   bool enabled = false;
@@ -176,6 +183,7 @@ struct msf_ctx {
   msf::FeatScratch feat;
   msf::BinScratch bin;
   msf::BatchScratch batch;
+  msf::ClusterScratch clu;
   msf::DevBuf host_staging;  // device-side staging for host label buffers
   msf::SegState last;        // retained segmentation of the last msf_segment call
   uint64_t epoch = 1;        // bumped whenever the dataset or its binning changes
@@ -564,6 +572,8 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels_dev, int
                 const void* labels_user);
 int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
                       int64_t* n_features);
+int cluster_run(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* field_labels_dev,
+                int32_t* point_labels_dev, float* centers_host, int64_t* counts_host, int* iters);
 // A batch of queries planned on the host (k_segment.cu): per-query geometry, scratch sizes and
 // the tables the batched kernels read. Device memory comes from the caller: each query's
 // scratch (batch_job_scratch_bytes, 256-byte aligned) and one plan area of

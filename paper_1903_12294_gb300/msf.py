@@ -33,7 +33,7 @@ EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
            "msf_segment_field_noalloc", "msf_segment_batch", "msf_server_create",
            "msf_server_submit", "msf_server_poll", "msf_server_release", "msf_server_get_stats",
-           "msf_server_destroy", "msf_set_wait_limit")
+           "msf_server_destroy", "msf_set_wait_limit", "msf_cluster")
 
 
 class msf_pred(ctypes.Structure):
@@ -65,6 +65,13 @@ class msf_feature(ctypes.Structure):
 
 
 FEATURE_DTYPE = np.dtype(msf_feature)
+
+
+class msf_cluster_params(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_int32), ("t1", ctypes.c_int32), ("attr", ctypes.c_int32),
+                ("k", ctypes.c_int32 * 4), ("w_p", ctypes.c_float), ("w_f", ctypes.c_float),
+                ("w_d", ctypes.c_float), ("c_f", ctypes.c_float), ("eps_c", ctypes.c_float),
+                ("max_iter", ctypes.c_int32)]
 
 
 class msf_server_config(ctypes.Structure):
@@ -135,6 +142,8 @@ def load_library(path: str = LIB_PATH):
         lib.msf_server_get_stats.argtypes = [P, ctypes.POINTER(msf_server_stats)]
         lib.msf_server_destroy.argtypes = [P]
         lib.msf_set_wait_limit.argtypes = [P, ctypes.c_longlong]
+        lib.msf_cluster.argtypes = [P, ctypes.POINTER(msf_cluster_params), P, P, i32, P, P,
+                                    ctypes.POINTER(ctypes.c_int)]
         lib.msf_status_string.argtypes = [i32]
         lib.msf_status_string.restype = ctypes.c_char_p
         for n in EXPORTS:
@@ -301,6 +310,30 @@ def msf_set_tile(ctx, by, bz, bt):
     _check(load_library().msf_set_tile(ctx, by, bz, bt), "msf_set_tile")
 
 
+def make_cluster_params(t0, t1, attr, k, w_p=1.0, w_f=1.0, w_d=1.0, c_f=1.0, eps_c=1e-3,
+                        max_iter=10) -> msf_cluster_params:
+    return msf_cluster_params(int(t0), int(t1), int(attr), (ctypes.c_int32 * 4)(*[int(x) for x in k]),
+                              float(w_p), float(w_f), float(w_d), float(c_f), float(eps_c),
+                              int(max_iter))
+
+
+def msf_cluster(ctx, prm: msf_cluster_params, field_labels=None, point_labels=None):
+    """Returns (centers [K][6] float32, counts [K][2] int64, iterations); the label buffers (host
+    or device, same kind) are filled when given."""
+    K = int(np.prod(list(prm.k)))
+    centers = np.zeros((K, 6), np.float32)
+    counts = np.zeros((K, 2), np.int64)
+    fp, fk = _ptr_kind(field_labels)
+    pp, pk = _ptr_kind(point_labels)
+    if field_labels is not None and point_labels is not None and fk != pk:
+        raise ValueError("label buffers must be both host or both device")
+    kind = fk if field_labels is not None else pk
+    it = ctypes.c_int(0)
+    _check(load_library().msf_cluster(ctx, ctypes.byref(prm), fp, pp, kind, centers.ctypes.data,
+                                      counts.ctypes.data, ctypes.byref(it)), "msf_cluster")
+    return centers, counts, int(it.value)
+
+
 def msf_set_wait_limit(ctx, cycles: int):
     _check(load_library().msf_set_wait_limit(ctx, int(cycles)), "msf_set_wait_limit")
 
@@ -446,6 +479,19 @@ class Context:
 
     def set_tile(self, by, bz, bt):
         msf_set_tile(self.h, by, bz, bt)
+
+    def cluster(self, t0, t1, attr, k, w_p=1.0, w_f=1.0, w_d=1.0, c_f=1.0, eps_c=1e-3,
+                max_iter=10):
+        """§3.2 clustering of the window; returns (field labels, point labels) device tensors,
+        centers [K][6], counts [K][2] and the number of centre updates."""
+        import torch
+        T, nz, ny, nx = self.shape
+        dev = f"cuda:{self.device}"
+        fl = torch.empty((t1 - t0, nz, ny, nx), dtype=torch.int32, device=dev)
+        pl = torch.empty((t1 - t0, max(self.P, 1)), dtype=torch.int32, device=dev)[:, :self.P]
+        prm = make_cluster_params(t0, t1, attr, k, w_p, w_f, w_d, c_f, eps_c, max_iter)
+        centers, counts, it = msf_cluster(self.h, prm, fl, pl.contiguous() if self.P else None)
+        return fl, pl, centers, counts, it
 
     def set_wait_limit(self, cycles):
         msf_set_wait_limit(self.h, cycles)
