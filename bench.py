@@ -274,6 +274,10 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
+    clustering = None
+    if rank == 0 and not args.no_cluster:
+        ctx.bin()
+        clustering = run_clustering(ctx, wl, dev)
     # the batched and served forms are reported from rank 0 (each replica would measure the same)
     batched = None
     if rank == 0 and not args.no_batched:
@@ -301,7 +305,7 @@ def run_gpu(args):
                              "unit": UNIT},
             "roofline": roof, "step_roofline": step_roof, "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": int(launches), "kernels": per_kernel, "cpu_baseline": cpu,
-            "batched": batched, "serving": serving,
+            "batched": batched, "serving": serving, "clustering": clustering,
         }
         print(json.dumps(out))
     if world > 1:
@@ -478,6 +482,59 @@ def run_serving(dev, seconds=10.0, rate=200.0, saturate=256):
             "pool_gb": pool / 2**30}
 
 
+def run_clustering(ctx, wl, dev, reps=3):
+    """The paper's clustering (§3.2) on the resident workload: k = 16 x 16 x 16 x 4 centres
+    (8 x 8 x 8 voxels x 8 steps each), the speed attribute as point variable, up to 10 updates;
+    sample-updates per second (field + point samples of the window times the updates made).
+    Beside it, the oracle and the GPU on the tiny workload (K = 128), the same run both ways."""
+    import numpy as np
+    import torch
+
+    from paper_1903_12294_gb300 import msf, synth
+    T, nz, ny, nx = wl.field.shape
+    args = dict(w_p=1.0, w_f=1.0, w_d=0.05, c_f=1.0, eps_c=1e-3, max_iter=10)
+    k = (16, 16, 16, 4)
+    stream = torch.cuda.current_stream(dev)
+    ctx.cluster(0, T, 0, k, **args)                                   # warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fl, pl, c, n, it = ctx.cluster(0, T, 0, k, **args)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    samples = int(n.sum())
+    del fl, pl
+    # like for like on the tiny workload
+    import oracle
+    tw = synth.tiny(device=dev)
+    tctx = msf.Context(dev.index, stream)
+    tctx.load(tw.field, tw.pos, tw.attr)
+    tctx.bin()
+    tctx.cluster(0, 8, 0, (4, 4, 4, 2), **args)
+    torch.cuda.synchronize()
+    g0 = time.perf_counter()
+    _, _, _, tn, tit = tctx.cluster(0, 8, 0, (4, 4, 4, 2), **args)
+    torch.cuda.synchronize()
+    g_ms = (time.perf_counter() - g0) * 1e3
+    key = tctx.bins("cpu")[0].numpy()
+    tctx.close()
+    f, p, a = tw.numpy()
+    oracle.build()
+    c0 = time.perf_counter()
+    ores = oracle.slic(f, p, a, key, 0, 8, 0, (4, 4, 4, 2), **args)
+    c_ms = (time.perf_counter() - c0) * 1e3
+    return {"workload": f"{nx}x{ny}x{nz} x {T} field + {wl.pos.shape[2]} points, k = {k} "
+                        f"({int(np.prod(k))} centres), attribute 0, {args}",
+            "ms_per_run": round(ms, 3), "updates": it, "samples": samples,
+            "g_sample_updates_per_s": round(samples * it / (ms * 1e-3) / 1e9, 3),
+            "tiny_like_for_like": {"gpu_ms": round(g_ms, 3), "oracle_ms": round(c_ms, 1),
+                                   "oracle_cores": 1, "updates": tit,
+                                   "identical_updates": ores[4] == tit}}
+
+
 def _oracle_sample(wl, t_lo, t_hi):
     """The oracle on timesteps [t_lo, t_hi) of the workload (bin + segment + features)."""
     import oracle
@@ -543,6 +600,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cluster", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.impl == "reference":
