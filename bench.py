@@ -507,6 +507,11 @@ def run_clustering(ctx, wl, dev, reps=3):
     ms = e0.elapsed_time(e1) / reps
     samples = int(n.sum())
     del fl, pl
+    ctx.kernel_times(reset=True)
+    ctx.profiling(True)                     # one more run for the per-kernel split
+    ctx.cluster(0, T, 0, k, **args)
+    ctx.profiling(False)
+    kms = {kk: round(vv[0], 3) for kk, vv in ctx.kernel_times(reset=True).items()}
     # like for like on the tiny workload
     import oracle
     tw = synth.tiny(device=dev)
@@ -530,6 +535,7 @@ def run_clustering(ctx, wl, dev, reps=3):
                         f"({int(np.prod(k))} centres), attribute 0, {args}",
             "ms_per_run": round(ms, 3), "updates": it, "samples": samples,
             "g_sample_updates_per_s": round(samples * it / (ms * 1e-3) / 1e9, 3),
+            "kernels_ms": kms,
             "tiny_like_for_like": {"gpu_ms": round(g_ms, 3), "oracle_ms": round(c_ms, 1),
                                    "oracle_cores": 1, "updates": tit,
                                    "identical_updates": ores[4] == tit}}

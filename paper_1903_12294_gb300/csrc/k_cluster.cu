@@ -260,6 +260,146 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_field(const __grid_const
   }
 }
 
+// Field samples in tiles of TX x TY x TZ voxels of one step (256 per block): the centres filed
+// in the cells around the tile are gathered into shared memory once and every thread scans
+// that list. A tile whose neighbourhood holds more than kCand centres (or spans more than 256
+// cells) falls back to the per-sample lookup.
+constexpr int kCand = 768;
+
+template <int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256, 4) k_slic_assign_field_tiled(const __grid_constant__ SlicArgs a) {
+  static_assert(TX * TY * TZ == 256, "one voxel per thread");
+  __shared__ float s_cx[kCand], s_cy[kCand], s_cz[kCand], s_ct[kCand], s_cf[kCand];
+  __shared__ int s_id[kCand];
+  __shared__ int s_warp[8];
+  __shared__ int s_lo[4], s_n[4];
+  __shared__ int s_total, s_over;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ntx = (a.nx + TX - 1) / TX, nty = (a.ny + TY - 1) / TY, ntz = (a.nz + TZ - 1) / TZ;
+  const int64_t ntiles = (int64_t)ntx * nty * ntz * a.tw;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int64_t r = tile;
+    const int bx = (int)(r % ntx); r /= ntx;
+    const int by = (int)(r % nty); r /= nty;
+    const int bz = (int)(r % ntz);
+    const int t = (int)(r / ntz);
+    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+    const float ts = __fadd_rn((float)(a.t0 + t), 0.5f);
+    if (tid < 4) {
+      int lo, hi, k;
+      if (tid == 0) {
+        k = a.k[0];
+        lo = cell_of(__fadd_rn((float)x0, 0.5f), a.C[0], k);
+        hi = cell_of(__fadd_rn((float)(min(x0 + TX, a.nx) - 1), 0.5f), a.C[0], k);
+      } else if (tid == 1) {
+        k = a.k[1];
+        lo = cell_of(__fadd_rn((float)y0, 0.5f), a.C[1], k);
+        hi = cell_of(__fadd_rn((float)(min(y0 + TY, a.ny) - 1), 0.5f), a.C[1], k);
+      } else if (tid == 2) {
+        k = a.k[2];
+        lo = cell_of(__fadd_rn((float)z0, 0.5f), a.C[2], k);
+        hi = cell_of(__fadd_rn((float)(min(z0 + TZ, a.nz) - 1), 0.5f), a.C[2], k);
+      } else {
+        k = a.k[3];
+        lo = hi = cell_of(__fsub_rn(ts, (float)a.t0), a.C[3], k);
+      }
+      lo = max(lo - 1, 0);
+      hi = min(hi + 1, k - 1);
+      s_lo[tid] = lo;
+      s_n[tid] = hi - lo + 1;
+    }
+    __syncthreads();
+    const int ncell = s_n[0] * s_n[1] * s_n[2] * s_n[3];
+    // one neighbouring cell per thread: its filed centres go to the shared list
+    int cnt = 0;
+    uint32_t c0 = 0;
+    if (ncell <= 256 && tid < ncell) {
+      int q = tid;
+      const int i = s_lo[0] + q % s_n[0]; q /= s_n[0];
+      const int j = s_lo[1] + q % s_n[1]; q /= s_n[1];
+      const int l = s_lo[2] + q % s_n[2]; q /= s_n[2];
+      const int m = s_lo[3] + q;
+      const int cell = ((m * a.k[2] + l) * a.k[1] + j) * a.k[0] + i;
+      c0 = __ldg(a.cell_start + cell);
+      cnt = (int)(__ldg(a.cell_start + cell + 1) - c0);
+    }
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    int off = x - cnt;
+    for (int q = 0; q < w; ++q) off += s_warp[q];
+    if (tid == 255) {
+      int tot = 0;
+      for (int q = 0; q < 8; ++q) tot += s_warp[q];
+      s_total = tot;
+      s_over = (ncell > 256 || tot > kCand) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool over = s_over != 0;
+    if (!over)
+      for (int q = 0; q < cnt; ++q) {
+        const int c = (int)__ldg(a.cell_items + c0 + q);
+        const float* cc = a.centers + 6 * (int64_t)c;
+        s_cx[off + q] = cc[0];
+        s_cy[off + q] = cc[1];
+        s_cz[off + q] = cc[2];
+        s_ct[off + q] = cc[3];
+        s_cf[off + q] = cc[5];
+        s_id[off + q] = c;
+      }
+    __syncthreads();
+    const int nc = s_total;
+    const int xv = x0 + tid % TX, yv = y0 + (tid / TX) % TY, zv = z0 + tid / (TX * TY);
+    int best = -1;
+    long long v[5] = {0, 0, 0, 0, 0};
+    if (xv < a.nx && yv < a.ny && zv < a.nz) {
+      const int64_t li = ((int64_t)t * a.nz + zv) * a.ny * a.nx + (int64_t)yv * a.nx + xv;
+      if (a.flabel[li] >= 0) {
+        const float f = __ldg(a.field + (int64_t)a.t0 * a.V + li);
+        const float xs = __fadd_rn((float)xv, 0.5f), ys = __fadd_rn((float)yv, 0.5f);
+        const float zs = __fadd_rn((float)zv, 0.5f);
+        if (over) {
+          best = best_centre<false>(a, xs, ys, zs, ts, a.w_f, f, 5);
+        } else {
+          float bd = 0.f;
+          for (int q = 0; q < nc; ++q) {
+            const float cx = s_cx[q], cy = s_cy[q], cz = s_cz[q], ct = s_ct[q];
+            if (!(fabsf(__fsub_rn(xs, cx)) <= a.C[0] && fabsf(__fsub_rn(ys, cy)) <= a.C[1] &&
+                  fabsf(__fsub_rn(zs, cz)) <= a.C[2] && fabsf(__fsub_rn(ts, ct)) <= a.C[3]))
+              continue;
+            const float dx = __fsub_rn(cx, xs), dy = __fsub_rn(cy, ys), dz = __fsub_rn(cz, zs);
+            const float dt = __fmul_rn(a.c_f, __fsub_rn(ct, ts));
+            const float sst = __fsqrt_rn(__fadd_rn(
+                __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)),
+                __fmul_rn(dt, dt)));
+            const float d = __fadd_rn(__fmul_rn(a.w_f, fabsf(__fsub_rn(f, s_cf[q]))),
+                                      __fmul_rn(a.w_d, sst));
+            const int c = s_id[q];
+            if (better(d, c, bd, best)) {
+              bd = d;
+              best = c;
+            }
+          }
+        }
+        if (best < 0) best = a.flabel[li];  // no centre in range: keeps its centre
+        a.flabel[li] = best;
+        v[0] = quantise(xs, a.kpos);
+        v[1] = quantise(ys, a.kpos);
+        v[2] = quantise(zs, a.kpos);
+        v[3] = quantise(ts, a.kpos);
+        v[4] = quantise(f, a.kf);
+      }
+    }
+    warp_accumulate(a.sums, best, v, 5);
+    __syncthreads();  // the shared list is rebuilt for the next tile
+  }
+}
+
 template <bool INIT>
 __global__ void __launch_bounds__(256, 4) k_slic_assign_points(const __grid_constant__ SlicArgs a) {
   const int64_t n = (int64_t)a.tw * a.P;
@@ -449,6 +589,7 @@ int cluster_run(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* flabel, in
   const unsigned gf = (unsigned)std::min<int64_t>((nfs + 255) / 256, (int64_t)ctx->sm_count * 32);
   const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nps + 255) / 256,
                                                                        (int64_t)ctx->sm_count * 32));
+  const unsigned gt = (unsigned)ctx->sm_count * 8;  // tiled field pass: persistent blocks
   k_slic_seed<<<kb, 256, 0, s>>>(a);
   {
     ScopedKernel k(ctx, "k_slic_assign_field");
@@ -484,7 +625,8 @@ int cluster_run(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* flabel, in
     }
     {
       ScopedKernel k(ctx, "k_slic_assign_field");
-      k_slic_assign_field<false><<<gf, 256, 0, s>>>(a);
+      if (d.nz > 1) k_slic_assign_field_tiled<8, 8, 4><<<gt, 256, 0, s>>>(a);
+      else k_slic_assign_field_tiled<16, 16, 1><<<gt, 256, 0, s>>>(a);
     }
     if (nps > 0) {
       ScopedKernel k(ctx, "k_slic_assign_points");
