@@ -41,9 +41,7 @@ def peaks():
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
 # the same kernel code on the same workload (profiles/kernels_mid_step.md): {(config, kernel):
 # bytes}. An entry is removed whenever its kernel changes.
-TRAFFIC = {
-    (2, "k_bin_reduce"): 406_917_120 + 745_671_168,
-}
+TRAFFIC = {}
 
 
 class Clocks:

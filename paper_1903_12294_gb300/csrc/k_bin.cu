@@ -365,40 +365,45 @@ __device__ __forceinline__ void reduce_issue(const BinArgs& b, uint32_t a0, uint
   for (int a = 0; a < A; ++a) bulk_g2s(s_sta + (size_t)a * R, b.rec_a + a * b.NRp + a0, bytes, bar);
 }
 
+// record range [r0, r1) of item row = t * nb + bucket
+__device__ __forceinline__ void item_range(const BinArgs& b, int64_t row, uint32_t nrec,
+                                           uint32_t& r0, uint32_t& r1) {
+  r0 = r1 = 0u;
+  if (nrec) {
+    r0 = __ldg(b.offs + row * b.nblk);
+    r1 = (row + 1 < (int64_t)b.T * b.nb) ? __ldg(b.offs + (row + 1) * b.nblk) : nrec;
+  }
+}
+
+// One block per item (t, bucket). Shared memory: sums [A][R] u64, counts [R] u32 and a staging
+// buffer of R * (1 + A) words for the records (rec_v, rec_a per attribute; in pieces of R when
+// the bucket has more), reused for the means [A][R] f32 and the non-empty lists once the records
+// are in. The accumulators are cleared while the first piece is in flight. After the records,
+// every warp owns 128 voxels (four per lane): it lists its non-empty ones, forms their means and
+// stores its outputs, with no further block-wide step.
 template <int A, bool KEEP>
 __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant__ BinArgs b) {
   extern __shared__ __align__(16) unsigned long long s_dyn64[];
   const int R = 1 << b.logR;
   unsigned long long* s_sum = s_dyn64;                                    // [A][R]
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_dyn64 + (size_t)A * R);  // [R]
-  uint32_t* s_stv = s_cnt + R;                                            // [R] staged rec_v
-  float* s_sta = reinterpret_cast<float*>(s_stv + R);                     // [A][R] staged rec_a
-  float* s_mean = reinterpret_cast<float*>(s_cnt + R);                    // [A][R] (after records)
-  uint32_t* s_list = s_cnt + R + (size_t)A * R;                           // [R]
+  uint32_t* s_stv = s_cnt + R;                                            // [R] record voxels
+  float* s_sta = reinterpret_cast<float*>(s_stv + R);                     // [A][R] values
+  float* s_mean = reinterpret_cast<float*>(s_stv);                        // after the records
+  uint32_t* s_list = s_stv + (size_t)A * R;
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_k[A > 0 ? A : 1];
   __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
-  __shared__ int s_nlist;
   const int bucket = blockIdx.x, t = blockIdx.y;
-  const int64_t row = (int64_t)t * b.nb + bucket;
-  uint32_t r0 = 0, r1 = 0;  // no records at all: the offsets were never formed
+  const int64_t item = (int64_t)t * b.nb + bucket;
   const uint32_t nrec = b.nrec ? *b.nrec : 0u;
-  if (nrec) {
-    r0 = b.offs[row * b.nblk];
-    r1 = (row + 1 < (int64_t)b.T * b.nb) ? b.offs[(row + 1) * b.nblk] : nrec;
-  }
-  // records in pieces of R words from the aligned-down start (16-byte bulk copies)
+  uint32_t r0, r1;
+  item_range(b, item, nrec, r0, r1);
   const uint32_t s0 = r0 & ~3u, e1 = (r1 + 3u) & ~3u;
   const int npiece = r1 > r0 ? (int)((e1 - s0 + (uint32_t)R - 1) / (uint32_t)R) : 0;
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     if (npiece) reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, R, &s_bar);
-  }
-  // clear the accumulators while the first piece is in flight
-  {
-    uint4* z = reinterpret_cast<uint4*>(s_dyn64);
-    const int n16 = (int)(((size_t)A * R * 8 + (size_t)R * 4) / 16);
-    for (int i = threadIdx.x; i < n16; i += kBinNT) z[i] = make_uint4(0, 0, 0, 0);
   }
   if (threadIdx.x < A) {
     const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.P * b.T);
@@ -406,106 +411,110 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
     s_f1[threadIdx.x] = pow2f(-(k / 2));
     s_f2[threadIdx.x] = pow2f(-(k - k / 2));
   }
-  if (threadIdx.x == 0) s_nlist = 0;
+  {
+    uint4* z = reinterpret_cast<uint4*>(s_dyn64);
+    const int n16 = (int)(((size_t)A * R * 8 + (size_t)R * 4) / 16);
+    for (int q = threadIdx.x; q < n16; q += kBinNT) z[q] = make_uint4(0, 0, 0, 0);
+  }
   __syncthreads();
   for (int piece = 0; piece < npiece; ++piece) {
     const bool ok = mbar_wait(&s_bar, (uint32_t)piece & 1u, b.wait_cycles);
     if (__syncthreads_or(!ok)) {  // the copy did not arrive in time
       if (threadIdx.x == 0) {
         atomicAdd(b.err, 1u);
-        mbar_wait(&s_bar, (uint32_t)piece & 1u);
+        mbar_wait(&s_bar, (uint32_t)piece & 1u);  // let it land before the block exits
       }
       return;
     }
     const uint32_t a0 = s0 + (uint32_t)piece * (uint32_t)R;
     const int m = (int)min((uint32_t)R, e1 - a0);
-    for (int i = threadIdx.x; i < m; i += kBinNT) {
-      const uint32_t r = a0 + (uint32_t)i;
+    for (int q = threadIdx.x; q < m; q += kBinNT) {
+      const uint32_t r = a0 + (uint32_t)q;
       if (r < r0 || r >= r1) continue;  // alignment slack of the neighbouring buckets
-      const uint32_t v = s_stv[i];
+      const uint32_t v = s_stv[q];
       atomicAdd(s_cnt + v, 1u);
 #pragma unroll
       for (int a = 0; a < A; ++a)
         atomicAdd(s_sum + (size_t)a * R + v,
-                  (unsigned long long)quantise(s_sta[(size_t)a * R + i], s_k[a]));
+                  (unsigned long long)quantise(s_sta[(size_t)a * R + q], s_k[a]));
     }
     __syncthreads();
     if (piece + 1 < npiece && threadIdx.x == 0) {
-      fence_proxy_async_smem();  // the reads above before the next copy overwrites the staging
+      fence_proxy_async_smem();  // the reads above before the next copy overwrites them
       const uint32_t a1 = a0 + (uint32_t)R;
       reduce_issue<A>(b, a1, min((uint32_t)R, e1 - a1), s_stv, s_sta, R, &s_bar);
     }
   }
-  // means of the non-empty voxels (listed, warp-aggregated); empty voxels get NaN at the store
-  const int64_t vbase = (int64_t)bucket << b.logR;
-  const int nv = (int)min((int64_t)R, b.V - vbase);
   const float qnan = __int_as_float(0x7fc00000);
   const int lane = threadIdx.x & 31;
+  const int wq = threadIdx.x & ~31;  // first thread of this warp
+  const int64_t vbase = (int64_t)bucket << b.logR;
+  const int nv = (int)min((int64_t)R, b.V - vbase);
   for (int i0 = 0; i0 < R; i0 += 4 * kBinNT) {
-    const int i = i0 + 4 * threadIdx.x;
-    unsigned nz = 0;
-    uint32_t c[4] = {0u, 0u, 0u, 0u};
-    if (i < R) {
-      const uint4 c4 = *reinterpret_cast<const uint4*>(s_cnt + i);
-      c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) nz += (c[e] != 0u);
-    }
-    int x = (int)nz;
+    const int wbase = i0 + 4 * wq;  // this warp's voxels [wbase, wbase + 128)
+    if (wbase >= R) break;          // warp-uniform
+    const int q = wbase + 4 * lane;
+    uint4 c4 = make_uint4(0u, 0u, 0u, 0u);
+    if (q < R) c4 = *reinterpret_cast<const uint4*>(s_cnt + q);
+    // this warp's non-empty voxels, listed in order
+    const int nz = (c4.x != 0u) + (c4.y != 0u) + (c4.z != 0u) + (c4.w != 0u);
+    int x = nz;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
       if (lane >= o) x += y;
     }
-    int base = 0;
-    if (lane == 31 && x) base = atomicAdd(&s_nlist, x);
-    base = __shfl_sync(0xFFFFFFFFu, base, 31) + x - (int)nz;
+    const int nw = __shfl_sync(0xFFFFFFFFu, x, 31);
+    if (A > 0 && nw) {
+      int pos = wbase + x - nz;
+      if (c4.x) s_list[pos++] = (uint32_t)q;
+      if (c4.y) s_list[pos++] = (uint32_t)(q + 1);
+      if (c4.z) s_list[pos++] = (uint32_t)(q + 2);
+      if (c4.w) s_list[pos] = (uint32_t)(q + 3);
+      __syncwarp();
+      for (int j = lane; j < nw; j += 32) {
+        const int u = (int)s_list[wbase + j];
+        const int c = (int)s_cnt[u];
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (c[e] != 0u) s_list[base++] = (uint32_t)(i + e);
-  }
-  __syncthreads();
-  const int nl = s_nlist;
-  for (int j = threadIdx.x; j < nl; j += kBinNT) {
-    const int i = (int)s_list[j];
-    const int c = (int)s_cnt[i];
-#pragma unroll
-    for (int a = 0; a < A; ++a)
-      s_mean[(size_t)a * R + i] = __fmul_rn(
-          __fmul_rn(div_count(i64_to_f32_rn((long long)s_sum[(size_t)a * R + i]), c), s_f1[a]),
-          s_f2[a]);
-  }
-  __syncthreads();
-  // one store of every output word: count, means (and sums), four voxels per thread
-  if ((b.V & 3) == 0) {
-    for (int i = 4 * threadIdx.x; i < nv; i += 4 * kBinNT) {
-      const int64_t v = vbase + i;
-      const uint4 c4 = *reinterpret_cast<const uint4*>(s_cnt + i);
+        for (int a = 0; a < A; ++a)
+          s_mean[(size_t)a * R + u] = __fmul_rn(
+              __fmul_rn(div_count(i64_to_f32_rn((long long)s_sum[(size_t)a * R + u]), c),
+                        s_f1[a]),
+              s_f2[a]);
+      }
+      __syncwarp();
+    }
+    if (q >= nv) continue;
+    const int64_t v = vbase + q;
+    if ((b.V & 3) == 0) {  // nv is then a multiple of four
       __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v), c4);
 #pragma unroll
       for (int a = 0; a < A; ++a) {
         const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
-        const float4 m4 = *reinterpret_cast<const float4*>(s_mean + (size_t)a * R + i);
+        const float4 m4 = *reinterpret_cast<const float4*>(s_mean + (size_t)a * R + q);
         __stcs(reinterpret_cast<float4*>(b.mean + o),
                make_float4(c4.x ? m4.x : qnan, c4.y ? m4.y : qnan, c4.z ? m4.z : qnan,
                            c4.w ? m4.w : qnan));
         if (KEEP) {
-          const unsigned long long* sq = s_sum + (size_t)a * R + i;
-          __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2((long long)sq[0], (long long)sq[1]));
-          __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2), make_longlong2((long long)sq[2], (long long)sq[3]));
+          const unsigned long long* sq = s_sum + (size_t)a * R + q;
+          __stcs(reinterpret_cast<longlong2*>(b.sumq + o),
+                 make_longlong2((long long)sq[0], (long long)sq[1]));
+          __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2),
+                 make_longlong2((long long)sq[2], (long long)sq[3]));
         }
       }
-    }
-  } else {
-    for (int i = threadIdx.x; i < nv; i += kBinNT) {
-      const int64_t v = vbase + i;
-      const uint32_t c = s_cnt[i];
-      __stcs(b.count + (int64_t)t * b.V + v, (int)c);
+    } else {
+      const uint32_t cc[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-      for (int a = 0; a < A; ++a) {
-        const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
-        __stcs(b.mean + o, c ? s_mean[(size_t)a * R + i] : qnan);
-        if (KEEP) __stcs(b.sumq + o, (long long)s_sum[(size_t)a * R + i]);
+      for (int e = 0; e < 4; ++e) {
+        if (q + e >= nv) break;
+        __stcs(b.count + (int64_t)t * b.V + v + e, (int)cc[e]);
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int64_t o = ((int64_t)a * b.T + t) * b.V + v + e;
+          __stcs(b.mean + o, cc[e] ? s_mean[(size_t)a * R + q + e] : qnan);
+          if (KEEP) __stcs(b.sumq + o, (long long)s_sum[(size_t)a * R + q + e]);
+        }
       }
     }
   }
