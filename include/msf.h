@@ -17,6 +17,11 @@
  *                         standard deviations (§3.4)
  *   msf_segment_batch     many queries (own thresholds, attributes, windows) labelled together
  *   msf_cluster           the paper's multifaceted 4D clustering of field and point samples
+ *   msf_merge_clusters    §3.3 merging of clusters whose centres agree in value (eps_m)
+ *   msf_relabel           apply a merge map to field or point labels
+ *   msf_cluster_stats     §3.4 per-cluster extent, means and standard deviations
+ *   msf_select_clusters   §3.4 range query over the centres' properties
+ *   msf_split_trajectories  §3.4 trajectory pieces: runs of consecutive timesteps in one feature
  *   msf_server_*          a query server over the resident dataset: continuous batching of
  *                         queries submitted from any thread, admitted by device memory
  *
@@ -386,6 +391,103 @@ int msf_set_wait_limit(msf_ctx* ctx, long long cycles);
 
 /* Short text for a status code. */
 const char* msf_status_string(int status);
+
+/* ---- §3.3 cluster merging, §3.4 summaries and trajectory pieces ------------------------ */
+
+/* Value terms compared by msf_merge_clusters. */
+#define MSF_MERGE_POINT 1 /* p_c, the centre's point value */
+#define MSF_MERGE_FIELD 2 /* f_c, the centre's field value */
+
+/* §3.3: merge clusters whose centres agree in value, ignoring the four space-time terms.
+ * centers: [K][6] fp32 (x, y, z, t, p_c, f_c) as msf_cluster writes them, host or device per
+ * centers_kind. Centres i and j match when, for every value term in `terms`, their values a and
+ * b are equal or 2 |a - b| < eps_m (|a| + |b|), i.e. their percent difference (|a - b| over the
+ * mean of |a| and |b|) lies below eps_m; each operation is one IEEE fp32 operation in the order
+ * written. MSF_MERGE_POINT | MSF_MERGE_FIELD is the paper's rule (both averages must match); a
+ * dataset without points merges on MSF_MERGE_FIELD alone. Matching is closed transitively: map
+ * [K] int32 (host or device per map_kind, caller-owned) receives, for every centre, the smallest
+ * centre index of its group, so a group's label is unique and independent of scheduling.
+ * *n_groups (host, may be NULL) receives the number of groups. Synchronises the stream.
+ * Errors: INVALID_ARG (NULL pointers, K < 1, eps_m negative or not finite, terms 0 or with
+ * unknown bits, a centre value not finite), TOO_LARGE (K > 2^18), OUT_OF_MEMORY, CUDA. */
+int msf_merge_clusters(msf_ctx* ctx, const float* centers, int centers_kind, int32_t K,
+                       float eps_m, int terms, int32_t* map, int map_kind, int32_t* n_groups);
+
+/* labels[i] = map[labels[i]] for the n labels (host or device per labels_kind, changed in
+ * place); negative labels stay. map: [K] int32, host or device per map_kind. A label >= K makes
+ * the call return INVALID_ARG with every label unchanged. Synchronises the stream.
+ * Errors: INVALID_ARG, TOO_LARGE (n >= 2^31), OUT_OF_MEMORY, CUDA. */
+int msf_relabel(msf_ctx* ctx, int32_t* labels, int labels_kind, int64_t n, const int32_t* map,
+                int map_kind, int32_t K);
+
+/* Summary of one cluster (§3.4: extent and standard deviations of the contained samples). */
+typedef struct {
+  int64_t n_field;    /* field samples (voxel-timesteps) with this label                    */
+  int64_t n_point;    /* point samples with this label                                      */
+  float lo[4], hi[4]; /* x, y, z, t extent of the samples' locations: a field sample at its
+                         voxel centre (x + 0.5, y + 0.5, z + 0.5), a point at its position,
+                         every sample at time t + 0.5; +inf / -inf without samples          */
+  double mean_field;  /* exact fixed-point field sum / n_field (NaN without field samples)  */
+  double std_field;   /* population standard deviation of the field samples' values        */
+  double mean_point;  /* the same over point samples of attribute `attr`                   */
+  double std_point;
+} msf_cluster_stat;
+
+/* Per-cluster summaries of a clustering of the window [t0, t1): field_labels [t1-t0][nz][ny]
+ * [nx] and point_labels [t1-t0][P] int32 (host or device per labels_kind; either may be NULL,
+ * which leaves that kind out), labels in [0, K) or negative (no cluster). Field samples whose
+ * value is not finite and point samples outside the grid or with a non-finite attribute value
+ * are left out whatever their label. out: [K] records, host or device per out_kind. Means come
+ * from exact fixed-point sums (scale as in binning, rounded to double once); deviations from
+ * fp64 sums of squared differences to that mean, whose order is not fixed (relative error
+ * about 1e-12). Synchronises the stream.
+ * Errors: NOT_LOADED, NOT_BINNED (point labels given), INVALID_ARG (window, attr, K < 1, a label
+ * >= K), TOO_LARGE (K > 2^20, a window of >= 2^31 samples of a kind), OUT_OF_MEMORY, CUDA. */
+int msf_cluster_stats(msf_ctx* ctx, int32_t t0, int32_t t1, int32_t attr,
+                      const int32_t* field_labels, const int32_t* point_labels, int labels_kind,
+                      int32_t K, msf_cluster_stat* out, int out_kind);
+
+/* §3.4 range query over centre properties: centre i is listed (ascending) when lo[j] <=
+ * centers[i][j] <= hi[j] for all six properties j (x, y, z, t, p_c, f_c); an infinite bound
+ * leaves that side open. centers: [K][6] fp32, host or device per centers_kind; lo, hi: host.
+ * out: int32 indices, host or device per out_kind, capacity cap; *n_out receives the count.
+ * cap < *n_out: nothing is written and the call returns MSF_ERR_CAPACITY (cap = 0 with out =
+ * NULL is a size query). Synchronises the stream.
+ * Errors: INVALID_ARG (NULL pointers, K < 1, a NaN bound), TOO_LARGE (K > 2^20), CAPACITY,
+ * OUT_OF_MEMORY, CUDA. */
+int msf_select_clusters(msf_ctx* ctx, const float* centers, int centers_kind, int32_t K,
+                        const float lo[6], const float hi[6], int32_t* out, int out_kind,
+                        int32_t cap, int32_t* n_out);
+
+/* Label space of msf_split_trajectories. */
+#define MSF_SPACE_POINTS 0 /* one label per point sample, [t1-t0][P] (as msf_cluster writes) */
+#define MSF_SPACE_VOXELS 1 /* one label per voxel-timestep, [t1-t0][nz][ny][nx] (msf_segment) */
+
+/* One piece of a trajectory: `length` consecutive timesteps from t_start (window-relative)
+ * over which point `point` is in feature (or cluster) `label`. */
+typedef struct {
+  int32_t point;
+  int32_t t_start;
+  int32_t length;
+  int32_t label;
+} msf_piece;
+
+/* §3.4 trajectory splitting: a trajectory whose samples change feature is cut into pieces, the
+ * maximal runs of consecutive timesteps of the window [t0, t1) over which its samples carry one
+ * non-negative label, and only pieces of at least min_len timesteps are kept (the paper connects
+ * samples with at least two consecutive timesteps in the feature: min_len = 2).
+ * labels (host or device per labels_kind): MSF_SPACE_POINTS gives every point sample's label;
+ * MSF_SPACE_VOXELS gives voxel labels, and a point sample takes the label of the voxel binning
+ * placed it in (-1 outside the grid). Pieces are written in (point, t_start) order to `pieces`
+ * (host or device per pieces_kind, capacity cap); *n_pieces receives their number. cap <
+ * *n_pieces: nothing is written and the call returns MSF_ERR_CAPACITY (cap = 0 with pieces =
+ * NULL is a size query). Synchronises the stream.
+ * Errors: NOT_LOADED, NOT_BINNED (voxel space), INVALID_ARG (window, min_len < 1, space, kinds,
+ * NULL labels), TOO_LARGE ((t1-t0) P or the window's voxel-timesteps >= 2^31), CAPACITY,
+ * OUT_OF_MEMORY, CUDA. */
+int msf_split_trajectories(msf_ctx* ctx, int32_t t0, int32_t t1, const int32_t* labels,
+                           int labels_kind, int labels_space, int32_t min_len, msf_piece* pieces,
+                           int pieces_kind, int64_t cap, int64_t* n_pieces);
 
 #ifdef __cplusplus
 }

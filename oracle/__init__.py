@@ -13,6 +13,10 @@ Functions and the passages they follow:
                   components by breadth-first flood fill (connectivity is this library's
                   definition; the paper's clustering imposes none, §3.3)
   ``features``  - per-feature averages (§3.2.2 cluster centre), extent and deviations (§3.4)
+  ``slic``      - the paper's multifaceted 4D clustering (§3.2; ``msf_slic.c``)
+  ``merge_clusters``, ``select_clusters``, ``cluster_stats``, ``split_trajectories`` - cluster
+                  merging (§3.3), range queries, summaries and trajectory pieces (§3.4;
+                  ``msf_post.c``)
 """
 from __future__ import annotations
 
@@ -26,6 +30,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "msf_oracle.c")
 _SRC_SLIC = os.path.join(_HERE, "msf_slic.c")
+_SRC_POST = os.path.join(_HERE, "msf_post.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
@@ -39,7 +44,7 @@ EDGE_ALL = EDGE_SPATIAL | EDGE_TEMPORAL | EDGE_TRAJ
 def build(force: bool = False) -> str:
     """Compile the oracle sources with gcc (portable flags only: the same source builds on x86
     and Arm; no floating-point contraction, so fp32 expressions round step by step)."""
-    srcs = [_SRC, _SRC_SLIC]
+    srcs = [_SRC, _SRC_SLIC, _SRC_POST]
     newest = max(os.path.getmtime(s) for s in srcs)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
@@ -75,6 +80,11 @@ class _FeatOut(ctypes.Structure):
         "max_field", "centroid", "sumq", "mean_attr", "std_attr")]
 
 
+class _StatsOut(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in (
+        "n_field", "n_point", "lo", "hi", "mean_field", "std_field", "mean_point", "std_point")]
+
+
 def _load():
     global _lib
     with _lock:
@@ -95,6 +105,18 @@ def _load():
                                         ctypes.POINTER(_SlicParams), P, P, P, P,
                                         ctypes.POINTER(ctypes.c_int)])
             lib.oracle_slic.restype = ctypes.c_int
+            lib.oracle_merge_clusters.argtypes = [ctypes.c_int, P, ctypes.c_float, ctypes.c_int, P]
+            lib.oracle_merge_clusters.restype = ctypes.c_int
+            lib.oracle_select_clusters.argtypes = [ctypes.c_int, P, P, P, P]
+            lib.oracle_select_clusters.restype = ctypes.c_int
+            lib.oracle_cluster_stats.argtypes = ([ctypes.c_int] * 4 + [P, i64, ctypes.c_int, P, P,
+                                                 P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                                 P, ctypes.c_int, ctypes.POINTER(_StatsOut)])
+            lib.oracle_cluster_stats.restype = ctypes.c_int
+            lib.oracle_point_labels.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, P, P, P]
+            lib.oracle_point_labels.restype = None
+            lib.oracle_split_trajectories.argtypes = [i64, ctypes.c_int, P, ctypes.c_int, P, i64]
+            lib.oracle_split_trajectories.restype = i64
             lib.oracle_scale_exponent.argtypes = [ctypes.c_double, i64]
             lib.oracle_scale_exponent.restype = ctypes.c_int
             _lib = lib
@@ -231,3 +253,81 @@ def slic(field, pos, attr, key, t0, t1, attr_index, k, w_p=1.0, w_f=1.0, w_d=1.0
     if rc != 0:
         raise RuntimeError(f"oracle_slic failed: {rc}")
     return fl, pl, centers, counts, int(it.value)
+
+
+MERGE_POINT, MERGE_FIELD = 1, 2
+
+
+def merge_clusters(centers, eps_m, terms=MERGE_POINT | MERGE_FIELD):
+    """§3.3 cluster merging (msf_post.c). centers [K][6] fp32. Returns (map [K] int32 with the
+    smallest centre index of each centre's group, number of groups)."""
+    c = np.ascontiguousarray(centers, dtype=np.float32)
+    K = c.shape[0]
+    m = np.empty(K, np.int32)
+    g = _load().oracle_merge_clusters(K, _ptr(c), float(eps_m), int(terms), _ptr(m))
+    if g < 0:
+        raise RuntimeError("oracle_merge_clusters failed")
+    return m, int(g)
+
+
+def select_clusters(centers, lo, hi):
+    """§3.4 range query: ascending indices i with lo[j] <= centers[i][j] <= hi[j] for all j."""
+    c = np.ascontiguousarray(centers, dtype=np.float32)
+    lo = np.ascontiguousarray(lo, dtype=np.float32)
+    hi = np.ascontiguousarray(hi, dtype=np.float32)
+    out = np.empty(max(c.shape[0], 1), np.int32)
+    n = _load().oracle_select_clusters(c.shape[0], _ptr(c), _ptr(lo), _ptr(hi), _ptr(out))
+    return out[:n].copy()
+
+
+def cluster_stats(field, pos, attr, key, t0, t1, attr_index, field_labels, point_labels, K):
+    """§3.4 per-cluster summaries (msf_post.c). Either label array may be None. Returns a dict
+    of n_field, n_point [K] int64; lo, hi [K][4] fp32 (x, y, z, t); mean_field, std_field,
+    mean_point, std_point [K] fp64."""
+    field = np.ascontiguousarray(field, dtype=np.float32)
+    T, nz, ny, nx = field.shape
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    attr = np.ascontiguousarray(attr, dtype=np.float32)
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    P = pos.shape[2] if pos.ndim == 3 else 0
+    A = attr.shape[1] if attr.ndim == 3 else 0
+    fl = None if field_labels is None else np.ascontiguousarray(field_labels, dtype=np.int32)
+    pl = None if point_labels is None else np.ascontiguousarray(point_labels, dtype=np.int32)
+    r = dict(n_field=np.empty(K, np.int64), n_point=np.empty(K, np.int64),
+             lo=np.empty((K, 4), np.float32), hi=np.empty((K, 4), np.float32),
+             mean_field=np.empty(K), std_field=np.empty(K), mean_point=np.empty(K),
+             std_point=np.empty(K))
+    o = _StatsOut(*[r[n].ctypes.data for n, _ in _StatsOut._fields_])
+    rc = _load().oracle_cluster_stats(nx, ny, nz, T, _ptr(field), P, A, _ptr(pos), _ptr(attr),
+                                      _ptr(key), int(t0), int(t1), int(attr_index),
+                                      ctypes.c_void_p(0) if fl is None else _ptr(fl),
+                                      ctypes.c_void_p(0) if pl is None else _ptr(pl), int(K),
+                                      ctypes.byref(o))
+    if rc != 0:
+        raise RuntimeError(f"oracle_cluster_stats failed: {rc}")
+    return r
+
+
+def point_labels(key, t0, voxel_labels):
+    """Labels of the window's point samples from voxel labels [Tw][NZ][NY][NX]: the label of the
+    voxel binning placed each sample in, -1 outside the grid."""
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    vl = np.ascontiguousarray(voxel_labels, dtype=np.int32)
+    tw = vl.shape[0]
+    V = int(np.prod(vl.shape[1:]))
+    P = key.shape[1]
+    out = np.empty((tw, P), np.int32)
+    _load().oracle_point_labels(V, P, int(t0), tw, _ptr(key), _ptr(vl), _ptr(out))
+    return out
+
+
+def split_trajectories(point_labels, min_len=2):
+    """§3.4 trajectory pieces (msf_post.c): [n][4] int32 rows (point, t_start, length, label) in
+    (point, t_start) order."""
+    pl = np.ascontiguousarray(point_labels, dtype=np.int32)
+    tw, P = pl.shape
+    lib = _load()
+    n = lib.oracle_split_trajectories(P, tw, _ptr(pl), int(min_len), ctypes.c_void_p(0), 0)
+    out = np.empty((max(n, 1), 4), np.int32)
+    lib.oracle_split_trajectories(P, tw, _ptr(pl), int(min_len), _ptr(out), n)
+    return out[:n].copy()
