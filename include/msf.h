@@ -408,8 +408,9 @@ const char* msf_status_string(int status);
  * [K] int32 (host or device per map_kind, caller-owned) receives, for every centre, the smallest
  * centre index of its group, so a group's label is unique and independent of scheduling.
  * *n_groups (host, may be NULL) receives the number of groups. Synchronises the stream.
- * Errors: INVALID_ARG (NULL pointers, K < 1, eps_m negative or not finite, terms 0 or with
- * unknown bits, a centre value not finite), TOO_LARGE (K > 2^18), OUT_OF_MEMORY, CUDA. */
+ * A NaN value matches nothing, not even itself. Errors: INVALID_ARG (NULL pointers, K < 1,
+ * eps_m negative or not finite, terms 0 or with unknown bits), TOO_LARGE (K > 2^18),
+ * OUT_OF_MEMORY, CUDA. */
 int msf_merge_clusters(msf_ctx* ctx, const float* centers, int centers_kind, int32_t K,
                        float eps_m, int terms, int32_t* map, int map_kind, int32_t* n_groups);
 

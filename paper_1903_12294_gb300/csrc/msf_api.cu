@@ -337,6 +337,7 @@ void msf_destroy(msf_ctx* c) {
                     &c->clu.scan_tmp, &c->clu.flab, &c->clu.plab})
     b->release();
   c->host_staging.release();
+  c->post.release();
   c->batch.release();
   c->timer.release();
   if (c->aux) {

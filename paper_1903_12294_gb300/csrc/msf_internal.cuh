@@ -151,6 +151,16 @@ struct ClusterScratch {
       plab;
 };
 
+// Scratch of the post-clustering steps (k_post.cu): staged inputs and outputs for host
+// pointers, per-point or per-centre counts and their scan, accumulators, a status word.
+struct PostScratch {
+  DevBuf in, in2, out, cnt, offs, scan_tmp, total, acc, status;
+  void release() {
+    for (DevBuf* b : {&in, &in2, &out, &cnt, &offs, &scan_tmp, &total, &acc, &status})
+      b->release();
+  }
+};
+
 // Named kernel timing (optional; on the context stream).
 struct KernelTimer {
   bool enabled = false;
@@ -184,6 +194,7 @@ struct msf_ctx {
   msf::BinScratch bin;
   msf::BatchScratch batch;
   msf::ClusterScratch clu;
+  msf::PostScratch post;
   msf::DevBuf host_staging;  // device-side staging for host label buffers
   msf::SegState last;        // retained segmentation of the last msf_segment call
   uint64_t epoch = 1;        // bumped whenever the dataset or its binning changes

@@ -33,7 +33,10 @@ EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
            "msf_segment_field_noalloc", "msf_segment_batch", "msf_server_create",
            "msf_server_submit", "msf_server_poll", "msf_server_release", "msf_server_get_stats",
-           "msf_server_destroy", "msf_set_wait_limit", "msf_cluster")
+           "msf_server_destroy", "msf_set_wait_limit", "msf_cluster", "msf_merge_clusters",
+           "msf_relabel", "msf_cluster_stats", "msf_select_clusters", "msf_split_trajectories")
+MSF_MERGE_POINT, MSF_MERGE_FIELD = 1, 2
+MSF_SPACE_POINTS, MSF_SPACE_VOXELS = 0, 1
 
 
 class msf_pred(ctypes.Structure):
@@ -65,6 +68,18 @@ class msf_feature(ctypes.Structure):
 
 
 FEATURE_DTYPE = np.dtype(msf_feature)
+
+
+class msf_cluster_stat(ctypes.Structure):
+    _fields_ = [("n_field", ctypes.c_int64), ("n_point", ctypes.c_int64),
+                ("lo", ctypes.c_float * 4), ("hi", ctypes.c_float * 4),
+                ("mean_field", ctypes.c_double), ("std_field", ctypes.c_double),
+                ("mean_point", ctypes.c_double), ("std_point", ctypes.c_double)]
+
+
+class msf_piece(ctypes.Structure):
+    _fields_ = [("point", ctypes.c_int32), ("t_start", ctypes.c_int32),
+                ("length", ctypes.c_int32), ("label", ctypes.c_int32)]
 
 
 class msf_cluster_params(ctypes.Structure):
@@ -144,6 +159,14 @@ def load_library(path: str = LIB_PATH):
         lib.msf_set_wait_limit.argtypes = [P, ctypes.c_longlong]
         lib.msf_cluster.argtypes = [P, ctypes.POINTER(msf_cluster_params), P, P, i32, P, P,
                                     ctypes.POINTER(ctypes.c_int)]
+        lib.msf_merge_clusters.argtypes = [P, P, i32, i32, ctypes.c_float, i32, P, i32,
+                                           ctypes.POINTER(ctypes.c_int32)]
+        lib.msf_relabel.argtypes = [P, P, i32, i64, P, i32, i32]
+        lib.msf_cluster_stats.argtypes = [P, i32, i32, i32, P, P, i32, i32, P, i32]
+        lib.msf_select_clusters.argtypes = [P, P, i32, i32, P, P, P, i32, i32,
+                                            ctypes.POINTER(ctypes.c_int32)]
+        lib.msf_split_trajectories.argtypes = [P, i32, i32, P, i32, i32, i32, P, i32, i64,
+                                               ctypes.POINTER(ctypes.c_int64)]
         lib.msf_status_string.argtypes = [i32]
         lib.msf_status_string.restype = ctypes.c_char_p
         for n in EXPORTS:
@@ -402,6 +425,93 @@ class _DeviceInt32:
 # convenience wrappers
 # ---------------------------------------------------------------------------------------------
 
+# numpy views of the record types (field order and offsets as in the C structs)
+CLUSTER_STAT_DTYPE = np.dtype({
+    "names": [f for f, _ in msf_cluster_stat._fields_],
+    "formats": ["<i8", "<i8", ("<f4", 4), ("<f4", 4), "<f8", "<f8", "<f8", "<f8"],
+    "offsets": [getattr(msf_cluster_stat, f).offset for f, _ in msf_cluster_stat._fields_],
+    "itemsize": ctypes.sizeof(msf_cluster_stat)})
+
+
+def msf_merge_clusters(ctx, centers, eps_m, terms=MSF_MERGE_POINT | MSF_MERGE_FIELD, out=None):
+    """§3.3 merging. centers [K][6] fp32 (host or device). Returns (map, n_groups); the map is
+    written to `out` when given (host or device int32 [K]), else to a new numpy array."""
+    cp, ck = _ptr_kind(centers)
+    K = int(centers.shape[0])
+    m = np.empty(K, np.int32) if out is None else out
+    mp, mk = _ptr_kind(m)
+    g = ctypes.c_int32(0)
+    _check(load_library().msf_merge_clusters(ctx, cp, ck, K, float(eps_m), int(terms), mp, mk,
+                                             ctypes.byref(g)), "msf_merge_clusters")
+    return m, int(g.value)
+
+
+def msf_relabel(ctx, labels, mapping):
+    """labels[i] = map[labels[i]] in place (host or device buffers)."""
+    lp, lk = _ptr_kind(labels)
+    mp, mk = _ptr_kind(mapping)
+    n = int(np.prod(labels.shape))
+    _check(load_library().msf_relabel(ctx, lp, lk, n, mp, mk, int(mapping.shape[0])),
+           "msf_relabel")
+
+
+def msf_cluster_stats(ctx, t0, t1, attr, field_labels, point_labels, K):
+    """§3.4 per-cluster summaries; returns a numpy record array [K] (CLUSTER_STAT_DTYPE)."""
+    fp, fk = _ptr_kind(field_labels)
+    pp, pk = _ptr_kind(point_labels)
+    if field_labels is not None and point_labels is not None and fk != pk:
+        raise ValueError("label buffers must be both host or both device")
+    kind = fk if field_labels is not None else pk
+    out = np.zeros(int(K), CLUSTER_STAT_DTYPE)
+    _check(load_library().msf_cluster_stats(ctx, int(t0), int(t1), int(attr), fp, pp, kind,
+                                            int(K), out.ctypes.data, MSF_HOST),
+           "msf_cluster_stats")
+    return out
+
+
+def msf_select_clusters(ctx, centers, lo, hi):
+    """§3.4 range query over centre properties: ascending int32 indices (numpy)."""
+    cp, ck = _ptr_kind(centers)
+    K = int(centers.shape[0])
+    lo = np.ascontiguousarray(lo, np.float32)
+    hi = np.ascontiguousarray(hi, np.float32)
+    n = ctypes.c_int32(0)
+    lib = load_library()
+    st = lib.msf_select_clusters(ctx, cp, ck, K, lo.ctypes.data, hi.ctypes.data, None, MSF_HOST,
+                                 0, ctypes.byref(n))
+    if st not in (MSF_OK, MSF_ERR_CAPACITY):
+        _check(st, "msf_select_clusters")
+    out = np.empty(max(n.value, 1), np.int32)
+    _check(lib.msf_select_clusters(ctx, cp, ck, K, lo.ctypes.data, hi.ctypes.data,
+                                   out.ctypes.data, MSF_HOST, out.size, ctypes.byref(n)),
+           "msf_select_clusters")
+    return out[:n.value].copy()
+
+
+def msf_split_trajectories(ctx, t0, t1, labels, space, min_len=2, out=None):
+    """§3.4 trajectory pieces. Returns an int32 array [n][4] (point, t_start, length, label);
+    `out` (host or device int32 [cap][4]) is filled instead when given and large enough, and
+    (out, n) is returned."""
+    lp, lk = _ptr_kind(labels)
+    n = ctypes.c_int64(0)
+    lib = load_library()
+    if out is not None:
+        op, ok = _ptr_kind(out)
+        _check(lib.msf_split_trajectories(ctx, int(t0), int(t1), lp, lk, int(space),
+                                          int(min_len), op, ok, int(out.shape[0]),
+                                          ctypes.byref(n)), "msf_split_trajectories")
+        return out, int(n.value)
+    st = lib.msf_split_trajectories(ctx, int(t0), int(t1), lp, lk, int(space), int(min_len),
+                                    None, MSF_HOST, 0, ctypes.byref(n))
+    if st not in (MSF_OK, MSF_ERR_CAPACITY):
+        _check(st, "msf_split_trajectories")
+    res = np.empty((max(n.value, 1), 4), np.int32)
+    _check(lib.msf_split_trajectories(ctx, int(t0), int(t1), lp, lk, int(space), int(min_len),
+                                      res.ctypes.data, MSF_HOST, res.shape[0], ctypes.byref(n)),
+           "msf_split_trajectories")
+    return res[:n.value].copy()
+
+
 class Context:
     """Owns one msf_ctx on a device; all calls run on the given (or torch's current) stream."""
 
@@ -492,6 +602,21 @@ class Context:
         prm = make_cluster_params(t0, t1, attr, k, w_p, w_f, w_d, c_f, eps_c, max_iter)
         centers, counts, it = msf_cluster(self.h, prm, fl, pl.contiguous() if self.P else None)
         return fl, pl, centers, counts, it
+
+    def merge_clusters(self, centers, eps_m, terms=MSF_MERGE_POINT | MSF_MERGE_FIELD, out=None):
+        return msf_merge_clusters(self.h, centers, eps_m, terms, out)
+
+    def relabel(self, labels, mapping):
+        msf_relabel(self.h, labels, mapping)
+
+    def cluster_stats(self, t0, t1, attr, field_labels, point_labels, K):
+        return msf_cluster_stats(self.h, t0, t1, attr, field_labels, point_labels, K)
+
+    def select_clusters(self, centers, lo, hi):
+        return msf_select_clusters(self.h, centers, lo, hi)
+
+    def split_trajectories(self, t0, t1, labels, space, min_len=2, out=None):
+        return msf_split_trajectories(self.h, t0, t1, labels, space, min_len, out)
 
     def set_wait_limit(self, cycles):
         msf_set_wait_limit(self.h, cycles)
