@@ -275,7 +275,9 @@ def run_gpu(args):
     clustering = None
     if rank == 0 and not args.no_cluster:
         ctx.bin()
-        clustering = run_clustering(ctx, wl, dev)
+        clustering, last = run_clustering(ctx, wl, dev)
+        clustering["post"] = run_post(ctx, wl, dev, *last)
+        del last
     # the batched and served forms are reported from rank 0 (each replica would measure the same)
     batched = None
     if rank == 0 and not args.no_batched:
@@ -504,7 +506,6 @@ def run_clustering(ctx, wl, dev, reps=3):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     samples = int(n.sum())
-    del fl, pl
     ctx.kernel_times(reset=True)
     ctx.profiling(True)                     # one more run for the per-kernel split
     ctx.cluster(0, T, 0, k, **args)
@@ -536,7 +537,63 @@ def run_clustering(ctx, wl, dev, reps=3):
             "kernels_ms": kms,
             "tiny_like_for_like": {"gpu_ms": round(g_ms, 3), "oracle_ms": round(c_ms, 1),
                                    "oracle_cores": 1, "updates": tit,
-                                   "identical_updates": ores[4] == tit}}
+                                   "identical_updates": ores[4] == tit}}, (fl, pl, c)
+
+
+def run_post(ctx, wl, dev, fl, pl, c, reps=5):
+    """The steps after a clustering, on its result (§3.3, §3.4): merging its centres (eps_m =
+    0.05, both value terms), relabelling its field labels, its per-cluster summaries, a range
+    query, and the trajectory pieces of its point labels and of the step's feature labels. Each
+    is timed through its C-ABI call (which synchronises), host clock, median of `reps`."""
+    import numpy as np
+    import torch
+
+    from paper_1903_12294_gb300 import msf
+    T = wl.field.shape[0]
+    P = wl.pos.shape[2]
+    K = len(c)
+    cd = torch.as_tensor(c).to(dev)
+    seg, _ = ctx.segment(wl.t0, wl.t1, wl.preds, wl.edges)
+    lo = np.full(6, -np.inf, np.float32)
+    hi = np.full(6, np.inf, np.float32)
+    lo[5] = 0.5                                   # centres of high field value
+    mapd = torch.empty(K, dtype=torch.int32, device=dev)
+    out = {}
+
+    def timed(name, fn, units=None, unit=None):
+        fn()                                      # warm-up
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            r = fn()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        ms = float(np.median(ts))
+        out[name] = {"ms": round(ms, 3)}
+        if units is not None:
+            out[name][unit] = round(units / (ms * 1e-3) / 1e9, 3)
+        return r
+
+    _, groups = timed("merge", lambda: ctx.merge_clusters(cd, 0.05, out=mapd),
+                      K * (K - 1) / 2, "g_pairs_per_s")
+    out["merge"].update({"centres": K, "groups": groups})
+    fl2 = fl.clone()
+    timed("relabel", lambda: ctx.relabel(fl2, mapd), fl.numel(), "g_labels_per_s")
+    st = timed("cluster_stats", lambda: ctx.cluster_stats(0, T, 0, fl, pl, K),
+               fl.numel() + pl.numel(), "g_samples_per_s")
+    out["cluster_stats"]["non_empty"] = int(((st["n_field"] + st["n_point"]) > 0).sum())
+    sel = timed("select", lambda: ctx.select_clusters(cd, lo, hi))
+    out["select"]["selected"] = int(len(sel))
+    # pieces into a device buffer of the right size (one count, scan and write pass per call)
+    for name, t0, t1, lab, space in [("pieces_points", 0, T, pl, msf.MSF_SPACE_POINTS),
+                                     ("pieces_voxels", wl.t0, wl.t1, seg, msf.MSF_SPACE_VOXELS)]:
+        n = len(ctx.split_trajectories(t0, t1, lab, space))
+        buf = torch.empty((max(n, 1), 4), dtype=torch.int32, device=dev)
+        timed(name, lambda: ctx.split_trajectories(t0, t1, lab, space, out=buf),
+              P * (t1 - t0), "g_point_samples_per_s")
+        out[name]["pieces"] = n
+        del buf
+    del seg, fl2
+    return out
 
 
 def _oracle_sample(wl, t_lo, t_hi):
