@@ -370,8 +370,45 @@ int msf_segment_field_noalloc(int nx, int ny, int nz, int tw, const float* field
 /* ---- tuning, profiling ---------------------------------------------------------------- */
 
 /* Tile shape of the labelling kernels: 32 x by x bz x bt voxel-timesteps with by*bz*bt = 256
- * and each a power of two. (0,0,0) restores the automatic choice. Errors: INVALID_ARG. */
+ * and each a power of two. (0,0,0) restores the automatic choice (a tuned shape when
+ * msf_autotune has tuned the problem's shape, else a fixed rule). Errors: INVALID_ARG. */
 int msf_set_tile(msf_ctx* ctx, int by, int bz, int bt);
+
+/* Schedule bits of msf_segment. Labels are canonical, so every schedule gives the same labels. */
+#define MSF_SCHED_FUSED_CRITERION 1 /* criterion inside the tile pass (else a streaming pass) */
+#define MSF_SCHED_SERIAL_JOINS 2    /* trajectory joins after the cross-tile joins on the
+                                       context stream (else side by side on two streams)     */
+
+/* Fix the schedule of msf_segment (MSF_SCHED_* bits), or -1 for the automatic one (a tuned
+ * schedule when msf_autotune has tuned the problem's shape, else 0). Errors: INVALID_ARG. */
+int msf_set_schedule(msf_ctx* ctx, int sched);
+
+/* Result of msf_autotune. */
+typedef struct {
+  int32_t by, bz, bt; /* chosen tile shape                                               */
+  int32_t sched;      /* chosen MSF_SCHED_* bits                                         */
+  float ms;           /* median time of msf_segment with them (device, CUDA events)      */
+  float ms_default;   /* the same for the fixed rule's tile shape and schedule 0         */
+  int32_t n_tried;    /* configurations timed                                            */
+} msf_tune_result;
+
+/* Time msf_segment on `crit` over tile shapes (by, bz, bt: powers of two with product 256,
+ * each at most the next power of two of ny, nz and the window length; by, bz >= 2 unless the
+ * grid is 2D) and the four schedules, `reps` timed runs each after one warm-up (reps < 1: 3),
+ * and keep the fastest for the problem's shape: grid, window length, edge classes and number
+ * of predicates. Later msf_segment calls with that shape use it unless msf_set_tile or
+ * msf_set_schedule fixed a choice. The paper has no counterpart (it has one GPU kernel per
+ * step). Invalidates the retained segmentation (call msf_segment again before
+ * msf_extract_features). `out` may be NULL. Synchronises the stream.
+ * Errors: those of msf_segment; INVALID_ARG for an empty window. */
+int msf_autotune(msf_ctx* ctx, const msf_criteria* crit, int reps, msf_tune_result* out);
+
+/* The tile shape and schedule msf_segment would use for `crit` now (cfg = by, bz, bt, sched).
+ * Errors: NOT_LOADED, INVALID_ARG. */
+int msf_get_tuning(msf_ctx* ctx, const msf_criteria* crit, int32_t cfg[4]);
+
+/* Forget every tuned configuration of this context. */
+int msf_tune_clear(msf_ctx* ctx);
 
 /* Per-kernel timing: when enabled, every kernel the context launches is bracketed by CUDA
  * events on its stream; msf_kernel_times fills up to `cap` (name, total ms, launches) entries

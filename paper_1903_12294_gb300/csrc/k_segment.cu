@@ -1029,35 +1029,47 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   a.edges = crit->edges;
   a.labels = labels;
   cudaStream_t s = ctx->stream;
+  const int sched = segment_schedule(ctx, crit);
   MSF_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * 4, s));
-  {
-    ScopedKernel k(ctx, "k_mask");
-    if ((a.g.nx & 3) == 0) launch_mask_np<true>(a, s);
-    else launch_mask_np<false>(a, s);
-  }
-  {
+  if (sched & MSF_SCHED_FUSED_CRITERION) {
+    // the criterion evaluated inside the tile pass (one kernel, latency-bound phases)
+    ScopedKernel k(ctx, "k_tile");
+    launch_tile_any(a, spatial, g.ntiles, s);
+  } else {
+    // the criterion as a streaming pass, the tile pass then starting from its row masks
+    {
+      ScopedKernel k(ctx, "k_mask");
+      if ((a.g.nx & 3) == 0) launch_mask_np<true>(a, s);
+      else launch_mask_np<false>(a, s);
+    }
     ScopedKernel k(ctx, "k_tile");
     if (spatial) launch_tile<-1, true, false>(a, g.ntiles, s);
     else launch_tile<-1, false, false>(a, g.ntiles, s);
   }
   MSF_CUDA_TRY(cudaGetLastError());
-  // cross-tile joins and trajectory joins touch only the union-find and commute: they run
-  // side by side, the trajectory pass on the auxiliary stream
+  // cross-tile joins and trajectory joins touch only the union-find and commute: by default
+  // they run side by side, the trajectory pass on the auxiliary stream; the serial schedule
+  // runs the trajectory pass after the cross-tile joins on the context stream
   const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1;
-  if (traj) {
-    MSF_TRY(ctx_fork(ctx));
-    ScopedKernel k(ctx, "k_links", ctx->aux);
+  const bool serial = sched & MSF_SCHED_SERIAL_JOINS;
+  auto links = [&](cudaStream_t ls) {
+    ScopedKernel k(ctx, "k_links", ls);
     const int64_t nchunk = (g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
     dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
-    if (spatial) k_links<true><<<grid, 256, 0, ctx->aux>>>(a);
-    else k_links<false><<<grid, 256, 0, ctx->aux>>>(a);
+    if (spatial) k_links<true><<<grid, 256, 0, ls>>>(a);
+    else k_links<false><<<grid, 256, 0, ls>>>(a);
+  };
+  if (traj && !serial) {
+    MSF_TRY(ctx_fork(ctx));
+    links(ctx->aux);
   }
   if ((crit->edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0) {
     ScopedKernel k(ctx, "k_hook");
     if (spatial) k_hook<true><<<g.ntiles, 256, 0, s>>>(a);
     else k_hook<false><<<g.ntiles, 256, 0, s>>>(a);
   }
-  if (traj) MSF_TRY(ctx_join(ctx));
+  if (traj && serial) links(s);
+  if (traj && !serial) MSF_TRY(ctx_join(ctx));
   {
     ScopedKernel k(ctx, "k_flatten");
     k_flatten<<<g.ntiles, 256, 0, s>>>(a);

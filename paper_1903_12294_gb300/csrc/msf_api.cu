@@ -190,10 +190,15 @@ int make_geometry(const msf_ctx* ctx, const msf_criteria* c, Geometry* g) {
   g->tw = c->t1 - c->t0;
   g->nxs = (d.nx + 31) / 32;
   int by, bz, bt;
+  const TuneEntry* tuned = ctx->tile_by ? nullptr : tune_find(ctx, c);
   if (ctx->tile_by) {
     by = ctx->tile_by;
     bz = ctx->tile_bz;
     bt = ctx->tile_bt;
+  } else if (tuned) {
+    by = tuned->by;
+    bz = tuned->bz;
+    bt = tuned->bt;
   } else if (d.nz == 1) {
     bz = 1;
     bt = std::min(16, 1 << ilog2(std::max(1, g->tw)));

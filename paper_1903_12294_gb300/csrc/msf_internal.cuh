@@ -161,6 +161,15 @@ struct PostScratch {
   }
 };
 
+// A tuned configuration of msf_segment for one problem shape (msf_autotune): the key is the
+// grid, the window length, the edge classes and the number of predicates.
+struct TuneEntry {
+  int nx, ny, nz, tw, npred;
+  uint32_t edges;
+  int by, bz, bt, sched;
+  float ms;
+};
+
 // Named kernel timing (optional; on the context stream).
 struct KernelTimer {
   bool enabled = false;
@@ -199,6 +208,8 @@ struct msf_ctx {
   msf::SegState last;        // retained segmentation of the last msf_segment call
   uint64_t epoch = 1;        // bumped whenever the dataset or its binning changes
   int tile_by = 0, tile_bz = 0, tile_bt = 0;
+  int sched = -1;                    // msf_segment schedule set by msf_set_schedule (-1: auto)
+  std::vector<msf::TuneEntry> tune;  // msf_autotune results, one per problem shape
   msf::KernelTimer timer;
   std::atomic<int> servers{0};  // query servers attached (the dataset is frozen meanwhile)
   long long wait_cycles = msf::kWaitCycles;  // limit of the kernels' bounded waits
@@ -633,6 +644,8 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc);
 bool seg_state_matches(const msf_ctx* ctx, const msf_criteria* crit, const void* labels);
 int validate_criteria(const msf_ctx* ctx, const msf_criteria* c);
 int make_geometry(const msf_ctx* ctx, const msf_criteria* c, Geometry* g);
+const TuneEntry* tune_find(const msf_ctx* ctx, const msf_criteria* c);
+int segment_schedule(const msf_ctx* ctx, const msf_criteria* c);  // MSF_SCHED_* bits
 void make_preds(const msf_ctx* ctx, const msf_criteria* c, DevPred* out);
 
 }  // namespace msf

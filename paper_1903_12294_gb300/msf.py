@@ -34,7 +34,9 @@ EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_segment_field_noalloc", "msf_segment_batch", "msf_server_create",
            "msf_server_submit", "msf_server_poll", "msf_server_release", "msf_server_get_stats",
            "msf_server_destroy", "msf_set_wait_limit", "msf_cluster", "msf_merge_clusters",
-           "msf_relabel", "msf_cluster_stats", "msf_select_clusters", "msf_split_trajectories")
+           "msf_relabel", "msf_cluster_stats", "msf_select_clusters", "msf_split_trajectories",
+           "msf_set_schedule", "msf_autotune", "msf_get_tuning", "msf_tune_clear")
+MSF_SCHED_FUSED_CRITERION, MSF_SCHED_SERIAL_JOINS = 1, 2
 MSF_MERGE_POINT, MSF_MERGE_FIELD = 1, 2
 MSF_SPACE_POINTS, MSF_SPACE_VOXELS = 0, 1
 
@@ -75,6 +77,12 @@ class msf_cluster_stat(ctypes.Structure):
                 ("lo", ctypes.c_float * 4), ("hi", ctypes.c_float * 4),
                 ("mean_field", ctypes.c_double), ("std_field", ctypes.c_double),
                 ("mean_point", ctypes.c_double), ("std_point", ctypes.c_double)]
+
+
+class msf_tune_result(ctypes.Structure):
+    _fields_ = [("by", ctypes.c_int32), ("bz", ctypes.c_int32), ("bt", ctypes.c_int32),
+                ("sched", ctypes.c_int32), ("ms", ctypes.c_float), ("ms_default", ctypes.c_float),
+                ("n_tried", ctypes.c_int32)]
 
 
 class msf_piece(ctypes.Structure):
@@ -167,6 +175,11 @@ def load_library(path: str = LIB_PATH):
                                             ctypes.POINTER(ctypes.c_int32)]
         lib.msf_split_trajectories.argtypes = [P, i32, i32, P, i32, i32, i32, P, i32, i64,
                                                ctypes.POINTER(ctypes.c_int64)]
+        lib.msf_set_schedule.argtypes = [P, i32]
+        lib.msf_autotune.argtypes = [P, ctypes.POINTER(msf_criteria), i32,
+                                     ctypes.POINTER(msf_tune_result)]
+        lib.msf_get_tuning.argtypes = [P, ctypes.POINTER(msf_criteria), P]
+        lib.msf_tune_clear.argtypes = [P]
         lib.msf_status_string.argtypes = [i32]
         lib.msf_status_string.restype = ctypes.c_char_p
         for n in EXPORTS:
@@ -425,6 +438,30 @@ class _DeviceInt32:
 # convenience wrappers
 # ---------------------------------------------------------------------------------------------
 
+def msf_set_schedule(ctx, sched: int):
+    _check(load_library().msf_set_schedule(ctx, int(sched)), "msf_set_schedule")
+
+
+def msf_autotune(ctx, crit: msf_criteria, reps: int = 3) -> dict:
+    """Tune msf_segment's tile shape and schedule for crit's problem shape; returns the result
+    as a dict (by, bz, bt, sched, ms, ms_default, n_tried)."""
+    r = msf_tune_result()
+    _check(load_library().msf_autotune(ctx, ctypes.byref(crit), int(reps), ctypes.byref(r)),
+           "msf_autotune")
+    return {f: getattr(r, f) for f, _ in msf_tune_result._fields_}
+
+
+def msf_get_tuning(ctx, crit: msf_criteria):
+    """(by, bz, bt, sched) msf_segment would use for crit now."""
+    cfg = (ctypes.c_int32 * 4)()
+    _check(load_library().msf_get_tuning(ctx, ctypes.byref(crit), cfg), "msf_get_tuning")
+    return tuple(cfg)
+
+
+def msf_tune_clear(ctx):
+    _check(load_library().msf_tune_clear(ctx), "msf_tune_clear")
+
+
 # numpy views of the record types (field order and offsets as in the C structs)
 CLUSTER_STAT_DTYPE = np.dtype({
     "names": [f for f, _ in msf_cluster_stat._fields_],
@@ -602,6 +639,18 @@ class Context:
         prm = make_cluster_params(t0, t1, attr, k, w_p, w_f, w_d, c_f, eps_c, max_iter)
         centers, counts, it = msf_cluster(self.h, prm, fl, pl.contiguous() if self.P else None)
         return fl, pl, centers, counts, it
+
+    def set_schedule(self, sched):
+        msf_set_schedule(self.h, sched)
+
+    def autotune(self, t0, t1, preds=(), edges=MSF_EDGE_ALL, reps=3):
+        return msf_autotune(self.h, make_criteria(t0, t1, preds, edges), reps)
+
+    def tuning(self, t0, t1, preds=(), edges=MSF_EDGE_ALL):
+        return msf_get_tuning(self.h, make_criteria(t0, t1, preds, edges))
+
+    def tune_clear(self):
+        msf_tune_clear(self.h)
 
     def merge_clusters(self, centers, eps_m, terms=MSF_MERGE_POINT | MSF_MERGE_FIELD, out=None):
         return msf_merge_clusters(self.h, centers, eps_m, terms, out)

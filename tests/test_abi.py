@@ -57,7 +57,7 @@ def test_struct_layouts_match_c_compiler(msflib, tmp_path):
         import pytest
         pytest.skip("no C compiler")
     structs = ["msf_pred", "msf_criteria", "msf_bin_stats", "msf_feature", "msf_server_config",
-               "msf_server_result", "msf_server_stats", "msf_cluster_params", "msf_cluster_stat",
+               "msf_server_result", "msf_server_stats", "msf_cluster_params", "msf_cluster_stat", "msf_tune_result",
                "msf_piece"]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "msf.h"', "int main(void) {"]
     for s in structs:
