@@ -103,17 +103,20 @@ class Clocks:
 # per-kernel algorithmic bytes: the bytes each kernel must move through HBM per launch by the
 # definition of its step (inputs it alone reads, outputs it alone writes); traffic of
 # intermediate state (sorted records, segment masks, union-find tables) is not counted
-def algorithmic_bytes(wl, n_pred_arrays, keep_sumq=False):
+def algorithmic_bytes(wl, n_pred_arrays, keep_sumq=False, fused_criterion=False):
     T, nz, ny, nx = wl.field.shape
     V = nx * ny * nz
     tw = wl.t1 - wl.t0
     P = wl.pos.shape[2]
     A = wl.attr.shape[1]
+    crit = V * tw * 4 * n_pred_arrays                        # field + predicate arrays in
     return {
         "k_bin_keys": P * T * (12 + 4),                      # positions in, voxel keys out
         "k_bin_place": P * T * 4 * A,                        # attributes in
         "k_bin_reduce": V * T * (4 + 4 * A + (8 * A if keep_sumq else 0)),  # count + means out
-        "k_mask": V * tw * 4 * n_pred_arrays,                # field + predicate arrays in
+        # the criterion's reads belong to its streaming pass, or to the tile pass that
+        # evaluates it when the schedule fuses them
+        ("k_tile" if fused_criterion else "k_mask"): crit,
         "k_links": P * tw * 4,                               # keys of the window in
         "k_final": V * tw * 4,                               # labels out
         "k_feat_vox": V * tw * 8,                            # labels + field in
@@ -153,6 +156,13 @@ def run_gpu(args):
     nf_out = msf.ctypes.c_int64(0)
 
     ctx.load(wl.field, wl.pos, wl.attr)
+    tuning = None
+    if not args.no_tune:
+        # tile shape and schedule of the query's segment pass picked by the library's
+        # autotuner (untimed, before the warm-up; every choice gives the same labels)
+        msf.msf_bin_particles(ctx.h, 0)
+        tuning = msf.msf_autotune(ctx.h, crit, 3)
+        tuning = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tuning.items()}
 
     def step():
         msf.msf_bin_particles(ctx.h, 0)
@@ -189,7 +199,8 @@ def run_gpu(args):
 
     # dominant kernel and its roofline (CUDA events around every launch on the context stream)
     npa = len({(s, a if s == 2 else 0) for s, a, *_ in wl.preds})
-    abytes = algorithmic_bytes(wl, npa)
+    fused = bool(msf.msf_get_tuning(ctx.h, crit)[3] & msf.MSF_SCHED_FUSED_CRITERION)
+    abytes = algorithmic_bytes(wl, npa, fused_criterion=fused)
     peak, peak_kind = peaks()
     per_kernel = {}
     for k, (tot, nl) in ktimes.items():
@@ -299,7 +310,7 @@ def run_gpu(args):
                        "step": "bin + criterion/label + features", "vt_per_step": vt,
                        "n_features": int(n_features),
                        "l2": "inputs larger than L2 (field alone 4*V*T bytes)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "tuning": tuning},
             "segment_only": {"ms": round(seg_ms, 4),
                              "value": round(vt / (seg_ms * 1e-3) / 1e9, 3) if seg_ms else None,
                              "unit": UNIT},
@@ -658,6 +669,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="segment with the fixed tile rule and schedule instead of the autotuner's")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
