@@ -221,6 +221,18 @@ int msf_extract_features(msf_ctx* ctx, const msf_criteria* crit, const int32_t* 
 int msf_segment_batch(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
                       int64_t* n_features);
 
+/* Replay batches through a captured CUDA graph (enable != 0; off by default). A batch whose
+ * shape (the dataset, each query's window, edge classes, predicate sources and operators, and
+ * the alignment of its label buffers) repeats the previous one's is run the first time as usual,
+ * captured into a graph the second time, and replayed from the graph from then on: the host
+ * then only fills the query tables (thresholds and label addresses may change between replays)
+ * and launches one graph. Results are identical either way. Disabling frees the graph.
+ * Errors: INVALID_ARG. */
+int msf_set_batch_graphs(msf_ctx* ctx, int enable);
+
+/* Number of batches this context has run by replaying a graph (host, may be NULL). */
+int msf_batch_graph_replays(msf_ctx* ctx, int64_t* replays);
+
 /* ---- multifaceted 4D clustering ------------------------------------------------------- */
 
 /* The paper's own segmentation (§3.2): a SLIC-style clustering of the field samples and the

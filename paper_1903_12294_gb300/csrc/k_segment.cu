@@ -1831,10 +1831,9 @@ static int launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b, 
   return MSF_OK;
 }
 
-int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* const* scratch,
-                     char* plan_dev, char* plan_host, cudaStream_t s, const StreamPair& sp,
-                     bool timed) {
-  // host image of every group's tables (the counts area is written by the device)
+// host image of every group's tables (the counts area is written by the device)
+static void batch_job_fill(BatchJob* job, int32_t* const* labels, char* const* scratch,
+                           char* plan_host) {
   for (BatchGroup& gr : job->groups) {
     const int nq = (int)gr.qs.size();
     for (int i = 0; i < nq; ++i) {
@@ -1866,6 +1865,11 @@ int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* 
     for (auto v : gr.row_q) h32[o++] = v;
     for (auto v : gr.row_tw) h32[o++] = v;
   }
+}
+
+// the plan up, every group's launches, the counts back: stream work only (capturable)
+static int batch_job_enqueue(msf_ctx* ctx, BatchJob* job, char* plan_dev, char* plan_host,
+                             cudaStream_t s, const StreamPair& sp, bool timed) {
   if (job->groups.empty()) return MSF_OK;
   // one copy of the tables up (the counts at the end of each group come back)
   MSF_CUDA_TRY(cudaMemcpyAsync(plan_dev, plan_host, job->plan_bytes, cudaMemcpyHostToDevice, s));
@@ -1898,6 +1902,63 @@ int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* 
   MSF_CUDA_TRY(cudaMemcpyAsync(plan_host + c0, plan_dev + c0, job->plan_bytes - c0,
                                cudaMemcpyDeviceToHost, s));
   return MSF_OK;
+}
+
+int batch_job_launch(msf_ctx* ctx, BatchJob* job, int32_t* const* labels, char* const* scratch,
+                     char* plan_dev, char* plan_host, cudaStream_t s, const StreamPair& sp,
+                     bool timed) {
+  batch_job_fill(job, labels, scratch, plan_host);
+  return batch_job_enqueue(ctx, job, plan_dev, plan_host, s, sp, timed);
+}
+
+// Everything the enqueued work of a batch takes by value besides the uploaded tables: the
+// dataset (epoch), the arena and host image addresses, each query's shape (window, edges,
+// predicate sources and operators) and whether its labels allow 16-byte stores. Thresholds and
+// label addresses travel in the tables, so a batch that differs only in those replays.
+static std::vector<int64_t> batch_signature(const msf_ctx* ctx, int nq, const msf_criteria* crits,
+                                            int32_t* const* labels, const char* base,
+                                            const char* host, size_t plan_bytes) {
+  std::vector<int64_t> sig = {(int64_t)ctx->epoch, (int64_t)(uintptr_t)base,
+                              (int64_t)(uintptr_t)host, (int64_t)plan_bytes, nq};
+  for (int i = 0; i < nq; ++i) {
+    const msf_criteria& c = crits[i];
+    sig.push_back(((int64_t)c.t0 << 32) | (uint32_t)c.t1);
+    sig.push_back(((int64_t)c.edges << 8) | ((int64_t)c.n_pred << 1) |
+                  (((uintptr_t)labels[i] & 15) == 0));
+    for (int j = 0; j < c.n_pred; ++j)
+      sig.push_back(((int64_t)c.pred[j].src << 40) | ((int64_t)c.pred[j].attr << 20) |
+                    c.pred[j].op);
+  }
+  return sig;
+}
+
+// Capture the batch's stream work into a graph and instantiate it (on a stream of the
+// context's own; nothing runs while capturing). On any failure the stream leaves capture mode
+// and the caller launches normally.
+static bool capture_batch(msf_ctx* ctx, BatchJob* job, char* plan_dev, char* plan_host,
+                          const StreamPair& sp, cudaGraphExec_t* exec) {
+  BatchScratch& B = ctx->batch;
+  if (!B.capture && cudaStreamCreateWithFlags(&B.capture, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    B.capture = nullptr;
+    return false;
+  }
+  cudaStream_t s = B.capture;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int st = batch_job_enqueue(ctx, job, plan_dev, plan_host, s, sp, false);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  bool ok = st == MSF_OK && e == cudaSuccess && graph;
+  if (ok) ok = cudaGraphInstantiate(exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();
+    *exec = nullptr;
+  }
+  return ok;
 }
 
 int batch_job_finish(const BatchJob* job, const char* plan_host, int64_t* n_features,
@@ -1952,8 +2013,36 @@ int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* 
   for (int i = 0; i < nq; ++i) scratch[i] = base + off[i];
   char* host = static_cast<char*>(ctx->batch.host);
   MSF_TRY(ctx_aux(ctx));
-  MSF_TRY(batch_job_launch(ctx, job, labels, scratch.data(), base + off_plan, host, ctx->stream,
-                           StreamPair{ctx->aux, ctx->ev_fork, ctx->ev_join}, true));
+  const StreamPair sp{ctx->aux, ctx->ev_fork, ctx->ev_join};
+  BatchScratch& B = ctx->batch;
+  bool launched = false;
+  if (B.graphs && !job->groups.empty()) {
+    // a shape seen before: fill the tables and replay its graph (captured on its second sight,
+    // after one plain run has set up every kernel attribute)
+    std::vector<int64_t> sig =
+        batch_signature(ctx, nq, crits, labels, base, host, job->plan_bytes);
+    if (B.graph && sig == B.graph_sig) {
+      batch_job_fill(job, labels, scratch.data(), host);
+      MSF_CUDA_TRY(cudaGraphLaunch(B.graph, ctx->stream));
+      ++B.graph_replays;
+      launched = true;
+    } else if (sig == B.seen_sig) {
+      batch_job_fill(job, labels, scratch.data(), host);
+      cudaGraphExec_t exec = nullptr;
+      if (capture_batch(ctx, job, base + off_plan, host, sp, &exec)) {
+        B.drop_graph();
+        B.graph = exec;
+        B.graph_sig = sig;
+        MSF_CUDA_TRY(cudaGraphLaunch(B.graph, ctx->stream));
+        launched = true;
+      }
+    } else {
+      B.seen_sig = std::move(sig);
+    }
+  }
+  if (!launched)
+    MSF_TRY(batch_job_launch(ctx, job, labels, scratch.data(), base + off_plan, host,
+                             ctx->stream, sp, true));
   MSF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   ctx->timer.flush();
   std::vector<int64_t> nf(nq, 0);

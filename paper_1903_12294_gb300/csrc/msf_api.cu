@@ -57,7 +57,17 @@ int BatchScratch::ensure_host(size_t n) {
   return MSF_OK;
 }
 
+void BatchScratch::drop_graph() {
+  if (graph) cudaGraphExecDestroy(graph);
+  graph = nullptr;
+  graph_sig.clear();
+  seen_sig.clear();
+}
+
 void BatchScratch::release() {
+  drop_graph();
+  if (capture) cudaStreamDestroy(capture);
+  capture = nullptr;
   arena.release();
   if (host) cudaFreeHost(host);
   host = nullptr;
@@ -567,6 +577,22 @@ int msf_set_tile(msf_ctx* c, int by, int bz, int bt) {
   c->tile_by = by;
   c->tile_bz = bz;
   c->tile_bt = bt;
+  return MSF_OK;
+}
+
+int msf_set_batch_graphs(msf_ctx* c, int enable) {
+  if (!c) return MSF_ERR_INVALID_ARG;
+  c->batch.graphs = enable != 0;
+  if (!enable) {
+    cudaSetDevice(c->device);
+    c->batch.drop_graph();
+  }
+  return MSF_OK;
+}
+
+int msf_batch_graph_replays(msf_ctx* c, int64_t* replays) {
+  if (!c) return MSF_ERR_INVALID_ARG;
+  if (replays) *replays = c->batch.graph_replays;
   return MSF_OK;
 }
 

@@ -136,7 +136,16 @@ struct BatchScratch {
   DevBuf arena;
   void* host = nullptr;
   size_t host_bytes = 0;
+  // captured launch sequence of the last batch shape seen twice (msf_set_batch_graphs): its
+  // signature holds everything the launches take by value (grids, table offsets, pointers)
+  bool graphs = false;
+  std::vector<int64_t> seen_sig, graph_sig;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t capture = nullptr;  // a stream of this context's own to capture on (the context
+                                   // stream may be the legacy default stream, which cannot be)
+  int64_t graph_replays = 0;
   int ensure_host(size_t n);
+  void drop_graph();
   void release();
 };
 

@@ -35,7 +35,8 @@ EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_server_submit", "msf_server_poll", "msf_server_release", "msf_server_get_stats",
            "msf_server_destroy", "msf_set_wait_limit", "msf_cluster", "msf_merge_clusters",
            "msf_relabel", "msf_cluster_stats", "msf_select_clusters", "msf_split_trajectories",
-           "msf_set_schedule", "msf_autotune", "msf_get_tuning", "msf_tune_clear")
+           "msf_set_schedule", "msf_autotune", "msf_get_tuning", "msf_tune_clear",
+           "msf_set_batch_graphs", "msf_batch_graph_replays")
 MSF_SCHED_FUSED_CRITERION, MSF_SCHED_SERIAL_JOINS = 1, 2
 MSF_MERGE_POINT, MSF_MERGE_FIELD = 1, 2
 MSF_SPACE_POINTS, MSF_SPACE_VOXELS = 0, 1
@@ -176,6 +177,8 @@ def load_library(path: str = LIB_PATH):
         lib.msf_split_trajectories.argtypes = [P, i32, i32, P, i32, i32, i32, P, i32, i64,
                                                ctypes.POINTER(ctypes.c_int64)]
         lib.msf_set_schedule.argtypes = [P, i32]
+        lib.msf_set_batch_graphs.argtypes = [P, i32]
+        lib.msf_batch_graph_replays.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         lib.msf_autotune.argtypes = [P, ctypes.POINTER(msf_criteria), i32,
                                      ctypes.POINTER(msf_tune_result)]
         lib.msf_get_tuning.argtypes = [P, ctypes.POINTER(msf_criteria), P]
@@ -639,6 +642,16 @@ class Context:
         prm = make_cluster_params(t0, t1, attr, k, w_p, w_f, w_d, c_f, eps_c, max_iter)
         centers, counts, it = msf_cluster(self.h, prm, fl, pl.contiguous() if self.P else None)
         return fl, pl, centers, counts, it
+
+    def set_batch_graphs(self, enable=True):
+        _check(load_library().msf_set_batch_graphs(self.h, int(bool(enable))),
+               "msf_set_batch_graphs")
+
+    def batch_graph_replays(self):
+        n = ctypes.c_int64(0)
+        _check(load_library().msf_batch_graph_replays(self.h, ctypes.byref(n)),
+               "msf_batch_graph_replays")
+        return int(n.value)
 
     def set_schedule(self, sched):
         msf_set_schedule(self.h, sched)

@@ -54,3 +54,48 @@ def test_batch_2d_time(gpu, orc):
                for t0, tw, th in ((0, 20, 0.6), (3, 5, 0.5), (15, 5, 0.55), (7, 1, 0.4),
                                   (2, 17, 0.7))]
     _check_batch(gpu, orc, f, pos, a, queries)
+
+
+def test_batch_graph_replay(gpu, orc):
+    """With graphs on, a repeated batch shape runs plainly, is captured, then replays; replays
+    pick up new thresholds and new label buffers, and a new shape runs plainly again. Every
+    result equals the single queries and the oracle."""
+    wl = synth.mid(n=40, T=10, P=20000, n_blobs=8)
+    f, p, a = wl.numpy()
+    o = orc.bin(f.shape, p, a)
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(*(torch.as_tensor(x).cuda().contiguous() for x in (f, p, a)))
+        ctx.bin()
+        ctx.set_batch_graphs(True)
+        shape = [(0, 10, "q", 7), (2, 6, "f", 7), (5, 9, "c", 3)]
+
+        def queries(th):
+            pr = {"q": [(F, 0, GT, th, 0), (M, 0, BAND, 0.3, 0.9)],
+                  "f": [(F, 0, GT, th + 0.05, 0)],
+                  "c": [(F, 0, GE, th, 0), (C, 0, GE, 1, 0)]}
+            return [(t0, t1, pr[k], e) for t0, t1, k, e in shape]
+
+        seen = []
+        for it, th in enumerate([0.5, 0.45, 0.55, 0.6]):
+            qs = queries(th)
+            labels, nfs = ctx.segment_batch(qs)
+            singles = [ctx.segment(t0, t1, pr, e) for (t0, t1, pr, e) in qs]
+            seen.append((qs, [lb.cpu().numpy() for lb in labels], nfs,
+                         [(ls.cpu().numpy(), ns) for ls, ns in singles]))
+        replays = ctx.batch_graph_replays()
+        # a different shape: plain launch, correct, and no replay
+        qs = [(1, 10, [(F, 0, GT, 0.5, 0)], 7)]
+        labels, nfs = ctx.segment_batch(qs)
+        ls, ns = ctx.segment(*qs[0])
+        assert nfs[0] == ns and torch.equal(labels[0], ls)
+        assert ctx.batch_graph_replays() == replays
+        ctx.set_batch_graphs(False)
+    finally:
+        ctx.close()
+    assert replays == 2                       # runs 3 and 4 (run 2 captures and launches)
+    for qs, labs, nfs, singles in seen:
+        for (t0, t1, pr, e), lb, nf, (ls, ns) in zip(qs, labs, nfs, singles):
+            assert nf == ns and np.array_equal(lb, ls)
+            want, n_o = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
+            assert nf == n_o and np.array_equal(lb, want)
