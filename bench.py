@@ -350,7 +350,11 @@ def run_batched(dev, reps=3):
 
     out = {}
     ctx.kernel_times(reset=True)
-    for name, fn in (("plain", plain), ("batched", batch)):
+    # the last arm is the same batch with graphs on: its warm-up runs plainly, then captures,
+    # and the timed calls replay the graph
+    for name, fn in (("plain", plain), ("batched", batch), ("batched_graph", batch)):
+        if name == "batched_graph":
+            ctx.set_batch_graphs(True)
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
@@ -369,6 +373,8 @@ def run_batched(dev, reps=3):
         fn()
         ctx.profiling(False)
         out[name]["kernels_ms"] = {k: round(v[0], 3) for k, v in ctx.kernel_times(reset=True).items()}
+    replays = ctx.batch_graph_replays()
+    ctx.set_batch_graphs(False)
     # same labels both ways
     ref = [l.clone() for l in labels]
     batch()
@@ -379,7 +385,10 @@ def run_batched(dev, reps=3):
     return {"workload": f"{nx}x{ny}x{nz} x {T}, {wl.pos.shape[2]} points x {wl.attr.shape[1]} "
                         f"attrs, {len(crits)} queries, T_w in 2..32, {vt} query-voxel-timesteps",
             "plain": out["plain"], "batched": out["batched"],
+            "batched_graph": dict(out["batched_graph"], graph_replays=replays),
             "speedup": round(out["plain"]["ms_per_batch"] / out["batched"]["ms_per_batch"], 2),
+            "speedup_graph": round(out["plain"]["ms_per_batch"] /
+                                   out["batched_graph"]["ms_per_batch"], 2),
             "labels_identical": bool(same)}
 
 
