@@ -41,7 +41,9 @@ def peaks():
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
 # the same kernel code on the same workload (profiles/kernels_mid_step.md): {(config, kernel):
 # bytes}. An entry is removed whenever its kernel changes.
-TRAFFIC = {}
+TRAFFIC = {
+    (2, "k_bin_reduce"): 406_903_040 + 744_466_944,
+}
 
 
 class Clocks:
@@ -157,7 +159,13 @@ def run_gpu(args):
 
     ctx.load(wl.field, wl.pos, wl.attr)
     tuning = None
-    if not args.no_tune:
+    if args.schedule:
+        # a fixed tile shape and schedule (to profile the configuration a tuning run chose)
+        by, bz, bt, sched = (int(x) for x in args.schedule.split(","))
+        ctx.set_tile(by, bz, bt)
+        ctx.set_schedule(sched)
+        tuning = {"fixed": [by, bz, bt, sched]}
+    elif not args.no_tune:
         # tile shape and schedule of the query's segment pass picked by the library's
         # autotuner (untimed, before the warm-up; every choice gives the same labels)
         msf.msf_bin_particles(ctx.h, 0)
@@ -680,6 +688,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="segment with the fixed tile rule and schedule instead of the autotuner's")
+    ap.add_argument("--schedule", default="",
+                    help="by,bz,bt,sched: segment with this tile shape and schedule, no tuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
