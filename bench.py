@@ -46,6 +46,30 @@ TRAFFIC = {
 }
 
 
+def d2d_copy_gbs(dev, nbytes=1 << 31, reps=5):
+    """A device-to-device copy of `nbytes` (torch copy_, CUDA events, median of `reps`): bytes
+    read plus bytes written per second, beside the roofline's measured peak."""
+    import torch
+    n = nbytes // 4
+    src = torch.empty(n, dtype=torch.float32, device=dev).fill_(1.0)
+    dst = torch.empty_like(src)
+    stream = torch.cuda.current_stream(dev)
+    dst.copy_(src)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dst.copy_(src)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = sorted(ts)[len(ts) // 2]
+    del src, dst
+    torch.cuda.empty_cache()
+    return round(2 * n * 4 / (ms * 1e-3) / 1e9, 1)
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -210,6 +234,7 @@ def run_gpu(args):
     fused = bool(msf.msf_get_tuning(ctx.h, crit)[3] & msf.MSF_SCHED_FUSED_CRITERION)
     abytes = algorithmic_bytes(wl, npa, fused_criterion=fused)
     peak, peak_kind = peaks()
+    copy_gbs = d2d_copy_gbs(dev) if rank == 0 else None
     per_kernel = {}
     for k, (tot, nl) in ktimes.items():
         e = {"ms_per_step": round(tot / args.steps, 4), "launches_per_step": nl // max(args.steps, 1)}
@@ -322,7 +347,8 @@ def run_gpu(args):
             "segment_only": {"ms": round(seg_ms, 4),
                              "value": round(vt / (seg_ms * 1e-3) / 1e9, 3) if seg_ms else None,
                              "unit": UNIT},
-            "roofline": roof, "step_roofline": step_roof, "clocks": clk.summary(), "e2e": e2e,
+            "roofline": roof, "step_roofline": step_roof, "d2d_copy_gb_per_s": copy_gbs,
+            "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": int(launches), "kernels": per_kernel, "cpu_baseline": cpu,
             "batched": batched, "serving": serving, "clustering": clustering,
         }
