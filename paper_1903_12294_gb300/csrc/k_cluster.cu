@@ -61,6 +61,10 @@ struct SlicArgs {
   int32_t* plabel;              // [tw][P]
   unsigned* moved;
   unsigned long long* valid;    // [0] samples, [1] max|f| bits, [2] max|p| bits
+  uint32_t* pcell_start;        // [K + 1] first slot of each cell's point samples
+  uint32_t* pcell_cursor;       // [K]
+  float4* psample;              // [slots] x, y, z, value of the point sample in the slot
+  uint32_t* pindex;             // [slots] its index t * P + p in the window
 };
 
 constexpr float kCellMargin = 1e-3f;
@@ -434,6 +438,172 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_points(const __grid_cons
   }
 }
 
+// ---- point samples grouped by cell ----------------------------------------------------------
+// The seed-grid cell of a point sample does not change between updates (its position is fixed),
+// and every sample of one cell searches the same 3^4 neighbourhood of cells. So the point samples
+// that take part are grouped by cell once per call (a counting sort; the order within a cell is whatever
+// the atomics give, which changes nothing: each sample's result depends on it alone and the
+// centre sums are exact), and each update then takes a cell at a time against a shared list of
+// its neighbourhood's centres, reading the grouped samples in order. (Field samples are taken
+// in tiles of voxels that lie in one cell already, so they need no grouping.)
+__device__ __forceinline__ int sample_cell(const SlicArgs& a, float xs, float ys, float zs,
+                                           float ts) {
+  const int ci = cell_of(xs, a.C[0], a.k[0]), cj = cell_of(ys, a.C[1], a.k[1]);
+  const int cl = cell_of(zs, a.C[2], a.k[2]);
+  const int cm = cell_of(__fsub_rn(ts, (float)a.t0), a.C[3], a.k[3]);
+  return ((cm * a.k[2] + cl) * a.k[1] + cj) * a.k[0] + ci;
+}
+
+// point sample li (taking part after the first assignment): position and value
+__device__ __forceinline__ bool point_sample(const SlicArgs& a, int64_t li, float4& s, float& ts) {
+  if (a.plabel[li] < 0) return false;
+  const int t = (int)(li / a.P);
+  const int64_t p = li - (int64_t)t * a.P;
+  const float* ps = a.pos + (int64_t)(a.t0 + t) * 3 * a.P;
+  s = make_float4(__ldg(ps + p), __ldg(ps + a.P + p), __ldg(ps + 2 * a.P + p),
+                  __ldg(a.attrp + ((int64_t)(a.t0 + t) * a.A + a.attr) * a.P + p));
+  ts = __fadd_rn((float)(a.t0 + t), 0.5f);
+  return true;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_slic_pgroup(const __grid_constant__ SlicArgs a) {
+  const int64_t n = (int64_t)a.tw * a.P;
+  uint32_t* cursor = a.pcell_cursor;
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < n;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    float4 sm;
+    float ts;
+    if (!point_sample(a, li, sm, ts)) continue;
+    const int cell = sample_cell(a, sm.x, sm.y, sm.z, ts);
+    if (!FILL) {
+      atomicAdd(cursor + cell, 1u);
+    } else {
+      const uint32_t slot = atomicAdd(cursor + cell, 1u);
+      a.psample[slot] = sm;
+      a.pindex[slot] = (uint32_t)li;
+    }
+  }
+}
+
+// One cell at a time (persistent blocks): its neighbourhood's filed centres into shared memory,
+// then its samples in slot order. Candidates, region test, distance and tie rule as best_centre.
+__global__ void __launch_bounds__(256, 4) k_slic_assign_points_cells(const __grid_constant__ SlicArgs a) {
+  constexpr int VS = 4;  // the centre's value slot (p_c)
+  __shared__ float s_cx[kCand], s_cy[kCand], s_cz[kCand], s_ct[kCand], s_cv[kCand];
+  __shared__ int s_id[kCand];
+  __shared__ int s_warp[8];
+  __shared__ int s_total;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t* gstart = a.pcell_start;
+  const float4* gsample = a.psample;
+  const uint32_t* gindex = a.pindex;
+  int32_t* label = a.plabel;
+  const float wv = a.w_p;
+  const int kv = a.kp;
+  const uint64_t per_t = (uint64_t)a.P;
+  for (int cell = blockIdx.x; cell < a.K; cell += gridDim.x) {
+    const uint32_t first = __ldg(gstart + cell), last = __ldg(gstart + cell + 1);
+    if (first == last) continue;  // block-uniform
+    int q0 = cell;
+    const int ci = q0 % a.k[0]; q0 /= a.k[0];
+    const int cj = q0 % a.k[1]; q0 /= a.k[1];
+    const int cl = q0 % a.k[2];
+    const int cm = q0 / a.k[2];
+    const int lo0 = max(ci - 1, 0), n0 = min(ci + 1, a.k[0] - 1) - lo0 + 1;
+    const int lo1 = max(cj - 1, 0), n1 = min(cj + 1, a.k[1] - 1) - lo1 + 1;
+    const int lo2 = max(cl - 1, 0), n2 = min(cl + 1, a.k[2] - 1) - lo2 + 1;
+    const int lo3 = max(cm - 1, 0), n3 = min(cm + 1, a.k[3] - 1) - lo3 + 1;
+    const int ncell = n0 * n1 * n2 * n3;  // at most 81
+    int cnt = 0;
+    uint32_t c0 = 0;
+    if (tid < ncell) {
+      int q = tid;
+      const int i = lo0 + q % n0; q /= n0;
+      const int j = lo1 + q % n1; q /= n1;
+      const int l = lo2 + q % n2; q /= n2;
+      const int m = lo3 + q;
+      const int nb = ((m * a.k[2] + l) * a.k[1] + j) * a.k[0] + i;
+      c0 = __ldg(a.cell_start + nb);
+      cnt = (int)(__ldg(a.cell_start + nb + 1) - c0);
+    }
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    int off = x - cnt;
+    for (int q = 0; q < w; ++q) off += s_warp[q];
+    if (tid == 255) {
+      int tot = 0;
+      for (int q = 0; q < 8; ++q) tot += s_warp[q];
+      s_total = tot;
+    }
+    __syncthreads();
+    const int nc = s_total;
+    const bool over = nc > kCand;
+    if (!over)
+      for (int q = 0; q < cnt; ++q) {
+        const int c = (int)__ldg(a.cell_items + c0 + q);
+        const float* cc = a.centers + 6 * (int64_t)c;
+        s_cx[off + q] = cc[0];
+        s_cy[off + q] = cc[1];
+        s_cz[off + q] = cc[2];
+        s_ct[off + q] = cc[3];
+        s_cv[off + q] = cc[VS];
+        s_id[off + q] = c;
+      }
+    __syncthreads();
+    for (uint32_t b0 = first; b0 < last; b0 += 256) {  // block-uniform trip count
+      const uint32_t slot = b0 + tid;
+      int best = -1;
+      long long v[5] = {0, 0, 0, 0, 0};
+      if (slot < last) {
+        const float4 sm = gsample[slot];
+        const uint32_t li = gindex[slot];
+        const int t = (int)(li / per_t);
+        const float xs = sm.x, ys = sm.y, zs = sm.z, vs = sm.w;
+        const float ts = __fadd_rn((float)(a.t0 + t), 0.5f);
+        if (over) {
+          best = best_centre<false>(a, xs, ys, zs, ts, wv, vs, VS);
+        } else {
+          float bd = 0.f;
+          for (int q = 0; q < nc; ++q) {
+            const float cx = s_cx[q], cy = s_cy[q], cz = s_cz[q], ct = s_ct[q];
+            if (!(fabsf(__fsub_rn(xs, cx)) <= a.C[0] && fabsf(__fsub_rn(ys, cy)) <= a.C[1] &&
+                  fabsf(__fsub_rn(zs, cz)) <= a.C[2] && fabsf(__fsub_rn(ts, ct)) <= a.C[3]))
+              continue;
+            const float dx = __fsub_rn(cx, xs), dy = __fsub_rn(cy, ys), dz = __fsub_rn(cz, zs);
+            const float dt = __fmul_rn(a.c_f, __fsub_rn(ct, ts));
+            const float sst = __fsqrt_rn(__fadd_rn(
+                __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)),
+                __fmul_rn(dt, dt)));
+            const float d = __fadd_rn(__fmul_rn(wv, fabsf(__fsub_rn(vs, s_cv[q]))),
+                                      __fmul_rn(a.w_d, sst));
+            const int c = s_id[q];
+            if (better(d, c, bd, best)) {
+              bd = d;
+              best = c;
+            }
+          }
+        }
+        if (best < 0) best = label[li];  // no centre in range: keeps its centre
+        label[li] = best;
+        v[0] = quantise(xs, a.kpos);
+        v[1] = quantise(ys, a.kpos);
+        v[2] = quantise(zs, a.kpos);
+        v[3] = quantise(ts, a.kpos);
+        v[4] = quantise(vs, kv);
+      }
+      warp_accumulate(a.sums, best, v, VS);
+    }
+    __syncthreads();  // the shared list is rebuilt for the next cell
+  }
+}
+
 // ---- centre update ---------------------------------------------------------------------------
 __device__ __forceinline__ float fixed_mean(long long sum, long long n, int k) {
   double m = __ll2double_rn(sum);
@@ -599,6 +769,25 @@ int cluster_run(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* flabel, in
     ScopedKernel k(ctx, "k_slic_assign_points");
     k_slic_assign_points<true><<<gp, 256, 0, s>>>(a);
   }
+  if (nps > 0) {  // the taking-part point samples grouped by cell, for every later assignment
+    MSF_TRY(S.pcell_start.ensure(sizeof(uint32_t) * ((size_t)a.K + 1)));
+    MSF_TRY(S.pcell_cursor.ensure(sizeof(uint32_t) * (size_t)a.K));
+    MSF_TRY(S.psample.ensure(sizeof(float4) * (size_t)nps));
+    MSF_TRY(S.pindex.ensure(sizeof(uint32_t) * (size_t)nps));
+    a.pcell_start = S.pcell_start.as<uint32_t>();
+    a.pcell_cursor = S.pcell_cursor.as<uint32_t>();
+    a.psample = S.psample.as<float4>();
+    a.pindex = S.pindex.as<uint32_t>();
+    ScopedKernel k(ctx, "k_slic_pgroup");
+    MSF_CUDA_TRY(cudaMemsetAsync(a.pcell_cursor, 0, sizeof(uint32_t) * a.K, s));
+    k_slic_pgroup<false><<<gp, 256, 0, s>>>(a);
+    MSF_TRY(scan_exclusive_u32(ctx, a.pcell_cursor, a.pcell_start, a.K, S.scan_tmp,
+                               a.pcell_start + a.K));
+    MSF_CUDA_TRY(cudaMemcpyAsync(a.pcell_cursor, a.pcell_start, sizeof(uint32_t) * a.K,
+                                 cudaMemcpyDeviceToDevice, s));
+    k_slic_pgroup<true><<<gp, 256, 0, s>>>(a);
+  }
+  const unsigned gpc = (unsigned)std::min<int64_t>(a.K, (int64_t)ctx->sm_count * 8);
   int it = 1;
   for (it = 1; it <= prm->max_iter; ++it) {
     MSF_CUDA_TRY(cudaMemsetAsync(a.moved, 0, sizeof(unsigned), s));
@@ -630,7 +819,7 @@ int cluster_run(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* flabel, in
     }
     if (nps > 0) {
       ScopedKernel k(ctx, "k_slic_assign_points");
-      k_slic_assign_points<false><<<gp, 256, 0, s>>>(a);
+      k_slic_assign_points_cells<<<gpc, 256, 0, s>>>(a);
     }
   }
   if (it > prm->max_iter) it = prm->max_iter;

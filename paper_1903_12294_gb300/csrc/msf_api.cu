@@ -349,7 +349,8 @@ void msf_destroy(msf_ctx* c) {
   c->last.cfid.release();
   for (DevBuf* b : {&c->clu.centers, &c->clu.prev, &c->clu.sums, &c->clu.counts,
                     &c->clu.cell_start, &c->clu.cell_cursor, &c->clu.cell_items, &c->clu.flags,
-                    &c->clu.scan_tmp, &c->clu.flab, &c->clu.plab})
+                    &c->clu.scan_tmp, &c->clu.flab, &c->clu.plab, &c->clu.pcell_start,
+                    &c->clu.pcell_cursor, &c->clu.psample, &c->clu.pindex})
     b->release();
   c->host_staging.release();
   c->post.release();

@@ -158,6 +158,9 @@ struct BinScratch {
 struct ClusterScratch {
   DevBuf centers, prev, sums, counts, cell_start, cell_cursor, cell_items, flags, scan_tmp, flab,
       plab;
+  // point samples grouped by the seed-grid cell that holds them: per cell the first slot, and
+  // per slot the sample (x, y, z, value) and its index
+  DevBuf pcell_start, pcell_cursor, psample, pindex;
 };
 
 // Scratch of the post-clustering steps (k_post.cu): staged inputs and outputs for host
