@@ -382,6 +382,9 @@ def run_batched(dev, reps=3):
     def batch():
         return msf.msf_segment_batch(ctx.h, crits, labels)
 
+    # the batched form's tile shape picked by the library's batch autotuner (untimed)
+    tuning = msf.msf_autotune_batch(ctx.h, crits, labels, 2)
+    tuning = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuning.items()}
     out = {}
     ctx.kernel_times(reset=True)
     # the last arm is the same batch with graphs on: its warm-up runs plainly, then captures,
@@ -420,6 +423,7 @@ def run_batched(dev, reps=3):
                         f"attrs, {len(crits)} queries, T_w in 2..32, {vt} query-voxel-timesteps",
             "plain": out["plain"], "batched": out["batched"],
             "batched_graph": dict(out["batched_graph"], graph_replays=replays),
+            "batch_tuning": tuning,
             "speedup": round(out["plain"]["ms_per_batch"] / out["batched"]["ms_per_batch"], 2),
             "speedup_graph": round(out["plain"]["ms_per_batch"] /
                                    out["batched_graph"]["ms_per_batch"], 2),

@@ -422,6 +422,27 @@ int msf_get_tuning(msf_ctx* ctx, const msf_criteria* crit, int32_t cfg[4]);
 /* Forget every tuned configuration of this context. */
 int msf_tune_clear(msf_ctx* ctx);
 
+/* Tile shape of the batched form (msf_segment_batch and the query server): 32 x by x bz x bt
+ * with by*bz*bt = 256, each a power of two; (0,0,0) restores the fixed rule (32x8x8x4, or
+ * 32x16x1x16 on a 2D grid). Errors: INVALID_ARG, BUSY (a query server is attached). */
+int msf_set_batch_tile(msf_ctx* ctx, int by, int bz, int bt);
+
+/* Schedule of the batched form: MSF_SCHED_FUSED_CRITERION (the default) evaluates the criterion
+ * inside the tile pass; without it the criterion of every query runs first as a streaming pass
+ * (grids whose nx is a multiple of 32; others keep the fused pass). Other bits are ignored.
+ * Errors: INVALID_ARG, BUSY (a query server is attached). */
+int msf_set_batch_schedule(msf_ctx* ctx, int sched);
+
+/* Time msf_segment_batch on this batch (nq queries, labels as for msf_segment_batch, which
+ * receive valid labels) over the tile shapes msf_autotune tries for the longest window and both
+ * criterion schedules, one warm-up and `reps` timed runs each (reps < 1: 3), and keep the
+ * fastest as the batched form's tile shape and schedule (msf_set_batch_tile,
+ * msf_set_batch_schedule). `out` (may be NULL) receives them, their time and the fixed rule's
+ * (32x8x8x4, fused). Synchronises the stream.
+ * Errors: those of msf_segment_batch; INVALID_ARG when no query has a window; BUSY. */
+int msf_autotune_batch(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
+                       int reps, msf_tune_result* out);
+
 /* Per-kernel timing: when enabled, every kernel the context launches is bracketed by CUDA
  * events on its stream; msf_kernel_times fills up to `cap` (name, total ms, launches) entries
  * accumulated since the last reset and returns the number of kernels seen (>= 0) or an error.

@@ -890,13 +890,13 @@ __global__ void __launch_bounds__(256) k_mask(const __grid_constant__ SegArgs a)
 // 256 apart; eight lanes cover one row. The row mask is put together from four warp ballots
 // (bit k of every lane's four voxels) rather than a lane reduction. FLOAT: no COUNT predicate.
 template <int NP, bool FLOAT>
-__global__ void __launch_bounds__(256) k_mask_lin(const __grid_constant__ SegArgs a) {
+__device__ __forceinline__ void mask_lin_block(const SegArgs& a, uint32_t blk) {
   constexpr int U = NP <= 2 ? 4 : 2;
   const int lane = threadIdx.x & 31, q = lane & 7;
   const uint32_t n4 = (uint32_t)(a.g.nseg * 8);  // 16-byte units of the window (< 2^29)
   const int64_t w0 = (int64_t)a.g.t0 * a.g.V / 4;
   uint32_t* mk = reinterpret_cast<uint32_t*>(a.seg);
-  const uint32_t i0 = blockIdx.x * (256u * U) + threadIdx.x;
+  const uint32_t i0 = blk * (256u * U) + threadIdx.x;
   uint4 raw[U][NP > 0 ? NP : 1];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -923,6 +923,11 @@ __global__ void __launch_bounds__(256) k_mask_lin(const __grid_constant__ SegArg
     const uint32_t m = row_mask4(lane, b0, b1, b2, b3);
     if (q == 0 && i < n4) mk[2 * (i >> 3)] = m;
   }
+}
+
+template <int NP, bool FLOAT>
+__global__ void __launch_bounds__(256) k_mask_lin(const __grid_constant__ SegArgs a) {
+  mask_lin_block<NP, FLOAT>(a, blockIdx.x);
 }
 
 template <bool VEC>
@@ -1498,6 +1503,19 @@ __global__ void __launch_bounds__(256, 5) k_tile_batch(const __grid_constant__ B
   }
 }
 
+// The criterion of every query of a group as a streaming pass (rows of 32 voxels contiguous:
+// nx a multiple of 32): query blockIdx.y, its window's 16-byte units in blocks strided by x.
+template <int NP, bool FLOAT>
+__global__ void __launch_bounds__(256) k_mask_batch(const __grid_constant__ BatchPlan b) {
+  constexpr int U = NP <= 2 ? 4 : 2;
+  __shared__ __align__(16) SegArgs s_args;
+  load_args(&s_args, b.qargs + blockIdx.y);
+  __syncthreads();
+  const uint32_t n4 = (uint32_t)(s_args.g.nseg * 8);
+  for (uint32_t blk = blockIdx.x; blk * (256u * U) < n4; blk += gridDim.x)
+    mask_lin_block<NP, FLOAT>(s_args, blk);
+}
+
 // (tile, query) = (blockIdx.x, blockIdx.y): the tile's cross-face joins with its pair set
 template <bool SPATIAL>
 __global__ void __launch_bounds__(256, 4) k_hook_batch(const __grid_constant__ BatchPlan b) {
@@ -1555,6 +1573,17 @@ static void launch_tile_batch(const BatchPlan& b, int grid, cudaStream_t s) {
   k_tile_batch<NP, SP, VEC><<<grid, 256, tile_dyn_smem<SP>(), s>>>(b);
 }
 
+template <bool FLOAT>
+static void launch_mask_batch_np(const BatchPlan& b, int np, dim3 grid, cudaStream_t s) {
+  switch (np) {
+    case 0: k_mask_batch<0, FLOAT><<<grid, 256, 0, s>>>(b); break;
+    case 1: k_mask_batch<1, FLOAT><<<grid, 256, 0, s>>>(b); break;
+    case 2: k_mask_batch<2, FLOAT><<<grid, 256, 0, s>>>(b); break;
+    case 3: k_mask_batch<3, FLOAT><<<grid, 256, 0, s>>>(b); break;
+    default: k_mask_batch<4, FLOAT><<<grid, 256, 0, s>>>(b); break;
+  }
+}
+
 template <bool SP, bool VEC>
 static void launch_tile_batch_np(const BatchPlan& b, int np, int grid, cudaStream_t s) {
   switch (np) {
@@ -1603,7 +1632,14 @@ struct BatchJob {
 };
 
 // Tile shape of every batched query: time chunks of 4 (16 for 2D+time) absolute steps.
-static void batch_tile(const Dataset& d, int* by, int* bz, int* bt) {
+static void batch_tile(const msf_ctx* ctx, int* by, int* bz, int* bt) {
+  if (ctx->batch_by) {  // set by msf_set_batch_tile or msf_autotune_batch
+    *by = ctx->batch_by;
+    *bz = ctx->batch_bz;
+    *bt = ctx->batch_bt;
+    return;
+  }
+  const Dataset& d = ctx->ds;
   *bt = d.nz == 1 ? 16 : 4;
   *by = d.nz == 1 ? 16 : 8;
   *bz = d.nz == 1 ? 1 : 8;
@@ -1613,7 +1649,7 @@ static void batch_tile(const Dataset& d, int* by, int* bz, int* bt) {
 static int batch_geometry(msf_ctx* ctx, const msf_criteria* c, Geometry* out) {
   const Dataset& d = ctx->ds;
   int by, bz, bt;
-  batch_tile(d, &by, &bz, &bt);
+  batch_tile(ctx, &by, &bz, &bt);
   const bool spatial = (c->edges & MSF_EDGE_SPATIAL) != 0;
   const int maxr = kSegPerTile * (spatial ? 16 : 32);
   Geometry g;
@@ -1730,7 +1766,7 @@ int batch_job_plan(msf_ctx* ctx, int nq, const msf_criteria* crits, BatchJob** o
   BatchJob* job = new BatchJob();
   job->nq = nq;
   job->scratch.assign(nq, 0);
-  batch_tile(d, &job->by, &job->bz, &job->bt);
+  batch_tile(ctx, &job->by, &job->bz, &job->bt);
   // groups by (predicate count, spatial edges); empty windows need no work
   for (int np = 0; np <= MSF_MAX_PRED; ++np)
     for (int sp = 0; sp < 2; ++sp) {
@@ -1769,10 +1805,31 @@ static int launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b, 
   const bool vec = (d.nx & 3) == 0;
   k_batch_prep<<<nq, 32, 0, s>>>(b.qargs);
   const int per_sm = 5;  // resident CTAs of the tile kernel per SM
+  // the criterion as a streaming pass over every query's window first (rows contiguous), or
+  // inside the tile pass
+  const bool streamed = !(ctx->batch_sched & MSF_SCHED_FUSED_CRITERION) && (d.nx & 31) == 0;
+  if (streamed) {
+    ScopedKernel k(ctx, "k_mask_batch", timed);
+    int64_t max4 = 1;
+    bool fl = true;
+    for (int i = 0; i < nq; ++i) {
+      max4 = std::max<int64_t>(max4, gr.args[i].g.nseg * 8);
+      for (int j = 0; j < np; ++j) fl &= !gr.args[i].pred[j].is_int;
+    }
+    const int U = np <= 2 ? 4 : 2;
+    const int64_t need = (max4 + 256 * U - 1) / (256 * U);
+    const unsigned gx = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(need, (int64_t)ctx->sm_count * 16 / nq + 1));
+    if (fl) launch_mask_batch_np<true>(b, np, dim3(gx, nq), s);
+    else launch_mask_batch_np<false>(b, np, dim3(gx, nq), s);
+  }
   {
     ScopedKernel k(ctx, "k_tile_batch", timed);
     const int grid = (int)std::min<int64_t>(gr.chunk_begin[gr.nchunk], (int64_t)ctx->sm_count * per_sm);
-    if (spatial) {
+    if (streamed) {
+      if (spatial) launch_tile_batch<-1, true, false>(b, std::max(grid, 1), s);
+      else launch_tile_batch<-1, false, false>(b, std::max(grid, 1), s);
+    } else if (spatial) {
       if (vec) launch_tile_batch_np<true, true>(b, np, std::max(grid, 1), s);
       else launch_tile_batch_np<true, false>(b, np, std::max(grid, 1), s);
     } else {
@@ -1919,7 +1976,10 @@ static std::vector<int64_t> batch_signature(const msf_ctx* ctx, int nq, const ms
                                             int32_t* const* labels, const char* base,
                                             const char* host, size_t plan_bytes) {
   std::vector<int64_t> sig = {(int64_t)ctx->epoch, (int64_t)(uintptr_t)base,
-                              (int64_t)(uintptr_t)host, (int64_t)plan_bytes, nq};
+                              (int64_t)(uintptr_t)host, (int64_t)plan_bytes, nq,
+                              ((int64_t)ctx->batch_by << 32) | (ctx->batch_bz << 16) |
+                                  ctx->batch_bt,
+                              ctx->batch_sched};
   for (int i = 0; i < nq; ++i) {
     const msf_criteria& c = crits[i];
     sig.push_back(((int64_t)c.t0 << 32) | (uint32_t)c.t1);

@@ -221,6 +221,8 @@ struct msf_ctx {
   uint64_t epoch = 1;        // bumped whenever the dataset or its binning changes
   int tile_by = 0, tile_bz = 0, tile_bt = 0;
   int sched = -1;                    // msf_segment schedule set by msf_set_schedule (-1: auto)
+  int batch_by = 0, batch_bz = 0, batch_bt = 0;  // tile of the batched form (0: fixed rule)
+  int batch_sched = 1;  // MSF_SCHED_* of the batched form: criterion fused into the tile pass
   std::vector<msf::TuneEntry> tune;  // msf_autotune results, one per problem shape
   msf::KernelTimer timer;
   std::atomic<int> servers{0};  // query servers attached (the dataset is frozen meanwhile)

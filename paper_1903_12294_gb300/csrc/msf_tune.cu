@@ -15,6 +15,8 @@ namespace msf {
 
 int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t* nfeat,
                 const void* labels_user);
+int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
+                      int64_t* n_features);
 
 namespace {
 
@@ -195,6 +197,136 @@ int msf_autotune(msf_ctx* c, const msf_criteria* crit, int reps, msf_tune_result
     out->bt = best.bt;
     out->sched = best.sched;
     out->ms = best.ms;
+    out->ms_default = ms_default;
+    out->n_tried = tried;
+  }
+  return MSF_OK;
+}
+
+int msf_set_batch_tile(msf_ctx* c, int by, int bz, int bt) {
+  if (!c) return MSF_ERR_INVALID_ARG;
+  if (c->servers.load() > 0) return MSF_ERR_BUSY;
+  if (by == 0 && bz == 0 && bt == 0) {
+    c->batch_by = c->batch_bz = c->batch_bt = 0;
+    return MSF_OK;
+  }
+  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+  if (!pow2(by) || !pow2(bz) || !pow2(bt) || by * bz * bt != kSegPerTile)
+    return MSF_ERR_INVALID_ARG;
+  c->batch_by = by;
+  c->batch_bz = bz;
+  c->batch_bt = bt;
+  return MSF_OK;
+}
+
+int msf_set_batch_schedule(msf_ctx* c, int sched) {
+  if (!c || sched < 0 || sched > (MSF_SCHED_FUSED_CRITERION | MSF_SCHED_SERIAL_JOINS))
+    return MSF_ERR_INVALID_ARG;
+  if (c->servers.load() > 0) return MSF_ERR_BUSY;
+  c->batch_sched = sched & MSF_SCHED_FUSED_CRITERION;
+  return MSF_OK;
+}
+
+int msf_autotune_batch(msf_ctx* c, int nq, const msf_criteria* crits, int32_t* const* labels,
+                       int reps, msf_tune_result* out) {
+  if (!c || nq < 1 || !crits || !labels) return MSF_ERR_INVALID_ARG;
+  if (c->servers.load() > 0) return MSF_ERR_BUSY;
+  int twmax = 0;
+  for (int i = 0; i < nq; ++i) {
+    Geometry g;
+    MSF_TRY(make_geometry(c, &crits[i], &g));
+    if (g.tw > 0 && !labels[i]) return MSF_ERR_INVALID_ARG;
+    twmax = std::max(twmax, g.tw);
+  }
+  if (twmax == 0) return MSF_ERR_INVALID_ARG;
+  if (reps < 1) reps = 3;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  MSF_TRY(ctx_field_ready(c));
+  const int keep_by = c->batch_by, keep_bz = c->batch_bz, keep_bt = c->batch_bt;
+  const int keep_sched = c->batch_sched;
+  const bool keep_graphs = c->batch.graphs;
+  c->batch.graphs = false;  // every run below launches plainly
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto restore = [&](bool keep_tile) {
+    if (keep_tile) {
+      c->batch_by = keep_by;
+      c->batch_bz = keep_bz;
+      c->batch_bt = keep_bt;
+      c->batch_sched = keep_sched;
+    }
+    c->batch.graphs = keep_graphs;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    restore(true);
+    return MSF_ERR_CUDA;
+  }
+  auto time_tile = [&](int by, int bz, int bt, int sched, float* ms) -> int {
+    c->batch_by = by;
+    c->batch_bz = bz;
+    c->batch_bt = bt;
+    c->batch_sched = sched;
+    MSF_TRY(segment_batch_run(c, nq, crits, labels, nullptr));
+    std::vector<float> t(reps);
+    for (int r = 0; r < reps; ++r) {
+      MSF_CUDA_TRY(cudaEventRecord(e0, c->stream));
+      MSF_TRY(segment_batch_run(c, nq, crits, labels, nullptr));
+      MSF_CUDA_TRY(cudaEventRecord(e1, c->stream));
+      MSF_CUDA_TRY(cudaEventSynchronize(e1));
+      MSF_CUDA_TRY(cudaEventElapsedTime(&t[r], e0, e1));
+    }
+    std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
+    *ms = t[reps / 2];
+    return MSF_OK;
+  };
+  // the fixed rule first
+  const Dataset& d = c->ds;
+  const int rby = d.nz == 1 ? 16 : 8, rbz = d.nz == 1 ? 1 : 8, rbt = d.nz == 1 ? 16 : 4;
+  float ms_default = 0.f;
+  int st = time_tile(0, 0, 0, MSF_SCHED_FUSED_CRITERION, &ms_default);
+  int bby = rby, bbz = rbz, bbt = rbt, bsched = MSF_SCHED_FUSED_CRITERION, tried = 1;
+  float best = ms_default;
+  const std::vector<int> tiles = tile_candidates(d, twmax);
+  const int nsched = (d.nx & 31) == 0 ? 2 : 1;  // the streamed criterion needs whole rows
+  for (size_t i = 0; st == MSF_OK && i < tiles.size(); ++i) {
+    const int by = tiles[i] >> 16, bz = (tiles[i] >> 8) & 0xFF, bt = tiles[i] & 0xFF;
+    for (int k = 0; st == MSF_OK && k < nsched; ++k) {
+      const int sched = k == 0 ? MSF_SCHED_FUSED_CRITERION : 0;
+      if (by == rby && bz == rbz && bt == rbt && sched == MSF_SCHED_FUSED_CRITERION) continue;
+      float ms = 0.f;
+      st = time_tile(by, bz, bt, sched, &ms);
+      if (st == MSF_ERR_TOO_LARGE || st == MSF_ERR_OUT_OF_MEMORY) {  // not a candidate here
+        st = MSF_OK;
+        continue;
+      }
+      ++tried;
+      if (st == MSF_OK && ms < best) {
+        best = ms;
+        bby = by;
+        bbz = bz;
+        bbt = bt;
+        bsched = sched;
+      }
+    }
+  }
+  if (st != MSF_OK) {
+    restore(true);
+    return st;
+  }
+  restore(false);
+  c->batch_by = bby;
+  c->batch_bz = bbz;
+  c->batch_bt = bbt;
+  c->batch_sched = bsched;
+  c->timer.flush();
+  if (out) {
+    out->by = bby;
+    out->bz = bbz;
+    out->bt = bbt;
+    out->sched = bsched;
+    out->ms = best;
     out->ms_default = ms_default;
     out->n_tried = tried;
   }

@@ -36,7 +36,8 @@ EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_server_destroy", "msf_set_wait_limit", "msf_cluster", "msf_merge_clusters",
            "msf_relabel", "msf_cluster_stats", "msf_select_clusters", "msf_split_trajectories",
            "msf_set_schedule", "msf_autotune", "msf_get_tuning", "msf_tune_clear",
-           "msf_set_batch_graphs", "msf_batch_graph_replays")
+           "msf_set_batch_graphs", "msf_batch_graph_replays", "msf_set_batch_tile",
+           "msf_autotune_batch", "msf_set_batch_schedule")
 MSF_SCHED_FUSED_CRITERION, MSF_SCHED_SERIAL_JOINS = 1, 2
 MSF_MERGE_POINT, MSF_MERGE_FIELD = 1, 2
 MSF_SPACE_POINTS, MSF_SPACE_VOXELS = 0, 1
@@ -178,6 +179,9 @@ def load_library(path: str = LIB_PATH):
                                                ctypes.POINTER(ctypes.c_int64)]
         lib.msf_set_schedule.argtypes = [P, i32]
         lib.msf_set_batch_graphs.argtypes = [P, i32]
+        lib.msf_set_batch_tile.argtypes = [P, i32, i32, i32]
+        lib.msf_set_batch_schedule.argtypes = [P, i32]
+        lib.msf_autotune_batch.argtypes = [P, i32, P, P, i32, ctypes.POINTER(msf_tune_result)]
         lib.msf_batch_graph_replays.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         lib.msf_autotune.argtypes = [P, ctypes.POINTER(msf_criteria), i32,
                                      ctypes.POINTER(msf_tune_result)]
@@ -454,6 +458,17 @@ def msf_autotune(ctx, crit: msf_criteria, reps: int = 3) -> dict:
     return {f: getattr(r, f) for f, _ in msf_tune_result._fields_}
 
 
+def msf_autotune_batch(ctx, crits, labels, reps: int = 3) -> dict:
+    """Tune the batched form's tile shape on this batch (labels as for msf_segment_batch)."""
+    n = len(crits)
+    arr = (msf_criteria * n)(*crits)
+    ptrs = (ctypes.c_void_p * n)(*[_ptr_kind(l)[0] if l is not None else None for l in labels])
+    r = msf_tune_result()
+    _check(load_library().msf_autotune_batch(ctx, n, arr, ptrs, int(reps), ctypes.byref(r)),
+           "msf_autotune_batch")
+    return {f: getattr(r, f) for f, _ in msf_tune_result._fields_}
+
+
 def msf_get_tuning(ctx, crit: msf_criteria):
     """(by, bz, bt, sched) msf_segment would use for crit now."""
     cfg = (ctypes.c_int32 * 4)()
@@ -642,6 +657,23 @@ class Context:
         prm = make_cluster_params(t0, t1, attr, k, w_p, w_f, w_d, c_f, eps_c, max_iter)
         centers, counts, it = msf_cluster(self.h, prm, fl, pl.contiguous() if self.P else None)
         return fl, pl, centers, counts, it
+
+    def set_batch_tile(self, by, bz, bt):
+        _check(load_library().msf_set_batch_tile(self.h, int(by), int(bz), int(bt)),
+               "msf_set_batch_tile")
+
+    def set_batch_schedule(self, sched):
+        _check(load_library().msf_set_batch_schedule(self.h, int(sched)),
+               "msf_set_batch_schedule")
+
+    def autotune_batch(self, queries, labels=None, reps=3):
+        import torch
+        T, nz, ny, nx = self.shape
+        crits = [make_criteria(t0, t1, p, e) for (t0, t1, p, e) in queries]
+        if labels is None:
+            labels = [torch.empty((t1 - t0, nz, ny, nx), dtype=torch.int32,
+                                  device=f"cuda:{self.device}") for (t0, t1, _, _) in queries]
+        return msf_autotune_batch(self.h, crits, labels, reps)
 
     def set_batch_graphs(self, enable=True):
         _check(load_library().msf_set_batch_graphs(self.h, int(bool(enable))),

@@ -99,3 +99,42 @@ def test_batch_graph_replay(gpu, orc):
             assert nf == ns and np.array_equal(lb, ls)
             want, n_o = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
             assert nf == n_o and np.array_equal(lb, want)
+
+
+def test_batch_tile_shapes_and_autotune(gpu, orc):
+    """Every batch tile shape and criterion schedule (fused, or streamed first on whole 32-voxel
+    rows) gives the single queries' labels; the batch autotuner keeps a valid choice, and the
+    batch then still gives them."""
+    wl = synth.mid(n=64, T=12, P=20000, n_blobs=8)
+    f, p, a = wl.numpy()
+    q = wl.preds
+    queries = [(0, 12, q, 7), (3, 11, [(F, 0, GT, 0.45, 0)], 7), (5, 6, q, 3), (1, 9, q, 6)]
+    o = orc.bin(f.shape, p, a)
+    want = [orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
+            for (t0, t1, pr, e) in queries]
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(*(torch.as_tensor(x).cuda().contiguous() for x in (f, p, a)))
+        ctx.bin()
+        got = []
+        for sched in (1, 0):
+            ctx.set_batch_schedule(sched)
+            for tile in [(4, 4, 16), (2, 16, 8), (16, 8, 2), (8, 8, 4)]:
+                ctx.set_batch_tile(*tile)
+                labels, nfs = ctx.segment_batch(queries)
+                got.append(((sched, tile), [l.cpu().numpy() for l in labels], nfs))
+        ctx.set_batch_tile(0, 0, 0)
+        ctx.set_batch_schedule(1)
+        r = ctx.autotune_batch(queries, reps=1)
+        assert r["by"] * r["bz"] * r["bt"] == 256 and r["n_tried"] > 3 and r["sched"] in (0, 1)
+        assert 0 < r["ms"] <= r["ms_default"]
+        labels, nfs = ctx.segment_batch(queries)
+        got.append(("tuned", [l.cpu().numpy() for l in labels], nfs))
+        with pytest.raises(gpu.MsfError) as e:
+            ctx.set_batch_tile(4, 4, 4)
+        assert e.value.status == gpu.MSF_ERR_INVALID_ARG
+    finally:
+        ctx.close()
+    for tile, labs, nfs in got:
+        for (lab_o, n_o), lb, nf in zip(want, labs, nfs):
+            assert nf == n_o and np.array_equal(lb, lab_o), tile
