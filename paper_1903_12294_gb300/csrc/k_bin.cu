@@ -38,7 +38,6 @@ int scan_exclusive_u32(msf_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t 
 
 constexpr int kBinPer = 4;             // samples per thread in the per-sample passes
 constexpr int kBinNT = 512;            // threads per CTA of the sort and reduce passes
-constexpr int kBinBlock = 256 * kBinPer;
 constexpr int kHistSmem = 8192;        // buckets counted in shared memory (else global atomics)
 
 struct BinArgs {
@@ -238,7 +237,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
     s_delta[i] = b.offs[((int64_t)t * b.nb + i) * b.nblk + blk];
     s_lpos[i] = b.hist[((int64_t)t * b.nb + i) * b.nblk + blk];  // counts, scanned below
   }
-  if (threadIdx.x < A) s_max[threadIdx.x] = 0u;
+  if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
   // exclusive scan of the block's bucket counts (one thread per chunk of buckets); s_delta
   // becomes global slot minus local position
@@ -309,7 +308,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
       b.rec_a[(int64_t)a * b.NRp + slot] = s_att[a * kPlaceStage + ha + i];
     }
   }
-  if (threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
+  if ((int)threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
 }
 
 // Fallback for many buckets (global histogram): one slot atomic per sample.
@@ -317,7 +316,7 @@ template <int A>
 __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant__ BinArgs b) {
   __shared__ unsigned s_max[A > 0 ? A : 1];
   const int t = blockIdx.y, blk = blockIdx.x;
-  if (threadIdx.x < A) s_max[threadIdx.x] = 0u;
+  if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
   const int64_t pbeg = (int64_t)blk * b.chunk;
   const int64_t pend = min(pbeg + b.chunk, b.P);
@@ -345,7 +344,7 @@ __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant_
     if ((threadIdx.x & 31) == 0 && m) atomicMax(s_max + a, m);
   }
   __syncthreads();
-  if (threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
+  if ((int)threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -405,7 +404,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
     mbar_init(&s_bar, 1);
     if (npiece) reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, R, &s_bar);
   }
-  if (threadIdx.x < A) {
+  if ((int)threadIdx.x < A) {
     const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.P * b.T);
     s_k[threadIdx.x] = k;
     s_f1[threadIdx.x] = pow2f(-(k / 2));

@@ -1762,7 +1762,6 @@ static int plan_group(msf_ctx* ctx, const msf_criteria* crits, BatchJob* job, Ba
 
 int batch_job_plan(msf_ctx* ctx, int nq, const msf_criteria* crits, BatchJob** out) {
   *out = nullptr;
-  const Dataset& d = ctx->ds;
   BatchJob* job = new BatchJob();
   job->nq = nq;
   job->scratch.assign(nq, 0);
