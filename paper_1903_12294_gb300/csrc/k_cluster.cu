@@ -7,9 +7,11 @@
 //   k_slic_valid    samples that take part, and the largest |value| of each kind (fixed-point
 //                   scales for the centre sums)
 //   k_slic_seed     centres at the grid cells' centres
-//   k_slic_assign_* one thread per field sample (voxel-timestep) / point sample: the best centre
-//                   among the candidates, and the sample's fixed-point contribution to that
-//                   centre's sums (warp-reduced)
+//   k_slic_assign_* the best centre of every sample among its candidates, and the sample's
+//                   fixed-point contribution to that centre's sums (warp-reduced): the first
+//                   pass one thread per sample; later field passes a tile of voxels of one cell
+//                   per block, later point passes one cell's grouped samples per block
+//                   (k_slic_pgroup groups them once), both against a shared candidate list
 //   k_slic_update   one thread per centre: means of its sums, counts, change test
 //   k_slic_cells*   centres sorted into the cells of the seed grid for the next assignment
 //
