@@ -52,6 +52,8 @@ struct SegArgs {
   int2* tileinfo;  // (runs, components) per tile
   int32_t* labels;
   unsigned long long* counters;  // [0] features, [1] error flags
+  uint32_t* pcomp;  // [tw][P] component of every point sample, kNoComp off the members; written
+                    // by the trajectory joins, read by the point statistics (null: not kept)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -657,6 +659,12 @@ __device__ __forceinline__ void links_chunk(const SegArgs& a, int64_t p, int s0)
       if (comp[j] != kNoComp && comp[j + 1] != kNoComp && comp[j] != comp[j + 1] && !same_voxel)
         gunion(a.cparent, comp[j], comp[j + 1]);
     }
+    if (a.pcomp) {  // each step once: the last chunk also keeps the window's last step
+      const int nw = s0 + L >= tw - 1 ? nk : L;
+#pragma unroll
+      for (int j = 0; j <= L; ++j)
+        if (j < nw) __stcs(a.pcomp + (int64_t)(s0 + j) * a.P + p, comp[j]);
+    }
   }
 }
 
@@ -1057,6 +1065,17 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   // runs the trajectory pass after the cross-tile joins on the context stream
   const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1;
   const bool serial = sched & MSF_SCHED_SERIAL_JOINS;
+  // When the last segmentation's features were extracted, the joins also keep every point
+  // sample's component for the next extraction's point statistics (which then need no lookups);
+  // a caller that only segments does not pay for the store.
+  SegState& LS = ctx->last;
+  LS.has_pcomp = false;
+  const bool keep = traj && ctx->keep_pcomp;
+  ctx->keep_pcomp = false;
+  if (keep) {
+    MSF_TRY(LS.pcomp.ensure(sizeof(uint32_t) * (size_t)a.P * (size_t)g.tw));
+    a.pcomp = LS.pcomp.as<uint32_t>();
+  }
   auto links = [&](cudaStream_t ls) {
     ScopedKernel k(ctx, "k_links", ls);
     const int64_t nchunk = (g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
@@ -1099,6 +1118,7 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   if (h[1]) return MSF_ERR_INTERNAL;
   if (nfeat) *nfeat = (int64_t)h[0];
   SegState& L = ctx->last;
+  L.has_pcomp = keep;
   L.valid = labels_user != nullptr;
   L.crit = *crit;
   L.labels_user = labels_user;
@@ -1226,20 +1246,32 @@ __global__ void __launch_bounds__(256, 4) k_feat_points(const __grid_constant__ 
   const int nchunk = (tw + L - 1) / L;
   for (int c = blockIdx.y; c < nchunk; c += gridDim.y) {
     const int s0 = c * L;
-    int32_t key[L];
-#pragma unroll
-    for (int j = 0; j < L; ++j)
-      key[j] = (in && s0 + j < tw) ? __ldcs(a.key + (int64_t)(a.g.t0 + s0 + j) * a.P + p) : -1;
     int32_t fid[L];
     int n = 0;
+    if (a.pcomp) {  // components kept by the trajectory joins: no lookups
+      uint32_t cp[L];
 #pragma unroll
-    for (int j = 0; j < L; ++j) {
-      fid[j] = -1;
-      if (key[j] >= 0) {
-        const int64_t cj = comp_of<SPATIAL>(a, s0 + j, key[j]);
-        if (cj >= 0) fid[j] = __ldg(cfid + cj);
+      for (int j = 0; j < L; ++j)
+        cp[j] = (in && s0 + j < tw) ? __ldcs(a.pcomp + (int64_t)(s0 + j) * a.P + p) : kNoComp;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        fid[j] = cp[j] != kNoComp ? __ldg(cfid + cp[j]) : -1;
+        n += fid[j] >= 0;
       }
-      n += fid[j] >= 0;
+    } else {
+      int32_t key[L];
+#pragma unroll
+      for (int j = 0; j < L; ++j)
+        key[j] = (in && s0 + j < tw) ? __ldcs(a.key + (int64_t)(a.g.t0 + s0 + j) * a.P + p) : -1;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        fid[j] = -1;
+        if (key[j] >= 0) {
+          const int64_t cj = comp_of<SPATIAL>(a, s0 + j, key[j]);
+          if (cj >= 0) fid[j] = __ldg(cfid + cj);
+        }
+        n += fid[j] >= 0;
+      }
     }
     // warp exclusive scan of the member counts -> packed positions
     int x = n;
@@ -1284,6 +1316,8 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
   const bool spatial = L.crit.edges & MSF_EDGE_SPATIAL;
   SegArgs a;
   MSF_TRY(seg_args(ctx, g, spatial, &a));
+  if (L.has_pcomp) a.pcomp = L.pcomp.as<uint32_t>();
+  ctx->keep_pcomp = true;  // features follow segmentations here: keep components next time
   MSF_TRY(L.cfid.ensure(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
   int32_t* cfid = L.cfid.as<int32_t>();
   cudaStream_t s = ctx->stream;

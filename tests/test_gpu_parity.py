@@ -31,16 +31,21 @@ def gpu_run(msf, field, pos, attr, t0, t1, preds, edges=7, tile=None, features=T
         if tile:
             ctx.set_tile(*tile)
         labels, n = ctx.segment(t0, t1, preds, edges)
-        feats = feats_generic = None
+        feats = feats_generic = feats_kept = None
         if features:
             # the labels msf_segment just wrote: statistics from the retained segmentation
             feats = ctx.features(t0, t1, labels, preds, edges)
             # the same labels in another buffer: statistics from the labels themselves
             feats_generic = ctx.features(t0, t1, labels.clone(), preds, edges)
+            # segmenting again after an extraction keeps the point samples' components in the
+            # trajectory joins, and the next extraction's point statistics read them
+            labels2, n2 = ctx.segment(t0, t1, preds, edges)
+            assert n2 == n and torch.equal(labels2, labels)
+            feats_kept = ctx.features(t0, t1, labels2, preds, edges)
         torch.cuda.synchronize()
         return dict(stats=st, key=key.numpy(), count=count.numpy(), mean=mean.numpy(),
                     sumq=sumq.numpy(), labels=labels.cpu().numpy(), n=n, feats=feats,
-                    feats_generic=feats_generic)
+                    feats_generic=feats_generic, feats_kept=feats_kept)
     finally:
         ctx.close()
 
@@ -95,6 +100,7 @@ def full_check(gpu, orc, field, pos, attr, t0, t1, preds, edges=7, tile=None):
     of = orc.features(field, o["count"], attr, o["key"], o["kscale"], t0, t1, lab)
     check_features(g["feats"], of, attr.shape[1])
     check_features(g["feats_generic"], of, attr.shape[1])
+    check_features(g["feats_kept"], of, attr.shape[1])
     return g, o, lab
 
 
