@@ -22,6 +22,9 @@
  *   msf_cluster_stats     §3.4 per-cluster extent, means and standard deviations
  *   msf_select_clusters   §3.4 range query over the centres' properties
  *   msf_split_trajectories  §3.4 trajectory pieces: runs of consecutive timesteps in one feature
+ *   msf_autotune, msf_autotune_batch  tile shapes and schedules of the labelling, timed on the
+ *                         caller's query or batch (no counterpart in the paper)
+ *   msf_set_batch_graphs  replay repeated batch shapes from a captured CUDA graph
  *   msf_server_*          a query server over the resident dataset: continuous batching of
  *                         queries submitted from any thread, admitted by device memory
  *
