@@ -561,8 +561,8 @@ typedef struct {
  * *n_pieces: nothing is written and the call returns MSF_ERR_CAPACITY (cap = 0 with pieces =
  * NULL is a size query). Synchronises the stream.
  * Errors: NOT_LOADED, NOT_BINNED (voxel space), INVALID_ARG (window, min_len < 1, space, kinds,
- * NULL labels), TOO_LARGE ((t1-t0) P or the window's voxel-timesteps >= 2^31), CAPACITY,
- * OUT_OF_MEMORY, CUDA. */
+ * NULL labels where there are samples), TOO_LARGE ((t1-t0) P or the window's voxel-timesteps
+ * >= 2^31), CAPACITY, OUT_OF_MEMORY, CUDA. A dataset without points has no pieces. */
 int msf_split_trajectories(msf_ctx* ctx, int32_t t0, int32_t t1, const int32_t* labels,
                            int labels_kind, int labels_space, int32_t min_len, msf_piece* pieces,
                            int pieces_kind, int64_t cap, int64_t* n_pieces);

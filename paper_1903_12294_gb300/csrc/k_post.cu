@@ -749,7 +749,7 @@ int msf_cluster_stats(msf_ctx* c, int32_t t0, int32_t t1, int32_t attr,
 int msf_split_trajectories(msf_ctx* c, int32_t t0, int32_t t1, const int32_t* labels,
                            int labels_kind, int labels_space, int32_t min_len, msf_piece* pieces,
                            int pieces_kind, int64_t cap, int64_t* n_pieces) {
-  if (!c || !labels || !n_pieces || min_len < 1 || cap < 0 || (cap > 0 && !pieces))
+  if (!c || !n_pieces || min_len < 1 || cap < 0 || (cap > 0 && !pieces))
     return MSF_ERR_INVALID_ARG;
   if ((labels_kind != MSF_HOST && labels_kind != MSF_DEVICE) ||
       (pieces_kind != MSF_HOST && pieces_kind != MSF_DEVICE))
@@ -764,6 +764,7 @@ int msf_split_trajectories(msf_ctx* c, int32_t t0, int32_t t1, const int32_t* la
   const int64_t tw = t1 - t0;
   if (tw * d.P >= ((int64_t)1 << 31) || (vox && tw * d.V >= ((int64_t)1 << 31)))
     return MSF_ERR_TOO_LARGE;
+  if (!labels && (vox || d.P > 0)) return MSF_ERR_INVALID_ARG;
   *n_pieces = 0;
   if (d.P == 0) return MSF_OK;
   MSF_CUDA_TRY(cudaSetDevice(c->device));

@@ -250,3 +250,34 @@ def test_pieces_edge_cases(gpu, orc):
             assert e.value.status == gpu.MSF_ERR_INVALID_ARG
     finally:
         ctx.close()
+
+
+def test_merge_at_the_largest_k(gpu):
+    """K = 2^18 (the limit): distinct values at eps_m = 0 give every centre its own group (the
+    identity map); eps_m above 2 gives one group. Closed forms, no oracle needed at this size."""
+    K = 1 << 18
+    c = np.zeros((K, 6), np.float32)
+    c[:, 4] = np.arange(K, dtype=np.float32) + 1.0
+    c[:, 5] = -(np.arange(K, dtype=np.float32) + 1.0)
+    ctx = gpu.Context(0)
+    try:
+        m, g = ctx.merge_clusters(torch.as_tensor(c).cuda(), 0.0,
+                                  out=torch.empty(K, dtype=torch.int32, device="cuda"))
+        assert g == K and np.array_equal(m.cpu().numpy(), np.arange(K, dtype=np.int32))
+        m, g = ctx.merge_clusters(c, 3.0)
+        assert g == 1 and (m == 0).all()
+    finally:
+        ctx.close()
+
+
+def test_pieces_without_points(gpu):
+    """A dataset without points has no trajectory pieces."""
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=(4, 3, 5, 8)).astype(np.float32)
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(torch.as_tensor(f).cuda(), None, None)
+        got = ctx.split_trajectories(0, 4, np.zeros((4, 0), np.int32), gpu.MSF_SPACE_POINTS)
+        assert got.shape == (0, 4)
+    finally:
+        ctx.close()
