@@ -397,9 +397,13 @@ int msf_set_tile(msf_ctx* ctx, int by, int bz, int bt);
 #define MSF_SCHED_FUSED_CRITERION 1 /* criterion inside the tile pass (else a streaming pass) */
 #define MSF_SCHED_SERIAL_JOINS 2    /* trajectory joins after the cross-tile joins on the
                                        context stream (else side by side on two streams)     */
+#define MSF_SCHED_PIPELINE 4        /* the tile pass in two launches split at a time-tile row;
+                                       the link chunks whose steps precede the split run
+                                       beside the second launch (ignored with SERIAL_JOINS,
+                                       without trajectory joins or below two tile rows)     */
 
-/* Fix the schedule of msf_segment (MSF_SCHED_* bits), or -1 for the automatic one (a tuned
- * schedule when msf_autotune has tuned the problem's shape, else 0). Errors: INVALID_ARG. */
+/* Fix the schedule of msf_segment (MSF_SCHED_* bits, 0..7), or -1 for the automatic one (a
+ * tuned schedule when msf_autotune has tuned the problem's shape, else 0). Errors: INVALID_ARG. */
 int msf_set_schedule(msf_ctx* ctx, int sched);
 
 /* Result of msf_autotune. */
@@ -413,7 +417,8 @@ typedef struct {
 
 /* Time msf_segment on `crit` over tile shapes (by, bz, bt: powers of two with product 256,
  * each at most the next power of two of ny, nz and the window length; by, bz >= 2 unless the
- * grid is 2D) and the four schedules, `reps` timed runs each after one warm-up (reps < 1: 3),
+ * grid is 2D) and the schedules (criterion streamed or fused, joins side by side, serial or
+ * pipelined), `reps` timed runs each after one warm-up (reps < 1: 3),
  * and keep the fastest for the problem's shape: grid, window length, edge classes and number
  * of predicates. Later msf_segment calls with that shape use it unless msf_set_tile or
  * msf_set_schedule fixed a choice. The paper has no counterpart (it has one GPU kernel per

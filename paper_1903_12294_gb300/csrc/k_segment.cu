@@ -54,6 +54,8 @@ struct SegArgs {
   unsigned long long* counters;  // [0] features, [1] error flags
   uint32_t* pcomp;  // [tw][P] component of every point sample, kNoComp off the members; written
                     // by the trajectory joins, read by the point statistics (null: not kept)
+  int tile0;            // first tile of a tile-pass launch that covers part of the tiles
+  int chunk0, chunk1;   // link chunks [chunk0, chunk1) of a join launch (chunk1 0: to the end)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(256, 6) k_tile(const __grid_constant__ SegArgs
   __shared__ int s_warp[8];
   extern __shared__ uint32_t s_dyn[];
   const TileSmem sm{s_mask, s_rb, s_warp, s_dyn, reinterpret_cast<uint16_t*>(s_dyn + MAXR), MAXR};
-  tile_body<NP, SPATIAL, VEC>(a, blockIdx.x, sm);
+  tile_body<NP, SPATIAL, VEC>(a, a.tile0 + (int)blockIdx.x, sm);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -674,7 +676,9 @@ __global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArg
   const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (p >= a.P) return;
   const int nchunk = (a.g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
-  for (int c = blockIdx.y; c < nchunk; c += gridDim.y) links_chunk<SPATIAL>(a, p, c * kLinkSteps);
+  const int c1 = a.chunk1 ? a.chunk1 : nchunk;
+  for (int c = a.chunk0 + (int)blockIdx.y; c < c1; c += gridDim.y)
+    links_chunk<SPATIAL>(a, p, c * kLinkSteps);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1044,27 +1048,45 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   cudaStream_t s = ctx->stream;
   const int sched = segment_schedule(ctx, crit);
   MSF_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * 4, s));
-  if (sched & MSF_SCHED_FUSED_CRITERION) {
-    // the criterion evaluated inside the tile pass (one kernel, latency-bound phases)
-    ScopedKernel k(ctx, "k_tile");
-    launch_tile_any(a, spatial, g.ntiles, s);
-  } else {
-    // the criterion as a streaming pass, the tile pass then starting from its row masks
-    {
-      ScopedKernel k(ctx, "k_mask");
-      if ((a.g.nx & 3) == 0) launch_mask_np<true>(a, s);
-      else launch_mask_np<false>(a, s);
-    }
-    ScopedKernel k(ctx, "k_tile");
-    if (spatial) launch_tile<-1, true, false>(a, g.ntiles, s);
-    else launch_tile<-1, false, false>(a, g.ntiles, s);
+  const bool fused = sched & MSF_SCHED_FUSED_CRITERION;
+  if (!fused) {  // the criterion as a streaming pass, the tile pass then starting from its masks
+    ScopedKernel k(ctx, "k_mask");
+    if ((a.g.nx & 3) == 0) launch_mask_np<true>(a, s);
+    else launch_mask_np<false>(a, s);
   }
-  MSF_CUDA_TRY(cudaGetLastError());
+  auto tiles = [&](int t0, int n) {  // the tile pass over tiles [t0, t0 + n)
+    ScopedKernel k(ctx, "k_tile");
+    SegArgs at = a;
+    at.tile0 = t0;
+    if (fused) launch_tile_any(at, spatial, n, s);  // criterion inside (latency-bound phases)
+    else if (spatial) launch_tile<-1, true, false>(at, n, s);
+    else launch_tile<-1, false, false>(at, n, s);
+  };
   // cross-tile joins and trajectory joins touch only the union-find and commute: by default
   // they run side by side, the trajectory pass on the auxiliary stream; the serial schedule
-  // runs the trajectory pass after the cross-tile joins on the context stream
+  // runs the trajectory pass after the cross-tile joins on the context stream; the pipelined
+  // one splits the tile pass at a time-tile row and starts the link chunks whose steps all lie
+  // before it while the later tiles are formed
   const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && g.tw > 1;
   const bool serial = sched & MSF_SCHED_SERIAL_JOINS;
+  const int nchunk = (g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
+  int split_tiles = 0, ready_chunks = 0;
+  if ((sched & MSF_SCHED_PIPELINE) && !serial && traj && g.tlt >= 2 && g.toff == 0) {
+    const int h = g.tlt / 2;
+    const int per_row = g.ntiles / g.tlt;     // tiles of one time-tile row
+    const int ready = h << g.lbt;             // window steps [0, ready) done after the first rows
+    // chunk c links steps c L .. c L + L: ready when c L + L < ready
+    ready_chunks = ready - 1 - kLinkSteps >= 0 ? (ready - 1 - kLinkSteps) / kLinkSteps + 1 : 0;
+    ready_chunks = std::min(ready_chunks, nchunk);
+    if (ready_chunks > 0) split_tiles = h * per_row;
+  }
+  if (split_tiles > 0) {
+    tiles(0, split_tiles);
+    MSF_CUDA_TRY(cudaGetLastError());
+  } else {
+    tiles(0, g.ntiles);
+  }
+  MSF_CUDA_TRY(cudaGetLastError());
   // When the last segmentation's features were extracted, the joins also keep every point
   // sample's component for the next extraction's point statistics (which then need no lookups);
   // a caller that only segments does not pay for the store.
@@ -1076,23 +1098,31 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
     MSF_TRY(LS.pcomp.ensure(sizeof(uint32_t) * (size_t)a.P * (size_t)g.tw));
     a.pcomp = LS.pcomp.as<uint32_t>();
   }
-  auto links = [&](cudaStream_t ls) {
+  auto links = [&](cudaStream_t ls, int c0, int c1) {  // link chunks [c0, c1)
     ScopedKernel k(ctx, "k_links", ls);
-    const int64_t nchunk = (g.tw - 1 + kLinkSteps - 1) / kLinkSteps;
-    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
-    if (spatial) k_links<true><<<grid, 256, 0, ls>>>(a);
-    else k_links<false><<<grid, 256, 0, ls>>>(a);
+    SegArgs al = a;
+    al.chunk0 = c0;
+    al.chunk1 = c1;
+    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min(c1 - c0, 65535));
+    if (spatial) k_links<true><<<grid, 256, 0, ls>>>(al);
+    else k_links<false><<<grid, 256, 0, ls>>>(al);
   };
-  if (traj && !serial) {
+  if (split_tiles > 0) {
+    MSF_TRY(ctx_fork(ctx));            // after the first tile rows
+    links(ctx->aux, 0, ready_chunks);
+    tiles(split_tiles, g.ntiles - split_tiles);
+    MSF_TRY(ctx_fork(ctx));            // after every tile
+    links(ctx->aux, ready_chunks, nchunk);
+  } else if (traj && !serial) {
     MSF_TRY(ctx_fork(ctx));
-    links(ctx->aux);
+    links(ctx->aux, 0, nchunk);
   }
   if ((crit->edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0) {
     ScopedKernel k(ctx, "k_hook");
     if (spatial) k_hook<true><<<g.ntiles, 256, 0, s>>>(a);
     else k_hook<false><<<g.ntiles, 256, 0, s>>>(a);
   }
-  if (traj && serial) links(s);
+  if (traj && serial) links(s, 0, nchunk);
   if (traj && !serial) MSF_TRY(ctx_join(ctx));
   {
     ScopedKernel k(ctx, "k_flatten");

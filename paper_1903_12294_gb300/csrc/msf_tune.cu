@@ -69,7 +69,8 @@ using namespace msf;
 extern "C" {
 
 int msf_set_schedule(msf_ctx* c, int sched) {
-  if (!c || sched < -1 || sched > (MSF_SCHED_FUSED_CRITERION | MSF_SCHED_SERIAL_JOINS))
+  if (!c || sched < -1 ||
+      sched > (MSF_SCHED_FUSED_CRITERION | MSF_SCHED_SERIAL_JOINS | MSF_SCHED_PIPELINE))
     return MSF_ERR_INVALID_ARG;
   c->sched = sched;
   return MSF_OK;
@@ -162,8 +163,12 @@ int msf_autotune(msf_ctx* c, const msf_criteria* crit, int reps, msf_tune_result
   const std::vector<int> tiles = tile_candidates(d, g0.tw);
   for (size_t i = 0; st == MSF_OK && i < tiles.size(); ++i) {
     const int by = tiles[i] >> 16, bz = (tiles[i] >> 8) & 0xFF, bt = tiles[i] & 0xFF;
-    for (int sched = 0; st == MSF_OK && sched < 4; ++sched) {
+    const int rows = (g0.tw + bt - 1) / bt;  // time-tile rows with this shape
+    for (int sched = 0; st == MSF_OK && sched < 8; ++sched) {
       if ((sched & MSF_SCHED_SERIAL_JOINS) && !traj) continue;  // same launches as without
+      if ((sched & MSF_SCHED_PIPELINE) &&
+          (!traj || rows < 2 || (sched & MSF_SCHED_SERIAL_JOINS)))
+        continue;  // no pipelined form: the same launches as a schedule already timed
       if (by == dby && bz == dbz && bt == dbt && sched == 0) continue;
       float ms = 0.f;
       st = time_config(by, bz, bt, sched, &ms);

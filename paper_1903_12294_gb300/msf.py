@@ -38,7 +38,7 @@ EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_set_schedule", "msf_autotune", "msf_get_tuning", "msf_tune_clear",
            "msf_set_batch_graphs", "msf_batch_graph_replays", "msf_set_batch_tile",
            "msf_autotune_batch", "msf_set_batch_schedule")
-MSF_SCHED_FUSED_CRITERION, MSF_SCHED_SERIAL_JOINS = 1, 2
+MSF_SCHED_FUSED_CRITERION, MSF_SCHED_SERIAL_JOINS, MSF_SCHED_PIPELINE = 1, 2, 4
 MSF_MERGE_POINT, MSF_MERGE_FIELD = 1, 2
 MSF_SPACE_POINTS, MSF_SPACE_VOXELS = 0, 1
 

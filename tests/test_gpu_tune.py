@@ -23,7 +23,7 @@ def test_every_schedule_gives_the_oracle_labels(gpu, orc, nx):
     ctx = _ctx(gpu, wl)
     try:
         got = {}
-        for sched in range(4):
+        for sched in range(8):
             ctx.set_schedule(sched)
             for tile in [(0, 0, 0), (8, 8, 4), (4, 32, 2), (32, 8, 1)]:
                 ctx.set_tile(*tile)
@@ -70,7 +70,7 @@ def test_autotune_keeps_an_applied_choice(gpu):
         rule = ctx.tuning(0, 12, wl.preds, wl.edges)
         assert rule[3] == 0
         r = ctx.autotune(0, 12, wl.preds, wl.edges, reps=2)
-        assert r["by"] * r["bz"] * r["bt"] == 256 and 0 <= r["sched"] <= 3
+        assert r["by"] * r["bz"] * r["bt"] == 256 and 0 <= r["sched"] <= 5
         assert r["n_tried"] > 4 and 0 < r["ms"] <= r["ms_default"]
         chosen = ctx.tuning(0, 12, wl.preds, wl.edges)
         assert chosen == (r["by"], r["bz"], r["bt"], r["sched"])
@@ -89,7 +89,7 @@ def test_autotune_keeps_an_applied_choice(gpu):
         ctx.tune_clear()
         assert ctx.tuning(0, 12, wl.preds, wl.edges) == rule
         with pytest.raises(gpu.MsfError) as e:
-            ctx.set_schedule(4)
+            ctx.set_schedule(8)
         assert e.value.status == gpu.MSF_ERR_INVALID_ARG
         with pytest.raises(gpu.MsfError) as e:
             ctx.autotune(3, 3, wl.preds, wl.edges)
