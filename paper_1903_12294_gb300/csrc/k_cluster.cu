@@ -316,8 +316,10 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_field_tiled(const __grid
     }
     __syncthreads();
     const int ncell = s_n[0] * s_n[1] * s_n[2] * s_n[3];
-    // one neighbouring cell per thread: its filed centres go to the shared list
-    int cnt = 0;
+    // one neighbouring cell per thread: its filed centres go to the shared list, except those
+    // whose time fails the search region for this tile's step (every sample of the tile has
+    // that time, so the region test would reject them for all of them)
+    int cnt = 0, kept = 0;
     uint32_t c0 = 0;
     if (ncell <= 256 && tid < ncell) {
       int q = tid;
@@ -328,8 +330,12 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_field_tiled(const __grid
       const int cell = ((m * a.k[2] + l) * a.k[1] + j) * a.k[0] + i;
       c0 = __ldg(a.cell_start + cell);
       cnt = (int)(__ldg(a.cell_start + cell + 1) - c0);
+      for (int r = 0; r < cnt; ++r) {
+        const int c = (int)__ldg(a.cell_items + c0 + r);
+        kept += fabsf(__fsub_rn(ts, a.centers[6 * (int64_t)c + 3])) <= a.C[3];
+      }
     }
-    int x = cnt;
+    int x = kept;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_field_tiled(const __grid
     }
     if (lane == 31) s_warp[w] = x;
     __syncthreads();
-    int off = x - cnt;
+    int off = x - kept;
     for (int q = 0; q < w; ++q) off += s_warp[q];
     if (tid == 255) {
       int tot = 0;
@@ -351,12 +357,14 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_field_tiled(const __grid
       for (int q = 0; q < cnt; ++q) {
         const int c = (int)__ldg(a.cell_items + c0 + q);
         const float* cc = a.centers + 6 * (int64_t)c;
-        s_cx[off + q] = cc[0];
-        s_cy[off + q] = cc[1];
-        s_cz[off + q] = cc[2];
-        s_ct[off + q] = cc[3];
-        s_cf[off + q] = cc[5];
-        s_id[off + q] = c;
+        if (!(fabsf(__fsub_rn(ts, cc[3])) <= a.C[3])) continue;
+        s_cx[off] = cc[0];
+        s_cy[off] = cc[1];
+        s_cz[off] = cc[2];
+        s_ct[off] = cc[3];
+        s_cf[off] = cc[5];
+        s_id[off] = c;
+        ++off;
       }
     __syncthreads();
     const int nc = s_total;
