@@ -384,3 +384,120 @@ def test_features_conservation_on_mid_slice(orc):
     # features are sorted by label and labels are component minima
     assert np.all(np.diff(feat["label"]) > 0)
     assert np.all(lab.reshape(-1)[feat["label"]] == feat["label"])
+
+
+# ---------------------------------------------------------------------------------------------
+# per-feature point moments (§3.2.2 centre averages, §3.4 deviations of the point samples)
+# ---------------------------------------------------------------------------------------------
+
+def _labels_from_ndimage(active):
+    """Canonical labels (component minimum window-linear index, -1 inactive) of the spatial +
+    temporal graph, from scipy's labelling alone (the oracle's labelling is not used)."""
+    from scipy import ndimage
+    s = np.zeros((3, 3, 3, 3), bool)
+    s[1] = True                       # all 27 offsets within a step
+    s[0, 1, 1, 1] = s[2, 1, 1, 1] = True
+    comp, n = ndimage.label(active, structure=s)
+    flat = comp.reshape(-1)
+    out = np.full(flat.size, -1, np.int32)
+    for c in range(1, n + 1):
+        idx = np.flatnonzero(flat == c)
+        out[idx] = idx.min()
+    return out.reshape(active.shape)
+
+
+def _numpy_point_moments(labels, key, attr, t0, V):
+    """Per feature label: (n_pts, mean, population std) of every attribute over the point
+    samples whose voxel-timestep carries that label, with raw fp32 values widened to fp64 and
+    non-finite values taken as 0 (they still count as samples)."""
+    tw = labels.shape[0]
+    lab = labels.reshape(tw, V)
+    out = {}
+    for t in range(tw):
+        for p in range(key.shape[1]):
+            v = key[t0 + t, p]
+            if v < 0 or lab[t, v] < 0:
+                continue
+            vals = attr[t0 + t, :, p].astype(np.float64)
+            vals = np.where(np.isfinite(vals), vals, 0.0)
+            out.setdefault(int(lab[t, v]), []).append(vals)
+    res = {}
+    for l, rows in out.items():
+        m = np.array(rows)
+        res[l] = (m.shape[0], m.mean(0), m.std(0))
+    return res
+
+
+def test_features_point_moments_two_valued_closed_form(orc):
+    """One feature of three voxels holding 1, 3 and 0 samples (n_vox = 3, n_pts = 4): attribute
+    0 is 1.0 in the lone sample and 3.0 in the other three, so mean = (1 + 9) / 4 = 2.5 and the
+    population variance of a two-valued set, n1 n2 (a - b)^2 / n^2 = 3 * 4 / 16 = 0.75;
+    attribute 1 is -2, 2, 2, 2: mean 1, variance 3 * 16 / 16 = 3. Dividing by n_vox, or mixing
+    the scaled fixed-point mean with unscaled squares, fails here."""
+    T, nz, ny, nx = 1, 1, 1, 5
+    field = np.zeros((T, nz, ny, nx), np.float32)
+    field[0, 0, 0, 1:4] = 1.0
+    pts = np.array([[1.5, 2.2, 2.5, 2.8, 0.5, 4.5],        # voxel 1 once, voxel 2 three times,
+                    [0.5] * 6, [0.5] * 6], np.float32)    # two samples off the feature
+    pos = pts[None]
+    attr = np.array([[[1.0, 3.0, 3.0, 3.0, 50.0, -50.0],
+                      [-2.0, 2.0, 2.0, 2.0, 9.0, 9.0]]], np.float32)
+    b = orc.bin(field.shape, pos, attr)
+    lab, nf = orc.segment(field, b["count"], b["mean"], b["key"], 0, 1, [(F, 0, GT, 0.5, 0)])
+    feat = orc.features(field, b["count"], attr, b["key"], b["kscale"], 0, 1, lab)
+    assert nf == 1 and feat["n_vox"][0] == 3 and feat["n_pts"][0] == 4
+    assert feat["mean_attr"][0].tolist() == [2.5, 1.0]
+    np.testing.assert_allclose(feat["std_attr"][0], [np.sqrt(0.75), np.sqrt(3.0)], rtol=1e-14)
+    k = b["kscale"]
+    assert feat["sumq"][0].tolist() == [int(10 * 2 ** int(k[0])), int(4 * 2 ** int(k[1]))]
+
+
+def test_features_point_moments_match_numpy(orc):
+    """Random window: voxels with 0, 1 and many samples (points clustered onto a few voxels),
+    three attributes of different scales, some non-finite values. Each feature's n_pts, mean and
+    population std of every attribute equal numpy's over the samples in its voxel-timesteps
+    (labels from scipy's labelling, not the oracle's)."""
+    rng = np.random.default_rng(1903)
+    T, nz, ny, nx = 4, 8, 8, 8
+    V = nz * ny * nx
+    field = rng.uniform(0, 1, (T, nz, ny, nx)).astype(np.float32)
+    P = 600
+    hot = rng.choice(V, 12, replace=False)                    # a few crowded voxels, members
+    field.reshape(T, V)[:, hot] = 1.0
+    pos = np.empty((T, 3, P), np.float32)
+    for t in range(T):
+        crowd = rng.random(P) < 0.5
+        v = np.where(crowd, hot[rng.integers(0, hot.size, P)], rng.integers(0, V, P))
+        z, y, x = v // (ny * nx), (v // nx) % ny, v % nx
+        pos[t] = np.stack([x + rng.random(P), y + rng.random(P), z + rng.random(P)])
+    pos[0, 0, :5] = np.nan                                    # a few samples off the grid
+    attr = np.stack([rng.normal(5.0, 2.0, (T, P)), rng.uniform(-1e-3, 3e-3, (T, P)),
+                     rng.exponential(100.0, (T, P))], 1).astype(np.float32)
+    attr[1, 0, 7] = np.nan                                   # non-finite samples inside a
+    attr[2, 2, 11] = np.inf                                  # crowded member voxel
+    for t, p in ((1, 7), (2, 11)):
+        v = int(hot[0])
+        pos[t, :, p] = (v % nx + 0.5, (v // nx) % ny + 0.5, v // (ny * nx) + 0.5)
+    b = orc.bin(field.shape, pos, attr)
+    t0, t1 = 1, 4
+    active = field[t0:t1] > 0.95
+    lab = _labels_from_ndimage(active)
+    feat = orc.features(field, b["count"], attr, b["key"], b["kscale"], t0, t1, lab)
+    ref = _numpy_point_moments(lab, b["key"], attr, t0, V)
+    counts = b["count"][t0:t1].reshape(t1 - t0, V)
+    n_vox = {int(l): int((lab == l).sum()) for l in feat["label"]}
+    assert any(feat["n_pts"][i] != n_vox[int(l)] for i, l in enumerate(feat["label"]))
+    assert counts[active.reshape(t1 - t0, V)].max() >= 3      # crowded voxels are members
+    checked = 0
+    for i, l in enumerate(feat["label"]):
+        n, m, s = ref.get(int(l), (0, None, None))
+        assert feat["n_pts"][i] == n
+        if n == 0:
+            assert np.isnan(feat["mean_attr"][i]).all()
+            continue
+        np.testing.assert_allclose(feat["mean_attr"][i], m, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(feat["std_attr"][i], s, rtol=1e-9, atol=1e-12)
+        checked += 1
+    assert checked >= 5
+    hot_label = {int(lab[t - t0].reshape(V)[hot[0]]) for t in (1, 2)}
+    assert hot_label <= {int(l) for l in feat["label"]}      # the non-finite samples count
