@@ -1,15 +1,20 @@
 """Benchmark: one step = the whole hot path (bin -> criterion + 4D labelling -> per-feature
-statistics) over the mid workload: 128^3 fp32 field x 32 timesteps, 1M particles with two
-attributes, criterion field > 0.5 AND mean speed in [q40, q90], all edge classes.
+statistics) over the combustion-shaped workload: 256^3 fp32 field x 24 timesteps, 8M particles
+with four attributes (temperature, mixture fraction, speed, age), criterion field > 0.5 AND mean
+temperature above its 60th percentile AND mean mixture fraction in its [q20, q80] band, all edge
+classes.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config 2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config 3]
 
-Prints one JSON line. ``value`` is voxel-timesteps per second (Gvt/s) with the dataset
-resident in HBM; ``e2e`` is the same metric through the C ABI with host buffers (the
-host->device copy of the field and particles and the device->host copy of the labels and the
-feature table inside every step). Under torchrun each rank runs its own replica (the path has
-no exchange step for independent workloads): weak scaling, value = all ranks' voxel-timesteps
-over the slowest rank's time.
+Prints one JSON line. ``value`` is voxel-timesteps per second (Gvt/s) of the whole step with the
+dataset resident in HBM (K steps timed with CUDA events, no per-kernel instrumentation);
+``segment_only`` is the same metric for the segment query alone (msf_segment, criterion +
+labelling), with its own roofline at the algorithmic bytes per voxel-timestep. ``e2e`` is the
+step through the C ABI with host buffers (the host->device copy of the field and particles and
+the device->host copy of the labels and the feature table inside every step). Per-kernel
+figures come from a second pass of K steps with CUDA events around every launch. Under
+torchrun each rank runs its own replica (the path has no exchange step for independent
+workloads): weak scaling, value = all ranks' voxel-timesteps over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -71,7 +76,9 @@ def d2d_copy_gbs(dev, nbytes=1 << 31, reps=5):
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+    """Samples SM clocks and throttle reasons with nvidia-smi while the context is open (the
+    warm-up, the timed steps and the profiled pass); summary() reports the samples taken
+    between two marks (the timed region) beside those of the whole session."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -80,12 +87,13 @@ class Clocks:
         self.index = index
         self.p = None
         self.lines = []
+        self.marks = {}
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -95,7 +103,10 @@ class Clocks:
 
     def _read(self):
         for line in self.p.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, name):
+        self.marks[name] = time.perf_counter()
 
     def __exit__(self, *exc):
         if self.p:
@@ -105,10 +116,11 @@ class Clocks:
             except Exception:
                 self.p.kill()
 
-    def summary(self):
+    @staticmethod
+    def _digest(lines):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue
@@ -120,10 +132,20 @@ class Clocks:
             for n, v in zip(names, f[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
-        if not sm:
+        return sm, mx, reasons
+
+    def summary(self, start=None, end=None):
+        t0 = self.marks.get(start, float("-inf"))
+        t1 = self.marks.get(end, float("inf"))
+        sm, mx, reasons = self._digest([ln for t, ln in self.lines if t0 <= t <= t1])
+        ssm, smx, sreasons = self._digest([ln for _, ln in self.lines])
+        if not ssm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm) if sm else statistics.median(ssm),
+                "sm_max_mhz": max(mx) if mx else max(smx), "reasons": sorted(reasons | sreasons),
+                "samples": len(sm),
+                "session": {"samples": len(ssm), "sm_mhz_median": statistics.median(ssm),
+                            "sm_mhz_min": min(ssm), "reasons": sorted(sreasons)}}
 
 
 # per-kernel algorithmic bytes: the bytes each kernel must move through HBM per launch by the
@@ -146,7 +168,44 @@ def algorithmic_bytes(wl, n_pred_arrays, keep_sumq=False, fused_criterion=False)
         "k_links": P * tw * 4,                               # keys of the window in
         "k_final": V * tw * 4,                               # labels out
         "k_feat_vox": V * tw * 8,                            # labels + field in
+        "k_feat_points": P * tw * (4 + 4 * A),               # keys + attributes of the window in
     }
+
+
+def segment_bytes_per_vt(wl, n_pred_arrays):
+    """Algorithmic bytes of one segment query per voxel-timestep: every distinct predicate
+    array read once (field, count or one attribute's means), the labels written once, and the
+    window's trajectory keys read once (4 P / V per step)."""
+    T, nz, ny, nx = wl.field.shape
+    V = nx * ny * nz
+    P = wl.pos.shape[2]
+    traj = 4.0 * P / V if (wl.edges & 4) and P else 0.0
+    return 4.0 * n_pred_arrays + 4.0 + traj
+
+
+def host_cpu():
+    """Model name and logical core count of the host (lscpu, else os.cpu_count)."""
+    model, cores = None, os.cpu_count()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() == "Model name" and model is None:
+                model = v.strip()
+            elif k.strip() == "CPU(s)":
+                cores = int(v.strip())
+    except Exception:
+        pass
+    return {"model": model, "logical_cores": cores}
+
+
+def input_sha256(*arrays):
+    """SHA-256 over the raw bytes of the generated inputs (host copies, in order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for a in arrays:
+        h.update(memoryview(a.numpy()).cast("B"))
+    return h.hexdigest()
 
 
 def run_gpu(args):
@@ -206,30 +265,45 @@ def run_gpu(args):
             raise msf.MsfError(st, "msf_extract_features")
         return n
 
-    for _ in range(args.warmup):
-        n_features = step()
-    torch.cuda.synchronize()
-    ctx.kernel_times(reset=True)
-    ctx.profiling(True)
-    barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            n_features = step()
-        ev1.record(stream)
+    def timed(fn, k):
+        barrier()
         torch.cuda.synchronize()
-    barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ktimes = ctx.kernel_times(reset=True)
-    ctx.profiling(False)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1) / k, r
+
+    with Clocks(local) as clk:
+        for _ in range(args.warmup):
+            n_features = step()
+        torch.cuda.synchronize()
+        # the headline: K steps, nothing instrumented
+        clk.mark("timed_start")
+        ms, n_features = timed(step, args.steps)
+        clk.mark("timed_end")
+        # the segment query alone (criterion + labelling, msf_segment with device labels)
+        for _ in range(args.warmup):
+            msf.msf_segment(ctx.h, crit, labels)
+        seg_ms, _ = timed(lambda: msf.msf_segment(ctx.h, crit, labels), args.steps)
+        seg_ms_long, _ = timed(lambda: msf.msf_segment(ctx.h, crit, labels),
+                               max(args.steps, 200))
+        # per-kernel split: K more steps with CUDA events around every launch (each on the
+        # stream the kernel runs on)
+        ctx.kernel_times(reset=True)
+        ctx.profiling(True)
+        ms_prof, _ = timed(step, args.steps)
+        ktimes = ctx.kernel_times(reset=True)
+        ctx.profiling(False)
     ms = replicas.max_over_ranks(ms, dev)
     value = replicas.weak_throughput(vt, ms, world) / 1e9
-    launches = sum(n for _, n in ktimes.values()) // max(args.steps, 1)
+    launches_per_step = sum(n for _, n in ktimes.values()) // max(args.steps, 1)
 
-    # dominant kernel and its roofline (CUDA events around every launch on the context stream)
+    # dominant kernel and its roofline (per-launch CUDA-event durations from the profiled pass)
     npa = len({(s, a if s == 2 else 0) for s, a, *_ in wl.preds})
     fused = bool(msf.msf_get_tuning(ctx.h, crit)[3] & msf.MSF_SCHED_FUSED_CRITERION)
     abytes = algorithmic_bytes(wl, npa, fused_criterion=fused)
@@ -257,29 +331,23 @@ def run_gpu(args):
     step_roof = {"algorithmic_bytes": step_bytes,
                  "achieved_gb_per_s": round(step_bytes / (ms * 1e-3) / 1e9, 1),
                  "frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4)}
-    # the segment pass alone (criterion + labelling, msf_segment with device labels), timed with
-    # CUDA events around the calls; the per-kernel sums above overlap where kernels run side by
-    # side on the auxiliary stream
-    for _ in range(args.warmup):
-        msf.msf_segment(ctx.h, crit, labels)
-    torch.cuda.synchronize()
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(args.steps):
-        msf.msf_segment(ctx.h, crit, labels)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    seg_ms = s0.elapsed_time(s1) / args.steps
+    bpv = segment_bytes_per_vt(wl, npa)
+    seg_roof = {"bound": "hbm", "bytes_per_vt": round(bpv, 3),
+                "achieved": round(bpv * vt / (seg_ms_long * 1e-3) / 1e9, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(bpv * vt / (seg_ms_long * 1e-3) / 1e9 / peak, 4)}
 
     # end to end through the C ABI with host buffers
     e2e = None
+    hashes = None
     if not args.no_e2e:
         hf = wl.field.cpu().pin_memory()
         hp = wl.pos.cpu().pin_memory()
         ha = wl.attr.cpu().pin_memory()
         hl = torch.empty((tw, nz, ny, nx), dtype=torch.int32).pin_memory()
         hfeat = np.zeros(fcap, msf.FEATURE_DTYPE)
+        if rank == 0:
+            hashes = {"field": input_sha256(hf), "pos": input_sha256(hp), "attr": input_sha256(ha)}
 
         def e2e_step():
             ctx.load(hf, hp, ha)
@@ -312,16 +380,30 @@ def run_gpu(args):
         e2e = {"value": round(replicas.weak_throughput(vt, ms_e2e, world) / 1e9, 3), "unit": UNIT,
                "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+        del hf, hp, ha, hl
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
+    ctx.close()
+    del labels, feats
+    wl_name, wl_shape = wl.name, (nx, ny, nz, T, wl.pos.shape[2], wl.attr.shape[1])
+    wl_desc = (wl.t0, wl.t1, wl.preds)
+    del wl
+    torch.cuda.empty_cache()
     clustering = None
     if rank == 0 and not args.no_cluster:
-        ctx.bin()
-        clustering, last = run_clustering(ctx, wl, dev)
-        clustering["post"] = run_post(ctx, wl, dev, *last)
+        # the paper's clustering on the mid workload (128^3 x 32, 1M points)
+        mwl = synth.mid(device=dev)
+        mctx = msf.Context(local, stream)
+        mctx.load(mwl.field, mwl.pos, mwl.attr)
+        mctx.bin()
+        clustering, last = run_clustering(mctx, mwl, dev)
+        clustering["post"] = run_post(mctx, mwl, dev, *last)
         del last
+        mctx.close()
+        del mwl
+        torch.cuda.empty_cache()
     # the batched and served forms are reported from rank 0 (each replica would measure the same)
     batched = None
     if rank == 0 and not args.no_batched:
@@ -330,26 +412,32 @@ def run_gpu(args):
     if rank == 0 and not args.no_serving:
         serving = run_serving(dev, seconds=args.serve_seconds)
 
-    ctx.close()
     if rank == 0:
+        cs = clk.summary("timed_start", "timed_end")
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"{wl.name}: {nx}x{ny}x{nz} fp32 field x {T} timesteps, "
-                                   f"{wl.pos.shape[2]} particles x {wl.attr.shape[1]} attributes, "
-                                   f"window [{wl.t0},{wl.t1}), preds {wl.preds}",
+            "config": {"workload": f"{wl_name}: {wl_shape[0]}x{wl_shape[1]}x{wl_shape[2]} fp32 "
+                                   f"field x {wl_shape[3]} timesteps, {wl_shape[4]} particles x "
+                                   f"{wl_shape[5]} attributes, window [{wl_desc[0]},{wl_desc[1]}), "
+                                   f"preds {wl_desc[2]}",
                        "step": "bin + criterion/label + features", "vt_per_step": vt,
                        "n_features": int(n_features),
                        "l2": "inputs larger than L2 (field alone 4*V*T bytes)",
-                       "parallelism": f"replicas x{world}", "tuning": tuning},
-            "segment_only": {"ms": round(seg_ms, 4),
+                       "parallelism": f"replicas x{world}", "tuning": tuning,
+                       "input_sha256": hashes},
+            "segment_only": {"ms": round(seg_ms, 4), "ms_200": round(seg_ms_long, 4),
                              "value": round(vt / (seg_ms * 1e-3) / 1e9, 3) if seg_ms else None,
-                             "unit": UNIT},
+                             "value_200": round(vt / (seg_ms_long * 1e-3) / 1e9, 3),
+                             "unit": UNIT, "roofline": seg_roof},
             "roofline": roof, "step_roofline": step_roof, "d2d_copy_gb_per_s": copy_gbs,
-            "clocks": clk.summary(), "e2e": e2e,
-            "gpu_launches": int(launches), "kernels": per_kernel, "cpu_baseline": cpu,
+            "clocks": cs, "e2e": e2e,
+            "gpu_launches": int(launches_per_step * args.steps),
+            "gpu_launches_per_step": int(launches_per_step),
+            "ms_per_step_profiled": round(ms_prof, 4),
+            "kernels": per_kernel, "cpu_baseline": cpu,
             "batched": batched, "serving": serving, "clustering": clustering,
         }
         print(json.dumps(out))
@@ -674,7 +762,7 @@ def cpu_baseline(wl, steps_in_sample=8):
     return {"value": round(vt / secs / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"timesteps [{wl.t0},{wl.t0 + n}) of the workload ({vt} voxel-timesteps, "
                       f"{wl.pos.shape[2]} particles): bin + segment + features, single thread",
-            "seconds": round(secs, 3)}
+            "seconds": round(secs, 3), "host": host_cpu()}
 
 
 def run_reference(args):
@@ -703,7 +791,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": wl.name, "sample": sample},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_cpu()},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
 
@@ -714,7 +802,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="segment with the fixed tile rule and schedule instead of the autotuner's")

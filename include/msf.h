@@ -212,6 +212,13 @@ int msf_segment(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int lab
  * records; *n_out receives the number of features. When cap < *n_out nothing is written and
  * the call returns MSF_ERR_CAPACITY (cap = 0 with out = NULL is a valid size query).
  * labels: host or device per labels_kind. Synchronises the stream.
+ * Shortcut: when `labels` is the buffer the last msf_segment of this context wrote, with the
+ * same criteria on the same binned dataset, the statistics come from that segmentation's
+ * retained component table instead of from the buffer. Library calls that write label buffers
+ * in between (msf_relabel, msf_cluster, msf_segment_batch, msf_autotune) drop the retained
+ * segmentation, so the buffer is read again. A caller that changes the buffer by any other
+ * means (its own kernels or copies) must do the same by calling msf_segment again first, or
+ * pass the labels in another buffer.
  * Errors: NOT_LOADED, NOT_BINNED, INVALID_ARG, TOO_LARGE, CAPACITY, OUT_OF_MEMORY, CUDA. */
 int msf_extract_features(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
                          int labels_kind, msf_feature* out, int out_kind, int64_t cap,
@@ -363,25 +370,28 @@ int msf_server_destroy(msf_server* srv);
 /* ---- allocation-free labelling ----------------------------------------------------------- */
 
 /* Field-only labelling that allocates nothing, for callers that cannot allocate device memory
- * when they need a segmentation: code running while its stream is captured into a CUDA graph,
- * where allocation calls are not allowed, and services that reserve all device memory up front
- * in their own pool and forbid cudaMalloc/cudaFree (which can synchronise the device or fail
- * under memory pressure). The paper has no counterpart; this is a service of this library.
+ * when they need a segmentation: services that reserve all of their device memory up front in
+ * a pool of their own and forbid further cudaMalloc/cudaFree (those calls can synchronise the
+ * whole device and can fail under memory pressure), real-time loops with a latency budget, and
+ * plug-ins whose host program owns the device memory. The paper has no counterpart; this is a
+ * service of this library.
  *
  * Computes what msf_segment computes for a dataset without points: labels of the window given
- * by `field` ([tw][nz][ny][nx] fp32, device) under one optional field predicate (`pred`, host,
- * NULL = every voxel-timestep is a member; src must be MSF_SRC_FIELD) with MSF_EDGE_SPATIAL and/or
- * MSF_EDGE_TEMPORAL edges. `labels` ([tw][nz][ny][nx] int32, device) receives the canonical
- * labels; `n_features` (host, may be NULL) the number of features. `stream` is a cudaStream_t
- * (NULL = legacy default stream); the call synchronises it before returning.
+ * by `field` ([tw][nz][ny][nx] fp32, device, 4-byte aligned; 16-byte aligned rows take a faster
+ * path) under one optional field predicate (`pred`, host, NULL = every voxel-timestep is a
+ * member; src must be MSF_SRC_FIELD) with MSF_EDGE_SPATIAL and/or MSF_EDGE_TEMPORAL edges.
+ * `labels` ([tw][nz][ny][nx] int32, device, 4-byte aligned) receives the canonical labels;
+ * `n_features` (host, may be NULL) the number of features. `stream` is a cudaStream_t (NULL =
+ * legacy default stream); the call synchronises it before returning.
  * No context is needed. Scratch is one 16 MiB array in the library's device image (present on
  * every device that loads the library until the process exits): windows that need more are
  * rejected with MSF_ERR_TOO_LARGE (about 4 million voxel-timesteps when nx is a multiple of 32).
  * The first call on each device looks up the array's device address; make that first call
- * before any stream capture. Every call shares the array, so calls that run concurrently on the
- * GPU (for example on different streams) race and must be serialised by the caller.
- * Errors: INVALID_ARG (sizes, NULL buffers, predicate not on the field, TRAJ or unknown edge
- * bits), TOO_LARGE, CUDA. tw == 0 is valid and writes nothing. */
+ * before any stream capture. Every call shares the array and finds the previous call's contents
+ * there (it clears what must start at zero itself), so calls that run concurrently on the GPU
+ * (for example on different streams) race and must be serialised by the caller.
+ * Errors: INVALID_ARG (sizes, NULL or misaligned buffers, predicate not on the field, TRAJ or
+ * unknown edge bits), TOO_LARGE, CUDA. tw == 0 is valid and writes nothing. */
 int msf_segment_field_noalloc(int nx, int ny, int nz, int tw, const float* field,
                               const msf_pred* pred, uint32_t edges, int32_t* labels,
                               int64_t* n_features, void* stream);

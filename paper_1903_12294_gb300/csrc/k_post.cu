@@ -545,6 +545,9 @@ int msf_relabel(msf_ctx* c, int32_t* labels, int labels_kind, int64_t n, const i
     return MSF_ERR_INVALID_ARG;
   if (n >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
   if (n == 0) return MSF_OK;
+  // the labels may be the buffer of the retained segmentation: its features no longer describe
+  // them, so msf_extract_features must read the buffer from now on
+  c->last.valid = false;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
   PostScratch& S = c->post;
   const int32_t* dm;

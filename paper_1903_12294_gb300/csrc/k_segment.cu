@@ -996,7 +996,10 @@ static void launch_tile_np(const SegArgs& a, int grid, cudaStream_t s) {
 }
 
 static void launch_tile_any(const SegArgs& a, bool spatial, int grid, cudaStream_t s) {
-  const bool vec = (a.g.nx & 3) == 0;  // rows start on 16-byte boundaries
+  // 16-byte loads need every row to start on a 16-byte boundary: nx a multiple of four (so
+  // that V is one too) and every predicate array 16-byte aligned
+  bool vec = (a.g.nx & 3) == 0;
+  for (int j = 0; j < a.npred; ++j) vec &= ((uintptr_t)a.pred[j].base & 15) == 0;
   if (spatial) {
     if (vec) launch_tile_np<true, true>(a, grid, s);
     else launch_tile_np<true, false>(a, grid, s);

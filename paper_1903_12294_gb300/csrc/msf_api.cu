@@ -544,6 +544,7 @@ int msf_cluster(msf_ctx* c, const msf_cluster_params* prm, int32_t* field_labels
   if (nf >= ((int64_t)1 << 31) || np >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
   MSF_TRY(ctx_field_ready(c));
+  c->last.valid = false;  // the label buffers may be the retained segmentation's
   int32_t* fl = field_labels;
   int32_t* pl = point_labels;
   if (labels_kind == MSF_HOST || !fl) {

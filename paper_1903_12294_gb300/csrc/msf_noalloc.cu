@@ -1,18 +1,20 @@
 // msf_segment_field_noalloc: field-only labelling that allocates nothing.
 //
-// Some callers cannot allocate device memory at the moment they need a segmentation: code
-// that runs while its stream is being captured into a CUDA graph (allocation calls are not
-// allowed there), and services that reserve all of their device memory up front in their own
-// pool and forbid further cudaMalloc/cudaFree (which can synchronise the device, stall other
-// work, or fail under memory pressure). This entry point serves them: it needs no context and
-// uses, as scratch, one fixed array that lives in the library's device image.
+// Some callers cannot allocate device memory at the moment they need a segmentation. A service
+// that reserves all of its device memory up front in a pool of its own, and then forbids any
+// further cudaMalloc/cudaFree, is one: those calls can synchronise the whole device (stalling
+// the other streams' work), and they can fail under memory pressure in the middle of serving.
+// A real-time loop with a latency budget is another, and so is a plug-in whose host program
+// owns the device memory. This entry point serves them: it needs no context and uses, as
+// scratch, one fixed array that lives in the library's device image.
 //
 // The array below is kNoAllocScratchBytes (16 MiB) on every device that loads the library,
 // held until the process exits. Host code cannot use the array's name as a device address, so
 // the first call on each device looks the address up with cudaGetSymbolAddress (with that
-// device current) and keeps it; later calls reuse it. All calls share the array and it keeps
-// the last call's contents: the call clears what must start at zero (the counters). Calls that
-// run at the same time on the GPU (for example on two streams) race on the array.
+// device current) and keeps it; later calls reuse it. That first call should therefore come
+// before any stream capture. All calls share the array and it keeps the last call's contents:
+// the call clears what must start at zero (the counters). Calls that run at the same time on
+// the GPU (for example on two streams) race on the array.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -65,6 +67,8 @@ extern "C" int msf_segment_field_noalloc(int nx, int ny, int nz, int tw, const f
     return MSF_OK;
   }
   if (!field || !labels) return MSF_ERR_INVALID_ARG;
+  // elements must be naturally aligned; rows on 16-byte boundaries take the vector path
+  if (((uintptr_t)field & 3) || ((uintptr_t)labels & 3)) return MSF_ERR_INVALID_ARG;
   Geometry g;
   MSF_TRY(geometry_for_dims(nx, ny, nz, tw, edges, &g));
   const bool spatial = edges & MSF_EDGE_SPATIAL;

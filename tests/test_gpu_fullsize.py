@@ -1,7 +1,9 @@
 """Full-size parity on the combustion-shaped, batched and serving workloads (the sizes the
 benchmark and its batched/served forms run), against the CPU oracle. The combustion window is
-compared whole (binning bit-exact, labels bit-exact, feature count); for the batched and served
-workloads the oracle labels the queries with the shortest windows, at the full dataset size."""
+compared whole (binning bit-exact, labels bit-exact for its three-predicate criterion and for a
+four-predicate one with a count predicate, feature statistics); for the batched and served
+workloads the oracle labels the queries with the shortest windows and the longest one (the whole
+32 steps of the batched dataset, 64 of the 96 served steps), at the full dataset size."""
 import numpy as np
 import pytest
 import torch
@@ -23,28 +25,34 @@ def _host_gib_available():
 
 
 def test_combustion_full_size(gpu, orc):
-    """256^3 x 24, 8M particles with four attributes, a conjunction of three predicates (the
-    comparison holds about 30 GiB of host arrays at its peak)."""
+    """256^3 x 24, 8M particles with four attributes, a conjunction of three predicates, then
+    the same with a fourth, count >= 2 (the comparison holds about 40 GiB of host arrays at its
+    peak)."""
+    from tests.test_gpu_parity import check_features
     if _host_gib_available() < 64:
         pytest.skip("needs 64 GiB of free host memory for the oracle's arrays")
     wl = synth.combustion(device="cuda")
     t0, t1, preds, edges = wl.t0, wl.t1, wl.preds, wl.edges
+    preds4 = list(preds) + [(synth.SRC_COUNT, 0, synth.OP_GE, 2.0, 0.0)]
     ctx = gpu.Context(0)
     try:
         ctx.load(wl.field, wl.pos, wl.attr)
         ctx.bin()
         labels, n = ctx.segment(t0, t1, preds, edges)
+        feats = ctx.features(t0, t1, labels, preds, edges)
+        lab = labels.cpu().numpy()
+        labels4, n4 = ctx.segment(t0, t1, preds4, edges)
+        lab4 = labels4.cpu().numpy()
         torch.cuda.synchronize()
         key, count, mean, _ = ctx.bins("cpu")
-        lab = labels.cpu().numpy()
-        del labels
+        del labels, labels4
     finally:
         ctx.close()
     f, p, a = wl.numpy()
     del wl
     torch.cuda.empty_cache()
     o = orc.bin(f.shape, p, a, keep_sumq=False)
-    del p, a
+    del p
     assert np.array_equal(key.numpy(), o["key"])
     assert np.array_equal(count.numpy(), o["count"])
     assert np.array_equal(mean.numpy().view(np.uint32), o["mean"].view(np.uint32))
@@ -52,6 +60,12 @@ def test_combustion_full_size(gpu, orc):
     ref, n_ref = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, preds, edges)
     assert n == n_ref
     assert np.array_equal(lab, ref)
+    of = orc.features(f, o["count"], a, o["key"], o["kscale"], t0, t1, ref)
+    check_features(feats, of, a.shape[1])
+    del ref, of, lab
+    ref4, n_ref4 = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, preds4, edges)
+    assert 0 < n4 == n_ref4 < n_ref
+    assert np.array_equal(lab4, ref4)
 
 
 def _shortest(queries, k):
@@ -59,31 +73,39 @@ def _shortest(queries, k):
 
 
 def test_batched_workload_full_size_sampled(gpu, orc):
-    """192^3 x 32, 4M points, 64 queries in one msf_segment_batch call; the three shortest
-    windows against the oracle."""
+    """192^3 x 32, 4M points, the 64 random queries plus one over all 32 steps in one
+    msf_segment_batch call; the three shortest windows and the 32-step one against the
+    oracle."""
     wl = synth.batched(device="cuda")
+    queries = list(wl.queries)
+    t0, t1, pr, e = queries[0]
+    queries.append((0, wl.field.shape[0], pr, e))
     ctx = gpu.Context(0)
     try:
         ctx.load(wl.field, wl.pos, wl.attr)
         ctx.bin()
-        labels, nfs = ctx.segment_batch(wl.queries)
+        labels, nfs = ctx.segment_batch(queries)
         torch.cuda.synchronize()
-        picks = _shortest(wl.queries, 3)
+        picks = _shortest(queries, 3) + [len(queries) - 1]
         got = {i: (labels[i].cpu().numpy(), nfs[i]) for i in picks}
+        del labels
     finally:
         ctx.close()
     f, p, a = wl.numpy()
     o = orc.bin(f.shape, p, a, keep_sumq=False)
     for i in picks:
-        t0, t1, pr, e = wl.queries[i]
+        t0, t1, pr, e = queries[i]
         ref, n_ref = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
         assert got[i][1] == n_ref and np.array_equal(got[i][0], ref), i
+    assert queries[picks[-1]][1] - queries[picks[-1]][0] == 32
 
 
 def test_serving_workload_full_size_sampled(gpu, orc):
-    """1024^2 x 96 with 208,334 walkers; 24 queries through the server at once; the three
-    shortest windows against the oracle."""
+    """1024^2 x 96 with 208,334 walkers; 24 random queries and one of 64 steps through the
+    server at once; the three shortest windows and the 64-step one against the oracle."""
     wl = synth.serving(device="cuda", nq=24)
+    t0, t1, pr, e = wl.queries[0]
+    wl.queries = list(wl.queries) + [(16, 80, pr, e)]
     ctx = gpu.Context(0)
     try:
         ctx.load(wl.field, wl.pos, wl.attr)
@@ -92,7 +114,7 @@ def test_serving_workload_full_size_sampled(gpu, orc):
         try:
             for i, (t0, t1, pr, e) in enumerate(wl.queries):
                 srv.submit(i, t0, t1, pr, e)
-            picks = set(_shortest(wl.queries, 3))
+            picks = set(_shortest(wl.queries, 3)) | {len(wl.queries) - 1}
             got, seen = {}, 0
             while seen < len(wl.queries):
                 for r in srv.poll(cap=64, timeout_ms=1000):

@@ -376,3 +376,34 @@ def test_mean_conversion_ties(gpu, orc):
     assert int(o["kscale"][0]) == k
     assert [int(x) for x in o["sumq"][0, 0, 0, 0, :len(sums)]] == sums
     check_bins(g, o)
+
+
+def test_features_after_relabel_in_place(gpu, orc):
+    """segment -> msf_relabel on the same buffer (two features merged into the smaller label,
+    which stays the merged set's smallest index) -> extract_features: the statistics describe
+    the relabelled buffer (the oracle's features of those labels), not the retained
+    segmentation."""
+    wl = synth.tiny()
+    f, p, a = wl.numpy()
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(*_tensors(f, p, a))
+        ctx.bin()
+        t0, t1 = 0, f.shape[0]
+        labels, n = ctx.segment(t0, t1, wl.preds)
+        before = ctx.features(t0, t1, labels, wl.preds)
+        assert n >= 3
+        l1, l2 = int(before["label"][0]), int(before["label"][-1])
+        K = int(labels.numel())
+        mapping = torch.arange(K, dtype=torch.int32, device="cuda")
+        mapping[l2] = l1
+        ctx.relabel(labels, mapping)
+        after = ctx.features(t0, t1, labels, wl.preds)
+        torch.cuda.synchronize()
+        lab = labels.cpu().numpy()
+    finally:
+        ctx.close()
+    assert after.shape[0] == n - 1
+    o = orc.bin(f.shape, p, a)
+    of = orc.features(f, o["count"], a, o["key"], o["kscale"], t0, t1, lab)
+    check_features(after, of, a.shape[1])
