@@ -7,7 +7,8 @@
  * that move over the same timesteps (§3.1, "Data Representation"). The library keeps one such
  * dataset resident on one GPU and answers segmentation queries over it:
  *
- *   msf_load_timesteps    copy the field and point samples to the device (§3.1)
+ *   msf_load_timesteps    copy the field and point samples to the device (§3.1); with
+ *                         msf_load_timesteps_mr the points may have their own time grid (§3.4)
  *   msf_bin_particles     the §3.1 preprocessing index: voxel of every point sample, and per
  *                         (voxel, timestep) the sample count and attribute aggregates
  *   msf_segment           combined field + point membership criterion (§3.2: variables chosen
@@ -175,6 +176,25 @@ int msf_set_stream(msf_ctx* ctx, void* stream);
 int msf_load_timesteps(msf_ctx* ctx, int nx, int ny, int nz, int T, const float* field,
                        int64_t P, int A, const float* pos, const float* attr, int ptr_kind);
 
+/* The same with point samples on their own time grid (§3.4: point and field data need not
+ * share a temporal resolution; §4.1: the particles of the combustion case are saved far more
+ * often than the field). Tp point steps; pos [Tp][3][P] and attr [Tp][A][P] as above; field_step
+ * (host, [Tp]) gives the field step each point step falls in: non-decreasing, inside [0, T) (a
+ * field step may hold several point steps, one, or none). field_step = NULL means Tp == T and
+ * point step j falls in field step j, which is msf_load_timesteps. Such a dataset changes three
+ * definitions: a voxel's count and attribute aggregates at field step t take every point sample
+ * of the point steps that fall in t; a trajectory link joins (key[j][p], field_step[j]) and
+ * (key[j+1][p], field_step[j+1]) for consecutive point steps (so it may join two voxels of one
+ * field step); a feature's point samples are all samples in its voxel-timesteps. The fixed-point
+ * scale counts all P * Tp samples. msf_cluster, the point labels of msf_cluster_stats and the
+ * voxel label space of msf_split_trajectories take one point step per field step and return
+ * MSF_ERR_INVALID_ARG on such a dataset. Errors: those of msf_load_timesteps; INVALID_ARG (a
+ * map that decreases or leaves [0, T), Tp < 1 with a map, Tp != T without), TOO_LARGE
+ * (Tp > 65535). */
+int msf_load_timesteps_mr(msf_ctx* ctx, int nx, int ny, int nz, int T, const float* field,
+                          int64_t P, int A, int Tp, const float* pos, const float* attr,
+                          const int32_t* field_step, int ptr_kind);
+
 /* The §3.1 preprocessing index over all T timesteps: key[t][p] = voxel of sample (p,t)
  * ((z*ny + y)*nx + x, or -1 when the position is non-finite or outside [0,n) in any axis),
  * count[t][v], the fixed-point sums and the fp32 means of every attribute (see
@@ -183,7 +203,8 @@ int msf_load_timesteps(msf_ctx* ctx, int nx, int ny, int nz, int T, const float*
  * OUT_OF_MEMORY, CUDA. */
 int msf_bin_particles(msf_ctx* ctx, unsigned flags, msf_bin_stats* stats);
 
-/* Copy the binning results out (each pointer may be NULL): key [T][P] int32,
+/* Copy the binning results out (each pointer may be NULL): key [T][P] int32 ([Tp][P] for a
+ * dataset loaded with its own point steps),
  * count [T][nz][ny][nx] int32, mean [A][T][nz][ny][nx] fp32, sumq [A][T][nz][ny][nx] int64
  * (only when binned with MSF_BIN_KEEP_SUMQ, else INVALID_ARG). ptr_kind applies to all four.
  * Synchronises the stream. */

@@ -8,7 +8,8 @@ The arithmetic lives in ``msf_oracle.c`` (plain C, fp64), built with gcc into
 ``liborc.so`` beside it; this module only marshals numpy arrays through ctypes.
 
 Functions and the passages they follow:
-  ``bin``       - §3.1 preprocessing index (point samples -> field voxels, per-voxel aggregates)
+  ``bin``       - §3.1 preprocessing index (point samples -> field voxels, per-voxel aggregates;
+                  point steps may fall several to a field step, §3.4 and §4.1)
   ``segment``   - combined field+point membership (§3.2, choice of variables) and 4D connected
                   components by breadth-first flood fill (connectivity is this library's
                   definition; the paper's clustering imposes none, §3.3)
@@ -94,6 +95,15 @@ def _load():
             i64 = ctypes.c_int64
             lib.oracle_bin.argtypes = [ctypes.c_int] * 4 + [i64, ctypes.c_int] + [P] * 8
             lib.oracle_bin.restype = ctypes.c_int
+            lib.oracle_bin_mr.argtypes = ([ctypes.c_int] * 5 + [P, i64, ctypes.c_int] + [P] * 8)
+            lib.oracle_bin_mr.restype = ctypes.c_int
+            lib.oracle_segment_mr.argtypes = ([ctypes.c_int] * 4 + [P, P, P, i64, ctypes.c_int, P, P,
+                                              ctypes.POINTER(_Criteria), P, P])
+            lib.oracle_segment_mr.restype = ctypes.c_int
+            lib.oracle_features_mr.argtypes = ([ctypes.c_int] * 4 + [P, P, i64, ctypes.c_int,
+                                               ctypes.c_int, P, P, P, P, ctypes.c_int,
+                                               ctypes.c_int, P, i64, ctypes.POINTER(_FeatOut), P])
+            lib.oracle_features_mr.restype = ctypes.c_int
             lib.oracle_segment.argtypes = [ctypes.c_int] * 4 + [P, P, P, i64, P,
                                                                 ctypes.POINTER(_Criteria), P, P]
             lib.oracle_segment.restype = ctypes.c_int
@@ -132,24 +142,40 @@ def scale_exponent(max_abs: float, n_samples: int) -> int:
     return int(_load().oracle_scale_exponent(float(max_abs), int(n_samples)))
 
 
-def bin(field_shape, pos, attr, keep_sumq=True):
-    """§3.1 preprocessing index. ``field_shape`` = (T, NZ, NY, NX); ``pos`` [T][3][P] fp32;
-    ``attr`` [T][A][P] fp32. Returns dict key, count, sumq, mean, kscale, outside."""
+def _fstep_array(fstep, Tp):
+    if fstep is None:
+        return None
+    f = np.ascontiguousarray(fstep, dtype=np.int32).reshape(-1)
+    if f.size != Tp:
+        raise ValueError("fstep must have one entry per point step")
+    return f
+
+
+def bin(field_shape, pos, attr, keep_sumq=True, fstep=None):
+    """§3.1 preprocessing index. ``field_shape`` = (T, NZ, NY, NX); ``pos`` [Tp][3][P] fp32;
+    ``attr`` [Tp][A][P] fp32; ``fstep`` [Tp] the field step of every point step
+    (non-decreasing; None: Tp == T, one point step per field step). Returns dict key [Tp][P],
+    count, sumq, mean ([A][T][...]), kscale, outside [Tp]."""
     T, nz, ny, nx = (int(s) for s in field_shape)
     pos = np.ascontiguousarray(pos, dtype=np.float32)
     P = pos.shape[2]
+    Tp = pos.shape[0]
     attr = np.ascontiguousarray(attr, dtype=np.float32)
-    if attr.ndim != 3 or attr.shape[0] != T or attr.shape[2] != P:
-        raise ValueError("attr must be [T][A][P]")
+    if attr.ndim != 3 or attr.shape[0] != Tp or attr.shape[2] != P:
+        raise ValueError("attr must be [Tp][A][P]")
+    fs = _fstep_array(fstep, Tp)
+    if fs is None and Tp != T:
+        raise ValueError("pos must be [T][3][P] without a step map")
     A = attr.shape[1]
-    key = np.empty((T, P), np.int32)
+    key = np.empty((Tp, P), np.int32)
     count = np.empty((T, nz, ny, nx), np.int32)
     sumq = np.empty((A, T, nz, ny, nx), np.int64) if keep_sumq else None
     mean = np.empty((A, T, nz, ny, nx), np.float32)
     kscale = np.zeros(max(A, 1), np.int32)
-    outside = np.empty(T, np.int64)
-    rc = _load().oracle_bin(nx, ny, nz, T, P, A, _ptr(pos), _ptr(attr), _ptr(key), _ptr(count),
-                            _ptr(sumq), _ptr(mean), _ptr(kscale), _ptr(outside))
+    outside = np.empty(Tp, np.int64)
+    rc = _load().oracle_bin_mr(nx, ny, nz, T, Tp, _ptr(fs), P, A, _ptr(pos), _ptr(attr),
+                               _ptr(key), _ptr(count), _ptr(sumq), _ptr(mean), _ptr(kscale),
+                               _ptr(outside))
     if rc != 0:
         raise RuntimeError(f"oracle_bin failed: {rc}")
     return dict(key=key, count=count, sumq=sumq, mean=mean, kscale=kscale[:A], outside=outside)
@@ -166,31 +192,38 @@ def make_criteria(t0, t1, preds=(), edges=EDGE_ALL):
     return c
 
 
-def segment(field, count, mean, key, t0, t1, preds=(), edges=EDGE_ALL):
-    """Criterion + 4D connected components. Returns (labels [Tw][NZ][NY][NX] int32, n_features)."""
+def segment(field, count, mean, key, t0, t1, preds=(), edges=EDGE_ALL, fstep=None):
+    """Criterion + 4D connected components. key [Tp][P]; fstep [Tp] maps point steps to field
+    steps (None: one per field step). Returns (labels [Tw][NZ][NY][NX] int32, n_features)."""
     field = np.ascontiguousarray(field, dtype=np.float32)
     T, nz, ny, nx = field.shape
     count = np.ascontiguousarray(count, dtype=np.int32)
     mean = np.ascontiguousarray(mean, dtype=np.float32)
     key = np.ascontiguousarray(key, dtype=np.int32)
     P = key.shape[1] if key.ndim == 2 else 0
+    Tp = key.shape[0] if key.ndim == 2 else T
+    fs = _fstep_array(fstep, Tp) if P else None
     crit = make_criteria(t0, t1, preds, edges)
     labels = np.empty((max(t1 - t0, 0), nz, ny, nx), np.int32)
     nf = ctypes.c_int64(0)
-    rc = _load().oracle_segment(nx, ny, nz, T, _ptr(field), _ptr(count), _ptr(mean), P,
-                                _ptr(key), ctypes.byref(crit), _ptr(labels), ctypes.byref(nf))
+    rc = _load().oracle_segment_mr(nx, ny, nz, T, _ptr(field), _ptr(count), _ptr(mean), P,
+                                   Tp if fs is not None else T, _ptr(fs), _ptr(key),
+                                   ctypes.byref(crit), _ptr(labels), ctypes.byref(nf))
     if rc != 0:
         raise RuntimeError(f"oracle_segment failed: {rc}")
     return labels, int(nf.value)
 
 
-def features(field, count, attr, key, kscale, t0, t1, labels):
-    """Per-feature statistics, ascending label order. Returns a dict of numpy arrays."""
+def features(field, count, attr, key, kscale, t0, t1, labels, fstep=None):
+    """Per-feature statistics, ascending label order. attr [Tp][A][P], key [Tp][P], fstep as
+    in ``segment``. Returns a dict of numpy arrays."""
     field = np.ascontiguousarray(field, dtype=np.float32)
     T, nz, ny, nx = field.shape
     count = np.ascontiguousarray(count, dtype=np.int32)
     key = np.ascontiguousarray(key, dtype=np.int32)
     P = key.shape[1] if key.ndim == 2 else 0
+    Tp = key.shape[0] if key.ndim == 2 else T
+    fs = _fstep_array(fstep, Tp) if P else None
     attr = np.ascontiguousarray(attr, dtype=np.float32)
     A = attr.shape[1] if attr.ndim == 3 else 0
     kscale = np.ascontiguousarray(np.asarray(kscale, dtype=np.int32).reshape(-1))
@@ -208,9 +241,10 @@ def features(field, count, attr, key, kscale, t0, t1, labels):
         mean_attr=np.empty((nf, Af), np.float64), std_attr=np.empty((nf, Af), np.float64))
     fo = _FeatOut(*[_ptr(out[n]) for n, _ in _FeatOut._fields_])
     n_out = ctypes.c_int64(0)
-    rc = _load().oracle_features(nx, ny, nz, T, _ptr(field), _ptr(count), P, A, _ptr(attr),
-                                 _ptr(key), _ptr(kscale), int(t0), int(t1), _ptr(labels), nf,
-                                 ctypes.byref(fo), ctypes.byref(n_out))
+    rc = _load().oracle_features_mr(nx, ny, nz, T, _ptr(field), _ptr(count), P, A,
+                                    Tp if fs is not None else T, _ptr(fs), _ptr(attr),
+                                    _ptr(key), _ptr(kscale), int(t0), int(t1), _ptr(labels), nf,
+                                    ctypes.byref(fo), ctypes.byref(n_out))
     if rc != 0:
         raise RuntimeError(f"oracle_features failed: {rc}")
     for n in ("sumq", "mean_attr", "std_attr"):
@@ -218,11 +252,11 @@ def features(field, count, attr, key, kscale, t0, t1, labels):
     return out
 
 
-def run_all(field, pos, attr, t0, t1, preds, edges=EDGE_ALL):
+def run_all(field, pos, attr, t0, t1, preds, edges=EDGE_ALL, fstep=None):
     """bin -> segment -> features in one call (the whole path, CPU)."""
-    b = bin(field.shape, pos, attr, keep_sumq=False)
-    labels, nf = segment(field, b["count"], b["mean"], b["key"], t0, t1, preds, edges)
-    f = features(field, b["count"], attr, b["key"], b["kscale"], t0, t1, labels)
+    b = bin(field.shape, pos, attr, keep_sumq=False, fstep=fstep)
+    labels, nf = segment(field, b["count"], b["mean"], b["key"], t0, t1, preds, edges, fstep)
+    f = features(field, b["count"], attr, b["key"], b["kscale"], t0, t1, labels, fstep)
     return b, labels, nf, f
 
 

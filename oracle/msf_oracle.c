@@ -8,8 +8,11 @@
  *
  * Data model (paper §3.1, "Data Representation"):
  *   field  F(t) = {x_f, y_f, z_f, v_f(t)} on a regular grid:   field[t][z][y][x], fp32
- *   points P(t) = {x_p(t), y_p(t), z_p(t), v_p(t)}, one id per trajectory:
- *          pos[t][c][p] (c = x,y,z, grid units), attr[t][a][p], fp32
+ *   points P(j) = {x_p(j), y_p(j), z_p(j), v_p(j)}, one id per trajectory:
+ *          pos[j][c][p] (c = x,y,z, grid units), attr[j][a][p], fp32
+ * Point and field samples may come at different temporal resolutions (§3.4; §4.1: the
+ * particles are saved far more often than the field). Point step j falls in field step
+ * fstep[j] (non-decreasing); fstep == NULL means one point step per field step (j = t).
  *
  * Steps:
  *   oracle_bin       - the §3.1 preprocessing index: which voxel each point sample lies in,
@@ -101,18 +104,33 @@ static float orc_mean(int64_t sumq, int32_t count, int k) {
   return m;
 }
 
-/* Binning of all T timesteps.
- *   key[t][p]        voxel of sample (p,t) or -1
- *   count[t][v]      number of samples in voxel v at t
+/* Field step of point step j (identity without a map). */
+static int orc_fstep(const int32_t* fstep, int j) { return fstep ? fstep[j] : j; }
+
+/* A map of point steps to field steps must be non-decreasing and inside [0, T). */
+static int orc_check_fstep(const int32_t* fstep, int Tp, int T) {
+  for (int j = 0; j < Tp; ++j) {
+    int t = orc_fstep(fstep, j);
+    if (t < 0 || t >= T) return 0;
+    if (j > 0 && t < orc_fstep(fstep, j - 1)) return 0;
+  }
+  return 1;
+}
+
+/* Binning of all point steps into the field steps they fall in.
+ *   key[j][p]        voxel of sample (p,j) or -1
+ *   count[t][v]      number of samples in voxel v over the point steps of field step t
  *   sumq[a][t][v]    sum of the quantised attribute a over those samples (int64, exact)
  *   mean[a][t][v]    fp32 mean: ((float)sumq / (float)count) * 2^-k_a in IEEE fp32, NaN if empty
- *   kscale[a]        the exponent k_a used
- *   outside[t]       samples with key -1 at t
- * sumq may be NULL. */
-int oracle_bin(int nx, int ny, int nz, int T, int64_t P, int A, const float* pos,
-               const float* attr, int32_t* key, int32_t* count, int64_t* sumq, float* mean,
-               int32_t* kscale, int64_t* outside) {
-  if (nx <= 0 || ny <= 0 || nz <= 0 || T <= 0 || P < 0 || A < 0) return ORC_ERR_ARG;
+ *   kscale[a]        the exponent k_a used (over all P * Tp samples)
+ *   outside[j]       samples with key -1 at point step j
+ * sumq may be NULL. Tp point steps, fstep as above (NULL: Tp == T, j = t). */
+int oracle_bin_mr(int nx, int ny, int nz, int T, int Tp, const int32_t* fstep, int64_t P, int A,
+                  const float* pos, const float* attr, int32_t* key, int32_t* count,
+                  int64_t* sumq, float* mean, int32_t* kscale, int64_t* outside) {
+  if (nx <= 0 || ny <= 0 || nz <= 0 || T <= 0 || Tp < 0 || P < 0 || A < 0) return ORC_ERR_ARG;
+  if (!fstep && Tp != T) return ORC_ERR_ARG;
+  if (!orc_check_fstep(fstep, Tp, T)) return ORC_ERR_ARG;
   const int64_t V = (int64_t)nx * ny * nz;
   int64_t* acc = NULL;
   if (A > 0) {
@@ -121,33 +139,36 @@ int oracle_bin(int nx, int ny, int nz, int T, int64_t P, int A, const float* pos
   }
   for (int a = 0; a < A; ++a) {
     double m = 0.0;
-    for (int t = 0; t < T; ++t)
+    for (int j = 0; j < Tp; ++j)
       for (int64_t p = 0; p < P; ++p) {
-        float v = attr[((int64_t)t * A + a) * P + p];
+        float v = attr[((int64_t)j * A + a) * P + p];
         if (isfinite(v) && fabs((double)v) > m) m = fabs((double)v);
       }
-    kscale[a] = oracle_scale_exponent(m, P * (int64_t)T);
+    kscale[a] = oracle_scale_exponent(m, P * (int64_t)Tp);
   }
+  int j = 0; /* point steps are visited in order, each field step taking its own */
   for (int t = 0; t < T; ++t) {
     int32_t* cnt = count + (int64_t)t * V;
     memset(cnt, 0, (size_t)V * sizeof(int32_t));
     if (A > 0) memset(acc, 0, (size_t)(A * V) * sizeof(int64_t));
-    int64_t out = 0;
-    const float* px = pos + ((int64_t)t * 3 + 0) * P;
-    const float* py = pos + ((int64_t)t * 3 + 1) * P;
-    const float* pz = pos + ((int64_t)t * 3 + 2) * P;
-    for (int64_t p = 0; p < P; ++p) {
-      int32_t v = orc_voxel_of(px[p], py[p], pz[p], nx, ny, nz);
-      key[(int64_t)t * P + p] = v;
-      if (v < 0) {
-        ++out;
-        continue;
+    for (; j < Tp && orc_fstep(fstep, j) == t; ++j) {
+      int64_t out = 0;
+      const float* px = pos + ((int64_t)j * 3 + 0) * P;
+      const float* py = pos + ((int64_t)j * 3 + 1) * P;
+      const float* pz = pos + ((int64_t)j * 3 + 2) * P;
+      for (int64_t p = 0; p < P; ++p) {
+        int32_t v = orc_voxel_of(px[p], py[p], pz[p], nx, ny, nz);
+        key[(int64_t)j * P + p] = v;
+        if (v < 0) {
+          ++out;
+          continue;
+        }
+        cnt[v] += 1;
+        for (int a = 0; a < A; ++a)
+          acc[(int64_t)a * V + v] += orc_quantise(attr[((int64_t)j * A + a) * P + p], kscale[a]);
       }
-      cnt[v] += 1;
-      for (int a = 0; a < A; ++a)
-        acc[(int64_t)a * V + v] += orc_quantise(attr[((int64_t)t * A + a) * P + p], kscale[a]);
+      outside[j] = out;
     }
-    outside[t] = out;
     for (int a = 0; a < A; ++a) {
       for (int64_t v = 0; v < V; ++v) {
         int64_t s = acc[(int64_t)a * V + v];
@@ -158,6 +179,14 @@ int oracle_bin(int nx, int ny, int nz, int T, int64_t P, int A, const float* pos
   }
   free(acc);
   return ORC_OK;
+}
+
+/* Binning with one point step per field step. */
+int oracle_bin(int nx, int ny, int nz, int T, int64_t P, int A, const float* pos,
+               const float* attr, int32_t* key, int32_t* count, int64_t* sumq, float* mean,
+               int32_t* kscale, int64_t* outside) {
+  return oracle_bin_mr(nx, ny, nz, T, T, NULL, P, A, pos, attr, key, count, sumq, mean, kscale,
+                       outside);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -211,12 +240,16 @@ static int orc_active(const orc_criteria* q, int t, int64_t v, int64_t V, int T,
  * whose vertices are the active voxel-timesteps and whose edges are
  *   spatial  : (x,y,z,t)-(x',y',z',t) with max(|dx|,|dy|,|dz|) = 1, no wrap (26 neighbours)
  *   temporal : (x,y,z,t)-(x,y,z,t+1)
- *   traj     : (key[t][p], t)-(key[t+1][p], t+1) for each point p and t, t+1 in the window
+ *   traj     : (key[j][p], fstep[j])-(key[j+1][p], fstep[j+1]) for each point p and consecutive
+ *              point steps j, j+1 whose field steps both lie in the window (with one point step
+ *              per field step: (key[t][p], t)-(key[t+1][p], t+1))
  * each class enabled by its bit in q->edges. Returns the number of components in *n_feat. */
-int oracle_segment(int nx, int ny, int nz, int T, const float* field, const int32_t* count,
-                   const float* mean, int64_t P, const int32_t* key, const orc_criteria* q,
-                   int32_t* labels, int64_t* n_feat) {
+int oracle_segment_mr(int nx, int ny, int nz, int T, const float* field, const int32_t* count,
+                      const float* mean, int64_t P, int Tp, const int32_t* fstep,
+                      const int32_t* key, const orc_criteria* q, int32_t* labels,
+                      int64_t* n_feat) {
   if (nx <= 0 || ny <= 0 || nz <= 0 || T <= 0) return ORC_ERR_ARG;
+  if (P > 0 && ((!fstep && Tp != T) || !orc_check_fstep(fstep, Tp, T))) return ORC_ERR_ARG;
   if (q->t0 < 0 || q->t1 > T || q->t1 < q->t0 || q->n_pred < 0 || q->n_pred > 4)
     return ORC_ERR_ARG;
   const int64_t V = (int64_t)nx * ny * nz;
@@ -235,20 +268,23 @@ int oracle_segment(int nx, int ny, int nz, int T, const float* field, const int3
       act[(int64_t)tw * V + v] = (uint8_t)orc_active(q, q->t0 + tw, v, V, T, field, count, mean);
 
   /* Trajectory links as an explicit adjacency list (both directions). */
-  int use_traj = (q->edges & ORC_EDGE_TRAJ) && P > 0 && Tw > 1;
+  int use_traj = (q->edges & ORC_EDGE_TRAJ) && P > 0 && Tp > 1;
   if (use_traj) {
     off = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
     if (!off) goto oom;
-    for (int tw = 0; tw + 1 < Tw; ++tw)
+    for (int j = 0; j + 1 < Tp; ++j) {
+      int ta = orc_fstep(fstep, j), tb = orc_fstep(fstep, j + 1);
+      if (ta < q->t0 || tb >= q->t1) continue;
       for (int64_t p = 0; p < P; ++p) {
-        int32_t a = key[(int64_t)(q->t0 + tw) * P + p];
-        int32_t b = key[(int64_t)(q->t0 + tw + 1) * P + p];
+        int32_t a = key[(int64_t)j * P + p];
+        int32_t b = key[(int64_t)(j + 1) * P + p];
         if (a < 0 || b < 0) continue;
-        int64_t u = (int64_t)tw * V + a, w = (int64_t)(tw + 1) * V + b;
+        int64_t u = (int64_t)(ta - q->t0) * V + a, w = (int64_t)(tb - q->t0) * V + b;
         if (!act[u] || !act[w]) continue;
         off[u + 1]++;
         off[w + 1]++;
       }
+    }
     for (int64_t i = 0; i < N; ++i) off[i + 1] += off[i];
     adj = (int32_t*)malloc((size_t)(off[N] > 0 ? off[N] : 1) * sizeof(int32_t));
     int64_t* fill = (int64_t*)malloc((size_t)N * sizeof(int64_t));
@@ -257,16 +293,19 @@ int oracle_segment(int nx, int ny, int nz, int T, const float* field, const int3
       goto oom;
     }
     memcpy(fill, off, (size_t)N * sizeof(int64_t));
-    for (int tw = 0; tw + 1 < Tw; ++tw)
+    for (int j = 0; j + 1 < Tp; ++j) {
+      int ta = orc_fstep(fstep, j), tb = orc_fstep(fstep, j + 1);
+      if (ta < q->t0 || tb >= q->t1) continue;
       for (int64_t p = 0; p < P; ++p) {
-        int32_t a = key[(int64_t)(q->t0 + tw) * P + p];
-        int32_t b = key[(int64_t)(q->t0 + tw + 1) * P + p];
+        int32_t a = key[(int64_t)j * P + p];
+        int32_t b = key[(int64_t)(j + 1) * P + p];
         if (a < 0 || b < 0) continue;
-        int64_t u = (int64_t)tw * V + a, w = (int64_t)(tw + 1) * V + b;
+        int64_t u = (int64_t)(ta - q->t0) * V + a, w = (int64_t)(tb - q->t0) * V + b;
         if (!act[u] || !act[w]) continue;
         adj[fill[u]++] = (int32_t)w;
         adj[fill[w]++] = (int32_t)u;
       }
+    }
     free(fill);
   }
 
@@ -334,6 +373,14 @@ oom:
   return ORC_ERR_MEM;
 }
 
+/* Labelling with one point step per field step. */
+int oracle_segment(int nx, int ny, int nz, int T, const float* field, const int32_t* count,
+                   const float* mean, int64_t P, const int32_t* key, const orc_criteria* q,
+                   int32_t* labels, int64_t* n_feat) {
+  return oracle_segment_mr(nx, ny, nz, T, field, count, mean, P, T, NULL, key, q, labels,
+                           n_feat);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Per-feature statistics (§3.2.2 cluster-centre averages, §3.4 extent and deviations)         */
 /* ------------------------------------------------------------------------------------------ */
@@ -364,11 +411,12 @@ int oracle_count_labels(int64_t N, const int32_t* labels) {
   return (int)nf;
 }
 
-int oracle_features(int nx, int ny, int nz, int T, const float* field, const int32_t* count,
-                    int64_t P, int A, const float* attr, const int32_t* key,
-                    const int32_t* kscale, int t0, int t1, const int32_t* labels, int64_t cap,
-                    orc_features_out* o, int64_t* n_out) {
+int oracle_features_mr(int nx, int ny, int nz, int T, const float* field, const int32_t* count,
+                       int64_t P, int A, int Tp, const int32_t* fstep, const float* attr,
+                       const int32_t* key, const int32_t* kscale, int t0, int t1,
+                       const int32_t* labels, int64_t cap, orc_features_out* o, int64_t* n_out) {
   if (nx <= 0 || ny <= 0 || nz <= 0 || T <= 0 || t0 < 0 || t1 > T || t1 < t0) return ORC_ERR_ARG;
+  if (P > 0 && ((!fstep && Tp != T) || !orc_check_fstep(fstep, Tp, T))) return ORC_ERR_ARG;
   const int64_t V = (int64_t)nx * ny * nz;
   const int Tw = t1 - t0;
   const int64_t N = V * Tw;
@@ -428,21 +476,25 @@ int oracle_features(int nx, int ny, int nz, int T, const float* field, const int
       sc[f * 4 + j] += c[j];
     }
   }
-  /* Point part: every sample whose voxel-timestep belongs to the feature. */
-  for (int tw = 0; tw < Tw; ++tw)
+  /* Point part: every sample whose voxel-timestep belongs to the feature (point step j lies in
+   * field step fstep[j]). */
+  for (int j = 0; j < (P > 0 ? Tp : 0); ++j) {
+    int t = orc_fstep(fstep, j);
+    if (t < t0 || t >= t1) continue;
     for (int64_t p = 0; p < P; ++p) {
-      int32_t v = key[(int64_t)(t0 + tw) * P + p];
+      int32_t v = key[(int64_t)j * P + p];
       if (v < 0) continue;
-      int32_t l = labels[(int64_t)tw * V + v];
+      int32_t l = labels[(int64_t)(t - t0) * V + v];
       if (l < 0) continue;
       int64_t f = fid[l];
       for (int a = 0; a < A; ++a) {
-        float av = attr[((int64_t)(t0 + tw) * A + a) * P + p];
+        float av = attr[((int64_t)j * A + a) * P + p];
         o->sumq[f * A + a] += orc_quantise(av, kscale[a]);
         double d = isfinite(av) ? (double)av : 0.0;
         sa2[f * A + a] += d * d;
       }
     }
+  }
   for (int64_t f = 0; f < nf; ++f) {
     double n = (double)o->n_vox[f];
     double m = o->sum_field[f] / n;
@@ -468,4 +520,13 @@ int oracle_features(int nx, int ny, int nz, int T, const float* field, const int
   free(sc);
   free(sa2);
   return ORC_OK;
+}
+
+/* Feature statistics with one point step per field step. */
+int oracle_features(int nx, int ny, int nz, int T, const float* field, const int32_t* count,
+                    int64_t P, int A, const float* attr, const int32_t* key,
+                    const int32_t* kscale, int t0, int t1, const int32_t* labels, int64_t cap,
+                    orc_features_out* o, int64_t* n_out) {
+  return oracle_features_mr(nx, ny, nz, T, field, count, P, A, T, NULL, attr, key, kscale, t0,
+                            t1, labels, cap, o, n_out);
 }

@@ -13,11 +13,15 @@
 //   k_bin_keys     one thread per 4 samples of one timestep: key[t][p], and per block a shared-
 //                  memory histogram of buckets merged into hist[t][bucket]
 //   scan           offsets[t][bucket] = exclusive prefix of hist
-//   k_bin_place    one CTA per 4096 samples of one timestep: the block's keys and attributes
-//                  arrive in shared memory by bulk asynchronous copy while the block reads its
-//                  slot ranges; the block sorts its samples by bucket in shared memory and writes
-//                  (voxel-in-bucket, attributes) records run by run; also the largest finite |v|
-//                  per attribute
+//   k_bin_place    one CTA per 4096 samples of one timestep: the block's keys, the same
+//                  points' keys at the next step and their attributes arrive in shared memory by
+//                  bulk asynchronous copy while the block reads its slot ranges; the block sorts
+//                  its samples by bucket in shared memory and writes (voxel, next voxel,
+//                  attributes) records run by run; also the largest finite |v| per attribute
+//
+// The records stay with the dataset as its point index: every in-domain sample, grouped by
+// timestep and within a step by bucket, so that the passes that look up something per sample
+// (trajectory joins, point statistics) touch the voxels of one bucket at a time.
 //   k_bin_reduce   one CTA per (bucket, timestep): its records arrive by bulk copy while the
 //                  accumulators are cleared; counts and fixed-point sums in shared memory, means
 //                  of the non-empty voxels into shared memory, then one vector store pass of
@@ -28,6 +32,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "msf_internal.cuh"
 
@@ -42,6 +47,9 @@ constexpr int kHistSmem = 8192;        // buckets counted in shared memory (else
 
 struct BinArgs {
   int nx, ny, nz, A, T;
+  int Tp;                       // point steps; point step j falls in field step fstep[j]
+  const int32_t* fstep;         // [Tp]
+  const int32_t* pj0;           // [T + 1] first point step of each field step
   int64_t V, P;
   int logR, nb;                 // bucket = voxel >> logR; nb buckets
   int nblk;                     // sample blocks per timestep
@@ -51,10 +59,11 @@ struct BinArgs {
   const float* pos;             // [T][3][P]
   const float* attr;            // [T][A][P]
   int32_t* key;                 // [T][P]
-  uint32_t* hist;               // [T][nb][nblk] samples per (bucket, block)
+  uint32_t* hist;               // samples per (field step, bucket, point step, block)
   uint32_t* offs;               // exclusive prefix of hist (slot ranges)
   uint32_t* cursor;             // running fill positions (global-histogram fallback)
-  uint32_t* rec_v;              // [P*T] voxel within bucket (+4 slack for rounded bulk copies)
+  uint32_t* rec_v;              // [P*T] voxel of the sample (+4 slack for rounded bulk copies)
+  int32_t* rec_n;               // [P*T] voxel of the same point at the next step, -1 if none
   float* rec_a;                 // [A][NRp] attribute values (+4 slack)
   unsigned* err;                // bounded waits that gave up
   long long wait_cycles;        // limit of those waits (SM cycles)
@@ -131,15 +140,25 @@ __device__ __forceinline__ float div_count(float x, int c) {
   return __fdiv_rn(x, __int2float_rn(c));
 }
 
+// Histogram slot of (point step j, bucket, block): ordered by field step, then bucket, then the
+// field step's point steps, then block, so that one exclusive scan lays the records out by
+// (field step, bucket), every point step and block of the field step taking its own range.
+// With one point step per field step this is (t * nb + bucket) * nblk + blk.
+__device__ __forceinline__ int64_t hist_index(const BinArgs& b, int j, int bucket, int blk) {
+  const int t = __ldg(b.fstep + j);
+  const int p0 = __ldg(b.pj0 + t), r = __ldg(b.pj0 + t + 1) - p0;
+  return (((int64_t)p0 * b.nb + (int64_t)bucket * r) + (j - p0)) * b.nblk + blk;
+}
+
 // ---------------------------------------------------------------------------------------------
 // pass 1: keys and the per-block bucket histograms
 // ---------------------------------------------------------------------------------------------
-// Block blk of timestep t owns samples [blk * chunk, (blk + 1) * chunk). Its histogram goes to
-// hist[(t * nb + bucket) * nblk + blk], so one exclusive scan yields every block's slot range.
+// Block blk of point step j owns samples [blk * chunk, (blk + 1) * chunk). Its histogram goes to
+// hist[hist_index(j, bucket, blk)], so one exclusive scan yields every block's slot range.
 template <bool SMEM>
 __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArgs b) {
   __shared__ uint32_t s_hist[SMEM ? kHistSmem : 1];
-  const int t = blockIdx.y, blk = blockIdx.x;
+  const int t = blockIdx.y, blk = blockIdx.x;  // t: the point step
   if (SMEM) {
     for (int i = threadIdx.x; i < b.nb; i += 256) s_hist[i] = 0u;
     __syncthreads();
@@ -169,7 +188,7 @@ __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArg
       } else if (SMEM) {
         atomicAdd(s_hist + (k >> b.logR), 1u);
       } else {
-        atomicAdd(b.hist + ((int64_t)t * b.nb + (k >> b.logR)) * b.nblk + blk, 1u);
+        atomicAdd(b.hist + hist_index(b, t, k >> b.logR, blk), 1u);
       }
     }
   }
@@ -177,8 +196,7 @@ __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArg
   if ((threadIdx.x & 31) == 0 && tot) atomicAdd(b.outside + t, (unsigned long long)tot);
   if (SMEM) {
     __syncthreads();
-    for (int i = threadIdx.x; i < b.nb; i += 256)
-      b.hist[((int64_t)t * b.nb + i) * b.nblk + blk] = s_hist[i];
+    for (int i = threadIdx.x; i < b.nb; i += 256) b.hist[hist_index(b, t, i, blk)] = s_hist[i];
   }
 }
 
@@ -198,15 +216,16 @@ template <int A>
 __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
   extern __shared__ __align__(16) uint32_t s_place[];
   int32_t* s_key = reinterpret_cast<int32_t*>(s_place);                   // [kPlaceStage]
-  float* s_att = reinterpret_cast<float*>(s_place + kPlaceStage);          // [A][kPlaceStage]
-  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + (1 + A) * kPlaceStage);  // [chunk]
-  uint32_t* s_delta = s_place + (1 + A) * kPlaceStage + kPlaceChunk / 2;   // [nb] slot - local
+  int32_t* s_keyn = reinterpret_cast<int32_t*>(s_place + kPlaceStage);    // [kPlaceStage]
+  float* s_att = reinterpret_cast<float*>(s_place + 2 * kPlaceStage);      // [A][kPlaceStage]
+  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + (2 + A) * kPlaceStage);  // [chunk]
+  uint32_t* s_delta = s_place + (2 + A) * kPlaceStage + kPlaceChunk / 2;   // [nb] slot - local
   uint32_t* s_lpos = s_delta + b.nb;                                       // [nb] fill cursor
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned s_max[A > 0 ? A : 1];
   __shared__ int s_warp[kBinNT / 32];
   __shared__ int s_n;
-  const int t = blockIdx.y, blk = blockIdx.x;
+  const int t = blockIdx.y, blk = blockIdx.x;  // t: the point step
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t pbeg = (int64_t)blk * b.chunk;
   const int n = (int)min((int64_t)b.chunk, b.P - pbeg);
@@ -214,9 +233,15 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
   // that the aligned-down copy brings in)
   const int64_t ek = (int64_t)t * b.P + pbeg;
   const int hk = (int)(ek & 3);
+  const bool has_next = t + 1 < b.Tp;
+  // a next point step in the same field step is flagged in bit 31 of the next voxel
+  const uint32_t same = has_next && __ldg(b.fstep + t + 1) == __ldg(b.fstep + t) ? 0x80000000u : 0u;
+  const int64_t ekn = ek + b.P;  // the same points at the next step
+  const int hkn = (int)(ekn & 3);
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     uint32_t tx = (uint32_t)(((hk + n + 3) & ~3) * 4);
+    if (has_next) tx += (uint32_t)(((hkn + n + 3) & ~3) * 4);
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int64_t ea = ((int64_t)t * A + a) * b.P + pbeg;
@@ -224,6 +249,8 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
     }
     mbar_expect_tx(&s_bar, tx);
     bulk_g2s(s_key, b.key + (ek - hk), (uint32_t)(((hk + n + 3) & ~3) * 4), &s_bar);
+    if (has_next)
+      bulk_g2s(s_keyn, b.key + (ekn - hkn), (uint32_t)(((hkn + n + 3) & ~3) * 4), &s_bar);
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int64_t ea = ((int64_t)t * A + a) * b.P + pbeg;
@@ -234,8 +261,9 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
   }
   // the block's slot ranges and bucket counts (overlapping the copies)
   for (int i = threadIdx.x; i < b.nb; i += kBinNT) {
-    s_delta[i] = b.offs[((int64_t)t * b.nb + i) * b.nblk + blk];
-    s_lpos[i] = b.hist[((int64_t)t * b.nb + i) * b.nblk + blk];  // counts, scanned below
+    const int64_t h = hist_index(b, t, i, blk);
+    s_delta[i] = b.offs[h];
+    s_lpos[i] = b.hist[h];  // counts, scanned below
   }
   if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
@@ -296,12 +324,13 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
   __syncthreads();
   // runs out: local position j of bucket bk goes to slot s_delta[bk] + j
   const int nr = s_n;
-  const uint32_t vmask = (1u << b.logR) - 1u;
   for (int j = threadIdx.x; j < nr; j += kBinNT) {
     const int i = s_inv[j];
     const int32_t k = s_key[hk + i];
     const uint32_t slot = s_delta[k >> b.logR] + (uint32_t)j;
-    b.rec_v[slot] = (uint32_t)k & vmask;
+    b.rec_v[slot] = (uint32_t)k;
+    const int32_t kn = has_next ? s_keyn[hkn + i] : -1;
+    b.rec_n[slot] = kn < 0 ? -1 : (int32_t)((uint32_t)kn | same);
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int ha = (int)((((int64_t)t * A + a) * b.P + pbeg) & 3);
@@ -315,7 +344,9 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
 template <int A>
 __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant__ BinArgs b) {
   __shared__ unsigned s_max[A > 0 ? A : 1];
-  const int t = blockIdx.y, blk = blockIdx.x;
+  const int t = blockIdx.y, blk = blockIdx.x;  // t: the point step
+  const bool has_next = t + 1 < b.Tp;
+  const uint32_t same = has_next && __ldg(b.fstep + t + 1) == __ldg(b.fstep + t) ? 0x80000000u : 0u;
   if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
   const int64_t pbeg = (int64_t)blk * b.chunk;
@@ -333,8 +364,10 @@ __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant_
     }
     if (k < 0) continue;
     const int bk = k >> b.logR;
-    const uint32_t slot = atomicAdd(b.cursor + ((int64_t)t * b.nb + bk) * b.nblk + blk, 1u);
-    b.rec_v[slot] = (uint32_t)k & ((1u << b.logR) - 1u);
+    const uint32_t slot = atomicAdd(b.cursor + hist_index(b, t, bk, blk), 1u);
+    b.rec_v[slot] = (uint32_t)k;
+    const int32_t kn = has_next ? __ldcs(b.key + (int64_t)(t + 1) * b.P + p) : -1;
+    b.rec_n[slot] = kn < 0 ? -1 : (int32_t)((uint32_t)kn | same);
 #pragma unroll
     for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * b.NRp + slot] = av[a];
   }
@@ -364,14 +397,17 @@ __device__ __forceinline__ void reduce_issue(const BinArgs& b, uint32_t a0, uint
   for (int a = 0; a < A; ++a) bulk_g2s(s_sta + (size_t)a * R, b.rec_a + a * b.NRp + a0, bytes, bar);
 }
 
-// record range [r0, r1) of item row = t * nb + bucket
-__device__ __forceinline__ void item_range(const BinArgs& b, int64_t row, uint32_t nrec,
+// record range [r0, r1) of the item (field step t, bucket): the slots of its point steps
+__device__ __forceinline__ void item_range(const BinArgs& b, int t, int bucket, uint32_t nrec,
                                            uint32_t& r0, uint32_t& r1) {
   r0 = r1 = 0u;
-  if (nrec) {
-    r0 = __ldg(b.offs + row * b.nblk);
-    r1 = (row + 1 < (int64_t)b.T * b.nb) ? __ldg(b.offs + (row + 1) * b.nblk) : nrec;
-  }
+  const int p0 = __ldg(b.pj0 + t), r = __ldg(b.pj0 + t + 1) - p0;
+  if (!nrec || r == 0) return;
+  const int64_t h0 = ((int64_t)p0 * b.nb + (int64_t)bucket * r) * b.nblk;
+  const int64_t h1 = h0 + (int64_t)r * b.nblk;  // the next bucket's (or step's) first slot
+  const int64_t TB = (int64_t)b.Tp * b.nb * b.nblk;
+  r0 = __ldg(b.offs + h0);
+  r1 = h1 < TB ? __ldg(b.offs + h1) : nrec;
 }
 
 // One block per item (t, bucket). Shared memory: sums [A][R] u64, counts [R] u32 and a staging
@@ -393,11 +429,10 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_k[A > 0 ? A : 1];
   __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
-  const int bucket = blockIdx.x, t = blockIdx.y;
-  const int64_t item = (int64_t)t * b.nb + bucket;
+  const int bucket = blockIdx.x, t = blockIdx.y;  // t: the field step
   const uint32_t nrec = b.nrec ? *b.nrec : 0u;
   uint32_t r0, r1;
-  item_range(b, item, nrec, r0, r1);
+  item_range(b, t, bucket, nrec, r0, r1);
   const uint32_t s0 = r0 & ~3u, e1 = (r1 + 3u) & ~3u;
   const int npiece = r1 > r0 ? (int)((e1 - s0 + (uint32_t)R - 1) / (uint32_t)R) : 0;
   if (threadIdx.x == 0) {
@@ -405,7 +440,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
     if (npiece) reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, R, &s_bar);
   }
   if ((int)threadIdx.x < A) {
-    const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.P * b.T);
+    const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.P * b.Tp);
     s_k[threadIdx.x] = k;
     s_f1[threadIdx.x] = pow2f(-(k / 2));
     s_f2[threadIdx.x] = pow2f(-(k - k / 2));
@@ -430,7 +465,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
     for (int q = threadIdx.x; q < m; q += kBinNT) {
       const uint32_t r = a0 + (uint32_t)q;
       if (r < r0 || r >= r1) continue;  // alignment slack of the neighbouring buckets
-      const uint32_t v = s_stv[q];
+      const uint32_t v = s_stv[q] & (uint32_t)(R - 1);  // voxel within the bucket
       atomicAdd(s_cnt + v, 1u);
 #pragma unroll
       for (int a = 0; a < A; ++a)
@@ -519,24 +554,35 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
   }
 }
 
+// Step boundaries of the records: the slot range of (t, bucket 0, block 0) starts step t.
+__global__ void k_bin_steps(const __grid_constant__ BinArgs b, uint32_t* step) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > b.T) return;
+  const int j = b.pj0[t];  // first point step of field step t
+  step[t] = j < b.Tp ? b.offs[(int64_t)j * b.nb * b.nblk] : *b.nrec;
+}
+
 // Bucket width per attribute count: sums, counts and the record staging area, R * (8 + 12 A)
 // bytes, within 64 KB of dynamic shared memory (three CTAs per SM); at most 2048 voxels.
-static int bucket_log2(int A) {
+static int bucket_log2(int A, int64_t V) {
   int l = 11;
   while (l > 6 && ((size_t)1 << l) * (8 + 12 * (size_t)A) > 64 * 1024) --l;
+  // a grid with more buckets than the shared-memory histograms hold takes wider buckets (fewer
+  // reduce CTAs per SM) rather than the global-atomic placement
+  while (l < 11 && ((V + ((int64_t)1 << l) - 1) >> l) > kHistSmem) ++l;
   return l;
 }
 
 static size_t reduce_smem(int A, int logR) { return ((size_t)1 << logR) * (8 + 12 * (size_t)A); }
 
 static size_t place_smem(int A, int nb) {
-  return sizeof(uint32_t) * ((1 + (size_t)A) * kPlaceStage + kPlaceChunk / 2 + 2 * (size_t)nb);
+  return sizeof(uint32_t) * ((2 + (size_t)A) * kPlaceStage + kPlaceChunk / 2 + 2 * (size_t)nb);
 }
 
 template <int A>
 static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, bool smem) {
   cudaStream_t s = ctx->stream;
-  const dim3 gs((unsigned)b.nblk, (unsigned)b.T);
+  const dim3 gs((unsigned)b.nblk, (unsigned)b.Tp);  // (block, point step)
   if (phase == 0) {
     ScopedKernel k(ctx, "k_bin_keys");
     if (smem) k_bin_keys<true><<<gs, 256, 0, s>>>(b);
@@ -558,18 +604,19 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
     ScopedKernel k(ctx, "k_bin_reduce");
     const size_t sm = reduce_smem(A, b.logR);
     const dim3 gr((unsigned)b.nb, (unsigned)b.T);
+    // the attribute is per device and set before every launch that needs more than before
     if (keep) {
-      static bool set = false;
-      if (!set) {
-        cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        set = true;
+      static std::atomic<size_t> set{0};
+      if (sm > set.load()) {
+        cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        set.store(sm);
       }
       k_bin_reduce<A, true><<<gr, kBinNT, sm, s>>>(b);
     } else {
-      static bool set = false;
-      if (!set) {
-        cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        set = true;
+      static std::atomic<size_t> set{0};
+      if (sm > set.load()) {
+        cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        set.store(sm);
       }
       k_bin_reduce<A, false><<<gr, kBinNT, sm, s>>>(b);
     }
@@ -601,9 +648,12 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.nz = d.nz;
   b.A = d.A;
   b.T = d.T;
+  b.Tp = d.Tp;
+  b.fstep = d.fstep.as<int32_t>();
+  b.pj0 = d.pj0.as<int32_t>();
   b.V = d.V;
   b.P = d.P;
-  b.logR = bucket_log2(d.A);
+  b.logR = bucket_log2(d.A, d.V);
   b.nb = (int)((d.V + ((int64_t)1 << b.logR) - 1) >> b.logR);
   // samples per block: the shared-memory sort handles kPlaceChunk; with too many buckets for
   // shared memory the blocks grow so that the per-block histograms stay small
@@ -613,20 +663,22 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
     while ((int64_t)b.nb * ((d.P + b.chunk - 1) / b.chunk) > (1 << 22) && b.chunk < ((int64_t)1 << 30))
       b.chunk <<= 1;
   b.nblk = (int)std::max<int64_t>(1, (d.P + b.chunk - 1) / b.chunk);
-  const int64_t TB = (int64_t)d.T * b.nb * b.nblk;
-  const int64_t NR = d.P * (int64_t)d.T;
+  const int64_t TB = (int64_t)d.Tp * b.nb * b.nblk;
+  const int64_t NR = d.P * (int64_t)d.Tp;
   const int Af = d.A > 0 ? d.A : 1;
   if (NR >= ((int64_t)1 << 32) || TB >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
   MSF_TRY(S.hist.ensure(sizeof(uint32_t) * TB));
   MSF_TRY(S.offs.ensure(sizeof(uint32_t) * TB));
-  MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * TB));
+  if (!smem) MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * TB));
   const int64_t NRp = (NR + 3) & ~(int64_t)3;
-  MSF_TRY(S.rec_v.ensure(sizeof(uint32_t) * (NRp + 4)));
-  MSF_TRY(S.rec_a.ensure(sizeof(float) * (NRp * Af + 4)));
+  MSF_TRY(d.rec_v.ensure(sizeof(uint32_t) * (NRp + 4)));
+  MSF_TRY(d.rec_n.ensure(sizeof(int32_t) * (NRp + 4)));
+  MSF_TRY(d.rec_a.ensure(sizeof(float) * (NRp * Af + 4)));
+  MSF_TRY(d.rec_step.ensure(sizeof(uint32_t) * (d.T + 1)));
   MSF_TRY(S.absmax.ensure(sizeof(unsigned) * MSF_MAX_ATTR));
-  MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.T));
+  MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.Tp));
   MSF_TRY(S.total.ensure(sizeof(uint32_t) * 4));  // [0] records, [2] error word
-  MSF_TRY(d.key.ensure(sizeof(int32_t) * (d.T * d.P + 4)));  // slack for rounded bulk copies
+  MSF_TRY(d.key.ensure(sizeof(int32_t) * ((int64_t)d.Tp * d.P + 4)));  // slack: bulk copies
   MSF_TRY(d.count.ensure(sizeof(int32_t) * d.T * d.V));
   MSF_TRY(d.mean.ensure(sizeof(float) * d.T * d.V * Af));
   if (keep) MSF_TRY(d.sumq.ensure(sizeof(int64_t) * d.T * d.V * Af));
@@ -636,8 +688,9 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.hist = S.hist.as<uint32_t>();
   b.offs = S.offs.as<uint32_t>();
   b.cursor = S.cursor.as<uint32_t>();
-  b.rec_v = S.rec_v.as<uint32_t>();
-  b.rec_a = S.rec_a.as<float>();
+  b.rec_v = d.rec_v.as<uint32_t>();
+  b.rec_n = d.rec_n.as<int32_t>();
+  b.rec_a = d.rec_a.as<float>();
   b.NRp = NRp;
   b.wait_cycles = ctx->wait_cycles;
   b.err = S.total.as<uint32_t>() + 2;
@@ -648,7 +701,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.sumq = keep ? d.sumq.as<long long>() : nullptr;
   MSF_CUDA_TRY(cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * TB, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.absmax, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
-  MSF_CUDA_TRY(cudaMemsetAsync(b.outside, 0, sizeof(unsigned long long) * d.T, s));
+  MSF_CUDA_TRY(cudaMemsetAsync(b.outside, 0, sizeof(unsigned long long) * d.Tp, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), s));
   b.nrec = nullptr;
   if (d.P > 0) {
@@ -664,9 +717,20 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   }
   launch_bin_a(ctx, b, keep, 2, smem);
   MSF_CUDA_TRY(cudaGetLastError());
-  std::vector<unsigned long long> out(d.T);
+  // first record of every step (the point index's step boundaries)
+  d.rec_stride = NRp;
+  d.h_rec_step.assign(d.T + 1, 0u);
+  if (d.P > 0) {
+    k_bin_steps<<<(d.T + 1 + 255) / 256, 256, 0, s>>>(b, d.rec_step.as<uint32_t>());
+    MSF_CUDA_TRY(cudaGetLastError());
+    MSF_CUDA_TRY(cudaMemcpyAsync(d.h_rec_step.data(), d.rec_step.p, sizeof(uint32_t) * (d.T + 1),
+                                 cudaMemcpyDeviceToHost, s));
+  } else {
+    MSF_CUDA_TRY(cudaMemsetAsync(d.rec_step.p, 0, sizeof(uint32_t) * (d.T + 1), s));
+  }
+  std::vector<unsigned long long> out(d.Tp);
   unsigned hmax[MSF_MAX_ATTR] = {};
-  MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.T,
+  MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.Tp,
                                cudaMemcpyDeviceToHost, s));
   MSF_CUDA_TRY(cudaMemcpyAsync(hmax, S.absmax.p, sizeof(hmax), cudaMemcpyDeviceToHost, s));
   uint32_t herr = 0;
@@ -681,12 +745,12 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
     float m;
     memcpy(&m, &hmax[a], sizeof(float));
     d.max_abs[a] = m;
-    d.kscale[a] = scale_exponent_bits(hmax[a], d.P * (int64_t)d.T);
+    d.kscale[a] = scale_exponent_bits(hmax[a], d.P * (int64_t)d.Tp);
   }
   int64_t o = 0;
   for (auto v : out) o += (int64_t)v;
   d.out_of_domain = o;
-  d.in_domain = d.P * (int64_t)d.T - o;
+  d.in_domain = d.P * (int64_t)d.Tp - o;
   d.binned = true;
   d.has_sumq = keep;
   return MSF_OK;

@@ -10,7 +10,8 @@
 //    wrote for the same query, the bits come from the component table and the statistics from
 //    its row masks and runs (k_segment.cu) - the labels are not read back;
 //  * any labelling (generic path): k_rootbits reads the labels, k_vox reduces one warp per
-//    32-voxel row, k_pts looks up the label of every point sample of the window.
+//    32-voxel row, k_pts looks up the label of every point sample of the window (from the
+//    dataset's point records).
 // k_records turns the accumulators into msf_feature records; k_labels fills in the labels.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -30,6 +31,11 @@ struct FeatArgs {
   const int32_t* count;   // [T][V]
   const float* attr;      // [T][A][P]
   const int32_t* key;     // [T][P]
+  // the dataset's point records: voxel, attributes [A][rec_stride], first record per step
+  const uint32_t* rec_v;
+  const float* rec_a;
+  const uint32_t* rec_step;
+  int64_t rec_stride;
   uint32_t* rootbits;     // [N/32]
   uint32_t* wordrank;     // [N/32]
   uint32_t* blocksums;
@@ -212,23 +218,32 @@ __global__ void __launch_bounds__(256) k_vox(const __grid_constant__ FeatArgs a)
                  __ldg(a.count + off));
 }
 
-// Generic path: every point sample of the window.
+// Generic path: every point sample of the window, from the point records (grouped by step
+// and bucket of voxels, so a warp's label lookups fall on a few neighbouring rows). Whole warps
+// iterate together (the reduction wants every lane).
 __global__ void __launch_bounds__(256) k_pts(const __grid_constant__ FeatArgs a) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int tw = blockIdx.y;
-  const int t = a.t0 + tw;
-  int64_t fid = -1;
-  if (p < a.P) {
-    const int32_t k = __ldcs(a.key + (int64_t)t * a.P + p);
-    if (k >= 0) {
-      const int32_t lbl = __ldg(a.labels + (int64_t)tw * a.V + k);
+  const uint32_t r0 = __ldg(a.rec_step + a.t0), r1 = __ldg(a.rec_step + a.t0 + a.tw);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w0 = (int64_t)r0 + (blockIdx.x * blockDim.x + (threadIdx.x & ~31u));
+       w0 < (int64_t)r1; w0 += stride) {
+    const int64_t ii = w0 + (threadIdx.x & 31);
+    const uint32_t i = ii < (int64_t)r1 ? (uint32_t)ii : r0;
+    int64_t fid = -1;
+    if (ii < (int64_t)r1) {
+      int lo = 0, hi = a.tw - 1;  // window step of the record
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(a.rec_step + a.t0 + mid) <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      const int32_t lbl = __ldg(a.labels + (int64_t)lo * a.V + __ldcs(a.rec_v + i));
       if (lbl >= 0) {
         fid = feature_rank(a.rk, lbl);
         if (fid < 0) atomicOr(&a.counters[1], 1ull);
       }
     }
+    accumulate_samples(a.acc, fid >= 0, fid, a.rec_a + i, a.rec_stride);
   }
-  accumulate_samples(a.acc, fid >= 0, fid, a.attr + (int64_t)t * a.A * a.P + p, a.P);
 }
 
 __global__ void __launch_bounds__(256) k_records(const __grid_constant__ FeatArgs a) {
@@ -333,6 +348,10 @@ int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
   a.count = d.count.as<int32_t>();
   a.attr = d.attr.as<float>();
   a.key = d.key.as<int32_t>();
+  a.rec_v = d.rec_v.as<uint32_t>();
+  a.rec_a = d.rec_a.as<float>();
+  a.rec_step = d.rec_step.as<uint32_t>();
+  a.rec_stride = d.rec_stride;
   for (int j = 0; j < d.A; ++j) {
     a.scale[j] = ldexp(1.0, d.kscale[j]);
     a.acc.kscale[j] = d.kscale[j];
@@ -438,9 +457,12 @@ int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
       const int64_t rows = (int64_t)g.tw * d.nz * d.ny * g.nxs;
       k_vox<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(a);
     }
-    if (d.P > 0 && d.A > 0) {
+    const int64_t nrec = d.h_rec_step.empty()
+                             ? 0
+                             : (int64_t)d.h_rec_step[g.t0 + g.tw] - (int64_t)d.h_rec_step[g.t0];
+    if (nrec > 0 && d.A > 0) {
       ScopedKernel k(ctx, "k_pts");
-      dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)a.tw);
+      const unsigned grid = (unsigned)std::min<int64_t>((nrec + 255) / 256, (int64_t)ctx->sm_count * 16);
       k_pts<<<grid, 256, 0, s>>>(a);
     }
   }

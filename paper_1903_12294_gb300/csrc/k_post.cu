@@ -663,6 +663,7 @@ int msf_cluster_stats(msf_ctx* c, int32_t t0, int32_t t1, int32_t attr,
   if (use_p) {
     if (attr < 0 || attr >= d.A) return MSF_ERR_INVALID_ARG;
     if (!d.binned) return MSF_ERR_NOT_BINNED;
+    if (d.multirate) return MSF_ERR_INVALID_ARG;  // point labels are [tw][P]: one step each
   }
   if (K > (1 << 20)) return MSF_ERR_TOO_LARGE;
   const int64_t tw = t1 - t0, nf = tw * d.V, np = use_p ? tw * d.P : 0;
@@ -764,6 +765,7 @@ int msf_split_trajectories(msf_ctx* c, int32_t t0, int32_t t1, const int32_t* la
   if (t0 < 0 || t1 > d.T || t1 <= t0) return MSF_ERR_INVALID_ARG;
   const bool vox = labels_space == MSF_SPACE_VOXELS;
   if (vox && !d.binned) return MSF_ERR_NOT_BINNED;
+  if (vox && d.multirate) return MSF_ERR_INVALID_ARG;  // one point step per field step only
   const int64_t tw = t1 - t0;
   if (tw * d.P >= ((int64_t)1 << 31) || (vox && tw * d.V >= ((int64_t)1 << 31)))
     return MSF_ERR_TOO_LARGE;

@@ -336,15 +336,17 @@ void msf_destroy(msf_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   Dataset& d = c->ds;
-  for (DevBuf* b : {&d.field, &d.pos, &d.attr, &d.key, &d.count, &d.mean, &d.sumq}) b->release();
+  for (DevBuf* b : {&d.field, &d.pos, &d.attr, &d.key, &d.count, &d.mean, &d.sumq, &d.rec_v,
+                    &d.rec_n, &d.rec_a, &d.rec_step, &d.fstep, &d.pj0})
+    b->release();
   for (DevBuf* b : {&c->seg.seg, &c->seg.runcomp, &c->seg.cparent,
                     &c->seg.cminli, &c->seg.tileinfo, &c->seg.counters})
     b->release();
   for (DevBuf* b : {&c->feat.rootbits, &c->feat.wordrank, &c->feat.blocksums, &c->feat.acc,
                     &c->feat.out})
     b->release();
-  for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.rec_v, &c->bin.rec_a,
-                    &c->bin.absmax, &c->bin.outside, &c->bin.scan_tmp, &c->bin.total})
+  for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.absmax,
+                    &c->bin.outside, &c->bin.scan_tmp, &c->bin.total})
     b->release();
   c->last.cfid.release();
   c->last.pcomp.release();
@@ -373,15 +375,28 @@ int msf_set_stream(msf_ctx* c, void* stream) {
   return MSF_OK;
 }
 
-int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* field, int64_t P,
-                       int A, const float* pos, const float* attr, int ptr_kind) {
+int msf_load_timesteps_mr(msf_ctx* c, int nx, int ny, int nz, int T, const float* field,
+                          int64_t P, int A, int Tp, const float* pos, const float* attr,
+                          const int32_t* field_step, int ptr_kind) {
   if (!c || nx <= 0 || ny <= 0 || nz <= 0 || T <= 0 || P < 0 || A < 0 || !field)
     return MSF_ERR_INVALID_ARG;
   if (c->servers.load() > 0) return MSF_ERR_BUSY;
   if (ptr_kind != MSF_HOST && ptr_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
   if (A > MSF_MAX_ATTR) return MSF_ERR_INVALID_ARG;
   if (P > 0 && (!pos || (A > 0 && !attr))) return MSF_ERR_INVALID_ARG;
-  if (T > 65535) return MSF_ERR_TOO_LARGE;
+  if (T > 65535 || Tp > 65535) return MSF_ERR_TOO_LARGE;
+  // the point steps' field steps: non-decreasing, inside [0, T); none given = one per step
+  std::vector<int32_t> fs;
+  if (field_step) {
+    if (Tp < 1) return MSF_ERR_INVALID_ARG;
+    fs.assign(field_step, field_step + Tp);
+    for (int j = 0; j < Tp; ++j)
+      if (fs[j] < 0 || fs[j] >= T || (j > 0 && fs[j] < fs[j - 1])) return MSF_ERR_INVALID_ARG;
+  } else {
+    if (Tp != T) return MSF_ERR_INVALID_ARG;
+    fs.resize(T);
+    for (int j = 0; j < T; ++j) fs[j] = j;
+  }
   const int64_t V = (int64_t)nx * ny * nz;
   if (V >= ((int64_t)1 << 31) || P >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
@@ -398,11 +413,27 @@ int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* f
   d.P = P;
   d.A = A;
   d.V = V;
+  d.Tp = Tp;
+  d.h_fstep = fs;
+  d.h_pj0.assign(T + 1, 0);
+  for (int t = 0, j = 0; t <= T; ++t) {
+    while (j < Tp && fs[j] < t) ++j;
+    d.h_pj0[t] = j;
+  }
+  d.multirate = Tp != T;
+  for (int j = 0; j < Tp && !d.multirate; ++j) d.multirate = fs[j] != j;
+  MSF_TRY(d.fstep.ensure(sizeof(int32_t) * Tp));
+  MSF_TRY(d.pj0.ensure(sizeof(int32_t) * (T + 1)));
+  // (pageable host memory: the copies are staged before the calls return)
+  MSF_CUDA_TRY(cudaMemcpyAsync(d.fstep.p, d.h_fstep.data(), sizeof(int32_t) * Tp,
+                               cudaMemcpyHostToDevice, c->stream));
+  MSF_CUDA_TRY(cudaMemcpyAsync(d.pj0.p, d.h_pj0.data(), sizeof(int32_t) * (T + 1),
+                               cudaMemcpyHostToDevice, c->stream));
   // points first on the context stream; then the field on the auxiliary stream, so that
   // binning (which reads only the points) overlaps the field's copy; readers of the field
   // wait for it (ctx_field_ready)
-  MSF_TRY(copy_in(d.pos, pos, sizeof(float) * 3 * P * T, ptr_kind, c->stream));
-  MSF_TRY(copy_in(d.attr, attr, sizeof(float) * A * P * T, ptr_kind, c->stream));
+  MSF_TRY(copy_in(d.pos, pos, sizeof(float) * 3 * P * Tp, ptr_kind, c->stream));
+  MSF_TRY(copy_in(d.attr, attr, sizeof(float) * A * P * Tp, ptr_kind, c->stream));
   if (P > 0) {
     MSF_TRY(ctx_fork(c));
     if (!c->ev_field) MSF_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_field, cudaEventDisableTiming));
@@ -414,6 +445,11 @@ int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* f
   }
   d.loaded = true;
   return MSF_OK;
+}
+
+int msf_load_timesteps(msf_ctx* c, int nx, int ny, int nz, int T, const float* field, int64_t P,
+                       int A, const float* pos, const float* attr, int ptr_kind) {
+  return msf_load_timesteps_mr(c, nx, ny, nz, T, field, P, A, T, pos, attr, nullptr, ptr_kind);
 }
 
 int msf_bin_particles(msf_ctx* c, unsigned flags, msf_bin_stats* stats) {
@@ -447,7 +483,7 @@ int msf_get_bins(msf_ctx* c, int32_t* key, int32_t* count, float* mean, int64_t*
   MSF_CUDA_TRY(cudaSetDevice(c->device));
   const cudaMemcpyKind k = ptr_kind == MSF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   cudaStream_t s = c->stream;
-  if (key && d.P > 0) MSF_CUDA_TRY(cudaMemcpyAsync(key, d.key.p, sizeof(int32_t) * d.T * d.P, k, s));
+  if (key && d.P > 0) MSF_CUDA_TRY(cudaMemcpyAsync(key, d.key.p, sizeof(int32_t) * d.Tp * d.P, k, s));
   if (count) MSF_CUDA_TRY(cudaMemcpyAsync(count, d.count.p, sizeof(int32_t) * d.T * d.V, k, s));
   if (mean && d.A > 0)
     MSF_CUDA_TRY(cudaMemcpyAsync(mean, d.mean.p, sizeof(float) * d.A * d.T * d.V, k, s));
@@ -538,6 +574,7 @@ int msf_cluster(msf_ctx* c, const msf_cluster_params* prm, int32_t* field_labels
   if (d.P > 0) {
     if (prm->attr < 0 || prm->attr >= d.A) return MSF_ERR_INVALID_ARG;
     if (!d.binned) return MSF_ERR_NOT_BINNED;
+    if (d.multirate) return MSF_ERR_INVALID_ARG;  // point labels are [tw][P]: one step each
   }
   const int64_t tw = prm->t1 - prm->t0;
   const int64_t nf = tw * d.V, np = tw * d.P;

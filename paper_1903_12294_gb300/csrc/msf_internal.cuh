@@ -52,8 +52,23 @@ struct Dataset {
   int64_t P = 0;
   int64_t V = 0;
   bool loaded = false, binned = false, has_sumq = false;
-  DevBuf field, pos, attr;          // [T][V] f32, [T][3][P] f32, [T][A][P] f32
-  DevBuf key, count, mean, sumq;    // [T][P] i32, [T][V] i32, [A][T][V] f32, [A][T][V] i64
+  // Point samples may come on a finer time grid than the field (§3.4): Tp point steps, point
+  // step j falling in field step fstep[j] (non-decreasing); field step t holds point steps
+  // [pj0[t], pj0[t+1]). With one point step per field step Tp == T and multirate is false.
+  int Tp = 0;
+  bool multirate = false;
+  std::vector<int32_t> h_fstep, h_pj0;
+  DevBuf fstep, pj0;                // device copies of the two maps
+  DevBuf field, pos, attr;          // [T][V] f32, [Tp][3][P] f32, [Tp][A][P] f32
+  DevBuf key, count, mean, sumq;    // [Tp][P] i32, [T][V] i32, [A][T][V] f32, [A][T][V] i64
+  // Point index (binning's records): every in-domain sample, grouped by field step and within
+  // a step by bucket of voxels: its voxel, the voxel of the same point at the next point step
+  // (-1 when there is none; bit 31 set when that next step falls in the same field step) and
+  // its attributes ([A][rec_stride]). rec_step[t] = first record of field step t (T + 1
+  // entries, on the device and on the host).
+  DevBuf rec_v, rec_n, rec_a, rec_step;
+  std::vector<uint32_t> h_rec_step;
+  int64_t rec_stride = 0;
   int32_t kscale[MSF_MAX_ATTR] = {};
   float max_abs[MSF_MAX_ATTR] = {};
   int64_t in_domain = 0, out_of_domain = 0;
@@ -152,7 +167,7 @@ struct BatchScratch {
 };
 
 struct BinScratch {
-  DevBuf hist, offs, cursor, rec_v, rec_a, absmax, outside, scan_tmp, total;
+  DevBuf hist, offs, cursor, absmax, outside, scan_tmp, total;
 };
 
 // Scratch of the clustering (k_cluster.cu): centres, their sums and cells, label buffers for

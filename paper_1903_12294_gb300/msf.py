@@ -29,6 +29,7 @@ MSF_MAX_PRED, MSF_MAX_ATTR = 4, 8
 
 # every entry point the header declares (checked by the CPU test-suite)
 EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
+           "msf_load_timesteps_mr",
            "msf_bin_particles", "msf_get_bins", "msf_segment", "msf_extract_features",
            "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
            "msf_segment_field_noalloc", "msf_segment_batch", "msf_server_create",
@@ -145,6 +146,8 @@ def load_library(path: str = LIB_PATH):
         lib.msf_destroy.restype = None
         lib.msf_set_stream.argtypes = [P, P]
         lib.msf_load_timesteps.argtypes = [P, i32, i32, i32, i32, P, i64, i32, P, P, i32]
+        lib.msf_load_timesteps_mr.argtypes = [P, i32, i32, i32, i32, P, i64, i32, i32, P, P, P,
+                                              i32]
         lib.msf_bin_particles.argtypes = [P, u32, ctypes.POINTER(msf_bin_stats)]
         lib.msf_get_bins.argtypes = [P, P, P, P, P, i32]
         lib.msf_segment.argtypes = [P, ctypes.POINTER(msf_criteria), P, i32,
@@ -272,6 +275,24 @@ def msf_load_timesteps(ctx, field, pos, attr):
         raise ValueError("field, pos and attr must all be host or all device")
     _check(load_library().msf_load_timesteps(ctx, nx, ny, nz, T, fp, P, A, pp, ap, k),
            "msf_load_timesteps")
+
+
+def msf_load_timesteps_mr(ctx, field, pos, attr, field_step):
+    """field [T][nz][ny][nx] fp32; pos [Tp][3][P], attr [Tp][A][P] fp32 on their own time grid;
+    field_step [Tp] (host sequence) the field step of each point step (non-decreasing)."""
+    import numpy as np
+    T, nz, ny, nx = field.shape
+    P = pos.shape[2] if pos is not None else 0
+    Tp = pos.shape[0] if pos is not None else len(field_step)
+    A = attr.shape[1] if attr is not None else 0
+    fp, k = _ptr_kind(field)
+    pp, kp = _ptr_kind(pos)
+    ap, ka = _ptr_kind(attr)
+    if P and (kp != k or (A and ka != k)):
+        raise ValueError("field, pos and attr must all be host or all device")
+    fs = np.ascontiguousarray(np.asarray(field_step, dtype=np.int32).reshape(-1))
+    _check(load_library().msf_load_timesteps_mr(ctx, nx, ny, nz, T, fp, P, A, int(Tp), pp, ap,
+                                                fs.ctypes.data, k), "msf_load_timesteps_mr")
 
 
 def msf_bin_particles(ctx, flags: int = 0) -> msf_bin_stats:
@@ -598,11 +619,17 @@ class Context:
     def set_stream(self, stream):
         msf_set_stream(self.h, stream)
 
-    def load(self, field, pos, attr):
-        msf_load_timesteps(self.h, field, pos, attr)
+    def load(self, field, pos, attr, field_step=None):
+        """field_step: the field step of each point step when the points have their own time
+        grid (pos [Tp][3][P]); None for one point step per field step."""
+        if field_step is None:
+            msf_load_timesteps(self.h, field, pos, attr)
+        else:
+            msf_load_timesteps_mr(self.h, field, pos, attr, field_step)
         self.shape = tuple(field.shape)
         self.P = pos.shape[2] if pos is not None else 0
         self.A = attr.shape[1] if attr is not None else 0
+        self.Tp = pos.shape[0] if pos is not None else self.shape[0]
 
     def bin(self, keep_sumq=False):
         return msf_bin_particles(self.h, MSF_BIN_KEEP_SUMQ if keep_sumq else 0)
@@ -610,7 +637,7 @@ class Context:
     def bins(self, device="cpu", sumq=False):
         import torch
         T, nz, ny, nx = self.shape
-        key = torch.empty((T, self.P), dtype=torch.int32, device=device)
+        key = torch.empty((getattr(self, "Tp", T), self.P), dtype=torch.int32, device=device)
         count = torch.empty((T, nz, ny, nx), dtype=torch.int32, device=device)
         mean = torch.empty((self.A, T, nz, ny, nx), dtype=torch.float32, device=device)
         sq = torch.empty((self.A, T, nz, ny, nx), dtype=torch.int64, device=device) \

@@ -54,6 +54,9 @@ class Workload:
     edges: int = EDGE_ALL
     queries: list = dc_field(default_factory=list)  # batched / served: [(t0, t1, preds, edges)]
     attr_names: tuple = ()
+    # point samples on their own time grid: pos/attr are [Tp][...] and point step j falls in
+    # field step field_step[j] (None: one point step per field step)
+    field_step: list = None
 
     @property
     def shape(self):
@@ -67,7 +70,7 @@ class Workload:
     def to(self, device):
         return Workload(self.name, self.field.to(device), self.pos.to(device),
                         self.attr.to(device), self.t0, self.t1, list(self.preds), self.edges,
-                        list(self.queries), self.attr_names)
+                        list(self.queries), self.attr_names, self.field_step)
 
     def numpy(self):
         return (self.field.cpu().numpy(), self.pos.cpu().numpy(), self.attr.cpu().numpy())
@@ -251,6 +254,31 @@ def tiny(device="cpu", n=32, T=8, P=20000, seed=SEED_BASE + 1):
     attr = spd[:, None, :].contiguous()
     preds = [(SRC_FIELD, 0, OP_GT, 0.4, 0.0), (SRC_COUNT, 0, OP_GE, 2.0, 0.0)]
     return Workload("tiny", f, pos, attr, 0, T, preds, EDGE_ALL, attr_names=("speed",))
+
+
+def multirate(device="cpu", n=32, T=8, r=4, P=20000, seed=SEED_BASE + 6, field_step=None):
+    """Points saved more often than the field (§4.1): the tiny workload's drifting blobs over T
+    field steps, and particles in the same vortex flow sampled r times per field step (Tp = r T
+    point steps, 2 voxel lengths of time per field step, so a point crosses voxels between the
+    point steps of one field step). ``field_step`` overrides the even map (any non-decreasing
+    map of len(field_step) point steps into [0, T))."""
+    rng = _rng(seed)
+    box = (n, n, n)
+    nb = 6
+    c0 = rng.uniform(6.0 / 32 * n, 26.0 / 32 * n, (nb, 3))
+    d = rng.normal(size=(nb, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    f = _blob_field(T, n, n, n, c0, d * 1.0, [3.0] * nb, [1.0] * nb, device)
+    f += 0.05 * torch.randn(f.shape, generator=_tgen(seed, device), device=device)
+    fs = list(field_step) if field_step is not None else [t for t in range(T) for _ in range(r)]
+    Tp = len(fs)
+    x0 = torch.rand((3, P), generator=_tgen(seed + 7, device), device=device) * n
+    vel = _Vortices(rng, box, device=device)
+    pos, spd = _advect(x0, vel, Tp, 2.0 * T / Tp, box, device)
+    attr = torch.stack([spd, pos[:, 2] / n], dim=1).contiguous()
+    preds = [(SRC_FIELD, 0, OP_GT, 0.4, 0.0), (SRC_COUNT, 0, OP_GE, 2.0, 0.0)]
+    return Workload("multirate", f, pos, attr, 0, T, preds, EDGE_ALL,
+                    attr_names=("speed", "height"), field_step=fs)
 
 
 def mid(device="cpu", n=128, T=32, P=1 << 20, seed=SEED_BASE + 2, n_blobs=40):
