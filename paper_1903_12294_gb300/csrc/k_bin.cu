@@ -13,15 +13,14 @@
 //   k_bin_keys     one thread per 4 samples of one timestep: key[t][p], and per block a shared-
 //                  memory histogram of buckets merged into hist[t][bucket]
 //   scan           offsets[t][bucket] = exclusive prefix of hist
-//   k_bin_place    one CTA per 4096 samples of one timestep: the block's keys, the same
-//                  points' keys at the next step and their attributes arrive in shared memory by
-//                  bulk asynchronous copy while the block reads its slot ranges; the block sorts
-//                  its samples by bucket in shared memory and writes (voxel, next voxel,
-//                  attributes) records run by run; also the largest finite |v| per attribute
+//   k_bin_place    one CTA per 4096 samples of one point step: the block's keys and attributes
+//                  arrive in shared memory by bulk asynchronous copy while the block reads its
+//                  slot ranges; the block sorts its samples by bucket in shared memory and writes
+//                  (voxel, attributes) records run by run; also the largest finite |v| per
+//                  attribute
 //
-// The records stay with the dataset as its point index: every in-domain sample, grouped by
-// timestep and within a step by bucket, so that the passes that look up something per sample
-// (trajectory joins, point statistics) touch the voxels of one bucket at a time.
+// Point samples may come on a finer time grid than the field (point step j falls in field step
+// fstep[j]); the records of all point steps of a field step go to that step's buckets.
 //   k_bin_reduce   one CTA per (bucket, timestep): its records arrive by bulk copy while the
 //                  accumulators are cleared; counts and fixed-point sums in shared memory, means
 //                  of the non-empty voxels into shared memory, then one vector store pass of
@@ -62,8 +61,7 @@ struct BinArgs {
   uint32_t* hist;               // samples per (field step, bucket, point step, block)
   uint32_t* offs;               // exclusive prefix of hist (slot ranges)
   uint32_t* cursor;             // running fill positions (global-histogram fallback)
-  uint32_t* rec_v;              // [P*T] voxel of the sample (+4 slack for rounded bulk copies)
-  int32_t* rec_n;               // [P*T] voxel of the same point at the next step, -1 if none
+  uint32_t* rec_v;              // [P*Tp] voxel of the sample (+4 slack for rounded bulk copies)
   float* rec_a;                 // [A][NRp] attribute values (+4 slack)
   unsigned* err;                // bounded waits that gave up
   long long wait_cycles;        // limit of those waits (SM cycles)
@@ -216,10 +214,9 @@ template <int A>
 __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
   extern __shared__ __align__(16) uint32_t s_place[];
   int32_t* s_key = reinterpret_cast<int32_t*>(s_place);                   // [kPlaceStage]
-  int32_t* s_keyn = reinterpret_cast<int32_t*>(s_place + kPlaceStage);    // [kPlaceStage]
-  float* s_att = reinterpret_cast<float*>(s_place + 2 * kPlaceStage);      // [A][kPlaceStage]
-  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + (2 + A) * kPlaceStage);  // [chunk]
-  uint32_t* s_delta = s_place + (2 + A) * kPlaceStage + kPlaceChunk / 2;   // [nb] slot - local
+  float* s_att = reinterpret_cast<float*>(s_place + kPlaceStage);          // [A][kPlaceStage]
+  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + (1 + A) * kPlaceStage);  // [chunk]
+  uint32_t* s_delta = s_place + (1 + A) * kPlaceStage + kPlaceChunk / 2;   // [nb] slot - local
   uint32_t* s_lpos = s_delta + b.nb;                                       // [nb] fill cursor
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned s_max[A > 0 ? A : 1];
@@ -233,15 +230,9 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
   // that the aligned-down copy brings in)
   const int64_t ek = (int64_t)t * b.P + pbeg;
   const int hk = (int)(ek & 3);
-  const bool has_next = t + 1 < b.Tp;
-  // a next point step in the same field step is flagged in bit 31 of the next voxel
-  const uint32_t same = has_next && __ldg(b.fstep + t + 1) == __ldg(b.fstep + t) ? 0x80000000u : 0u;
-  const int64_t ekn = ek + b.P;  // the same points at the next step
-  const int hkn = (int)(ekn & 3);
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     uint32_t tx = (uint32_t)(((hk + n + 3) & ~3) * 4);
-    if (has_next) tx += (uint32_t)(((hkn + n + 3) & ~3) * 4);
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int64_t ea = ((int64_t)t * A + a) * b.P + pbeg;
@@ -249,8 +240,6 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
     }
     mbar_expect_tx(&s_bar, tx);
     bulk_g2s(s_key, b.key + (ek - hk), (uint32_t)(((hk + n + 3) & ~3) * 4), &s_bar);
-    if (has_next)
-      bulk_g2s(s_keyn, b.key + (ekn - hkn), (uint32_t)(((hkn + n + 3) & ~3) * 4), &s_bar);
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int64_t ea = ((int64_t)t * A + a) * b.P + pbeg;
@@ -329,8 +318,6 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
     const int32_t k = s_key[hk + i];
     const uint32_t slot = s_delta[k >> b.logR] + (uint32_t)j;
     b.rec_v[slot] = (uint32_t)k;
-    const int32_t kn = has_next ? s_keyn[hkn + i] : -1;
-    b.rec_n[slot] = kn < 0 ? -1 : (int32_t)((uint32_t)kn | same);
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int ha = (int)((((int64_t)t * A + a) * b.P + pbeg) & 3);
@@ -345,8 +332,6 @@ template <int A>
 __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant__ BinArgs b) {
   __shared__ unsigned s_max[A > 0 ? A : 1];
   const int t = blockIdx.y, blk = blockIdx.x;  // t: the point step
-  const bool has_next = t + 1 < b.Tp;
-  const uint32_t same = has_next && __ldg(b.fstep + t + 1) == __ldg(b.fstep + t) ? 0x80000000u : 0u;
   if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
   const int64_t pbeg = (int64_t)blk * b.chunk;
@@ -366,8 +351,6 @@ __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant_
     const int bk = k >> b.logR;
     const uint32_t slot = atomicAdd(b.cursor + hist_index(b, t, bk, blk), 1u);
     b.rec_v[slot] = (uint32_t)k;
-    const int32_t kn = has_next ? __ldcs(b.key + (int64_t)(t + 1) * b.P + p) : -1;
-    b.rec_n[slot] = kn < 0 ? -1 : (int32_t)((uint32_t)kn | same);
 #pragma unroll
     for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * b.NRp + slot] = av[a];
   }
@@ -554,14 +537,6 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
   }
 }
 
-// Step boundaries of the records: the slot range of (t, bucket 0, block 0) starts step t.
-__global__ void k_bin_steps(const __grid_constant__ BinArgs b, uint32_t* step) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t > b.T) return;
-  const int j = b.pj0[t];  // first point step of field step t
-  step[t] = j < b.Tp ? b.offs[(int64_t)j * b.nb * b.nblk] : *b.nrec;
-}
-
 // Bucket width per attribute count: sums, counts and the record staging area, R * (8 + 12 A)
 // bytes, within 64 KB of dynamic shared memory (three CTAs per SM); at most 2048 voxels.
 static int bucket_log2(int A, int64_t V) {
@@ -576,7 +551,7 @@ static int bucket_log2(int A, int64_t V) {
 static size_t reduce_smem(int A, int logR) { return ((size_t)1 << logR) * (8 + 12 * (size_t)A); }
 
 static size_t place_smem(int A, int nb) {
-  return sizeof(uint32_t) * ((2 + (size_t)A) * kPlaceStage + kPlaceChunk / 2 + 2 * (size_t)nb);
+  return sizeof(uint32_t) * ((1 + (size_t)A) * kPlaceStage + kPlaceChunk / 2 + 2 * (size_t)nb);
 }
 
 template <int A>
@@ -671,10 +646,8 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_TRY(S.offs.ensure(sizeof(uint32_t) * TB));
   if (!smem) MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * TB));
   const int64_t NRp = (NR + 3) & ~(int64_t)3;
-  MSF_TRY(d.rec_v.ensure(sizeof(uint32_t) * (NRp + 4)));
-  MSF_TRY(d.rec_n.ensure(sizeof(int32_t) * (NRp + 4)));
-  MSF_TRY(d.rec_a.ensure(sizeof(float) * (NRp * Af + 4)));
-  MSF_TRY(d.rec_step.ensure(sizeof(uint32_t) * (d.T + 1)));
+  MSF_TRY(S.rec_v.ensure(sizeof(uint32_t) * (NRp + 4)));
+  MSF_TRY(S.rec_a.ensure(sizeof(float) * (NRp * Af + 4)));
   MSF_TRY(S.absmax.ensure(sizeof(unsigned) * MSF_MAX_ATTR));
   MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.Tp));
   MSF_TRY(S.total.ensure(sizeof(uint32_t) * 4));  // [0] records, [2] error word
@@ -688,9 +661,8 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.hist = S.hist.as<uint32_t>();
   b.offs = S.offs.as<uint32_t>();
   b.cursor = S.cursor.as<uint32_t>();
-  b.rec_v = d.rec_v.as<uint32_t>();
-  b.rec_n = d.rec_n.as<int32_t>();
-  b.rec_a = d.rec_a.as<float>();
+  b.rec_v = S.rec_v.as<uint32_t>();
+  b.rec_a = S.rec_a.as<float>();
   b.NRp = NRp;
   b.wait_cycles = ctx->wait_cycles;
   b.err = S.total.as<uint32_t>() + 2;
@@ -717,17 +689,6 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   }
   launch_bin_a(ctx, b, keep, 2, smem);
   MSF_CUDA_TRY(cudaGetLastError());
-  // first record of every step (the point index's step boundaries)
-  d.rec_stride = NRp;
-  d.h_rec_step.assign(d.T + 1, 0u);
-  if (d.P > 0) {
-    k_bin_steps<<<(d.T + 1 + 255) / 256, 256, 0, s>>>(b, d.rec_step.as<uint32_t>());
-    MSF_CUDA_TRY(cudaGetLastError());
-    MSF_CUDA_TRY(cudaMemcpyAsync(d.h_rec_step.data(), d.rec_step.p, sizeof(uint32_t) * (d.T + 1),
-                                 cudaMemcpyDeviceToHost, s));
-  } else {
-    MSF_CUDA_TRY(cudaMemsetAsync(d.rec_step.p, 0, sizeof(uint32_t) * (d.T + 1), s));
-  }
   std::vector<unsigned long long> out(d.Tp);
   unsigned hmax[MSF_MAX_ATTR] = {};
   MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.Tp,

@@ -10,8 +10,7 @@
 //    wrote for the same query, the bits come from the component table and the statistics from
 //    its row masks and runs (k_segment.cu) - the labels are not read back;
 //  * any labelling (generic path): k_rootbits reads the labels, k_vox reduces one warp per
-//    32-voxel row, k_pts looks up the label of every point sample of the window (from the
-//    dataset's point records).
+//    32-voxel row, k_pts looks up the label of every point sample of the window.
 // k_records turns the accumulators into msf_feature records; k_labels fills in the labels.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -31,11 +30,10 @@ struct FeatArgs {
   const int32_t* count;   // [T][V]
   const float* attr;      // [T][A][P]
   const int32_t* key;     // [T][P]
-  // the dataset's point records: voxel, attributes [A][rec_stride], first record per step
-  const uint32_t* rec_v;
-  const float* rec_a;
-  const uint32_t* rec_step;
-  int64_t rec_stride;
+  // the window's point steps [j0, j0 + nj) (key and attr rows), point step j falling in
+  // absolute field step fstep[j]
+  const int32_t* fstep;
+  int j0, nj;
   uint32_t* rootbits;     // [N/32]
   uint32_t* wordrank;     // [N/32]
   uint32_t* blocksums;
@@ -190,60 +188,64 @@ __global__ void __launch_bounds__(256) k_feat_init(const __grid_constant__ FeatA
   }
 }
 
-// Generic path: one warp per 32-voxel row (t, z, y, xs); lane = x offset.
+// Generic path: 64 consecutive 32-voxel rows (t, z, y, xs) per block, one warp per row at a time
+// (lane = x offset); the block sums into its shared-memory table and commits each feature once.
+constexpr int kVoxRows = 64;
+
 __global__ void __launch_bounds__(256) k_vox(const __grid_constant__ FeatArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  __shared__ VoxTable s_tab;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nrows = (int64_t)a.tw * a.nz * a.ny * a.nxs;
-  if (row >= nrows) return;
-  const int xs = (int)(row % a.nxs);
-  int64_t r = row / a.nxs;
-  const int y = (int)(r % a.ny);
-  r /= a.ny;
-  const int z = (int)(r % a.nz);
-  const int tw = (int)(r / a.nz);
-  const int x = xs * 32 + lane;
-  const int64_t vox = ((int64_t)z * a.ny + y) * a.nx + x;
-  int32_t lbl = -1;
-  if (x < a.nx) lbl = __ldcs(a.labels + (int64_t)tw * a.V + vox);
-  int64_t fid = -1;
-  if (lbl >= 0) {
-    fid = feature_rank(a.rk, lbl);
-    if (fid < 0) atomicOr(&a.counters[1], 1ull);
+  const int64_t rbase = (int64_t)blockIdx.x * kVoxRows;
+  s_tab.clear();
+  __syncthreads();
+  for (int k = warp; k < kVoxRows; k += 8) {
+    const int64_t row = rbase + k;
+    if (row >= nrows) break;  // warp-uniform
+    const int xs = (int)(row % a.nxs);
+    int64_t r = row / a.nxs;
+    const int y = (int)(r % a.ny);
+    r /= a.ny;
+    const int z = (int)(r % a.nz);
+    const int tw = (int)(r / a.nz);
+    const int x = xs * 32 + lane;
+    const int64_t vox = ((int64_t)z * a.ny + y) * a.nx + x;
+    int32_t lbl = -1;
+    if (x < a.nx) lbl = __ldcs(a.labels + (int64_t)tw * a.V + vox);
+    int64_t fid = -1;
+    if (lbl >= 0) {
+      fid = feature_rank(a.rk, lbl);
+      if (fid < 0) atomicOr(&a.counters[1], 1ull);
+    }
+    const unsigned act = __ballot_sync(0xFFFFFFFFu, fid >= 0);
+    if (fid >= 0) {
+      const int64_t off = (int64_t)(a.t0 + tw) * a.V + vox;
+      reduce_row(act, fid, lane, xs * 32, tw, z, y, __ldg(a.field + off), __ldg(a.count + off),
+                 [&](int64_t f, const RowSums& rs) { s_tab.add(a.acc, f, rs); });
+    }
+    __syncwarp();
   }
-  const unsigned act = __ballot_sync(0xFFFFFFFFu, fid >= 0);
-  if (fid < 0) return;
-  const int64_t off = (int64_t)(a.t0 + tw) * a.V + vox;
-  accumulate_row(a.acc, act, fid, lane, xs * 32, tw, z, y, __ldg(a.field + off),
-                 __ldg(a.count + off));
+  __syncthreads();
+  s_tab.flush(a.acc);
 }
 
-// Generic path: every point sample of the window, from the point records (grouped by step
-// and bucket of voxels, so a warp's label lookups fall on a few neighbouring rows). Whole warps
-// iterate together (the reduction wants every lane).
+// Generic path: every point sample of the window, one thread per (point step, point).
 __global__ void __launch_bounds__(256) k_pts(const __grid_constant__ FeatArgs a) {
-  const uint32_t r0 = __ldg(a.rec_step + a.t0), r1 = __ldg(a.rec_step + a.t0 + a.tw);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t w0 = (int64_t)r0 + (blockIdx.x * blockDim.x + (threadIdx.x & ~31u));
-       w0 < (int64_t)r1; w0 += stride) {
-    const int64_t ii = w0 + (threadIdx.x & 31);
-    const uint32_t i = ii < (int64_t)r1 ? (uint32_t)ii : r0;
-    int64_t fid = -1;
-    if (ii < (int64_t)r1) {
-      int lo = 0, hi = a.tw - 1;  // window step of the record
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(a.rec_step + a.t0 + mid) <= i) lo = mid;
-        else hi = mid - 1;
-      }
-      const int32_t lbl = __ldg(a.labels + (int64_t)lo * a.V + __ldcs(a.rec_v + i));
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = (int64_t)a.j0 + blockIdx.y;  // absolute point step
+  const int tw = __ldg(a.fstep + j) - a.t0;       // its window field step
+  int64_t fid = -1;
+  if (p < a.P) {
+    const int32_t k = __ldcs(a.key + j * a.P + p);
+    if (k >= 0) {
+      const int32_t lbl = __ldg(a.labels + (int64_t)tw * a.V + k);
       if (lbl >= 0) {
         fid = feature_rank(a.rk, lbl);
         if (fid < 0) atomicOr(&a.counters[1], 1ull);
       }
     }
-    accumulate_samples(a.acc, fid >= 0, fid, a.rec_a + i, a.rec_stride);
   }
+  accumulate_samples(a.acc, fid >= 0, fid, a.attr + j * a.A * a.P + p, a.P);
 }
 
 __global__ void __launch_bounds__(256) k_records(const __grid_constant__ FeatArgs a) {
@@ -348,10 +350,11 @@ int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
   a.count = d.count.as<int32_t>();
   a.attr = d.attr.as<float>();
   a.key = d.key.as<int32_t>();
-  a.rec_v = d.rec_v.as<uint32_t>();
-  a.rec_a = d.rec_a.as<float>();
-  a.rec_step = d.rec_step.as<uint32_t>();
-  a.rec_stride = d.rec_stride;
+  a.fstep = d.fstep.as<int32_t>();
+  if (!d.h_pj0.empty()) {
+    a.j0 = d.h_pj0[g.t0];
+    a.nj = d.h_pj0[g.t0 + g.tw] - a.j0;
+  }
   for (int j = 0; j < d.A; ++j) {
     a.scale[j] = ldexp(1.0, d.kscale[j]);
     a.acc.kscale[j] = d.kscale[j];
@@ -455,14 +458,11 @@ int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels,
     {
       ScopedKernel k(ctx, "k_vox");
       const int64_t rows = (int64_t)g.tw * d.nz * d.ny * g.nxs;
-      k_vox<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(a);
+      k_vox<<<(unsigned)((rows + kVoxRows - 1) / kVoxRows), 256, 0, s>>>(a);
     }
-    const int64_t nrec = d.h_rec_step.empty()
-                             ? 0
-                             : (int64_t)d.h_rec_step[g.t0 + g.tw] - (int64_t)d.h_rec_step[g.t0];
-    if (nrec > 0 && d.A > 0) {
+    if (d.P > 0 && d.A > 0 && a.nj > 0) {
       ScopedKernel k(ctx, "k_pts");
-      const unsigned grid = (unsigned)std::min<int64_t>((nrec + 255) / 256, (int64_t)ctx->sm_count * 16);
+      dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)a.nj);
       k_pts<<<grid, 256, 0, s>>>(a);
     }
   }

@@ -52,16 +52,15 @@ struct SegArgs {
   int2* tileinfo;  // (runs, components) per tile
   int32_t* labels;
   unsigned long long* counters;  // [0] features, [1] error flags
-  uint32_t* pcomp;  // component of every point record of the window (record order), kNoComp
-                    // off the members; written by the trajectory joins, read by the point
-                    // statistics (null: not kept)
+  uint32_t* pcomp;  // [nj][P] component of every point sample of the window, kNoComp off the
+                    // members; written by the trajectory joins, read by the point statistics
+                    // (null: not kept)
   int tile0;            // first tile of a tile-pass launch that covers part of the tiles
   int chunk0, chunk1;   // link chunks [chunk0, chunk1) of a join launch (chunk1 0: to the end)
-  // the dataset's point records (binning's point index): voxel, next voxel, step starts
-  const uint32_t* rec_v;
-  const int32_t* rec_n;
-  const uint32_t* rec_step;  // [T + 1] absolute
-  int lstep0, lstep1;        // window steps whose records a join launch takes
+  // the window's point steps (points may be sampled more often than the field): absolute point
+  // steps [j0, j0 + nj), point step j falling in absolute field step fstep[j]
+  const int32_t* fstep;
+  int j0, nj;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -632,56 +631,61 @@ __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) 
   return __ldg(a.runcomp + e.y + run_index(run_starts(e.x, SPATIAL), b));
 }
 
-// Window step (relative) of record i: the last step s in [s_lo, s_hi] whose first record is at
-// or before i (rec_step ascending).
-__device__ __forceinline__ int record_step(const uint32_t* rec_step, int t0, int s_lo, int s_hi,
-                                           uint32_t i) {
-  while (s_lo < s_hi) {
-    const int mid = (s_lo + s_hi + 1) >> 1;
-    if (__ldg(rec_step + t0 + mid) <= i) s_lo = mid;
-    else s_hi = mid - 1;
-  }
-  return s_lo;
-}
+// One thread per point and chunk of kLinkSteps point steps of the window: the point's voxel
+// keys at those point steps (and at the first one of the next chunk) are loaded once and turned
+// into components once, so each key serves both the link ending and the link starting there.
+// A link joins the components of consecutive point steps j, j+1 (their field steps fstep[j] and
+// fstep[j+1] may be equal when points are sampled more often than the field, or apart by more
+// than one when a field step holds no point step) when both are members. A point that stays in
+// one voxel over adjacent field steps needs no join when temporal edges are on (the temporal
+// edge joins the two voxel-timesteps already); over one field step it is one vertex.
+constexpr int kLinkSteps = 8;
 
-// Trajectory joins from the point records of window steps [s0, s1), record r0 + k by thread
-// k of `nthreads` (grid-stride). Records come grouped by step and, within a step, by bucket of
-// consecutive voxels, so neighbouring threads look up components of neighbouring rows (few
-// distinct row-table sectors per warp), and the next voxel of a point lies near its voxel. A
-// record joins its voxel-timestep to the point's next one: in the next window step, or in the
-// same step when bit 31 flags a next point step inside the same field step (points on a finer
-// time grid than the field). A join to the same voxel needs no union when temporal edges join
-// the two already, or when both ends are the same voxel-timestep. Records of the window's last
-// step join only inside that step; with `a.pcomp` every record also keeps its component.
 template <bool SPATIAL>
-__device__ __forceinline__ void links_records(const SegArgs& a, int s0, int s1, int64_t k0,
-                                              int64_t nthreads) {
-  const int t0 = a.g.t0;
-  const uint32_t r0 = __ldg(a.rec_step + t0 + s0);
-  const uint32_t r1 = __ldg(a.rec_step + t0 + s1);
-  const uint32_t base = __ldg(a.rec_step + t0);
+__device__ __forceinline__ void links_chunk(const SegArgs& a, int64_t p, int c0) {
+  constexpr int L = kLinkSteps;
   const bool temporal = (a.edges & MSF_EDGE_TEMPORAL) != 0;
-  for (int64_t ii = (int64_t)r0 + k0; ii < (int64_t)r1; ii += nthreads) {
-    const uint32_t i = (uint32_t)ii;
-    const int s = record_step(a.rec_step, t0, s0, s1 - 1, i);
-    const uint32_t va = __ldcs(a.rec_v + i);
-    const int32_t nb = __ldcs(a.rec_n + i);
-    const int64_t ca = comp_of<SPATIAL>(a, s, (int32_t)va);
-    if (a.pcomp) __stcs(a.pcomp + (i - base), ca >= 0 ? (uint32_t)ca : kNoComp);
-    if (ca < 0 || nb == -1) continue;
-    const bool same_step = nb < 0;
-    const uint32_t vb = (uint32_t)nb & 0x7FFFFFFFu;
-    if (!same_step && s + 1 >= a.g.tw) continue;
-    if (vb == va && (same_step || temporal)) continue;
-    const int64_t cb = comp_of<SPATIAL>(a, same_step ? s : s + 1, (int32_t)vb);
-    if (cb >= 0 && cb != ca) gunion(a.cparent, (uint32_t)ca, (uint32_t)cb);
+  const int nk = min(L + 1, a.nj - c0);  // keys of window point steps c0 .. c0 + nk - 1
+  int32_t key[L + 1];
+  int st[L + 1];
+  uint32_t comp[L + 1];
+#pragma unroll
+  for (int j = 0; j <= L; ++j) {
+    const int64_t pj = (int64_t)a.j0 + c0 + j;
+    key[j] = j < nk ? __ldcs(a.key + pj * a.P + p) : -1;
+    st[j] = j < nk ? __ldg(a.fstep + pj) - a.g.t0 : 0;  // window field step (uniform)
+  }
+#pragma unroll
+  for (int j = 0; j <= L; ++j) {
+    comp[j] = kNoComp;
+    if (key[j] >= 0) {
+      const int64_t cj = comp_of<SPATIAL>(a, st[j], key[j]);
+      if (cj >= 0) comp[j] = (uint32_t)cj;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const bool temporal_edge = temporal && key[j] == key[j + 1] && st[j + 1] == st[j] + 1;
+    if (comp[j] != kNoComp && comp[j + 1] != kNoComp && comp[j] != comp[j + 1] && !temporal_edge)
+      gunion(a.cparent, comp[j], comp[j + 1]);
+  }
+  if (a.pcomp) {  // each point step once: the last chunk also keeps the window's last one
+    const int nw = c0 + L >= a.nj - 1 ? nk : L;
+#pragma unroll
+    for (int j = 0; j <= L; ++j)
+      if (j < nw) __stcs(a.pcomp + (int64_t)(c0 + j) * a.P + p, comp[j]);
   }
 }
 
+// chunks [chunk0, chunk1) of the window's point steps (chunk1 0: to the end) in grid y
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_links_rec(const __grid_constant__ SegArgs a) {
-  links_records<SPATIAL>(a, a.lstep0, a.lstep1, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                         (int64_t)gridDim.x * blockDim.x);
+__global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArgs a) {
+  const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (p >= a.P) return;
+  const int nchunk = (a.nj - 1 + kLinkSteps - 1) / kLinkSteps;
+  const int c1 = a.chunk1 ? a.chunk1 : nchunk;
+  for (int c = a.chunk0 + (int)blockIdx.y; c < c1; c += gridDim.y)
+    links_chunk<SPATIAL>(a, p, c * kLinkSteps);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -701,7 +705,9 @@ __device__ __forceinline__ void flatten_body(const SegArgs& a, const int tile, i
       ++roots;
     } else {
       a.cparent[c] = r;
-      atomicMin(&a.cminli[r], __ldcg(a.cminli + c));
+      // roots are the sets' smallest ids and mostly hold the smallest index already
+      const int32_t mc = __ldcg(a.cminli + c);
+      if (mc < __ldcg(a.cminli + r)) atomicMin(&a.cminli[r], mc);
     }
   }
   if (roots) atomicAdd(&s_n, roots);
@@ -1033,29 +1039,12 @@ static int seg_args(msf_ctx* ctx, const Geometry& g, bool spatial, SegArgs* a) {
   a->tileinfo = S.tileinfo.as<int2>();
   a->counters = S.counters.as<unsigned long long>();
   const Dataset& d = ctx->ds;
-  a->rec_v = d.rec_v.as<uint32_t>();
-  a->rec_n = d.rec_n.as<int32_t>();
-  a->rec_step = d.rec_step.as<uint32_t>();
+  a->fstep = d.fstep.as<int32_t>();
+  if (!d.h_pj0.empty()) {  // the window's point steps
+    a->j0 = d.h_pj0[g.t0];
+    a->nj = d.h_pj0[g.t0 + g.tw] - a->j0;
+  }
   return MSF_OK;
-}
-
-// Records of window steps [s0, s1) (host copy of the step boundaries).
-static int64_t window_records(const msf_ctx* ctx, const Geometry& g, int s0, int s1) {
-  const std::vector<uint32_t>& rs = ctx->ds.h_rec_step;
-  if (rs.empty() || s1 <= s0) return 0;
-  return (int64_t)rs[g.t0 + s1] - (int64_t)rs[g.t0 + s0];
-}
-
-// Trajectory joins (and kept components) over the records of window steps [s0, s1).
-template <bool SP>
-static void launch_links_rec(msf_ctx* ctx, const SegArgs& a, int s0, int s1, cudaStream_t st) {
-  const int64_t n = window_records(ctx, a.g, s0, s1);
-  if (n <= 0) return;
-  SegArgs al = a;
-  al.lstep0 = s0;
-  al.lstep1 = s1;
-  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sm_count * 16);
-  k_links_rec<SP><<<grid, 256, 0, st>>>(al);
 }
 
 int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t* nfeat,
@@ -1094,17 +1083,23 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   // cross-tile joins and trajectory joins touch only the union-find and commute: by default
   // they run side by side, the trajectory pass on the auxiliary stream; the serial schedule
   // runs the trajectory pass after the cross-tile joins on the context stream; the pipelined
-  // one splits the tile pass at a time-tile row and starts the joins of the records whose step
-  // and next step both lie before it while the later tiles are formed
-  const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && (g.tw > 1 || ctx->ds.multirate);
+  // one splits the tile pass at a time-tile row and starts the link chunks whose point steps
+  // all fall in field steps before it while the later tiles are formed
+  const Dataset& ds = ctx->ds;
+  const bool traj = (crit->edges & MSF_EDGE_TRAJ) && a.P > 0 && a.nj > 1;
   const bool serial = sched & MSF_SCHED_SERIAL_JOINS;
-  int split_tiles = 0, ready_steps = 0;
+  int split_tiles = 0, ready_chunks = 0;
   if ((sched & MSF_SCHED_PIPELINE) && !serial && traj && g.tlt >= 2 && g.toff == 0) {
     const int h = g.tlt / 2;
     const int per_row = g.ntiles / g.tlt;     // tiles of one time-tile row
-    const int ready = h << g.lbt;             // window steps [0, ready) done after the first rows
-    ready_steps = std::min(ready - 1, g.tw - 1);  // records of step s join s and s + 1
-    if (ready_steps > 0) split_tiles = h * per_row;
+    const int ready = h << g.lbt;             // window field steps [0, ready) done after them
+    // chunk c takes window point steps c L .. c L + L: ready when the last of them falls in a
+    // field step before `ready`
+    const int jr = ds.h_pj0[std::min(g.t0 + ready, g.t0 + g.tw)] - a.j0;  // point steps ready
+    ready_chunks = jr - 1 - kLinkSteps >= 0 ? (jr - 1 - kLinkSteps) / kLinkSteps + 1 : 0;
+    const int nchunk_all = (a.nj - 1 + kLinkSteps - 1) / kLinkSteps;
+    ready_chunks = std::min(ready_chunks, nchunk_all);
+    if (ready_chunks > 0) split_tiles = h * per_row;
   }
   if (split_tiles > 0) {
     tiles(0, split_tiles);
@@ -1121,34 +1116,36 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   const bool keep = traj && ctx->keep_pcomp;
   ctx->keep_pcomp = false;
   if (keep) {
-    MSF_TRY(LS.pcomp.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, window_records(ctx, g, 0, g.tw))));
+    MSF_TRY(LS.pcomp.ensure(sizeof(uint32_t) * (size_t)a.P * (size_t)std::max(a.nj, 1)));
     a.pcomp = LS.pcomp.as<uint32_t>();
   }
-  // the joins take the records of window steps [s0, s1): a record links its step to the next;
-  // the last step's records join only inside their field step (points on a finer time grid)
-  // and keep their components (when kept)
-  const int last_step = (keep || ctx->ds.multirate) ? g.tw : g.tw - 1;
-  auto links = [&](cudaStream_t ls, int s0, int s1) {
+  const int nchunk = (a.nj - 1 + kLinkSteps - 1) / kLinkSteps;
+  auto links = [&](cudaStream_t ls, int c0, int c1) {  // link chunks [c0, c1)
+    if (c1 <= c0) return;
     ScopedKernel k(ctx, "k_links", ls);
-    if (spatial) launch_links_rec<true>(ctx, a, s0, s1, ls);
-    else launch_links_rec<false>(ctx, a, s0, s1, ls);
+    SegArgs al = a;
+    al.chunk0 = c0;
+    al.chunk1 = c1;
+    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min(c1 - c0, 65535));
+    if (spatial) k_links<true><<<grid, 256, 0, ls>>>(al);
+    else k_links<false><<<grid, 256, 0, ls>>>(al);
   };
   if (split_tiles > 0) {
     MSF_TRY(ctx_fork(ctx));            // after the first tile rows
-    links(ctx->aux, 0, ready_steps);
+    links(ctx->aux, 0, ready_chunks);
     tiles(split_tiles, g.ntiles - split_tiles);
     MSF_TRY(ctx_fork(ctx));            // after every tile
-    links(ctx->aux, ready_steps, last_step);
+    links(ctx->aux, ready_chunks, nchunk);
   } else if (traj && !serial) {
     MSF_TRY(ctx_fork(ctx));
-    links(ctx->aux, 0, last_step);
+    links(ctx->aux, 0, nchunk);
   }
   if ((crit->edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0) {
     ScopedKernel k(ctx, "k_hook");
     if (spatial) k_hook<true><<<g.ntiles, 256, 0, s>>>(a);
     else k_hook<false><<<g.ntiles, 256, 0, s>>>(a);
   }
-  if (traj && serial) links(s, 0, last_step);
+  if (traj && serial) links(s, 0, nchunk);
   if (traj && !serial) MSF_TRY(ctx_join(ctx));
   {
     ScopedKernel k(ctx, "k_flatten");
@@ -1243,11 +1240,13 @@ __global__ void __launch_bounds__(256) k_feat_vox(const __grid_constant__ SegArg
   __shared__ int32_t s_fid[MAXR];
   __shared__ uint32_t s_mask[kSegPerTile];
   __shared__ uint32_t s_rb[kSegPerTile];
+  __shared__ VoxTable s_tab;  // the tile's features: one commit per feature met
   const Geometry& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tile = blockIdx.x;
   const int nrun = min(a.tileinfo[tile].x, MAXR);
   if (nrun == 0) return;
+  s_tab.clear();
   const TileCoord tc = tile_coord(g, tile);
   const int BY = 1 << g.lby, BZ = 1 << g.lbz;
   const uint32_t rbase = (uint32_t)tile * (uint32_t)a.maxr;
@@ -1276,44 +1275,86 @@ __global__ void __launch_bounds__(256) k_feat_vox(const __grid_constant__ SegArg
       const int x = tc.xs * 32 + lane;
       const int64_t fid = s_fid[s_rb[sg] + run_index(run_starts(m, SPATIAL), lane)];
       const int64_t off = (int64_t)(g.t0 + tw) * g.V + ((int64_t)z * g.ny + y) * g.nx + x;
-      accumulate_row(acc, m, fid, lane, tc.xs * 32, tw, z, y, __ldg(field + off),
-                     __ldg(count + off));
+      reduce_row(m, fid, lane, tc.xs * 32, tw, z, y, __ldg(field + off), __ldg(count + off),
+                 [&](int64_t f, const RowSums& r) { s_tab.add(acc, f, r); });
     }
     __syncwarp();  // one row's warp-synchronous reduction at a time
   }
+  __syncthreads();
+  s_tab.flush(acc);
 }
 
-// Point statistics from the point records of the window, one record per thread: a sample
-// counts for the feature of the component of its voxel-timestep, if that is a member. The
-// records of a warp are consecutive, from a few neighbouring voxels, so they mostly share one
-// feature (the warp then reduces by butterfly) and their attributes are read contiguously.
+// Point statistics: one thread per point and chunk of kLinkSteps point steps of the window,
+// (point step, point) in order so that keys are read coalesced; a sample counts for the feature
+// of the component of its voxel-timestep (its point step's field step), if that is a member.
+// Each warp packs its member samples into shared memory and reduces them 32 at a time (the
+// warp-level reduction wants full warps).
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_feat_points(const __grid_constant__ SegArgs a,
-                                                     FeatAcc acc,
-                                                     const int32_t* __restrict__ cfid,
-                                                     const float* __restrict__ rec_a,
-                                                     int64_t rec_stride) {
-  const int t0 = a.g.t0;
-  const uint32_t r0 = __ldg(a.rec_step + t0), r1 = __ldg(a.rec_step + t0 + a.g.tw);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // whole warps iterate together (the reduction wants every lane)
-  for (int64_t w0 = (int64_t)r0 + (blockIdx.x * blockDim.x + (threadIdx.x & ~31u));
-       w0 < (int64_t)r1; w0 += stride) {
-    const int64_t ii = w0 + (threadIdx.x & 31);
-    const uint32_t i = ii < (int64_t)r1 ? (uint32_t)ii : r0;
-    int32_t fid = -1;
-    if (ii < (int64_t)r1) {
-      uint32_t c;
-      if (a.pcomp) {
-        c = __ldcs(a.pcomp + (i - r0));
-      } else {
-        const int s = record_step(a.rec_step, t0, 0, a.g.tw - 1, i);
-        const int64_t cc = comp_of<SPATIAL>(a, s, (int32_t)__ldcs(a.rec_v + i));
-        c = cc >= 0 ? (uint32_t)cc : kNoComp;
+__global__ void __launch_bounds__(256, 4) k_feat_points(const __grid_constant__ SegArgs a,
+                                                        FeatAcc acc,
+                                                        const int32_t* __restrict__ cfid,
+                                                        const float* __restrict__ attr) {
+  constexpr int L = kLinkSteps;
+  __shared__ int2 s_buf[8][32 * L];  // per warp: (feature, step * 32 + lane)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t pbase = (int64_t)blockIdx.x * 256 + w * 32;
+  const int64_t p = pbase + lane;
+  const bool in = p < a.P;
+  const int nj = a.nj;
+  const int nchunk = (nj + L - 1) / L;
+  for (int c = blockIdx.y; c < nchunk; c += gridDim.y) {
+    const int s0 = c * L;
+    int32_t fid[L];
+    int n = 0;
+    if (a.pcomp) {  // components kept by the trajectory joins: no lookups
+      uint32_t cp[L];
+#pragma unroll
+      for (int j = 0; j < L; ++j)
+        cp[j] = (in && s0 + j < nj) ? __ldcs(a.pcomp + (int64_t)(s0 + j) * a.P + p) : kNoComp;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        fid[j] = cp[j] != kNoComp ? __ldg(cfid + cp[j]) : -1;
+        n += fid[j] >= 0;
       }
-      if (c != kNoComp) fid = __ldg(cfid + c);
+    } else {
+      int32_t key[L];
+#pragma unroll
+      for (int j = 0; j < L; ++j)
+        key[j] = (in && s0 + j < nj) ? __ldcs(a.key + ((int64_t)a.j0 + s0 + j) * a.P + p) : -1;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        fid[j] = -1;
+        if (key[j] >= 0) {
+          const int st = __ldg(a.fstep + a.j0 + s0 + j) - a.g.t0;
+          const int64_t cj = comp_of<SPATIAL>(a, st, key[j]);
+          if (cj >= 0) fid[j] = __ldg(cfid + cj);
+        }
+        n += fid[j] >= 0;
+      }
     }
-    accumulate_samples(acc, fid >= 0, fid, rec_a + i, rec_stride);
+    // warp exclusive scan of the member counts -> packed positions
+    int x = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    int pos = x - n;
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      if (fid[j] >= 0) s_buf[w][pos++] = make_int2(fid[j], (j << 5) | lane);
+    __syncwarp();
+    for (int b = 0; b < total; b += 32) {
+      const int i = b + lane;
+      const bool ok = i < total;
+      const int2 e = ok ? s_buf[w][i] : make_int2(-1, 0);
+      const int j = e.y >> 5;
+      accumulate_samples(acc, ok, e.x,
+                         attr + (((int64_t)a.j0 + s0 + j) * acc.A) * a.P + pbase + (e.y & 31),
+                         a.P);
+    }
+    __syncwarp();
   }
 }
 
@@ -1346,16 +1387,14 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
   }
   // voxel and point statistics only add into the accumulators: the point pass runs beside the
   // voxel pass on the auxiliary stream
-  const int64_t nrec = window_records(ctx, g, 0, g.tw);
-  const bool points = nrec > 0 && d.A > 0;
+  const bool points = a.P > 0 && d.A > 0 && a.nj > 0;
   if (points) {
     MSF_TRY(ctx_fork(ctx));
     ScopedKernel k(ctx, "k_feat_points", ctx->aux);
-    const unsigned grid = (unsigned)std::min<int64_t>((nrec + 255) / 256, (int64_t)ctx->sm_count * 16);
-    if (spatial)
-      k_feat_points<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.rec_a.as<float>(), d.rec_stride);
-    else
-      k_feat_points<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.rec_a.as<float>(), d.rec_stride);
+    const int64_t nchunk = (a.nj + kLinkSteps - 1) / kLinkSteps;
+    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
+    if (spatial) k_feat_points<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
+    else k_feat_points<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
   }
   {
     ScopedKernel k(ctx, "k_feat_vox");
@@ -1582,18 +1621,17 @@ __global__ void __launch_bounds__(256, 4) k_hook_batch(const __grid_constant__ B
   hook_tile<SPATIAL>(s_args, blockIdx.x, s_set);
 }
 
-// (record block, step item) = (blockIdx.x, row0 + blockIdx.y): one window step of one query
-// per item, the step's point records strided over grid x; items in absolute-timestep order, so
-// the queries that cover a step read its records back to back (shared through L2)
+// (point block, chunk item) = (blockIdx.x, row0 + blockIdx.y); chunk items in absolute point
+// step order, so the queries that cover a step read its key rows back to back (shared
+// through L2)
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_links_batch(const __grid_constant__ BatchPlan b) {
+__global__ void __launch_bounds__(256, 4) k_links_batch(const __grid_constant__ BatchPlan b) {
   __shared__ __align__(16) SegArgs s_args;
   const int64_t item = b.row0 + blockIdx.y;
   load_args(&s_args, b.qargs + b.row_q[item]);
   __syncthreads();
-  const int s = b.row_tw[item];
-  links_records<SPATIAL>(s_args, s, s + 1, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                         (int64_t)gridDim.x * blockDim.x);
+  const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (p < s_args.P) links_chunk<SPATIAL>(s_args, p, b.row_tw[item]);
 }
 
 // query = blockIdx.y; x strides over that query's tiles
@@ -1752,9 +1790,9 @@ static int plan_group(msf_ctx* ctx, const msf_criteria* crits, BatchJob* job, Ba
     a.key = d.key.as<int32_t>();
     a.P = d.P;
     a.maxr = maxr;
-    a.rec_v = d.rec_v.as<uint32_t>();
-    a.rec_n = d.rec_n.as<int32_t>();
-    a.rec_step = d.rec_step.as<uint32_t>();
+    a.fstep = d.fstep.as<int32_t>();
+    a.j0 = d.h_pj0[c.t0];
+    a.nj = d.h_pj0[c.t1] - a.j0;
     job->scratch[gr.qs[i]] = fixed_scratch_bytes(g, spatial);
     const int k0 = c.t0 >> lbt, k1 = (c.t1 - 1) >> lbt;
     cmin = std::min(cmin, k0);
@@ -1784,26 +1822,24 @@ static int plan_group(msf_ctx* ctx, const msf_criteria* crits, BatchJob* job, Ba
     gr.k0[i] = (crits[gr.qs[i]].t0 >> lbt) - cmin;
     gr.seg_begin[i + 1] = gr.seg_begin[i] + gr.args[i].g.nseg;
     gr.tile_begin[i + 1] = gr.tile_begin[i] + gr.args[i].g.ntiles;
-    const int tw = gr.args[i].g.tw;
-    const bool traj = (gr.args[i].edges & MSF_EDGE_TRAJ) && d.P > 0 && (tw > 1 || d.multirate);
-    // the records of window step s join s and s + 1; the last step's records join only inside
-    // their field step (points on a finer time grid than the field)
-    const int nsteps = traj ? (d.multirate ? tw : tw - 1) : 0;
-    gr.row_begin[i + 1] = gr.row_begin[i] + nsteps;
+    const int nj = gr.args[i].nj;
+    const bool traj = (gr.args[i].edges & MSF_EDGE_TRAJ) && d.P > 0 && nj > 1;
+    const int nlinkc = traj ? (nj - 1 + kLinkSteps - 1) / kLinkSteps : 0;
+    gr.row_begin[i + 1] = gr.row_begin[i] + nlinkc;
   }
   if (gr.qlist.empty()) gr.qlist.push_back(0);
-  // trajectory step items (one window step of one query) sorted by absolute timestep
-  std::vector<std::pair<int, int>> rows;  // (absolute t, query)
+  // trajectory chunk items (kLinkSteps point steps each) sorted by absolute first point step
+  std::vector<std::pair<int, int>> rows;  // (absolute point step, query)
   for (int i = 0; i < nq; ++i)
     for (int64_t r = 0; r < gr.row_begin[i + 1] - gr.row_begin[i]; ++r)
-      rows.push_back({crits[gr.qs[i]].t0 + (int)r, i});
+      rows.push_back({gr.args[i].j0 + (int)r * kLinkSteps, i});
   std::stable_sort(rows.begin(), rows.end(),
                    [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
                      return x.first < y.first;
                    });
   for (auto& r : rows) {
     gr.row_q.push_back(r.second);
-    gr.row_tw.push_back(r.first - crits[gr.qs[r.second]].t0);
+    gr.row_tw.push_back(r.first - gr.args[r.second].j0);  // window point step of the chunk
   }
   if (gr.row_q.empty()) {
     gr.row_q.push_back(0);
@@ -1915,13 +1951,9 @@ static int launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b, 
   const bool side = nrows > 0 && sp.aux;
   if (side) MSF_TRY(sp.fork(s));
   const cudaStream_t ls = side ? sp.aux : s;
-  // records per step item: the largest step's, 8 per thread
-  int64_t max_step_rec = 1;
-  for (int t = 0; t < d.T && !d.h_rec_step.empty(); ++t)
-    max_step_rec = std::max<int64_t>(max_step_rec, (int64_t)d.h_rec_step[t + 1] - d.h_rec_step[t]);
   for (int64_t r0 = 0; r0 < nrows; r0 += 65535) {  // gridDim.y limit per launch
     ScopedKernel k(ctx, "k_links_batch", ls, timed);
-    const int64_t gx = (max_step_rec + 256 * 8 - 1) / (256 * 8);
+    const int64_t gx = (d.P + 255) / 256;
     dim3 grid((unsigned)std::max<int64_t>(gx, 1), (unsigned)std::min<int64_t>(65535, nrows - r0));
     BatchPlan br = b;
     br.row0 = r0;

@@ -336,8 +336,8 @@ void msf_destroy(msf_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   Dataset& d = c->ds;
-  for (DevBuf* b : {&d.field, &d.pos, &d.attr, &d.key, &d.count, &d.mean, &d.sumq, &d.rec_v,
-                    &d.rec_n, &d.rec_a, &d.rec_step, &d.fstep, &d.pj0})
+  for (DevBuf* b : {&d.field, &d.pos, &d.attr, &d.key, &d.count, &d.mean, &d.sumq, &d.fstep,
+                    &d.pj0})
     b->release();
   for (DevBuf* b : {&c->seg.seg, &c->seg.runcomp, &c->seg.cparent,
                     &c->seg.cminli, &c->seg.tileinfo, &c->seg.counters})
@@ -345,8 +345,8 @@ void msf_destroy(msf_ctx* c) {
   for (DevBuf* b : {&c->feat.rootbits, &c->feat.wordrank, &c->feat.blocksums, &c->feat.acc,
                     &c->feat.out})
     b->release();
-  for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.absmax,
-                    &c->bin.outside, &c->bin.scan_tmp, &c->bin.total})
+  for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.rec_v, &c->bin.rec_a,
+                    &c->bin.absmax, &c->bin.outside, &c->bin.scan_tmp, &c->bin.total})
     b->release();
   c->last.cfid.release();
   c->last.pcomp.release();

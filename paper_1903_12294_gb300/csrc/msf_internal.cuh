@@ -61,14 +61,6 @@ struct Dataset {
   DevBuf fstep, pj0;                // device copies of the two maps
   DevBuf field, pos, attr;          // [T][V] f32, [Tp][3][P] f32, [Tp][A][P] f32
   DevBuf key, count, mean, sumq;    // [Tp][P] i32, [T][V] i32, [A][T][V] f32, [A][T][V] i64
-  // Point index (binning's records): every in-domain sample, grouped by field step and within
-  // a step by bucket of voxels: its voxel, the voxel of the same point at the next point step
-  // (-1 when there is none; bit 31 set when that next step falls in the same field step) and
-  // its attributes ([A][rec_stride]). rec_step[t] = first record of field step t (T + 1
-  // entries, on the device and on the host).
-  DevBuf rec_v, rec_n, rec_a, rec_step;
-  std::vector<uint32_t> h_rec_step;
-  int64_t rec_stride = 0;
   int32_t kscale[MSF_MAX_ATTR] = {};
   float max_abs[MSF_MAX_ATTR] = {};
   int64_t in_domain = 0, out_of_domain = 0;
@@ -167,7 +159,7 @@ struct BatchScratch {
 };
 
 struct BinScratch {
-  DevBuf hist, offs, cursor, absmax, outside, scan_tmp, total;
+  DevBuf hist, offs, cursor, rec_v, rec_a, absmax, outside, scan_tmp, total;
 };
 
 // Scratch of the clustering (k_cluster.cu): centres, their sums and cells, label buffers for
@@ -460,24 +452,33 @@ __device__ __forceinline__ bool df_safe(float x) {
   return a == 0.f || (a >= 1.0e-18f && a <= 1.0e18f);  // squares neither overflow nor go subnormal
 }
 
+// Sums of one group of voxels (one feature) of a 32-voxel row, as its leader lane holds them.
+struct RowSums {
+  unsigned n;           // voxels
+  int sum_c;            // point samples in them
+  int sum_x;            // sum of x
+  unsigned kmin, kmax;  // order-preserving keys of the smallest and largest field value
+  double s1, s2;        // sum of field values and of their squares
+  int tw, z, y, xlo, xhi;
+};
+
 // Voxels of one 32-voxel row (fixed tw, z, y; lane = x - x0): the lanes in `act` with the same
-// feature reduce in the warp and the group's first lane commits one atomic per quantity. All
-// lanes of `act`, and only those, must call this.
-__device__ __forceinline__ void accumulate_row(const FeatAcc& acc, unsigned act, int64_t fid,
-                                               int lane, int x0, int tw, int z, int y, float f,
-                                               int c) {
+// feature reduce in the warp and the group's first lane hands the group's sums to
+// sink(fid, RowSums). All lanes of `act`, and only those, must call this.
+template <class Sink>
+__device__ __forceinline__ void reduce_row(unsigned act, int64_t fid, int lane, int x0, int tw,
+                                           int z, int y, float f, int c, Sink&& sink) {
   const unsigned grp = __match_any_sync(act, fid);
   const int x = x0 + lane;
-  const int n = __popc(grp);
-  const int sum_c = __reduce_add_sync(grp, c);
-  const int sum_x = __reduce_add_sync(grp, x);
+  RowSums r;
+  r.n = __popc(grp);
+  r.sum_c = __reduce_add_sync(grp, c);
+  r.sum_x = __reduce_add_sync(grp, x);
   const bool isnan_f = f != f;
-  const unsigned kmin = __reduce_min_sync(grp, isnan_f ? float_key(INFINITY) : float_key(f));
-  const unsigned kmax = __reduce_max_sync(grp, isnan_f ? float_key(-INFINITY) : float_key(f));
+  r.kmin = __reduce_min_sync(grp, isnan_f ? float_key(INFINITY) : float_key(f));
+  r.kmax = __reduce_max_sync(grp, isnan_f ? float_key(-INFINITY) : float_key(f));
   const int leader = __ffs(grp) - 1;
-  const bool fast = __all_sync(grp, df_safe(f));
-  double s1, s2;
-  if (fast) {
+  if (__all_sync(grp, df_safe(f))) {
     const float p = __fmul_rn(f, f), pe = __fmaf_rn(f, f, -p);  // f*f == p + pe exactly
     float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
     for (unsigned m = grp; m; m &= m - 1) {
@@ -486,46 +487,159 @@ __device__ __forceinline__ void accumulate_row(const FeatAcc& acc, unsigned act,
       df_add(h2, l2, __shfl_sync(grp, p, src));
       df_add(h2, l2, __shfl_sync(grp, pe, src));
     }
-    s1 = f2d(h1);
-    s2 = f2d(h2);
-    if (lane == leader) {
-      const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + fid;
-      atomicAdd(acc.sf + i, f2d(l1));
-      atomicAdd(acc.sf2 + i, f2d(l2));
-    }
+    r.s1 = f2d(h1) + f2d(l1);
+    r.s2 = f2d(h2) + f2d(l2);
   } else {  // non-finite or extreme values: plain fp64 (rare)
-    s1 = 0.0;
-    s2 = 0.0;
+    r.s1 = 0.0;
+    r.s2 = 0.0;
     for (unsigned m = grp; m; m &= m - 1) {
       const double v = (double)__shfl_sync(grp, f, __ffs(m) - 1);
-      s1 += v;
-      s2 += v * v;
+      r.s1 += v;
+      r.s2 += v * v;
     }
   }
   if (lane != leader) return;
+  r.tw = tw;
+  r.z = z;
+  r.y = y;
+  r.xlo = x0 + leader;
+  r.xhi = x0 + (31 - __clz(grp));
+  sink(fid, r);
+}
+
+// One group's sums into the accumulators (copy blockIdx.x % K).
+__device__ __forceinline__ void commit_row(const FeatAcc& acc, int64_t fid, const RowSums& r) {
   const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + fid;
-  atomicAdd(acc.n_vox + i, (unsigned long long)n);
-  atomicAdd(acc.n_pts + i, (unsigned long long)sum_c);
-  atomicAdd(acc.sf + i, s1);
-  atomicAdd(acc.sf2 + i, s2);
-  atomicMin(acc.fmin + i, kmin);
-  atomicMax(acc.fmax + i, kmax);
+  atomicAdd(acc.n_vox + i, (unsigned long long)r.n);
+  atomicAdd(acc.n_pts + i, (unsigned long long)r.sum_c);
+  atomicAdd(acc.sf + i, r.s1);
+  atomicAdd(acc.sf2 + i, r.s2);
+  atomicMin(acc.fmin + i, r.kmin);
+  atomicMax(acc.fmax + i, r.kmax);
   int* bmn = acc.bbmin + i * 4;
   int* bmx = acc.bbmax + i * 4;
-  atomicMin(bmn + 0, tw);
-  atomicMax(bmx + 0, tw);
-  atomicMin(bmn + 1, z);
-  atomicMax(bmx + 1, z);
-  atomicMin(bmn + 2, y);
-  atomicMax(bmx + 2, y);
-  atomicMin(bmn + 3, x0 + leader);
-  atomicMax(bmx + 3, x0 + (31 - __clz(grp)));
+  atomicMin(bmn + 0, r.tw);
+  atomicMax(bmx + 0, r.tw);
+  atomicMin(bmn + 1, r.z);
+  atomicMax(bmx + 1, r.z);
+  atomicMin(bmn + 2, r.y);
+  atomicMax(bmx + 2, r.y);
+  atomicMin(bmn + 3, r.xlo);
+  atomicMax(bmx + 3, r.xhi);
   unsigned long long* scp = acc.sc + i * 4;
-  atomicAdd(scp + 0, (unsigned long long)n * (unsigned long long)tw);
-  atomicAdd(scp + 1, (unsigned long long)n * (unsigned long long)z);
-  atomicAdd(scp + 2, (unsigned long long)n * (unsigned long long)y);
-  atomicAdd(scp + 3, (unsigned long long)sum_x);
+  atomicAdd(scp + 0, (unsigned long long)r.n * (unsigned long long)r.tw);
+  atomicAdd(scp + 1, (unsigned long long)r.n * (unsigned long long)r.z);
+  atomicAdd(scp + 2, (unsigned long long)r.n * (unsigned long long)r.y);
+  atomicAdd(scp + 3, (unsigned long long)r.sum_x);
 }
+
+// Voxels of one 32-voxel row straight into the accumulators.
+__device__ __forceinline__ void accumulate_row(const FeatAcc& acc, unsigned act, int64_t fid,
+                                               int lane, int x0, int tw, int z, int y, float f,
+                                               int c) {
+  reduce_row(act, fid, lane, x0, tw, z, y, f, c,
+             [&](int64_t g, const RowSums& r) { commit_row(acc, g, r); });
+}
+
+// ---------------------------------------------------------------------------------------------
+// block-private feature tables in shared memory
+//
+// With many small features (hundreds of thousands), the groups of a row or a warp are small and
+// their global atomics bound the statistics passes. A block first sums into a small open-
+// addressing table keyed by feature (shared-memory atomics), then commits each feature it met
+// once. A feature that finds no free slot within a few probes goes straight to the
+// accumulators. The caller clears the table, synchronises, accumulates, synchronises, flushes.
+// ---------------------------------------------------------------------------------------------
+constexpr int kTabSlots = 128;
+constexpr int kTabProbes = 16;
+constexpr long long kTabEmpty = -1ll;
+
+__device__ __forceinline__ int tab_slot(long long* key, int64_t fid) {
+  uint32_t h = (uint32_t)(((unsigned long long)fid * 0x9E3779B97F4A7C15ull) >> 57);
+#pragma unroll 1
+  for (int i = 0; i < kTabProbes; ++i) {
+    const long long old = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(key + h),
+                                               (unsigned long long)kTabEmpty,
+                                               (unsigned long long)fid);
+    if (old == kTabEmpty || old == fid) return (int)h;
+    h = (h + 1) & (kTabSlots - 1);
+  }
+  return -1;
+}
+
+struct VoxTable {
+  long long key[kTabSlots];
+  unsigned n_vox[kTabSlots];
+  unsigned long long n_pts[kTabSlots];
+  double sf[kTabSlots], sf2[kTabSlots];
+  unsigned fmin[kTabSlots], fmax[kTabSlots];
+  int bbmin[kTabSlots][4], bbmax[kTabSlots][4];
+  unsigned long long sc[kTabSlots][4];
+
+  __device__ __forceinline__ void clear() {
+    for (int i = threadIdx.x; i < kTabSlots; i += blockDim.x) {
+      key[i] = kTabEmpty;
+      n_vox[i] = 0u;
+      n_pts[i] = 0ull;
+      sf[i] = 0.0;
+      sf2[i] = 0.0;
+      fmin[i] = 0xFFFFFFFFu;
+      fmax[i] = 0u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        bbmin[i][j] = 0x7FFFFFFF;
+        bbmax[i][j] = -1;
+        sc[i][j] = 0ull;
+      }
+    }
+  }
+  // one group's sums: into its slot, or into the accumulators when the table is crowded
+  __device__ __forceinline__ void add(const FeatAcc& acc, int64_t fid, const RowSums& r) {
+    const int k = tab_slot(key, fid);
+    if (k < 0) {
+      commit_row(acc, fid, r);
+      return;
+    }
+    atomicAdd(n_vox + k, r.n);
+    atomicAdd(n_pts + k, (unsigned long long)r.sum_c);
+    atomicAdd(sf + k, r.s1);
+    atomicAdd(sf2 + k, r.s2);
+    atomicMin(fmin + k, r.kmin);
+    atomicMax(fmax + k, r.kmax);
+    atomicMin(&bbmin[k][0], r.tw);
+    atomicMax(&bbmax[k][0], r.tw);
+    atomicMin(&bbmin[k][1], r.z);
+    atomicMax(&bbmax[k][1], r.z);
+    atomicMin(&bbmin[k][2], r.y);
+    atomicMax(&bbmax[k][2], r.y);
+    atomicMin(&bbmin[k][3], r.xlo);
+    atomicMax(&bbmax[k][3], r.xhi);
+    atomicAdd(&sc[k][0], (unsigned long long)r.n * (unsigned long long)r.tw);
+    atomicAdd(&sc[k][1], (unsigned long long)r.n * (unsigned long long)r.z);
+    atomicAdd(&sc[k][2], (unsigned long long)r.n * (unsigned long long)r.y);
+    atomicAdd(&sc[k][3], (unsigned long long)r.sum_x);
+  }
+  // every feature met, once into the accumulators
+  __device__ __forceinline__ void flush(const FeatAcc& acc) {
+    for (int k = threadIdx.x; k < kTabSlots; k += blockDim.x) {
+      const long long f = key[k];
+      if (f == kTabEmpty) continue;
+      const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + f;
+      atomicAdd(acc.n_vox + i, (unsigned long long)n_vox[k]);
+      atomicAdd(acc.n_pts + i, n_pts[k]);
+      atomicAdd(acc.sf + i, sf[k]);
+      atomicAdd(acc.sf2 + i, sf2[k]);
+      atomicMin(acc.fmin + i, fmin[k]);
+      atomicMax(acc.fmax + i, fmax[k]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        atomicMin(acc.bbmin + i * 4 + j, bbmin[k][j]);
+        atomicMax(acc.bbmax + i * 4 + j, bbmax[k][j]);
+        atomicAdd(acc.sc + i * 4 + j, sc[k][j]);
+      }
+    }
+  }
+};
 
 // Point samples (one per lane in `ok`): lanes of the same feature reduce their exact
 // fixed-point attribute values and double-float squares; the group's first lane commits.
