@@ -475,9 +475,18 @@ def run_batched(dev, reps=3):
     tuning = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuning.items()}
     out = {}
     ctx.kernel_times(reset=True)
+    tuned_sched = tuning.get("sched")
+
+    def phases():  # the same batch with one launch per phase (for the per-phase split)
+        ctx.set_batch_schedule(1)
+        try:
+            return batch()
+        finally:
+            ctx.set_batch_schedule(tuned_sched)
     # the last arm is the same batch with graphs on: its warm-up runs plainly, then captures,
     # and the timed calls replay the graph
-    for name, fn in (("plain", plain), ("batched", batch), ("batched_graph", batch)):
+    for name, fn in (("plain", plain), ("batched", batch), ("batched_phases", phases),
+                     ("batched_graph", batch)):
         if name == "batched_graph":
             ctx.set_batch_graphs(True)
         for _ in range(2):
@@ -510,6 +519,7 @@ def run_batched(dev, reps=3):
     return {"workload": f"{nx}x{ny}x{nz} x {T}, {wl.pos.shape[2]} points x {wl.attr.shape[1]} "
                         f"attrs, {len(crits)} queries, T_w in 2..32, {vt} query-voxel-timesteps",
             "plain": out["plain"], "batched": out["batched"],
+            "batched_phases": out["batched_phases"],
             "batched_graph": dict(out["batched_graph"], graph_replays=replays),
             "batch_tuning": tuning,
             "speedup": round(out["plain"]["ms_per_batch"] / out["batched"]["ms_per_batch"], 2),

@@ -428,6 +428,11 @@ int msf_set_tile(msf_ctx* ctx, int by, int bz, int bt);
 #define MSF_SCHED_FUSED_CRITERION 1 /* criterion inside the tile pass (else a streaming pass) */
 #define MSF_SCHED_SERIAL_JOINS 2    /* trajectory joins after the cross-tile joins on the
                                        context stream (else side by side on two streams)     */
+#define MSF_SCHED_PERSISTENT 8      /* batched form only: every phase of a batch (tiles,
+                                       cross-tile and trajectory joins, flattening, label write)
+                                       in one persistent launch that pulls work from a device
+                                       queue, the phases of different queries overlapping; its
+                                       waits are bounded (MSF_ERR_TIMEOUT, msf_set_wait_limit) */
 #define MSF_SCHED_PIPELINE 4        /* the tile pass in two launches split at a time-tile row;
                                        the link chunks whose steps precede the split run
                                        beside the second launch (ignored with SERIAL_JOINS,
@@ -470,18 +475,21 @@ int msf_tune_clear(msf_ctx* ctx);
  * 32x16x1x16 on a 2D grid). Errors: INVALID_ARG, BUSY (a query server is attached). */
 int msf_set_batch_tile(msf_ctx* ctx, int by, int bz, int bt);
 
-/* Schedule of the batched form: MSF_SCHED_FUSED_CRITERION (the default) evaluates the criterion
- * inside the tile pass; without it the criterion of every query runs first as a streaming pass
- * (grids whose nx is a multiple of 32; others keep the fused pass). Other bits are ignored.
- * Errors: INVALID_ARG, BUSY (a query server is attached). */
+/* Schedule of the batched form: MSF_SCHED_PERSISTENT | MSF_SCHED_FUSED_CRITERION (the default)
+ * runs each batch group as one persistent launch with the criterion inside its tile items;
+ * MSF_SCHED_FUSED_CRITERION alone launches the phases one after the other with the criterion
+ * inside the tile pass; 0 runs the criterion of every query first as a streaming pass (grids
+ * whose nx is a multiple of 32; others keep the fused pass). MSF_SCHED_SERIAL_JOINS is ignored.
+ * Errors: INVALID_ARG (unknown bits), BUSY (a query server is attached). */
 int msf_set_batch_schedule(msf_ctx* ctx, int sched);
 
 /* Time msf_segment_batch on this batch (nq queries, labels as for msf_segment_batch, which
- * receive valid labels) over the tile shapes msf_autotune tries for the longest window and both
- * criterion schedules, one warm-up and `reps` timed runs each (reps < 1: 3), and keep the
- * fastest as the batched form's tile shape and schedule (msf_set_batch_tile,
- * msf_set_batch_schedule). `out` (may be NULL) receives them, their time and the fixed rule's
- * (32x8x8x4, fused). Synchronises the stream.
+ * receive valid labels) over the tile shapes msf_autotune tries for the longest window and the
+ * schedules (persistent launch; phase launches with the criterion fused or streamed), one
+ * warm-up and `reps` timed runs each (reps < 1: 3), and keep the fastest as the batched form's
+ * tile shape and schedule (msf_set_batch_tile, msf_set_batch_schedule). `out` (may be NULL)
+ * receives them, their time and the fixed rule's (32x8x8x4, persistent). Synchronises the
+ * stream.
  * Errors: those of msf_segment_batch; INVALID_ARG when no query has a window; BUSY. */
 int msf_autotune_batch(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
                        int reps, msf_tune_result* out);

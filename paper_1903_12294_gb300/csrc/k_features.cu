@@ -231,6 +231,8 @@ __global__ void __launch_bounds__(256) k_vox(const __grid_constant__ FeatArgs a)
 
 // Generic path: every point sample of the window, one thread per (point step, point).
 __global__ void __launch_bounds__(256) k_pts(const __grid_constant__ FeatArgs a) {
+  __shared__ HotCache s_hot[8];
+  hot_clear(s_hot[threadIdx.x >> 5]);
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t j = (int64_t)a.j0 + blockIdx.y;  // absolute point step
   const int tw = __ldg(a.fstep + j) - a.t0;       // its window field step
@@ -245,7 +247,9 @@ __global__ void __launch_bounds__(256) k_pts(const __grid_constant__ FeatArgs a)
       }
     }
   }
-  accumulate_samples(a.acc, fid >= 0, fid, a.attr + j * a.A * a.P + p, a.P);
+  accumulate_samples_hot(a.acc, s_hot[threadIdx.x >> 5], fid >= 0, fid,
+                         a.attr + j * a.A * a.P + p, a.P);
+  hot_flush(a.acc, s_hot[threadIdx.x >> 5]);
 }
 
 __global__ void __launch_bounds__(256) k_records(const __grid_constant__ FeatArgs a) {

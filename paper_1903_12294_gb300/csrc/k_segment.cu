@@ -66,6 +66,14 @@ struct SegArgs {
 // ---------------------------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------------------------
+// Loads of the compact segmentation (row table, run components). Between launches it is read-
+// only and may go through the read-only cache; in the fused batched launch other blocks of the
+// same launch wrote it, so its loads go to L2 (CG).
+template <bool CG, class T>
+__device__ __forceinline__ T ld_seg(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
 __device__ __forceinline__ uint32_t run_starts(uint32_t m, bool spatial) {
   // With spatial edges a run is a maximal stretch of consecutive members along x; without
   // them every member is its own unit.
@@ -520,21 +528,21 @@ __global__ void __launch_bounds__(256, 6) k_tile(const __grid_constant__ SegArgs
 // last runs of the nine rows to the left (another tile), the backward rows in y/z that lie in
 // another tile, and the row one step earlier when the segment opens a time chunk. Every join of
 // two components goes through join(c0, c1).
-template <bool SPATIAL, class J>
+template <bool SPATIAL, bool CG, class J>
 __device__ __forceinline__ void hook_seg(const SegArgs& a, int tw, int z, int y, int xs,
                                          uint32_t m, uint32_t rb, J&& join) {
   const Geometry& g = a.g;
   const uint32_t st = run_starts(m, SPATIAL);
 
   auto join_rows = [&](int64_t gs2, bool spatial_rows) {
-    const uint2 e2 = __ldg(a.seg + gs2);
+    const uint2 e2 = ld_seg<CG>(a.seg + gs2);
     const uint32_t m2 = e2.x;
     if (!m2) return;
     const uint32_t st2 = run_starts(m2, SPATIAL);
     const uint32_t rb2 = e2.y;
     row_contacts(m, m2, spatial_rows, SPATIAL, [&](int x1, int x2) {
-      const uint32_t c1 = __ldg(a.runcomp + rb + run_index(st, x1));
-      const uint32_t c2 = __ldg(a.runcomp + rb2 + run_index(st2, x2));
+      const uint32_t c1 = ld_seg<CG>(a.runcomp + rb + run_index(st, x1));
+      const uint32_t c2 = ld_seg<CG>(a.runcomp + rb2 + run_index(st2, x2));
       if (c1 != c2) join(c1, c2);
     });
   };
@@ -543,14 +551,14 @@ __device__ __forceinline__ void hook_seg(const SegArgs& a, int tw, int z, int y,
     // x-neighbour segments (always another tile): bit 0 here against bit 31 of the segment
     // to the left, for all 9 (dy, dz)
     if ((m & 1u) && xs > 0) {
-      const uint32_t c0 = __ldg(a.runcomp + rb);
+      const uint32_t c0 = ld_seg<CG>(a.runcomp + rb);
       uint32_t last = kNoComp;
       for (int k = 0; k < 9; ++k) {
         const int z2 = z + k / 3 - 1, y2 = y + k % 3 - 1;
         if (z2 < 0 || z2 >= g.nz || y2 < 0 || y2 >= g.ny) continue;
-        const uint2 e2 = __ldg(a.seg + seg_index(g, tw, z2, y2, xs - 1));
+        const uint2 e2 = ld_seg<CG>(a.seg + seg_index(g, tw, z2, y2, xs - 1));
         if (!(e2.x >> 31)) continue;
-        const uint32_t c2 = __ldg(a.runcomp + e2.y + __popc(run_starts(e2.x, SPATIAL)) - 1);
+        const uint32_t c2 = ld_seg<CG>(a.runcomp + e2.y + __popc(run_starts(e2.x, SPATIAL)) - 1);
         if (c2 != c0 && c2 != last) join(c0, c2);
         last = c2;
       }
@@ -590,7 +598,7 @@ __device__ __forceinline__ bool pair_first_seen(unsigned long long* set, uint32_
 }
 
 // One tile's cross-face joins, one thread per segment (s_set cleared by the caller).
-template <bool SPATIAL>
+template <bool SPATIAL, bool CG = false>
 __device__ __forceinline__ void hook_tile(const SegArgs& a, int tile, unsigned long long* s_set) {
   const Geometry& g = a.g;
   const TileCoord tc = tile_coord(g, tile);
@@ -600,9 +608,9 @@ __device__ __forceinline__ void hook_tile(const SegArgs& a, int tile, unsigned l
   const int y = (tc.ty << g.lby) + ly, z = (tc.tz << g.lbz) + lz;
   const int tw = (tc.tt << g.lbt) + lt - g.toff;
   if (y >= g.ny || z >= g.nz || tw < 0 || tw >= g.tw) return;
-  const uint2 e = __ldg(a.seg + seg_index(g, tw, z, y, tc.xs));
+  const uint2 e = ld_seg<CG>(a.seg + seg_index(g, tw, z, y, tc.xs));
   if (!e.x) return;
-  hook_seg<SPATIAL>(a, tw, z, y, tc.xs, e.x, e.y, [&](uint32_t c0, uint32_t c1) {
+  hook_seg<SPATIAL, CG>(a, tw, z, y, tc.xs, e.x, e.y, [&](uint32_t c0, uint32_t c1) {
     if (pair_first_seen(s_set, c0, c1)) gunion(a.cparent, c0, c1);
   });
 }
@@ -619,16 +627,16 @@ __global__ void __launch_bounds__(256, 4) k_hook(const __grid_constant__ SegArgs
 // ---------------------------------------------------------------------------------------------
 // k_links: trajectory links and the point samples of the features
 // ---------------------------------------------------------------------------------------------
-template <bool SPATIAL>
+template <bool SPATIAL, bool CG = false>
 __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) {
   const Geometry& g = a.g;
   uint32_t yz, x, z, y;
   g.fnx.divmod((uint32_t)v, yz, x);
   g.fny.divmod(yz, z, y);
-  const uint2 e = __ldg(a.seg + seg_index(g, tw, (int)z, (int)y, (int)(x >> 5)));
+  const uint2 e = ld_seg<CG>(a.seg + seg_index(g, tw, (int)z, (int)y, (int)(x >> 5)));
   const int b = x & 31;
   if (!((e.x >> b) & 1u)) return -1;
-  return __ldg(a.runcomp + e.y + run_index(run_starts(e.x, SPATIAL), b));
+  return ld_seg<CG>(a.runcomp + e.y + run_index(run_starts(e.x, SPATIAL), b));
 }
 
 // One thread per point and chunk of kLinkSteps point steps of the window: the point's voxel
@@ -641,7 +649,7 @@ __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) 
 // edge joins the two voxel-timesteps already); over one field step it is one vertex.
 constexpr int kLinkSteps = 8;
 
-template <bool SPATIAL>
+template <bool SPATIAL, bool CG = false>
 __device__ __forceinline__ void links_chunk(const SegArgs& a, int64_t p, int c0) {
   constexpr int L = kLinkSteps;
   const bool temporal = (a.edges & MSF_EDGE_TEMPORAL) != 0;
@@ -659,7 +667,7 @@ __device__ __forceinline__ void links_chunk(const SegArgs& a, int64_t p, int c0)
   for (int j = 0; j <= L; ++j) {
     comp[j] = kNoComp;
     if (key[j] >= 0) {
-      const int64_t cj = comp_of<SPATIAL>(a, st[j], key[j]);
+      const int64_t cj = comp_of<SPATIAL, CG>(a, st[j], key[j]);
       if (cj >= 0) comp[j] = (uint32_t)cj;
     }
   }
@@ -695,7 +703,7 @@ __device__ __forceinline__ void flatten_body(const SegArgs& a, const int tile, i
   int& s_n = *s_n_ptr;
   if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
-  const int nc = min(a.tileinfo[tile].y, a.g.cmax);
+  const int nc = min(__ldcg(&a.tileinfo[tile].y), a.g.cmax);
   const uint32_t cbase = (uint32_t)tile * (uint32_t)a.g.cmax;
   int roots = 0;
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
@@ -731,7 +739,7 @@ __device__ __forceinline__ void final_body(const SegArgs& a, const int tile, int
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TileCoord tc = tile_coord(g, tile);
   const int BY = 1 << g.lby, BZ = 1 << g.lbz;
-  const int nrun = min(a.tileinfo[tile].x, MAXR);
+  const int nrun = min(__ldcg(&a.tileinfo[tile].x), MAXR);
   const uint32_t rbase = (uint32_t)tile * (uint32_t)a.maxr;
   for (int r = tid; r < nrun; r += 256) {
     const uint32_t c = __ldcg(a.runcomp + rbase + r);
@@ -1296,12 +1304,14 @@ __global__ void __launch_bounds__(256, 4) k_feat_points(const __grid_constant__ 
                                                         const float* __restrict__ attr) {
   constexpr int L = kLinkSteps;
   __shared__ int2 s_buf[8][32 * L];  // per warp: (feature, step * 32 + lane)
+  __shared__ HotCache s_hot[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t pbase = (int64_t)blockIdx.x * 256 + w * 32;
   const int64_t p = pbase + lane;
   const bool in = p < a.P;
   const int nj = a.nj;
   const int nchunk = (nj + L - 1) / L;
+  hot_clear(s_hot[w]);
   for (int c = blockIdx.y; c < nchunk; c += gridDim.y) {
     const int s0 = c * L;
     int32_t fid[L];
@@ -1350,12 +1360,14 @@ __global__ void __launch_bounds__(256, 4) k_feat_points(const __grid_constant__ 
       const bool ok = i < total;
       const int2 e = ok ? s_buf[w][i] : make_int2(-1, 0);
       const int j = e.y >> 5;
-      accumulate_samples(acc, ok, e.x,
-                         attr + (((int64_t)a.j0 + s0 + j) * acc.A) * a.P + pbase + (e.y & 31),
-                         a.P);
+      accumulate_samples_hot(acc, s_hot[w], ok, e.x,
+                             attr + (((int64_t)a.j0 + s0 + j) * acc.A) * a.P + pbase + (e.y & 31),
+                             a.P);
+      __syncwarp();  // the cached sums one reduction at a time
     }
     __syncwarp();
   }
+  hot_flush(acc, s_hot[w]);
 }
 
 int seg_mark_roots(msf_ctx* ctx, uint32_t* rootbits, unsigned long long* counter) {
@@ -1552,6 +1564,21 @@ struct BatchPlan {
   const int* row_q;            // [items] query of each chunk item, items in timestep order
   const int* row_tw;           // [items] window-relative first step of each chunk item
   int64_t row0;                // first trajectory row of this launch (gridDim.y rows each)
+  // the fused launch (k_batch_fused): work segments in pipeline order with their first items,
+  // per-query prefixes of trajectory items (link chunk x point block) and of cross-face items
+  // (the query's tiles, or none without spatial and temporal edges), the queue head, per-query
+  // phase counters and the error word of the bounded waits
+  const int4* fseg;            // [nfseg] (work type, first query, end query, 0)
+  const int64_t* fseg_begin;   // [nfseg + 1]
+  int nfseg;
+  int64_t nitems;
+  const int64_t* link_begin;   // [nq + 1]
+  const int64_t* hook_begin;   // [nq + 1]
+  int npb;                     // point blocks of kFusedPoints points per link chunk
+  unsigned long long* head;
+  unsigned* qsync;             // [nq][3]: tiles formed, joins done, tiles flattened
+  unsigned* err;
+  long long wait_cycles;
 };
 
 // Largest i < n with begin[i] <= idx (begin ascending, begin[0] == 0).
@@ -1660,6 +1687,166 @@ __global__ void __launch_bounds__(256) k_final_batch(const __grid_constant__ Bat
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// fused batched launch: every phase of every query of a group in one persistent kernel
+// ---------------------------------------------------------------------------------------------
+// Blocks pull items from one queue (an atomic head). The queue lists the work of groups of
+// queries as a software pipeline: the tiles of group g, the trajectory and cross-face joins of
+// group g - 1, the flattening of group g - 2 and the label write of group g - 3, then the next
+// g. A block waits (bounded) until its item's query has finished the phase the item needs:
+// joins need every tile of the query, flattening every join, the label write every flattened
+// tile. Every item waits only for items earlier in the queue, which blocks already hold, so
+// the launch always progresses; a wait that runs out sets the error word and every block
+// leaves. Phases of different queries therefore overlap on the device: the issue-bound tile
+// work of one group beside the L2-bound joins of another.
+enum : int { kFTile = 0, kFLink = 1, kFHook = 2, kFFlat = 3, kFFinal = 4 };
+constexpr int kFusedPoints = 2048;  // points of one trajectory item (8 per thread)
+constexpr int kFusedGroup = 4;      // queries per pipeline group
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Wait until *p >= target; false when `limit` SM cycles pass first or another block gave up.
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, const unsigned* err,
+                                           long long limit) {
+  if (ld_acquire(p) >= target) return true;
+  if (limit <= 0) return false;
+  const long long t0 = clock64();
+  while (ld_acquire(p) < target) {
+    if (*(volatile const unsigned*)err) return false;
+    if (clock64() - t0 > limit) return false;
+    __nanosleep(100);
+  }
+  return true;
+}
+
+// Largest i in [0, n) with begin[i] <= idx (begin ascending).
+__device__ __forceinline__ int find_range_n(const int64_t* begin, int n, int64_t idx) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(begin + mid) <= idx) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int NP, bool SPATIAL, bool VEC>
+__global__ void __launch_bounds__(256, 4) k_batch_fused(const __grid_constant__ BatchPlan b) {
+  constexpr int MAXR = kSegPerTile * (SPATIAL ? 16 : 32);
+  __shared__ uint32_t s_mask[kSegPerTile];
+  __shared__ uint32_t s_rb[kSegPerTile];
+  __shared__ int s_warp[8];
+  __shared__ __align__(16) SegArgs s_args;
+  __shared__ int s_type, s_q, s_ok, s_n;
+  __shared__ long long s_idx;
+  extern __shared__ __align__(16) uint32_t s_dyn[];  // tile: run union-find; hook: pair set;
+                                                     // label write: run labels
+  const TileSmem sm{s_mask, s_rb, s_warp, s_dyn, reinterpret_cast<uint16_t*>(s_dyn + MAXR), MAXR};
+  while (true) {
+    if (threadIdx.x == 0) {
+      const long long item = (long long)atomicAdd(b.head, 1ull);
+      int type = -1, q = 0;
+      long long idx = 0;
+      if (item < b.nitems && !*(volatile const unsigned*)b.err) {
+        const int si = find_range_n(b.fseg_begin, b.nfseg, item);
+        const int4 sg = __ldg(b.fseg + si);
+        type = sg.x;
+        const int64_t* pre = type == kFLink ? b.link_begin
+                             : type == kFHook ? b.hook_begin : b.tile_begin;
+        const int64_t local = item - __ldg(b.fseg_begin + si) + __ldg(pre + sg.y);
+        q = sg.y + find_range_n(pre + sg.y, sg.z - sg.y, local);
+        idx = local - __ldg(pre + q);
+      }
+      s_type = type;
+      s_q = q;
+      s_idx = idx;
+    }
+    __syncthreads();
+    const int type = s_type;
+    if (type < 0) break;  // queue drained (or a wait gave up)
+    const int q = s_q;
+    const long long idx = s_idx;
+    load_args(&s_args, b.qargs + q);
+    if (threadIdx.x == 0) {
+      // what the item needs from its query
+      const unsigned* cq = b.qsync + 3 * q;
+      const unsigned ntile = (unsigned)(__ldg(b.tile_begin + q + 1) - __ldg(b.tile_begin + q));
+      const unsigned njoin = (unsigned)(__ldg(b.link_begin + q + 1) - __ldg(b.link_begin + q) +
+                                        __ldg(b.hook_begin + q + 1) - __ldg(b.hook_begin + q));
+      bool ok = true;
+      if (type == kFLink || type == kFHook) ok = wait_count(cq, ntile, b.err, b.wait_cycles);
+      else if (type == kFFlat)
+        ok = wait_count(cq, ntile, b.err, b.wait_cycles) &&
+             wait_count(cq + 1, njoin, b.err, b.wait_cycles);
+      else if (type == kFFinal) ok = wait_count(cq + 2, ntile, b.err, b.wait_cycles);
+      if (!ok) atomicOr(b.err, 1u);
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    if (type == kFTile) {
+      tile_body<NP, SPATIAL, VEC>(s_args, (int)idx, sm);
+    } else if (type == kFLink) {
+      const int c = (int)(idx / b.npb), pb = (int)(idx - (long long)c * b.npb);
+#pragma unroll 1
+      for (int k = 0; k < kFusedPoints / 256; ++k) {
+        const int64_t p = (int64_t)pb * kFusedPoints + k * 256 + threadIdx.x;
+        if (p < s_args.P) links_chunk<SPATIAL, true>(s_args, p, c * kLinkSteps);
+      }
+    } else if (type == kFHook) {
+      unsigned long long* s_set = reinterpret_cast<unsigned long long*>(s_dyn);
+      for (int i = threadIdx.x; i < kHookSet; i += 256) s_set[i] = ~0ull;
+      __syncthreads();
+      hook_tile<SPATIAL, true>(s_args, (int)idx, s_set);
+    } else if (type == kFFlat) {
+      flatten_body(s_args, (int)idx, &s_n);
+    } else {
+      final_body<SPATIAL, VEC>(s_args, (int)idx, reinterpret_cast<int32_t*>(s_dyn), s_mask, s_rb);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && type != kFFinal) {
+      __threadfence();  // the item's writes before its count
+      atomicAdd(b.qsync + 3 * q + (type == kFTile ? 0 : type == kFFlat ? 2 : 1), 1u);
+    }
+  }
+}
+
+template <bool SP>
+static constexpr size_t fused_dyn_smem() {
+  const size_t tile = tile_dyn_smem<SP>();
+  const size_t hook = sizeof(unsigned long long) * kHookSet;
+  const size_t fin = sizeof(int32_t) * kSegPerTile * (SP ? 16 : 32);
+  return std::max(tile, std::max(hook, fin));
+}
+
+template <int NP, bool SP, bool VEC>
+static int launch_fused(msf_ctx* ctx, const BatchPlan& b, cudaStream_t s) {
+  static std::atomic<uint64_t> attr_set{0};
+  const size_t smem = fused_dyn_smem<SP>();
+  ensure_smem_attr(k_batch_fused<NP, SP, VEC>, smem, attr_set);
+  int per_sm = 0;
+  MSF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fused<NP, SP, VEC>,
+                                                             256, smem));
+  const int64_t grid = std::min<int64_t>(b.nitems, (int64_t)ctx->sm_count * std::max(per_sm, 1));
+  k_batch_fused<NP, SP, VEC><<<(unsigned)std::max<int64_t>(grid, 1), 256, smem, s>>>(b);
+  return MSF_OK;
+}
+
+template <bool SP, bool VEC>
+static int launch_fused_np(msf_ctx* ctx, const BatchPlan& b, int np, cudaStream_t s) {
+  switch (np) {
+    case 0: return launch_fused<0, SP, VEC>(ctx, b, s);
+    case 1: return launch_fused<1, SP, VEC>(ctx, b, s);
+    case 2: return launch_fused<2, SP, VEC>(ctx, b, s);
+    case 3: return launch_fused<3, SP, VEC>(ctx, b, s);
+    default: return launch_fused<4, SP, VEC>(ctx, b, s);
+  }
+}
+
 template <int NP, bool SP, bool VEC>
 static void launch_tile_batch(const BatchPlan& b, int grid, cudaStream_t s) {
   static std::atomic<uint64_t> attr_set{0};
@@ -1715,6 +1902,13 @@ struct BatchGroup {
   std::vector<int64_t> chunk_begin, seg_begin, tile_begin, row_begin;
   std::vector<int> chunk_nq, chunk_qoff, qlist, k0, row_q, row_tw;
   size_t off_args = 0, off_i64 = 0, off_i32 = 0, off_cnt = 0;  // in the job's plan area
+  // fused launch: per-query prefixes of trajectory and cross-face items, the work segments in
+  // pipeline order, their first items; the queue head, error word and phase counters (zero in
+  // the host image, so every upload of the plan resets them)
+  std::vector<int64_t> link_begin, hook_begin, fseg_begin;
+  std::vector<int4> fseg;
+  int npb = 1;
+  size_t off_fused = 0, off_sync = 0;
 };
 
 struct BatchJob {
@@ -1845,6 +2039,42 @@ static int plan_group(msf_ctx* ctx, const msf_criteria* crits, BatchJob* job, Ba
     gr.row_q.push_back(0);
     gr.row_tw.push_back(0);
   }
+  // fused launch: trajectory items are (link chunk, block of kFusedPoints points); cross-face
+  // items are the query's tiles when it has spatial or temporal edges
+  gr.npb = (int)std::max<int64_t>(1, (d.P + kFusedPoints - 1) / kFusedPoints);
+  gr.link_begin.assign(nq + 1, 0);
+  gr.hook_begin.assign(nq + 1, 0);
+  for (int i = 0; i < nq; ++i) {
+    gr.link_begin[i + 1] = gr.link_begin[i] + (gr.row_begin[i + 1] - gr.row_begin[i]) * gr.npb;
+    const bool hooks = (gr.args[i].edges & (MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL)) != 0;
+    gr.hook_begin[i + 1] = gr.hook_begin[i] + (hooks ? gr.args[i].g.ntiles : 0);
+  }
+  // the pipeline: groups of kFusedGroup queries; at step g the tiles of group g, the joins of
+  // group g - 1, the flattening of group g - 2 and the label write of group g - 3
+  {
+    const int ngq = (nq + kFusedGroup - 1) / kFusedGroup;
+    gr.fseg.clear();
+    gr.fseg_begin.assign(1, 0);
+    auto add = [&](int type, int grp, const std::vector<int64_t>& pre) {
+      if (grp < 0 || grp >= ngq) return;
+      const int q0 = grp * kFusedGroup, q1 = std::min(nq, q0 + kFusedGroup);
+      const int64_t n = pre[q1] - pre[q0];
+      if (n <= 0) return;
+      gr.fseg.push_back(make_int4(type, q0, q1, 0));
+      gr.fseg_begin.push_back(gr.fseg_begin.back() + n);
+    };
+    for (int g = 0; g < ngq + 3; ++g) {
+      add(kFTile, g, gr.tile_begin);
+      add(kFLink, g - 1, gr.link_begin);
+      add(kFHook, g - 1, gr.hook_begin);
+      add(kFFlat, g - 2, gr.tile_begin);
+      add(kFFinal, g - 3, gr.tile_begin);
+    }
+    if (gr.fseg.empty()) {  // keep the tables non-empty
+      gr.fseg.push_back(make_int4(kFFinal, 0, 0, 0));
+      gr.fseg_begin.push_back(0);
+    }
+  }
   // layout in the job's plan area: argument table, int64 tables, int32 tables, counts
   gr.off_args = job->plan_bytes;
   size_t o = gr.off_args + up256(sizeof(SegArgs) * nq);
@@ -1854,6 +2084,11 @@ static int plan_group(msf_ctx* ctx, const msf_criteria* crits, BatchJob* job, Ba
   o += up256(sizeof(int) * ((size_t)nchunk * 2 + gr.qlist.size() + nq + 2 * gr.row_q.size()));
   gr.off_cnt = o;
   o += up256(sizeof(unsigned long long) * 2 * nq);
+  gr.off_fused = o;
+  o += up256(sizeof(int64_t) * (2 * (size_t)(nq + 1) + gr.fseg_begin.size()) +
+             sizeof(int4) * gr.fseg.size());
+  gr.off_sync = o;
+  o += up256(sizeof(unsigned long long) + sizeof(unsigned) * (2 + 3 * (size_t)nq));
   job->plan_bytes = o;
   return MSF_OK;
 }
@@ -1901,6 +2136,15 @@ static int launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b, 
   const int np = gr.np;
   const bool vec = (d.nx & 3) == 0;
   k_batch_prep<<<nq, 32, 0, s>>>(b.qargs);
+  if (ctx->batch_sched & MSF_SCHED_PERSISTENT) {  // every phase in one persistent launch
+    bool vq = vec;
+    for (int i = 0; i < nq; ++i) vq &= ((uintptr_t)gr.args[i].labels & 15) == 0;
+    ScopedKernel k(ctx, "k_batch_fused", timed);
+    if (spatial) return vq ? launch_fused_np<true, true>(ctx, b, np, s)
+                           : launch_fused_np<true, false>(ctx, b, np, s);
+    return vq ? launch_fused_np<false, true>(ctx, b, np, s)
+              : launch_fused_np<false, false>(ctx, b, np, s);
+  }
   const int per_sm = 5;  // resident CTAs of the tile kernel per SM
   // the criterion as a streaming pass over every query's window first (rows contiguous), or
   // inside the tile pass
@@ -2018,6 +2262,14 @@ static void batch_job_fill(BatchJob* job, int32_t* const* labels, char* const* s
     for (auto v : gr.k0) h32[o++] = v;
     for (auto v : gr.row_q) h32[o++] = v;
     for (auto v : gr.row_tw) h32[o++] = v;
+    int64_t* f64 = reinterpret_cast<int64_t*>(plan_host + gr.off_fused);
+    o = 0;
+    for (auto v : gr.link_begin) f64[o++] = v;
+    for (auto v : gr.hook_begin) f64[o++] = v;
+    for (auto v : gr.fseg_begin) f64[o++] = v;
+    memcpy(f64 + o, gr.fseg.data(), sizeof(int4) * gr.fseg.size());
+    memset(plan_host + gr.off_sync, 0,
+           sizeof(unsigned long long) + sizeof(unsigned) * (2 + 3 * (size_t)nq));
   }
 }
 
@@ -2046,6 +2298,18 @@ static int batch_job_enqueue(msf_ctx* ctx, BatchJob* job, char* plan_dev, char* 
     b.row_q = b.k0 + nq;
     b.row_tw = b.row_q + gr.row_q.size();
     b.nspat = gr.nspat;
+    const int64_t* f64 = reinterpret_cast<const int64_t*>(plan_dev + gr.off_fused);
+    b.link_begin = f64;
+    b.hook_begin = f64 + (nq + 1);
+    b.fseg_begin = b.hook_begin + (nq + 1);
+    b.fseg = reinterpret_cast<const int4*>(b.fseg_begin + gr.fseg_begin.size());
+    b.nfseg = (int)gr.fseg.size();
+    b.nitems = gr.fseg_begin.back();
+    b.npb = gr.npb;
+    b.head = reinterpret_cast<unsigned long long*>(plan_dev + gr.off_sync);
+    b.err = reinterpret_cast<unsigned*>(b.head + 1);
+    b.qsync = b.err + 2;
+    b.wait_cycles = ctx->wait_cycles;
     MSF_TRY(launch_group(ctx, gr, b, s, sp, timed));
     auto* cnt = reinterpret_cast<unsigned long long*>(plan_dev + gr.off_cnt);
     k_batch_counts<<<(nq + 255) / 256, 256, 0, s>>>(b.qargs, nq, cnt);
@@ -2125,8 +2389,11 @@ int batch_job_finish(const BatchJob* job, const char* plan_host, int64_t* n_feat
     for (int i = 0; i < job->nq; ++i) n_features[i] = 0;
   for (const BatchGroup& gr : job->groups) {
     const auto* cnt = reinterpret_cast<const unsigned long long*>(plan_host + gr.off_cnt);
+    // a bounded wait of the fused launch that gave up
+    const unsigned gave_up = *reinterpret_cast<const unsigned*>(
+        plan_host + gr.off_sync + sizeof(unsigned long long));
     for (size_t i = 0; i < gr.qs.size(); ++i) {
-      const int st = cnt[2 * i + 1] ? MSF_ERR_INTERNAL : MSF_OK;
+      const int st = gave_up ? MSF_ERR_TIMEOUT : cnt[2 * i + 1] ? MSF_ERR_INTERNAL : MSF_OK;
       if (status) status[gr.qs[i]] = st;
       if (st != MSF_OK) st_all = st;
       if (n_features) n_features[gr.qs[i]] = (int64_t)cnt[2 * i];
@@ -2135,17 +2402,22 @@ int batch_job_finish(const BatchJob* job, const char* plan_host, int64_t* n_feat
   return st_all;
 }
 
-size_t batch_plan_bound(int nq, int T, int nz) {
-  // every query of a batch in one group is the largest table set; a group boundary adds at
-  // most four 256-byte roundings, and there are at most 2 * (MSF_MAX_PRED + 1) groups (more
-  // only past 65535 queries)
-  const int bt = nz == 1 ? 16 : 4;
-  const size_t nchunk = (size_t)(T + bt - 1) / bt + 1;
+size_t batch_plan_bound(int nq, int T, int Tp, int nz) {
+  // every query of a batch in one group is the largest table set (time chunks of one step at
+  // the least, trajectory chunks of every point step); a group boundary adds at most six
+  // 256-byte roundings, and there are at most 2 * (MSF_MAX_PRED + 1) groups (more only past
+  // 65535 queries)
+  (void)nz;
+  const size_t nchunk = (size_t)T + 1;
+  const size_t rows = (size_t)nq * ((size_t)Tp / kLinkSteps + 2);
   const int ngroups = 2 * (MSF_MAX_PRED + 1) + nq / 65535 + 1;
+  const size_t nseg = 5 * ((size_t)nq / kFusedGroup + 4) + 1;
   size_t b = sizeof(SegArgs) * (size_t)nq + sizeof(int64_t) * (ngroups * (nchunk + 4) + 3 * (size_t)nq) +
-             sizeof(int) * (ngroups * (2 * nchunk + 1) + nchunk * nq + nq + 2 * (size_t)nq * T) +
+             sizeof(int) * (ngroups * (2 * nchunk + 1) + nchunk * nq + nq + 2 * rows) +
              sizeof(unsigned long long) * 2 * (size_t)nq;
-  return b + (size_t)ngroups * 4 * 256;
+  b += ngroups * (sizeof(int64_t) * (2 + nseg) + sizeof(int4) * nseg + 16) +
+       sizeof(int64_t) * 2 * (size_t)nq + sizeof(unsigned) * 3 * (size_t)nq;
+  return b + (size_t)ngroups * 6 * 256;
 }
 
 int segment_batch_run(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,

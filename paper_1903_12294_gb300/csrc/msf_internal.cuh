@@ -232,7 +232,9 @@ struct msf_ctx {
   int sched = -1;                    // msf_segment schedule set by msf_set_schedule (-1: auto)
   bool keep_pcomp = false;  // the next msf_segment keeps point components (features followed)
   int batch_by = 0, batch_bz = 0, batch_bt = 0;  // tile of the batched form (0: fixed rule)
-  int batch_sched = 1;  // MSF_SCHED_* of the batched form: criterion fused into the tile pass
+  // MSF_SCHED_* of the batched form: criterion fused into the tile pass, every phase in one
+  // persistent launch
+  int batch_sched = MSF_SCHED_FUSED_CRITERION | MSF_SCHED_PERSISTENT;
   std::vector<msf::TuneEntry> tune;  // msf_autotune results, one per problem shape
   msf::KernelTimer timer;
   std::atomic<int> servers{0};  // query servers attached (the dataset is frozen meanwhile)
@@ -734,6 +736,59 @@ __device__ __forceinline__ void accumulate_samples(const FeatAcc& acc, bool ok, 
                  });
 }
 
+// A warp's sums for one feature kept in shared memory: the first feature the warp commits
+// claims it (most point samples of a labelling often belong to one large feature), and its later
+// sums add there without atomics; every other feature goes straight to the accumulators. The
+// warp flushes the cache once at the end. Within one reduce_samples call a feature has one
+// leader lane, so the cached sums have a single writer at a time.
+struct HotCache {
+  long long fid;
+  unsigned long long sq[MSF_MAX_ATTR];
+  double sa2[MSF_MAX_ATTR];
+};
+
+__device__ __forceinline__ void hot_clear(HotCache& h) {
+  if ((threadIdx.x & 31) == 0) {
+    h.fid = -1;
+    for (int j = 0; j < MSF_MAX_ATTR; ++j) {
+      h.sq[j] = 0ull;
+      h.sa2[j] = 0.0;
+    }
+  }
+  __syncwarp();
+}
+
+// reduce_samples committing through the warp's cache
+__device__ __forceinline__ void accumulate_samples_hot(const FeatAcc& acc, HotCache& h, bool ok,
+                                                       int64_t fid, const float* attr_p,
+                                                       int64_t P) {
+  reduce_samples(acc, ok, fid, attr_p, P,
+                 [&](int64_t f, int j, unsigned long long qs, double a2, double b2) {
+                   if (j == 0 && h.fid < 0)
+                     atomicCAS(reinterpret_cast<unsigned long long*>(&h.fid), ~0ull,
+                               (unsigned long long)f);
+                   if (h.fid == f) {
+                     h.sq[j] += qs;
+                     h.sa2[j] += a2 + b2;
+                     return;
+                   }
+                   const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + f;
+                   atomicAdd(acc.sq + i * acc.A + j, qs);
+                   atomicAdd(acc.sa2 + i * acc.A + j, a2);
+                   if (b2 != 0.0) atomicAdd(acc.sa2 + i * acc.A + j, b2);
+                 });
+}
+
+__device__ __forceinline__ void hot_flush(const FeatAcc& acc, HotCache& h) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  if (h.fid >= 0 && lane < acc.A) {
+    const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + h.fid;
+    atomicAdd(acc.sq + i * acc.A + lane, h.sq[lane]);
+    atomicAdd(acc.sa2 + i * acc.A + lane, h.sa2[lane]);
+  }
+}
+
 // entry points of the translation units
 int bin_run(msf_ctx* ctx, unsigned flags);
 int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels_dev, int64_t* nfeat,
@@ -760,8 +815,9 @@ int batch_job_finish(const BatchJob* job, const char* plan_host, int64_t* n_feat
 void batch_job_free(BatchJob* job);
 // Device scratch of one query labelled in a batch (its geometry uses the batch tile shape).
 int batch_query_scratch(msf_ctx* ctx, const msf_criteria* c, size_t* bytes);
-// Upper bound of batch_job_plan_bytes for nq queries on a dataset of T steps and nz planes.
-size_t batch_plan_bound(int nq, int T, int nz);
+// Upper bound of batch_job_plan_bytes for nq queries on a dataset of T field steps, Tp point
+// steps and nz planes.
+size_t batch_plan_bound(int nq, int T, int Tp, int nz);
 int features_run(msf_ctx* ctx, const msf_criteria* crit, const int32_t* labels_dev,
                  const void* labels_user, msf_feature* out, int out_kind, int64_t cap,
                  int64_t* n_out);

@@ -360,7 +360,7 @@ extern "C" int msf_server_create(msf_ctx* ctx, const msf_server_config* cfg, msf
   srv->alloc.reset(PoolAlloc::round(c.pool_bytes) == c.pool_bytes ? c.pool_bytes
                                                                    : c.pool_bytes & ~(uint64_t)255);
   srv->slots.resize(c.slots);
-  const size_t plan_cap = batch_plan_bound(c.max_batch, ctx->ds.T, ctx->ds.nz);
+  const size_t plan_cap = batch_plan_bound(c.max_batch, ctx->ds.T, ctx->ds.Tp, ctx->ds.nz);
   int st = MSF_OK;
   if (cudaMalloc(&srv->pool, srv->alloc.cap()) != cudaSuccess) st = MSF_ERR_OUT_OF_MEMORY;
   for (Slot& s : srv->slots) {

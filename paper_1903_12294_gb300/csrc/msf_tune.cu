@@ -225,10 +225,14 @@ int msf_set_batch_tile(msf_ctx* c, int by, int bz, int bt) {
 }
 
 int msf_set_batch_schedule(msf_ctx* c, int sched) {
-  if (!c || sched < 0 || sched > (MSF_SCHED_FUSED_CRITERION | MSF_SCHED_SERIAL_JOINS))
+  if (!c || sched < 0 ||
+      (sched & ~(MSF_SCHED_FUSED_CRITERION | MSF_SCHED_SERIAL_JOINS | MSF_SCHED_PERSISTENT)))
     return MSF_ERR_INVALID_ARG;
   if (c->servers.load() > 0) return MSF_ERR_BUSY;
-  c->batch_sched = sched & MSF_SCHED_FUSED_CRITERION;
+  // the persistent launch evaluates the criterion inside its tile items
+  c->batch_sched = sched & MSF_SCHED_PERSISTENT
+                       ? (MSF_SCHED_FUSED_CRITERION | MSF_SCHED_PERSISTENT)
+                       : (sched & MSF_SCHED_FUSED_CRITERION);
   return MSF_OK;
 }
 
@@ -289,17 +293,21 @@ int msf_autotune_batch(msf_ctx* c, int nq, const msf_criteria* crits, int32_t* c
   // the fixed rule first
   const Dataset& d = c->ds;
   const int rby = d.nz == 1 ? 16 : 8, rbz = d.nz == 1 ? 1 : 8, rbt = d.nz == 1 ? 16 : 4;
+  const int kDefault = MSF_SCHED_FUSED_CRITERION | MSF_SCHED_PERSISTENT;
   float ms_default = 0.f;
-  int st = time_tile(0, 0, 0, MSF_SCHED_FUSED_CRITERION, &ms_default);
-  int bby = rby, bbz = rbz, bbt = rbt, bsched = MSF_SCHED_FUSED_CRITERION, tried = 1;
+  int st = time_tile(0, 0, 0, kDefault, &ms_default);
+  int bby = rby, bbz = rbz, bbt = rbt, bsched = kDefault, tried = 1;
   float best = ms_default;
   const std::vector<int> tiles = tile_candidates(d, twmax);
-  const int nsched = (d.nx & 31) == 0 ? 2 : 1;  // the streamed criterion needs whole rows
+  // the persistent launch, the phase launches with the criterion in the tile pass, and (whole
+  // rows only) the phase launches with the criterion streamed first
+  const int scheds[3] = {kDefault, MSF_SCHED_FUSED_CRITERION, 0};
+  const int nsched = (d.nx & 31) == 0 ? 3 : 2;
   for (size_t i = 0; st == MSF_OK && i < tiles.size(); ++i) {
     const int by = tiles[i] >> 16, bz = (tiles[i] >> 8) & 0xFF, bt = tiles[i] & 0xFF;
     for (int k = 0; st == MSF_OK && k < nsched; ++k) {
-      const int sched = k == 0 ? MSF_SCHED_FUSED_CRITERION : 0;
-      if (by == rby && bz == rbz && bt == rbt && sched == MSF_SCHED_FUSED_CRITERION) continue;
+      const int sched = scheds[k];
+      if (by == rby && bz == rbz && bt == rbt && sched == kDefault) continue;
       float ms = 0.f;
       st = time_tile(by, bz, bt, sched, &ms);
       if (st == MSF_ERR_TOO_LARGE || st == MSF_ERR_OUT_OF_MEMORY) {  // not a candidate here

@@ -12,22 +12,30 @@ F, C, M = 0, 1, 2
 GT, GE, LT, LE, BAND = 0, 1, 2, 3, 4
 
 
+PERSISTENT = 9   # MSF_SCHED_PERSISTENT | MSF_SCHED_FUSED_CRITERION: one persistent launch
+
+
 def _check_batch(gpu, orc, f, p, a, queries):
+    """The batch in one persistent launch (the default) and in one launch per phase."""
     ctx = gpu.Context(0)
     try:
         ctx.load(*(torch.as_tensor(x).cuda().contiguous() for x in (f, p, a)))
         ctx.bin()
-        labels, nfs = ctx.segment_batch(queries)
+        runs = []
+        for sched in (PERSISTENT, 1):
+            ctx.set_batch_schedule(sched)
+            runs.append(ctx.segment_batch(queries))
         singles = [ctx.segment(t0, t1, pr, e) for (t0, t1, pr, e) in queries]
         torch.cuda.synchronize()
     finally:
         ctx.close()
     o = orc.bin(f.shape, p, a)
-    for (t0, t1, pr, e), lb, nf, (ls, ns) in zip(queries, labels, nfs, singles):
-        assert nf == ns
-        assert torch.equal(lb, ls)
-        lab, n_o = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
-        assert nf == n_o and np.array_equal(lb.cpu().numpy(), lab)
+    for labels, nfs in runs:
+        for (t0, t1, pr, e), lb, nf, (ls, ns) in zip(queries, labels, nfs, singles):
+            assert nf == ns
+            assert torch.equal(lb, ls)
+            lab, n_o = orc.segment(f, o["count"], o["mean"], o["key"], t0, t1, pr, e)
+            assert nf == n_o and np.array_equal(lb.cpu().numpy(), lab)
 
 
 def test_batch_mixed_windows_and_criteria(gpu, orc):
@@ -102,9 +110,9 @@ def test_batch_graph_replay(gpu, orc):
 
 
 def test_batch_tile_shapes_and_autotune(gpu, orc):
-    """Every batch tile shape and criterion schedule (fused, or streamed first on whole 32-voxel
-    rows) gives the single queries' labels; the batch autotuner keeps a valid choice, and the
-    batch then still gives them."""
+    """Every batch tile shape and schedule (one persistent launch; phase launches with the
+    criterion fused, or streamed first on whole 32-voxel rows) gives the single queries'
+    labels; the batch autotuner keeps a valid choice, and the batch then still gives them."""
     wl = synth.mid(n=64, T=12, P=20000, n_blobs=8)
     f, p, a = wl.numpy()
     q = wl.preds
@@ -117,16 +125,17 @@ def test_batch_tile_shapes_and_autotune(gpu, orc):
         ctx.load(*(torch.as_tensor(x).cuda().contiguous() for x in (f, p, a)))
         ctx.bin()
         got = []
-        for sched in (1, 0):
+        for sched in (PERSISTENT, 1, 0):
             ctx.set_batch_schedule(sched)
             for tile in [(4, 4, 16), (2, 16, 8), (16, 8, 2), (8, 8, 4)]:
                 ctx.set_batch_tile(*tile)
                 labels, nfs = ctx.segment_batch(queries)
                 got.append(((sched, tile), [l.cpu().numpy() for l in labels], nfs))
         ctx.set_batch_tile(0, 0, 0)
-        ctx.set_batch_schedule(1)
+        ctx.set_batch_schedule(PERSISTENT)
         r = ctx.autotune_batch(queries, reps=1)
-        assert r["by"] * r["bz"] * r["bt"] == 256 and r["n_tried"] > 3 and r["sched"] in (0, 1)
+        assert r["by"] * r["bz"] * r["bt"] == 256 and r["n_tried"] > 3
+        assert r["sched"] in (0, 1, PERSISTENT)
         assert 0 < r["ms"] <= r["ms_default"]
         labels, nfs = ctx.segment_batch(queries)
         got.append(("tuned", [l.cpu().numpy() for l in labels], nfs))

@@ -38,3 +38,29 @@ def test_wait_timeout_is_reported_and_recoverable(gpu):
     finally:
         ref_ctx.close()
     assert n == n_ref and torch.equal(lab, ref)
+
+
+def test_fused_batch_wait_timeout_is_reported_and_recoverable(gpu):
+    """The persistent batched launch waits (bounded) on its queries' phase counters; with a
+    limit of 0 the first wait that is not already met gives up, every block leaves, the batch
+    reports MSF_ERR_TIMEOUT, and the same batch then runs normally with the limit restored."""
+    wl = synth.mid(n=48, T=10, P=20000, n_blobs=8)
+    dev = [x.cuda() for x in (wl.field, wl.pos, wl.attr)]
+    queries = [(t0, t0 + 6, wl.preds, 7) for t0 in range(5)]
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(*dev)
+        ctx.bin()
+        ctx.set_batch_schedule(9)
+        want = [ctx.segment(t0, t1, pr, e) for (t0, t1, pr, e) in queries]
+        ctx.set_wait_limit(0)
+        with pytest.raises(gpu.MsfError) as e:
+            ctx.segment_batch(queries)
+        assert e.value.status == gpu.MSF_ERR_TIMEOUT
+        ctx.set_wait_limit(-1)
+        labels, nfs = ctx.segment_batch(queries)
+        torch.cuda.synchronize()
+        for (lw, nw), lb, nf in zip(want, labels, nfs):
+            assert nf == nw and torch.equal(lb, lw)
+    finally:
+        ctx.close()
