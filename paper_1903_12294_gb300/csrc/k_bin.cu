@@ -50,6 +50,8 @@ struct BinArgs {
   const int32_t* fstep;         // [Tp]
   const int32_t* pj0;           // [T + 1] first point step of each field step
   int64_t V, P;
+  int64_t scale_n;              // point samples the fixed-point scale counts (P * Tp, or a
+                                // whole dataset's when binning one slab of it)
   int logR, nb;                 // bucket = voxel >> logR; nb buckets
   int nblk;                     // sample blocks per timestep
   int64_t chunk;                // samples per block
@@ -71,15 +73,6 @@ struct BinArgs {
   float* mean;                  // [A][T][V]
   long long* sumq;              // [A][T][V] or null
 };
-
-// Voxel of one sample: cells are [i, i+1); non-finite or outside positions give -1.
-__device__ __forceinline__ int32_t voxel_of(float px, float py, float pz, int nx, int ny, int nz) {
-  if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) return -1;
-  const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
-  if (fx < 0.f || fy < 0.f || fz < 0.f) return -1;
-  if (fx >= (float)nx || fy >= (float)ny || fz >= (float)nz) return -1;
-  return ((int)fz * ny + (int)fy) * nx + (int)fx;
-}
 
 // k = 62 - e - b from the fp32 bits of max|v| (e: frexp exponent, 0 for zero) and the sample
 // count (b: smallest with 2^b >= n + 1).
@@ -423,7 +416,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
     if (npiece) reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, R, &s_bar);
   }
   if ((int)threadIdx.x < A) {
-    const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.P * b.Tp);
+    const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.scale_n);
     s_k[threadIdx.x] = k;
     s_f1[threadIdx.x] = pow2f(-(k / 2));
     s_f2[threadIdx.x] = pow2f(-(k - k / 2));
@@ -628,6 +621,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.pj0 = d.pj0.as<int32_t>();
   b.V = d.V;
   b.P = d.P;
+  b.scale_n = d.scale_fixed ? d.scale_samples : d.P * (int64_t)d.Tp;
   b.logR = bucket_log2(d.A, d.V);
   b.nb = (int)((d.V + ((int64_t)1 << b.logR) - 1) >> b.logR);
   // samples per block: the shared-memory sort handles kPlaceChunk; with too many buckets for
@@ -672,7 +666,11 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.mean = d.mean.as<float>();
   b.sumq = keep ? d.sumq.as<long long>() : nullptr;
   MSF_CUDA_TRY(cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * TB, s));
-  MSF_CUDA_TRY(cudaMemsetAsync(b.absmax, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
+  if (d.scale_fixed)  // the whole dataset's maxima: a slab's can only be smaller
+    MSF_CUDA_TRY(cudaMemcpyAsync(b.absmax, d.scale_absmax, sizeof(unsigned) * MSF_MAX_ATTR,
+                                 cudaMemcpyHostToDevice, s));
+  else
+    MSF_CUDA_TRY(cudaMemsetAsync(b.absmax, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.outside, 0, sizeof(unsigned long long) * d.Tp, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), s));
   b.nrec = nullptr;
@@ -706,7 +704,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
     float m;
     memcpy(&m, &hmax[a], sizeof(float));
     d.max_abs[a] = m;
-    d.kscale[a] = scale_exponent_bits(hmax[a], d.P * (int64_t)d.Tp);
+    d.kscale[a] = scale_exponent_bits(hmax[a], (long long)b.scale_n);
   }
   int64_t o = 0;
   for (auto v : out) o += (int64_t)v;

@@ -2262,12 +2262,14 @@ static void batch_job_fill(BatchJob* job, int32_t* const* labels, char* const* s
     for (auto v : gr.k0) h32[o++] = v;
     for (auto v : gr.row_q) h32[o++] = v;
     for (auto v : gr.row_tw) h32[o++] = v;
-    int64_t* f64 = reinterpret_cast<int64_t*>(plan_host + gr.off_fused);
+    // the int4 segments first (the area is 256-byte aligned), then the int64 prefixes
+    memcpy(plan_host + gr.off_fused, gr.fseg.data(), sizeof(int4) * gr.fseg.size());
+    int64_t* f64 = reinterpret_cast<int64_t*>(plan_host + gr.off_fused +
+                                              sizeof(int4) * gr.fseg.size());
     o = 0;
     for (auto v : gr.link_begin) f64[o++] = v;
     for (auto v : gr.hook_begin) f64[o++] = v;
     for (auto v : gr.fseg_begin) f64[o++] = v;
-    memcpy(f64 + o, gr.fseg.data(), sizeof(int4) * gr.fseg.size());
     memset(plan_host + gr.off_sync, 0,
            sizeof(unsigned long long) + sizeof(unsigned) * (2 + 3 * (size_t)nq));
   }
@@ -2298,11 +2300,12 @@ static int batch_job_enqueue(msf_ctx* ctx, BatchJob* job, char* plan_dev, char* 
     b.row_q = b.k0 + nq;
     b.row_tw = b.row_q + gr.row_q.size();
     b.nspat = gr.nspat;
-    const int64_t* f64 = reinterpret_cast<const int64_t*>(plan_dev + gr.off_fused);
+    b.fseg = reinterpret_cast<const int4*>(plan_dev + gr.off_fused);  // 16-byte aligned
+    const int64_t* f64 = reinterpret_cast<const int64_t*>(plan_dev + gr.off_fused +
+                                                          sizeof(int4) * gr.fseg.size());
     b.link_begin = f64;
     b.hook_begin = f64 + (nq + 1);
     b.fseg_begin = b.hook_begin + (nq + 1);
-    b.fseg = reinterpret_cast<const int4*>(b.fseg_begin + gr.fseg_begin.size());
     b.nfseg = (int)gr.fseg.size();
     b.nitems = gr.fseg_begin.back();
     b.npb = gr.npb;

@@ -414,6 +414,7 @@ int msf_load_timesteps_mr(msf_ctx* c, int nx, int ny, int nz, int T, const float
   d.A = A;
   d.V = V;
   d.Tp = Tp;
+  d.scale_fixed = false;
   d.h_fstep = fs;
   d.h_pj0.assign(T + 1, 0);
   for (int t = 0, j = 0; t <= T; ++t) {

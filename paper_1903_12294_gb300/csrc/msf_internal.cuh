@@ -61,6 +61,12 @@ struct Dataset {
   DevBuf fstep, pj0;                // device copies of the two maps
   DevBuf field, pos, attr;          // [T][V] f32, [Tp][3][P] f32, [Tp][A][P] f32
   DevBuf key, count, mean, sumq;    // [Tp][P] i32, [T][V] i32, [A][T][V] f32, [A][T][V] i64
+  // Binning of one time slab of a larger dataset (out-of-core labelling) takes the whole
+  // dataset's fixed-point scale: its largest finite |v| per attribute (fp32 bits) and its number
+  // of point samples. Set after a load; the next load clears it.
+  bool scale_fixed = false;
+  unsigned scale_absmax[MSF_MAX_ATTR] = {};
+  int64_t scale_samples = 0;
   int32_t kscale[MSF_MAX_ATTR] = {};
   float max_abs[MSF_MAX_ATTR] = {};
   int64_t in_domain = 0, out_of_domain = 0;
@@ -342,6 +348,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
   while (!mbar_try_wait(bar, parity))
     if (clock64() - t0 > limit) return false;
   return true;
+}
+
+// Voxel of one point sample: cells are [i, i+1) in grid units; a non-finite position or one
+// outside [0, n) in any axis gives -1. Linear index (z * ny + y) * nx + x.
+__device__ __forceinline__ int32_t voxel_of(float px, float py, float pz, int nx, int ny, int nz) {
+  if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) return -1;
+  const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+  if (fx < 0.f || fy < 0.f || fz < 0.f) return -1;
+  if (fx >= (float)nx || fy >= (float)ny || fz >= (float)nz) return -1;
+  return ((int)fz * ny + (int)fy) * nx + (int)fx;
 }
 
 // q = round_half_even(v * 2^k) with integer operations only: v = +-man * 2^(exp - 150), so
