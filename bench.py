@@ -477,15 +477,19 @@ def run_batched(dev, reps=3):
     ctx.kernel_times(reset=True)
     tuned_sched = tuning.get("sched")
 
-    def phases():  # the same batch with one launch per phase (for the per-phase split)
-        ctx.set_batch_schedule(1)
-        try:
-            return batch()
-        finally:
-            ctx.set_batch_schedule(tuned_sched)
-    # the last arm is the same batch with graphs on: its warm-up runs plainly, then captures,
-    # and the timed calls replay the graph
-    for name, fn in (("plain", plain), ("batched", batch), ("batched_phases", phases),
+    def with_sched(sched):  # the same batch (tuned tiles) with another schedule
+        def run():
+            ctx.set_batch_schedule(sched)
+            try:
+                return batch()
+            finally:
+                ctx.set_batch_schedule(tuned_sched)
+        return run
+    # the phase launches (their per-phase split) and the persistent launch, beside the tuned
+    # choice; the last arm is the tuned batch with graphs on: its warm-up runs plainly, then
+    # captures, and the timed calls replay the graph
+    for name, fn in (("plain", plain), ("batched", batch), ("batched_phases", with_sched(1)),
+                     ("batched_persistent", with_sched(msf.MSF_SCHED_PERSISTENT | 1)),
                      ("batched_graph", batch)):
         if name == "batched_graph":
             ctx.set_batch_graphs(True)
@@ -520,6 +524,7 @@ def run_batched(dev, reps=3):
                         f"attrs, {len(crits)} queries, T_w in 2..32, {vt} query-voxel-timesteps",
             "plain": out["plain"], "batched": out["batched"],
             "batched_phases": out["batched_phases"],
+            "batched_persistent": out["batched_persistent"],
             "batched_graph": dict(out["batched_graph"], graph_replays=replays),
             "batch_tuning": tuning,
             "speedup": round(out["plain"]["ms_per_batch"] / out["batched"]["ms_per_batch"], 2),

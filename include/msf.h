@@ -388,6 +388,31 @@ int msf_server_get_stats(msf_server* srv, msf_server_stats* out);
  * (including labels not yet released). Errors: INVALID_ARG. */
 int msf_server_destroy(msf_server* srv);
 
+/* ---- out-of-core labelling --------------------------------------------------------------- */
+
+/* Label a window of a dataset that stays in host memory, streaming it through the device in
+ * time slabs (§3.4 and §4.3: data that does not fit the GPU's memory is processed there in
+ * chunks). The dataset arguments are those of msf_load_timesteps_mr, all host memory (pinned
+ * memory copies faster; the caller keeps ownership). Slabs of `slab_steps` field steps of the
+ * window [crit->t0, crit->t1) go to the device one at a time with the point steps that fall in
+ * them; each is binned with the whole dataset's fixed-point scale (so every count and mean is
+ * the whole dataset's binning), labelled, and its labels copied into `labels` (host,
+ * [t1-t0][nz][ny][nx] int32, caller-owned). Components that meet across a cut (a temporal edge
+ * between the planes of field steps b-1 and b, or a trajectory link between consecutive point
+ * steps in different slabs) are then joined and relabelled with their smallest index in a last
+ * pass over the labels, so `labels` and `n_features` (host, may be NULL) equal msf_segment's on
+ * the whole dataset resident. Device memory in use is about one slab's (its field, points,
+ * binning and labelling state) rather than the dataset's. The context serves as the staging
+ * area: its dataset is replaced and, on return, the context holds none (load one again before
+ * msf_segment). The paper has no counterpart for the joins at the cuts (its clustering has no
+ * connectivity). Synchronises the stream.
+ * Errors: those of msf_load_timesteps_mr and msf_segment; INVALID_ARG (slab_steps < 1, NULL
+ * buffers), BUSY (a query server is attached), OUT_OF_MEMORY, CUDA. */
+int msf_segment_streamed(msf_ctx* ctx, int nx, int ny, int nz, int T, const float* field,
+                         int64_t P, int A, int Tp, const float* pos, const float* attr,
+                         const int32_t* field_step, const msf_criteria* crit, int slab_steps,
+                         int32_t* labels, int64_t* n_features);
+
 /* ---- allocation-free labelling ----------------------------------------------------------- */
 
 /* Field-only labelling that allocates nothing, for callers that cannot allocate device memory
@@ -475,12 +500,13 @@ int msf_tune_clear(msf_ctx* ctx);
  * 32x16x1x16 on a 2D grid). Errors: INVALID_ARG, BUSY (a query server is attached). */
 int msf_set_batch_tile(msf_ctx* ctx, int by, int bz, int bt);
 
-/* Schedule of the batched form: MSF_SCHED_PERSISTENT | MSF_SCHED_FUSED_CRITERION (the default)
- * runs each batch group as one persistent launch with the criterion inside its tile items;
- * MSF_SCHED_FUSED_CRITERION alone launches the phases one after the other with the criterion
- * inside the tile pass; 0 runs the criterion of every query first as a streaming pass (grids
- * whose nx is a multiple of 32; others keep the fused pass). MSF_SCHED_SERIAL_JOINS is ignored.
- * Errors: INVALID_ARG (unknown bits), BUSY (a query server is attached). */
+/* Schedule of the batched form: MSF_SCHED_FUSED_CRITERION (the default) launches the phases
+ * one after the other with the criterion inside the tile pass; MSF_SCHED_PERSISTENT (with or
+ * without MSF_SCHED_FUSED_CRITERION) runs each batch group as one persistent launch with the
+ * criterion inside its tile items; 0 runs the criterion of every query first as a streaming
+ * pass (grids whose nx is a multiple of 32; others keep the fused pass).
+ * MSF_SCHED_SERIAL_JOINS is ignored. Errors: INVALID_ARG (unknown bits), BUSY (a query server
+ * is attached). */
 int msf_set_batch_schedule(msf_ctx* ctx, int sched);
 
 /* Time msf_segment_batch on this batch (nq queries, labels as for msf_segment_batch, which
@@ -488,8 +514,8 @@ int msf_set_batch_schedule(msf_ctx* ctx, int sched);
  * schedules (persistent launch; phase launches with the criterion fused or streamed), one
  * warm-up and `reps` timed runs each (reps < 1: 3), and keep the fastest as the batched form's
  * tile shape and schedule (msf_set_batch_tile, msf_set_batch_schedule). `out` (may be NULL)
- * receives them, their time and the fixed rule's (32x8x8x4, persistent). Synchronises the
- * stream.
+ * receives them, their time and the fixed rule's (32x8x8x4, phase launches, criterion fused).
+ * Synchronises the stream.
  * Errors: those of msf_segment_batch; INVALID_ARG when no query has a window; BUSY. */
 int msf_autotune_batch(msf_ctx* ctx, int nq, const msf_criteria* crits, int32_t* const* labels,
                        int reps, msf_tune_result* out);

@@ -19,7 +19,8 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmsf.so")
 
 SOURCES = ["msf_api.cu", "msf_scan.cu", "k_bin.cu", "k_segment.cu", "k_features.cu",
-           "k_cluster.cu", "k_post.cu", "msf_tune.cu", "msf_server.cu", "msf_noalloc.cu"]
+           "k_cluster.cu", "k_post.cu", "msf_tune.cu", "msf_server.cu", "msf_noalloc.cu",
+           "msf_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -194,22 +194,24 @@ __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArg
 // ---------------------------------------------------------------------------------------------
 // pass 2: records in bucket order (and the attribute maxima)
 // ---------------------------------------------------------------------------------------------
-// The block's keys and attributes (each an aligned-down, rounded-up span of its row) come into
-// shared memory by bulk asynchronous copy, while the threads read the block's slot ranges. The
-// block then sorts its samples by bucket in shared memory (a counting sort against its own
-// histogram, through an index permutation) and writes each bucket's run to its slot range, so
-// that a warp's stores land in a few contiguous runs rather than 32 scattered sectors.
+// The block's keys (an aligned-down, rounded-up span of its row) come into shared memory by bulk
+// asynchronous copy while the threads read the block's slot ranges and take the attribute
+// maxima (coalesced reads). The block then sorts its samples by bucket in shared memory (a
+// counting sort against its own histogram, through an index permutation) and writes each
+// bucket's run to its slot range, gathering the attributes of the sorted samples from its own
+// rows (read a moment earlier: cache hits), so that a warp's stores land in a few contiguous runs
+// rather than 32 scattered sectors. Keeping the attributes out of shared memory lets more blocks
+// share an SM on grids with many buckets.
 constexpr int kPlaceChunk = 4096;              // samples per block in the shared-memory path
-constexpr int kPlaceStage = kPlaceChunk + 8;   // staged elements per array (alignment slack)
+constexpr int kPlaceStage = kPlaceChunk + 8;   // staged keys (alignment slack)
 constexpr int kPlaceSmemMax = 200 * 1024;
 
 template <int A>
-__global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
+__global__ void __launch_bounds__(kBinNT, 2) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
   extern __shared__ __align__(16) uint32_t s_place[];
   int32_t* s_key = reinterpret_cast<int32_t*>(s_place);                   // [kPlaceStage]
-  float* s_att = reinterpret_cast<float*>(s_place + kPlaceStage);          // [A][kPlaceStage]
-  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + (1 + A) * kPlaceStage);  // [chunk]
-  uint32_t* s_delta = s_place + (1 + A) * kPlaceStage + kPlaceChunk / 2;   // [nb] slot - local
+  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + kPlaceStage);    // [chunk]
+  uint32_t* s_delta = s_place + kPlaceStage + kPlaceChunk / 2;             // [nb] slot - local
   uint32_t* s_lpos = s_delta + b.nb;                                       // [nb] fill cursor
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned s_max[A > 0 ? A : 1];
@@ -219,35 +221,35 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t pbeg = (int64_t)blk * b.chunk;
   const int n = (int)min((int64_t)b.chunk, b.P - pbeg);
-  // element offsets of the block's rows and their misalignment (elements before the row start
+  // element offset of the block's key row and its misalignment (elements before the row start
   // that the aligned-down copy brings in)
   const int64_t ek = (int64_t)t * b.P + pbeg;
   const int hk = (int)(ek & 3);
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
-    uint32_t tx = (uint32_t)(((hk + n + 3) & ~3) * 4);
-#pragma unroll
-    for (int a = 0; a < A; ++a) {
-      const int64_t ea = ((int64_t)t * A + a) * b.P + pbeg;
-      tx += (uint32_t)((((int)(ea & 3) + n + 3) & ~3) * 4);
-    }
-    mbar_expect_tx(&s_bar, tx);
-    bulk_g2s(s_key, b.key + (ek - hk), (uint32_t)(((hk + n + 3) & ~3) * 4), &s_bar);
-#pragma unroll
-    for (int a = 0; a < A; ++a) {
-      const int64_t ea = ((int64_t)t * A + a) * b.P + pbeg;
-      const int ha = (int)(ea & 3);
-      bulk_g2s(s_att + a * kPlaceStage, b.attr + (ea - ha), (uint32_t)(((ha + n + 3) & ~3) * 4),
-               &s_bar);
-    }
+    const uint32_t bytes = (uint32_t)(((hk + n + 3) & ~3) * 4);
+    mbar_expect_tx(&s_bar, bytes);
+    bulk_g2s(s_key, b.key + (ek - hk), bytes, &s_bar);
   }
-  // the block's slot ranges and bucket counts (overlapping the copies)
+  // the block's slot ranges and bucket counts (overlapping the copy)
   for (int i = threadIdx.x; i < b.nb; i += kBinNT) {
     const int64_t h = hist_index(b, t, i, blk);
     s_delta[i] = b.offs[h];
     s_lpos[i] = b.hist[h];  // counts, scanned below
   }
   if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
+  // largest finite |v| of every attribute over the block's samples (coalesced)
+  const float* arow = b.attr + (int64_t)t * A * b.P + pbeg;
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    unsigned lmax = 0u;
+    for (int i = threadIdx.x; i < n; i += kBinNT) {
+      const float v = __ldg(arow + (int64_t)a * b.P + i);
+      if (isfinite(v)) lmax = max(lmax, __float_as_uint(fabsf(v)));
+    }
+    const unsigned m = __reduce_max_sync(0xFFFFFFFFu, lmax);
+    if (lane == 0 && m) atomicMax(s_max + a, m);
+  }
   __syncthreads();
   // exclusive scan of the block's bucket counts (one thread per chunk of buckets); s_delta
   // becomes global slot minus local position
@@ -275,33 +277,20 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
     }
   }
   const bool ok = mbar_wait(&s_bar, 0, b.wait_cycles);
-  if (__syncthreads_or(!ok)) {  // the copies did not arrive in time
+  if (__syncthreads_or(!ok)) {  // the copy did not arrive in time
     if (threadIdx.x == 0) {
       atomicAdd(b.err, 1u);
-      mbar_wait(&s_bar, 0);      // let copies still in flight land before the block exits
+      mbar_wait(&s_bar, 0);      // let the copy still in flight land before the block exits
     }
     return;
   }
   // counting sort: s_inv[local position] = sample
-  unsigned lmax[A > 0 ? A : 1];
-#pragma unroll
-  for (int a = 0; a < A; ++a) lmax[a] = 0u;
   for (int i = threadIdx.x; i < n; i += kBinNT) {
     const int32_t k = s_key[hk + i];
     if (k >= 0) {
       const uint32_t pos = atomicAdd(s_lpos + (k >> b.logR), 1u);
       s_inv[pos] = (uint16_t)i;
     }
-  }
-#pragma unroll
-  for (int a = 0; a < A; ++a) {
-    const int ha = (int)((((int64_t)t * A + a) * b.P + pbeg) & 3);
-    for (int i = threadIdx.x; i < n; i += kBinNT) {
-      const float v = s_att[a * kPlaceStage + ha + i];
-      if (isfinite(v)) lmax[a] = max(lmax[a], __float_as_uint(fabsf(v)));
-    }
-    const unsigned m = __reduce_max_sync(0xFFFFFFFFu, lmax[a]);
-    if (lane == 0 && m) atomicMax(s_max + a, m);
   }
   __syncthreads();
   // runs out: local position j of bucket bk goes to slot s_delta[bk] + j
@@ -312,10 +301,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_place_sorted(const __grid_con
     const uint32_t slot = s_delta[k >> b.logR] + (uint32_t)j;
     b.rec_v[slot] = (uint32_t)k;
 #pragma unroll
-    for (int a = 0; a < A; ++a) {
-      const int ha = (int)((((int64_t)t * A + a) * b.P + pbeg) & 3);
-      b.rec_a[(int64_t)a * b.NRp + slot] = s_att[a * kPlaceStage + ha + i];
-    }
+    for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * b.NRp + slot] = __ldg(arow + (int64_t)a * b.P + i);
   }
   if ((int)threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
 }
@@ -544,7 +530,8 @@ static int bucket_log2(int A, int64_t V) {
 static size_t reduce_smem(int A, int logR) { return ((size_t)1 << logR) * (8 + 12 * (size_t)A); }
 
 static size_t place_smem(int A, int nb) {
-  return sizeof(uint32_t) * ((1 + (size_t)A) * kPlaceStage + kPlaceChunk / 2 + 2 * (size_t)nb);
+  (void)A;
+  return sizeof(uint32_t) * ((size_t)kPlaceStage + kPlaceChunk / 2 + 2 * (size_t)nb);
 }
 
 template <int A>

@@ -1700,8 +1700,8 @@ __global__ void __launch_bounds__(256) k_final_batch(const __grid_constant__ Bat
 // leaves. Phases of different queries therefore overlap on the device: the issue-bound tile
 // work of one group beside the L2-bound joins of another.
 enum : int { kFTile = 0, kFLink = 1, kFHook = 2, kFFlat = 3, kFFinal = 4 };
-constexpr int kFusedPoints = 2048;  // points of one trajectory item (8 per thread)
-constexpr int kFusedGroup = 4;      // queries per pipeline group
+constexpr int kFusedPoints = 256;   // points of one trajectory item (one per thread)
+constexpr int kFusedGroup = 8;      // queries per pipeline group
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -1792,11 +1792,8 @@ __global__ void __launch_bounds__(256, 4) k_batch_fused(const __grid_constant__ 
       tile_body<NP, SPATIAL, VEC>(s_args, (int)idx, sm);
     } else if (type == kFLink) {
       const int c = (int)(idx / b.npb), pb = (int)(idx - (long long)c * b.npb);
-#pragma unroll 1
-      for (int k = 0; k < kFusedPoints / 256; ++k) {
-        const int64_t p = (int64_t)pb * kFusedPoints + k * 256 + threadIdx.x;
-        if (p < s_args.P) links_chunk<SPATIAL, true>(s_args, p, c * kLinkSteps);
-      }
+      const int64_t p = (int64_t)pb * kFusedPoints + threadIdx.x;
+      if (p < s_args.P) links_chunk<SPATIAL, true>(s_args, p, c * kLinkSteps);
     } else if (type == kFHook) {
       unsigned long long* s_set = reinterpret_cast<unsigned long long*>(s_dyn);
       for (int i = threadIdx.x; i < kHookSet; i += 256) s_set[i] = ~0ull;

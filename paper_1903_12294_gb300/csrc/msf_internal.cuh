@@ -238,9 +238,9 @@ struct msf_ctx {
   int sched = -1;                    // msf_segment schedule set by msf_set_schedule (-1: auto)
   bool keep_pcomp = false;  // the next msf_segment keeps point components (features followed)
   int batch_by = 0, batch_bz = 0, batch_bt = 0;  // tile of the batched form (0: fixed rule)
-  // MSF_SCHED_* of the batched form: criterion fused into the tile pass, every phase in one
-  // persistent launch
-  int batch_sched = MSF_SCHED_FUSED_CRITERION | MSF_SCHED_PERSISTENT;
+  // MSF_SCHED_* of the batched form: criterion fused into the tile pass, one launch per phase
+  // (the batch autotuner also tries the persistent launch)
+  int batch_sched = MSF_SCHED_FUSED_CRITERION;
   std::vector<msf::TuneEntry> tune;  // msf_autotune results, one per problem shape
   msf::KernelTimer timer;
   std::atomic<int> servers{0};  // query servers attached (the dataset is frozen meanwhile)

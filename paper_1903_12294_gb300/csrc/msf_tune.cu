@@ -293,15 +293,15 @@ int msf_autotune_batch(msf_ctx* c, int nq, const msf_criteria* crits, int32_t* c
   // the fixed rule first
   const Dataset& d = c->ds;
   const int rby = d.nz == 1 ? 16 : 8, rbz = d.nz == 1 ? 1 : 8, rbt = d.nz == 1 ? 16 : 4;
-  const int kDefault = MSF_SCHED_FUSED_CRITERION | MSF_SCHED_PERSISTENT;
+  const int kDefault = MSF_SCHED_FUSED_CRITERION;
   float ms_default = 0.f;
   int st = time_tile(0, 0, 0, kDefault, &ms_default);
   int bby = rby, bbz = rbz, bbt = rbt, bsched = kDefault, tried = 1;
   float best = ms_default;
   const std::vector<int> tiles = tile_candidates(d, twmax);
-  // the persistent launch, the phase launches with the criterion in the tile pass, and (whole
+  // the phase launches with the criterion in the tile pass, the persistent launch, and (whole
   // rows only) the phase launches with the criterion streamed first
-  const int scheds[3] = {kDefault, MSF_SCHED_FUSED_CRITERION, 0};
+  const int scheds[3] = {kDefault, MSF_SCHED_FUSED_CRITERION | MSF_SCHED_PERSISTENT, 0};
   const int nsched = (d.nx & 31) == 0 ? 3 : 2;
   for (size_t i = 0; st == MSF_OK && i < tiles.size(); ++i) {
     const int by = tiles[i] >> 16, bz = (tiles[i] >> 8) & 0xFF, bt = tiles[i] & 0xFF;

@@ -29,7 +29,7 @@ MSF_MAX_PRED, MSF_MAX_ATTR = 4, 8
 
 # every entry point the header declares (checked by the CPU test-suite)
 EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
-           "msf_load_timesteps_mr",
+           "msf_load_timesteps_mr", "msf_segment_streamed",
            "msf_bin_particles", "msf_get_bins", "msf_segment", "msf_extract_features",
            "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
            "msf_segment_field_noalloc", "msf_segment_batch", "msf_server_create",
@@ -40,6 +40,7 @@ EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_set_batch_graphs", "msf_batch_graph_replays", "msf_set_batch_tile",
            "msf_autotune_batch", "msf_set_batch_schedule")
 MSF_SCHED_FUSED_CRITERION, MSF_SCHED_SERIAL_JOINS, MSF_SCHED_PIPELINE = 1, 2, 4
+MSF_SCHED_PERSISTENT = 8
 MSF_MERGE_POINT, MSF_MERGE_FIELD = 1, 2
 MSF_SPACE_POINTS, MSF_SPACE_VOXELS = 0, 1
 
@@ -148,6 +149,9 @@ def load_library(path: str = LIB_PATH):
         lib.msf_load_timesteps.argtypes = [P, i32, i32, i32, i32, P, i64, i32, P, P, i32]
         lib.msf_load_timesteps_mr.argtypes = [P, i32, i32, i32, i32, P, i64, i32, i32, P, P, P,
                                               i32]
+        lib.msf_segment_streamed.argtypes = [P, i32, i32, i32, i32, P, i64, i32, i32, P, P, P,
+                                             ctypes.POINTER(msf_criteria), i32, P,
+                                             ctypes.POINTER(ctypes.c_int64)]
         lib.msf_bin_particles.argtypes = [P, u32, ctypes.POINTER(msf_bin_stats)]
         lib.msf_get_bins.argtypes = [P, P, P, P, P, i32]
         lib.msf_segment.argtypes = [P, ctypes.POINTER(msf_criteria), P, i32,
@@ -293,6 +297,33 @@ def msf_load_timesteps_mr(ctx, field, pos, attr, field_step):
     fs = np.ascontiguousarray(np.asarray(field_step, dtype=np.int32).reshape(-1))
     _check(load_library().msf_load_timesteps_mr(ctx, nx, ny, nz, T, fp, P, A, int(Tp), pp, ap,
                                                 fs.ctypes.data, k), "msf_load_timesteps_mr")
+
+
+def msf_segment_streamed(ctx, field, pos, attr, crit: msf_criteria, slab_steps, labels,
+                         field_step=None) -> int:
+    """Out-of-core labelling of crit's window over host arrays (numpy or CPU tensors): field
+    [T][nz][ny][nx], pos [Tp][3][P], attr [Tp][A][P] fp32, field_step [Tp] or None; labels a host
+    int32 array [t1-t0][nz][ny][nx]. Returns the number of features."""
+    import numpy as np
+    T, nz, ny, nx = field.shape
+    P = pos.shape[2] if pos is not None else 0
+    Tp = pos.shape[0] if pos is not None else T
+    A = attr.shape[1] if attr is not None else 0
+    ptrs = []
+    for x in (field, pos, attr, labels):
+        p, k = _ptr_kind(x)
+        if p and k != MSF_HOST:
+            raise ValueError("msf_segment_streamed takes host arrays")
+        ptrs.append(p)
+    fs = None
+    if field_step is not None:
+        fs = np.ascontiguousarray(np.asarray(field_step, dtype=np.int32).reshape(-1))
+    n = ctypes.c_int64(0)
+    _check(load_library().msf_segment_streamed(
+        ctx, nx, ny, nz, T, ptrs[0], P, A, int(Tp), ptrs[1], ptrs[2],
+        fs.ctypes.data if fs is not None else None, ctypes.byref(crit), int(slab_steps), ptrs[3],
+        ctypes.byref(n)), "msf_segment_streamed")
+    return int(n.value)
 
 
 def msf_bin_particles(ctx, flags: int = 0) -> msf_bin_stats:
