@@ -66,6 +66,8 @@ struct BinArgs {
   uint32_t* rec_v;              // [P*Tp] voxel of the sample (+4 slack for rounded bulk copies)
   float* rec_a;                 // [A][NRp] attribute values (+4 slack)
   unsigned* err;                // bounded waits that gave up
+  uint32_t* ovf;                // items (t * nb + bucket) left to the wide reduce
+  uint32_t* novf;               // their number
   long long wait_cycles;        // limit of those waits (SM cycles)
   unsigned* absmax;             // [A] float bits of max finite |v|
   unsigned long long* outside;  // [T]
@@ -231,13 +233,14 @@ __global__ void __launch_bounds__(kBinNT, 2) k_bin_place_sorted(const __grid_con
     mbar_expect_tx(&s_bar, bytes);
     bulk_g2s(s_key, b.key + (ek - hk), bytes, &s_bar);
   }
+  if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   // the block's slot ranges and bucket counts (overlapping the copy)
   for (int i = threadIdx.x; i < b.nb; i += kBinNT) {
     const int64_t h = hist_index(b, t, i, blk);
     s_delta[i] = b.offs[h];
     s_lpos[i] = b.hist[h];  // counts, scanned below
   }
-  if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
+  __syncthreads();  // the maxima cleared before any warp adds to them
   // largest finite |v| of every attribute over the block's samples (coalesced)
   const float* arow = b.attr + (int64_t)t * A * b.P + pbeg;
 #pragma unroll
@@ -372,14 +375,169 @@ __device__ __forceinline__ void item_range(const BinArgs& b, int t, int bucket, 
   r1 = h1 < TB ? __ldg(b.offs + h1) : nrec;
 }
 
-// One block per item (t, bucket). Shared memory: sums [A][R] u64, counts [R] u32 and a staging
-// buffer of R * (1 + A) words for the records (rec_v, rec_a per attribute; in pieces of R when
-// the bucket has more), reused for the means [A][R] f32 and the non-empty lists once the records
-// are in. The accumulators are cleared while the first piece is in flight. After the records,
-// every warp owns 128 voxels (four per lane): it lists its non-empty ones, forms their means and
-// stores its outputs, with no further block-wide step.
+// One block per item (field step t, bucket): the bucket's records (at most kRedStage of them)
+// arrive by one bulk copy while the voxel counts are cleared; the block counts the records per
+// voxel (32-bit shared atomics), turns the counts into each voxel's range by a block scan, and
+// sorts the records into those ranges (an index permutation); each thread then owns four
+// consecutive voxels, sums their records' fixed-point values in registers, forms the means and
+// stores counts and means with 16-byte stores. A bucket with more records than the staging area
+// holds is listed for k_bin_reduce_wide and left to it.
+constexpr int kRedStage = 2048;  // records staged per bucket (plus alignment slack)
+
 template <int A, bool KEEP>
 __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant__ BinArgs b) {
+  extern __shared__ __align__(16) uint32_t s_red[];
+  constexpr int SS = kRedStage + 8;                                      // staged elements
+  const int R = 1 << b.logR;
+  uint32_t* s_stv = s_red;                                               // [SS] voxels
+  float* s_sta = reinterpret_cast<float*>(s_red + SS);                   // [A][SS] values
+  uint32_t* s_cnt = s_red + (1 + A) * SS;                                // [R] counts
+  uint32_t* s_end = s_cnt + R;                                           // [R] range ends
+  uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_end + R);              // [SS] sorted records
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int s_warp[kBinNT / 32];
+  __shared__ int s_k[A > 0 ? A : 1];
+  __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
+  const int bucket = blockIdx.x, t = blockIdx.y;  // t: the field step
+  const uint32_t nrec = b.nrec ? *b.nrec : 0u;
+  uint32_t r0, r1;
+  item_range(b, t, bucket, nrec, r0, r1);
+  if (r1 - r0 > (uint32_t)kRedStage) {  // too many records to stage: the wide pass takes it
+    if (threadIdx.x == 0) b.ovf[atomicAdd(b.novf, 1u)] = (uint32_t)t * (uint32_t)b.nb + bucket;
+    return;
+  }
+  const uint32_t s0 = r0 & ~3u, e1 = (r1 + 3u) & ~3u;
+  const bool any = r1 > r0;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    if (any) reduce_issue<A>(b, s0, e1 - s0, s_stv, s_sta, SS, &s_bar);
+  }
+  if ((int)threadIdx.x < A) {
+    const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.scale_n);
+    s_k[threadIdx.x] = k;
+    s_f1[threadIdx.x] = pow2f(-(k / 2));
+    s_f2[threadIdx.x] = pow2f(-(k - k / 2));
+  }
+  for (int q = threadIdx.x; q < R / 4; q += kBinNT)
+    reinterpret_cast<uint4*>(s_cnt)[q] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  const int m = (int)(e1 - s0);
+  if (any) {
+    const bool ok = mbar_wait(&s_bar, 0, b.wait_cycles);
+    if (__syncthreads_or(!ok)) {  // the copy did not arrive in time
+      if (threadIdx.x == 0) {
+        atomicAdd(b.err, 1u);
+        mbar_wait(&s_bar, 0);      // let it land before the block exits
+      }
+      return;
+    }
+    for (int q = threadIdx.x; q < m; q += kBinNT) {
+      const uint32_t r = s0 + (uint32_t)q;
+      if (r < r0 || r >= r1) continue;  // alignment slack of the neighbouring buckets
+      atomicAdd(s_cnt + (s_stv[q] & (uint32_t)(R - 1)), 1u);
+    }
+  }
+  __syncthreads();
+  // ranges: exclusive block scan of the counts, four consecutive voxels per thread
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int carry = 0;
+  for (int base = 0; base < R; base += 4 * kBinNT) {
+    const int q = base + 4 * (int)threadIdx.x;
+    uint4 c4 = make_uint4(0u, 0u, 0u, 0u);
+    if (q < R) c4 = *reinterpret_cast<const uint4*>(s_cnt + q);
+    const int tot = (int)(c4.x + c4.y + c4.z + c4.w);
+    int x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    int run = carry + x - tot;
+    for (int k = 0; k < w; ++k) run += s_warp[k];
+    int all = 0;
+    for (int k = 0; k < kBinNT / 32; ++k) all += s_warp[k];
+    if (q < R)
+      *reinterpret_cast<uint4*>(s_end + q) =
+          make_uint4((uint32_t)run, (uint32_t)run + c4.x, (uint32_t)run + c4.x + c4.y,
+                     (uint32_t)run + c4.x + c4.y + c4.z);
+    carry += all;
+    __syncthreads();
+  }
+  // sort: each record to the next place of its voxel's range (s_end becomes the range ends)
+  if (any)
+    for (int q = threadIdx.x; q < m; q += kBinNT) {
+      const uint32_t r = s0 + (uint32_t)q;
+      if (r < r0 || r >= r1) continue;
+      const uint32_t pos = atomicAdd(s_end + (s_stv[q] & (uint32_t)(R - 1)), 1u);
+      s_idx[pos] = (uint16_t)q;
+    }
+  __syncthreads();
+  // four voxels per thread: sums in registers, means, 16-byte stores
+  const float qnan = __int_as_float(0x7fc00000);
+  const int64_t vbase = (int64_t)bucket << b.logR;
+  const int nv = (int)min((int64_t)R, b.V - vbase);
+  for (int q = 4 * (int)threadIdx.x; q < nv; q += 4 * kBinNT) {
+    uint32_t c[4], e[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      c[k] = q + k < R ? s_cnt[q + k] : 0u;
+      e[k] = q + k < R ? s_end[q + k] : 0u;
+    }
+    float mv[A > 0 ? A : 1][4];
+    long long sv[A > 0 ? A : 1][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t st = e[k] - c[k];
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        long long sum = 0;
+        for (uint32_t i = st; i < e[k]; ++i)
+          sum += quantise(s_sta[(size_t)a * SS + s_idx[i]], s_k[a]);
+        sv[a][k] = sum;
+        mv[a][k] = c[k] ? __fmul_rn(__fmul_rn(div_count(i64_to_f32_rn(sum), (int)c[k]), s_f1[a]),
+                                    s_f2[a])
+                        : qnan;
+      }
+    }
+    const int64_t v = vbase + q;
+    if ((b.V & 3) == 0) {  // nv is then a multiple of four
+      __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v),
+             make_uint4(c[0], c[1], c[2], c[3]));
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
+        __stcs(reinterpret_cast<float4*>(b.mean + o), make_float4(mv[a][0], mv[a][1], mv[a][2], mv[a][3]));
+        if (KEEP) {
+          __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2(sv[a][0], sv[a][1]));
+          __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2), make_longlong2(sv[a][2], sv[a][3]));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (q + k >= nv) break;
+        __stcs(b.count + (int64_t)t * b.V + v + k, (int)c[k]);
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int64_t o = ((int64_t)a * b.T + t) * b.V + v + k;
+          __stcs(b.mean + o, mv[a][k]);
+          if (KEEP) __stcs(b.sumq + o, sv[a][k]);
+        }
+      }
+    }
+  }
+}
+
+// Buckets with more records than k_bin_reduce stages (listed by it): the records arrive in
+// pieces of R; counts and fixed-point sums accumulate in shared memory (sums [A][R] u64,
+// counts [R] u32, then the staging buffer of R * (1 + A) words, reused for the means [A][R]
+// f32 and the non-empty lists once the records are in). After the records, every warp owns 128
+// voxels (four per lane): it lists its non-empty ones, forms their means and stores its outputs.
+// Blocks take listed items in turn.
+template <int A, bool KEEP>
+__global__ void __launch_bounds__(kBinNT, 1) k_bin_reduce_wide(const __grid_constant__ BinArgs b) {
   extern __shared__ __align__(16) unsigned long long s_dyn64[];
   const int R = 1 << b.logR;
   unsigned long long* s_sum = s_dyn64;                                    // [A][R]
@@ -391,21 +549,27 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_k[A > 0 ? A : 1];
   __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
-  const int bucket = blockIdx.x, t = blockIdx.y;  // t: the field step
-  const uint32_t nrec = b.nrec ? *b.nrec : 0u;
-  uint32_t r0, r1;
-  item_range(b, t, bucket, nrec, r0, r1);
-  const uint32_t s0 = r0 & ~3u, e1 = (r1 + 3u) & ~3u;
-  const int npiece = r1 > r0 ? (int)((e1 - s0 + (uint32_t)R - 1) / (uint32_t)R) : 0;
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar, 1);
-    if (npiece) reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, R, &s_bar);
-  }
+  if (threadIdx.x == 0) mbar_init(&s_bar, 1);
   if ((int)threadIdx.x < A) {
     const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.scale_n);
     s_k[threadIdx.x] = k;
     s_f1[threadIdx.x] = pow2f(-(k / 2));
     s_f2[threadIdx.x] = pow2f(-(k - k / 2));
+  }
+  uint32_t phase = 0;  // copies this block has waited for (the mbarrier's phase)
+  const uint32_t nwide = *b.novf;
+  for (uint32_t it = blockIdx.x; it < nwide; it += gridDim.x) {
+  __syncthreads();  // the previous item's reads of shared memory are done
+  const uint32_t itm = b.ovf[it];
+  const int bucket = (int)(itm % (uint32_t)b.nb), t = (int)(itm / (uint32_t)b.nb);
+  const uint32_t nrec = b.nrec ? *b.nrec : 0u;
+  uint32_t r0, r1;
+  item_range(b, t, bucket, nrec, r0, r1);
+  const uint32_t s0 = r0 & ~3u, e1 = (r1 + 3u) & ~3u;
+  const int npiece = r1 > r0 ? (int)((e1 - s0 + (uint32_t)R - 1) / (uint32_t)R) : 0;
+  if (threadIdx.x == 0 && npiece) {
+    fence_proxy_async_smem();
+    reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, R, &s_bar);
   }
   {
     uint4* z = reinterpret_cast<uint4*>(s_dyn64);
@@ -413,12 +577,12 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
     for (int q = threadIdx.x; q < n16; q += kBinNT) z[q] = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
-  for (int piece = 0; piece < npiece; ++piece) {
-    const bool ok = mbar_wait(&s_bar, (uint32_t)piece & 1u, b.wait_cycles);
+  for (int piece = 0; piece < npiece; ++piece, ++phase) {
+    const bool ok = mbar_wait(&s_bar, phase & 1u, b.wait_cycles);
     if (__syncthreads_or(!ok)) {  // the copy did not arrive in time
       if (threadIdx.x == 0) {
         atomicAdd(b.err, 1u);
-        mbar_wait(&s_bar, (uint32_t)piece & 1u);  // let it land before the block exits
+        mbar_wait(&s_bar, phase & 1u);  // let it land before the block exits
       }
       return;
     }
@@ -514,20 +678,27 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
       }
     }
   }
+  }  // items
 }
 
-// Bucket width per attribute count: sums, counts and the record staging area, R * (8 + 12 A)
-// bytes, within 64 KB of dynamic shared memory (three CTAs per SM); at most 2048 voxels.
+// Bucket width: 2048 voxels (the sorted reduce stages records, not per-voxel sums, so the
+// width no longer depends on the attribute count), wider when the grid has more buckets than
+// the shared-memory histograms hold and the wide pass's sums still fit.
 static int bucket_log2(int A, int64_t V) {
   int l = 11;
-  while (l > 6 && ((size_t)1 << l) * (8 + 12 * (size_t)A) > 64 * 1024) --l;
-  // a grid with more buckets than the shared-memory histograms hold takes wider buckets (fewer
-  // reduce CTAs per SM) rather than the global-atomic placement
-  while (l < 11 && ((V + ((int64_t)1 << l) - 1) >> l) > kHistSmem) ++l;
+  while (l < 12 && ((V + ((int64_t)1 << l) - 1) >> l) > kHistSmem &&
+         ((size_t)2 << l) * (8 + 12 * (size_t)A) <= (size_t)220 * 1024)
+    ++l;
   return l;
 }
 
-static size_t reduce_smem(int A, int logR) { return ((size_t)1 << logR) * (8 + 12 * (size_t)A); }
+static size_t reduce_smem(int A, int logR) {
+  const size_t R = (size_t)1 << logR, SS = kRedStage + 8;
+  return sizeof(uint32_t) * ((1 + (size_t)A) * SS + 2 * R) + sizeof(uint16_t) * SS;
+}
+static size_t reduce_wide_smem(int A, int logR) {
+  return ((size_t)1 << logR) * (8 + 12 * (size_t)A);
+}
 
 static size_t place_smem(int A, int nb) {
   (void)A;
@@ -556,24 +727,48 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
       k_bin_place_atomic<A><<<gs, 256, 0, s>>>(b);
     }
   } else {
-    ScopedKernel k(ctx, "k_bin_reduce");
-    const size_t sm = reduce_smem(A, b.logR);
-    const dim3 gr((unsigned)b.nb, (unsigned)b.T);
-    // the attribute is per device and set before every launch that needs more than before
-    if (keep) {
-      static std::atomic<size_t> set{0};
-      if (sm > set.load()) {
-        cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        set.store(sm);
+    {
+      ScopedKernel k(ctx, "k_bin_reduce");
+      const size_t sm = reduce_smem(A, b.logR);
+      const dim3 gr((unsigned)b.nb, (unsigned)b.T);
+      // the attribute is per device and set before every launch that needs more than before
+      if (keep) {
+        static std::atomic<size_t> set{0};
+        if (sm > set.load()) {
+          cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+          set.store(sm);
+        }
+        k_bin_reduce<A, true><<<gr, kBinNT, sm, s>>>(b);
+      } else {
+        static std::atomic<size_t> set{0};
+        if (sm > set.load()) {
+          cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+          set.store(sm);
+        }
+        k_bin_reduce<A, false><<<gr, kBinNT, sm, s>>>(b);
       }
-      k_bin_reduce<A, true><<<gr, kBinNT, sm, s>>>(b);
-    } else {
-      static std::atomic<size_t> set{0};
-      if (sm > set.load()) {
-        cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        set.store(sm);
+    }
+    {
+      // the buckets k_bin_reduce listed (more records than it stages); blocks beyond their
+      // number leave at once
+      ScopedKernel k(ctx, "k_bin_reduce_wide");
+      const size_t sm = reduce_wide_smem(A, b.logR);
+      const unsigned g = (unsigned)std::min<int64_t>((int64_t)b.nb * b.T, (int64_t)ctx->sm_count * 2);
+      if (keep) {
+        static std::atomic<size_t> set{0};
+        if (sm > set.load()) {
+          cudaFuncSetAttribute(k_bin_reduce_wide<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+          set.store(sm);
+        }
+        k_bin_reduce_wide<A, true><<<g, kBinNT, sm, s>>>(b);
+      } else {
+        static std::atomic<size_t> set{0};
+        if (sm > set.load()) {
+          cudaFuncSetAttribute(k_bin_reduce_wide<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+          set.store(sm);
+        }
+        k_bin_reduce_wide<A, false><<<g, kBinNT, sm, s>>>(b);
       }
-      k_bin_reduce<A, false><<<gr, kBinNT, sm, s>>>(b);
     }
   }
 }
@@ -631,7 +826,8 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_TRY(S.rec_a.ensure(sizeof(float) * (NRp * Af + 4)));
   MSF_TRY(S.absmax.ensure(sizeof(unsigned) * MSF_MAX_ATTR));
   MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.Tp));
-  MSF_TRY(S.total.ensure(sizeof(uint32_t) * 4));  // [0] records, [2] error word
+  MSF_TRY(S.total.ensure(sizeof(uint32_t) * 4));  // [0] records, [2] error word, [3] wide items
+  MSF_TRY(S.ovf.ensure(sizeof(uint32_t) * (size_t)d.T * (size_t)b.nb));
   MSF_TRY(d.key.ensure(sizeof(int32_t) * ((int64_t)d.Tp * d.P + 4)));  // slack: bulk copies
   MSF_TRY(d.count.ensure(sizeof(int32_t) * d.T * d.V));
   MSF_TRY(d.mean.ensure(sizeof(float) * d.T * d.V * Af));
@@ -647,6 +843,8 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.NRp = NRp;
   b.wait_cycles = ctx->wait_cycles;
   b.err = S.total.as<uint32_t>() + 2;
+  b.novf = S.total.as<uint32_t>() + 3;
+  b.ovf = S.ovf.as<uint32_t>();
   b.absmax = S.absmax.as<unsigned>();
   b.outside = S.outside.as<unsigned long long>();
   b.count = d.count.as<int32_t>();
@@ -659,7 +857,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   else
     MSF_CUDA_TRY(cudaMemsetAsync(b.absmax, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.outside, 0, sizeof(unsigned long long) * d.Tp, s));
-  MSF_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), s));
+  MSF_CUDA_TRY(cudaMemsetAsync(b.err, 0, 2 * sizeof(uint32_t), s));  // error word, wide items
   b.nrec = nullptr;
   if (d.P > 0) {
     launch_bin_a(ctx, b, keep, 0, smem);

@@ -346,7 +346,8 @@ void msf_destroy(msf_ctx* c) {
                     &c->feat.out})
     b->release();
   for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.rec_v, &c->bin.rec_a,
-                    &c->bin.absmax, &c->bin.outside, &c->bin.scan_tmp, &c->bin.total})
+                    &c->bin.absmax, &c->bin.outside, &c->bin.scan_tmp, &c->bin.total,
+                    &c->bin.ovf})
     b->release();
   c->last.cfid.release();
   c->last.pcomp.release();

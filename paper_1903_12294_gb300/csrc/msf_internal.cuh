@@ -165,7 +165,7 @@ struct BatchScratch {
 };
 
 struct BinScratch {
-  DevBuf hist, offs, cursor, rec_v, rec_a, absmax, outside, scan_tmp, total;
+  DevBuf hist, offs, cursor, rec_v, rec_a, absmax, outside, scan_tmp, total, ovf;
 };
 
 // Scratch of the clustering (k_cluster.cu): centres, their sums and cells, label buffers for
