@@ -205,15 +205,17 @@ __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArg
 // rather than 32 scattered sectors. Keeping the attributes out of shared memory lets more blocks
 // share an SM on grids with many buckets.
 constexpr int kPlaceChunk = 4096;              // samples per block in the shared-memory path
-constexpr int kPlaceStage = kPlaceChunk + 8;   // staged keys (alignment slack)
+constexpr int kPlaceChunkWide = 8192;          // the same on grids with many buckets (half the
+                                               // histogram entries of the keys and scan passes)
 constexpr int kPlaceSmemMax = 200 * 1024;
 
 template <int A>
 __global__ void __launch_bounds__(kBinNT, 2) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
   extern __shared__ __align__(16) uint32_t s_place[];
-  int32_t* s_key = reinterpret_cast<int32_t*>(s_place);                   // [kPlaceStage]
-  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + kPlaceStage);    // [chunk]
-  uint32_t* s_delta = s_place + kPlaceStage + kPlaceChunk / 2;             // [nb] slot - local
+  const int stage = (int)b.chunk + 8;                                      // keys + slack
+  int32_t* s_key = reinterpret_cast<int32_t*>(s_place);                   // [stage]
+  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + stage);          // [chunk]
+  uint32_t* s_delta = s_place + stage + (int)b.chunk / 2;                  // [nb] slot - local
   uint32_t* s_lpos = s_delta + b.nb;                                       // [nb] fill cursor
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned s_max[A > 0 ? A : 1];
@@ -489,6 +491,12 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
     long long sv[A > 0 ? A : 1][4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        sv[a][k] = 0;
+        mv[a][k] = qnan;
+      }
+      if (!c[k]) continue;  // empty voxel: count 0, mean NaN, no arithmetic
       const uint32_t st = e[k] - c[k];
 #pragma unroll
       for (int a = 0; a < A; ++a) {
@@ -496,9 +504,7 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
         for (uint32_t i = st; i < e[k]; ++i)
           sum += quantise(s_sta[(size_t)a * SS + s_idx[i]], s_k[a]);
         sv[a][k] = sum;
-        mv[a][k] = c[k] ? __fmul_rn(__fmul_rn(div_count(i64_to_f32_rn(sum), (int)c[k]), s_f1[a]),
-                                    s_f2[a])
-                        : qnan;
+        mv[a][k] = __fmul_rn(__fmul_rn(div_count(i64_to_f32_rn(sum), (int)c[k]), s_f1[a]), s_f2[a]);
       }
     }
     const int64_t v = vbase + q;
@@ -700,9 +706,8 @@ static size_t reduce_wide_smem(int A, int logR) {
   return ((size_t)1 << logR) * (8 + 12 * (size_t)A);
 }
 
-static size_t place_smem(int A, int nb) {
-  (void)A;
-  return sizeof(uint32_t) * ((size_t)kPlaceStage + kPlaceChunk / 2 + 2 * (size_t)nb);
+static size_t place_smem(int64_t chunk, int nb) {
+  return sizeof(uint32_t) * ((size_t)chunk + 8 + (size_t)chunk / 2 + 2 * (size_t)nb);
 }
 
 template <int A>
@@ -715,14 +720,14 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
     else k_bin_keys<false><<<gs, 256, 0, s>>>(b);
   } else if (phase == 1) {
     ScopedKernel k(ctx, "k_bin_place");
-    if (smem) {  // caller guarantees place_smem(A, nb) <= kPlaceSmemMax
+    if (smem) {  // caller guarantees place_smem(chunk, nb) <= kPlaceSmemMax
       static bool set = false;
       if (!set) {
         cudaFuncSetAttribute(k_bin_place_sorted<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kPlaceSmemMax);
         set = true;
       }
-      k_bin_place_sorted<A><<<gs, kBinNT, place_smem(A, b.nb), s>>>(b);
+      k_bin_place_sorted<A><<<gs, kBinNT, place_smem(b.chunk, b.nb), s>>>(b);
     } else {
       k_bin_place_atomic<A><<<gs, 256, 0, s>>>(b);
     }
@@ -808,8 +813,11 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.nb = (int)((d.V + ((int64_t)1 << b.logR) - 1) >> b.logR);
   // samples per block: the shared-memory sort handles kPlaceChunk; with too many buckets for
   // shared memory the blocks grow so that the per-block histograms stay small
-  const bool smem = b.nb <= kHistSmem && place_smem(d.A, b.nb) <= (size_t)kPlaceSmemMax;
-  b.chunk = kPlaceChunk;
+  const bool smem = b.nb <= kHistSmem && place_smem(kPlaceChunk, b.nb) <= (size_t)kPlaceSmemMax;
+  // many buckets: twice the samples per block, as long as two blocks still share an SM
+  b.chunk = (smem && b.nb >= 4096 && place_smem(kPlaceChunkWide, b.nb) <= (size_t)114 * 1024)
+                ? kPlaceChunkWide
+                : kPlaceChunk;
   if (!smem)
     while ((int64_t)b.nb * ((d.P + b.chunk - 1) / b.chunk) > (1 << 22) && b.chunk < ((int64_t)1 << 30))
       b.chunk <<= 1;

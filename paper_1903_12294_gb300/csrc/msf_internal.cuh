@@ -496,7 +496,26 @@ __device__ __forceinline__ void reduce_row(unsigned act, int64_t fid, int lane, 
   r.kmin = __reduce_min_sync(grp, isnan_f ? float_key(INFINITY) : float_key(f));
   r.kmax = __reduce_max_sync(grp, isnan_f ? float_key(-INFINITY) : float_key(f));
   const int leader = __ffs(grp) - 1;
-  if (__all_sync(grp, df_safe(f))) {
+  const bool whole = grp == act && act == 0xFFFFFFFFu;  // one feature fills the row
+  if (whole && __all_sync(0xFFFFFFFFu, df_safe(f))) {
+    // butterfly over the full warp: (h, l) double-float pairs combined by exact TwoSum
+    float h1 = f, l1 = 0.f;
+    float h2 = __fmul_rn(f, f), l2 = __fmaf_rn(f, f, -h2);  // f*f == h2 + l2 exactly
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      float s, e;
+      const float a1 = __shfl_xor_sync(0xFFFFFFFFu, h1, o), b1 = __shfl_xor_sync(0xFFFFFFFFu, l1, o);
+      two_sum(h1, a1, s, e);
+      h1 = s;
+      l1 = __fadd_rn(__fadd_rn(l1, b1), e);
+      const float a2 = __shfl_xor_sync(0xFFFFFFFFu, h2, o), b2 = __shfl_xor_sync(0xFFFFFFFFu, l2, o);
+      two_sum(h2, a2, s, e);
+      h2 = s;
+      l2 = __fadd_rn(__fadd_rn(l2, b2), e);
+    }
+    r.s1 = f2d(h1) + f2d(l1);
+    r.s2 = f2d(h2) + f2d(l2);
+  } else if (__all_sync(grp, df_safe(f))) {
     const float p = __fmul_rn(f, f), pe = __fmaf_rn(f, f, -p);  // f*f == p + pe exactly
     float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
     for (unsigned m = grp; m; m &= m - 1) {
