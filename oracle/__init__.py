@@ -115,6 +115,11 @@ def _load():
                                         ctypes.POINTER(_SlicParams), P, P, P, P,
                                         ctypes.POINTER(ctypes.c_int)])
             lib.oracle_slic.restype = ctypes.c_int
+            lib.oracle_slic_mr.argtypes = ([ctypes.c_int] * 4 + [P, i64, ctypes.c_int,
+                                           ctypes.c_int, P, P, P, P,
+                                           ctypes.POINTER(_SlicParams), P, P, P, P,
+                                           ctypes.POINTER(ctypes.c_int)])
+            lib.oracle_slic_mr.restype = ctypes.c_int
             lib.oracle_merge_clusters.argtypes = [ctypes.c_int, P, ctypes.c_float, ctypes.c_int, P]
             lib.oracle_merge_clusters.restype = ctypes.c_int
             lib.oracle_select_clusters.argtypes = [ctypes.c_int, P, P, P, P]
@@ -261,29 +266,38 @@ def run_all(field, pos, attr, t0, t1, preds, edges=EDGE_ALL, fstep=None):
 
 
 def slic(field, pos, attr, key, t0, t1, attr_index, k, w_p=1.0, w_f=1.0, w_d=1.0, c_f=1.0,
-         eps_c=1e-3, max_iter=10):
+         eps_c=1e-3, max_iter=10, fstep=None):
     """§3.2 multifaceted 4D clustering (msf_slic.c). k = (kx, ky, kz, kt) seeds per dimension.
-    Returns (field_label [Tw][NZ][NY][NX] int32, point_label [Tw][P] int32, centers [K][6] fp32
-    (x, y, z, t, p_c, f_c), counts [K][2] int64 (field, point samples), updates made)."""
+    pos/attr/key are per point step ([Tp][...]); fstep [Tp] maps point steps to field steps
+    (None: one per field step). Returns (field_label [Tw][NZ][NY][NX] int32, point_label
+    [window point steps][P] int32, centers [K][6] fp32 (x, y, z, t, p_c, f_c), counts [K][2]
+    int64 (field, point samples), updates made)."""
     field = np.ascontiguousarray(field, dtype=np.float32)
     T, nz, ny, nx = field.shape
     pos = np.ascontiguousarray(pos, dtype=np.float32)
     attr = np.ascontiguousarray(attr, dtype=np.float32)
     key = np.ascontiguousarray(key, dtype=np.int32)
     P = pos.shape[2] if pos.ndim == 3 else 0
+    Tp = pos.shape[0] if pos.ndim == 3 else T
     A = attr.shape[1] if attr.ndim == 3 else 0
+    fs = _fstep_array(fstep, Tp) if fstep is not None else None
     prm = _SlicParams(int(t0), int(t1), int(attr_index), (ctypes.c_int * 4)(*[int(x) for x in k]),
                       float(w_p), float(w_f), float(w_d), float(c_f), float(eps_c), int(max_iter))
     K = int(np.prod(k))
     tw = t1 - t0
+    if fs is None:
+        nj = tw
+    else:
+        nj = int(np.count_nonzero((fs >= t0) & (fs < t1)))
     fl = np.empty((tw, nz, ny, nx), np.int32)
-    pl = np.empty((tw, P), np.int32)
+    pl = np.empty((nj, P), np.int32)
     centers = np.empty((K, 6), np.float32)
     counts = np.empty((K, 2), np.int64)
     it = ctypes.c_int(0)
-    rc = _load().oracle_slic(nx, ny, nz, T, _ptr(field), P, A, _ptr(pos), _ptr(attr), _ptr(key),
-                             ctypes.byref(prm), _ptr(fl), _ptr(pl), _ptr(centers), _ptr(counts),
-                             ctypes.byref(it))
+    rc = _load().oracle_slic_mr(nx, ny, nz, T, _ptr(field), P, A, Tp if fs is not None else T,
+                                _ptr(fs), _ptr(pos), _ptr(attr), _ptr(key), ctypes.byref(prm),
+                                _ptr(fl), _ptr(pl), _ptr(centers), _ptr(counts),
+                                ctypes.byref(it))
     if rc != 0:
         raise RuntimeError(f"oracle_slic failed: {rc}")
     return fl, pl, centers, counts, int(it.value)

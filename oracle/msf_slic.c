@@ -17,7 +17,9 @@
  *   S_st    sqrt(dx^2 + dy^2 + dz^2 + (c_f dt)^2).
  *
  * Readings where the paper is silent (also stated in the library):
- *   - a field sample sits at its voxel's centre (x + 0.5, ...); every sample's time is t + 0.5;
+ *   - a field sample sits at its voxel's centre (x + 0.5, ...); every sample's time is t + 0.5,
+ *     or, for points on their own time grid, f + (i + 0.5) / r for the i-th of the r point
+ *     steps that fall in field step f;
  *     a point sits at its position; only points inside the grid (binning key >= 0) take part;
  *   - samples whose value (field, or the chosen point attribute) is not finite take no part;
  *   - distances and the convergence test are IEEE fp32 operations in exactly the order written
@@ -45,6 +47,14 @@ typedef struct {
 static float f_sub(float a, float b) { volatile float r = a - b; return r; }
 static float f_mul(float a, float b) { volatile float r = a * b; return r; }
 static float f_add(float a, float b) { volatile float r = a + b; return r; }
+static float f_div(float a, float b) { volatile float r = a / b; return r; }
+
+/* Points on their own time grid (§3.4): point step j falls in field step fstep[j]; the r point
+ * steps of field step f split its unit of time evenly, the i-th (0-based) at time
+ * f + (i + 0.5) / r (with one point step per field step: f + 0.5, as a field sample). */
+static float point_time(int f, int i, int r) {
+  return f_add((float)f, f_div(f_add((float)i, 0.5f), (float)r));
+}
 
 static float s_st(const float* c, float xs, float ys, float zs, float ts, float cf) {
   const float dx = f_sub(c[0], xs), dy = f_sub(c[1], ys), dz = f_sub(c[2], zs);
@@ -90,14 +100,39 @@ static float fixed_mean(int64_t sum, int64_t n, int k) {
  * counts [K][2] (field samples, point samples), *iters = centre updates made.
  * Returns 0, or -1 for bad arguments, -2 when out of memory.
  */
-int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, int A,
-                const float* pos, const float* attr, const int32_t* key,
-                const orc_slic_params* prm, int32_t* field_label, int32_t* point_label,
-                float* centers, int64_t* counts, int* iters) {
+int oracle_slic_mr(int nx, int ny, int nz, int T, const float* field, int64_t P, int A,
+                   int Tp, const int32_t* fstep, const float* pos, const float* attr,
+                   const int32_t* key, const orc_slic_params* prm, int32_t* field_label,
+                   int32_t* point_label, float* centers, int64_t* counts, int* iters) {
   const int t0 = prm->t0, t1 = prm->t1, tw = t1 - t0;
   if (tw <= 0 || t0 < 0 || t1 > T || prm->k[0] < 1 || prm->k[1] < 1 || prm->k[2] < 1 ||
       prm->k[3] < 1 || (P > 0 && (prm->attr < 0 || prm->attr >= A)))
     return -1;
+  if (!fstep && Tp != T) return -1;
+  /* the window's point steps [j0, j0 + nj); for each its field step, rank and count */
+  int j0 = 0, nj = 0;
+  for (int j = 0; j < Tp; ++j) {
+    const int f = fstep ? fstep[j] : j;
+    if (j > 0 && f < (fstep ? fstep[j - 1] : j - 1)) return -1;
+    if (f < t0) j0 = j + 1;
+    else if (f < t1) ++nj;
+  }
+  int* pf = (int*)malloc(sizeof(int) * (size_t)(nj > 0 ? nj : 1));
+  int* pi = (int*)malloc(sizeof(int) * (size_t)(nj > 0 ? nj : 1));
+  int* pr = (int*)malloc(sizeof(int) * (size_t)(nj > 0 ? nj : 1));
+  if (!pf || !pi || !pr) {
+    free(pf);
+    free(pi);
+    free(pr);
+    return -2;
+  }
+  for (int jj = 0; jj < nj; ++jj) {
+    const int j = j0 + jj;
+    pf[jj] = fstep ? fstep[j] : j;
+    pi[jj] = (jj > 0 && pf[jj - 1] == pf[jj]) ? pi[jj - 1] + 1 : 0;
+  }
+  for (int jj = nj - 1; jj >= 0; --jj)
+    pr[jj] = (jj + 1 < nj && pf[jj + 1] == pf[jj]) ? pr[jj + 1] : pi[jj] + 1;
   const int64_t V = (int64_t)nx * ny * nz;
   const int K = prm->k[0] * prm->k[1] * prm->k[2] * prm->k[3];
   float C[4];
@@ -129,10 +164,11 @@ int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, in
         if (fabs((double)f) > fmax) fmax = fabs((double)f);
       }
     }
-  for (int t = 0; t < tw; ++t)
+  for (int jj = 0; jj < nj; ++jj)
     for (int64_t p = 0; p < P; ++p) {
-      const float a = attr[((int64_t)(t0 + t) * A + prm->attr) * P + p];
-      if (key[(int64_t)(t0 + t) * P + p] >= 0 && isfinite(a)) {
+      const int64_t j = j0 + jj;
+      const float a = attr[(j * A + prm->attr) * P + p];
+      if (key[j * P + p] >= 0 && isfinite(a)) {
         ++nvalid;
         if (fabs((double)a) > pmax) pmax = fabs((double)a);
       }
@@ -149,6 +185,9 @@ int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, in
   if (!sums || !prev) {
     free(sums);
     free(prev);
+    free(pf);
+    free(pi);
+    free(pr);
     return -2;
   }
   const float cf = prm->c_f;
@@ -177,17 +216,17 @@ int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, in
           }
           field_label[li] = best;
         }
-  for (int t = 0; t < tw; ++t)
+  for (int jj = 0; jj < nj; ++jj)
     for (int64_t p = 0; p < P; ++p) {
-      const int64_t si = (int64_t)(t0 + t) * P + p;
-      const float a = attr[((int64_t)(t0 + t) * A + prm->attr) * P + p];
-      if (key[si] < 0 || !isfinite(a)) {
-        point_label[(int64_t)t * P + p] = -1;
+      const int64_t j = j0 + jj;
+      const float a = attr[(j * A + prm->attr) * P + p];
+      if (key[j * P + p] < 0 || !isfinite(a)) {
+        point_label[(int64_t)jj * P + p] = -1;
         continue;
       }
-      const float* ps = pos + (int64_t)(t0 + t) * 3 * P;
+      const float* ps = pos + j * 3 * P;
       const float xs = ps[p], ys = ps[P + p], zs = ps[2 * P + p];
-      const float ts = f_add((float)(t0 + t), 0.5f);
+      const float ts = point_time(pf[jj], pi[jj], pr[jj]);
       int best = 0;
       float bd = INFINITY;
       for (int c = 0; c < K; ++c) {
@@ -197,7 +236,7 @@ int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, in
           best = c;
         }
       }
-      point_label[(int64_t)t * P + p] = best;
+      point_label[(int64_t)jj * P + p] = best;
     }
 
   int it = 0;
@@ -220,17 +259,18 @@ int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, in
             s[5] += quant(field[(int64_t)(t0 + t) * V + v], kf);
             s[6] += 1;
           }
-    for (int t = 0; t < tw; ++t)
+    for (int jj = 0; jj < nj; ++jj)
       for (int64_t p = 0; p < P; ++p) {
-        const int c = point_label[(int64_t)t * P + p];
+        const int c = point_label[(int64_t)jj * P + p];
         if (c < 0) continue;
-        const float* ps = pos + (int64_t)(t0 + t) * 3 * P;
+        const int64_t j = j0 + jj;
+        const float* ps = pos + j * 3 * P;
         int64_t* s = sums + 8 * c;
         s[0] += quant(ps[p], kpos);
         s[1] += quant(ps[P + p], kpos);
         s[2] += quant(ps[2 * P + p], kpos);
-        s[3] += quant(f_add((float)(t0 + t), 0.5f), kpos);
-        s[4] += quant(attr[((int64_t)(t0 + t) * A + prm->attr) * P + p], kp);
+        s[3] += quant(point_time(pf[jj], pi[jj], pr[jj]), kpos);
+        s[4] += quant(attr[(j * A + prm->attr) * P + p], kp);
         s[7] += 1;
       }
     for (int c = 0; c < K; ++c) {
@@ -275,14 +315,15 @@ int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, in
             }
             if (best >= 0) field_label[li] = best;
           }
-    for (int t = 0; t < tw; ++t)
+    for (int jj = 0; jj < nj; ++jj)
       for (int64_t p = 0; p < P; ++p) {
-        const int64_t li = (int64_t)t * P + p;
+        const int64_t li = (int64_t)jj * P + p;
         if (point_label[li] < 0) continue;
-        const float a = attr[((int64_t)(t0 + t) * A + prm->attr) * P + p];
-        const float* ps = pos + (int64_t)(t0 + t) * 3 * P;
+        const int64_t j = j0 + jj;
+        const float a = attr[(j * A + prm->attr) * P + p];
+        const float* ps = pos + j * 3 * P;
         const float xs = ps[p], ys = ps[P + p], zs = ps[2 * P + p];
-        const float ts = f_add((float)(t0 + t), 0.5f);
+        const float ts = point_time(pf[jj], pi[jj], pr[jj]);
         int best = -1;
         float bd = INFINITY;
         for (int c = 0; c < K; ++c) {
@@ -306,5 +347,17 @@ int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, in
   *iters = it;
   free(sums);
   free(prev);
+  free(pf);
+  free(pi);
+  free(pr);
   return 0;
+}
+
+/* The clustering with one point step per field step. */
+int oracle_slic(int nx, int ny, int nz, int T, const float* field, int64_t P, int A,
+                const float* pos, const float* attr, const int32_t* key,
+                const orc_slic_params* prm, int32_t* field_label, int32_t* point_label,
+                float* centers, int64_t* counts, int* iters) {
+  return oracle_slic_mr(nx, ny, nz, T, field, P, A, T, NULL, pos, attr, key, prm, field_label,
+                        point_label, centers, counts, iters);
 }

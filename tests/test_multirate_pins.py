@@ -168,3 +168,64 @@ def test_multirate_repeated_steps_reduce_to_one_rate(orc):
     assert np.array_equal(f3["n_pts"], r * f1["n_pts"])
     np.testing.assert_allclose(f3["mean_attr"], f1["mean_attr"], rtol=1e-12)
     np.testing.assert_allclose(f3["std_attr"], f1["std_attr"], rtol=1e-9, atol=1e-12)
+
+
+def test_multirate_cluster_one_centre_time_is_the_step_mean(orc):
+    """§3.2 with points on their own grid, k = 1: the r point steps of field step f sit
+    symmetrically about f + 0.5 (at f + (i + 0.5) / r), so after one update the one centre's time
+    is the mean over all samples of their field step + 0.5, whatever the map (with every point
+    inside the grid); its position is the mean of voxel centres and point positions, and it
+    counts every sample of the window."""
+    rng = np.random.default_rng(41)
+    T, nz, ny, nx, P, A = 4, 3, 5, 6, 40, 2
+    fstep = np.array([0, 0, 0, 1, 2, 2, 2, 2, 2, 3, 3], np.int32)
+    Tp = fstep.size
+    pos, attr = _inputs(rng, Tp, nz, ny, nx, P, A)
+    # every point inside the grid: each point step takes part with all P samples (the symmetry
+    # about f + 0.5 holds for whole point steps)
+    pos = np.stack([rng.uniform(0.05, m - 0.05, (Tp, P)) for m in (nx, ny, nz)],
+                   1).astype(np.float32)
+    field = rng.random((T, nz, ny, nx)).astype(np.float32)
+    b = orc.bin(field.shape, pos, attr, fstep=fstep)
+    t0, t1 = 1, 4
+    fl, pl, c, n, it = orc.slic(field, pos, attr, b["key"], t0, t1, 1, (1, 1, 1, 1),
+                                max_iter=1, fstep=fstep)
+    js = np.nonzero((fstep >= t0) & (fstep < t1))[0]
+    assert pl.shape == (js.size, P)
+    inside = b["key"][js] >= 0
+    assert np.array_equal(pl >= 0, inside) and (pl[inside] == 0).all() and (fl == 0).all()
+    nvox = nz * ny * nx
+    tf = np.repeat(np.arange(t0, t1) + 0.5, nvox)
+    tp = np.repeat(fstep[js] + 0.5, P)[inside.ravel()]
+    assert n[0, 0] == tf.size and n[0, 1] == tp.size
+    np.testing.assert_allclose(float(c[0, 3]), np.concatenate([tf, tp]).mean(), rtol=2e-7)
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    px = pos[js, 0, :].astype(np.float64)[inside]
+    fx = np.tile((xx + 0.5).ravel(), t1 - t0)
+    np.testing.assert_allclose(float(c[0, 0]), np.concatenate([fx, px]).mean(), rtol=2e-7)
+    np.testing.assert_allclose(float(c[0, 4]), attr[js, 1, :].astype(np.float64)[inside].mean(),
+                               rtol=2e-6)
+
+
+@pytest.mark.parametrize("r", [2, 3])
+def test_multirate_cluster_point_steps_join_their_time_seed(orc, r):
+    """k = (1, 1, 1, r tw) on a map of r point steps per field step: the seeds' times,
+    t0 + (m + 0.5) / r, are exactly the point times f + (i + 0.5) / r, and all seeds share one
+    position, so the first assignment puts point step jj of the window (and nothing else) on
+    seed jj; field samples at f + 0.5 lie between two seeds for even r (the tie goes to the
+    lower one) and on seed r (f - t0) + (r - 1) / 2 for odd r."""
+    rng = np.random.default_rng(43 + r)
+    T, nz, ny, nx, P, A = 3, 2, 3, 4, 30, 1
+    fstep = np.repeat(np.arange(T, dtype=np.int32), r)
+    pos, attr = _inputs(rng, fstep.size, nz, ny, nx, P, A)
+    field = rng.random((T, nz, ny, nx)).astype(np.float32)
+    b = orc.bin(field.shape, pos, attr, fstep=fstep)
+    t0, t1 = 1, 3
+    tw = t1 - t0
+    fl, pl, c, n, it = orc.slic(field, pos, attr, b["key"], t0, t1, 0, (1, 1, 1, r * tw),
+                                max_iter=1, fstep=fstep)
+    inside = b["key"][r * t0:r * t1] >= 0
+    want = np.broadcast_to(np.arange(r * tw)[:, None], inside.shape)
+    assert np.array_equal(pl[inside], want[inside]) and (pl[~inside] == -1).all()
+    fwant = r * np.arange(tw) + (r - 1) // 2
+    assert np.array_equal(fl.reshape(tw, -1), np.broadcast_to(fwant[:, None], (tw, nz * ny * nx)))
