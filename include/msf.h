@@ -186,9 +186,10 @@ int msf_load_timesteps(msf_ctx* ctx, int nx, int ny, int nz, int T, const float*
  * of the point steps that fall in t; a trajectory link joins (key[j][p], field_step[j]) and
  * (key[j+1][p], field_step[j+1]) for consecutive point steps (so it may join two voxels of one
  * field step); a feature's point samples are all samples in its voxel-timesteps. The fixed-point
- * scale counts all P * Tp samples. msf_cluster, the point labels of msf_cluster_stats and the
- * voxel label space of msf_split_trajectories take one point step per field step and return
- * MSF_ERR_INVALID_ARG on such a dataset. Errors: those of msf_load_timesteps; INVALID_ARG (a
+ * scale counts all P * Tp samples. msf_cluster takes every point step of its window, the i-th
+ * (0-based) of the r point steps of field step f at time f + (i + 0.5) / r. The point labels of
+ * msf_cluster_stats and the voxel label space of msf_split_trajectories take one point step per
+ * field step and return MSF_ERR_INVALID_ARG on such a dataset. Errors: those of msf_load_timesteps; INVALID_ARG (a
  * map that decreases or leaves [0, T), Tp < 1 with a map, Tp != T without), TOO_LARGE
  * (Tp > 65535). */
 int msf_load_timesteps_mr(msf_ctx* ctx, int nx, int ny, int nz, int T, const float* field,
@@ -284,7 +285,9 @@ int msf_batch_graph_replays(msf_ctx* ctx, int64_t* replays);
  * (§3.2.3), keeping its centre when none does.
  * Readings: a field sample sits at its voxel's centre (x + 0.5, y + 0.5, z + 0.5) and every
  * sample's time is t + 0.5; points take part when binning placed them inside the grid; samples
- * whose value is not finite take no part (label -1); distances and the change test are IEEE fp32
+ * whose value is not finite take no part (label -1); points on their own time grid
+ * (msf_load_timesteps_mr) sit at f + (i + 0.5) / r, the i-th of the r point steps of field step
+ * f, IEEE fp32 in that order; distances and the change test are IEEE fp32
  * operations in the order written, ties go to the lower centre index; centre sums are exact
  * int64 fixed point (scale as in binning), means are (double)sum / n * 2^-k rounded to fp32; a
  * centre without samples keeps its values (without point or field samples: keeps p_c or f_c);
@@ -299,8 +302,9 @@ typedef struct msf_cluster_params {
   int32_t max_iter;     /* most centre updates (>= 1) */
 } msf_cluster_params;
 
-/* Cluster the window. field_labels [t1-t0][nz][ny][nx] and point_labels [t1-t0][P] (int32, host
- * or device per labels_kind, caller-owned, either may be NULL) receive each sample's centre
+/* Cluster the window. field_labels [t1-t0][nz][ny][nx] and point_labels [nj][P] (int32, host
+ * or device per labels_kind, caller-owned, either may be NULL; nj = t1-t0, or for a dataset of
+ * msf_load_timesteps_mr the point steps that fall in the window) receive each sample's centre
  * index (-1 for samples that take no part): the assignment the last centres were computed
  * from. centers (host, may be NULL) receives [K][6] fp32 (x, y, z, t, p_c, f_c) and counts (host,
  * may be NULL) [K][2] int64 (field samples, point samples) of the last update, K = k0*k1*k2*k3;

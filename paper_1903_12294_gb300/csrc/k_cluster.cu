@@ -42,6 +42,7 @@ struct SlicArgs {
   int nx, ny, nz, T, A;
   int64_t V, P;
   int t0, tw;
+  int j0, nj;                   // the window's point steps [j0, j0 + nj)
   int attr;
   int k[4];
   float C[4];
@@ -52,6 +53,8 @@ struct SlicArgs {
   const float* pos;
   const float* attrp;
   const int32_t* key;
+  const int32_t* fstep;         // [Tp] field step of each point step
+  const int32_t* pj0;           // [T + 1] first point step of each field step
   float* centers;               // [K][6] x, y, z, t, p_c, f_c
   float* prev;                  // [K][6]
   unsigned long long* sums;     // [K][8] x, y, z, t, p, f, n_field, n_point
@@ -60,14 +63,24 @@ struct SlicArgs {
   uint32_t* cell_cursor;        // [K]
   uint32_t* cell_items;         // [16 K]
   int32_t* flabel;              // [tw][V]
-  int32_t* plabel;              // [tw][P]
+  int32_t* plabel;              // [nj][P]
   unsigned* moved;
   unsigned long long* valid;    // [0] samples, [1] max|f| bits, [2] max|p| bits
   uint32_t* pcell_start;        // [K + 1] first slot of each cell's point samples
   uint32_t* pcell_cursor;       // [K]
   float4* psample;              // [slots] x, y, z, value of the point sample in the slot
-  uint32_t* pindex;             // [slots] its index t * P + p in the window
+  uint32_t* pindex;             // [slots] its index t * P + p in the window (t: point step)
 };
+
+// Time of window point step t: with r point steps in field step f, the i-th (0-based) sits at
+// f + (i + 0.5) / r, spreading them evenly over the field step's unit of time (one per field
+// step: f + 0.5, as a field sample of step f).
+__device__ __forceinline__ float point_time(const SlicArgs& a, int t) {
+  const int j = a.j0 + t;
+  const int f = __ldg(a.fstep + j);
+  const int p0 = __ldg(a.pj0 + f), r = __ldg(a.pj0 + f + 1) - p0;
+  return __fadd_rn((float)f, __fdiv_rn(__fadd_rn((float)(j - p0), 0.5f), (float)r));
+}
 
 constexpr float kCellMargin = 1e-3f;
 
@@ -147,7 +160,7 @@ __device__ __forceinline__ void warp_accumulate(unsigned long long* sums, int be
 
 // ---- samples that take part, and value ranges ------------------------------------------------
 __global__ void __launch_bounds__(256) k_slic_valid(const __grid_constant__ SlicArgs a) {
-  const int64_t nf = (int64_t)a.tw * a.V, np = (int64_t)a.tw * a.P;
+  const int64_t nf = (int64_t)a.tw * a.V, np = (int64_t)a.nj * a.P;
   unsigned long long n = 0;
   unsigned fm = 0, pm = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf + np;
@@ -160,8 +173,8 @@ __global__ void __launch_bounds__(256) k_slic_valid(const __grid_constant__ Slic
       }
     } else {
       const int64_t j = i - nf, t = j / a.P, p = j - t * a.P;
-      const float v = __ldg(a.attrp + ((a.t0 + t) * a.A + a.attr) * a.P + p);
-      if (__ldg(a.key + (a.t0 + t) * a.P + p) >= 0 && isfinite(v)) {
+      const float v = __ldg(a.attrp + ((a.j0 + t) * a.A + a.attr) * a.P + p);
+      if (__ldg(a.key + (a.j0 + t) * a.P + p) >= 0 && isfinite(v)) {
         ++n;
         pm = max(pm, __float_as_uint(fabsf(v)));
       }
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_field_tiled(const __grid
 
 template <bool INIT>
 __global__ void __launch_bounds__(256, 4) k_slic_assign_points(const __grid_constant__ SlicArgs a) {
-  const int64_t n = (int64_t)a.tw * a.P;
+  const int64_t n = (int64_t)a.nj * a.P;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t li = base + threadIdx.x;
@@ -425,13 +438,13 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_points(const __grid_cons
     if (li < n) {
       const int t = (int)(li / a.P);
       const int64_t p = li - (int64_t)t * a.P;
-      const int64_t si = (int64_t)(a.t0 + t) * a.P + p;
-      const float pv = __ldg(a.attrp + ((int64_t)(a.t0 + t) * a.A + a.attr) * a.P + p);
+      const int64_t si = (int64_t)(a.j0 + t) * a.P + p;
+      const float pv = __ldg(a.attrp + ((int64_t)(a.j0 + t) * a.A + a.attr) * a.P + p);
       const bool take = INIT ? (__ldg(a.key + si) >= 0 && isfinite(pv)) : a.plabel[li] >= 0;
       if (take) {
-        const float* ps = a.pos + (int64_t)(a.t0 + t) * 3 * a.P;
+        const float* ps = a.pos + (int64_t)(a.j0 + t) * 3 * a.P;
         const float xs = __ldg(ps + p), ys = __ldg(ps + a.P + p), zs = __ldg(ps + 2 * a.P + p);
-        const float ts = __fadd_rn((float)(a.t0 + t), 0.5f);
+        const float ts = point_time(a, t);
         best = best_centre<INIT>(a, xs, ys, zs, ts, a.w_p, pv, 4);
         if (!INIT && best < 0) best = a.plabel[li];
         a.plabel[li] = best;
@@ -469,16 +482,16 @@ __device__ __forceinline__ bool point_sample(const SlicArgs& a, int64_t li, floa
   if (a.plabel[li] < 0) return false;
   const int t = (int)(li / a.P);
   const int64_t p = li - (int64_t)t * a.P;
-  const float* ps = a.pos + (int64_t)(a.t0 + t) * 3 * a.P;
+  const float* ps = a.pos + (int64_t)(a.j0 + t) * 3 * a.P;
   s = make_float4(__ldg(ps + p), __ldg(ps + a.P + p), __ldg(ps + 2 * a.P + p),
-                  __ldg(a.attrp + ((int64_t)(a.t0 + t) * a.A + a.attr) * a.P + p));
-  ts = __fadd_rn((float)(a.t0 + t), 0.5f);
+                  __ldg(a.attrp + ((int64_t)(a.j0 + t) * a.A + a.attr) * a.P + p));
+  ts = point_time(a, t);
   return true;
 }
 
 template <bool FILL>
 __global__ void __launch_bounds__(256) k_slic_pgroup(const __grid_constant__ SlicArgs a) {
-  const int64_t n = (int64_t)a.tw * a.P;
+  const int64_t n = (int64_t)a.nj * a.P;
   uint32_t* cursor = a.pcell_cursor;
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < n;
        li += (int64_t)gridDim.x * blockDim.x) {
@@ -576,7 +589,7 @@ __global__ void __launch_bounds__(256, 4) k_slic_assign_points_cells(const __gri
         const uint32_t li = gindex[slot];
         const int t = (int)(li / per_t);
         const float xs = sm.x, ys = sm.y, zs = sm.z, vs = sm.w;
-        const float ts = __fadd_rn((float)(a.t0 + t), 0.5f);
+        const float ts = point_time(a, t);
         if (over) {
           best = best_centre<false>(a, xs, ys, zs, ts, wv, vs, VS);
         } else {
@@ -710,6 +723,8 @@ int cluster_run(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* flabel, in
   a.P = d.A > 0 ? d.P : 0;
   a.t0 = prm->t0;
   a.tw = prm->t1 - prm->t0;
+  a.j0 = d.h_pj0[prm->t0];
+  a.nj = d.h_pj0[prm->t1] - a.j0;
   a.attr = prm->attr;
   for (int i = 0; i < 4; ++i) a.k[i] = prm->k[i];
   a.K = prm->k[0] * prm->k[1] * prm->k[2] * prm->k[3];
@@ -728,6 +743,8 @@ int cluster_run(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* flabel, in
   a.pos = d.pos.as<float>();
   a.attrp = d.attr.as<float>();
   a.key = d.key.as<int32_t>();
+  a.fstep = d.fstep.as<int32_t>();
+  a.pj0 = d.pj0.as<int32_t>();
   MSF_TRY(S.centers.ensure(sizeof(float) * 6 * (size_t)a.K));
   MSF_TRY(S.prev.ensure(sizeof(float) * 6 * (size_t)a.K));
   MSF_TRY(S.sums.ensure(sizeof(unsigned long long) * 8 * (size_t)a.K));
@@ -765,7 +782,7 @@ int cluster_run(msf_ctx* ctx, const msf_cluster_params* prm, int32_t* flabel, in
   a.kf = fixed_scale_host((double)fmax, (long long)hv[0]);
   a.kp = fixed_scale_host((double)pmax, (long long)hv[0]);
   const unsigned kb = (unsigned)((a.K + 255) / 256);
-  const int64_t nfs = (int64_t)a.tw * a.V, nps = (int64_t)a.tw * a.P;
+  const int64_t nfs = (int64_t)a.tw * a.V, nps = (int64_t)a.nj * a.P;
   const unsigned gf = (unsigned)std::min<int64_t>((nfs + 255) / 256, (int64_t)ctx->sm_count * 32);
   const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nps + 255) / 256,
                                                                        (int64_t)ctx->sm_count * 32));

@@ -576,10 +576,10 @@ int msf_cluster(msf_ctx* c, const msf_cluster_params* prm, int32_t* field_labels
   if (d.P > 0) {
     if (prm->attr < 0 || prm->attr >= d.A) return MSF_ERR_INVALID_ARG;
     if (!d.binned) return MSF_ERR_NOT_BINNED;
-    if (d.multirate) return MSF_ERR_INVALID_ARG;  // point labels are [tw][P]: one step each
   }
   const int64_t tw = prm->t1 - prm->t0;
-  const int64_t nf = tw * d.V, np = tw * d.P;
+  const int64_t nj = d.h_pj0[prm->t1] - d.h_pj0[prm->t0];  // the window's point steps
+  const int64_t nf = tw * d.V, np = nj * d.P;
   if (nf >= ((int64_t)1 << 31) || np >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
   MSF_CUDA_TRY(cudaSetDevice(c->device));
   MSF_TRY(ctx_field_ready(c));

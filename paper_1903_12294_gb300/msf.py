@@ -661,6 +661,11 @@ class Context:
         self.P = pos.shape[2] if pos is not None else 0
         self.A = attr.shape[1] if attr is not None else 0
         self.Tp = pos.shape[0] if pos is not None else self.shape[0]
+        T = self.shape[0]
+        fs = (np.arange(self.Tp) if field_step is None
+              else np.asarray(field_step, dtype=np.int64).reshape(-1))
+        # first point step of each field step, [T + 1]
+        self.pj0 = np.searchsorted(fs, np.arange(T + 1), side="left").astype(np.int64)
 
     def bin(self, keep_sumq=False):
         return msf_bin_particles(self.h, MSF_BIN_KEEP_SUMQ if keep_sumq else 0)
@@ -705,13 +710,15 @@ class Context:
 
     def cluster(self, t0, t1, attr, k, w_p=1.0, w_f=1.0, w_d=1.0, c_f=1.0, eps_c=1e-3,
                 max_iter=10):
-        """§3.2 clustering of the window; returns (field labels, point labels) device tensors,
-        centers [K][6], counts [K][2] and the number of centre updates."""
+        """§3.2 clustering of the window; returns (field labels [t1-t0][nz][ny][nx], point labels
+        [nj][P] over the window's point steps) device tensors, centers [K][6], counts [K][2] and
+        the number of centre updates."""
         import torch
         T, nz, ny, nx = self.shape
         dev = f"cuda:{self.device}"
         fl = torch.empty((t1 - t0, nz, ny, nx), dtype=torch.int32, device=dev)
-        pl = torch.empty((t1 - t0, max(self.P, 1)), dtype=torch.int32, device=dev)[:, :self.P]
+        nj = int(self.pj0[t1] - self.pj0[t0])  # the point steps that fall in the window
+        pl = torch.empty((nj, max(self.P, 1)), dtype=torch.int32, device=dev)[:, :self.P]
         prm = make_cluster_params(t0, t1, attr, k, w_p, w_f, w_d, c_f, eps_c, max_iter)
         centers, counts, it = msf_cluster(self.h, prm, fl, pl.contiguous() if self.P else None)
         return fl, pl, centers, counts, it

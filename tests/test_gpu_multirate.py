@@ -84,15 +84,50 @@ def test_multirate_batched_matches_oracle(gpu, orc):
         assert n == n_ref and np.array_equal(lab, ref), (t0, t1, e)
 
 
+@pytest.mark.parametrize("mapping,k,t0,t1", [("even", (4, 4, 4, 3), 0, 8),
+                                             ("uneven", (3, 5, 2, 4), 2, 8),
+                                             ("uneven", (5, 3, 3, 1), 5, 6)])
+def test_multirate_cluster_matches_oracle(gpu, orc, mapping, k, t0, t1):
+    """§3.2 clustering with points on their own grid (the i-th of the r point steps of field
+    step f at time f + (i + 0.5) / r): field and point labels, centres (bit-exact), counts and
+    updates as the oracle's; point labels cover the window's point steps. The uneven map holds
+    field steps with one, several and no point steps."""
+    fs = None if mapping == "even" else [0, 0, 1, 1, 1, 1, 1, 3, 3, 4, 5, 5, 5, 6, 7, 7, 7, 7]
+    wl = synth.multirate(n=24, T=8, r=3, P=6000, field_step=fs)
+    f, p, a = wl.numpy()
+    fstep = np.asarray(wl.field_step, np.int32)
+    kw = dict(w_p=2.0, w_f=1.0, w_d=0.2, c_f=1.5, eps_c=1e-3, max_iter=7)
+    ctx = _load(gpu, wl)
+    try:
+        ctx.bin()
+        fl, pl, c, n, it = ctx.cluster(t0, t1, 0, k, **kw)
+        torch.cuda.synchronize()
+        key = ctx.bins("cpu")[0].numpy()
+        g = (fl.cpu().numpy(), pl.cpu().numpy(), c, n, it)
+    finally:
+        ctx.close()
+    o = orc.slic(f, p, a, key, t0, t1, 0, k, fstep=fstep, **kw)
+    nj = int(np.count_nonzero((fstep >= t0) & (fstep < t1)))
+    assert g[1].shape == (nj, p.shape[2]) and o[1].shape == g[1].shape
+    assert g[4] == o[4]
+    assert np.array_equal(g[0], o[0])
+    assert np.array_equal(g[1], o[1])
+    assert np.array_equal(g[2].view(np.uint32), o[2].view(np.uint32))
+    assert np.array_equal(g[3], o[3])
+    assert g[3][:, 1].sum() == np.count_nonzero(g[1] >= 0) > 0
+
+
 def test_multirate_refusals(gpu):
-    """The steps that take one point step per field step refuse a dataset on its own grid; a
-    map that decreases is refused at load."""
+    """The steps that take one point step per field step (point labels of msf_cluster_stats)
+    refuse a dataset on its own grid; a map that decreases is refused at load."""
     wl = synth.multirate(n=16, T=4, r=2, P=500)
     ctx = _load(gpu, wl)
     try:
         ctx.bin()
+        fl, pl, c, n, it = ctx.cluster(0, 4, 0, (2, 2, 2, 1))
+        assert pl.shape == (8, 500)
         with pytest.raises(gpu.MsfError):
-            ctx.cluster(0, 4, 0, (2, 2, 2, 1))
+            ctx.cluster_stats(0, 4, 0, fl, pl, 8)
         with pytest.raises(gpu.MsfError):
             ctx.load(wl.field.cuda(), wl.pos.cuda(), wl.attr.cuda(),
                      field_step=[0, 1, 0, 2, 2, 3, 3, 3])
