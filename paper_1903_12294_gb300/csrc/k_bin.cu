@@ -10,21 +10,20 @@
 // Schedule: a counting sort of the samples by voxel range ("bucket" of R consecutive voxels),
 // so that the per-voxel sums are formed in shared memory rather than with global atomics
 // (scattered L2 atomics run at a fixed rate that would bound the whole pass):
-//   k_bin_keys     one thread per 4 samples of one timestep: key[t][p], and per block a shared-
-//                  memory histogram of buckets merged into hist[t][bucket]
-//   scan           offsets[t][bucket] = exclusive prefix of hist
-//   k_bin_place    one CTA per 4096 samples of one point step: the block's keys and attributes
-//                  arrive in shared memory by bulk asynchronous copy while the block reads its
-//                  slot ranges; the block sorts its samples by bucket in shared memory and writes
-//                  (voxel, attributes) records run by run; also the largest finite |v| per
-//                  attribute
+//   k_bin_keys     one thread per 4 samples of one point step: key[j][p], and per block (at least
+//                  eight samples per bucket) a shared-memory histogram of buckets, added into
+//                  hist[field step][bucket]
+//   scan           offsets = exclusive prefix of hist (every bucket's slot range)
+//   k_bin_place    one CTA per 8192 samples of one point step: each sample, read in order, takes
+//                  its bucket's next slot (one global cursor per bucket) and is stored there as a
+//                  (voxel, attributes) record; also the largest finite |v| per attribute
 //
 // Point samples may come on a finer time grid than the field (point step j falls in field step
 // fstep[j]); the records of all point steps of a field step go to that step's buckets.
-//   k_bin_reduce   one CTA per (bucket, timestep): its records arrive by bulk copy while the
-//                  accumulators are cleared; counts and fixed-point sums in shared memory, means
-//                  of the non-empty voxels into shared memory, then one vector store pass of
-//                  count and mean (and the sums) for all R voxels
+//   k_bin_reduce   one CTA per (bucket, field step): its records arrive by bulk copy while the
+//                  counters are cleared; a counting sort by voxel in shared memory; counts with
+//                  NaN means stored for every voxel, then the sums and means of the non-empty
+//                  voxels (one lane each) stored over them
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -53,18 +52,18 @@ struct BinArgs {
   int64_t scale_n;              // point samples the fixed-point scale counts (P * Tp, or a
                                 // whole dataset's when binning one slab of it)
   int logR, nb;                 // bucket = voxel >> logR; nb buckets
-  int nblk;                     // sample blocks per timestep
-  int64_t chunk;                // samples per block
+  int nblk;                     // sample blocks per point step of the keys pass
+  int64_t chunk;                // samples per block of the keys pass
   const uint32_t* nrec;         // device: records in all (samples inside the grid); null = none
-  int64_t NRp;                  // stride of rec_a between attributes (P*T rounded up to 4)
   const float* pos;             // [T][3][P]
   const float* attr;            // [T][A][P]
   int32_t* key;                 // [T][P]
-  uint32_t* hist;               // samples per (field step, bucket, point step, block)
-  uint32_t* offs;               // exclusive prefix of hist (slot ranges)
-  uint32_t* cursor;             // running fill positions (global-histogram fallback)
-  uint32_t* rec_v;              // [P*Tp] voxel of the sample (+4 slack for rounded bulk copies)
-  float* rec_a;                 // [A][NRp] attribute values (+4 slack)
+  uint32_t* hist;               // [T][nb] samples per (field step, bucket)
+  uint32_t* offs;               // [T][nb] exclusive prefix of hist (slot ranges)
+  uint32_t* cursor;             // [T][nb] next free slot, from offs
+  uint2* rec_vn;                // [P*Tp] the sample's voxel, and the same point's voxel at the
+                                // next point step (-1 at the last or outside the grid)
+  float* rec_a;                 // [P*Tp][rec_aw(A)] attribute values (+4 slack)
   unsigned* err;                // bounded waits that gave up
   uint32_t* ovf;                // items (t * nb + bucket) left to the wide reduce
   uint32_t* novf;               // their number
@@ -85,13 +84,22 @@ __host__ __device__ __forceinline__ int scale_exponent_bits(unsigned mbits, long
     if (E) {
       e = E - 126;
     } else {
+#ifdef __CUDA_ARCH__
+      const int L = 32 - __clz((int)mbits);
+#else
       int L = 0;
       for (unsigned m = mbits; m; m >>= 1) ++L;
+#endif
       e = L - 149;
     }
   }
+  // b = the bit length of n (n >= 0): the smallest b with 2^b > n
+#ifdef __CUDA_ARCH__
+  const int b = n > 0 ? 64 - __clzll(n) : 0;
+#else
   int b = 0;
   while (((long long)1 << b) < n + 1) ++b;
+#endif
   return 62 - e - b;
 }
 
@@ -133,25 +141,17 @@ __device__ __forceinline__ float div_count(float x, int c) {
   return __fdiv_rn(x, __int2float_rn(c));
 }
 
-// Histogram slot of (point step j, bucket, block): ordered by field step, then bucket, then the
-// field step's point steps, then block, so that one exclusive scan lays the records out by
-// (field step, bucket), every point step and block of the field step taking its own range.
-// With one point step per field step this is (t * nb + bucket) * nblk + blk.
-__device__ __forceinline__ int64_t hist_index(const BinArgs& b, int j, int bucket, int blk) {
-  const int t = __ldg(b.fstep + j);
-  const int p0 = __ldg(b.pj0 + t), r = __ldg(b.pj0 + t + 1) - p0;
-  return (((int64_t)p0 * b.nb + (int64_t)bucket * r) + (j - p0)) * b.nblk + blk;
-}
-
 // ---------------------------------------------------------------------------------------------
 // pass 1: keys and the per-block bucket histograms
 // ---------------------------------------------------------------------------------------------
-// Block blk of point step j owns samples [blk * chunk, (blk + 1) * chunk). Its histogram goes to
-// hist[hist_index(j, bucket, blk)], so one exclusive scan yields every block's slot range.
+// Block blk of point step j owns samples [blk * chunk, (blk + 1) * chunk). Its histogram is added
+// into hist[fstep[j]][bucket] (one atomic per non-empty bucket), so that one exclusive scan
+// yields every bucket's slot range, all point steps of a field step together.
 template <bool SMEM>
 __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArgs b) {
   __shared__ uint32_t s_hist[SMEM ? kHistSmem : 1];
   const int t = blockIdx.y, blk = blockIdx.x;  // t: the point step
+  uint32_t* hrow = b.hist + (int64_t)__ldg(b.fstep + t) * b.nb;
   if (SMEM) {
     for (int i = threadIdx.x; i < b.nb; i += 256) s_hist[i] = 0u;
     __syncthreads();
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArg
       } else if (SMEM) {
         atomicAdd(s_hist + (k >> b.logR), 1u);
       } else {
-        atomicAdd(b.hist + hist_index(b, t, k >> b.logR, blk), 1u);
+        atomicAdd(hrow + (k >> b.logR), 1u);
       }
     }
   }
@@ -189,154 +189,96 @@ __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArg
   if ((threadIdx.x & 31) == 0 && tot) atomicAdd(b.outside + t, (unsigned long long)tot);
   if (SMEM) {
     __syncthreads();
-    for (int i = threadIdx.x; i < b.nb; i += 256) b.hist[hist_index(b, t, i, blk)] = s_hist[i];
+    for (int i = threadIdx.x; i < b.nb; i += 256)
+      if (s_hist[i]) atomicAdd(hrow + i, s_hist[i]);
   }
 }
 
 // ---------------------------------------------------------------------------------------------
 // pass 2: records in bucket order (and the attribute maxima)
 // ---------------------------------------------------------------------------------------------
-// The block's keys (an aligned-down, rounded-up span of its row) come into shared memory by bulk
-// asynchronous copy while the threads read the block's slot ranges and take the attribute
-// maxima (coalesced reads). The block then sorts its samples by bucket in shared memory (a
-// counting sort against its own histogram, through an index permutation) and writes each
-// bucket's run to its slot range, gathering the attributes of the sorted samples from its own
-// rows (read a moment earlier: cache hits), so that a warp's stores land in a few contiguous runs
-// rather than 32 scattered sectors. Keeping the attributes out of shared memory lets more blocks
-// share an SM on grids with many buckets.
-constexpr int kPlaceChunk = 4096;              // samples per block in the shared-memory path
-constexpr int kPlaceChunkWide = 8192;          // the same on grids with many buckets (half the
-                                               // histogram entries of the keys and scan passes)
-constexpr int kPlaceSmemMax = 200 * 1024;
-
-template <int A>
-__global__ void __launch_bounds__(kBinNT, 2) k_bin_place_sorted(const __grid_constant__ BinArgs b) {
-  extern __shared__ __align__(16) uint32_t s_place[];
-  const int stage = (int)b.chunk + 8;                                      // keys + slack
-  int32_t* s_key = reinterpret_cast<int32_t*>(s_place);                   // [stage]
-  uint16_t* s_inv = reinterpret_cast<uint16_t*>(s_place + stage);          // [chunk]
-  uint32_t* s_delta = s_place + stage + (int)b.chunk / 2;                  // [nb] slot - local
-  uint32_t* s_lpos = s_delta + b.nb;                                       // [nb] fill cursor
-  __shared__ __align__(8) uint64_t s_bar;
-  __shared__ unsigned s_max[A > 0 ? A : 1];
-  __shared__ int s_warp[kBinNT / 32];
-  __shared__ int s_n;
-  const int t = blockIdx.y, blk = blockIdx.x;  // t: the point step
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t pbeg = (int64_t)blk * b.chunk;
-  const int n = (int)min((int64_t)b.chunk, b.P - pbeg);
-  // element offset of the block's key row and its misalignment (elements before the row start
-  // that the aligned-down copy brings in)
-  const int64_t ek = (int64_t)t * b.P + pbeg;
-  const int hk = (int)(ek & 3);
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar, 1);
-    const uint32_t bytes = (uint32_t)(((hk + n + 3) & ~3) * 4);
-    mbar_expect_tx(&s_bar, bytes);
-    bulk_g2s(s_key, b.key + (ek - hk), bytes, &s_bar);
-  }
-  if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
-  // the block's slot ranges and bucket counts (overlapping the copy)
-  for (int i = threadIdx.x; i < b.nb; i += kBinNT) {
-    const int64_t h = hist_index(b, t, i, blk);
-    s_delta[i] = b.offs[h];
-    s_lpos[i] = b.hist[h];  // counts, scanned below
-  }
-  __syncthreads();  // the maxima cleared before any warp adds to them
-  // largest finite |v| of every attribute over the block's samples (coalesced)
-  const float* arow = b.attr + (int64_t)t * A * b.P + pbeg;
-#pragma unroll
-  for (int a = 0; a < A; ++a) {
-    unsigned lmax = 0u;
-    for (int i = threadIdx.x; i < n; i += kBinNT) {
-      const float v = __ldg(arow + (int64_t)a * b.P + i);
-      if (isfinite(v)) lmax = max(lmax, __float_as_uint(fabsf(v)));
-    }
-    const unsigned m = __reduce_max_sync(0xFFFFFFFFu, lmax);
-    if (lane == 0 && m) atomicMax(s_max + a, m);
-  }
-  __syncthreads();
-  // exclusive scan of the block's bucket counts (one thread per chunk of buckets); s_delta
-  // becomes global slot minus local position
-  {
-    const int per = (b.nb + kBinNT - 1) / kBinNT;
-    const int lo = threadIdx.x * per, hi = min(lo + per, b.nb);
-    int tot = 0;
-    for (int i = lo; i < hi; ++i) tot += (int)s_lpos[i];
-    int x = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    int run = x - tot;
-    for (int k = 0; k < w; ++k) run += s_warp[k];
-    if (threadIdx.x == kBinNT - 1) s_n = run + tot;
-    for (int i = lo; i < hi; ++i) {
-      const int c = (int)s_lpos[i];
-      s_lpos[i] = (uint32_t)run;
-      s_delta[i] -= (uint32_t)run;
-      run += c;
-    }
-  }
-  const bool ok = mbar_wait(&s_bar, 0, b.wait_cycles);
-  if (__syncthreads_or(!ok)) {  // the copy did not arrive in time
-    if (threadIdx.x == 0) {
-      atomicAdd(b.err, 1u);
-      mbar_wait(&s_bar, 0);      // let the copy still in flight land before the block exits
-    }
-    return;
-  }
-  // counting sort: s_inv[local position] = sample
-  for (int i = threadIdx.x; i < n; i += kBinNT) {
-    const int32_t k = s_key[hk + i];
-    if (k >= 0) {
-      const uint32_t pos = atomicAdd(s_lpos + (k >> b.logR), 1u);
-      s_inv[pos] = (uint16_t)i;
-    }
-  }
-  __syncthreads();
-  // runs out: local position j of bucket bk goes to slot s_delta[bk] + j
-  const int nr = s_n;
-  for (int j = threadIdx.x; j < nr; j += kBinNT) {
-    const int i = s_inv[j];
-    const int32_t k = s_key[hk + i];
-    const uint32_t slot = s_delta[k >> b.logR] + (uint32_t)j;
-    b.rec_v[slot] = (uint32_t)k;
-#pragma unroll
-    for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * b.NRp + slot] = __ldg(arow + (int64_t)a * b.P + i);
-  }
-  if ((int)threadIdx.x < A && s_max[threadIdx.x]) atomicMax(b.absmax + threadIdx.x, s_max[threadIdx.x]);
+// A record is the sample's voxel with the same point's voxel at the next point step (rec_vn, 8
+// bytes: what a trajectory link joins) and its attributes (rec_a, A values padded to 1, 2, 4 or
+// 8 words so that one vector store writes them). The block reads its samples in order
+// (coalesced keys and attributes, several per thread in flight) and sends each to the next free
+// slot of its bucket, taken from one global cursor per (field step, bucket). Records thus fill
+// every bucket's range front to back in the order they arrive from all blocks, so a partly
+// written sector is completed within microseconds while it is still in L2 (per-block slot
+// ranges would leave one partial sector per block and bucket open for a block's whole life and
+// push them out to DRAM half-written). The order within a bucket changes nothing downstream:
+// counts and fixed-point sums are exact.
+__host__ __device__ constexpr int rec_aw(int A) {
+  return A <= 0 ? 0 : A == 1 ? 1 : A == 2 ? 2 : A <= 4 ? 4 : 8;
 }
 
-// Fallback for many buckets (global histogram): one slot atomic per sample.
+constexpr int kPlaceNT = 512;                  // threads per block of the place pass
+constexpr int kPlacePer = 4;                   // samples per thread in flight
+constexpr int kPlaceChunk = 8192;              // samples per block of the place pass
+constexpr int kChunkMax = 65536;               // samples per block of the keys pass, at most
+
 template <int A>
-__global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant__ BinArgs b) {
+__device__ __forceinline__ float attr_or_zero(const float (&av)[A > 0 ? A : 1], int a) {
+  return a < A ? av[a < A ? a : 0] : 0.f;
+}
+
+template <int A>
+__device__ __forceinline__ void put_record(const BinArgs& b, uint32_t slot, int32_t k, int32_t kn,
+                                           const float (&av)[A > 0 ? A : 1]) {
+  constexpr int AW = rec_aw(A);
+  b.rec_vn[slot] = make_uint2((uint32_t)k, (uint32_t)kn);
+  float* dst = b.rec_a + (size_t)slot * AW;
+  if constexpr (AW == 1) {
+    dst[0] = av[0];
+  } else if constexpr (AW == 2) {
+    *reinterpret_cast<float2*>(dst) = make_float2(av[0], attr_or_zero<A>(av, 1));
+  } else if constexpr (AW == 4) {
+    *reinterpret_cast<float4*>(dst) = make_float4(av[0], attr_or_zero<A>(av, 1),
+                                                  attr_or_zero<A>(av, 2), attr_or_zero<A>(av, 3));
+  } else if constexpr (AW == 8) {
+    *reinterpret_cast<float4*>(dst) = make_float4(av[0], attr_or_zero<A>(av, 1),
+                                                  attr_or_zero<A>(av, 2), attr_or_zero<A>(av, 3));
+    *reinterpret_cast<float4*>(dst + 4) = make_float4(attr_or_zero<A>(av, 4), attr_or_zero<A>(av, 5),
+                                                      attr_or_zero<A>(av, 6), attr_or_zero<A>(av, 7));
+  }
+}
+
+template <int A>
+__global__ void __launch_bounds__(kPlaceNT) k_bin_place(const __grid_constant__ BinArgs b) {
   __shared__ unsigned s_max[A > 0 ? A : 1];
-  const int t = blockIdx.y, blk = blockIdx.x;  // t: the point step
+  const int j = blockIdx.y, blk = blockIdx.x;  // j: the point step
+  uint32_t* crow = b.cursor + (int64_t)__ldg(b.fstep + j) * b.nb;
   if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
-  const int64_t pbeg = (int64_t)blk * b.chunk;
-  const int64_t pend = min(pbeg + b.chunk, b.P);
+  const int64_t pbeg = (int64_t)blk * kPlaceChunk;
+  const int64_t pend = min(pbeg + kPlaceChunk, b.P);
+  const int32_t* krow = b.key + (int64_t)j * b.P;
+  const bool nxt = j + 1 < b.Tp;  // the next point step's keys follow this step's row
+  const float* arow = b.attr + (int64_t)j * A * b.P;
   unsigned lmax[A > 0 ? A : 1];
 #pragma unroll
-  for (int a = 0; a < A; ++a) lmax[a] = 0u;
-  for (int64_t p = pbeg + threadIdx.x; p < pend; p += 256) {
-    const int32_t k = __ldcs(b.key + (int64_t)t * b.P + p);
-    float av[A > 0 ? A : 1];
+  for (int a = 0; a < (A > 0 ? A : 1); ++a) lmax[a] = 0u;
+  for (int64_t q0 = pbeg + threadIdx.x; q0 < pend; q0 += (int64_t)kPlaceNT * kPlacePer) {
+    int32_t k[kPlacePer], kn[kPlacePer];
+    float av[kPlacePer][A > 0 ? A : 1];
 #pragma unroll
-    for (int a = 0; a < A; ++a) {
-      av[a] = __ldcs(b.attr + ((int64_t)t * A + a) * b.P + p);
-      if (isfinite(av[a])) lmax[a] = max(lmax[a], __float_as_uint(fabsf(av[a])));
+    for (int u = 0; u < kPlacePer; ++u) {
+      const int64_t p = q0 + (int64_t)u * kPlaceNT;
+      const bool in = p < pend;
+      k[u] = in ? __ldcs(krow + p) : -1;
+      kn[u] = (in && nxt) ? __ldg(krow + b.P + p) : -1;
+#pragma unroll
+      for (int a = 0; a < (A > 0 ? A : 1); ++a)
+        av[u][a] = (in && A > 0) ? __ldcs(arow + (int64_t)a * b.P + p) : 0.f;
     }
-    if (k < 0) continue;
-    const int bk = k >> b.logR;
-    const uint32_t slot = atomicAdd(b.cursor + hist_index(b, t, bk, blk), 1u);
-    b.rec_v[slot] = (uint32_t)k;
 #pragma unroll
-    for (int a = 0; a < A; ++a) b.rec_a[(int64_t)a * b.NRp + slot] = av[a];
+    for (int u = 0; u < kPlacePer; ++u) {
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+        if (isfinite(av[u][a])) lmax[a] = max(lmax[a], __float_as_uint(fabsf(av[u][a])));
+      if (k[u] < 0) continue;
+      const uint32_t slot = atomicAdd(crow + (k[u] >> b.logR), 1u);
+      put_record<A>(b, slot, k[u], kn[u], av[u]);
+    }
   }
 #pragma unroll
   for (int a = 0; a < A; ++a) {
@@ -350,54 +292,118 @@ __global__ void __launch_bounds__(256) k_bin_place_atomic(const __grid_constant_
 // ---------------------------------------------------------------------------------------------
 // pass 3: per (bucket, timestep) counts, sums, means
 // ---------------------------------------------------------------------------------------------
-// Shared memory: sums [A][R] u64, counts [R] u32, then a staging area of R * (1 + A) words that
-// first holds the bucket's records (rec_v, rec_a per attribute; R words each, in pieces when the
-// bucket has more) and afterwards the means [A][R] f32 and the non-empty voxel list [R].
-// Bulk copies of records [a0, a0 + n) (n a multiple of 4) into the staging area.
+// Bulk copies of records [a0, a0 + n) (a0 and n multiples of 4) into a staging area.
 template <int A>
 __device__ __forceinline__ void reduce_issue(const BinArgs& b, uint32_t a0, uint32_t n,
-                                             uint32_t* s_stv, float* s_sta, int R, uint64_t* bar) {
-  const uint32_t bytes = 4u * n;
-  mbar_expect_tx(bar, bytes * (1 + A));
-  bulk_g2s(s_stv, b.rec_v + a0, bytes, bar);
-#pragma unroll
-  for (int a = 0; a < A; ++a) bulk_g2s(s_sta + (size_t)a * R, b.rec_a + a * b.NRp + a0, bytes, bar);
+                                             uint2* s_stv, float* s_sta, uint64_t* bar) {
+  constexpr int AW = rec_aw(A);
+  mbar_expect_tx(bar, 4u * n * (2 + AW));
+  bulk_g2s(s_stv, b.rec_vn + a0, 8u * n, bar);
+  if (AW) bulk_g2s(s_sta, b.rec_a + (size_t)a0 * AW, 4u * n * AW, bar);
 }
 
 // record range [r0, r1) of the item (field step t, bucket): the slots of its point steps
 __device__ __forceinline__ void item_range(const BinArgs& b, int t, int bucket, uint32_t nrec,
                                            uint32_t& r0, uint32_t& r1) {
   r0 = r1 = 0u;
-  const int p0 = __ldg(b.pj0 + t), r = __ldg(b.pj0 + t + 1) - p0;
-  if (!nrec || r == 0) return;
-  const int64_t h0 = ((int64_t)p0 * b.nb + (int64_t)bucket * r) * b.nblk;
-  const int64_t h1 = h0 + (int64_t)r * b.nblk;  // the next bucket's (or step's) first slot
-  const int64_t TB = (int64_t)b.Tp * b.nb * b.nblk;
-  r0 = __ldg(b.offs + h0);
-  r1 = h1 < TB ? __ldg(b.offs + h1) : nrec;
+  if (!nrec) return;
+  const int64_t h = (int64_t)t * b.nb + bucket;
+  r0 = __ldg(b.offs + h);
+  r1 = h + 1 < (int64_t)b.T * b.nb ? __ldg(b.offs + h + 1) : nrec;
+}
+
+// the fixed-point exponent of attribute a and the two exact factors of 2^-k
+__device__ __forceinline__ void item_scale(const BinArgs& b, int a, int* s_k, float* s_f1,
+                                           float* s_f2) {
+  const int k = scale_exponent_bits(b.absmax[a], (long long)b.scale_n);
+  s_k[a] = k;
+  s_f1[a] = pow2f(-(k / 2));
+  s_f2[a] = pow2f(-(k - k / 2));
+}
+
+// The staged attribute values of record q, as AW words.
+template <int A>
+__device__ __forceinline__ void staged_attrs(const float* s_sta, int q, float (&v)[A > 0 ? A : 1]) {
+  constexpr int AW = rec_aw(A);
+  if constexpr (AW == 1) {
+    v[0] = s_sta[q];
+  } else if constexpr (AW == 2) {
+    const float2 x = reinterpret_cast<const float2*>(s_sta)[q];
+    v[0] = x.x;
+    if (A > 1) v[A > 1 ? 1 : 0] = x.y;
+  } else if constexpr (AW == 4) {
+    const float4 x = reinterpret_cast<const float4*>(s_sta)[q];
+    const float w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int a = 0; a < A; ++a) v[a] = w[a];
+  } else if constexpr (AW == 8) {
+    const float4 x = reinterpret_cast<const float4*>(s_sta)[2 * q];
+    const float4 y = reinterpret_cast<const float4*>(s_sta)[2 * q + 1];
+    const float w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int a = 0; a < A; ++a) v[a] = w[a];
+  }
+}
+
+// Count, NaN mean (and zero sum) of four consecutive voxels v.. of field step t; the tail of a
+// grid whose voxel count is not a multiple of four takes scalar stores.
+template <int A, bool KEEP>
+__device__ __forceinline__ void store_empty4(const BinArgs& b, int t, int64_t v, int nleft,
+                                             uint4 c4) {
+  const float qnan = __int_as_float(0x7fc00000);
+  if ((b.V & 3) == 0) {  // v is then a multiple of four and all four exist
+    __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v), c4);
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
+      __stcs(reinterpret_cast<float4*>(b.mean + o), make_float4(qnan, qnan, qnan, qnan));
+      if (KEEP) {
+        __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2(0, 0));
+        __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2), make_longlong2(0, 0));
+      }
+    }
+  } else {
+    const uint32_t cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (e >= nleft) break;
+      __stcs(b.count + (int64_t)t * b.V + v + e, (int)cc[e]);
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const int64_t o = ((int64_t)a * b.T + t) * b.V + v + e;
+        __stcs(b.mean + o, qnan);
+        if (KEEP) __stcs(b.sumq + o, 0ll);
+      }
+    }
+  }
 }
 
 // One block per item (field step t, bucket): the bucket's records (at most kRedStage of them)
-// arrive by one bulk copy while the voxel counts are cleared; the block counts the records per
+// arrive by bulk copy while the voxel counters are cleared; the block counts the records per
 // voxel (32-bit shared atomics), turns the counts into each voxel's range by a block scan, and
-// sorts the records into those ranges (an index permutation); each thread then owns four
-// consecutive voxels, sums their records' fixed-point values in registers, forms the means and
-// stores counts and means with 16-byte stores. A bucket with more records than the staging area
-// holds is listed for k_bin_reduce_wide and left to it.
+// sorts the records into those ranges (an index permutation). The scan's pass, four voxels per
+// thread, also stores every voxel's count with a NaN mean (16-byte stores) and lists the
+// non-empty voxels block-wide, those with one record apart from the others; the block's threads
+// then take the listed voxels one each, so that means and fixed-point sums are formed only where
+// there are samples, with all lanes busy, and stored over the NaN (ordered after it by the block
+// barrier). A bucket with more records than the staging area holds is listed for
+// k_bin_reduce_wide and left to it.
 constexpr int kRedStage = 2048;  // records staged per bucket (plus alignment slack)
 
 template <int A, bool KEEP>
-__global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant__ BinArgs b) {
+__global__ void __launch_bounds__(kBinNT, A <= 4 ? 3 : 2) k_bin_reduce(const __grid_constant__ BinArgs b) {
+  constexpr int AW = rec_aw(A);
+  constexpr int SS = kRedStage + 8;                                      // staged records
   extern __shared__ __align__(16) uint32_t s_red[];
-  constexpr int SS = kRedStage + 8;                                      // staged elements
   const int R = 1 << b.logR;
-  uint32_t* s_stv = s_red;                                               // [SS] voxels
-  float* s_sta = reinterpret_cast<float*>(s_red + SS);                   // [A][SS] values
-  uint32_t* s_cnt = s_red + (1 + A) * SS;                                // [R] counts
-  uint32_t* s_end = s_cnt + R;                                           // [R] range ends
-  uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_end + R);              // [SS] sorted records
+  float* s_sta = reinterpret_cast<float*>(s_red);                       // [SS][AW] values
+  uint2* s_stv = reinterpret_cast<uint2*>(s_red + SS * AW);              // [SS] voxel pairs
+  uint32_t* s_pos = s_red + SS * (AW + 2);                               // [R] counts, then ends
+  uint16_t* s_idx = reinterpret_cast<uint16_t*>(s_pos + R);              // [SS] sorted records
+  uint16_t* s_list1 = s_idx + SS;                                        // [R] one-record voxels
+  uint16_t* s_list2 = s_list1 + R;                                       // [R] the others
   __shared__ __align__(8) uint64_t s_bar;
-  __shared__ int s_warp[kBinNT / 32];
+  __shared__ int2 s_warp2[kBinNT / 32];
   __shared__ int s_k[A > 0 ? A : 1];
   __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
   const int bucket = blockIdx.x, t = blockIdx.y;  // t: the field step
@@ -412,16 +418,11 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
   const bool any = r1 > r0;
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
-    if (any) reduce_issue<A>(b, s0, e1 - s0, s_stv, s_sta, SS, &s_bar);
+    if (any) reduce_issue<A>(b, s0, e1 - s0, s_stv, s_sta, &s_bar);
   }
-  if ((int)threadIdx.x < A) {
-    const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.scale_n);
-    s_k[threadIdx.x] = k;
-    s_f1[threadIdx.x] = pow2f(-(k / 2));
-    s_f2[threadIdx.x] = pow2f(-(k - k / 2));
-  }
+  if ((int)threadIdx.x < A) item_scale(b, threadIdx.x, s_k, s_f1, s_f2);
   for (int q = threadIdx.x; q < R / 4; q += kBinNT)
-    reinterpret_cast<uint4*>(s_cnt)[q] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(s_pos)[q] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   const int m = (int)(e1 - s0);
   if (any) {
@@ -436,101 +437,129 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
     for (int q = threadIdx.x; q < m; q += kBinNT) {
       const uint32_t r = s0 + (uint32_t)q;
       if (r < r0 || r >= r1) continue;  // alignment slack of the neighbouring buckets
-      atomicAdd(s_cnt + (s_stv[q] & (uint32_t)(R - 1)), 1u);
+      atomicAdd(s_pos + (s_stv[q].x & (uint32_t)(R - 1)), 1u);
     }
   }
   __syncthreads();
-  // ranges: exclusive block scan of the counts, four consecutive voxels per thread
+  // One pass of four consecutive voxels per thread: the range starts (an exclusive block scan of
+  // the counts, in place), the voxels with one record and those with more listed block-wide
+  // (their places from the same scan), and every voxel's count stored with a NaN mean.
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int carry = 0;
+  const int64_t vbase = (int64_t)bucket << b.logR;
+  const int nv = (int)min((int64_t)R, b.V - vbase);
+  int carry = 0, carry1 = 0, carry2 = 0;
   for (int base = 0; base < R; base += 4 * kBinNT) {
     const int q = base + 4 * (int)threadIdx.x;
     uint4 c4 = make_uint4(0u, 0u, 0u, 0u);
-    if (q < R) c4 = *reinterpret_cast<const uint4*>(s_cnt + q);
+    if (q < R) c4 = *reinterpret_cast<const uint4*>(s_pos + q);
     const int tot = (int)(c4.x + c4.y + c4.z + c4.w);
-    int x = tot;
+    const int n1 = (c4.x == 1u) + (c4.y == 1u) + (c4.z == 1u) + (c4.w == 1u);
+    const int n2 = (c4.x > 1u) + (c4.y > 1u) + (c4.z > 1u) + (c4.w > 1u);
+    int x = tot, y12 = n1 | (n2 << 16);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
+      const int u = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      const int v = __shfl_up_sync(0xFFFFFFFFu, y12, o);
+      if (lane >= o) {
+        x += u;
+        y12 += v;
+      }
     }
-    if (lane == 31) s_warp[w] = x;
+    if (lane == 31) s_warp2[w] = make_int2(x, y12);
     __syncthreads();
-    int run = carry + x - tot;
-    for (int k = 0; k < w; ++k) run += s_warp[k];
-    int all = 0;
-    for (int k = 0; k < kBinNT / 32; ++k) all += s_warp[k];
-    if (q < R)
-      *reinterpret_cast<uint4*>(s_end + q) =
+    // the warps' totals, scanned by every warp (16 lanes)
+    int2 wt = lane < kBinNT / 32 ? s_warp2[lane] : make_int2(0, 0);
+#pragma unroll
+    for (int o = 1; o < kBinNT / 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xFFFFFFFFu, wt.x, o);
+      const int v = __shfl_up_sync(0xFFFFFFFFu, wt.y, o);
+      if (lane >= o) {
+        wt.x += u;
+        wt.y += v;
+      }
+    }
+    const int all = __shfl_sync(0xFFFFFFFFu, wt.x, kBinNT / 32 - 1);
+    const int all12 = __shfl_sync(0xFFFFFFFFu, wt.y, kBinNT / 32 - 1);
+    const int wx = w ? __shfl_sync(0xFFFFFFFFu, wt.x, w - 1) : 0;
+    const int wy = w ? __shfl_sync(0xFFFFFFFFu, wt.y, w - 1) : 0;
+    const int run = carry + x - tot + wx;
+    const int e12 = y12 - (n1 | (n2 << 16)) + wy;  // exclusive, both fields
+    int p1 = carry1 + (e12 & 0xFFFF), p2 = carry2 + (e12 >> 16);
+    if (q < R) {
+      *reinterpret_cast<uint4*>(s_pos + q) =
           make_uint4((uint32_t)run, (uint32_t)run + c4.x, (uint32_t)run + c4.x + c4.y,
                      (uint32_t)run + c4.x + c4.y + c4.z);
+      const uint32_t cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (cc[e] == 1u) s_list1[p1++] = (uint16_t)(q + e);
+        else if (cc[e] > 1u) s_list2[p2++] = (uint16_t)(q + e);
+      }
+      if (q < nv) store_empty4<A, KEEP>(b, t, vbase + q, nv - q, c4);
+    }
     carry += all;
+    carry1 += all12 & 0xFFFF;
+    carry2 += all12 >> 16;
     __syncthreads();
   }
-  // sort: each record to the next place of its voxel's range (s_end becomes the range ends)
+  const int N1 = carry1, N2 = carry2;
+  // sort: each record to the next place of its voxel's range (s_pos becomes the range ends, so
+  // voxel u's records sit at [u ? s_pos[u - 1] : 0, s_pos[u]))
   if (any)
     for (int q = threadIdx.x; q < m; q += kBinNT) {
       const uint32_t r = s0 + (uint32_t)q;
       if (r < r0 || r >= r1) continue;
-      const uint32_t pos = atomicAdd(s_end + (s_stv[q] & (uint32_t)(R - 1)), 1u);
+      const uint32_t pos = atomicAdd(s_pos + (s_stv[q].x & (uint32_t)(R - 1)), 1u);
       s_idx[pos] = (uint16_t)q;
     }
-  __syncthreads();
-  // four voxels per thread: sums in registers, means, 16-byte stores
-  const float qnan = __int_as_float(0x7fc00000);
-  const int64_t vbase = (int64_t)bucket << b.logR;
-  const int nv = (int)min((int64_t)R, b.V - vbase);
-  for (int q = 4 * (int)threadIdx.x; q < nv; q += 4 * kBinNT) {
-    uint32_t c[4], e[4];
+  __syncthreads();  // the ranges, and the NaN stores before the means over them
+  if constexpr (A > 0) {
+    int kq[A];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      c[k] = q + k < R ? s_cnt[q + k] : 0u;
-      e[k] = q + k < R ? s_end[q + k] : 0u;
-    }
-    float mv[A > 0 ? A : 1][4];
-    long long sv[A > 0 ? A : 1][4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-#pragma unroll
-      for (int a = 0; a < A; ++a) {
-        sv[a][k] = 0;
-        mv[a][k] = qnan;
-      }
-      if (!c[k]) continue;  // empty voxel: count 0, mean NaN, no arithmetic
-      const uint32_t st = e[k] - c[k];
+    for (int a = 0; a < A; ++a) kq[a] = s_k[a];
+    // One record: its mean is its value quantised and scaled back. (float)sum / 1 of the
+    // general chain is the quantised value itself, which fp32 holds exactly (a 24-bit mantissa
+    // shifted left, or an integer below 2^24), so it is formed in fp32: v * 2^k is exact (two
+    // power-of-two factors; a product too small for a normal fp32 is below one half either
+    // way), rounding it to an integer (half to even) is the quantisation, and adding +0 turns
+    // a negative zero into the positive zero the integer path gives.
+    for (int i = threadIdx.x; i < N1; i += kBinNT) {
+      const int u = s_list1[i];
+      float vv[A];
+      staged_attrs<A>(s_sta, s_idx[s_pos[u] - 1u], vv);
 #pragma unroll
       for (int a = 0; a < A; ++a) {
-        long long sum = 0;
-        for (uint32_t i = st; i < e[k]; ++i)
-          sum += quantise(s_sta[(size_t)a * SS + s_idx[i]], s_k[a]);
-        sv[a][k] = sum;
-        mv[a][k] = __fmul_rn(__fmul_rn(div_count(i64_to_f32_rn(sum), (int)c[k]), s_f1[a]), s_f2[a]);
+        const int k = kq[a];
+        const int64_t o = ((int64_t)a * b.T + t) * b.V + vbase + u;
+        const float qv =
+            isfinite(vv[a])
+                ? __fadd_rn(rintf(__fmul_rn(__fmul_rn(vv[a], pow2f(k / 2)), pow2f(k - k / 2))), 0.0f)
+                : 0.0f;
+        __stcs(b.mean + o, __fmul_rn(__fmul_rn(qv, pow2f(-(k / 2))), pow2f(-(k - k / 2))));
+        if (KEEP) __stcs(b.sumq + o, quantise(vv[a], k));
       }
     }
-    const int64_t v = vbase + q;
-    if ((b.V & 3) == 0) {  // nv is then a multiple of four
-      __stcs(reinterpret_cast<uint4*>(b.count + (int64_t)t * b.V + v),
-             make_uint4(c[0], c[1], c[2], c[3]));
+    // More records: exact fixed-point sums, then the fp32 mean chain.
+    for (int i = threadIdx.x; i < N2; i += kBinNT) {
+      const int u = s_list2[i];
+      const uint32_t e = s_pos[u], st = u ? s_pos[u - 1] : 0u;
+      long long sum[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) sum[a] = 0;
+      for (uint32_t y = st; y < e; ++y) {
+        float vv[A];
+        staged_attrs<A>(s_sta, s_idx[y], vv);
+#pragma unroll
+        for (int a = 0; a < A; ++a) sum[a] += quantise(vv[a], kq[a]);
+      }
+      const int c = (int)(e - st);
 #pragma unroll
       for (int a = 0; a < A; ++a) {
-        const int64_t o = ((int64_t)a * b.T + t) * b.V + v;
-        __stcs(reinterpret_cast<float4*>(b.mean + o), make_float4(mv[a][0], mv[a][1], mv[a][2], mv[a][3]));
-        if (KEEP) {
-          __stcs(reinterpret_cast<longlong2*>(b.sumq + o), make_longlong2(sv[a][0], sv[a][1]));
-          __stcs(reinterpret_cast<longlong2*>(b.sumq + o + 2), make_longlong2(sv[a][2], sv[a][3]));
-        }
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (q + k >= nv) break;
-        __stcs(b.count + (int64_t)t * b.V + v + k, (int)c[k]);
-#pragma unroll
-        for (int a = 0; a < A; ++a) {
-          const int64_t o = ((int64_t)a * b.T + t) * b.V + v + k;
-          __stcs(b.mean + o, mv[a][k]);
-          if (KEEP) __stcs(b.sumq + o, sv[a][k]);
-        }
+        const int k = kq[a];
+        const int64_t o = ((int64_t)a * b.T + t) * b.V + vbase + u;
+        __stcs(b.mean + o, __fmul_rn(__fmul_rn(div_count(i64_to_f32_rn(sum[a]), c),
+                                               pow2f(-(k / 2))), pow2f(-(k - k / 2))));
+        if (KEEP) __stcs(b.sumq + o, sum[a]);
       }
     }
   }
@@ -538,30 +567,26 @@ __global__ void __launch_bounds__(kBinNT, 3) k_bin_reduce(const __grid_constant_
 
 // Buckets with more records than k_bin_reduce stages (listed by it): the records arrive in
 // pieces of R; counts and fixed-point sums accumulate in shared memory (sums [A][R] u64,
-// counts [R] u32, then the staging buffer of R * (1 + A) words, reused for the means [A][R]
-// f32 and the non-empty lists once the records are in). After the records, every warp owns 128
-// voxels (four per lane): it lists its non-empty ones, forms their means and stores its outputs.
-// Blocks take listed items in turn.
+// counts [R] u32, then the staging buffer of R records, reused for the means [A][R] f32 and the
+// non-empty lists once the records are in). After the records, every warp owns 128 voxels (four
+// per lane): it lists its non-empty ones, forms their means and stores its outputs. Blocks take
+// listed items in turn.
 template <int A, bool KEEP>
 __global__ void __launch_bounds__(kBinNT, 1) k_bin_reduce_wide(const __grid_constant__ BinArgs b) {
+  constexpr int AW = rec_aw(A);
   extern __shared__ __align__(16) unsigned long long s_dyn64[];
   const int R = 1 << b.logR;
   unsigned long long* s_sum = s_dyn64;                                    // [A][R]
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_dyn64 + (size_t)A * R);  // [R]
-  uint32_t* s_stv = s_cnt + R;                                            // [R] record voxels
-  float* s_sta = reinterpret_cast<float*>(s_stv + R);                     // [A][R] values
-  float* s_mean = reinterpret_cast<float*>(s_stv);                        // after the records
-  uint32_t* s_list = s_stv + (size_t)A * R;
+  float* s_sta = reinterpret_cast<float*>(s_cnt + R);                     // [R][AW] values
+  uint2* s_stv = reinterpret_cast<uint2*>(s_sta + (size_t)AW * R);       // [R] voxel pairs
+  float* s_mean = s_sta;                                                  // after the records
+  uint32_t* s_list = reinterpret_cast<uint32_t*>(s_sta) + (size_t)A * R;
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_k[A > 0 ? A : 1];
   __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
   if (threadIdx.x == 0) mbar_init(&s_bar, 1);
-  if ((int)threadIdx.x < A) {
-    const int k = scale_exponent_bits(b.absmax[threadIdx.x], (long long)b.scale_n);
-    s_k[threadIdx.x] = k;
-    s_f1[threadIdx.x] = pow2f(-(k / 2));
-    s_f2[threadIdx.x] = pow2f(-(k - k / 2));
-  }
+  if ((int)threadIdx.x < A) item_scale(b, threadIdx.x, s_k, s_f1, s_f2);
   uint32_t phase = 0;  // copies this block has waited for (the mbarrier's phase)
   const uint32_t nwide = *b.novf;
   for (uint32_t it = blockIdx.x; it < nwide; it += gridDim.x) {
@@ -575,7 +600,7 @@ __global__ void __launch_bounds__(kBinNT, 1) k_bin_reduce_wide(const __grid_cons
   const int npiece = r1 > r0 ? (int)((e1 - s0 + (uint32_t)R - 1) / (uint32_t)R) : 0;
   if (threadIdx.x == 0 && npiece) {
     fence_proxy_async_smem();
-    reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, R, &s_bar);
+    reduce_issue<A>(b, s0, min((uint32_t)R, e1 - s0), s_stv, s_sta, &s_bar);
   }
   {
     uint4* z = reinterpret_cast<uint4*>(s_dyn64);
@@ -597,18 +622,19 @@ __global__ void __launch_bounds__(kBinNT, 1) k_bin_reduce_wide(const __grid_cons
     for (int q = threadIdx.x; q < m; q += kBinNT) {
       const uint32_t r = a0 + (uint32_t)q;
       if (r < r0 || r >= r1) continue;  // alignment slack of the neighbouring buckets
-      const uint32_t v = s_stv[q] & (uint32_t)(R - 1);  // voxel within the bucket
+      const uint32_t v = s_stv[q].x & (uint32_t)(R - 1);  // voxel within the bucket
       atomicAdd(s_cnt + v, 1u);
+      float vv[A > 0 ? A : 1];
+      staged_attrs<A>(s_sta, q, vv);
 #pragma unroll
       for (int a = 0; a < A; ++a)
-        atomicAdd(s_sum + (size_t)a * R + v,
-                  (unsigned long long)quantise(s_sta[(size_t)a * R + q], s_k[a]));
+        atomicAdd(s_sum + (size_t)a * R + v, (unsigned long long)quantise(vv[a], s_k[a]));
     }
     __syncthreads();
     if (piece + 1 < npiece && threadIdx.x == 0) {
       fence_proxy_async_smem();  // the reads above before the next copy overwrites them
       const uint32_t a1 = a0 + (uint32_t)R;
-      reduce_issue<A>(b, a1, min((uint32_t)R, e1 - a1), s_stv, s_sta, R, &s_bar);
+      reduce_issue<A>(b, a1, min((uint32_t)R, e1 - a1), s_stv, s_sta, &s_bar);
     }
   }
   const float qnan = __int_as_float(0x7fc00000);
@@ -688,68 +714,59 @@ __global__ void __launch_bounds__(kBinNT, 1) k_bin_reduce_wide(const __grid_cons
 }
 
 // Bucket width: 2048 voxels (the sorted reduce stages records, not per-voxel sums, so the
-// width no longer depends on the attribute count), wider when the grid has more buckets than
-// the shared-memory histograms hold and the wide pass's sums still fit.
+// width does not depend on the attribute count), wider when the grid has more buckets than the
+// shared-memory histograms hold and the wide pass's sums still fit.
+static size_t reduce_smem(int A, int logR) {
+  const size_t R = (size_t)1 << logR, SS = kRedStage + 8;
+  return 4 * SS * (2 + (size_t)rec_aw(A)) + 4 * R + 2 * SS + 4 * R;
+}
+static size_t reduce_wide_smem(int A, int logR) {
+  const size_t R = (size_t)1 << logR;
+  return R * (8 * (size_t)A + 4 + 4 * (2 + (size_t)rec_aw(A)));
+}
+
 static int bucket_log2(int A, int64_t V) {
   int l = 11;
   while (l < 12 && ((V + ((int64_t)1 << l) - 1) >> l) > kHistSmem &&
-         ((size_t)2 << l) * (8 + 12 * (size_t)A) <= (size_t)220 * 1024)
+         reduce_wide_smem(A, l + 1) <= (size_t)220 * 1024)
     ++l;
   return l;
 }
 
-static size_t reduce_smem(int A, int logR) {
-  const size_t R = (size_t)1 << logR, SS = kRedStage + 8;
-  return sizeof(uint32_t) * ((1 + (size_t)A) * SS + 2 * R) + sizeof(uint16_t) * SS;
-}
-static size_t reduce_wide_smem(int A, int logR) {
-  return ((size_t)1 << logR) * (8 + 12 * (size_t)A);
-}
-
-static size_t place_smem(int64_t chunk, int nb) {
-  return sizeof(uint32_t) * ((size_t)chunk + 8 + (size_t)chunk / 2 + 2 * (size_t)nb);
+template <typename K>
+static void allow_smem(K kernel, size_t bytes, std::atomic<size_t>& set) {
+  // The attribute is per device and set before every launch that needs more than before (also
+  // just under 48 KB: the default limit counts the static shared memory too).
+  if (bytes > set.load()) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    set.store(bytes);
+  }
 }
 
 template <int A>
 static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, bool smem) {
   cudaStream_t s = ctx->stream;
   const dim3 gs((unsigned)b.nblk, (unsigned)b.Tp);  // (block, point step)
+  const dim3 gp((unsigned)((b.P + kPlaceChunk - 1) / kPlaceChunk), (unsigned)b.Tp);
   if (phase == 0) {
     ScopedKernel k(ctx, "k_bin_keys");
     if (smem) k_bin_keys<true><<<gs, 256, 0, s>>>(b);
     else k_bin_keys<false><<<gs, 256, 0, s>>>(b);
   } else if (phase == 1) {
     ScopedKernel k(ctx, "k_bin_place");
-    if (smem) {  // caller guarantees place_smem(chunk, nb) <= kPlaceSmemMax
-      static bool set = false;
-      if (!set) {
-        cudaFuncSetAttribute(k_bin_place_sorted<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kPlaceSmemMax);
-        set = true;
-      }
-      k_bin_place_sorted<A><<<gs, kBinNT, place_smem(b.chunk, b.nb), s>>>(b);
-    } else {
-      k_bin_place_atomic<A><<<gs, 256, 0, s>>>(b);
-    }
+    k_bin_place<A><<<gp, kPlaceNT, 0, s>>>(b);
   } else {
     {
       ScopedKernel k(ctx, "k_bin_reduce");
       const size_t sm = reduce_smem(A, b.logR);
       const dim3 gr((unsigned)b.nb, (unsigned)b.T);
-      // the attribute is per device and set before every launch that needs more than before
       if (keep) {
         static std::atomic<size_t> set{0};
-        if (sm > set.load()) {
-          cudaFuncSetAttribute(k_bin_reduce<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-          set.store(sm);
-        }
+        allow_smem(k_bin_reduce<A, true>, sm, set);
         k_bin_reduce<A, true><<<gr, kBinNT, sm, s>>>(b);
       } else {
         static std::atomic<size_t> set{0};
-        if (sm > set.load()) {
-          cudaFuncSetAttribute(k_bin_reduce<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-          set.store(sm);
-        }
+        allow_smem(k_bin_reduce<A, false>, sm, set);
         k_bin_reduce<A, false><<<gr, kBinNT, sm, s>>>(b);
       }
     }
@@ -761,17 +778,11 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
       const unsigned g = (unsigned)std::min<int64_t>((int64_t)b.nb * b.T, (int64_t)ctx->sm_count * 2);
       if (keep) {
         static std::atomic<size_t> set{0};
-        if (sm > set.load()) {
-          cudaFuncSetAttribute(k_bin_reduce_wide<A, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-          set.store(sm);
-        }
+        allow_smem(k_bin_reduce_wide<A, true>, sm, set);
         k_bin_reduce_wide<A, true><<<g, kBinNT, sm, s>>>(b);
       } else {
         static std::atomic<size_t> set{0};
-        if (sm > set.load()) {
-          cudaFuncSetAttribute(k_bin_reduce_wide<A, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-          set.store(sm);
-        }
+        allow_smem(k_bin_reduce_wide<A, false>, sm, set);
         k_bin_reduce_wide<A, false><<<g, kBinNT, sm, s>>>(b);
       }
     }
@@ -811,27 +822,28 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.scale_n = d.scale_fixed ? d.scale_samples : d.P * (int64_t)d.Tp;
   b.logR = bucket_log2(d.A, d.V);
   b.nb = (int)((d.V + ((int64_t)1 << b.logR) - 1) >> b.logR);
-  // samples per block: the shared-memory sort handles kPlaceChunk; with too many buckets for
-  // shared memory the blocks grow so that the per-block histograms stay small
-  const bool smem = b.nb <= kHistSmem && place_smem(kPlaceChunk, b.nb) <= (size_t)kPlaceSmemMax;
-  // many buckets: twice the samples per block, as long as two blocks still share an SM
-  b.chunk = (smem && b.nb >= 4096 && place_smem(kPlaceChunkWide, b.nb) <= (size_t)114 * 1024)
-                ? kPlaceChunkWide
-                : kPlaceChunk;
-  if (!smem)
-    while ((int64_t)b.nb * ((d.P + b.chunk - 1) / b.chunk) > (1 << 22) && b.chunk < ((int64_t)1 << 30))
-      b.chunk <<= 1;
+  // Samples per block of the keys pass: at least eight per bucket on average (each block adds
+  // its shared-memory histogram into the global one, one atomic per bucket), from 4096 up to
+  // kChunkMax. With more buckets than shared memory holds, every sample adds to the global
+  // histogram directly.
+  const bool smem = b.nb <= kHistSmem;
+  b.chunk = 4096;
+  while (b.chunk < kChunkMax && b.chunk < 8 * (int64_t)b.nb) b.chunk <<= 1;
   b.nblk = (int)std::max<int64_t>(1, (d.P + b.chunk - 1) / b.chunk);
-  const int64_t TB = (int64_t)d.Tp * b.nb * b.nblk;
+  const int64_t TB = (int64_t)d.T * b.nb;
   const int64_t NR = d.P * (int64_t)d.Tp;
   const int Af = d.A > 0 ? d.A : 1;
-  if (NR >= ((int64_t)1 << 32) || TB >= ((int64_t)1 << 31)) return MSF_ERR_TOO_LARGE;
+  const int AW = rec_aw(d.A);
+  if (NR >= ((int64_t)1 << 32) || TB >= ((int64_t)1 << 31) ||
+      (d.P + kPlaceChunk - 1) / kPlaceChunk > 0x7FFFFFFF)
+    return MSF_ERR_TOO_LARGE;
   MSF_TRY(S.hist.ensure(sizeof(uint32_t) * TB));
   MSF_TRY(S.offs.ensure(sizeof(uint32_t) * TB));
-  if (!smem) MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * TB));
+  MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * TB));
+  // records: voxels [NR] and attributes [NR][AW], with room for the rounded-up bulk copies
   const int64_t NRp = (NR + 3) & ~(int64_t)3;
-  MSF_TRY(S.rec_v.ensure(sizeof(uint32_t) * (NRp + 4)));
-  MSF_TRY(S.rec_a.ensure(sizeof(float) * (NRp * Af + 4)));
+  MSF_TRY(S.rec_vn.ensure(sizeof(uint2) * (NRp + 4)));
+  MSF_TRY(S.rec_a.ensure(sizeof(float) * ((NRp + 4) * (AW > 0 ? AW : 1))));
   MSF_TRY(S.absmax.ensure(sizeof(unsigned) * MSF_MAX_ATTR));
   MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.Tp));
   MSF_TRY(S.total.ensure(sizeof(uint32_t) * 4));  // [0] records, [2] error word, [3] wide items
@@ -846,9 +858,8 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.hist = S.hist.as<uint32_t>();
   b.offs = S.offs.as<uint32_t>();
   b.cursor = S.cursor.as<uint32_t>();
-  b.rec_v = S.rec_v.as<uint32_t>();
+  b.rec_vn = S.rec_vn.as<uint2>();
   b.rec_a = S.rec_a.as<float>();
-  b.NRp = NRp;
   b.wait_cycles = ctx->wait_cycles;
   b.err = S.total.as<uint32_t>() + 2;
   b.novf = S.total.as<uint32_t>() + 3;
@@ -871,9 +882,8 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
     launch_bin_a(ctx, b, keep, 0, smem);
     MSF_CUDA_TRY(cudaGetLastError());
     MSF_TRY(scan_exclusive_u32(ctx, b.hist, b.offs, TB, S.scan_tmp, S.total.as<uint32_t>()));
-    if (!smem)
-      MSF_CUDA_TRY(cudaMemcpyAsync(b.cursor, b.offs, sizeof(uint32_t) * TB,
-                                   cudaMemcpyDeviceToDevice, s));
+    MSF_CUDA_TRY(cudaMemcpyAsync(b.cursor, b.offs, sizeof(uint32_t) * TB,
+                                 cudaMemcpyDeviceToDevice, s));
     launch_bin_a(ctx, b, keep, 1, smem);
     MSF_CUDA_TRY(cudaGetLastError());
     b.nrec = S.total.as<uint32_t>();  // the scan's total: the last bucket's end
@@ -885,14 +895,22 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.Tp,
                                cudaMemcpyDeviceToHost, s));
   MSF_CUDA_TRY(cudaMemcpyAsync(hmax, S.absmax.p, sizeof(hmax), cudaMemcpyDeviceToHost, s));
-  uint32_t herr = 0;
+  uint32_t herr = 0, hrec = 0;
   MSF_CUDA_TRY(cudaMemcpyAsync(&herr, b.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (d.P > 0)
+    MSF_CUDA_TRY(cudaMemcpyAsync(&hrec, S.total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  S.rec_valid = false;
   MSF_CUDA_TRY(cudaStreamSynchronize(s));
   ctx->timer.flush();
   if (herr) {
     d.binned = false;
     return MSF_ERR_TIMEOUT;
   }
+  S.rec_valid = d.P > 0;
+  S.rec_logR = b.logR;
+  S.rec_nb = b.nb;
+  S.rec_aw = AW;
+  S.rec_n = hrec;
   for (int a = 0; a < d.A; ++a) {
     float m;
     memcpy(&m, &hmax[a], sizeof(float));

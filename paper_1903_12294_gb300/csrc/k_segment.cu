@@ -697,6 +697,83 @@ __global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArg
 }
 
 // ---------------------------------------------------------------------------------------------
+// the binned records (while they hold the loaded dataset's binning)
+// ---------------------------------------------------------------------------------------------
+// Binning leaves every in-grid point sample as a record grouped by (field step, bucket of
+// consecutive voxels): its voxel, its point's voxel at the next point step, its attributes. The
+// trajectory joins (one point step per field step) and the point statistics walk them instead
+// of the points in id order: the 32 records of a warp lie in one bucket (a few rows of the
+// grid), so their component lookups hit cached rows. Block (x, y) of a pass takes records
+// [x * kRecChunk, (x + 1) * kRecChunk) of its field step.
+constexpr int kRecChunk = 32768;
+
+struct RecView {
+  const uint2* rec_vn;    // [records] voxel, the point's voxel at the next point step (or -1)
+  const float* rec_a;     // [records][aw] attributes
+  const uint32_t* offs;   // [T][nb] first record of each (field step, bucket)
+  uint32_t nrec;
+  int nb, T, aw;
+};
+
+static RecView rec_view(const msf_ctx* ctx) {
+  const BinScratch& B = ctx->bin;
+  return RecView{B.rec_vn.as<uint2>(), B.rec_a.as<float>(), B.offs.as<uint32_t>(), B.rec_n,
+                 B.rec_nb, ctx->ds.T, B.rec_aw};
+}
+
+// records [b0, b1) of block x of field step t; false when the block has none
+__device__ __forceinline__ bool rec_block(const RecView& rv, int t, uint32_t& b0, uint32_t& b1) {
+  const int64_t h = (int64_t)t * rv.nb;
+  const uint32_t rb = __ldg(rv.offs + h);
+  const uint32_t re = h + rv.nb < (int64_t)rv.T * rv.nb ? __ldg(rv.offs + h + rv.nb) : rv.nrec;
+  b0 = rb + blockIdx.x * (uint32_t)kRecChunk;
+  if (b0 >= re) return false;
+  b1 = min(re, b0 + (uint32_t)kRecChunk);
+  return true;
+}
+
+// Trajectory joins from the records, for a dataset with one point step per field step: a record
+// of window field step tw joins its voxel there with its point's voxel at tw + 1, under the same
+// rule as links_chunk. Window field steps [ta, ta + gridDim.y) are the sources. Four records per
+// lane in flight; neighbouring records (one bucket) often join the same pair of components, so
+// each distinct pair in a warp is joined once.
+constexpr int kRecLinkPer = 4;
+
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256) k_links_rec(const __grid_constant__ SegArgs a,
+                                                   const __grid_constant__ RecView rv, int ta) {
+  const int tw = ta + (int)blockIdx.y;
+  uint32_t b0, b1;
+  if (!rec_block(rv, a.g.t0 + tw, b0, b1)) return;
+  const bool temporal = (a.edges & MSF_EDGE_TEMPORAL) != 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (uint32_t base = b0 + 32u * kRecLinkPer * w; base < b1;
+       base += 256u * kRecLinkPer) {  // warp-uniform
+    uint2 e[kRecLinkPer];
+#pragma unroll
+    for (int u = 0; u < kRecLinkPer; ++u) {
+      const uint32_t r = base + 32u * u + lane;
+      e[u] = r < b1 ? __ldcs(rv.rec_vn + r) : make_uint2(0u, 0xFFFFFFFFu);
+    }
+#pragma unroll
+    for (int u = 0; u < kRecLinkPer; ++u) {
+      int64_t ca = -1, cb = -1;
+      if ((int32_t)e[u].y >= 0 && !(temporal && e[u].x == e[u].y)) {
+        ca = comp_of<SPATIAL>(a, tw, (int32_t)e[u].x);
+        if (ca >= 0) cb = comp_of<SPATIAL>(a, tw + 1, (int32_t)e[u].y);
+      }
+      const bool need = ca >= 0 && cb >= 0 && ca != cb;
+      const unsigned nm = __ballot_sync(0xFFFFFFFFu, need);
+      if (need) {
+        const unsigned long long key = ((unsigned long long)ca << 32) | (unsigned long long)cb;
+        const unsigned grp = __match_any_sync(nm, key);
+        if (lane == __ffs(grp) - 1) gunion(a.cparent, (uint32_t)ca, (uint32_t)cb);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // k_flatten: compress to roots, smallest index onto the root, count features
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void flatten_body(const SegArgs& a, const int tile, int* s_n_ptr) {
@@ -1121,16 +1198,29 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   // a caller that only segments does not pay for the store.
   SegState& LS = ctx->last;
   LS.has_pcomp = false;
-  const bool keep = traj && ctx->keep_pcomp;
+  const bool keep = traj && ctx->keep_pcomp && !(ctx->bin.rec_valid && ds.binned);
   ctx->keep_pcomp = false;
   if (keep) {
     MSF_TRY(LS.pcomp.ensure(sizeof(uint32_t) * (size_t)a.P * (size_t)std::max(a.nj, 1)));
     a.pcomp = LS.pcomp.as<uint32_t>();
   }
   const int nchunk = (a.nj - 1 + kLinkSteps - 1) / kLinkSteps;
+  // With one point step per field step and the dataset's records at hand, the joins walk the
+  // records: chunk c's joins are those from window field steps [c L, c L + L).
+  const bool rec_links = ctx->bin.rec_valid && ds.binned && !ds.multirate;
   auto links = [&](cudaStream_t ls, int c0, int c1) {  // link chunks [c0, c1)
     if (c1 <= c0) return;
     ScopedKernel k(ctx, "k_links", ls);
+    if (rec_links) {
+      const int ta = c0 * kLinkSteps, tb = std::min(c1 * kLinkSteps, g.tw - 1);
+      if (tb <= ta) return;
+      const RecView rv = rec_view(ctx);
+      dim3 grid((unsigned)std::max<int64_t>(1, (a.P + kRecChunk - 1) / kRecChunk),
+                (unsigned)(tb - ta));
+      if (spatial) k_links_rec<true><<<grid, 256, 0, ls>>>(a, rv, ta);
+      else k_links_rec<false><<<grid, 256, 0, ls>>>(a, rv, ta);
+      return;
+    }
     SegArgs al = a;
     al.chunk0 = c0;
     al.chunk1 = c1;
@@ -1370,6 +1460,69 @@ __global__ void __launch_bounds__(256, 4) k_feat_points(const __grid_constant__ 
   hot_flush(acc, s_hot[w]);
 }
 
+// Point statistics from the binned records (while they hold the loaded dataset's binning): the
+// samples of the window's field steps, grouped by (field step, bucket of consecutive voxels),
+// each with its voxel and its attributes side by side. A warp takes 32 consecutive records:
+// their voxels lie in one bucket (a few rows of the grid), so the component lookups hit cached
+// rows, and its lanes mostly share one feature (the butterfly path of reduce_samples). The
+// samples are those of every point step falling in the window's field steps that binning placed
+// inside the grid: the same as the per-point pass takes. Block (x, y) takes records
+// [x * kRecChunk, (x + 1) * kRecChunk) of window field step y.
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256) k_feat_points_rec(const __grid_constant__ SegArgs a,
+                                                         FeatAcc acc,
+                                                         const int32_t* __restrict__ cfid,
+                                                         const __grid_constant__ RecView rv) {
+  constexpr int L = 8;                  // records per lane per round of lookups
+  __shared__ int2 s_buf[8][32 * L];     // per warp: (feature, record) of its members, packed
+  __shared__ HotCache s_hot[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tw = blockIdx.y;
+  uint32_t b0, b1;
+  if (!rec_block(rv, a.g.t0 + tw, b0, b1)) return;  // block-uniform
+  hot_clear(s_hot[w]);
+  for (uint32_t base = b0 + 32u * L * w; base < b1; base += 256u * L) {  // warp-uniform
+    int32_t fid[L];
+    int n = 0;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      const uint32_t r = base + 32u * j + lane;
+      fid[j] = r < b1 ? (int32_t)__ldcs(&rv.rec_vn[r].x) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      if (fid[j] >= 0) {
+        const int64_t cj = comp_of<SPATIAL>(a, tw, fid[j]);
+        fid[j] = cj >= 0 ? __ldg(cfid + cj) : -1;
+      }
+      n += fid[j] >= 0;
+    }
+    // the warp's members packed in record order, then reduced 32 at a time
+    int x = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    int pos = x - n;
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      if (fid[j] >= 0) s_buf[w][pos++] = make_int2(fid[j], 32 * j + lane);
+    __syncwarp();
+    for (int i0 = 0; i0 < total; i0 += 32) {
+      const int i = i0 + lane;
+      const bool ok = i < total;
+      const int2 e = ok ? s_buf[w][i] : make_int2(-1, 0);
+      accumulate_samples_hot<true>(acc, s_hot[w], ok, e.x,
+                                   rv.rec_a + (size_t)(base + e.y) * rv.aw, 1);
+      __syncwarp();  // the cached sums one reduction at a time
+    }
+    __syncwarp();  // the buffer is refilled next round
+  }
+  hot_flush(acc, s_hot[w]);
+}
+
 int seg_mark_roots(msf_ctx* ctx, uint32_t* rootbits, unsigned long long* counter) {
   (void)counter;
   const SegState& L = ctx->last;
@@ -1387,8 +1540,11 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
   const bool spatial = L.crit.edges & MSF_EDGE_SPATIAL;
   SegArgs a;
   MSF_TRY(seg_args(ctx, g, spatial, &a));
+  const bool recs = ctx->bin.rec_valid && ctx->ds.binned;
   if (L.has_pcomp) a.pcomp = L.pcomp.as<uint32_t>();
-  ctx->keep_pcomp = true;  // features follow segmentations here: keep components next time
+  // features follow segmentations here: keep components next time (unless the binned records
+  // serve the point statistics)
+  ctx->keep_pcomp = !recs;
   MSF_TRY(L.cfid.ensure(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
   int32_t* cfid = L.cfid.as<int32_t>();
   cudaStream_t s = ctx->stream;
@@ -1403,10 +1559,22 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
   if (points) {
     MSF_TRY(ctx_fork(ctx));
     ScopedKernel k(ctx, "k_feat_points", ctx->aux);
-    const int64_t nchunk = (a.nj + kLinkSteps - 1) / kLinkSteps;
-    dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
-    if (spatial) k_feat_points<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
-    else k_feat_points<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
+    if (recs) {
+      const BinScratch& B = ctx->bin;
+      const RecView rv = rec_view(ctx);
+      int rmax = 1;  // most point steps in one field step of the window
+      for (int t = g.t0; t < g.t0 + g.tw; ++t)
+        rmax = std::max(rmax, d.h_pj0[t + 1] - d.h_pj0[t]);
+      const int64_t nx = (a.P * rmax + kRecChunk - 1) / kRecChunk;
+      dim3 grid((unsigned)std::max<int64_t>(nx, 1), (unsigned)g.tw);
+      if (spatial) k_feat_points_rec<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, rv);
+      else k_feat_points_rec<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, rv);
+    } else {
+      const int64_t nchunk = (a.nj + kLinkSteps - 1) / kLinkSteps;
+      dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
+      if (spatial) k_feat_points<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
+      else k_feat_points<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
+    }
   }
   {
     ScopedKernel k(ctx, "k_feat_vox");

@@ -345,10 +345,11 @@ void msf_destroy(msf_ctx* c) {
   for (DevBuf* b : {&c->feat.rootbits, &c->feat.wordrank, &c->feat.blocksums, &c->feat.acc,
                     &c->feat.out})
     b->release();
-  for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.rec_v, &c->bin.rec_a,
+  for (DevBuf* b : {&c->bin.hist, &c->bin.offs, &c->bin.cursor, &c->bin.rec_vn, &c->bin.rec_a,
                     &c->bin.absmax, &c->bin.outside, &c->bin.scan_tmp, &c->bin.total,
                     &c->bin.ovf})
     b->release();
+  c->bin.rec_valid = false;
   c->last.cfid.release();
   c->last.pcomp.release();
   for (DevBuf* b : {&c->clu.centers, &c->clu.prev, &c->clu.sums, &c->clu.counts,
@@ -404,6 +405,7 @@ int msf_load_timesteps_mr(msf_ctx* c, int nx, int ny, int nz, int T, const float
   Dataset& d = c->ds;
   d.loaded = false;
   d.binned = false;
+  c->bin.rec_valid = false;
   d.has_sumq = false;
   c->epoch++;
   c->last.valid = false;

@@ -165,7 +165,14 @@ struct BatchScratch {
 };
 
 struct BinScratch {
-  DevBuf hist, offs, cursor, rec_v, rec_a, absmax, outside, scan_tmp, total, ovf;
+  DevBuf hist, offs, cursor, rec_vn, rec_a, absmax, outside, scan_tmp, total, ovf;
+  // The records of the last binning stay for the trajectory joins and the feature statistics:
+  // the samples grouped by (field step, bucket of 2^rec_logR voxels) in the slot ranges
+  // offs[t][bucket], each its voxel and its point's voxel at the next point step (rec_vn) and
+  // rec_aw attribute words (rec_a); rec_n of them in all.
+  bool rec_valid = false;
+  int rec_logR = 0, rec_nb = 0, rec_aw = 0;
+  uint32_t rec_n = 0;
 };
 
 // Scratch of the clustering (k_cluster.cu): centres, their sums and cells, label buffers for
@@ -464,6 +471,15 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
   lo = __fadd_rn(lo, e);
 }
 
+// Double-float accumulator (hi + lo) plus another double-float (h + l), renormalised.
+__device__ __forceinline__ void df_add2(float& hi, float& lo, float h, float l) {
+  float s, e;
+  two_sum(hi, h, s, e);
+  e = __fadd_rn(e, __fadd_rn(lo, l));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
 // Both terms of a double-float are exact in fp32; their fp64 sum is formed in L2 atomics.
 __device__ __forceinline__ bool df_safe(float x) {
   const float a = fabsf(x);
@@ -476,9 +492,32 @@ struct RowSums {
   int sum_c;            // point samples in them
   int sum_x;            // sum of x
   unsigned kmin, kmax;  // order-preserving keys of the smallest and largest field value
-  double s1, s2;        // sum of field values and of their squares
+  // sum of field values and of their squares: double-float pairs (h + l, each exact in fp32),
+  // or for non-finite or extreme values plain fp64 sums (s1d, s2d; dbl set)
+  float s1h, s1l, s2h, s2l;
+  double s1d, s2d;
+  bool dbl;
   int tw, z, y, xlo, xhi;
 };
+
+// A double-float pair into an fp64 accumulator in global memory: the two terms convert to fp64
+// by integer operations and add in L2 atomics, so no fp64 arithmetic runs on the SM (whose fp64
+// rate is a small fraction of its fp32 rate on this part).
+__device__ __forceinline__ void add_pair(double* p, float h, float l) {
+  if (h != 0.f) atomicAdd(p, f2d(h));
+  if (l != 0.f) atomicAdd(p, f2d(l));
+}
+
+// a group's field sums into accumulator slot i
+__device__ __forceinline__ void commit_fsums(const FeatAcc& acc, int64_t i, const RowSums& r) {
+  if (r.dbl) {
+    atomicAdd(acc.sf + i, r.s1d);
+    atomicAdd(acc.sf2 + i, r.s2d);
+  } else {
+    add_pair(acc.sf + i, r.s1h, r.s1l);
+    add_pair(acc.sf2 + i, r.s2h, r.s2l);
+  }
+}
 
 // Voxels of one 32-voxel row (fixed tw, z, y; lane = x - x0): the lanes in `act` with the same
 // feature reduce in the warp and the group's first lane hands the group's sums to
@@ -513,8 +552,11 @@ __device__ __forceinline__ void reduce_row(unsigned act, int64_t fid, int lane, 
       h2 = s;
       l2 = __fadd_rn(__fadd_rn(l2, b2), e);
     }
-    r.s1 = f2d(h1) + f2d(l1);
-    r.s2 = f2d(h2) + f2d(l2);
+    r.s1h = h1;
+    r.s1l = l1;
+    r.s2h = h2;
+    r.s2l = l2;
+    r.dbl = false;
   } else if (__all_sync(grp, df_safe(f))) {
     const float p = __fmul_rn(f, f), pe = __fmaf_rn(f, f, -p);  // f*f == p + pe exactly
     float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
@@ -524,16 +566,20 @@ __device__ __forceinline__ void reduce_row(unsigned act, int64_t fid, int lane, 
       df_add(h2, l2, __shfl_sync(grp, p, src));
       df_add(h2, l2, __shfl_sync(grp, pe, src));
     }
-    r.s1 = f2d(h1) + f2d(l1);
-    r.s2 = f2d(h2) + f2d(l2);
+    r.s1h = h1;
+    r.s1l = l1;
+    r.s2h = h2;
+    r.s2l = l2;
+    r.dbl = false;
   } else {  // non-finite or extreme values: plain fp64 (rare)
-    r.s1 = 0.0;
-    r.s2 = 0.0;
+    r.s1d = 0.0;
+    r.s2d = 0.0;
     for (unsigned m = grp; m; m &= m - 1) {
       const double v = (double)__shfl_sync(grp, f, __ffs(m) - 1);
-      r.s1 += v;
-      r.s2 += v * v;
+      r.s1d += v;
+      r.s2d += v * v;
     }
+    r.dbl = true;
   }
   if (lane != leader) return;
   r.tw = tw;
@@ -549,8 +595,7 @@ __device__ __forceinline__ void commit_row(const FeatAcc& acc, int64_t fid, cons
   const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + fid;
   atomicAdd(acc.n_vox + i, (unsigned long long)r.n);
   atomicAdd(acc.n_pts + i, (unsigned long long)r.sum_c);
-  atomicAdd(acc.sf + i, r.s1);
-  atomicAdd(acc.sf2 + i, r.s2);
+  commit_fsums(acc, i, r);
   atomicMin(acc.fmin + i, r.kmin);
   atomicMax(acc.fmax + i, r.kmax);
   int* bmn = acc.bbmin + i * 4;
@@ -585,10 +630,17 @@ __device__ __forceinline__ void accumulate_row(const FeatAcc& acc, unsigned act,
 // their global atomics bound the statistics passes. A block first sums into a small open-
 // addressing table keyed by feature (shared-memory atomics), then commits each feature it met
 // once. A feature that finds no free slot within a few probes goes straight to the
-// accumulators. The caller clears the table, synchronises, accumulates, synchronises, flushes.
+// accumulators. The field sums stay out of shared-memory atomics (fp64 ones would run as
+// compare-and-swap loops on the SM's narrow fp64 unit): every warp keeps double-float sums for
+// up to kWarpSlots features of its own, which only the warp writes (one group per feature and
+// row, its leader lane), and flushes them once; a feature the warp has no room for adds its
+// sums in L2 directly. The caller (8 warps) clears the table, synchronises, accumulates,
+// synchronises, flushes.
 // ---------------------------------------------------------------------------------------------
 constexpr int kTabSlots = 128;
 constexpr int kTabProbes = 16;
+constexpr int kTabWarps = 8;   // warps of a block that uses a table
+constexpr int kWarpSlots = 8;  // features with warp-private field sums, per warp
 constexpr long long kTabEmpty = -1ll;
 
 __device__ __forceinline__ int tab_slot(long long* key, int64_t fid) {
@@ -608,18 +660,21 @@ struct VoxTable {
   long long key[kTabSlots];
   unsigned n_vox[kTabSlots];
   unsigned long long n_pts[kTabSlots];
-  double sf[kTabSlots], sf2[kTabSlots];
   unsigned fmin[kTabSlots], fmax[kTabSlots];
   int bbmin[kTabSlots][4], bbmax[kTabSlots][4];
   unsigned long long sc[kTabSlots][4];
+  long long wkey[kTabWarps][kWarpSlots];
+  float4 wsf[kTabWarps][kWarpSlots];  // per warp: sum of f (h, l) and of f^2 (h, l)
 
   __device__ __forceinline__ void clear() {
+    for (int i = threadIdx.x; i < kTabWarps * kWarpSlots; i += blockDim.x) {
+      (&wkey[0][0])[i] = kTabEmpty;
+      (&wsf[0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     for (int i = threadIdx.x; i < kTabSlots; i += blockDim.x) {
       key[i] = kTabEmpty;
       n_vox[i] = 0u;
       n_pts[i] = 0ull;
-      sf[i] = 0.0;
-      sf2[i] = 0.0;
       fmin[i] = 0xFFFFFFFFu;
       fmax[i] = 0u;
 #pragma unroll
@@ -630,6 +685,28 @@ struct VoxTable {
       }
     }
   }
+  // a group's field sums: into the warp's own slot for the feature, else into L2
+  __device__ __forceinline__ void add_fsums(const FeatAcc& acc, int64_t fid, const RowSums& r) {
+    const int w = (threadIdx.x >> 5) & (kTabWarps - 1);
+    if (!r.dbl) {
+      uint32_t h = (uint32_t)(((unsigned long long)fid * 0x9E3779B97F4A7C15ull) >> 61);
+#pragma unroll 1
+      for (int i = 0; i < 4; ++i) {
+        const long long old = (long long)atomicCAS(
+            reinterpret_cast<unsigned long long*>(&wkey[w][h]), (unsigned long long)kTabEmpty,
+            (unsigned long long)fid);
+        if (old == kTabEmpty || old == fid) {
+          float4 x = wsf[w][h];
+          df_add2(x.x, x.y, r.s1h, r.s1l);
+          df_add2(x.z, x.w, r.s2h, r.s2l);
+          wsf[w][h] = x;
+          return;
+        }
+        h = (h + 1) & (kWarpSlots - 1);
+      }
+    }
+    commit_fsums(acc, (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + fid, r);
+  }
   // one group's sums: into its slot, or into the accumulators when the table is crowded
   __device__ __forceinline__ void add(const FeatAcc& acc, int64_t fid, const RowSums& r) {
     const int k = tab_slot(key, fid);
@@ -639,8 +716,7 @@ struct VoxTable {
     }
     atomicAdd(n_vox + k, r.n);
     atomicAdd(n_pts + k, (unsigned long long)r.sum_c);
-    atomicAdd(sf + k, r.s1);
-    atomicAdd(sf2 + k, r.s2);
+    add_fsums(acc, fid, r);
     atomicMin(fmin + k, r.kmin);
     atomicMax(fmax + k, r.kmax);
     atomicMin(&bbmin[k][0], r.tw);
@@ -658,14 +734,20 @@ struct VoxTable {
   }
   // every feature met, once into the accumulators
   __device__ __forceinline__ void flush(const FeatAcc& acc) {
+    for (int k = threadIdx.x; k < kTabWarps * kWarpSlots; k += blockDim.x) {
+      const long long f = (&wkey[0][0])[k];
+      if (f == kTabEmpty) continue;
+      const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + f;
+      const float4 x = (&wsf[0][0])[k];
+      add_pair(acc.sf + i, x.x, x.y);
+      add_pair(acc.sf2 + i, x.z, x.w);
+    }
     for (int k = threadIdx.x; k < kTabSlots; k += blockDim.x) {
       const long long f = key[k];
       if (f == kTabEmpty) continue;
       const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + f;
       atomicAdd(acc.n_vox + i, (unsigned long long)n_vox[k]);
       atomicAdd(acc.n_pts + i, n_pts[k]);
-      atomicAdd(acc.sf + i, sf[k]);
-      atomicAdd(acc.sf2 + i, sf2[k]);
       atomicMin(acc.fmin + i, fmin[k]);
       atomicMax(acc.fmax + i, fmax[k]);
 #pragma unroll
@@ -683,8 +765,10 @@ struct VoxTable {
 // Every lane of the warp must call this.
 // Point samples of one warp (lane: ok, feature fid, attributes at attr_p + j * P): the lanes
 // with the same feature reduce in the warp (exact 64-bit fixed-point sums; double-float sums of
-// squares), and one lane per feature hands the sums to sink(f, j, qs, s2a, s2b) with
-// s2 = s2a + s2b. All 32 lanes must call this.
+// squares), and one lane per feature hands the sums to sink(f, j, qs, h, l, w, dbl, one): the sum
+// of squares is h + l (a double-float pair, each exact in fp32), or w in fp64 when dbl is set
+// (non-finite or extreme values, rare); one is set when all the warp's samples belong to f (the
+// call then has a single leader). All 32 lanes must call this.
 template <class Sink>
 __device__ __forceinline__ void reduce_samples(const FeatAcc& acc, bool ok, int64_t fid,
                                                const float* attr_p, int64_t P, Sink&& sink) {
@@ -706,9 +790,12 @@ __device__ __forceinline__ void reduce_samples(const FeatAcc& acc, bool ok, int6
       const unsigned long long qs = (unsigned long long)s0 + ((unsigned long long)s1 << 21) +
                                     ((unsigned long long)s2 << 42);
       const float d = (ok && isfinite(v)) ? v : 0.f;
-      double a2 = 0.0, b2 = 0.0;
-      if (__all_sync(0xFFFFFFFFu, df_safe(d))) {
-        float h = __fmul_rn(d, d), l = __fmaf_rn(d, d, -h);  // d*d == h + l exactly
+      float h = 0.f, l = 0.f;
+      double w = 0.0;
+      const bool dbl = !__all_sync(0xFFFFFFFFu, df_safe(d));
+      if (!dbl) {
+        h = __fmul_rn(d, d);
+        l = __fmaf_rn(d, d, -h);  // d*d == h + l exactly
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
           const float h2 = __shfl_xor_sync(0xFFFFFFFFu, h, o), l2 = __shfl_xor_sync(0xFFFFFFFFu, l, o);
@@ -717,15 +804,12 @@ __device__ __forceinline__ void reduce_samples(const FeatAcc& acc, bool ok, int6
           h = sh;
           l = __fadd_rn(__fadd_rn(l, l2), se);
         }
-        a2 = f2d(h);
-        b2 = f2d(l);
       } else {  // non-finite or extreme values: plain fp64 (rare)
-        double w = (double)d * (double)d;
+        w = (double)d * (double)d;
 #pragma unroll
         for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, o);
-        a2 = w;
       }
-      if (lane == first) sink(f0, j, qs, a2, b2);
+      if (lane == first) sink(f0, j, qs, h, l, w, dbl, true);
     }
     return;
   }
@@ -738,24 +822,23 @@ __device__ __forceinline__ void reduce_samples(const FeatAcc& acc, bool ok, int6
     const float d = isfinite(v) ? v : 0.f;
     long long qs = 0;
     for (unsigned m = grp; m; m &= m - 1) qs += __shfl_sync(grp, q, __ffs(m) - 1);
-    double a2 = 0.0, b2 = 0.0;
-    if (__all_sync(grp, df_safe(d))) {
+    float h = 0.f, l = 0.f;
+    double w = 0.0;
+    const bool dbl = !__all_sync(grp, df_safe(d));
+    if (!dbl) {
       const float p = __fmul_rn(d, d), pe = __fmaf_rn(d, d, -p);
-      float h = 0.f, l = 0.f;
       for (unsigned m = grp; m; m &= m - 1) {
         const int src = __ffs(m) - 1;
         df_add(h, l, __shfl_sync(grp, p, src));
         df_add(h, l, __shfl_sync(grp, pe, src));
       }
-      a2 = f2d(h);
-      b2 = f2d(l);
     } else {
       for (unsigned m = grp; m; m &= m - 1) {
-        const double w = (double)__shfl_sync(grp, d, __ffs(m) - 1);
-        a2 += w * w;
+        const double x = (double)__shfl_sync(grp, d, __ffs(m) - 1);
+        w += x * x;
       }
     }
-    if (lane == leader) sink(fid, j, (unsigned long long)qs, a2, b2);
+    if (lane == leader) sink(fid, j, (unsigned long long)qs, h, l, w, dbl, false);
   }
 }
 
@@ -763,11 +846,12 @@ __device__ __forceinline__ void reduce_samples(const FeatAcc& acc, bool ok, int6
 __device__ __forceinline__ void accumulate_samples(const FeatAcc& acc, bool ok, int64_t fid,
                                                    const float* attr_p, int64_t P) {
   reduce_samples(acc, ok, fid, attr_p, P,
-                 [&](int64_t f, int j, unsigned long long qs, double a2, double b2) {
+                 [&](int64_t f, int j, unsigned long long qs, float h, float l, double w,
+                     bool dbl, bool) {
                    const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + f;
                    atomicAdd(acc.sq + i * acc.A + j, qs);
-                   atomicAdd(acc.sa2 + i * acc.A + j, a2);
-                   if (b2 != 0.0) atomicAdd(acc.sa2 + i * acc.A + j, b2);
+                   if (dbl) atomicAdd(acc.sa2 + i * acc.A + j, w);
+                   else add_pair(acc.sa2 + i * acc.A + j, h, l);
                  });
 }
 
@@ -779,7 +863,7 @@ __device__ __forceinline__ void accumulate_samples(const FeatAcc& acc, bool ok, 
 struct HotCache {
   long long fid;
   unsigned long long sq[MSF_MAX_ATTR];
-  double sa2[MSF_MAX_ATTR];
+  float sh[MSF_MAX_ATTR], sl[MSF_MAX_ATTR];  // sums of squares, double-float
 };
 
 __device__ __forceinline__ void hot_clear(HotCache& h) {
@@ -787,30 +871,56 @@ __device__ __forceinline__ void hot_clear(HotCache& h) {
     h.fid = -1;
     for (int j = 0; j < MSF_MAX_ATTR; ++j) {
       h.sq[j] = 0ull;
-      h.sa2[j] = 0.0;
+      h.sh[j] = 0.f;
+      h.sl[j] = 0.f;
     }
   }
   __syncwarp();
 }
 
-// reduce_samples committing through the warp's cache
-__device__ __forceinline__ void accumulate_samples_hot(const FeatAcc& acc, HotCache& h, bool ok,
+// the cached sums into the accumulators (one lane; the cache is then empty)
+__device__ __forceinline__ void hot_commit(const FeatAcc& acc, HotCache& c) {
+  if (c.fid < 0) return;
+  const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + c.fid;
+  for (int j = 0; j < acc.A; ++j) {
+    atomicAdd(acc.sq + i * acc.A + j, c.sq[j]);
+    add_pair(acc.sa2 + i * acc.A + j, c.sh[j], c.sl[j]);
+    c.sq[j] = 0ull;
+    c.sh[j] = c.sl[j] = 0.f;
+  }
+  c.fid = -1;
+}
+
+// reduce_samples committing through the warp's cache (double-float additions in fp32). With
+// EVICT a call whose samples all belong to one other feature commits the cached feature and
+// caches that one instead: samples walked in voxel order come in runs of one feature, and the
+// run at hand is the one worth caching.
+template <bool EVICT = false>
+__device__ __forceinline__ void accumulate_samples_hot(const FeatAcc& acc, HotCache& c, bool ok,
                                                        int64_t fid, const float* attr_p,
                                                        int64_t P) {
   reduce_samples(acc, ok, fid, attr_p, P,
-                 [&](int64_t f, int j, unsigned long long qs, double a2, double b2) {
-                   if (j == 0 && h.fid < 0)
-                     atomicCAS(reinterpret_cast<unsigned long long*>(&h.fid), ~0ull,
-                               (unsigned long long)f);
-                   if (h.fid == f) {
-                     h.sq[j] += qs;
-                     h.sa2[j] += a2 + b2;
-                     return;
+                 [&](int64_t f, int j, unsigned long long qs, float h, float l, double w,
+                     bool dbl, bool one) {
+                   if (j == 0) {
+                     if (EVICT && one && c.fid != f) {
+                       hot_commit(acc, c);  // the single leader of this call: no race
+                       c.fid = f;
+                     } else if (c.fid < 0) {
+                       atomicCAS(reinterpret_cast<unsigned long long*>(&c.fid), ~0ull,
+                                 (unsigned long long)f);
+                     }
                    }
                    const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + f;
+                   if (c.fid == f) {
+                     c.sq[j] += qs;
+                     if (dbl) atomicAdd(acc.sa2 + i * acc.A + j, w);
+                     else df_add2(c.sh[j], c.sl[j], h, l);
+                     return;
+                   }
                    atomicAdd(acc.sq + i * acc.A + j, qs);
-                   atomicAdd(acc.sa2 + i * acc.A + j, a2);
-                   if (b2 != 0.0) atomicAdd(acc.sa2 + i * acc.A + j, b2);
+                   if (dbl) atomicAdd(acc.sa2 + i * acc.A + j, w);
+                   else add_pair(acc.sa2 + i * acc.A + j, h, l);
                  });
 }
 
@@ -820,7 +930,7 @@ __device__ __forceinline__ void hot_flush(const FeatAcc& acc, HotCache& h) {
   if (h.fid >= 0 && lane < acc.A) {
     const int64_t i = (int64_t)(blockIdx.x & (acc.K - 1)) * acc.F + h.fid;
     atomicAdd(acc.sq + i * acc.A + lane, h.sq[lane]);
-    atomicAdd(acc.sa2 + i * acc.A + lane, h.sa2[lane]);
+    add_pair(acc.sa2 + i * acc.A + lane, h.sh[lane], h.sl[lane]);
   }
 }
 

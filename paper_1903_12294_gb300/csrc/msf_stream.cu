@@ -272,6 +272,7 @@ extern "C" int msf_segment_streamed(msf_ctx* c, int nx, int ny, int nz, int T, c
   // the context's device memory served as the staging area: it holds no dataset now
   c->ds.loaded = false;
   c->ds.binned = false;
+  c->bin.rec_valid = false;
   c->ds.scale_fixed = false;
   c->last.valid = false;
   c->epoch++;
