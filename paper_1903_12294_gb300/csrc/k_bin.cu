@@ -60,7 +60,7 @@ struct BinArgs {
   int32_t* key;                 // [T][P]
   uint32_t* hist;               // [T][nb] samples per (field step, bucket)
   uint32_t* offs;               // [T][nb] exclusive prefix of hist (slot ranges)
-  uint32_t* cursor;             // [T][nb] next free slot, from offs
+  uint32_t* cursor;             // [T][nb] next free slot, from offs, one per kCurStride words
   uint2* rec_vn;                // [P*Tp] the sample's voxel, and the same point's voxel at the
                                 // next point step (-1 at the last or outside the grid)
   float* rec_a;                 // [P*Tp][rec_aw(A)] attribute values (+4 slack)
@@ -68,6 +68,7 @@ struct BinArgs {
   uint32_t* ovf;                // items (t * nb + bucket) left to the wide reduce
   uint32_t* novf;               // their number
   long long wait_cycles;        // limit of those waits (SM cycles)
+  int pf_ahead;                 // reduce: items ahead whose records a block prefetches to L2
   unsigned* absmax;             // [A] float bits of max finite |v|
   unsigned long long* outside;  // [T]
   int32_t* count;               // [T][V]
@@ -103,8 +104,6 @@ __host__ __device__ __forceinline__ int scale_exponent_bits(unsigned mbits, long
   return 62 - e - b;
 }
 
-// 2^x as fp32 for -126 <= x <= 127, built from the bits.
-__device__ __forceinline__ float pow2f(int x) { return __uint_as_float((uint32_t)(x + 127) << 23); }
 
 // int64 -> fp32, round to nearest-even, with integer operations only (the hardware conversion
 // of 64-bit integers issues on the fp64 pipe, which is narrow on this part). |s| < 2^62.
@@ -215,6 +214,9 @@ constexpr int kPlaceNT = 512;                  // threads per block of the place
 constexpr int kPlacePer = 4;                   // samples per thread in flight
 constexpr int kPlaceChunk = 8192;              // samples per block of the place pass
 constexpr int kChunkMax = 65536;               // samples per block of the keys pass, at most
+constexpr int kCurStride = 8;                  // words between two buckets' cursors: one per
+                                               // 32-byte sector, so that the slot atomics of
+                                               // neighbouring buckets do not queue on one sector
 
 template <int A>
 __device__ __forceinline__ float attr_or_zero(const float (&av)[A > 0 ? A : 1], int a) {
@@ -242,11 +244,18 @@ __device__ __forceinline__ void put_record(const BinArgs& b, uint32_t slot, int3
   }
 }
 
+// the cursors start at the scan's offsets
+__global__ void __launch_bounds__(256) k_bin_cursors(const uint32_t* __restrict__ offs,
+                                                     uint32_t* __restrict__ cursor, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256)
+    cursor[i * kCurStride] = __ldg(offs + i);
+}
+
 template <int A>
 __global__ void __launch_bounds__(kPlaceNT) k_bin_place(const __grid_constant__ BinArgs b) {
   __shared__ unsigned s_max[A > 0 ? A : 1];
   const int j = blockIdx.y, blk = blockIdx.x;  // j: the point step
-  uint32_t* crow = b.cursor + (int64_t)__ldg(b.fstep + j) * b.nb;
+  uint32_t* crow = b.cursor + (int64_t)__ldg(b.fstep + j) * b.nb * kCurStride;
   if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
   const int64_t pbeg = (int64_t)blk * kPlaceChunk;
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(kPlaceNT) k_bin_place(const __grid_constant__ 
       for (int a = 0; a < A; ++a)
         if (isfinite(av[u][a])) lmax[a] = max(lmax[a], __float_as_uint(fabsf(av[u][a])));
       if (k[u] < 0) continue;
-      const uint32_t slot = atomicAdd(crow + (k[u] >> b.logR), 1u);
+      const uint32_t slot = atomicAdd(crow + (k[u] >> b.logR) * kCurStride, 1u);
       put_record<A>(b, slot, k[u], kn[u], av[u]);
     }
   }
@@ -419,6 +428,18 @@ __global__ void __launch_bounds__(kBinNT, A <= 4 ? 3 : 2) k_bin_reduce(const __g
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     if (any) reduce_issue<A>(b, s0, e1 - s0, s_stv, s_sta, &s_bar);
+    // the records of the item one wave of blocks later, into L2 (its block then copies from
+    // there instead of from DRAM)
+    const int64_t nxt = (int64_t)t * b.nb + bucket + b.pf_ahead;
+    if (nxt < (int64_t)b.T * b.nb) {
+      uint32_t q0, q1;
+      item_range(b, (int)(nxt / b.nb), (int)(nxt % b.nb), nrec, q0, q1);
+      if (q1 > q0 && q1 - q0 <= (uint32_t)kRedStage) {
+        const uint32_t p0 = q0 & ~3u, p1 = (q1 + 3u) & ~3u;
+        prefetch_l2(b.rec_vn + p0, 8u * (p1 - p0));
+        if (rec_aw(A)) prefetch_l2(b.rec_a + (size_t)p0 * rec_aw(A), 4u * rec_aw(A) * (p1 - p0));
+      }
+    }
   }
   if ((int)threadIdx.x < A) item_scale(b, threadIdx.x, s_k, s_f1, s_f2);
   for (int q = threadIdx.x; q < R / 4; q += kBinNT)
@@ -839,7 +860,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
     return MSF_ERR_TOO_LARGE;
   MSF_TRY(S.hist.ensure(sizeof(uint32_t) * TB));
   MSF_TRY(S.offs.ensure(sizeof(uint32_t) * TB));
-  MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * TB));
+  MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * kCurStride * TB));
   // records: voxels [NR] and attributes [NR][AW], with room for the rounded-up bulk copies
   const int64_t NRp = (NR + 3) & ~(int64_t)3;
   MSF_TRY(S.rec_vn.ensure(sizeof(uint2) * (NRp + 4)));
@@ -861,6 +882,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.rec_vn = S.rec_vn.as<uint2>();
   b.rec_a = S.rec_a.as<float>();
   b.wait_cycles = ctx->wait_cycles;
+  b.pf_ahead = ctx->sm_count * (d.A <= 4 ? 3 : 2);  // resident reduce blocks
   b.err = S.total.as<uint32_t>() + 2;
   b.novf = S.total.as<uint32_t>() + 3;
   b.ovf = S.ovf.as<uint32_t>();
@@ -882,8 +904,12 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
     launch_bin_a(ctx, b, keep, 0, smem);
     MSF_CUDA_TRY(cudaGetLastError());
     MSF_TRY(scan_exclusive_u32(ctx, b.hist, b.offs, TB, S.scan_tmp, S.total.as<uint32_t>()));
-    MSF_CUDA_TRY(cudaMemcpyAsync(b.cursor, b.offs, sizeof(uint32_t) * TB,
-                                 cudaMemcpyDeviceToDevice, s));
+    {
+      ScopedKernel k(ctx, "k_bin_cursors");
+      k_bin_cursors<<<(unsigned)std::min<int64_t>((TB + 255) / 256, (int64_t)ctx->sm_count * 16),
+                      256, 0, s>>>(b.offs, b.cursor, TB);
+    }
+    MSF_CUDA_TRY(cudaGetLastError());
     launch_bin_a(ctx, b, keep, 1, smem);
     MSF_CUDA_TRY(cudaGetLastError());
     b.nrec = S.total.as<uint32_t>();  // the scan's total: the last bucket's end

@@ -335,6 +335,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// bulk prefetch of [src, src + bytes) into L2 (16-byte aligned, a multiple of 16 bytes)
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -763,6 +767,18 @@ struct VoxTable {
 // Point samples (one per lane in `ok`): lanes of the same feature reduce their exact
 // fixed-point attribute values and double-float squares; the group's first lane commits.
 // Every lane of the warp must call this.
+// 2^x as fp32 for -126 <= x <= 127, built from the bits.
+__device__ __forceinline__ float pow2f(int x) { return __uint_as_float((uint32_t)(x + 127) << 23); }
+
+// exact 64-bit sum (mod 2^64) over the lanes of mask m, from three group reductions of the
+// 21/21/22-bit parts (each part sum of up to 32 lanes fits 32 bits)
+__device__ __forceinline__ unsigned long long limb_sum(unsigned m, unsigned long long u) {
+  const uint32_t s0 = __reduce_add_sync(m, (uint32_t)(u & 0x1FFFFFull));
+  const uint32_t s1 = __reduce_add_sync(m, (uint32_t)((u >> 21) & 0x1FFFFFull));
+  const uint32_t s2 = __reduce_add_sync(m, (uint32_t)(u >> 42));
+  return (unsigned long long)s0 + ((unsigned long long)s1 << 21) + ((unsigned long long)s2 << 42);
+}
+
 // Point samples of one warp (lane: ok, feature fid, attributes at attr_p + j * P): the lanes
 // with the same feature reduce in the warp (exact 64-bit fixed-point sums; double-float sums of
 // squares), and one lane per feature hands the sums to sink(f, j, qs, h, l, w, dbl, one): the sum
@@ -814,23 +830,40 @@ __device__ __forceinline__ void reduce_samples(const FeatAcc& acc, bool ok, int6
     return;
   }
   if (!ok) return;
+  // Several features: the lanes of each feature's group reduce with the hardware group
+  // reductions, no member loops. The fixed-point values sum exactly as three 21/21/22-bit
+  // limbs. Each square d*d = p + pe (exact) is put on a fixed-point grid of the group,
+  // 2^-52 of the group's largest square (k2 from the largest exponent): every term then fits
+  // 53 bits, the group's sum of up to 32 of them fits 58, and it sums exactly as limbs; the
+  // sum becomes a double-float pair again (24 significant bits, then the rest). Squares below
+  // 2^-52 of the largest drop out, well inside the sums' fp64-level tolerance.
   const unsigned grp = __match_any_sync(act, fid);
   const int leader = __ffs(grp) - 1;
   for (int j = 0; j < acc.A; ++j) {
     const float v = __ldg(attr_p + (int64_t)j * P);
-    const long long q = quantise(v, acc.kscale[j]);
+    const unsigned long long u = (unsigned long long)quantise(v, acc.kscale[j]);
+    const unsigned long long qs = limb_sum(grp, u);
     const float d = isfinite(v) ? v : 0.f;
-    long long qs = 0;
-    for (unsigned m = grp; m; m &= m - 1) qs += __shfl_sync(grp, q, __ffs(m) - 1);
     float h = 0.f, l = 0.f;
     double w = 0.0;
-    const bool dbl = !__all_sync(grp, df_safe(d));
+    const float ad = fabsf(d);
+    const bool dbl = !__all_sync(grp, ad == 0.f || (ad >= 0x1p-40f && ad <= 1.0e18f));
     if (!dbl) {
-      const float p = __fmul_rn(d, d), pe = __fmaf_rn(d, d, -p);
-      for (unsigned m = grp; m; m &= m - 1) {
-        const int src = __ffs(m) - 1;
-        df_add(h, l, __shfl_sync(grp, p, src));
-        df_add(h, l, __shfl_sync(grp, pe, src));
+      const unsigned emax = __reduce_max_sync(grp, (__float_as_uint(d) >> 23) & 0xFFu);
+      if (emax) {
+        const int k2 = 304 - 2 * (int)emax;  // |d| < 2^(emax-126): d*d * 2^k2 < 2^52
+        const float p = __fmul_rn(d, d), pe = __fmaf_rn(d, d, -p);
+        const unsigned long long q2 =
+            (unsigned long long)(quantise(p, k2) + quantise(pe, k2));
+        const unsigned long long S = limb_sum(grp, q2);
+        const int sh = max(0, 40 - __clzll(S));  // S >> sh: at most 24 significant bits
+        const unsigned long long a = S >> sh;
+        h = __fmul_rn(__fmul_rn(__uint2float_rn((uint32_t)a), pow2f((sh - k2) / 2)),
+                      pow2f((sh - k2) - (sh - k2) / 2));
+        const unsigned long long r = S - (a << sh);  // below 2^sh: its top 24 bits
+        const int sr = max(0, sh - 24);
+        l = __fmul_rn(__fmul_rn(__uint2float_rn((uint32_t)(r >> sr)), pow2f((sr - k2) / 2)),
+                      pow2f((sr - k2) - (sr - k2) / 2));
       }
     } else {
       for (unsigned m = grp; m; m &= m - 1) {
