@@ -345,7 +345,10 @@ def run_gpu(args):
         hp = wl.pos.cpu().pin_memory()
         ha = wl.attr.cpu().pin_memory()
         hl = torch.empty((tw, nz, ny, nx), dtype=torch.int32).pin_memory()
-        hfeat = np.zeros(fcap, msf.FEATURE_DTYPE)
+        # the feature table lands in pinned host memory too (pageable memory would copy at a
+        # fraction of the link's rate)
+        hfeat_t = torch.zeros((fcap * msf.FEATURE_DTYPE.itemsize,), dtype=torch.uint8).pin_memory()
+        hfeat = hfeat_t.numpy().view(msf.FEATURE_DTYPE)
         if rank == 0:
             hashes = {"field": input_sha256(hf), "pos": input_sha256(hp), "attr": input_sha256(ha)}
 
@@ -380,7 +383,7 @@ def run_gpu(args):
         e2e = {"value": round(replicas.weak_throughput(vt, ms_e2e, world) / 1e9, 3), "unit": UNIT,
                "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
-        del hf, hp, ha, hl
+        del hf, hp, ha, hl, hfeat, hfeat_t
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

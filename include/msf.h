@@ -170,7 +170,13 @@ int msf_set_stream(msf_ctx* ctx, void* stream);
  *                                  all timesteps (its trajectory)
  *   attr  [T][A][P]                v_p(t), A point attributes (A <= MSF_MAX_ATTR)
  * ptr_kind says whether the three pointers are host or device memory. P may be 0 (pos and
- * attr may then be NULL); A may be 0. The previous binning is discarded.
+ * attr may then be NULL); A may be 0. The previous binning is discarded. Host data is copied
+ * asynchronously (the host link, not the device, bounds a load): the point steps in chunks of
+ * field steps, then the field, on a copy stream of the context; msf_bin_particles bins each
+ * chunk as it arrives, and every call that reads the field waits for it. Page-locked host
+ * buffers must therefore stay unchanged until msf_bin_particles and the first call that reads
+ * the field (for P = 0: the first call that reads the field) have returned; pageable buffers
+ * are staged before the copies are queued and may be reused at once.
  * Errors: INVALID_ARG (sizes <= 0, A > MSF_MAX_ATTR, NULL pointers), TOO_LARGE (nx*ny*nz >=
  * 2^31 or P >= 2^31), OUT_OF_MEMORY, CUDA. */
 int msf_load_timesteps(msf_ctx* ctx, int nx, int ny, int nz, int T, const float* field,

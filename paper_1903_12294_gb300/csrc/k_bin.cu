@@ -54,12 +54,14 @@ struct BinArgs {
   int logR, nb;                 // bucket = voxel >> logR; nb buckets
   int nblk;                     // sample blocks per point step of the keys pass
   int64_t chunk;                // samples per block of the keys pass
-  const uint32_t* nrec;         // device: records in all (samples inside the grid); null = none
+  int jbase;                    // keys and place passes: first point step of the launch
   const float* pos;             // [T][3][P]
   const float* attr;            // [T][A][P]
   int32_t* key;                 // [T][P]
   uint32_t* hist;               // [T][nb] samples per (field step, bucket)
-  uint32_t* offs;               // [T][nb] exclusive prefix of hist (slot ranges)
+  uint32_t* offs;               // [T][nb + 1] slot ranges: the step's record region (from
+                                // pj0[t] * P) split by the exclusive prefix of hist; [t][nb]
+                                // ends the step's records
   uint32_t* cursor;             // [T][nb] next free slot, from offs, one per kCurStride words
   uint2* rec_vn;                // [P*Tp] the sample's voxel, and the same point's voxel at the
                                 // next point step (-1 at the last or outside the grid)
@@ -149,7 +151,7 @@ __device__ __forceinline__ float div_count(float x, int c) {
 template <bool SMEM>
 __global__ void __launch_bounds__(256) k_bin_keys(const __grid_constant__ BinArgs b) {
   __shared__ uint32_t s_hist[SMEM ? kHistSmem : 1];
-  const int t = blockIdx.y, blk = blockIdx.x;  // t: the point step
+  const int t = b.jbase + blockIdx.y, blk = blockIdx.x;  // t: the point step
   uint32_t* hrow = b.hist + (int64_t)__ldg(b.fstep + t) * b.nb;
   if (SMEM) {
     for (int i = threadIdx.x; i < b.nb; i += 256) s_hist[i] = 0u;
@@ -214,9 +216,9 @@ constexpr int kPlaceNT = 512;                  // threads per block of the place
 constexpr int kPlacePer = 4;                   // samples per thread in flight
 constexpr int kPlaceChunk = 8192;              // samples per block of the place pass
 constexpr int kChunkMax = 65536;               // samples per block of the keys pass, at most
-constexpr int kCurStride = 8;                  // words between two buckets' cursors: one per
-                                               // 32-byte sector, so that the slot atomics of
-                                               // neighbouring buckets do not queue on one sector
+constexpr int kCurStride = 32;                 // words between two buckets' cursors: one per
+                                               // 128-byte line, so that the slot atomics of
+                                               // neighbouring buckets do not queue on one line
 
 template <int A>
 __device__ __forceinline__ float attr_or_zero(const float (&av)[A > 0 ? A : 1], int a) {
@@ -244,17 +246,57 @@ __device__ __forceinline__ void put_record(const BinArgs& b, uint32_t slot, int3
   }
 }
 
-// the cursors start at the scan's offsets
-__global__ void __launch_bounds__(256) k_bin_cursors(const uint32_t* __restrict__ offs,
-                                                     uint32_t* __restrict__ cursor, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256)
-    cursor[i * kCurStride] = __ldg(offs + i);
+// One block per field step t of [t0, t0 + gridDim.x): the step's records take the region that
+// starts at pj0[t] * P (room for all of its point steps' samples), so that field steps bin
+// independently of each other; the exclusive prefix of its bucket counts splits the region into
+// the buckets' slot ranges (offs[t][nb]: the end of its records), and the slot cursors start
+// there.
+constexpr int kScanNT = 1024;
+
+__global__ void __launch_bounds__(kScanNT) k_bin_scan_steps(const __grid_constant__ BinArgs b,
+                                                             int t0) {
+  __shared__ uint32_t s_w[kScanNT / 32];
+  const int t = t0 + (int)blockIdx.x;
+  const uint32_t* h = b.hist + (int64_t)t * b.nb;
+  uint32_t* o = b.offs + (int64_t)t * (b.nb + 1);
+  uint32_t* c = b.cursor + (int64_t)t * b.nb * kCurStride;
+  const uint32_t base = (uint32_t)((int64_t)__ldg(b.pj0 + t) * b.P);
+  const int per = (b.nb + kScanNT - 1) / kScanNT;
+  const int lo = min((int)threadIdx.x * per, b.nb), hi = min(lo + per, b.nb);
+  uint32_t sum = 0;
+  for (int i = lo; i < hi; ++i) sum += h[i];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t y = s_w[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t z = __shfl_up_sync(0xFFFFFFFFu, y, d);
+      if (lane >= d) y += z;
+    }
+    s_w[lane] = y;
+  }
+  __syncthreads();
+  uint32_t run = base + (x - sum) + (w ? s_w[w - 1] : 0u);
+  for (int i = lo; i < hi; ++i) {
+    o[i] = run;
+    c[(int64_t)i * kCurStride] = run;
+    run += h[i];
+  }
+  if (threadIdx.x == kScanNT - 1) o[b.nb] = base + s_w[kScanNT / 32 - 1];
 }
 
 template <int A>
 __global__ void __launch_bounds__(kPlaceNT) k_bin_place(const __grid_constant__ BinArgs b) {
   __shared__ unsigned s_max[A > 0 ? A : 1];
-  const int j = blockIdx.y, blk = blockIdx.x;  // j: the point step
+  const int j = b.jbase + blockIdx.y, blk = blockIdx.x;  // j: the point step
   uint32_t* crow = b.cursor + (int64_t)__ldg(b.fstep + j) * b.nb * kCurStride;
   if ((int)threadIdx.x < A) s_max[threadIdx.x] = 0u;
   __syncthreads();
@@ -312,13 +354,13 @@ __device__ __forceinline__ void reduce_issue(const BinArgs& b, uint32_t a0, uint
 }
 
 // record range [r0, r1) of the item (field step t, bucket): the slots of its point steps
-__device__ __forceinline__ void item_range(const BinArgs& b, int t, int bucket, uint32_t nrec,
-                                           uint32_t& r0, uint32_t& r1) {
+__device__ __forceinline__ void item_range(const BinArgs& b, int t, int bucket, uint32_t& r0,
+                                           uint32_t& r1) {
   r0 = r1 = 0u;
-  if (!nrec) return;
-  const int64_t h = (int64_t)t * b.nb + bucket;
+  if (b.P == 0) return;
+  const int64_t h = (int64_t)t * (b.nb + 1) + bucket;
   r0 = __ldg(b.offs + h);
-  r1 = h + 1 < (int64_t)b.T * b.nb ? __ldg(b.offs + h + 1) : nrec;
+  r1 = __ldg(b.offs + h + 1);
 }
 
 // the fixed-point exponent of attribute a and the two exact factors of 2^-k
@@ -416,9 +458,8 @@ __global__ void __launch_bounds__(kBinNT, A <= 4 ? 3 : 2) k_bin_reduce(const __g
   __shared__ int s_k[A > 0 ? A : 1];
   __shared__ float s_f1[A > 0 ? A : 1], s_f2[A > 0 ? A : 1];
   const int bucket = blockIdx.x, t = blockIdx.y;  // t: the field step
-  const uint32_t nrec = b.nrec ? *b.nrec : 0u;
   uint32_t r0, r1;
-  item_range(b, t, bucket, nrec, r0, r1);
+  item_range(b, t, bucket, r0, r1);
   if (r1 - r0 > (uint32_t)kRedStage) {  // too many records to stage: the wide pass takes it
     if (threadIdx.x == 0) b.ovf[atomicAdd(b.novf, 1u)] = (uint32_t)t * (uint32_t)b.nb + bucket;
     return;
@@ -433,7 +474,7 @@ __global__ void __launch_bounds__(kBinNT, A <= 4 ? 3 : 2) k_bin_reduce(const __g
     const int64_t nxt = (int64_t)t * b.nb + bucket + b.pf_ahead;
     if (nxt < (int64_t)b.T * b.nb) {
       uint32_t q0, q1;
-      item_range(b, (int)(nxt / b.nb), (int)(nxt % b.nb), nrec, q0, q1);
+      item_range(b, (int)(nxt / b.nb), (int)(nxt % b.nb), q0, q1);
       if (q1 > q0 && q1 - q0 <= (uint32_t)kRedStage) {
         const uint32_t p0 = q0 & ~3u, p1 = (q1 + 3u) & ~3u;
         prefetch_l2(b.rec_vn + p0, 8u * (p1 - p0));
@@ -614,9 +655,8 @@ __global__ void __launch_bounds__(kBinNT, 1) k_bin_reduce_wide(const __grid_cons
   __syncthreads();  // the previous item's reads of shared memory are done
   const uint32_t itm = b.ovf[it];
   const int bucket = (int)(itm % (uint32_t)b.nb), t = (int)(itm / (uint32_t)b.nb);
-  const uint32_t nrec = b.nrec ? *b.nrec : 0u;
   uint32_t r0, r1;
-  item_range(b, t, bucket, nrec, r0, r1);
+  item_range(b, t, bucket, r0, r1);
   const uint32_t s0 = r0 & ~3u, e1 = (r1 + 3u) & ~3u;
   const int npiece = r1 > r0 ? (int)((e1 - s0 + (uint32_t)R - 1) / (uint32_t)R) : 0;
   if (threadIdx.x == 0 && npiece) {
@@ -764,21 +804,23 @@ static void allow_smem(K kernel, size_t bytes, std::atomic<size_t>& set) {
   }
 }
 
+// phase 0: keys of point steps [j0, j0 + nj); 1: their records; 2: every (bucket, field step)
 template <int A>
-static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, bool smem) {
-  cudaStream_t s = ctx->stream;
-  const dim3 gs((unsigned)b.nblk, (unsigned)b.Tp);  // (block, point step)
-  const dim3 gp((unsigned)((b.P + kPlaceChunk - 1) / kPlaceChunk), (unsigned)b.Tp);
+static void launch_bin(msf_ctx* ctx, BinArgs b, bool keep, int phase, bool smem, cudaStream_t s,
+                       int j0, int nj) {
+  b.jbase = j0;
+  const dim3 gs((unsigned)b.nblk, (unsigned)nj);  // (block, point step)
+  const dim3 gp((unsigned)((b.P + kPlaceChunk - 1) / kPlaceChunk), (unsigned)nj);
   if (phase == 0) {
-    ScopedKernel k(ctx, "k_bin_keys");
+    ScopedKernel k(ctx, "k_bin_keys", s);
     if (smem) k_bin_keys<true><<<gs, 256, 0, s>>>(b);
     else k_bin_keys<false><<<gs, 256, 0, s>>>(b);
   } else if (phase == 1) {
-    ScopedKernel k(ctx, "k_bin_place");
+    ScopedKernel k(ctx, "k_bin_place", s);
     k_bin_place<A><<<gp, kPlaceNT, 0, s>>>(b);
   } else {
     {
-      ScopedKernel k(ctx, "k_bin_reduce");
+      ScopedKernel k(ctx, "k_bin_reduce", s);
       const size_t sm = reduce_smem(A, b.logR);
       const dim3 gr((unsigned)b.nb, (unsigned)b.T);
       if (keep) {
@@ -794,7 +836,7 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
     {
       // the buckets k_bin_reduce listed (more records than it stages); blocks beyond their
       // number leave at once
-      ScopedKernel k(ctx, "k_bin_reduce_wide");
+      ScopedKernel k(ctx, "k_bin_reduce_wide", s);
       const size_t sm = reduce_wide_smem(A, b.logR);
       const unsigned g = (unsigned)std::min<int64_t>((int64_t)b.nb * b.T, (int64_t)ctx->sm_count * 2);
       if (keep) {
@@ -810,17 +852,18 @@ static void launch_bin(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, boo
   }
 }
 
-static void launch_bin_a(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, bool smem) {
+static void launch_bin_a(msf_ctx* ctx, const BinArgs& b, bool keep, int phase, bool smem,
+                         cudaStream_t s, int j0 = 0, int nj = 0) {
   switch (b.A) {
-    case 0: launch_bin<0>(ctx, b, keep, phase, smem); break;
-    case 1: launch_bin<1>(ctx, b, keep, phase, smem); break;
-    case 2: launch_bin<2>(ctx, b, keep, phase, smem); break;
-    case 3: launch_bin<3>(ctx, b, keep, phase, smem); break;
-    case 4: launch_bin<4>(ctx, b, keep, phase, smem); break;
-    case 5: launch_bin<5>(ctx, b, keep, phase, smem); break;
-    case 6: launch_bin<6>(ctx, b, keep, phase, smem); break;
-    case 7: launch_bin<7>(ctx, b, keep, phase, smem); break;
-    default: launch_bin<8>(ctx, b, keep, phase, smem); break;
+    case 0: launch_bin<0>(ctx, b, keep, phase, smem, s, j0, nj); break;
+    case 1: launch_bin<1>(ctx, b, keep, phase, smem, s, j0, nj); break;
+    case 2: launch_bin<2>(ctx, b, keep, phase, smem, s, j0, nj); break;
+    case 3: launch_bin<3>(ctx, b, keep, phase, smem, s, j0, nj); break;
+    case 4: launch_bin<4>(ctx, b, keep, phase, smem, s, j0, nj); break;
+    case 5: launch_bin<5>(ctx, b, keep, phase, smem, s, j0, nj); break;
+    case 6: launch_bin<6>(ctx, b, keep, phase, smem, s, j0, nj); break;
+    case 7: launch_bin<7>(ctx, b, keep, phase, smem, s, j0, nj); break;
+    default: launch_bin<8>(ctx, b, keep, phase, smem, s, j0, nj); break;
   }
 }
 
@@ -859,7 +902,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
       (d.P + kPlaceChunk - 1) / kPlaceChunk > 0x7FFFFFFF)
     return MSF_ERR_TOO_LARGE;
   MSF_TRY(S.hist.ensure(sizeof(uint32_t) * TB));
-  MSF_TRY(S.offs.ensure(sizeof(uint32_t) * TB));
+  MSF_TRY(S.offs.ensure(sizeof(uint32_t) * (TB + d.T)));
   MSF_TRY(S.cursor.ensure(sizeof(uint32_t) * kCurStride * TB));
   // records: voxels [NR] and attributes [NR][AW], with room for the rounded-up bulk copies
   const int64_t NRp = (NR + 3) & ~(int64_t)3;
@@ -867,7 +910,7 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   MSF_TRY(S.rec_a.ensure(sizeof(float) * ((NRp + 4) * (AW > 0 ? AW : 1))));
   MSF_TRY(S.absmax.ensure(sizeof(unsigned) * MSF_MAX_ATTR));
   MSF_TRY(S.outside.ensure(sizeof(unsigned long long) * d.Tp));
-  MSF_TRY(S.total.ensure(sizeof(uint32_t) * 4));  // [0] records, [2] error word, [3] wide items
+  MSF_TRY(S.total.ensure(sizeof(uint32_t) * 4));  // [2] error word, [3] wide items
   MSF_TRY(S.ovf.ensure(sizeof(uint32_t) * (size_t)d.T * (size_t)b.nb));
   MSF_TRY(d.key.ensure(sizeof(int32_t) * ((int64_t)d.Tp * d.P + 4)));  // slack: bulk copies
   MSF_TRY(d.count.ensure(sizeof(int32_t) * d.T * d.V));
@@ -891,6 +934,15 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   b.count = d.count.as<int32_t>();
   b.mean = d.mean.as<float>();
   b.sumq = keep ? d.sumq.as<long long>() : nullptr;
+  // Points still coming in from the host (msf_load_timesteps with host pointers): the field
+  // steps are binned chunk by chunk as their point steps arrive. Every field step's records own
+  // the region from pj0[t] * P, so the steps' histograms, slot ranges and records are
+  // independent of each other; a chunk's records need the keys of the next chunk's first point
+  // step (the next-step voxel), so keys run one chunk ahead of the records.
+  std::vector<int> ct = {0, d.T};
+  const bool piped = ctx->points_pending && d.P > 0;
+  if (piped) ct = ctx->chunk_t;
+  ctx->points_pending = false;
   MSF_CUDA_TRY(cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * TB, s));
   if (d.scale_fixed)  // the whole dataset's maxima: a slab's can only be smaller
     MSF_CUDA_TRY(cudaMemcpyAsync(b.absmax, d.scale_absmax, sizeof(unsigned) * MSF_MAX_ATTR,
@@ -899,32 +951,36 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
     MSF_CUDA_TRY(cudaMemsetAsync(b.absmax, 0, sizeof(unsigned) * MSF_MAX_ATTR, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.outside, 0, sizeof(unsigned long long) * d.Tp, s));
   MSF_CUDA_TRY(cudaMemsetAsync(b.err, 0, 2 * sizeof(uint32_t), s));  // error word, wide items
-  b.nrec = nullptr;
   if (d.P > 0) {
-    launch_bin_a(ctx, b, keep, 0, smem);
-    MSF_CUDA_TRY(cudaGetLastError());
-    MSF_TRY(scan_exclusive_u32(ctx, b.hist, b.offs, TB, S.scan_tmp, S.total.as<uint32_t>()));
-    {
-      ScopedKernel k(ctx, "k_bin_cursors");
-      k_bin_cursors<<<(unsigned)std::min<int64_t>((TB + 255) / 256, (int64_t)ctx->sm_count * 16),
-                      256, 0, s>>>(b.offs, b.cursor, TB);
+    const int G = (int)ct.size() - 1;
+    auto keys = [&](int g) -> int {
+      if (piped) MSF_CUDA_TRY(cudaStreamWaitEvent(s, ctx->ev_chunk[g], 0));
+      const int j0 = d.h_pj0[ct[g]], j1 = d.h_pj0[ct[g + 1]];
+      if (j1 > j0) launch_bin_a(ctx, b, keep, 0, smem, s, j0, j1 - j0);
+      MSF_CUDA_TRY(cudaGetLastError());
+      return MSF_OK;
+    };
+    MSF_TRY(keys(0));
+    for (int g = 0; g < G; ++g) {
+      if (g + 1 < G) MSF_TRY(keys(g + 1));
+      {
+        ScopedKernel k(ctx, "k_bin_scan_steps", s);
+        k_bin_scan_steps<<<(unsigned)(ct[g + 1] - ct[g]), kScanNT, 0, s>>>(b, ct[g]);
+      }
+      const int j0 = d.h_pj0[ct[g]], j1 = d.h_pj0[ct[g + 1]];
+      if (j1 > j0) launch_bin_a(ctx, b, keep, 1, smem, s, j0, j1 - j0);
+      MSF_CUDA_TRY(cudaGetLastError());
     }
-    MSF_CUDA_TRY(cudaGetLastError());
-    launch_bin_a(ctx, b, keep, 1, smem);
-    MSF_CUDA_TRY(cudaGetLastError());
-    b.nrec = S.total.as<uint32_t>();  // the scan's total: the last bucket's end
   }
-  launch_bin_a(ctx, b, keep, 2, smem);
+  launch_bin_a(ctx, b, keep, 2, smem, s);
   MSF_CUDA_TRY(cudaGetLastError());
   std::vector<unsigned long long> out(d.Tp);
   unsigned hmax[MSF_MAX_ATTR] = {};
   MSF_CUDA_TRY(cudaMemcpyAsync(out.data(), S.outside.p, sizeof(unsigned long long) * d.Tp,
                                cudaMemcpyDeviceToHost, s));
   MSF_CUDA_TRY(cudaMemcpyAsync(hmax, S.absmax.p, sizeof(hmax), cudaMemcpyDeviceToHost, s));
-  uint32_t herr = 0, hrec = 0;
+  uint32_t herr = 0;
   MSF_CUDA_TRY(cudaMemcpyAsync(&herr, b.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  if (d.P > 0)
-    MSF_CUDA_TRY(cudaMemcpyAsync(&hrec, S.total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   S.rec_valid = false;
   MSF_CUDA_TRY(cudaStreamSynchronize(s));
   ctx->timer.flush();
@@ -936,7 +992,6 @@ int bin_run(msf_ctx* ctx, unsigned flags) {
   S.rec_logR = b.logR;
   S.rec_nb = b.nb;
   S.rec_aw = AW;
-  S.rec_n = hrec;
   for (int a = 0; a < d.A; ++a) {
     float m;
     memcpy(&m, &hmax[a], sizeof(float));

@@ -710,22 +710,22 @@ constexpr int kRecChunk = 32768;
 struct RecView {
   const uint2* rec_vn;    // [records] voxel, the point's voxel at the next point step (or -1)
   const float* rec_a;     // [records][aw] attributes
-  const uint32_t* offs;   // [T][nb] first record of each (field step, bucket)
-  uint32_t nrec;
-  int nb, T, aw;
+  const uint32_t* offs;   // [T][nb + 1] first record of each (field step, bucket); [t][nb]
+                          // ends field step t's records
+  int nb, aw;
 };
 
 static RecView rec_view(const msf_ctx* ctx) {
   const BinScratch& B = ctx->bin;
-  return RecView{B.rec_vn.as<uint2>(), B.rec_a.as<float>(), B.offs.as<uint32_t>(), B.rec_n,
-                 B.rec_nb, ctx->ds.T, B.rec_aw};
+  return RecView{B.rec_vn.as<uint2>(), B.rec_a.as<float>(), B.offs.as<uint32_t>(), B.rec_nb,
+                 B.rec_aw};
 }
 
 // records [b0, b1) of block x of field step t; false when the block has none
 __device__ __forceinline__ bool rec_block(const RecView& rv, int t, uint32_t& b0, uint32_t& b1) {
-  const int64_t h = (int64_t)t * rv.nb;
+  const int64_t h = (int64_t)t * (rv.nb + 1);
   const uint32_t rb = __ldg(rv.offs + h);
-  const uint32_t re = h + rv.nb < (int64_t)rv.T * rv.nb ? __ldg(rv.offs + h + rv.nb) : rv.nrec;
+  const uint32_t re = __ldg(rv.offs + h + rv.nb);
   b0 = rb + blockIdx.x * (uint32_t)kRecChunk;
   if (b0 >= re) return false;
   b1 = min(re, b0 + (uint32_t)kRecChunk);

@@ -368,6 +368,12 @@ void msf_destroy(msf_ctx* c) {
     cudaEventDestroy(c->ev_join);
   }
   if (c->ev_field) cudaEventDestroy(c->ev_field);
+  if (c->copy) {
+    cudaStreamSynchronize(c->copy);
+    cudaStreamDestroy(c->copy);
+    cudaEventDestroy(c->ev_copy);
+  }
+  for (cudaEvent_t e : c->ev_chunk) cudaEventDestroy(e);
   delete c;
 }
 
@@ -433,9 +439,56 @@ int msf_load_timesteps_mr(msf_ctx* c, int nx, int ny, int nz, int T, const float
                                cudaMemcpyHostToDevice, c->stream));
   MSF_CUDA_TRY(cudaMemcpyAsync(d.pj0.p, d.h_pj0.data(), sizeof(int32_t) * (T + 1),
                                cudaMemcpyHostToDevice, c->stream));
-  // points first on the context stream; then the field on the auxiliary stream, so that
-  // binning (which reads only the points) overlaps the field's copy; readers of the field
-  // wait for it (ctx_field_ready)
+  c->points_pending = false;
+  if (ptr_kind == MSF_HOST && P > 0) {
+    // Host data over the link (its bandwidth, not the device's, bounds the load): the points in
+    // chunks of field steps on the copy stream, each chunk's arrival an event that binning waits
+    // for, so that it bins a chunk while the next ones are still coming; then the field, whose
+    // readers wait for it (ctx_field_ready).
+    if (!c->copy) {
+      MSF_CUDA_TRY(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking));
+      MSF_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming));
+    }
+    if (!c->ev_field) MSF_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_field, cudaEventDisableTiming));
+    MSF_TRY(d.pos.ensure(sizeof(float) * 3 * P * Tp + 16));
+    MSF_TRY(d.attr.ensure(sizeof(float) * std::max(A, 1) * P * Tp + 16));
+    MSF_TRY(d.field.ensure(sizeof(float) * V * T + 16));
+    MSF_CUDA_TRY(cudaEventRecord(c->ev_copy, c->stream));  // earlier readers of the buffers
+    MSF_CUDA_TRY(cudaStreamWaitEvent(c->copy, c->ev_copy, 0));
+    const int per = std::max(1, T / 12);  // field steps per chunk: about a dozen chunks
+    c->chunk_t.clear();
+    for (int t = 0; t < T; t += per) c->chunk_t.push_back(t);
+    c->chunk_t.push_back(T);
+    const int G = (int)c->chunk_t.size() - 1;
+    while ((int)c->ev_chunk.size() < G) {
+      cudaEvent_t e;
+      MSF_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c->ev_chunk.push_back(e);
+    }
+    for (int g = 0; g < G; ++g) {
+      const int64_t j0 = d.h_pj0[c->chunk_t[g]], j1 = d.h_pj0[c->chunk_t[g + 1]];
+      if (j1 > j0) {
+        MSF_CUDA_TRY(cudaMemcpyAsync(d.pos.as<float>() + j0 * 3 * P, pos + j0 * 3 * P,
+                                     sizeof(float) * 3 * P * (j1 - j0), cudaMemcpyHostToDevice,
+                                     c->copy));
+        if (A > 0)
+          MSF_CUDA_TRY(cudaMemcpyAsync(d.attr.as<float>() + j0 * A * P, attr + j0 * A * P,
+                                       sizeof(float) * A * P * (j1 - j0), cudaMemcpyHostToDevice,
+                                       c->copy));
+      }
+      MSF_CUDA_TRY(cudaEventRecord(c->ev_chunk[g], c->copy));
+    }
+    MSF_CUDA_TRY(cudaMemcpyAsync(d.field.p, field, sizeof(float) * V * T, cudaMemcpyHostToDevice,
+                                 c->copy));
+    MSF_CUDA_TRY(cudaEventRecord(c->ev_field, c->copy));
+    c->field_pending = true;
+    c->points_pending = true;
+    d.loaded = true;
+    return MSF_OK;
+  }
+  // device data: points first on the context stream; then the field on the auxiliary stream,
+  // so that binning (which reads only the points) overlaps the field's copy; readers of the
+  // field wait for it (ctx_field_ready)
   MSF_TRY(copy_in(d.pos, pos, sizeof(float) * 3 * P * Tp, ptr_kind, c->stream));
   MSF_TRY(copy_in(d.attr, attr, sizeof(float) * A * P * Tp, ptr_kind, c->stream));
   if (P > 0) {

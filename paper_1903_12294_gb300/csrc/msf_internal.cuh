@@ -168,11 +168,10 @@ struct BinScratch {
   DevBuf hist, offs, cursor, rec_vn, rec_a, absmax, outside, scan_tmp, total, ovf;
   // The records of the last binning stay for the trajectory joins and the feature statistics:
   // the samples grouped by (field step, bucket of 2^rec_logR voxels) in the slot ranges
-  // offs[t][bucket], each its voxel and its point's voxel at the next point step (rec_vn) and
-  // rec_aw attribute words (rec_a); rec_n of them in all.
+  // offs[t][bucket] (offs [T][nb + 1]; offs[t][nb] ends field step t's records), each its voxel
+  // and its point's voxel at the next point step (rec_vn) and rec_aw attribute words (rec_a).
   bool rec_valid = false;
   int rec_logR = 0, rec_nb = 0, rec_aw = 0;
-  uint32_t rec_n = 0;
 };
 
 // Scratch of the clustering (k_cluster.cu): centres, their sums and cells, label buffers for
@@ -256,10 +255,18 @@ struct msf_ctx {
   // back into the context stream with events; created on first use)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // the field's copy in can run on the auxiliary stream beside binning; readers of the field
-  // wait for this event first
+  // the field's copy in can run beside binning; readers of the field wait for this event first
   cudaEvent_t ev_field = nullptr;
   bool field_pending = false;
+  // Host data comes in on a copy stream: the point steps of field steps [chunk_t[g],
+  // chunk_t[g+1]) are in when ev_chunk[g] has passed, so that binning takes each chunk while
+  // the next ones are still on the link; the field follows, then ev_field (which therefore
+  // also covers every point chunk).
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_copy = nullptr;          // the context stream's work before the copies
+  std::vector<cudaEvent_t> ev_chunk;
+  std::vector<int> chunk_t;
+  bool points_pending = false;
 };
 
 namespace msf {
