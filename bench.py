@@ -226,7 +226,7 @@ def run_gpu(args):
     barrier = replicas.barrier
     barrier()
 
-    wl = synth.make(args.config, device=dev)
+    wl = synth.make(args.config, device=dev, **({"T": args.timesteps} if args.timesteps else {}))
     T, nz, ny, nx = wl.field.shape
     V = nx * ny * nz
     tw = wl.t1 - wl.t0
@@ -313,7 +313,9 @@ def run_gpu(args):
     for k, (tot, nl) in ktimes.items():
         e = {"ms_per_step": round(tot / args.steps, 4), "launches_per_step": nl // max(args.steps, 1)}
         if abytes.get(k) and nl:
-            gbs = abytes[k] / (tot / nl * 1e-3) / 1e9
+            # the kernel's algorithmic bytes of one step over its time in one step (a kernel may
+            # launch more than once per step, e.g. a tile pass split in halves)
+            gbs = abytes[k] / (tot / args.steps * 1e-3) / 1e9
             e.update({"algorithmic_bytes": abytes[k], "gb_per_s": round(gbs, 1),
                       "frac": round(gbs / peak, 4)})
         per_kernel[k] = e
@@ -322,6 +324,7 @@ def run_gpu(args):
     ab = abytes.get(name)
     roof = None
     if ab:
+        ab = ab * args.steps / nl  # per launch: the step's bytes over its launches
         ach = ab / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(ach / peak, 4),
@@ -352,15 +355,19 @@ def run_gpu(args):
         if rank == 0:
             hashes = {"field": input_sha256(hf), "pos": input_sha256(hp), "attr": input_sha256(ha)}
 
+        nseg_out = msf.ctypes.c_int64(0)
+
         def e2e_step():
+            # load (host data streamed in chunks, binned as it arrives), bin, then labels and
+            # features in one call whose host labels go down the link beside the feature passes
             ctx.load(hf, hp, ha)
             msf.msf_bin_particles(ctx.h, 0)
-            msf.msf_segment(ctx.h, crit, hl)
-            st = lib.msf_extract_features(ctx.h, msf.ctypes.byref(crit), hl.data_ptr(),
-                                          msf.MSF_HOST, hfeat.ctypes.data, msf.MSF_HOST, fcap,
+            st = lib.msf_segment_features(ctx.h, msf.ctypes.byref(crit), hl.data_ptr(),
+                                          msf.MSF_HOST, msf.ctypes.byref(nseg_out),
+                                          hfeat.ctypes.data, msf.MSF_HOST, fcap,
                                           msf.ctypes.byref(nf_out))
             if st != 0:
-                raise msf.MsfError(st, "msf_extract_features")
+                raise msf.MsfError(st, "msf_segment_features")
             return int(nf_out.value)
 
         for _ in range(max(1, args.warmup)):
@@ -792,7 +799,7 @@ def run_reference(args):
 
     from paper_1903_12294_gb300 import synth
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    wl = synth.make(args.config, device=dev)
+    wl = synth.make(args.config, device=dev, **({"T": args.timesteps} if args.timesteps else {}))
     T, nz, ny, nx = wl.field.shape
     n = 2   # timesteps per step sample
     for _ in range(args.warmup):
@@ -831,6 +838,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--timesteps", type=int, default=0,
+                    help="the workload with this many timesteps (same grid and points per step): "
+                         "a smaller case of the same kernels for profiler captures; 0 = as named")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -252,6 +252,17 @@ int msf_extract_features(msf_ctx* ctx, const msf_criteria* crit, const int32_t* 
                          int labels_kind, msf_feature* out, int out_kind, int64_t cap,
                          int64_t* n_out);
 
+/* msf_segment then msf_extract_features of the same query in one call: labels as msf_segment
+ * writes them (host or device per labels_kind), *n_features the feature count, and the feature
+ * records as msf_extract_features returns them (out, out_kind, cap, *n_out). With host labels
+ * their copy down the link runs beside the feature passes (which read the segmentation the call
+ * keeps, not the labels), so the two overlap. Synchronises the stream. Errors: those of
+ * msf_segment and msf_extract_features (CAPACITY when cap is below the feature count: the labels
+ * are then complete and *n_out holds the count). */
+int msf_segment_features(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels,
+                         int labels_kind, int64_t* n_features, msf_feature* out, int out_kind,
+                         int64_t cap, int64_t* n_out);
+
 /* Many queries in one go: the labels of crits[i] go to labels[i] (device, [t1-t0][nz][ny][nx]
  * int32, caller-owned; may be NULL for an empty window) and, if n_features is not NULL, their
  * feature counts to n_features[i] (host). Results are identical to nq separate msf_segment calls.

@@ -598,6 +598,43 @@ int msf_extract_features(msf_ctx* c, const msf_criteria* crit, const int32_t* la
   return features_run(c, crit, src, labels, out, out_kind, cap, n_out);
 }
 
+int msf_segment_features(msf_ctx* c, const msf_criteria* crit, int32_t* labels, int labels_kind,
+                         int64_t* n_features, msf_feature* out, int out_kind, int64_t cap,
+                         int64_t* n_out) {
+  if (!c || !crit || !n_out || cap < 0) return MSF_ERR_INVALID_ARG;
+  if (labels_kind != MSF_HOST && labels_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
+  if (out_kind != MSF_HOST && out_kind != MSF_DEVICE) return MSF_ERR_INVALID_ARG;
+  if (cap > 0 && !out) return MSF_ERR_INVALID_ARG;
+  MSF_TRY(validate_criteria(c, crit));
+  if (!c->ds.binned) return MSF_ERR_NOT_BINNED;
+  const int64_t N = (int64_t)(crit->t1 - crit->t0) * c->ds.V;
+  if (N > 0 && !labels) return MSF_ERR_INVALID_ARG;
+  MSF_CUDA_TRY(cudaSetDevice(c->device));
+  MSF_TRY(ctx_field_ready(c));
+  int32_t* dst = labels;
+  if (labels_kind == MSF_HOST && N > 0) {
+    MSF_TRY(c->host_staging.ensure(sizeof(int32_t) * N));
+    dst = c->host_staging.as<int32_t>();
+  }
+  MSF_TRY(segment_run(c, crit, dst, n_features, labels));
+  const bool down = labels_kind == MSF_HOST && N > 0;
+  if (down) {
+    // the labels go down the link on the copy stream while the feature passes run (they read
+    // the retained segmentation, not the labels)
+    if (!c->copy) {
+      MSF_CUDA_TRY(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking));
+      MSF_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming));
+    }
+    MSF_CUDA_TRY(cudaEventRecord(c->ev_copy, c->stream));
+    MSF_CUDA_TRY(cudaStreamWaitEvent(c->copy, c->ev_copy, 0));
+    MSF_CUDA_TRY(cudaMemcpyAsync(labels, dst, sizeof(int32_t) * N, cudaMemcpyDeviceToHost,
+                                 c->copy));
+  }
+  const int st = features_run(c, crit, dst, labels, out, out_kind, cap, n_out);
+  if (down) MSF_CUDA_TRY(cudaStreamSynchronize(c->copy));
+  return st;
+}
+
 int msf_segment_batch(msf_ctx* c, int nq, const msf_criteria* crits, int32_t* const* labels,
                       int64_t* n_features) {
   if (!c || nq < 0 || (nq > 0 && (!crits || !labels))) return MSF_ERR_INVALID_ARG;

@@ -31,6 +31,7 @@ MSF_MAX_PRED, MSF_MAX_ATTR = 4, 8
 EXPORTS = ("msf_create", "msf_destroy", "msf_set_stream", "msf_load_timesteps",
            "msf_load_timesteps_mr", "msf_segment_streamed",
            "msf_bin_particles", "msf_get_bins", "msf_segment", "msf_extract_features",
+           "msf_segment_features",
            "msf_set_tile", "msf_set_profiling", "msf_kernel_times", "msf_status_string",
            "msf_segment_field_noalloc", "msf_segment_batch", "msf_server_create",
            "msf_server_submit", "msf_server_poll", "msf_server_release", "msf_server_get_stats",
@@ -158,6 +159,8 @@ def load_library(path: str = LIB_PATH):
                                     ctypes.POINTER(ctypes.c_int64)]
         lib.msf_extract_features.argtypes = [P, ctypes.POINTER(msf_criteria), P, i32, P, i32,
                                              i64, ctypes.POINTER(ctypes.c_int64)]
+        lib.msf_segment_features.argtypes = [P, ctypes.POINTER(msf_criteria), P, i32,
+                                             ctypes.POINTER(i64), P, i32, i64, ctypes.POINTER(i64)]
         lib.msf_set_tile.argtypes = [P, i32, i32, i32]
         lib.msf_set_profiling.argtypes = [P, i32]
         lib.msf_kernel_times.argtypes = [P, P, P, P, i32, i32]
@@ -366,6 +369,21 @@ def msf_extract_features(ctx, crit: msf_criteria, labels, cap=None):
     _check(lib.msf_extract_features(ctx, ctypes.byref(crit), lp, lk, out.ctypes.data, MSF_HOST,
                                     cap, ctypes.byref(n)), "msf_extract_features")
     return out[:int(n.value)]
+
+
+def msf_segment_features(ctx, crit: msf_criteria, labels, cap):
+    """msf_segment into `labels` (host or device tensor) and the features of that labelling in
+    one call (the host labels' copy overlaps the feature passes). Returns (number of features,
+    numpy structured array of the features, dtype FEATURE_DTYPE)."""
+    lib = load_library()
+    lp, lk = _ptr_kind(labels)
+    nf = ctypes.c_int64(0)
+    n = ctypes.c_int64(0)
+    out = np.zeros(max(int(cap), 1), FEATURE_DTYPE)
+    _check(lib.msf_segment_features(ctx, ctypes.byref(crit), lp, lk, ctypes.byref(nf),
+                                    out.ctypes.data, MSF_HOST, int(cap), ctypes.byref(n)),
+           "msf_segment_features")
+    return int(nf.value), out[:int(n.value)]
 
 
 def msf_segment_field_noalloc(field, labels, pred=None, edges=MSF_EDGE_SPATIAL | MSF_EDGE_TEMPORAL,

@@ -229,6 +229,44 @@ def test_host_buffers_and_repeatability(gpu, orc):
         ctx.close()
 
 
+def test_segment_features_in_one_call(gpu, orc):
+    """msf_segment_features (labels and features in one call, the host labels' copy beside the
+    feature passes) gives msf_segment's labels and the oracle's features, with host and device
+    labels, on a pinned host buffer too."""
+    wl = synth.tiny()
+    f, p, a = wl.numpy()
+    ctx = gpu.Context(0)
+    try:
+        ctx.load(f, p, a)
+        ctx.bin()
+        crit = gpu.make_criteria(0, 8, wl.preds)
+        lab_ref, n_ref = ctx.segment(0, 8, wl.preds)
+        fe_ref = ctx.features(0, 8, lab_ref, wl.preds)
+        got = [fe_ref]
+        for host in ("pageable", "pinned", "device"):
+            if host == "device":
+                lab = torch.full((8, 32, 32, 32), -5, dtype=torch.int32, device="cuda")
+            else:
+                lab = torch.full((8, 32, 32, 32), -5, dtype=torch.int32)
+                if host == "pinned":
+                    lab = lab.pin_memory()
+            nf, fe = gpu.msf_segment_features(ctx.h, crit, lab, len(fe_ref) + 3)
+            assert nf == n_ref and len(fe) == len(fe_ref)
+            assert torch.equal(lab.cuda(), lab_ref)
+            got.append(fe)
+        with pytest.raises(gpu.MsfError):  # capacity below the feature count
+            gpu.msf_segment_features(ctx.h, crit, torch.empty((8, 32, 32, 32), dtype=torch.int32),
+                                     1)
+    finally:
+        ctx.close()
+    # integer statistics are exact; the fp64 sums add in L2 atomics in no fixed order, so the
+    # floating-point ones match the oracle within the parity tolerance, run by run
+    o = orc.run_all(f, p, a, 0, 8, wl.preds)
+    assert n_ref == o[2]
+    for fe in got:
+        check_features(fe, o[3], a.shape[1])
+
+
 def test_errors_are_status_codes(gpu):
     ctx = gpu.Context(0)
     try:
