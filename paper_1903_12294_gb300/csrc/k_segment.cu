@@ -704,8 +704,10 @@ __global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArg
 // trajectory joins (one point step per field step) and the point statistics walk them instead
 // of the points in id order: the 32 records of a warp lie in one bucket (a few rows of the
 // grid), so their component lookups hit cached rows. Block (x, y) of a pass takes records
-// [x * kRecChunk, (x + 1) * kRecChunk) of its field step.
-constexpr int kRecChunk = 32768;
+// [x * chunk, (x + 1) * chunk) of its field step: large chunks (few cache flushes per block)
+// where there are many records, smaller ones so that a pass still has enough blocks to fill
+// the GPU where there are few.
+constexpr uint32_t kRecChunkMax = 32768, kRecChunkMin = 2048;
 
 struct RecView {
   const uint2* rec_vn;    // [records] voxel, the point's voxel at the next point step (or -1)
@@ -713,12 +715,23 @@ struct RecView {
   const uint32_t* offs;   // [T][nb + 1] first record of each (field step, bucket); [t][nb]
                           // ends field step t's records
   int nb, aw;
+  uint32_t chunk;         // records per block
 };
 
 static RecView rec_view(const msf_ctx* ctx) {
   const BinScratch& B = ctx->bin;
   return RecView{B.rec_vn.as<uint2>(), B.rec_a.as<float>(), B.offs.as<uint32_t>(), B.rec_nb,
-                 B.rec_aw};
+                 B.rec_aw, kRecChunkMax};
+}
+
+// Records per block for a pass over `steps` field steps of at most `per_step` records each: at
+// least eight blocks per SM, within [kRecChunkMin, kRecChunkMax].
+static uint32_t rec_chunk(int64_t per_step, int steps, int sm_count) {
+  const int64_t want = (int64_t)sm_count * 8;
+  const int64_t blocks_per_step = std::max<int64_t>(1, (want + steps - 1) / std::max(steps, 1));
+  int64_t c = (per_step + blocks_per_step - 1) / blocks_per_step;
+  c = (c + 255) / 256 * 256;
+  return (uint32_t)std::min<int64_t>(kRecChunkMax, std::max<int64_t>(kRecChunkMin, c));
 }
 
 // records [b0, b1) of block x of field step t; false when the block has none
@@ -726,9 +739,9 @@ __device__ __forceinline__ bool rec_block(const RecView& rv, int t, uint32_t& b0
   const int64_t h = (int64_t)t * (rv.nb + 1);
   const uint32_t rb = __ldg(rv.offs + h);
   const uint32_t re = __ldg(rv.offs + h + rv.nb);
-  b0 = rb + blockIdx.x * (uint32_t)kRecChunk;
+  b0 = rb + blockIdx.x * rv.chunk;
   if (b0 >= re) return false;
-  b1 = min(re, b0 + (uint32_t)kRecChunk);
+  b1 = min(re, b0 + rv.chunk);
   return true;
 }
 
@@ -1214,8 +1227,9 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
     if (rec_links) {
       const int ta = c0 * kLinkSteps, tb = std::min(c1 * kLinkSteps, g.tw - 1);
       if (tb <= ta) return;
-      const RecView rv = rec_view(ctx);
-      dim3 grid((unsigned)std::max<int64_t>(1, (a.P + kRecChunk - 1) / kRecChunk),
+      RecView rv = rec_view(ctx);
+      rv.chunk = rec_chunk(a.P, tb - ta, ctx->sm_count);
+      dim3 grid((unsigned)std::max<int64_t>(1, (a.P + rv.chunk - 1) / rv.chunk),
                 (unsigned)(tb - ta));
       if (spatial) k_links_rec<true><<<grid, 256, 0, ls>>>(a, rv, ta);
       else k_links_rec<false><<<grid, 256, 0, ls>>>(a, rv, ta);
@@ -1467,7 +1481,7 @@ __global__ void __launch_bounds__(256, 4) k_feat_points(const __grid_constant__ 
 // rows, and its lanes mostly share one feature (the butterfly path of reduce_samples). The
 // samples are those of every point step falling in the window's field steps that binning placed
 // inside the grid: the same as the per-point pass takes. Block (x, y) takes records
-// [x * kRecChunk, (x + 1) * kRecChunk) of window field step y.
+// [x * chunk, (x + 1) * chunk) of window field step y.
 template <bool SPATIAL>
 __global__ void __launch_bounds__(256) k_feat_points_rec(const __grid_constant__ SegArgs a,
                                                          FeatAcc acc,
@@ -1561,11 +1575,12 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
     ScopedKernel k(ctx, "k_feat_points", ctx->aux);
     if (recs) {
       const BinScratch& B = ctx->bin;
-      const RecView rv = rec_view(ctx);
+      RecView rv = rec_view(ctx);
       int rmax = 1;  // most point steps in one field step of the window
       for (int t = g.t0; t < g.t0 + g.tw; ++t)
         rmax = std::max(rmax, d.h_pj0[t + 1] - d.h_pj0[t]);
-      const int64_t nx = (a.P * rmax + kRecChunk - 1) / kRecChunk;
+      rv.chunk = rec_chunk(a.P * rmax, g.tw, ctx->sm_count);
+      const int64_t nx = (a.P * rmax + rv.chunk - 1) / rv.chunk;
       dim3 grid((unsigned)std::max<int64_t>(nx, 1), (unsigned)g.tw);
       if (spatial) k_feat_points_rec<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, rv);
       else k_feat_points_rec<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, rv);

@@ -459,12 +459,24 @@ __device__ __forceinline__ unsigned float_key(float f) {
 
 // float -> double by bit manipulation (exact); zero, subnormal, inf and NaN take the slow path.
 __device__ __forceinline__ double f2d(float f) {
+  // fp32 -> fp64 by integer operations only (every fp32 value is exact in fp64; the hardware
+  // conversion would issue on the narrow fp64 pipe)
   const uint32_t b = __float_as_uint(f);
-  const uint32_t e = (b >> 23) & 0xFFu;
-  if ((b & 0x7FFFFFFFu) == 0u) return 0.0;
-  if (e == 0u || e == 0xFFu) return (double)f;
-  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
-  return __hiloint2double((int)hi, (int)((b & 0x7u) << 29));
+  const uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  uint32_t hi, lo;
+  if (e != 0u) {  // normal, or inf/nan (exponent all ones in both formats)
+    hi = sign | ((e == 0xFFu ? 0x7FFu : e + 896u) << 20) | (m >> 3);
+    lo = (m & 7u) << 29;
+  } else if (m == 0u) {  // signed zero
+    hi = sign;
+    lo = 0u;
+  } else {  // subnormal m * 2^-149: leading one at bit p, exponent p - 149
+    const int p = 31 - __clz((int)m);
+    const unsigned long long mant = ((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFull;
+    hi = sign | ((uint32_t)(p + 874) << 20) | (uint32_t)(mant >> 32);
+    lo = (uint32_t)mant;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // s + e == a + b exactly (Knuth's TwoSum, IEEE fp32, no reassociation).
