@@ -47,7 +47,10 @@ def peaks():
 # the same kernel code on the same workload (profiles/kernels_mid_step.md): {(config, kernel):
 # bytes}. An entry is removed whenever its kernel changes.
 TRAFFIC = {
-    (2, "k_bin_reduce"): 406_967_296 + 744_210_944,
+    # ncu DRAM bytes (read + write) of one launch, from a single-kernel capture of the unchanged
+    # kernel (profiles/); combustion: the 4-timestep capture (--timesteps 4) scaled by 6 to the
+    # 24-step launch (a launch's records and voxels grow in proportion to its field steps)
+    (3, "k_feat_points"): (600_034_560 + 9_865_984) * 6,
 }
 
 
