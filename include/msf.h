@@ -228,10 +228,8 @@ int msf_get_bins(msf_ctx* ctx, int32_t* key, int32_t* count, float* mean, int64_
  * INVALID_ARG (window outside [0,T], t1 < t0, n_pred outside [0,4], bad source/op/attribute,
  * COUNT threshold outside int32, unknown edge bits), TOO_LARGE ((t1-t0)*nx*ny*nz >= 2^31),
  * OUT_OF_MEMORY, CUDA. t1 == t0 is valid: nothing is written and n_features is 0.
- * When the previous segmentation's features were extracted (msf_extract_features on it), the
- * trajectory joins of this one also keep every point sample's component (4 bytes per sample of
- * the window), so that the next extraction's point statistics need no lookups; a caller that
- * only segments does not pay for that store. */
+ * With one point step per field step the trajectory joins walk the binning's records (kept
+ * until the next msf_load_timesteps or msf_bin_particles). */
 int msf_segment(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int labels_kind,
                 int64_t* n_features);
 

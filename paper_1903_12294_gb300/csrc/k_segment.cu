@@ -16,8 +16,10 @@
 //   k_hook     one CTA per tile, one thread per segment: joins components across the tile's
 //              lower faces (x, y, z and the t-chunk boundary) with a global union-find on the
 //              component table, each distinct component pair once per tile.
-//   k_links    one thread per (point, chunk of 8 steps): joins the components of key[t][p] and
-//              key[t+1][p], and records the point samples that fall in member voxel-timesteps.
+//   k_links    trajectory joins: on a binned dataset with one point step per field step, from
+//              the binning's records in bucket order (each record holds its voxel at t and its
+//              point's voxel at t+1); otherwise one thread per (point, chunk of 8 point steps)
+//              joining the components of key[j][p] and key[j+1][p].
 //   k_flatten  one CTA per tile: path-compresses every component to its root and reduces the
 //              smallest index onto the root; counts roots (= features).
 //   k_final    one CTA per tile: resolves each run's label in shared memory and streams the
@@ -52,9 +54,6 @@ struct SegArgs {
   int2* tileinfo;  // (runs, components) per tile
   int32_t* labels;
   unsigned long long* counters;  // [0] features, [1] error flags
-  uint32_t* pcomp;  // [nj][P] component of every point sample of the window, kNoComp off the
-                    // members; written by the trajectory joins, read by the point statistics
-                    // (null: not kept)
   int tile0;            // first tile of a tile-pass launch that covers part of the tiles
   int chunk0, chunk1;   // link chunks [chunk0, chunk1) of a join launch (chunk1 0: to the end)
   // the window's point steps (points may be sampled more often than the field): absolute point
@@ -677,12 +676,6 @@ __device__ __forceinline__ void links_chunk(const SegArgs& a, int64_t p, int c0)
     if (comp[j] != kNoComp && comp[j + 1] != kNoComp && comp[j] != comp[j + 1] && !temporal_edge)
       gunion(a.cparent, comp[j], comp[j + 1]);
   }
-  if (a.pcomp) {  // each point step once: the last chunk also keeps the window's last one
-    const int nw = c0 + L >= a.nj - 1 ? nk : L;
-#pragma unroll
-    for (int j = 0; j <= L; ++j)
-      if (j < nw) __stcs(a.pcomp + (int64_t)(c0 + j) * a.P + p, comp[j]);
-  }
 }
 
 // chunks [chunk0, chunk1) of the window's point steps (chunk1 0: to the end) in grid y
@@ -1206,17 +1199,6 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
     tiles(0, g.ntiles);
   }
   MSF_CUDA_TRY(cudaGetLastError());
-  // When the last segmentation's features were extracted, the joins also keep every point
-  // sample's component for the next extraction's point statistics (which then need no lookups);
-  // a caller that only segments does not pay for the store.
-  SegState& LS = ctx->last;
-  LS.has_pcomp = false;
-  const bool keep = traj && ctx->keep_pcomp && !(ctx->bin.rec_valid && ds.binned);
-  ctx->keep_pcomp = false;
-  if (keep) {
-    MSF_TRY(LS.pcomp.ensure(sizeof(uint32_t) * (size_t)a.P * (size_t)std::max(a.nj, 1)));
-    a.pcomp = LS.pcomp.as<uint32_t>();
-  }
   const int nchunk = (a.nj - 1 + kLinkSteps - 1) / kLinkSteps;
   // With one point step per field step and the dataset's records at hand, the joins walk the
   // records: chunk c's joins are those from window field steps [c L, c L + L).
@@ -1283,7 +1265,6 @@ int segment_run(msf_ctx* ctx, const msf_criteria* crit, int32_t* labels, int64_t
   if (h[1]) return MSF_ERR_INTERNAL;
   if (nfeat) *nfeat = (int64_t)h[0];
   SegState& L = ctx->last;
-  L.has_pcomp = keep;
   L.valid = labels_user != nullptr;
   L.crit = *crit;
   L.labels_user = labels_user;
@@ -1396,84 +1377,6 @@ __global__ void __launch_bounds__(256) k_feat_vox(const __grid_constant__ SegArg
   s_tab.flush(acc);
 }
 
-// Point statistics: one thread per point and chunk of kLinkSteps point steps of the window,
-// (point step, point) in order so that keys are read coalesced; a sample counts for the feature
-// of the component of its voxel-timestep (its point step's field step), if that is a member.
-// Each warp packs its member samples into shared memory and reduces them 32 at a time (the
-// warp-level reduction wants full warps).
-template <bool SPATIAL>
-__global__ void __launch_bounds__(256, 4) k_feat_points(const __grid_constant__ SegArgs a,
-                                                        FeatAcc acc,
-                                                        const int32_t* __restrict__ cfid,
-                                                        const float* __restrict__ attr) {
-  constexpr int L = kLinkSteps;
-  __shared__ int2 s_buf[8][32 * L];  // per warp: (feature, step * 32 + lane)
-  __shared__ HotCache s_hot[8];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t pbase = (int64_t)blockIdx.x * 256 + w * 32;
-  const int64_t p = pbase + lane;
-  const bool in = p < a.P;
-  const int nj = a.nj;
-  const int nchunk = (nj + L - 1) / L;
-  hot_clear(s_hot[w]);
-  for (int c = blockIdx.y; c < nchunk; c += gridDim.y) {
-    const int s0 = c * L;
-    int32_t fid[L];
-    int n = 0;
-    if (a.pcomp) {  // components kept by the trajectory joins: no lookups
-      uint32_t cp[L];
-#pragma unroll
-      for (int j = 0; j < L; ++j)
-        cp[j] = (in && s0 + j < nj) ? __ldcs(a.pcomp + (int64_t)(s0 + j) * a.P + p) : kNoComp;
-#pragma unroll
-      for (int j = 0; j < L; ++j) {
-        fid[j] = cp[j] != kNoComp ? __ldg(cfid + cp[j]) : -1;
-        n += fid[j] >= 0;
-      }
-    } else {
-      int32_t key[L];
-#pragma unroll
-      for (int j = 0; j < L; ++j)
-        key[j] = (in && s0 + j < nj) ? __ldcs(a.key + ((int64_t)a.j0 + s0 + j) * a.P + p) : -1;
-#pragma unroll
-      for (int j = 0; j < L; ++j) {
-        fid[j] = -1;
-        if (key[j] >= 0) {
-          const int st = __ldg(a.fstep + a.j0 + s0 + j) - a.g.t0;
-          const int64_t cj = comp_of<SPATIAL>(a, st, key[j]);
-          if (cj >= 0) fid[j] = __ldg(cfid + cj);
-        }
-        n += fid[j] >= 0;
-      }
-    }
-    // warp exclusive scan of the member counts -> packed positions
-    int x = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    const int total = __shfl_sync(0xFFFFFFFFu, x, 31);
-    int pos = x - n;
-#pragma unroll
-    for (int j = 0; j < L; ++j)
-      if (fid[j] >= 0) s_buf[w][pos++] = make_int2(fid[j], (j << 5) | lane);
-    __syncwarp();
-    for (int b = 0; b < total; b += 32) {
-      const int i = b + lane;
-      const bool ok = i < total;
-      const int2 e = ok ? s_buf[w][i] : make_int2(-1, 0);
-      const int j = e.y >> 5;
-      accumulate_samples_hot(acc, s_hot[w], ok, e.x,
-                             attr + (((int64_t)a.j0 + s0 + j) * acc.A) * a.P + pbase + (e.y & 31),
-                             a.P);
-      __syncwarp();  // the cached sums one reduction at a time
-    }
-    __syncwarp();
-  }
-  hot_flush(acc, s_hot[w]);
-}
-
 // Point statistics from the binned records (while they hold the loaded dataset's binning): the
 // samples of the window's field steps, grouped by (field step, bucket of consecutive voxels),
 // each with its voxel and its attributes side by side. A warp takes 32 consecutive records:
@@ -1554,11 +1457,9 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
   const bool spatial = L.crit.edges & MSF_EDGE_SPATIAL;
   SegArgs a;
   MSF_TRY(seg_args(ctx, g, spatial, &a));
+  // a binned dataset with points always has its records (binning leaves them valid until the
+  // next load or binning)
   const bool recs = ctx->bin.rec_valid && ctx->ds.binned;
-  if (L.has_pcomp) a.pcomp = L.pcomp.as<uint32_t>();
-  // features follow segmentations here: keep components next time (unless the binned records
-  // serve the point statistics)
-  ctx->keep_pcomp = !recs;
   MSF_TRY(L.cfid.ensure(sizeof(int32_t) * (size_t)g.ntiles * g.cmax));
   int32_t* cfid = L.cfid.as<int32_t>();
   cudaStream_t s = ctx->stream;
@@ -1570,26 +1471,18 @@ int seg_feature_stats(msf_ctx* ctx, const RankArrays& rk, const FeatAcc& acc) {
   // voxel and point statistics only add into the accumulators: the point pass runs beside the
   // voxel pass on the auxiliary stream
   const bool points = a.P > 0 && d.A > 0 && a.nj > 0;
+  if (points && !recs) return MSF_ERR_INTERNAL;  // not reached: see above
   if (points) {
     MSF_TRY(ctx_fork(ctx));
     ScopedKernel k(ctx, "k_feat_points", ctx->aux);
-    if (recs) {
-      const BinScratch& B = ctx->bin;
-      RecView rv = rec_view(ctx);
-      int rmax = 1;  // most point steps in one field step of the window
-      for (int t = g.t0; t < g.t0 + g.tw; ++t)
-        rmax = std::max(rmax, d.h_pj0[t + 1] - d.h_pj0[t]);
-      rv.chunk = rec_chunk(a.P * rmax, g.tw, ctx->sm_count);
-      const int64_t nx = (a.P * rmax + rv.chunk - 1) / rv.chunk;
-      dim3 grid((unsigned)std::max<int64_t>(nx, 1), (unsigned)g.tw);
-      if (spatial) k_feat_points_rec<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, rv);
-      else k_feat_points_rec<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, rv);
-    } else {
-      const int64_t nchunk = (a.nj + kLinkSteps - 1) / kLinkSteps;
-      dim3 grid((unsigned)((a.P + 255) / 256), (unsigned)std::min<int64_t>(nchunk, 65535));
-      if (spatial) k_feat_points<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
-      else k_feat_points<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, d.attr.as<float>());
-    }
+    RecView rv = rec_view(ctx);
+    int rmax = 1;  // most point steps in one field step of the window
+    for (int t = g.t0; t < g.t0 + g.tw; ++t) rmax = std::max(rmax, d.h_pj0[t + 1] - d.h_pj0[t]);
+    rv.chunk = rec_chunk(a.P * rmax, g.tw, ctx->sm_count);
+    const int64_t nx = (a.P * rmax + rv.chunk - 1) / rv.chunk;
+    dim3 grid((unsigned)std::max<int64_t>(nx, 1), (unsigned)g.tw);
+    if (spatial) k_feat_points_rec<true><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, rv);
+    else k_feat_points_rec<false><<<grid, 256, 0, ctx->aux>>>(a, acc, cfid, rv);
   }
   {
     ScopedKernel k(ctx, "k_feat_vox");

@@ -351,7 +351,6 @@ void msf_destroy(msf_ctx* c) {
     b->release();
   c->bin.rec_valid = false;
   c->last.cfid.release();
-  c->last.pcomp.release();
   for (DevBuf* b : {&c->clu.centers, &c->clu.prev, &c->clu.sums, &c->clu.counts,
                     &c->clu.cell_start, &c->clu.cell_cursor, &c->clu.cell_items, &c->clu.flags,
                     &c->clu.scan_tmp, &c->clu.flab, &c->clu.plab, &c->clu.pcell_start,

@@ -142,8 +142,6 @@ struct SegState {
   int maxr = 0;
   int64_t n_features = 0;
   DevBuf cfid;                        // feature index of every component
-  DevBuf pcomp;                       // component of every point sample (trajectory joins)
-  bool has_pcomp = false;             // pcomp holds this segmentation's components
 };
 
 // Device arena and pinned host staging of msf_segment_batch (grow-only).
@@ -242,7 +240,6 @@ struct msf_ctx {
   uint64_t epoch = 1;        // bumped whenever the dataset or its binning changes
   int tile_by = 0, tile_bz = 0, tile_bt = 0;
   int sched = -1;                    // msf_segment schedule set by msf_set_schedule (-1: auto)
-  bool keep_pcomp = false;  // the next msf_segment keeps point components (features followed)
   int batch_by = 0, batch_bz = 0, batch_bt = 0;  // tile of the batched form (0: fixed rule)
   // MSF_SCHED_* of the batched form: criterion fused into the tile pass, one launch per phase
   // (the batch autotuner also tries the persistent launch)
