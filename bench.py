@@ -50,7 +50,7 @@ TRAFFIC = {
     # ncu DRAM bytes (read + write) of one launch, from a single-kernel capture of the unchanged
     # kernel (profiles/); combustion: the 4-timestep capture (--timesteps 4) scaled by 6 to the
     # 24-step launch (a launch's records and voxels grow in proportion to its field steps)
-    (3, "k_feat_points"): (600_034_560 + 9_865_984) * 6,
+    (3, "k_feat_points"): (600_658_176 + 10_216_960) * 6,
 }
 
 

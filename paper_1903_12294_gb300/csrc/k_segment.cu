@@ -629,11 +629,21 @@ __global__ void __launch_bounds__(256, 4) k_hook(const __grid_constant__ SegArgs
 template <bool SPATIAL, bool CG = false>
 __device__ __forceinline__ int64_t comp_of(const SegArgs& a, int tw, int32_t v) {
   const Geometry& g = a.g;
-  uint32_t yz, x, z, y;
-  g.fnx.divmod((uint32_t)v, yz, x);
-  g.fny.divmod(yz, z, y);
-  const uint2 e = ld_seg<CG>(a.seg + seg_index(g, tw, (int)z, (int)y, (int)(x >> 5)));
-  const int b = x & 31;
+  int64_t gs;
+  int b;
+  if ((g.nx & 31) == 0) {
+    // rows are whole segments: the segment table's order (step, z, y, x / 32) is the voxel
+    // order cut into 32-voxel pieces
+    gs = (int64_t)tw * ((int64_t)g.nz * g.ny * g.nxs) + (v >> 5);
+    b = v & 31;
+  } else {
+    uint32_t yz, x, z, y;
+    g.fnx.divmod((uint32_t)v, yz, x);
+    g.fny.divmod(yz, z, y);
+    gs = seg_index(g, tw, (int)z, (int)y, (int)(x >> 5));
+    b = x & 31;
+  }
+  const uint2 e = ld_seg<CG>(a.seg + gs);
   if (!((e.x >> b) & 1u)) return -1;
   return ld_seg<CG>(a.runcomp + e.y + run_index(run_starts(e.x, SPATIAL), b));
 }
