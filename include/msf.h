@@ -195,9 +195,9 @@ int msf_load_timesteps(msf_ctx* ctx, int nx, int ny, int nz, int T, const float*
  * scale counts all P * Tp samples. msf_cluster takes every point step of its window, the i-th
  * (0-based) of the r point steps of field step f at time f + (i + 0.5) / r. The point labels of
  * msf_cluster_stats and the voxel label space of msf_split_trajectories take one point step per
- * field step and return MSF_ERR_INVALID_ARG on such a dataset. Errors: those of msf_load_timesteps; INVALID_ARG (a
- * map that decreases or leaves [0, T), Tp < 1 with a map, Tp != T without), TOO_LARGE
- * (Tp > 65535). */
+ * field step and return MSF_ERR_INVALID_ARG on such a dataset. Errors: those of
+ * msf_load_timesteps; INVALID_ARG (a map that decreases or leaves [0, T), Tp < 1 with a map,
+ * Tp != T without), TOO_LARGE (Tp > 65535). */
 int msf_load_timesteps_mr(msf_ctx* ctx, int nx, int ny, int nz, int T, const float* field,
                           int64_t P, int A, int Tp, const float* pos, const float* attr,
                           const int32_t* field_step, int ptr_kind);
@@ -206,8 +206,13 @@ int msf_load_timesteps_mr(msf_ctx* ctx, int nx, int ny, int nz, int T, const flo
  * ((z*ny + y)*nx + x, or -1 when the position is non-finite or outside [0,n) in any axis),
  * count[t][v], the fixed-point sums and the fp32 means of every attribute (see
  * msf_bin_stats). With MSF_BIN_KEEP_SUMQ the int64 sums are kept for msf_get_bins. `stats`
- * may be NULL. Synchronises the stream. Errors: NOT_LOADED, INVALID_ARG (unknown flag),
- * OUT_OF_MEMORY, CUDA. */
+ * may be NULL. After a load from host memory the field steps are binned chunk by chunk as their
+ * point steps arrive (the last chunk, and the per-voxel means, once all have). The records of
+ * this binning (every in-grid sample with its voxel, the same point's voxel at the next point
+ * step and its attributes, grouped by field step and voxel range) stay until the next load or
+ * binning: the trajectory joins of msf_segment and the point statistics of the features walk
+ * them. Synchronises the stream. Errors: NOT_LOADED, INVALID_ARG (unknown flag), OUT_OF_MEMORY,
+ * TOO_LARGE (P * Tp >= 2^32), TIMEOUT (a copy wait gave up), CUDA. */
 int msf_bin_particles(msf_ctx* ctx, unsigned flags, msf_bin_stats* stats);
 
 /* Copy the binning results out (each pointer may be NULL): key [T][P] int32 ([Tp][P] for a
