@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(256, 4) k_links(const __grid_constant__ SegArg
 // [x * chunk, (x + 1) * chunk) of its field step: large chunks (few cache flushes per block)
 // where there are many records, smaller ones so that a pass still has enough blocks to fill
 // the GPU where there are few.
-constexpr uint32_t kRecChunkMax = 32768, kRecChunkMin = 2048;
+constexpr uint32_t kRecChunkMax = 32768, kRecChunkMin = 1024;
 
 struct RecView {
   const uint2* rec_vn;    // [records] voxel, the point's voxel at the next point step (or -1)
@@ -727,8 +727,8 @@ static RecView rec_view(const msf_ctx* ctx) {
                  B.rec_aw, kRecChunkMax};
 }
 
-// Records per block for a pass over `steps` field steps of at most `per_step` records each: at
-// least eight blocks per SM, within [kRecChunkMin, kRecChunkMax].
+// Records per block for a pass of `steps` block rows (field steps, or batch items) over at most
+// `per_step` records each: at least eight blocks per SM, within [kRecChunkMin, kRecChunkMax].
 static uint32_t rec_chunk(int64_t per_step, int steps, int sm_count) {
   const int64_t want = (int64_t)sm_count * 8;
   const int64_t blocks_per_step = std::max<int64_t>(1, (want + steps - 1) / std::max(steps, 1));
@@ -755,12 +755,10 @@ __device__ __forceinline__ bool rec_block(const RecView& rv, int t, uint32_t& b0
 // each distinct pair in a warp is joined once.
 constexpr int kRecLinkPer = 4;
 
+// the joins of records [b0, b1) of window field step tw (a warp-uniform loop)
 template <bool SPATIAL>
-__global__ void __launch_bounds__(256) k_links_rec(const __grid_constant__ SegArgs a,
-                                                   const __grid_constant__ RecView rv, int ta) {
-  const int tw = ta + (int)blockIdx.y;
-  uint32_t b0, b1;
-  if (!rec_block(rv, a.g.t0 + tw, b0, b1)) return;
+__device__ __forceinline__ void links_rec_range(const SegArgs& a, const RecView& rv, int tw,
+                                                uint32_t b0, uint32_t b1) {
   const bool temporal = (a.edges & MSF_EDGE_TEMPORAL) != 0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (uint32_t base = b0 + 32u * kRecLinkPer * w; base < b1;
@@ -787,6 +785,15 @@ __global__ void __launch_bounds__(256) k_links_rec(const __grid_constant__ SegAr
       }
     }
   }
+}
+
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256) k_links_rec(const __grid_constant__ SegArgs a,
+                                                   const __grid_constant__ RecView rv, int ta) {
+  const int tw = ta + (int)blockIdx.y;
+  uint32_t b0, b1;
+  if (!rec_block(rv, a.g.t0 + tw, b0, b1)) return;
+  links_rec_range<SPATIAL>(a, rv, tw, b0, b1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1747,6 +1754,26 @@ __global__ void __launch_bounds__(256, 4) k_links_batch(const __grid_constant__ 
   if (p < s_args.P) links_chunk<SPATIAL>(s_args, p, b.row_tw[item]);
 }
 
+// The same joins from the binned records, for a dataset with one point step per field step:
+// item (query, first window step c0) takes the records of the query's window field steps
+// [c0, c0 + kLinkSteps) that have a next step in its window, block x the x-th chunk of each.
+template <bool SPATIAL>
+__global__ void __launch_bounds__(256, 4) k_links_batch_rec(const __grid_constant__ BatchPlan b,
+                                                         const __grid_constant__ RecView rv) {
+  __shared__ __align__(16) SegArgs s_args;
+  const int64_t item = b.row0 + blockIdx.y;
+  load_args(&s_args, b.qargs + b.row_q[item]);
+  __syncthreads();
+  const int c0 = b.row_tw[item];
+  for (int st = 0; st < kLinkSteps; ++st) {
+    const int tw = c0 + st;
+    if (tw >= s_args.g.tw - 1) break;  // block-uniform
+    uint32_t b0, b1;
+    if (!rec_block(rv, s_args.g.t0 + tw, b0, b1)) continue;  // block-uniform
+    links_rec_range<SPATIAL>(s_args, rv, tw, b0, b1);
+  }
+}
+
 // query = blockIdx.y; x strides over that query's tiles
 __global__ void __launch_bounds__(256) k_flatten_batch(const __grid_constant__ BatchPlan b) {
   __shared__ int s_n;
@@ -2278,14 +2305,25 @@ static int launch_group(msf_ctx* ctx, const BatchGroup& gr, const BatchPlan& b, 
   const bool side = nrows > 0 && sp.aux;
   if (side) MSF_TRY(sp.fork(s));
   const cudaStream_t ls = side ? sp.aux : s;
+  // with one point step per field step the joins walk the binned records (as msf_segment's do)
+  const bool rec_links = ctx->bin.rec_valid && d.binned && !d.multirate;
   for (int64_t r0 = 0; r0 < nrows; r0 += 65535) {  // gridDim.y limit per launch
     ScopedKernel k(ctx, "k_links_batch", ls, timed);
-    const int64_t gx = (d.P + 255) / 256;
-    dim3 grid((unsigned)std::max<int64_t>(gx, 1), (unsigned)std::min<int64_t>(65535, nrows - r0));
+    const int64_t ny = std::min<int64_t>(65535, nrows - r0);
     BatchPlan br = b;
     br.row0 = r0;
-    if (spatial) k_links_batch<true><<<grid, 256, 0, ls>>>(br);
-    else k_links_batch<false><<<grid, 256, 0, ls>>>(br);
+    if (rec_links) {
+      RecView rv = rec_view(ctx);
+      rv.chunk = rec_chunk(d.P, (int)ny, ctx->sm_count);  // a block row per item
+      dim3 grid((unsigned)std::max<int64_t>(1, (d.P + rv.chunk - 1) / rv.chunk), (unsigned)ny);
+      if (spatial) k_links_batch_rec<true><<<grid, 256, 0, ls>>>(br, rv);
+      else k_links_batch_rec<false><<<grid, 256, 0, ls>>>(br, rv);
+    } else {
+      const int64_t gx = (d.P + 255) / 256;
+      dim3 grid((unsigned)std::max<int64_t>(gx, 1), (unsigned)ny);
+      if (spatial) k_links_batch<true><<<grid, 256, 0, ls>>>(br);
+      else k_links_batch<false><<<grid, 256, 0, ls>>>(br);
+    }
   }
   // 2D grids: y = query (<= 65535 per group), x = tile
   if (any_link) {
