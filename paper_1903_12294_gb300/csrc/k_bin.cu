@@ -36,9 +36,6 @@
 
 namespace msf {
 
-int scan_exclusive_u32(msf_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, DevBuf& tmp,
-                       uint32_t* total);
-
 constexpr int kBinPer = 4;             // samples per thread in the per-sample passes
 constexpr int kBinNT = 512;            // threads per CTA of the sort and reduce passes
 constexpr int kHistSmem = 8192;        // buckets counted in shared memory (else global atomics)
